@@ -1,0 +1,316 @@
+#!/usr/bin/env python3
+"""Benchmark: matmul-sumcheck proofs of a LoRA fine-tuning step on GB300.
+
+Metric: matmul MACs proved per second (sum over the step's products of
+m.k.n, divided by wall time), and ms per LoRA-step proof, batched (one plan,
+CUDA-graph replay of the whole step) against the unbatched per-matmul path.
+Every proof is bit-exact with the oracle (tests/test_gpu_parity.py,
+tests/test_gpu_fullsize.py).
+
+Default workload: the 7B-shaped step -- 32 layers x {q,k,v,o}, hidden 4096,
+sequence 512, LoRA rank per layer from {8, 16, 64}; eight products per
+projection (1024 proofs).  Synthetic int16 fixed-point tensors (the paper's
+LLaMA weights and C4 data are not available).  Inputs (~5.4 GB) are far
+larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank proves its own full step (independent proofs, no
+collective: weak scaling); rank 0 prints one JSON line.
+"""
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2508_21393_gb300 import workload as W  # noqa: E402
+
+METRIC = "matmul MACs proved/sec and ms per LoRA step proof (batched vs unbatched), bit-exact"
+UNIT = "MAC/s"
+SMS = 152
+SM_MAX_MHZ = 2070.0
+# IMAD.WIDE.U32 (32x32->64 multiply-add) issue rate per SM per clock used for
+# the ALU roofline of the int16 fold: 64 32-bit integer multiply-adds per SM
+# per clock, a wide (64-bit result) one taking two of them.
+MADWIDE_PER_SM_CLK = 32
+WORKLOADS = {
+    "7b-step": "batched 7B-shaped LoRA step: 32 layers x {q,k,v,o}, hidden 4096, seq 512, ranks {8,16,64}",
+    "7b-proj": "one 7B-shaped LoRA projection, n=1024, d=k=4096, r=16, eight products",
+    "13b-step": "batched 13B-shaped LoRA step: 40 layers x {q,k,v,o}, hidden 5120, seq 2048, rank 16",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="7b-step", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-unbatched", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-projections", type=int, default=2)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def step_jobs(kind, seed):
+    projs = W.make_step(kind, seed)
+    jobs = [j for t in projs for j in W.projection_products(t, seed)]
+    return projs, jobs
+
+
+def oracle_sample(kind, seed, nproj):
+    """Time the oracle on the first `nproj` projections of the workload."""
+    import oracle
+    spec = W.step_layers(kind, seed)[:nproj]
+    projs = [W.lora_projection(seed, *s) for s in spec]
+    jobs = [j for t in projs for j in W.projection_products(t, seed)]
+    macs = sum(W.macs(j) for j in jobs)
+    t0 = time.perf_counter()
+    for j in jobs:
+        oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"])
+    dt = time.perf_counter() - t0
+    return macs / dt, dt, len(jobs), macs
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(dev)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(", ") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def run_reference(args, rank, world):
+    """The oracle (pure-Python CPU prover), timed on this host, as the reference arm."""
+    if rank != 0:
+        return
+    cores = 1
+    per_step = []
+    macs_step = None
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, W.GLOBAL_SEED, 1)
+    for _ in range(args.steps):
+        rate, dt, nj, macs = oracle_sample(args.workload, W.GLOBAL_SEED, 1)
+        per_step.append(dt)
+        macs_step = macs
+    total = sum(per_step)
+    value = macs_step * args.steps / total
+    sample = f"1 projection (8 proofs, {macs_step} MACs) of the {args.workload} workload per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int (Fr, 255-bit)",
+        "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    # The oracle CPU baseline runs before any CUDA work (no forked pools after it).
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt, nj, macs = oracle_sample(args.workload, W.GLOBAL_SEED, args.cpu_sample_projections)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {args.cpu_sample_projections} projections ({nj} proofs, {macs} MACs) "
+                         f"of the same workload, single process, {dt:.1f} s"}
+
+    import torch
+    from paper_2508_21393_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.lib()
+    seed = W.GLOBAL_SEED + 1000003 * rank
+    projs, jobs = step_jobs(args.workload, seed)
+    macs_step = sum(W.macs(j) for j in jobs)
+    entries = sum(W.fold_entries(j) for j in jobs)
+
+    dev, keep = {}, []
+    for t in projs:
+        for key in ("X", "W", "A", "B", "dY", "H", "dH"):
+            dev[id(t[key])] = torch.from_numpy(t[key]).cuda()
+    djobs = [B.job(dev[id(j["P"])], dev[id(j["Q"])], j["tp"], j["tq"], j["seed"]) for j in jobs]
+    in_bytes = sum(x.numel() * 2 for x in dev.values())
+
+    stream = torch.cuda.current_stream()
+    opts = B.vl_batch_opts()
+    opts.timing_runs = max(args.steps, 1)
+    plan = B.vl_plan_create(djobs, opts)
+    nws = B.vl_plan_workspace_bytes(plan)
+    ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
+    out = torch.empty(len(djobs) * ctypes.sizeof(B.vl_proof), dtype=torch.uint8, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        B.vl_plan_run(plan, ws.data_ptr(), nws, out.data_ptr(), B.VL_DEVICE, stream)
+    torch.cuda.synchronize()
+    status = np.frombuffer(out.cpu().numpy().tobytes(), dtype=np.int32).reshape(len(djobs), -1)[:, 6]
+    assert (status == 0).all(), "a proof reported a non-OK status"
+    B.vl_plan_phase_ms(plan, 0, reset=1)
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        B.vl_plan_run(plan, ws.data_ptr(), nws, out.data_ptr(), B.VL_DEVICE, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    phases = B.vl_plan_phase_ms(plan, args.steps, reset=1)
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = macs_step * world / (ms_max / 1e3)
+
+    fold_ms = statistics.mean(p[1] for p in phases)
+    pro_ms = statistics.mean(p[0] for p in phases)
+    rnd_ms = statistics.mean(p[2] for p in phases)
+    madw = 8 * entries  # eight 32x32->64 multiply-adds per int16 entry
+    peak = SMS * MADWIDE_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = madw / (fold_ms / 1e3) / 1e12
+    hbm_gbs = 2 * entries / (fold_ms / 1e3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+
+    # Unbatched per-matmul path: each product proved by its own plan (graph),
+    # one after another on the same stream.
+    unbatched_ms = None
+    if not args.no_unbatched:
+        one = B.vl_batch_opts()
+        one.timing_runs = 1
+        plans = [B.vl_plan_create([j], one) for j in djobs]
+        sizes = [B.vl_plan_workspace_bytes(p) for p in plans]
+        ws1 = torch.empty(max(sizes), dtype=torch.uint8, device="cuda")
+        for p, sz in zip(plans, sizes):
+            B.vl_plan_run(p, ws1.data_ptr(), sz, out.data_ptr(), B.VL_DEVICE, stream)
+        torch.cuda.synchronize()
+        u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u0.record(stream)
+        for p, sz in zip(plans, sizes):
+            B.vl_plan_run(p, ws1.data_ptr(), sz, out.data_ptr(), B.VL_DEVICE, stream)
+        u1.record(stream)
+        torch.cuda.synchronize()
+        unbatched_ms = u0.elapsed_time(u1)
+        for p in plans:
+            B.vl_plan_destroy(p)
+        del ws1
+
+    # End to end through the C ABI: pinned host operands in, host proofs out.
+    e2e = None
+    if not args.no_e2e:
+        host = {}
+        for t in projs:
+            for key in ("X", "W", "A", "B", "dY", "H", "dH"):
+                h = torch.empty(t[key].shape, dtype=torch.int16, pin_memory=True)
+                h.copy_(torch.from_numpy(t[key]))
+                host[id(t[key])] = h
+        hjobs = [B.job(host[id(j["P"])], host[id(j["Q"])], j["tp"], j["tq"], j["seed"]) for j in jobs]
+        hopts = B.vl_batch_opts()
+        hopts.timing_runs = 1
+        hplan = B.vl_plan_create(hjobs, hopts)
+        hn = B.vl_plan_workspace_bytes(hplan)
+        del ws
+        hws = torch.empty(hn, dtype=torch.uint8, device="cuda")
+        hout = (B.vl_proof * len(hjobs))()
+        for _ in range(2):
+            B.vl_plan_run(hplan, hws.data_ptr(), hn, hout, B.VL_HOST, stream)
+        ksteps = max(1, min(args.steps, 5))
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            B.vl_plan_run(hplan, hws.data_ptr(), hn, hout, B.VL_HOST, stream)
+        e2e_s = (time.perf_counter() - t0) / ksteps
+        et = torch.tensor([e2e_s], device="cuda")
+        if world > 1:
+            dist.all_reduce(et, op=dist.ReduceOp.MAX)
+        e2e = {"value": macs_step * world / float(et.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(h.numel() * 2 for h in host.values())),
+               "d2h_bytes_per_step": int(ctypes.sizeof(B.vl_proof) * len(hjobs)),
+               "ms_per_step": 1e3 * float(et.item()), "steps": ksteps}
+        B.vl_plan_destroy(hplan)
+
+    launches = args.steps * B.vl_plan_launches(plan)
+    B.vl_plan_destroy(plan)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int16 operands, Fr (255-bit) arithmetic", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "proofs_per_step": len(jobs),
+                   "macs_per_step": macs_step, "fold_entries_per_step": entries,
+                   "input_bytes_per_step": in_bytes, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single GPU",
+                   "batched_ms_per_step": ms_max, "unbatched_ms_per_step": unbatched_ms,
+                   "phase_ms": {"clear+prologue": pro_ms, "fold": fold_ms, "rounds": rnd_ms}},
+        "roofline": {"bound": "alu", "kernel": "fold_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "Tmadwide/s", "frac": achieved / peak, "traffic": None,
+                     "hbm_gbs_algorithmic": hbm_gbs,
+                     "hbm_frac_of_measured": hbm_gbs / peaks["hbm_gbs"] if "hbm_gbs" in peaks else None,
+                     "peak_note": "152 SMs x 32 IMAD.WIDE/clk x 2070 MHz (derived)"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * verilora.h - C ABI of the GB300 (sm_103a) matmul-sumcheck prover.
+ *
+ * What is proved.  zkMat (Sec. IV-B) proves each matrix product of a LoRA
+ * step with the sumcheck protocol over multilinear extensions (Sec. II-B,
+ * Eq. eq:MLE; Sec. II-C, Eq. eq:matmul and eq:zk-mle-matmul).  For
+ * A = op(P) (m x k) and B = op(Q) (k x n), dimensions zero-padded to powers
+ * of two D0 = 2^d0, D1 = 2^d1, D2 = 2^d2, the prover draws u in F^d0 and
+ * v in F^d2 from the transcript and runs d1 rounds of sumcheck on
+ *     sum_{w in {0,1}^d1} A~(u, w) . B~(w, v) = c   (c = C~(u, v) when C = A.B)
+ * over the BLS12-381 scalar field (Sec. V), with SHA-256 Fiat-Shamir
+ * challenges (Sec. IV-A footnote).  Commitments and lookups are outside this
+ * library: the verifier evaluates A~, B~, C~ directly from the matrices.
+ *
+ * Conventions.
+ *  - Field elements (vl_fr) are canonical, 8 x 32-bit limbs, little endian.
+ *  - Matrices are row-major with a leading dimension `ld` (elements between
+ *    row starts, ld >= cols).  `trans` = 1 means the operand is the transpose
+ *    of the stored matrix; no transpose is ever materialised.
+ *  - Row bits are the high MLE variables; variable 1 is the most significant
+ *    bit of an index, and sumcheck binds it first.
+ *  - int16 entries are fixed-point values embedded as x mod r (x < 0 maps to
+ *    r - |x|); the prover folds them without converting them to field form.
+ *  - The transcript format (start state, absorb, counter-mode squeeze) is
+ *    this library's own; it is written out in the transcript source header.
+ *
+ * Ownership.  The caller owns every buffer: operand matrices, the device
+ * workspace (size from vl_workspace_bytes / vl_plan_workspace_bytes, any
+ * alignment >= 256 bytes), the proof outputs and the CUDA stream.  The
+ * library never allocates device memory.  Operands must stay unchanged
+ * until the call's stream work has finished.
+ *
+ * Errors.  Every call returns VL_OK (0) or one of the codes below; nothing
+ * throws.  vl_strerror() names a code.  A failed call leaves outputs
+ * unspecified.
+ */
+#ifndef VERILORA_H
+#define VERILORA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define VL_OK 0
+#define VL_EINVAL 1   /* null pointer, bad enum, bad leading dimension       */
+#define VL_ESHAPE 2   /* inner dimensions differ, empty or oversized dims    */
+#define VL_ENOMEM 3   /* workspace smaller than required                     */
+#define VL_ECUDA 4    /* a CUDA runtime call failed                          */
+#define VL_ETIMEOUT 5 /* a bounded device-side wait gave up                  */
+#define VL_REJECT 6   /* vl_verify_matmul: the proof does not verify         */
+
+/* Element types of a vl_mat. */
+#define VL_I16 1     /* int16 fixed-point, 2 bytes                            */
+#define VL_I64 2     /* int64, 8 bytes (claimed products for the verifier)    */
+#define VL_FR_MONT 3 /* field element in Montgomery form (x.2^256 mod r), 32 B */
+
+/* Memory spaces. */
+#define VL_DEVICE 0
+#define VL_HOST 1
+
+/* Limits: reduced dimensions (m and n) <= 2^16 (exactness of the 64-bit column
+ * sums of the int16 fold), k <= 2^VL_MAX_ROUNDS. */
+#define VL_MAX_ROUNDS 24
+#define VL_MAX_REDUCE (1 << 16)
+
+typedef struct vl_fr {
+  uint32_t limb[8];
+} vl_fr;
+
+typedef struct vl_mat {
+  const void* data; /* device or host pointer, per `space`; caller-owned   */
+  int64_t rows;     /* stored rows                                         */
+  int64_t cols;     /* stored columns                                      */
+  int64_t ld;       /* elements between consecutive stored rows (>= cols)  */
+  int32_t dtype;    /* VL_I16, VL_I64 or VL_FR_MONT                        */
+  int32_t trans;    /* 1: the operand is the stored matrix transposed      */
+  int32_t space;    /* VL_DEVICE or VL_HOST                                */
+  int32_t reserved; /* must be 0                                           */
+} vl_mat;
+
+/* Public transcript inputs of one proof: a 64-bit seed and three 32-byte
+ * commitment stand-ins (bindings to P, Q, C; zeros when unused). */
+typedef struct vl_fs_init {
+  uint64_t seed;
+  uint8_t bind[3][32];
+} vl_fs_init;
+
+/* One proof.  g[i] = (g_i(0), g_i(1), g_i(2)) for rounds i < d1; entries at
+ * i >= d1 are zero.  `state` is the transcript state after the last absorb.
+ * `status` is VL_OK for a finished proof. */
+typedef struct vl_proof {
+  int32_t m, k, n, d0, d1, d2;
+  int32_t status;
+  int32_t reserved;
+  vl_fr c;
+  vl_fr g[VL_MAX_ROUNDS][3];
+  vl_fr a_r;
+  vl_fr b_r;
+  uint8_t state[32];
+} vl_proof;
+
+/* One product to prove: C = op(P) . op(Q). */
+typedef struct vl_job {
+  vl_mat P;
+  vl_mat Q;
+  vl_fs_init fs;
+} vl_job;
+
+/* Batch options; 0 in any field selects the default or the autotuned value. */
+typedef struct vl_batch_opts {
+  int32_t colsum_rows;   /* stored rows per column-sum fold tile              */
+  int32_t rowdot_cols;   /* stored columns per row-dot fold tile              */
+  int32_t persistent;    /* 1: one persistent launch; 2: phase launches       */
+  int32_t use_graph;     /* 1: capture vl_plan_run in a CUDA graph; 2: never   */
+  int32_t timing_runs;   /* runs kept by vl_plan_phase_ms (0: 64)             */
+  int32_t reserved[3];
+} vl_batch_opts;
+
+typedef struct vl_plan vl_plan; /* opaque batched-step plan */
+
+/* Version of this ABI (major * 100 + minor). */
+int32_t vl_version(void);
+
+/* Name of a status code (static string). */
+const char* vl_strerror(int32_t status);
+
+/*
+ * Device workspace needed to prove `njobs` products in one batch, in bytes.
+ * Host-space operands add staging room for one device copy of each distinct
+ * host matrix.  Returns 0 on invalid input.
+ */
+size_t vl_workspace_bytes(const vl_job* jobs, int32_t njobs, const vl_batch_opts* opts);
+
+/*
+ * Prove one product (Sec. II-C via zkMat, Sec. IV-B).  P, Q: device or host
+ * int16 / Montgomery matrices; fs: transcript inputs; workspace: caller's
+ * device buffer of at least vl_workspace_bytes() for this single job; out:
+ * host proof.  Runs on `stream` (a cudaStream_t, NULL for the legacy
+ * stream) and synchronises it before returning.
+ */
+int32_t vl_prove_matmul(const vl_mat* P, const vl_mat* Q, const vl_fs_init* fs,
+                        void* workspace, size_t workspace_bytes, vl_proof* out, void* stream);
+
+/*
+ * Prove all jobs of a batch (the products of a LoRA step, Protocol 2 phases 1
+ * and 2) in one pass of the device pipeline.  out: njobs proofs in
+ * `out_space` memory; for VL_HOST the call synchronises the stream, for
+ * VL_DEVICE it returns with the work enqueued.  Each proof is byte-identical
+ * to the same job proved alone.
+ */
+int32_t vl_prove_batch(const vl_job* jobs, int32_t njobs, void* workspace, size_t workspace_bytes,
+                       vl_proof* out, int32_t out_space, void* stream, const vl_batch_opts* opts);
+
+/*
+ * Reusable plan for a fixed batch (same shapes, same operand pointers): the
+ * descriptor tables are built once, and vl_plan_run replays a CUDA graph of
+ * the whole step after its first call.  The plan copies `jobs`.
+ */
+int32_t vl_plan_create(const vl_job* jobs, int32_t njobs, const vl_batch_opts* opts, vl_plan** plan);
+size_t vl_plan_workspace_bytes(const vl_plan* plan);
+/* Enqueue one proving pass; out: njobs proofs in `out_space` memory (VL_HOST
+ * synchronises).  Host-space operands are copied in on every run. */
+int32_t vl_plan_run(vl_plan* plan, void* workspace, size_t workspace_bytes, vl_proof* out,
+                    int32_t out_space, void* stream);
+/* Number of kernel launches one vl_plan_run enqueues (graph nodes included). */
+int32_t vl_plan_launches(const vl_plan* plan);
+/*
+ * Device time of the most recent proving passes of a plan, from CUDA events
+ * the plan records on its stream at the phase boundaries of every run
+ * (inside the graph when one is used).  ms: max_runs x 3 floats per run:
+ * [0] accumulator clear + prologue (transcripts, challenges, eq tables),
+ * [1] fold, [2] claims + sumcheck rounds.  Fills the last min(max_runs, runs
+ * since the previous reset, opts.timing_runs) runs, oldest first, waiting for the last
+ * one to finish.  reset != 0 restarts the count.  Returns the number of runs
+ * filled, or -status on error.
+ */
+int32_t vl_plan_phase_ms(vl_plan* plan, float* ms, int32_t max_runs, int32_t reset);
+void vl_plan_destroy(vl_plan* plan);
+
+/*
+ * Verify a proof on the host (Def. def:ip verifier; Sec. V-B completeness).
+ * P, Q, C are HOST matrices (C: the claimed m x n product, VL_I64 or VL_I16).
+ * Replays the transcript, checks g_i(0) + g_i(1) against the running claim,
+ * the final claim against a_r . b_r, and evaluates A~(u, r), B~(r, v) and
+ * C~(u, v) directly (the stand-in for commitment openings).
+ * Returns VL_OK (accept), VL_REJECT, or an input error.
+ */
+int32_t vl_verify_matmul(const vl_mat* P, const vl_mat* Q, const vl_mat* C, const vl_fs_init* fs,
+                         const vl_proof* proof);
+
+/*
+ * Encode int16 fixed-point values into field elements in Montgomery form
+ * (Sec. II-C embeds integer tensors into F; x < 0 maps to r - |x|):
+ * dst[i * cols + j] = (src[i, j] mod r) . 2^256 mod r, 32 bytes each, dense
+ * row-major.  src and dst are device pointers; runs asynchronously on
+ * `stream`.  The output can be proved with dtype VL_FR_MONT.
+ */
+int32_t vl_encode(const vl_mat* src, void* dst, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VERILORA_H */

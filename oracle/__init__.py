@@ -22,9 +22,11 @@ from .field import R_MOD, fr, fr_add, fr_sub, fr_mul, fr_inv, fr_to_bytes, fr_fr
 from .transcript import Transcript
 from .mle import eq_table, eq_value, mle_eval_bruteforce, mle_eval_matrix, fold_rows, fold_cols
 from .sumcheck import Proof, prove_matmul, verify_matmul, round_poly_eval
+from .encode import encode_montgomery, limbs_le32
 
 __all__ = [
     "R_MOD", "fr", "fr_add", "fr_sub", "fr_mul", "fr_inv", "fr_to_bytes", "fr_from_bytes",
     "Transcript", "eq_table", "eq_value", "mle_eval_bruteforce", "mle_eval_matrix",
     "fold_rows", "fold_cols", "Proof", "prove_matmul", "verify_matmul", "round_poly_eval",
+    "encode_montgomery", "limbs_le32",
 ]

@@ -1,0 +1,294 @@
+"""ctypes binding of libverilora.so (include/verilora.h), same names as the C ABI.
+
+Argument marshalling only: every step of the proving path runs in the CUDA
+library.  PyTorch is used for device memory and streams.  If the library is
+missing the calls raise; there is no fallback.
+
+Helpers: ``mat`` wraps a torch tensor (device or host) or a NumPy array
+(host) as a ``vl_mat``; ``fs_init`` builds transcript inputs;
+``proof_bytes`` serialises a proof canonically (six u32le dims, c, the d1
+round triples, a_r, b_r, the final transcript state).
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_lib", "libverilora.so")
+
+VL_OK, VL_EINVAL, VL_ESHAPE, VL_ENOMEM, VL_ECUDA, VL_ETIMEOUT, VL_REJECT = range(7)
+VL_I16, VL_I64, VL_FR_MONT = 1, 2, 3
+VL_DEVICE, VL_HOST = 0, 1
+VL_MAX_ROUNDS = 24
+VL_MAX_REDUCE = 1 << 16
+
+# Every symbol include/verilora.h declares.
+EXPORTS = ("vl_version", "vl_strerror", "vl_workspace_bytes", "vl_prove_matmul", "vl_prove_batch",
+           "vl_plan_create", "vl_plan_workspace_bytes", "vl_plan_run", "vl_plan_launches", "vl_plan_phase_ms",
+           "vl_plan_destroy", "vl_verify_matmul", "vl_encode")
+
+
+class vl_fr(ctypes.Structure):
+    _fields_ = [("limb", ctypes.c_uint32 * 8)]
+
+    def to_int(self):
+        return sum(int(self.limb[i]) << (32 * i) for i in range(8))
+
+
+class vl_mat(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("rows", ctypes.c_int64), ("cols", ctypes.c_int64),
+                ("ld", ctypes.c_int64), ("dtype", ctypes.c_int32), ("trans", ctypes.c_int32),
+                ("space", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class vl_fs_init(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("bind", (ctypes.c_uint8 * 32) * 3)]
+
+
+class vl_proof(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("k", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("d0", ctypes.c_int32), ("d1", ctypes.c_int32), ("d2", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("c", vl_fr), ("g", (vl_fr * 3) * VL_MAX_ROUNDS), ("a_r", vl_fr), ("b_r", vl_fr),
+                ("state", ctypes.c_uint8 * 32)]
+
+
+class vl_job(ctypes.Structure):
+    _fields_ = [("P", vl_mat), ("Q", vl_mat), ("fs", vl_fs_init)]
+
+
+class vl_batch_opts(ctypes.Structure):
+    _fields_ = [("colsum_rows", ctypes.c_int32), ("rowdot_cols", ctypes.c_int32),
+                ("persistent", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("timing_runs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class VLError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {vl_strerror(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libverilora.so once (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libverilora.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    L.vl_version.restype = ctypes.c_int32
+    L.vl_strerror.argtypes = [ctypes.c_int32]
+    L.vl_strerror.restype = ctypes.c_char_p
+    L.vl_workspace_bytes.argtypes = [P(vl_job), ctypes.c_int32, P(vl_batch_opts)]
+    L.vl_workspace_bytes.restype = ctypes.c_size_t
+    L.vl_prove_matmul.argtypes = [P(vl_mat), P(vl_mat), P(vl_fs_init), ctypes.c_void_p, ctypes.c_size_t,
+                                  P(vl_proof), ctypes.c_void_p]
+    L.vl_prove_matmul.restype = ctypes.c_int32
+    L.vl_prove_batch.argtypes = [P(vl_job), ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                 ctypes.c_int32, ctypes.c_void_p, P(vl_batch_opts)]
+    L.vl_prove_batch.restype = ctypes.c_int32
+    L.vl_plan_create.argtypes = [P(vl_job), ctypes.c_int32, P(vl_batch_opts), P(ctypes.c_void_p)]
+    L.vl_plan_create.restype = ctypes.c_int32
+    L.vl_plan_workspace_bytes.argtypes = [ctypes.c_void_p]
+    L.vl_plan_workspace_bytes.restype = ctypes.c_size_t
+    L.vl_plan_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_int32,
+                              ctypes.c_void_p]
+    L.vl_plan_run.restype = ctypes.c_int32
+    L.vl_plan_launches.argtypes = [ctypes.c_void_p]
+    L.vl_plan_launches.restype = ctypes.c_int32
+    L.vl_plan_phase_ms.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.c_int32]
+    L.vl_plan_phase_ms.restype = ctypes.c_int32
+    L.vl_plan_destroy.argtypes = [ctypes.c_void_p]
+    L.vl_plan_destroy.restype = None
+    L.vl_verify_matmul.argtypes = [P(vl_mat), P(vl_mat), P(vl_mat), P(vl_fs_init), P(vl_proof)]
+    L.vl_verify_matmul.restype = ctypes.c_int32
+    L.vl_encode.argtypes = [P(vl_mat), ctypes.c_void_p, ctypes.c_void_p]
+    L.vl_encode.restype = ctypes.c_int32
+    _lib = L
+    return L
+
+
+def _check(code, what):
+    if code != VL_OK:
+        raise VLError(code, what)
+
+
+# ------------------------------------------------------------------ helpers --
+
+def _torch():
+    import torch
+    return torch
+
+
+def mat(a, trans=0, dtype=None):
+    """vl_mat view of a 2-D torch tensor (device or host) or NumPy array (host).
+
+    int16 -> VL_I16, int64 -> VL_I64; a tensor/array of shape (rows, cols, 8)
+    with 4-byte elements holds Montgomery field elements (VL_FR_MONT).
+    Rows must be contiguous (unit column stride).
+    """
+    m = vl_mat()
+    if isinstance(a, np.ndarray):
+        if a.ndim == 3:
+            assert a.shape[2] == 8 and a.dtype.itemsize == 4 and a.flags["C_CONTIGUOUS"]
+            m.dtype, m.ld = VL_FR_MONT, a.shape[1]
+        else:
+            assert a.ndim == 2 and a.strides[1] == a.itemsize, "unit column stride required"
+            m.dtype = {np.dtype(np.int16): VL_I16, np.dtype(np.int64): VL_I64}[a.dtype]
+            m.ld = a.strides[0] // a.itemsize
+        m.data = a.ctypes.data
+        m.space = VL_HOST
+    else:
+        torch = _torch()
+        if a.dim() == 3:
+            assert a.shape[2] == 8 and a.element_size() == 4 and a.is_contiguous()
+            m.dtype, m.ld = VL_FR_MONT, a.shape[1]
+        else:
+            assert a.dim() == 2 and a.stride(1) == 1, "unit column stride required"
+            m.dtype = {torch.int16: VL_I16, torch.int64: VL_I64}[a.dtype]
+            m.ld = a.stride(0)
+        m.data = a.data_ptr()
+        m.space = VL_DEVICE if a.is_cuda else VL_HOST
+    m.rows, m.cols = int(a.shape[0]), int(a.shape[1])
+    m.trans = int(trans)
+    m.reserved = 0
+    if dtype is not None:
+        m.dtype = dtype
+    return m
+
+
+def fs_init(seed, binds=None):
+    f = vl_fs_init()
+    f.seed = int(seed) & ((1 << 64) - 1)
+    for i in range(3):
+        b = bytes(32) if binds is None else bytes(binds[i])
+        for j in range(32):
+            f.bind[i][j] = b[j]
+    return f
+
+
+def job(P, Q, tp=0, tq=0, seed=0, binds=None):
+    j = vl_job()
+    j.P = mat(P, tp)
+    j.Q = mat(Q, tq)
+    j.fs = fs_init(seed, binds)
+    return j
+
+
+def jobs_array(jobs):
+    arr = (vl_job * len(jobs))()
+    for i, j in enumerate(jobs):
+        arr[i] = j
+    return arr
+
+
+def proof_bytes(p):
+    """Canonical proof serialisation (same layout as the oracle's Proof.to_bytes)."""
+    out = b"".join(int(x).to_bytes(4, "little") for x in (p.m, p.k, p.n, p.d0, p.d1, p.d2))
+    out += bytes(p.c)
+    for i in range(p.d1):
+        for q in range(3):
+            out += bytes(p.g[i][q])
+    out += bytes(p.a_r) + bytes(p.b_r) + bytes(p.state)
+    return out
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return _torch().cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ----------------------------------------------------------- C ABI, by name --
+
+def vl_version():
+    return lib().vl_version()
+
+
+def vl_strerror(code):
+    return lib().vl_strerror(int(code)).decode()
+
+
+def vl_workspace_bytes(jobs, opts=None):
+    arr = jobs_array(jobs)
+    return lib().vl_workspace_bytes(arr, len(jobs), ctypes.byref(opts) if opts is not None else None)
+
+
+def vl_prove_matmul(P, Q, fs, workspace, workspace_bytes, stream=None):
+    """Prove one product; returns a host vl_proof.  P, Q: vl_mat."""
+    out = vl_proof()
+    _check(lib().vl_prove_matmul(ctypes.byref(P), ctypes.byref(Q), ctypes.byref(fs), workspace,
+                                 workspace_bytes, ctypes.byref(out), _stream_ptr(stream)), "vl_prove_matmul")
+    return out
+
+
+def vl_prove_batch(jobs, workspace, workspace_bytes, out=None, out_space=VL_HOST, stream=None, opts=None):
+    """Prove a batch.  For VL_HOST returns the ctypes array of proofs; for
+    VL_DEVICE `out` is a device pointer (int) to len(jobs) proofs."""
+    arr = jobs_array(jobs)
+    if out_space == VL_HOST:
+        res = (vl_proof * len(jobs))()
+        ptr = ctypes.addressof(res)
+    else:
+        res, ptr = None, int(out)
+    _check(lib().vl_prove_batch(arr, len(jobs), workspace, workspace_bytes, ptr, out_space, _stream_ptr(stream),
+                                ctypes.byref(opts) if opts is not None else None), "vl_prove_batch")
+    return res
+
+
+def vl_plan_create(jobs, opts=None):
+    arr = jobs_array(jobs)
+    h = ctypes.c_void_p()
+    _check(lib().vl_plan_create(arr, len(jobs), ctypes.byref(opts) if opts is not None else None,
+                                ctypes.byref(h)), "vl_plan_create")
+    return h.value
+
+
+def vl_plan_workspace_bytes(plan):
+    return lib().vl_plan_workspace_bytes(plan)
+
+
+def vl_plan_run(plan, workspace, workspace_bytes, out, out_space=VL_DEVICE, stream=None):
+    ptr = ctypes.addressof(out) if out_space == VL_HOST else int(out)
+    _check(lib().vl_plan_run(plan, workspace, workspace_bytes, ptr, out_space, _stream_ptr(stream)), "vl_plan_run")
+
+
+def vl_plan_launches(plan):
+    return lib().vl_plan_launches(plan)
+
+
+def vl_plan_phase_ms(plan, max_runs, reset=1):
+    """Per-run phase times [(clear+prologue, fold, rounds) ms, ...] of the last runs."""
+    buf = (ctypes.c_float * (3 * max(max_runs, 1)))()
+    n = lib().vl_plan_phase_ms(plan, buf, max_runs, reset)
+    if n < 0:
+        raise VLError(-n, "vl_plan_phase_ms")
+    return [(buf[3 * i], buf[3 * i + 1], buf[3 * i + 2]) for i in range(n)]
+
+
+def vl_plan_destroy(plan):
+    lib().vl_plan_destroy(plan)
+
+
+def vl_verify_matmul(P, Q, C, fs, proof):
+    """Host verifier: True (accept) / False (reject); raises on input errors."""
+    code = lib().vl_verify_matmul(ctypes.byref(P), ctypes.byref(Q), ctypes.byref(C), ctypes.byref(fs),
+                                  ctypes.byref(proof))
+    if code == VL_REJECT:
+        return False
+    _check(code, "vl_verify_matmul")
+    return True
+
+
+def vl_encode(src, dst, stream=None):
+    """Encode a device int16 vl_mat into dst (device pointer, rows*cols*32 bytes)."""
+    _check(lib().vl_encode(ctypes.byref(src), int(dst), _stream_ptr(stream)), "vl_encode")

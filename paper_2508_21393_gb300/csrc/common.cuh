@@ -1,0 +1,78 @@
+// Device-side descriptors shared by the prover kernels and the host engine.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fr.cuh"
+#include "verilora.h"
+
+namespace vl {
+
+// How a fold task reduces its stored matrix.
+//   COLSUM: out[c] = sum_r W[r] . M[r, c]   (reduce over stored rows)
+//   ROWDOT: out[r] = sum_c M[r, c] . W[c]   (reduce over stored columns)
+// f_A comes from op(P) folded against E_u over its m rows: COLSUM when P is
+// stored m x k, ROWDOT when stored k x m (trans).  f_B comes from op(Q)
+// folded against E_v over its n columns: ROWDOT when Q is stored k x n,
+// COLSUM when stored n x k (trans).
+enum : int32_t { MODE_COLSUM = 0, MODE_ROWDOT = 1 };
+
+// Per-proof mutable state (device, in the workspace).
+struct ProofScratch {
+  uint8_t state[32];  // transcript state after the u, v squeezes
+  Fr corrA;           // 2^15 . sum E_u  (Montgomery), int16 offset correction
+  Fr corrB;           // 2^15 . sum E_v
+  int32_t status;
+  int32_t pad[7];
+};
+
+// Per-proof read-only descriptor (device copy of the plan).
+struct DevProof {
+  int32_t m, k, n, d0, d1, d2;
+  int32_t tp, tq;
+  int32_t dtypeA, dtypeB;  // VL_I16 or VL_FR_MONT
+  int32_t pad0, pad1;
+  uint64_t seed;
+  uint8_t binds[96];
+  Fr* eqA;                 // m entries, E_u in double-Montgomery form (x.R^2)
+  Fr* eqB;                 // n entries, E_v
+  unsigned long long* accA;  // k x 8 column sums (f_A numerators)
+  unsigned long long* accB;  // k x 8
+  Fr* fA;                  // 2^d1 working vector for the rounds (Montgomery)
+  Fr* fB;
+  ProofScratch* scr;
+};
+
+struct FoldTask {
+  const void* mat;  // stored matrix (device)
+  int64_t ld;       // elements between stored rows
+  int32_t rows, cols;
+  int32_t mode, dtype;
+  int32_t proof, side;  // side 0: weights E_u, output accA; side 1: E_v, accB
+};
+
+struct FoldTile {
+  int32_t task;
+  int32_t r0, r1;  // stored rows [r0, r1)
+  int32_t c0, c1;  // stored columns [c0, c1)
+  int32_t pad[3];
+};
+
+// Fold tile geometry (threads per CTA and per-thread vector widths).
+static constexpr int FOLD_THREADS = 256;
+static constexpr int COLSUM_VEC = 4;                              // int16 columns per thread
+static constexpr int COLSUM_TILE_COLS = FOLD_THREADS * COLSUM_VEC;  // 1024
+static constexpr int ROWDOT_ROWS_PER_WARP = 4;
+static constexpr int ROWDOT_TILE_ROWS = (FOLD_THREADS / 32) * ROWDOT_ROWS_PER_WARP;  // 32
+static constexpr int FR_COLSUM_TILE_COLS = FOLD_THREADS;          // Montgomery operands: 1 col/thread
+
+cudaError_t launch_prologue(const DevProof* proofs, int nproofs, cudaStream_t st);
+// Raise the fold kernel's dynamic shared-memory limit (call before capture).
+cudaError_t fold_set_smem(int smem_bytes);
+cudaError_t launch_fold(const FoldTask* tasks, const FoldTile* tiles, int ntiles,
+                        const DevProof* proofs, int smem_bytes, cudaStream_t st);
+cudaError_t launch_rounds(const DevProof* proofs, int nproofs, vl_proof* out, cudaStream_t st);
+cudaError_t launch_encode(const int16_t* src, int64_t rows, int64_t cols, int64_t ld, Fr* dst,
+                          cudaStream_t st);
+
+}  // namespace vl

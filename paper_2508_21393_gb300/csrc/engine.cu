@@ -1,0 +1,510 @@
+// Host engine and C ABI of the prover (see include/verilora.h).
+//
+// A plan turns a list of products (jobs) into device descriptor tables:
+// one DevProof per job, two fold tasks per job (op(P) against E_u, op(Q)
+// against E_v) cut into fold tiles, and a workspace layout.  One proving pass
+// is four stream operations: zero the fold accumulators, the prologue kernel
+// (transcripts, challenges, eq tables), the fold kernel over all tiles of all
+// jobs, and the rounds kernel (claims, sumcheck rounds, proofs).  A plan can
+// capture that pass in a CUDA graph and replay it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace vl;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
+
+int ceil_log2(int64_t x) {
+  int d = 0;
+  while ((int64_t(1) << d) < x) d++;
+  return d;
+}
+
+size_t esize(int32_t dtype) {
+  return dtype == VL_I16 ? 2 : dtype == VL_I64 ? 8 : dtype == VL_FR_MONT ? 32 : 0;
+}
+
+int check_mat(const vl_mat* M, bool prover) {
+  if (!M || !M->data) return VL_EINVAL;
+  if (M->reserved != 0 || (M->trans != 0 && M->trans != 1)) return VL_EINVAL;
+  if (M->space != VL_DEVICE && M->space != VL_HOST) return VL_EINVAL;
+  if (prover && M->dtype != VL_I16 && M->dtype != VL_FR_MONT) return VL_EINVAL;
+  if (!esize(M->dtype)) return VL_EINVAL;
+  if (M->rows < 1 || M->cols < 1) return VL_ESHAPE;
+  if (M->ld < M->cols) return VL_EINVAL;
+  if (M->dtype == VL_FR_MONT && (reinterpret_cast<uintptr_t>(M->data) & 15)) return VL_EINVAL;
+  return VL_OK;
+}
+
+struct Dims {
+  int64_t m, k, n;
+};
+
+int job_dims(const vl_job& j, Dims* d) {
+  int e;
+  if ((e = check_mat(&j.P, true)) != VL_OK) return e;
+  if ((e = check_mat(&j.Q, true)) != VL_OK) return e;
+  const int64_t m = j.P.trans ? j.P.cols : j.P.rows;
+  const int64_t k = j.P.trans ? j.P.rows : j.P.cols;
+  const int64_t kq = j.Q.trans ? j.Q.cols : j.Q.rows;
+  const int64_t n = j.Q.trans ? j.Q.rows : j.Q.cols;
+  if (k != kq) return VL_ESHAPE;
+  if (m > VL_MAX_REDUCE || n > VL_MAX_REDUCE || k > (int64_t(1) << VL_MAX_ROUNDS)) return VL_ESHAPE;
+  d->m = m;
+  d->k = k;
+  d->n = n;
+  return VL_OK;
+}
+
+struct Staged {
+  size_t off;
+  size_t bytes;
+};
+
+}  // namespace
+
+struct vl_plan {
+  std::vector<vl_job> jobs;
+  vl_batch_opts opts{};
+  std::vector<DevProof> proofs;
+  std::vector<FoldTask> tasks;
+  std::vector<FoldTile> tiles;
+  int fold_smem = 0;
+  // workspace layout (offsets from the workspace base)
+  size_t off_proofs = 0, off_scr = 0, off_tasks = 0, off_tiles = 0;
+  size_t off_acc = 0, acc_bytes = 0, off_out = 0, total = 0;
+  struct PerProof {
+    size_t eqA, eqB, accA, accB, fA, fB;
+  };
+  std::vector<PerProof> pp;
+  std::map<const void*, Staged> staging;  // host operand -> device copy
+  // bound state
+  void* bound_ws = nullptr;
+  vl_proof* bound_out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  // phase timing: events at the four phase boundaries of every run, taken
+  // from a ring of `ring_runs` runs; in a graph the event-record nodes are
+  // pointed at the current ring slot before each launch.
+  int ring_runs = 64;
+  static constexpr int NEV = 4;  // before clear, before fold, after fold, after rounds
+  std::vector<cudaEvent_t> ring;
+  cudaEvent_t cap_ev[NEV] = {};
+  cudaGraphNode_t ev_node[NEV] = {};
+  long runs = 0, timing_base = 0;
+};
+
+namespace {
+
+void add_fold_task(vl_plan* p, const vl_mat& M, int32_t mode, int proof, int side) {
+  FoldTask t{};
+  t.mat = nullptr;  // bound at run time
+  t.ld = M.ld;
+  t.rows = (int32_t)M.rows;
+  t.cols = (int32_t)M.cols;
+  t.mode = mode;
+  t.dtype = M.dtype;
+  t.proof = proof;
+  t.side = side;
+  const int task = (int)p->tasks.size();
+  p->tasks.push_back(t);
+  const bool fr = M.dtype == VL_FR_MONT;
+  if (mode == MODE_COLSUM) {
+    const int tc = fr ? FR_COLSUM_TILE_COLS : COLSUM_TILE_COLS;
+    const int tr = p->opts.colsum_rows > 0 ? p->opts.colsum_rows : 256;
+    for (int c0 = 0; c0 < t.cols; c0 += tc)
+      for (int r0 = 0; r0 < t.rows; r0 += tr) {
+        FoldTile ft{};
+        ft.task = task;
+        ft.r0 = r0;
+        ft.r1 = std::min<int>(t.rows, r0 + tr);
+        ft.c0 = c0;
+        ft.c1 = std::min<int>(t.cols, c0 + tc);
+        p->tiles.push_back(ft);
+        p->fold_smem = std::max(p->fold_smem, (ft.r1 - ft.r0) * 32);
+      }
+  } else {
+    int tcmax = p->opts.rowdot_cols > 0 ? p->opts.rowdot_cols : 2048;
+    tcmax = (tcmax + 3) & ~3;
+    for (int c0 = 0; c0 < t.cols; c0 += tcmax)
+      for (int r0 = 0; r0 < t.rows; r0 += ROWDOT_TILE_ROWS) {
+        FoldTile ft{};
+        ft.task = task;
+        ft.r0 = r0;
+        ft.r1 = std::min<int>(t.rows, r0 + ROWDOT_TILE_ROWS);
+        ft.c0 = c0;
+        ft.c1 = std::min<int>(t.cols, c0 + tcmax);
+        p->tiles.push_back(ft);
+        const int pitch = ((ft.c1 - ft.c0) + 3) & ~3;
+        p->fold_smem = std::max(p->fold_smem, pitch * 32);
+      }
+  }
+}
+
+int build_plan(vl_plan* p) {
+  const int np = (int)p->jobs.size();
+  p->proofs.resize(np);
+  p->pp.resize(np);
+  size_t off = 0;
+  p->off_proofs = off;
+  off = align_up(off + sizeof(DevProof) * np);
+  p->off_scr = off;
+  off = align_up(off + sizeof(ProofScratch) * np);
+  p->off_out = off;
+  off = align_up(off + sizeof(vl_proof) * np);
+
+  for (int i = 0; i < np; i++) {
+    const vl_job& j = p->jobs[i];
+    Dims d;
+    int e = job_dims(j, &d);
+    if (e != VL_OK) return e;
+    DevProof& P = p->proofs[i];
+    std::memset(&P, 0, sizeof(P));
+    P.m = (int32_t)d.m;
+    P.k = (int32_t)d.k;
+    P.n = (int32_t)d.n;
+    P.d0 = ceil_log2(d.m);
+    P.d1 = ceil_log2(d.k);
+    P.d2 = ceil_log2(d.n);
+    P.tp = j.P.trans;
+    P.tq = j.Q.trans;
+    P.dtypeA = j.P.dtype;
+    P.dtypeB = j.Q.dtype;
+    P.seed = j.fs.seed;
+    std::memcpy(P.binds, j.fs.bind, 96);
+    // f_A: op(P) over its m rows.  Stored m x k -> column sums; stored k x m -> row dots.
+    add_fold_task(p, j.P, j.P.trans ? MODE_ROWDOT : MODE_COLSUM, i, 0);
+    // f_B: op(Q) over its n columns.  Stored k x n -> row dots; stored n x k -> column sums.
+    add_fold_task(p, j.Q, j.Q.trans ? MODE_COLSUM : MODE_ROWDOT, i, 1);
+  }
+  p->off_tasks = off;
+  off = align_up(off + sizeof(FoldTask) * p->tasks.size());
+  p->off_tiles = off;
+  off = align_up(off + sizeof(FoldTile) * p->tiles.size());
+  // accumulators: one contiguous region, zeroed each pass
+  p->off_acc = off;
+  for (int i = 0; i < np; i++) {
+    const size_t kb = (size_t)p->proofs[i].k * 8 * sizeof(unsigned long long);
+    p->pp[i].accA = off;
+    off = align_up(off + kb);
+    p->pp[i].accB = off;
+    off = align_up(off + kb);
+  }
+  p->acc_bytes = off - p->off_acc;
+  for (int i = 0; i < np; i++) {
+    const DevProof& P = p->proofs[i];
+    p->pp[i].eqA = off;
+    off = align_up(off + sizeof(Fr) * P.m);
+    p->pp[i].eqB = off;
+    off = align_up(off + sizeof(Fr) * P.n);
+    p->pp[i].fA = off;
+    off = align_up(off + sizeof(Fr) * ((size_t)1 << P.d1));
+    p->pp[i].fB = off;
+    off = align_up(off + sizeof(Fr) * ((size_t)1 << P.d1));
+  }
+  // staging for host operands (one device copy per distinct host pointer)
+  for (const vl_job& j : p->jobs) {
+    for (const vl_mat* M : {&j.P, &j.Q}) {
+      if (M->space != VL_HOST) continue;
+      const size_t bytes = ((size_t)(M->rows - 1) * M->ld + M->cols) * esize(M->dtype);
+      auto it = p->staging.find(M->data);
+      if (it != p->staging.end()) {
+        if (it->second.bytes < bytes) return VL_EINVAL;  // same pointer, different extent
+        continue;
+      }
+      p->staging[M->data] = Staged{off, bytes};
+      off = align_up(off + bytes);
+    }
+  }
+  p->total = off;
+  if (p->fold_smem > 200 * 1024) return VL_ESHAPE;
+  return VL_OK;
+}
+
+const void* operand_ptr(const vl_plan* p, const vl_mat& M, uint8_t* ws) {
+  if (M.space == VL_DEVICE) return M.data;
+  return ws + p->staging.at(M.data).off;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? VL_OK : VL_ECUDA; }
+
+// Fill device pointers for this workspace and upload the descriptor tables.
+int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
+  const int np = (int)p->jobs.size();
+  for (int i = 0; i < np; i++) {
+    DevProof& P = p->proofs[i];
+    P.eqA = reinterpret_cast<Fr*>(ws + p->pp[i].eqA);
+    P.eqB = reinterpret_cast<Fr*>(ws + p->pp[i].eqB);
+    P.accA = reinterpret_cast<unsigned long long*>(ws + p->pp[i].accA);
+    P.accB = reinterpret_cast<unsigned long long*>(ws + p->pp[i].accB);
+    P.fA = reinterpret_cast<Fr*>(ws + p->pp[i].fA);
+    P.fB = reinterpret_cast<Fr*>(ws + p->pp[i].fB);
+    P.scr = reinterpret_cast<ProofScratch*>(ws + p->off_scr) + i;
+  }
+  for (FoldTask& t : p->tasks) {
+    const vl_job& j = p->jobs[t.proof];
+    t.mat = operand_ptr(p, t.side ? j.Q : j.P, ws);
+  }
+  cudaError_t e = cudaMemcpyAsync(ws + p->off_proofs, p->proofs.data(), sizeof(DevProof) * np,
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !p->tasks.empty())
+    e = cudaMemcpyAsync(ws + p->off_tasks, p->tasks.data(), sizeof(FoldTask) * p->tasks.size(),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !p->tiles.empty())
+    e = cudaMemcpyAsync(ws + p->off_tiles, p->tiles.data(), sizeof(FoldTile) * p->tiles.size(),
+                        cudaMemcpyHostToDevice, st);
+  // The host vectors must outlive the copies: wait for them.
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && p->fold_smem > 0) e = fold_set_smem(p->fold_smem);
+  return cuda_status(e);
+}
+
+cudaError_t ensure_events(vl_plan* p) {
+  if (!p->ring.empty()) return cudaSuccess;
+  p->ring.resize((size_t)p->ring_runs * vl_plan::NEV);
+  for (cudaEvent_t& ev : p->ring) {
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return e;
+  }
+  for (cudaEvent_t& ev : p->cap_ev) {
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaEvent_t* slot_events(vl_plan* p, long run) {
+  return &p->ring[(size_t)(run % p->ring_runs) * vl_plan::NEV];
+}
+
+// The device part of one proving pass (graph-capturable).  `ev`: the four
+// phase-boundary events to record.
+cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t st, cudaEvent_t* ev) {
+  const DevProof* dp = reinterpret_cast<const DevProof*>(ws + p->off_proofs);
+  const FoldTask* dt = reinterpret_cast<const FoldTask*>(ws + p->off_tasks);
+  const FoldTile* dl = reinterpret_cast<const FoldTile*>(ws + p->off_tiles);
+  const int np = (int)p->jobs.size();
+  cudaError_t e = cudaEventRecord(ev[0], st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws + p->off_acc, 0, p->acc_bytes, st);
+  if (e == cudaSuccess) e = launch_prologue(dp, np, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+  if (e == cudaSuccess) e = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
+  if (e == cudaSuccess) e = launch_rounds(dp, np, dout, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
+  return e;
+}
+
+// After capture: find the event-record node of each phase-boundary event.
+cudaError_t find_event_nodes(vl_plan* p) {
+  size_t n = 0;
+  cudaError_t e = cudaGraphGetNodes(p->graph, nullptr, &n);
+  if (e != cudaSuccess) return e;
+  std::vector<cudaGraphNode_t> nodes(n);
+  e = cudaGraphGetNodes(p->graph, nodes.data(), &n);
+  if (e != cudaSuccess) return e;
+  int found = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord) continue;
+    cudaEvent_t ev;
+    if (cudaGraphEventRecordNodeGetEvent(nd, &ev) != cudaSuccess) continue;
+    for (int q = 0; q < vl_plan::NEV; q++)
+      if (ev == p->cap_ev[q]) {
+        p->ev_node[q] = nd;
+        found++;
+      }
+  }
+  return found == vl_plan::NEV ? cudaSuccess : cudaErrorUnknown;
+}
+
+void drop_graph(vl_plan* p) {
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->gexec = nullptr;
+  p->graph = nullptr;
+}
+
+int stage_host_operands(vl_plan* p, uint8_t* ws, cudaStream_t st) {
+  for (auto& kv : p->staging) {
+    cudaError_t e = cudaMemcpyAsync(ws + kv.second.off, kv.first, kv.second.bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return VL_ECUDA;
+  }
+  return VL_OK;
+}
+
+int run_plan(vl_plan* p, void* workspace, size_t ws_bytes, vl_proof* out, int32_t out_space,
+             cudaStream_t st, bool graph) {
+  if (!workspace || !out) return VL_EINVAL;
+  if (out_space != VL_DEVICE && out_space != VL_HOST) return VL_EINVAL;
+  if (ws_bytes < p->total) return VL_ENOMEM;
+  if (reinterpret_cast<uintptr_t>(workspace) & (ALIGN - 1)) return VL_EINVAL;
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  vl_proof* dout = out_space == VL_DEVICE ? out : reinterpret_cast<vl_proof*>(ws + p->off_out);
+  if (ensure_events(p) != cudaSuccess) return VL_ECUDA;
+  if (p->bound_ws != workspace) {
+    drop_graph(p);
+    int e = bind_workspace(p, ws, st);
+    if (e != VL_OK) return e;
+    p->bound_ws = workspace;
+  }
+  int e = stage_host_operands(p, ws, st);
+  if (e != VL_OK) return e;
+  cudaEvent_t* ev = slot_events(p, p->runs);
+  if (graph) {
+    if (p->gexec && p->bound_out != dout) drop_graph(p);
+    if (!p->gexec) {
+      cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+      if (ce != cudaSuccess) return VL_ECUDA;
+      cudaError_t ke = enqueue_pass(p, ws, dout, st, p->cap_ev);
+      ce = cudaStreamEndCapture(st, &p->graph);
+      if (ke != cudaSuccess || ce != cudaSuccess) {
+        drop_graph(p);
+        return VL_ECUDA;
+      }
+      if (find_event_nodes(p) != cudaSuccess || cudaGraphInstantiate(&p->gexec, p->graph, 0) != cudaSuccess) {
+        drop_graph(p);
+        return VL_ECUDA;
+      }
+      p->bound_out = dout;
+    }
+    for (int q = 0; q < vl_plan::NEV; q++)
+      if (cudaGraphExecEventRecordNodeSetEvent(p->gexec, p->ev_node[q], ev[q]) != cudaSuccess) return VL_ECUDA;
+    if (cudaGraphLaunch(p->gexec, st) != cudaSuccess) return VL_ECUDA;
+  } else {
+    if (enqueue_pass(p, ws, dout, st, ev) != cudaSuccess) return VL_ECUDA;
+  }
+  p->runs++;
+  if (out_space == VL_HOST) {
+    const size_t bytes = sizeof(vl_proof) * p->jobs.size();
+    if (cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return VL_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return VL_ECUDA;
+  }
+  return VL_OK;
+}
+
+int make_plan(const vl_job* jobs, int32_t njobs, const vl_batch_opts* opts, vl_plan** out) {
+  if (!jobs || njobs < 1 || !out) return VL_EINVAL;
+  vl_plan* p = new (std::nothrow) vl_plan();
+  if (!p) return VL_ENOMEM;
+  p->jobs.assign(jobs, jobs + njobs);
+  if (opts) p->opts = *opts;
+  if (p->opts.timing_runs > 0) p->ring_runs = p->opts.timing_runs;
+  int e = build_plan(p);
+  if (e != VL_OK) {
+    delete p;
+    return e;
+  }
+  *out = p;
+  return VL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t vl_version(void) { return 100; }
+
+const char* vl_strerror(int32_t s) {
+  switch (s) {
+    case VL_OK: return "ok";
+    case VL_EINVAL: return "invalid argument";
+    case VL_ESHAPE: return "invalid shape";
+    case VL_ENOMEM: return "workspace too small";
+    case VL_ECUDA: return "CUDA error";
+    case VL_ETIMEOUT: return "device wait timed out";
+    case VL_REJECT: return "proof rejected";
+    default: return "unknown status";
+  }
+}
+
+size_t vl_workspace_bytes(const vl_job* jobs, int32_t njobs, const vl_batch_opts* opts) {
+  vl_plan* p = nullptr;
+  if (make_plan(jobs, njobs, opts, &p) != VL_OK) return 0;
+  const size_t t = p->total;
+  delete p;
+  return t;
+}
+
+int32_t vl_plan_create(const vl_job* jobs, int32_t njobs, const vl_batch_opts* opts, vl_plan** plan) {
+  return make_plan(jobs, njobs, opts, plan);
+}
+
+size_t vl_plan_workspace_bytes(const vl_plan* plan) { return plan ? plan->total : 0; }
+
+int32_t vl_plan_launches(const vl_plan* plan) { return plan ? 3 : 0; }
+
+int32_t vl_plan_run(vl_plan* plan, void* workspace, size_t workspace_bytes, vl_proof* out, int32_t out_space,
+                    void* stream) {
+  if (!plan) return VL_EINVAL;
+  const bool graph = plan->opts.use_graph != 2;
+  return run_plan(plan, workspace, workspace_bytes, out, out_space, static_cast<cudaStream_t>(stream), graph);
+}
+
+int32_t vl_plan_phase_ms(vl_plan* plan, float* ms, int32_t max_runs, int32_t reset) {
+  if (!plan || (!ms && max_runs > 0) || max_runs < 0) return -VL_EINVAL;
+  const long avail = std::min<long>(plan->runs - plan->timing_base, plan->ring_runs);
+  const long cnt = std::min<long>(avail, max_runs);
+  for (long i = 0; i < cnt; i++) {
+    const long run = plan->runs - cnt + i;
+    cudaEvent_t* ev = slot_events(plan, run);
+    if (cudaEventSynchronize(ev[3]) != cudaSuccess) return -VL_ECUDA;
+    for (int q = 0; q < 3; q++)
+      if (cudaEventElapsedTime(&ms[i * 3 + q], ev[q], ev[q + 1]) != cudaSuccess) return -VL_ECUDA;
+  }
+  if (reset) plan->timing_base = plan->runs;
+  return (int32_t)cnt;
+}
+
+void vl_plan_destroy(vl_plan* plan) {
+  if (!plan) return;
+  drop_graph(plan);
+  for (cudaEvent_t ev : plan->ring) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : plan->cap_ev)
+    if (ev) cudaEventDestroy(ev);
+  delete plan;
+}
+
+int32_t vl_prove_batch(const vl_job* jobs, int32_t njobs, void* workspace, size_t workspace_bytes, vl_proof* out,
+                       int32_t out_space, void* stream, const vl_batch_opts* opts) {
+  vl_plan* p = nullptr;
+  int e = make_plan(jobs, njobs, opts, &p);
+  if (e != VL_OK) return e;
+  // Descriptor tables are uploaded synchronously, so the host plan can go
+  // while device work is still queued.
+  e = run_plan(p, workspace, workspace_bytes, out, out_space, static_cast<cudaStream_t>(stream), false);
+  vl_plan_destroy(p);
+  return e;
+}
+
+int32_t vl_prove_matmul(const vl_mat* P, const vl_mat* Q, const vl_fs_init* fs, void* workspace,
+                        size_t workspace_bytes, vl_proof* out, void* stream) {
+  if (!P || !Q || !fs || !out) return VL_EINVAL;
+  vl_job j;
+  j.P = *P;
+  j.Q = *Q;
+  j.fs = *fs;
+  return vl_prove_batch(&j, 1, workspace, workspace_bytes, out, VL_HOST, stream, nullptr);
+}
+
+int32_t vl_encode(const vl_mat* src, void* dst, void* stream) {
+  if (!src || !dst) return VL_EINVAL;
+  int e = check_mat(src, true);
+  if (e != VL_OK) return e;
+  if (src->dtype != VL_I16 || src->space != VL_DEVICE) return VL_EINVAL;
+  if (reinterpret_cast<uintptr_t>(dst) & 15) return VL_EINVAL;
+  return cuda_status(launch_encode(static_cast<const int16_t*>(src->data), src->rows, src->cols, src->ld,
+                                   static_cast<Fr*>(dst), static_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

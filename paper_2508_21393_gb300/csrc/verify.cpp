@@ -1,0 +1,163 @@
+// Host verifier of one matmul sumcheck proof (the verifier of Def. def:ip,
+// checked for completeness in Sec. V-B and soundness in Sec. V-A).
+//
+// It replays the transcript from the public statement (seed, dims, transpose
+// flags, binds), re-derives u, v and every r_i, checks g_i(0) + g_i(1)
+// against the running claim, evaluates g_i(r_i) by Lagrange interpolation
+// through 0, 1, 2, checks the final claim a_r . b_r, the final transcript
+// state, and evaluates A~(u, r), B~(r, v), C~(u, v) directly from the
+// matrices (the stand-in for polynomial-commitment openings, Sec. II-A).
+#include <cstring>
+#include <vector>
+
+#include "fr.cuh"
+#include "transcript.cuh"
+#include "verilora.h"
+
+using namespace vl;
+
+namespace {
+
+int ceil_log2(int64_t x) {
+  int d = 0;
+  while ((int64_t(1) << d) < x) d++;
+  return d;
+}
+
+Fr fr_from_api(const vl_fr& x) {
+  Fr a;
+  for (int i = 0; i < 8; i++) a.v[i] = x.limb[i];
+  return a;
+}
+
+// Entry (i, j) of op(M) as a canonical field element.
+struct HostMat {
+  const vl_mat* M;
+  int64_t rows() const { return M->trans ? M->cols : M->rows; }
+  int64_t cols() const { return M->trans ? M->rows : M->cols; }
+  Fr at(int64_t i, int64_t j) const {
+    const int64_t r = M->trans ? j : i, c = M->trans ? i : j;
+    const int64_t idx = r * M->ld + c;
+    switch (M->dtype) {
+      case VL_I16: return fr_from_i64(static_cast<const int16_t*>(M->data)[idx]);
+      case VL_I64: return fr_from_i64(static_cast<const int64_t*>(M->data)[idx]);
+      default: return from_mont(static_cast<const Fr*>(M->data)[idx]);
+    }
+  }
+};
+
+// eq table in Montgomery form, MSB-first variables, `size` leading entries.
+std::vector<Fr> eq_table(const std::vector<Fr>& x, int64_t size) {
+  std::vector<Fr> t(1, fr_r1());
+  for (size_t v = 0; v < x.size(); v++) {
+    std::vector<Fr> n(t.size() * 2);
+    const Fr one_minus = fr_sub(fr_r1(), x[v]);
+    for (size_t j = 0; j < t.size(); j++) {
+      n[2 * j] = mont_mul(t[j], one_minus);
+      n[2 * j + 1] = mont_mul(t[j], x[v]);
+    }
+    t.swap(n);
+  }
+  t.resize((size_t)size);
+  return t;
+}
+
+// M~(x, y) = sum_{i,j} eq(x, i) M[i, j] eq(y, j) (Montgomery result).
+Fr mle_eval(const HostMat& M, const std::vector<Fr>& x, const std::vector<Fr>& y) {
+  const std::vector<Fr> ex = eq_table(x, M.rows()), ey = eq_table(y, M.cols());
+  Fr total = fr_zero();
+  for (int64_t i = 0; i < M.rows(); i++) {
+    Fr row = fr_zero();
+    for (int64_t j = 0; j < M.cols(); j++) row = fr_add(row, mont_mul(to_mont(M.at(i, j)), ey[j]));
+    total = fr_add(total, mont_mul(row, ex[i]));
+  }
+  return total;
+}
+
+Fr inv2_mont() {
+  // (r + 1) / 2 for odd r.
+  Fr h;
+  uint32_t carry = 0;
+  for (int i = 7; i >= 0; i--) {
+    const uint32_t l = r_limb(i);
+    h.v[i] = (l >> 1) | (carry << 31);
+    carry = l & 1;
+  }
+  Fr one = fr_small(1);
+  return to_mont(fr_add(h, one));
+}
+
+// g(x) through (0, g0), (1, g1), (2, g2); all Montgomery.
+Fr interp(const Fr& g0, const Fr& g1, const Fr& g2, const Fr& x) {
+  const Fr one = fr_r1(), two = fr_add(one, one), i2 = inv2_mont();
+  const Fr xm1 = fr_sub(x, one), xm2 = fr_sub(x, two);
+  const Fr l0 = mont_mul(mont_mul(xm1, xm2), i2);
+  const Fr l1 = fr_neg(mont_mul(x, xm2));
+  const Fr l2 = mont_mul(mont_mul(x, xm1), i2);
+  return fr_add(fr_add(mont_mul(g0, l0), mont_mul(g1, l1)), mont_mul(g2, l2));
+}
+
+int check_host_mat(const vl_mat* M) {
+  if (!M || !M->data) return VL_EINVAL;
+  if (M->space != VL_HOST || M->reserved != 0) return VL_EINVAL;
+  if (M->dtype != VL_I16 && M->dtype != VL_I64 && M->dtype != VL_FR_MONT) return VL_EINVAL;
+  if (M->trans != 0 && M->trans != 1) return VL_EINVAL;
+  if (M->rows < 1 || M->cols < 1) return VL_ESHAPE;
+  if (M->ld < M->cols) return VL_EINVAL;
+  return VL_OK;
+}
+
+}  // namespace
+
+extern "C" int32_t vl_verify_matmul(const vl_mat* P, const vl_mat* Q, const vl_mat* C, const vl_fs_init* fs,
+                                    const vl_proof* proof) {
+  int e;
+  if ((e = check_host_mat(P)) != VL_OK || (e = check_host_mat(Q)) != VL_OK || (e = check_host_mat(C)) != VL_OK)
+    return e;
+  if (!fs || !proof) return VL_EINVAL;
+  const HostMat A{P}, B{Q}, Cm{C};
+  const int64_t m = A.rows(), k = A.cols(), n = B.cols();
+  if (B.rows() != k || Cm.rows() != m || Cm.cols() != n) return VL_ESHAPE;
+  if (m > VL_MAX_REDUCE || n > VL_MAX_REDUCE || k > (int64_t(1) << VL_MAX_ROUNDS)) return VL_ESHAPE;
+  const int d0 = ceil_log2(m), d1 = ceil_log2(k), d2 = ceil_log2(n);
+  if (proof->m != m || proof->k != k || proof->n != n || proof->d0 != d0 || proof->d1 != d1 || proof->d2 != d2)
+    return VL_REJECT;
+  if (proof->status != VL_OK) return VL_REJECT;
+  // Every transmitted element must be canonical.
+  if (!lt_r(fr_from_api(proof->c)) || !lt_r(fr_from_api(proof->a_r)) || !lt_r(fr_from_api(proof->b_r)))
+    return VL_REJECT;
+  for (int i = 0; i < d1; i++)
+    for (int q = 0; q < 3; q++)
+      if (!lt_r(fr_from_api(proof->g[i][q]))) return VL_REJECT;
+
+  uint8_t S[32];
+  ts_start(S, fs->seed, (uint32_t)m, (uint32_t)k, (uint32_t)n, (uint32_t)P->trans, (uint32_t)Q->trans,
+           &fs->bind[0][0]);
+  std::vector<Fr> u(d0), v(d2), rs;
+  for (int t = 0; t < d0; t++) u[t] = to_mont(ts_challenge(S, LBL_U, t));
+  ts_squeeze_done(S, LBL_U, d0);
+  for (int t = 0; t < d2; t++) v[t] = to_mont(ts_challenge(S, LBL_V, t));
+  ts_squeeze_done(S, LBL_V, d2);
+
+  const Fr c = fr_from_api(proof->c);
+  if (!fr_eq(to_mont(c), mle_eval(Cm, u, v))) return VL_REJECT;
+  ts_absorb_fr(S, LBL_C, &c, 1);
+  Fr claim = to_mont(c);
+  for (int i = 0; i < d1; i++) {
+    const Fr g[3] = {fr_from_api(proof->g[i][0]), fr_from_api(proof->g[i][1]), fr_from_api(proof->g[i][2])};
+    if (!fr_eq(fr_add(g[0], g[1]), from_mont(claim))) return VL_REJECT;
+    ts_absorb_fr(S, LBL_G, g, 3);
+    const Fr r = to_mont(ts_challenge(S, LBL_R, 0));
+    ts_squeeze_done(S, LBL_R, 1);
+    rs.push_back(r);
+    claim = interp(to_mont(g[0]), to_mont(g[1]), to_mont(g[2]), r);
+  }
+  const Fr ar = fr_from_api(proof->a_r), br = fr_from_api(proof->b_r);
+  if (!fr_eq(claim, mont_mul(to_mont(ar), to_mont(br)))) return VL_REJECT;
+  const Fr fin[2] = {ar, br};
+  ts_absorb_fr(S, LBL_F, fin, 2);
+  if (std::memcmp(S, proof->state, 32) != 0) return VL_REJECT;
+  if (!fr_eq(to_mont(ar), mle_eval(A, u, rs))) return VL_REJECT;
+  if (!fr_eq(to_mont(br), mle_eval(B, rs, v))) return VL_REJECT;
+  return VL_OK;
+}

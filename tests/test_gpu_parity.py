@@ -1,0 +1,215 @@
+"""GPU parity: every proof from the CUDA path equals the oracle's proof byte
+for byte (transcript state included), through the C ABI.
+
+Shapes span several fold tiles and ragged tails in every orientation
+(column-sum tiles of 1024 columns x 256 rows, row-dot tiles of 32 rows x 2048
+columns), transposed operands, unaligned leading dimensions and base
+pointers, Montgomery-form operands, batches, graph replay and host-space
+operands.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2508_21393_gb300 import binding as B
+from paper_2508_21393_gb300 import workload as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no GPU", allow_module_level=True)
+
+
+def _rand(rng, shape):
+    return rng.integers(-(1 << 15), 1 << 15, size=shape).astype(np.int16)
+
+
+def _ws(nbytes):
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+
+
+def gpu_prove(P, Q, tp=0, tq=0, seed=0):
+    Pd = torch.from_numpy(np.ascontiguousarray(P)).cuda()
+    Qd = torch.from_numpy(np.ascontiguousarray(Q)).cuda()
+    jb = B.job(Pd, Qd, tp, tq, seed)
+    n = B.vl_workspace_bytes([jb])
+    assert n > 0
+    ws = _ws(n)
+    pf = B.vl_prove_matmul(jb.P, jb.Q, jb.fs, ws.data_ptr(), n)
+    assert pf.status == 0
+    return pf
+
+
+def _shapes(m, k, n, tp, tq, rng):
+    A = _rand(rng, (m, k))
+    Bm = _rand(rng, (k, n))
+    P = np.ascontiguousarray(A.T) if tp else A
+    Q = np.ascontiguousarray(Bm.T) if tq else Bm
+    return A, Bm, P, Q
+
+
+def test_single_matmul_64x128x64():
+    job = W.single_matmul()
+    pf = gpu_prove(job["P"], job["Q"], 0, 0, job["seed"])
+    ref = oracle.prove_matmul(job["P"], job["Q"], 0, 0, seed=job["seed"])
+    assert B.proof_bytes(pf) == ref.to_bytes()
+
+
+@pytest.mark.parametrize("m,k,n,tp,tq", [
+    (37, 53, 29, 0, 0), (1, 1, 1, 0, 0), (5, 1, 3, 0, 0), (1, 64, 1, 0, 0), (2, 3, 1, 1, 1),
+    (300, 1100, 70, 0, 0),     # column-sum: 2 column tiles x 2 row tiles; row-dot: 35 row tiles
+    (70, 40, 2100, 0, 0),      # row-dot over 2100 columns: two column chunks
+    (2100, 40, 70, 1, 1),      # transposed: row-dot over 2100 columns, column-sum of Q^T
+    (257, 33, 300, 1, 1), (64, 128, 64, 1, 0), (64, 128, 64, 0, 1),
+    (3, 4097, 5, 0, 0),        # k just above a power of two: d1 = 13, mostly padding
+])
+def test_ragged_and_transposed(m, k, n, tp, tq):
+    rng = np.random.default_rng(m * 7919 + k * 31 + n + 100 * tp + 1000 * tq)
+    A, Bm, P, Q = _shapes(m, k, n, tp, tq, rng)
+    seed = m * k + n
+    pf = gpu_prove(P, Q, tp, tq, seed)
+    ref = oracle.prove_matmul(P, Q, tp, tq, seed=seed)
+    assert B.proof_bytes(pf) == ref.to_bytes()
+
+
+def test_extreme_values():
+    """All entries at the int16 extremes (the +2^15 offset and its correction)."""
+    m, k, n = 33, 70, 40
+    for val in (-(1 << 15), (1 << 15) - 1, 0):
+        P = np.full((m, k), val, np.int16)
+        Q = np.full((k, n), -(1 << 15), np.int16)
+        pf = gpu_prove(P, Q, 0, 0, 5)
+        assert B.proof_bytes(pf) == oracle.prove_matmul(P, Q, 0, 0, seed=5).to_bytes()
+
+
+def test_unaligned_views():
+    rng = np.random.default_rng(3)
+    big = _rand(rng, (90, 203))
+    Qbig = _rand(rng, (1 + 150 * 77,))
+    Pd_full = torch.from_numpy(big).cuda()
+    Pd = Pd_full[5:85, 3:153]                      # ld = 203 (odd), base offset 3 elements
+    Qd = torch.from_numpy(Qbig).cuda()[1:].view(150, 77)  # base misaligned by 2 bytes
+    jb = B.job(Pd, Qd, 0, 0, 42)
+    n = B.vl_workspace_bytes([jb])
+    ws = _ws(n)
+    pf = B.vl_prove_matmul(jb.P, jb.Q, jb.fs, ws.data_ptr(), n)
+    ref = oracle.prove_matmul(big[5:85, 3:153], Qbig[1:].reshape(150, 77), 0, 0, seed=42)
+    assert B.proof_bytes(pf) == ref.to_bytes()
+
+
+def _encode(Md):
+    out = torch.empty((Md.shape[0], Md.shape[1], 8), dtype=torch.int32, device="cuda")
+    B.vl_encode(B.mat(Md), out.data_ptr())
+    return out
+
+
+def test_encode_matches_definition():
+    rng = np.random.default_rng(11)
+    M = _rand(rng, (67, 45))
+    M[0, :4] = [0, 1, -1, -(1 << 15)]
+    out = _encode(torch.from_numpy(M).cuda()).cpu().numpy().view(np.uint32)
+    for i in range(M.shape[0]):
+        for j in range(M.shape[1]):
+            assert list(out[i, j]) == oracle.limbs_le32(oracle.encode_montgomery(int(M[i, j])))
+
+
+@pytest.mark.parametrize("m,k,n,tp,tq", [(37, 53, 29, 0, 0), (300, 260, 20, 1, 1), (5, 600, 7, 0, 1)])
+def test_montgomery_operands_prove_the_same_statement(m, k, n, tp, tq):
+    rng = np.random.default_rng(m + k + n)
+    A, Bm, P, Q = _shapes(m, k, n, tp, tq, rng)
+    Pe = _encode(torch.from_numpy(P).cuda())
+    Qe = _encode(torch.from_numpy(Q).cuda())
+    jb = B.job(Pe, Qe, tp, tq, 77)
+    nb = B.vl_workspace_bytes([jb])
+    ws = _ws(nb)
+    pf = B.vl_prove_matmul(jb.P, jb.Q, jb.fs, ws.data_ptr(), nb)
+    ref = oracle.prove_matmul(P, Q, tp, tq, seed=77)
+    assert B.proof_bytes(pf) == ref.to_bytes()
+
+
+def _lora_jobs(n=64, d=256, k=256, r=8, layer=0, proj="q"):
+    t = W.lora_projection(W.GLOBAL_SEED, layer, proj, n, d, k, r)
+    return W.projection_products(t)
+
+
+def _dev_jobs(jobs):
+    keep, out = [], []
+    cache = {}
+    for j in jobs:
+        for key in ("P", "Q"):
+            a = j[key]
+            if id(a) not in cache:
+                cache[id(a)] = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        Pd, Qd = cache[id(j["P"])], cache[id(j["Q"])]
+        out.append(B.job(Pd, Qd, j["tp"], j["tq"], j["seed"]))
+    keep.append(cache)
+    return out, keep
+
+
+def test_lora_step_batch_equals_alone_and_oracle():
+    jobs = _lora_jobs() + _lora_jobs(n=32, d=128, k=192, r=16, layer=1, proj="o")
+    dj, keep = _dev_jobs(jobs)
+    nb = B.vl_workspace_bytes(dj)
+    ws = _ws(nb)
+    proofs = B.vl_prove_batch(dj, ws.data_ptr(), nb)
+    for j, jb, pf in zip(jobs, dj, proofs):
+        ref = oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes()
+        assert B.proof_bytes(pf) == ref, j["name"]
+        n1 = B.vl_workspace_bytes([jb])
+        ws1 = _ws(n1)
+        alone = B.vl_prove_matmul(jb.P, jb.Q, jb.fs, ws1.data_ptr(), n1)
+        assert B.proof_bytes(alone) == ref, j["name"]
+
+
+def test_plan_graph_replay_device_output():
+    jobs = _lora_jobs(n=48, d=128, k=128, r=8)
+    dj, keep = _dev_jobs(jobs)
+    plan = B.vl_plan_create(dj)
+    try:
+        nb = B.vl_plan_workspace_bytes(plan)
+        ws = _ws(nb)
+        out = torch.zeros(len(dj) * ctypes.sizeof(B.vl_proof), dtype=torch.uint8, device="cuda")
+        refs = [oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes() for j in jobs]
+        for _ in range(3):
+            out.zero_()
+            B.vl_plan_run(plan, ws.data_ptr(), nb, out.data_ptr(), B.VL_DEVICE)
+            torch.cuda.synchronize()
+            host = (B.vl_proof * len(dj)).from_buffer_copy(out.cpu().numpy().tobytes())
+            for pf, ref in zip(host, refs):
+                assert B.proof_bytes(pf) == ref
+    finally:
+        B.vl_plan_destroy(plan)
+
+
+def test_host_operands_and_host_output():
+    jobs = _lora_jobs(n=40, d=96, k=160, r=8, layer=2, proj="v")
+    hj = [B.job(np.ascontiguousarray(j["P"]), np.ascontiguousarray(j["Q"]), j["tp"], j["tq"], j["seed"])
+          for j in jobs]
+    plan = B.vl_plan_create(hj)
+    try:
+        nb = B.vl_plan_workspace_bytes(plan)
+        ws = _ws(nb)
+        out = (B.vl_proof * len(hj))()
+        for _ in range(2):
+            B.vl_plan_run(plan, ws.data_ptr(), nb, out, B.VL_HOST)
+            for j, pf in zip(jobs, out):
+                ref = oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes()
+                assert B.proof_bytes(pf) == ref
+    finally:
+        B.vl_plan_destroy(plan)
+
+
+def test_gpu_proofs_verify_and_perturbations_reject():
+    rng = np.random.default_rng(19)
+    A, Bm, P, Q = _shapes(24, 50, 12, 1, 0, rng)
+    C = W.exact_matmul(A, Bm)
+    pf = gpu_prove(P, Q, 1, 0, 314)
+    fs = B.fs_init(314)
+    assert B.vl_verify_matmul(B.mat(P, 1), B.mat(Q, 0), B.mat(C), fs, pf)
+    opf = oracle.prove_matmul(P, Q, 1, 0, seed=314)
+    assert oracle.verify_matmul(P, Q, C, opf, 1, 0, seed=314)[0]
+    pf.g[2][1].limb[3] ^= 1
+    assert not B.vl_verify_matmul(B.mat(P, 1), B.mat(Q, 0), B.mat(C), fs, pf)
