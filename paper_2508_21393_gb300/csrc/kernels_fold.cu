@@ -280,8 +280,14 @@ __global__ void __launch_bounds__(FOLD_THREADS) fold_kernel(const FoldTask* __re
   }
 }
 
+// The limit is per kernel and process-wide, so it only ever grows: a plan
+// bound later with smaller tiles must not lower it under an earlier plan.
 cudaError_t fold_set_smem(int smem_bytes) {
-  return cudaFuncSetAttribute(fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  static int current = 48 * 1024;
+  if (smem_bytes <= current) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e == cudaSuccess) current = smem_bytes;
+  return e;
 }
 
 cudaError_t launch_fold(const FoldTask* tasks, const FoldTile* tiles, int ntiles, const DevProof* proofs,
