@@ -5,7 +5,7 @@ Metric: matmul MACs proved per second (sum over the step's products of
 m.k.n, divided by wall time), and ms per LoRA-step proof, batched (one plan,
 CUDA-graph replay of the whole step) against the unbatched per-matmul path.
 Every proof is bit-exact with the oracle (tests/test_gpu_parity.py,
-tests/test_gpu_fullsize.py).
+tests/test_gpu_parity_fullsize.py).
 
 Default workload: the 7B-shaped step -- 32 layers x {q,k,v,o}, hidden 4096,
 sequence 512, LoRA rank per layer from {8, 16, 64}; eight products per

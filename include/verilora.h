@@ -128,6 +128,10 @@ int32_t vl_version(void);
 /* Name of a status code (static string). */
 const char* vl_strerror(int32_t status);
 
+/* Detail of the last VL_ECUDA failure on the calling thread: the failing
+ * step and the CUDA error string ("" if none).  Valid until the next call. */
+const char* vl_last_error(void);
+
 /*
  * Device workspace needed to prove `njobs` products in one batch, in bytes.
  * Host-space operands add staging room for one device copy of each distinct

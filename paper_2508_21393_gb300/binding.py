@@ -25,7 +25,7 @@ VL_MAX_ROUNDS = 24
 VL_MAX_REDUCE = 1 << 16
 
 # Every symbol include/verilora.h declares.
-EXPORTS = ("vl_version", "vl_strerror", "vl_workspace_bytes", "vl_prove_matmul", "vl_prove_batch",
+EXPORTS = ("vl_version", "vl_strerror", "vl_last_error", "vl_workspace_bytes", "vl_prove_matmul", "vl_prove_batch",
            "vl_plan_create", "vl_plan_workspace_bytes", "vl_plan_run", "vl_plan_launches", "vl_plan_phase_ms",
            "vl_plan_destroy", "vl_verify_matmul", "vl_encode")
 
@@ -67,7 +67,8 @@ class vl_batch_opts(ctypes.Structure):
 
 class VLError(RuntimeError):
     def __init__(self, code, what):
-        super().__init__(f"{what}: {vl_strerror(code)} ({code})")
+        detail = f" [{vl_last_error()}]" if code == VL_ECUDA else ""
+        super().__init__(f"{what}: {vl_strerror(code)} ({code}){detail}")
         self.code = code
 
 
@@ -86,6 +87,7 @@ def lib():
     L.vl_version.restype = ctypes.c_int32
     L.vl_strerror.argtypes = [ctypes.c_int32]
     L.vl_strerror.restype = ctypes.c_char_p
+    L.vl_last_error.restype = ctypes.c_char_p
     L.vl_workspace_bytes.argtypes = [P(vl_job), ctypes.c_int32, P(vl_batch_opts)]
     L.vl_workspace_bytes.restype = ctypes.c_size_t
     L.vl_prove_matmul.argtypes = [P(vl_mat), P(vl_mat), P(vl_fs_init), ctypes.c_void_p, ctypes.c_size_t,
@@ -216,6 +218,10 @@ def vl_version():
 
 def vl_strerror(code):
     return lib().vl_strerror(int(code)).decode()
+
+
+def vl_last_error():
+    return lib().vl_last_error().decode()
 
 
 def vl_workspace_bytes(jobs, opts=None):

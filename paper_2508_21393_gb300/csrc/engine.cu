@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <new>
@@ -100,6 +101,7 @@ struct vl_plan {
   static constexpr int NEV = 4;  // before clear, before fold, after fold, after rounds
   std::vector<cudaEvent_t> ring;
   cudaEvent_t cap_ev[NEV] = {};
+  cudaStream_t cap_stream = nullptr;  // private stream for graph capture
   cudaGraphNode_t ev_node[NEV] = {};
   long runs = 0, timing_base = 0;
 };
@@ -236,7 +238,17 @@ const void* operand_ptr(const vl_plan* p, const vl_mat& M, uint8_t* ws) {
   return ws + p->staging.at(M.data).off;
 }
 
-int cuda_status(cudaError_t e) { return e == cudaSuccess ? VL_OK : VL_ECUDA; }
+thread_local char g_last_error[256] = "";
+
+void note_error(const char* where, cudaError_t e) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+}
+
+int cuda_status(cudaError_t e, const char* where = "cuda") {
+  if (e == cudaSuccess) return VL_OK;
+  note_error(where, e);
+  return VL_ECUDA;
+}
 
 // Fill device pointers for this workspace and upload the descriptor tables.
 int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
@@ -266,7 +278,7 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
   // The host vectors must outlive the copies: wait for them.
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess && p->fold_smem > 0) e = fold_set_smem(p->fold_smem);
-  return cuda_status(e);
+  return cuda_status(e, "bind_workspace");
 }
 
 cudaError_t ensure_events(vl_plan* p) {
@@ -338,7 +350,7 @@ void drop_graph(vl_plan* p) {
 int stage_host_operands(vl_plan* p, uint8_t* ws, cudaStream_t st) {
   for (auto& kv : p->staging) {
     cudaError_t e = cudaMemcpyAsync(ws + kv.second.off, kv.first, kv.second.bytes, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return VL_ECUDA;
+    if (e != cudaSuccess) return cuda_status(e, "stage host operand");
   }
   return VL_OK;
 }
@@ -351,7 +363,7 @@ int run_plan(vl_plan* p, void* workspace, size_t ws_bytes, vl_proof* out, int32_
   if (reinterpret_cast<uintptr_t>(workspace) & (ALIGN - 1)) return VL_EINVAL;
   uint8_t* ws = static_cast<uint8_t*>(workspace);
   vl_proof* dout = out_space == VL_DEVICE ? out : reinterpret_cast<vl_proof*>(ws + p->off_out);
-  if (ensure_events(p) != cudaSuccess) return VL_ECUDA;
+  if (cudaError_t ee = ensure_events(p)) return cuda_status(ee, "cudaEventCreate");
   if (p->bound_ws != workspace) {
     drop_graph(p);
     int e = bind_workspace(p, ws, st);
@@ -361,34 +373,47 @@ int run_plan(vl_plan* p, void* workspace, size_t ws_bytes, vl_proof* out, int32_
   int e = stage_host_operands(p, ws, st);
   if (e != VL_OK) return e;
   cudaEvent_t* ev = slot_events(p, p->runs);
+  cudaError_t ce;
   if (graph) {
     if (p->gexec && p->bound_out != dout) drop_graph(p);
     if (!p->gexec) {
-      cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-      if (ce != cudaSuccess) return VL_ECUDA;
-      cudaError_t ke = enqueue_pass(p, ws, dout, st, p->cap_ev);
-      ce = cudaStreamEndCapture(st, &p->graph);
+      // Capture on a private stream: the caller's stream may be the legacy
+      // default stream, which cannot be captured.  The graph is then launched
+      // on the caller's stream.
+      if (!p->cap_stream && (ce = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_status(ce, "cudaStreamCreate");
+      if ((ce = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_status(ce, "cudaStreamBeginCapture");
+      cudaError_t ke = enqueue_pass(p, ws, dout, p->cap_stream, p->cap_ev);
+      ce = cudaStreamEndCapture(p->cap_stream, &p->graph);
       if (ke != cudaSuccess || ce != cudaSuccess) {
         drop_graph(p);
-        return VL_ECUDA;
+        return cuda_status(ke != cudaSuccess ? ke : ce, "graph capture");
       }
-      if (find_event_nodes(p) != cudaSuccess || cudaGraphInstantiate(&p->gexec, p->graph, 0) != cudaSuccess) {
+      if ((ce = find_event_nodes(p)) != cudaSuccess) {
         drop_graph(p);
-        return VL_ECUDA;
+        return cuda_status(ce, "graph event nodes");
+      }
+      if ((ce = cudaGraphInstantiate(&p->gexec, p->graph, 0)) != cudaSuccess) {
+        p->gexec = nullptr;
+        drop_graph(p);
+        return cuda_status(ce, "cudaGraphInstantiate");
       }
       p->bound_out = dout;
     }
     for (int q = 0; q < vl_plan::NEV; q++)
-      if (cudaGraphExecEventRecordNodeSetEvent(p->gexec, p->ev_node[q], ev[q]) != cudaSuccess) return VL_ECUDA;
-    if (cudaGraphLaunch(p->gexec, st) != cudaSuccess) return VL_ECUDA;
+      if ((ce = cudaGraphExecEventRecordNodeSetEvent(p->gexec, p->ev_node[q], ev[q])) != cudaSuccess)
+        return cuda_status(ce, "cudaGraphExecEventRecordNodeSetEvent");
+    if ((ce = cudaGraphLaunch(p->gexec, st)) != cudaSuccess) return cuda_status(ce, "cudaGraphLaunch");
   } else {
-    if (enqueue_pass(p, ws, dout, st, ev) != cudaSuccess) return VL_ECUDA;
+    if ((ce = enqueue_pass(p, ws, dout, st, ev)) != cudaSuccess) return cuda_status(ce, "enqueue_pass");
   }
   p->runs++;
   if (out_space == VL_HOST) {
     const size_t bytes = sizeof(vl_proof) * p->jobs.size();
-    if (cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return VL_ECUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return VL_ECUDA;
+    if ((ce = cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_status(ce, "proof copy-out");
+    if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_status(ce, "cudaStreamSynchronize");
   }
   return VL_OK;
 }
@@ -466,9 +491,12 @@ int32_t vl_plan_phase_ms(vl_plan* plan, float* ms, int32_t max_runs, int32_t res
   return (int32_t)cnt;
 }
 
+const char* vl_last_error(void) { return g_last_error; }
+
 void vl_plan_destroy(vl_plan* plan) {
   if (!plan) return;
   drop_graph(plan);
+  if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
   for (cudaEvent_t ev : plan->ring) cudaEventDestroy(ev);
   for (cudaEvent_t ev : plan->cap_ev)
     if (ev) cudaEventDestroy(ev);
@@ -504,7 +532,8 @@ int32_t vl_encode(const vl_mat* src, void* dst, void* stream) {
   if (src->dtype != VL_I16 || src->space != VL_DEVICE) return VL_EINVAL;
   if (reinterpret_cast<uintptr_t>(dst) & 15) return VL_EINVAL;
   return cuda_status(launch_encode(static_cast<const int16_t*>(src->data), src->rows, src->cols, src->ld,
-                                   static_cast<Fr*>(dst), static_cast<cudaStream_t>(stream)));
+                                   static_cast<Fr*>(dst), static_cast<cudaStream_t>(stream)),
+                     "encode_kernel");
 }
 
 }  // extern "C"
