@@ -159,6 +159,8 @@ def mat(a, trans=0, dtype=None):
         m.data = a.data_ptr()
         m.space = VL_DEVICE if a.is_cuda else VL_HOST
     m.rows, m.cols = int(a.shape[0]), int(a.shape[1])
+    if m.rows == 1 and m.ld < m.cols:
+        m.ld = m.cols  # a size-1 dimension may report any stride
     m.trans = int(trans)
     m.reserved = 0
     if dtype is not None:
