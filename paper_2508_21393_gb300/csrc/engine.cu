@@ -306,14 +306,15 @@ cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t s
   const FoldTask* dt = reinterpret_cast<const FoldTask*>(ws + p->off_tasks);
   const FoldTile* dl = reinterpret_cast<const FoldTile*>(ws + p->off_tiles);
   const int np = (int)p->jobs.size();
-  cudaError_t e = cudaEventRecord(ev[0], st);
+  // External records become event-record nodes when captured in a graph.
+  cudaError_t e = cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
   if (e == cudaSuccess) e = cudaMemsetAsync(ws + p->off_acc, 0, p->acc_bytes, st);
   if (e == cudaSuccess) e = launch_prologue(dp, np, st);
-  if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
   if (e == cudaSuccess) e = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, st);
-  if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
   if (e == cudaSuccess) e = launch_rounds(dp, np, dout, st);
-  if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
   return e;
 }
 
