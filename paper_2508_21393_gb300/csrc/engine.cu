@@ -301,20 +301,23 @@ cudaEvent_t* slot_events(vl_plan* p, long run) {
 
 // The device part of one proving pass (graph-capturable).  `ev`: the four
 // phase-boundary events to record.
-cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t st, cudaEvent_t* ev) {
+cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t st, cudaEvent_t* ev,
+                         bool capturing) {
   const DevProof* dp = reinterpret_cast<const DevProof*>(ws + p->off_proofs);
   const FoldTask* dt = reinterpret_cast<const FoldTask*>(ws + p->off_tasks);
   const FoldTile* dl = reinterpret_cast<const FoldTile*>(ws + p->off_tiles);
   const int np = (int)p->jobs.size();
-  // External records become event-record nodes when captured in a graph.
-  cudaError_t e = cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
+  // Under capture, external records become event-record nodes of the graph
+  // (the flag is only valid while capturing).
+  const unsigned flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  cudaError_t e = cudaEventRecordWithFlags(ev[0], st, flags);
   if (e == cudaSuccess) e = cudaMemsetAsync(ws + p->off_acc, 0, p->acc_bytes, st);
   if (e == cudaSuccess) e = launch_prologue(dp, np, st);
-  if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[1], st, flags);
   if (e == cudaSuccess) e = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, st);
-  if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2], st, flags);
   if (e == cudaSuccess) e = launch_rounds(dp, np, dout, st);
-  if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[3], st, flags);
   return e;
 }
 
@@ -385,7 +388,7 @@ int run_plan(vl_plan* p, void* workspace, size_t ws_bytes, vl_proof* out, int32_
         return cuda_status(ce, "cudaStreamCreate");
       if ((ce = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_status(ce, "cudaStreamBeginCapture");
-      cudaError_t ke = enqueue_pass(p, ws, dout, p->cap_stream, p->cap_ev);
+      cudaError_t ke = enqueue_pass(p, ws, dout, p->cap_stream, p->cap_ev, true);
       ce = cudaStreamEndCapture(p->cap_stream, &p->graph);
       if (ke != cudaSuccess || ce != cudaSuccess) {
         drop_graph(p);
@@ -407,7 +410,7 @@ int run_plan(vl_plan* p, void* workspace, size_t ws_bytes, vl_proof* out, int32_
         return cuda_status(ce, "cudaGraphExecEventRecordNodeSetEvent");
     if ((ce = cudaGraphLaunch(p->gexec, st)) != cudaSuccess) return cuda_status(ce, "cudaGraphLaunch");
   } else {
-    if ((ce = enqueue_pass(p, ws, dout, st, ev)) != cudaSuccess) return cuda_status(ce, "enqueue_pass");
+    if ((ce = enqueue_pass(p, ws, dout, st, ev, false)) != cudaSuccess) return cuda_status(ce, "enqueue_pass");
   }
   p->runs++;
   if (out_space == VL_HOST) {
