@@ -43,6 +43,7 @@ SM_MAX_MHZ = 2070.0
 # the ALU roofline of the int16 fold: 64 32-bit integer multiply-adds per SM
 # per clock, a wide (64-bit result) one taking two of them.
 MADWIDE_PER_SM_CLK = 32
+STEP_KIND = {"7b-step": "7b", "7b-proj": "7b-proj", "13b-step": "13b"}
 WORKLOADS = {
     "7b-step": "batched 7B-shaped LoRA step: 32 layers x {q,k,v,o}, hidden 4096, seq 512, ranks {8,16,64}",
     "7b-proj": "one 7B-shaped LoRA projection, n=1024, d=k=4096, r=16, eight products",
@@ -69,7 +70,7 @@ def dist_env():
 
 
 def step_jobs(kind, seed):
-    projs = W.make_step(kind, seed)
+    projs = W.make_step(STEP_KIND[kind], seed)
     jobs = [j for t in projs for j in W.projection_products(t, seed)]
     return projs, jobs
 
@@ -77,7 +78,7 @@ def step_jobs(kind, seed):
 def oracle_sample(kind, seed, nproj):
     """Time the oracle on the first `nproj` projections of the workload."""
     import oracle
-    spec = W.step_layers(kind, seed)[:nproj]
+    spec = W.step_layers(STEP_KIND[kind], seed)[:nproj]
     projs = [W.lora_projection(seed, *s) for s in spec]
     jobs = [j for t in projs for j in W.projection_products(t, seed)]
     macs = sum(W.macs(j) for j in jobs)
