@@ -235,15 +235,17 @@ def main():
         one = B.vl_batch_opts()
         one.timing_runs = 1
         plans = [B.vl_plan_create([j], one) for j in djobs]
-        sizes = [B.vl_plan_workspace_bytes(p) for p in plans]
-        ws1 = torch.empty(max(sizes), dtype=torch.uint8, device="cuda")
-        for p, sz in zip(plans, sizes):
-            B.vl_plan_run(p, ws1.data_ptr(), sz, out.data_ptr(), B.VL_DEVICE, stream)
+        sizes = [(B.vl_plan_workspace_bytes(p) + 255) // 256 * 256 for p in plans]
+        offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+        ws1 = torch.empty(int(sum(sizes)), dtype=torch.uint8, device="cuda")  # one slice per plan
+        base = ws1.data_ptr()
+        for p, sz, o in zip(plans, sizes, offs):
+            B.vl_plan_run(p, base + int(o), sz, out.data_ptr(), B.VL_DEVICE, stream)
         torch.cuda.synchronize()
         u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         u0.record(stream)
-        for p, sz in zip(plans, sizes):
-            B.vl_plan_run(p, ws1.data_ptr(), sz, out.data_ptr(), B.VL_DEVICE, stream)
+        for p, sz, o in zip(plans, sizes, offs):
+            B.vl_plan_run(p, base + int(o), sz, out.data_ptr(), B.VL_DEVICE, stream)
         u1.record(stream)
         torch.cuda.synchronize()
         unbatched_ms = u0.elapsed_time(u1)

@@ -167,7 +167,12 @@ int32_t vl_prove_batch(const vl_job* jobs, int32_t njobs, void* workspace, size_
 int32_t vl_plan_create(const vl_job* jobs, int32_t njobs, const vl_batch_opts* opts, vl_plan** plan);
 size_t vl_plan_workspace_bytes(const vl_plan* plan);
 /* Enqueue one proving pass; out: njobs proofs in `out_space` memory (VL_HOST
- * synchronises).  Host-space operands are copied in on every run. */
+ * synchronises).  Host-space operands are copied in on every run.  The first
+ * run on a workspace uploads the plan's descriptor tables into it (a
+ * synchronous copy); later runs reuse them.  Several plans may take turns on
+ * one workspace (same base pointer): a plan re-uploads its tables when
+ * another plan used the workspace since its last run.  Runs that overlap in
+ * time on the GPU must use disjoint workspaces. */
 int32_t vl_plan_run(vl_plan* plan, void* workspace, size_t workspace_bytes, vl_proof* out,
                     int32_t out_space, void* stream);
 /* Number of kernel launches one vl_plan_run enqueues (graph nodes included). */

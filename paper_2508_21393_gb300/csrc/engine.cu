@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -244,6 +245,29 @@ void note_error(const char* where, cudaError_t e) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
 }
 
+// Which plan last wrote its descriptor tables into a workspace (by base
+// pointer).  A plan whose workspace was taken over by another plan re-binds
+// (re-uploads its tables) before its next run.
+std::mutex g_ws_mu;
+std::map<const void*, const vl_plan*> g_ws_owner;
+
+bool owns_workspace(const vl_plan* p, const void* ws) {
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  auto it = g_ws_owner.find(ws);
+  return it != g_ws_owner.end() && it->second == p;
+}
+
+void claim_workspace(const vl_plan* p, const void* ws) {
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  g_ws_owner[ws] = p;
+}
+
+void release_workspaces(const vl_plan* p) {
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  for (auto it = g_ws_owner.begin(); it != g_ws_owner.end();)
+    it = it->second == p ? g_ws_owner.erase(it) : std::next(it);
+}
+
 int cuda_status(cudaError_t e, const char* where = "cuda") {
   if (e == cudaSuccess) return VL_OK;
   note_error(where, e);
@@ -368,11 +392,13 @@ int run_plan(vl_plan* p, void* workspace, size_t ws_bytes, vl_proof* out, int32_
   uint8_t* ws = static_cast<uint8_t*>(workspace);
   vl_proof* dout = out_space == VL_DEVICE ? out : reinterpret_cast<vl_proof*>(ws + p->off_out);
   if (cudaError_t ee = ensure_events(p)) return cuda_status(ee, "cudaEventCreate");
-  if (p->bound_ws != workspace) {
-    drop_graph(p);
+  if (p->bound_ws != workspace || !owns_workspace(p, workspace)) {
+    // The graph holds kernel arguments into the workspace; rebuilt on change.
+    if (p->bound_ws != workspace) drop_graph(p);
     int e = bind_workspace(p, ws, st);
     if (e != VL_OK) return e;
     p->bound_ws = workspace;
+    claim_workspace(p, workspace);
   }
   int e = stage_host_operands(p, ws, st);
   if (e != VL_OK) return e;
@@ -499,6 +525,7 @@ const char* vl_last_error(void) { return g_last_error; }
 
 void vl_plan_destroy(vl_plan* plan) {
   if (!plan) return;
+  release_workspaces(plan);
   drop_graph(plan);
   if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
   for (cudaEvent_t ev : plan->ring) cudaEventDestroy(ev);

@@ -213,3 +213,25 @@ def test_gpu_proofs_verify_and_perturbations_reject():
     assert oracle.verify_matmul(P, Q, C, opf, 1, 0, seed=314)[0]
     pf.g[2][1].limb[3] ^= 1
     assert not B.vl_verify_matmul(B.mat(P, 1), B.mat(Q, 0), B.mat(C), fs, pf)
+
+
+def test_plans_taking_turns_on_one_workspace():
+    """Two plans alternate on one workspace: each re-uploads its tables."""
+    ja = _lora_jobs(n=32, d=64, k=96, r=8, layer=3, proj="k")
+    jb_ = [_lora_jobs(n=24, d=80, k=48, r=16, layer=4, proj="q")[i] for i in (0, 3, 6)]
+    da, ka = _dev_jobs(ja)
+    db, kb = _dev_jobs(jb_)
+    pa, pb = B.vl_plan_create(da), B.vl_plan_create(db)
+    try:
+        nb = max(B.vl_plan_workspace_bytes(pa), B.vl_plan_workspace_bytes(pb))
+        ws = _ws(nb)
+        ra = [oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes() for j in ja]
+        rb = [oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes() for j in jb_]
+        for _ in range(2):
+            for plan, refs in ((pa, ra), (pb, rb)):
+                out = (B.vl_proof * len(refs))()
+                B.vl_plan_run(plan, ws.data_ptr(), nb, out, B.VL_HOST)
+                assert [B.proof_bytes(p) for p in out] == refs
+    finally:
+        B.vl_plan_destroy(pa)
+        B.vl_plan_destroy(pb)
