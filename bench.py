@@ -54,7 +54,7 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="7b-step", choices=sorted(WORKLOADS))
@@ -198,6 +198,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(local)
+    time.sleep(0.6)  # let the sampler take its first reading before the timed region
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
