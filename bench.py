@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-projections", type=int, default=2)
+    ap.add_argument("--layers", type=int, default=0,
+                    help="prove only the first L layers of the step (profiling captures); 0 = all")
     return ap.parse_args()
 
 
@@ -69,8 +71,8 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def step_jobs(kind, seed):
-    projs = W.make_step(STEP_KIND[kind], seed)
+def step_jobs(kind, seed, layers=0):
+    projs = W.make_step(STEP_KIND[kind], seed, layers=range(layers) if layers > 0 else None)
     jobs = [j for t in projs for j in W.projection_products(t, seed)]
     return projs, jobs
 
@@ -169,7 +171,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.lib()
     seed = W.GLOBAL_SEED + 1000003 * rank
-    projs, jobs = step_jobs(args.workload, seed)
+    projs, jobs = step_jobs(args.workload, seed, args.layers)
     macs_step = sum(W.macs(j) for j in jobs)
     entries = sum(W.fold_entries(j) for j in jobs)
 
@@ -297,7 +299,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int16 operands, Fr (255-bit) arithmetic", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "proofs_per_step": len(jobs),
+        "config": {"workload": WORKLOADS[args.workload] + (f", first {args.layers} layers" if args.layers else ""),
+                   "proofs_per_step": len(jobs),
                    "macs_per_step": macs_step, "fold_entries_per_step": entries,
                    "input_bytes_per_step": in_bytes, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas{world}" if world > 1 else "single GPU",
