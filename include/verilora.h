@@ -202,6 +202,35 @@ int32_t vl_verify_matmul(const vl_mat* P, const vl_mat* Q, const vl_mat* C, cons
                          const vl_proof* proof);
 
 /*
+ * Prove one product without allocating device memory and without a
+ * caller-provided workspace.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc -- for example a plug-in
+ * running inside a host application that owns all device memory through its
+ * own pool and forbids allocations outside it, or a latency-critical loop
+ * that cannot take the implicit device synchronisation of cudaMalloc/cudaFree.
+ *
+ * Scratch: one file-scope device array of VL_NOALLOC_SCRATCH_BYTES inside the
+ * library.  Every GPU on which the library is used holds it until the process
+ * exits.  A job whose scratch does not fit is refused with VL_ENOMEM and a
+ * message in vl_last_error() (a single 7B- or 13B-shaped projection product
+ * fits; the scratch grows with k and the row/column counts).
+ * Set-up: the first call on each device, with that device current, looks up
+ * the array's device address; make that first call before any stream capture
+ * on the device.
+ * Sharing: all calls use the same array, which keeps the previous call's
+ * contents (the call clears what must start at zero).  Two calls running on
+ * the GPU at the same time would race on it; within one process the entry
+ * point prevents that by holding a lock for the whole call, which ends only
+ * after its stream has finished.
+ * P, Q: DEVICE matrices (VL_I16 or VL_FR_MONT); fs: transcript inputs; out:
+ * host proof.  The result is byte-identical to vl_prove_matmul's.  Calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ */
+#define VL_NOALLOC_SCRATCH_BYTES (8u << 20)
+int32_t vl_prove_matmul_noalloc(const vl_mat* P, const vl_mat* Q, const vl_fs_init* fs, vl_proof* out,
+                                void* stream);
+
+/*
  * Encode int16 fixed-point values into field elements in Montgomery form
  * (Sec. II-C embeds integer tensors into F; x < 0 maps to r - |x|):
  * dst[i * cols + j] = (src[i, j] mod r) . 2^256 mod r, 32 bytes each, dense

@@ -27,7 +27,8 @@ VL_MAX_REDUCE = 1 << 16
 # Every symbol include/verilora.h declares.
 EXPORTS = ("vl_version", "vl_strerror", "vl_last_error", "vl_workspace_bytes", "vl_prove_matmul", "vl_prove_batch",
            "vl_plan_create", "vl_plan_workspace_bytes", "vl_plan_run", "vl_plan_launches", "vl_plan_phase_ms",
-           "vl_plan_destroy", "vl_verify_matmul", "vl_encode")
+           "vl_plan_destroy", "vl_verify_matmul", "vl_encode", "vl_prove_matmul_noalloc")
+VL_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
 class vl_fr(ctypes.Structure):
@@ -111,6 +112,8 @@ def lib():
     L.vl_plan_destroy.restype = None
     L.vl_verify_matmul.argtypes = [P(vl_mat), P(vl_mat), P(vl_mat), P(vl_fs_init), P(vl_proof)]
     L.vl_verify_matmul.restype = ctypes.c_int32
+    L.vl_prove_matmul_noalloc.argtypes = [P(vl_mat), P(vl_mat), P(vl_fs_init), P(vl_proof), ctypes.c_void_p]
+    L.vl_prove_matmul_noalloc.restype = ctypes.c_int32
     L.vl_encode.argtypes = [P(vl_mat), ctypes.c_void_p, ctypes.c_void_p]
     L.vl_encode.restype = ctypes.c_int32
     _lib = L
@@ -236,6 +239,15 @@ def vl_prove_matmul(P, Q, fs, workspace, workspace_bytes, stream=None):
     out = vl_proof()
     _check(lib().vl_prove_matmul(ctypes.byref(P), ctypes.byref(Q), ctypes.byref(fs), workspace,
                                  workspace_bytes, ctypes.byref(out), _stream_ptr(stream)), "vl_prove_matmul")
+    return out
+
+
+def vl_prove_matmul_noalloc(P, Q, fs, stream=None):
+    """Prove one product of device matrices with no workspace and no device
+    allocation (scratch is a fixed array inside the library); host vl_proof."""
+    out = vl_proof()
+    _check(lib().vl_prove_matmul_noalloc(ctypes.byref(P), ctypes.byref(Q), ctypes.byref(fs), ctypes.byref(out),
+                                         _stream_ptr(stream)), "vl_prove_matmul_noalloc")
     return out
 
 

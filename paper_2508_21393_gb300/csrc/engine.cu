@@ -568,3 +568,78 @@ int32_t vl_encode(const vl_mat* src, void* dst, void* stream) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------- no-allocation variant --
+//
+// vl_prove_matmul_noalloc: the same proving pass as vl_prove_matmul, with the
+// workspace replaced by a file-scope device array, for callers that cannot
+// allocate device memory.  Host code must not use the array's name as a
+// device address: the address is looked up once per device below.
+
+namespace {
+
+__device__ __align__(256) uint8_t g_noalloc_scratch[VL_NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;  // held for a whole call: calls never overlap on the GPU
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device (set-up on first use).
+int noalloc_scratch_ptr(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return VL_EINVAL;
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(no-allocation scratch)");
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return VL_OK;
+}
+
+}  // namespace
+
+extern "C" int32_t vl_prove_matmul_noalloc(const vl_mat* P, const vl_mat* Q, const vl_fs_init* fs, vl_proof* out,
+                                           void* stream) {
+  if (!P || !Q || !fs || !out) return VL_EINVAL;
+  if (P->space != VL_DEVICE || Q->space != VL_DEVICE) return VL_EINVAL;
+  vl_job j;
+  j.P = *P;
+  j.Q = *Q;
+  j.fs = *fs;
+  vl_plan* p = nullptr;
+  int e = make_plan(&j, 1, nullptr, &p);
+  if (e != VL_OK) return e;
+  if (p->total > VL_NOALLOC_SCRATCH_BYTES) {
+    snprintf(g_last_error, sizeof(g_last_error),
+             "vl_prove_matmul_noalloc: job needs %zu bytes of scratch, the fixed array holds %u", p->total,
+             (unsigned)VL_NOALLOC_SCRATCH_BYTES);
+    vl_plan_destroy(p);
+    return VL_ENOMEM;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  void* ptr = nullptr;
+  e = noalloc_scratch_ptr(&ptr);
+  uint8_t* ws = static_cast<uint8_t*>(ptr);
+  if (e == VL_OK) e = bind_workspace(p, ws, st);  // descriptor tables into the array (synchronous)
+  if (e == VL_OK) {
+    const DevProof* dp = reinterpret_cast<const DevProof*>(ws + p->off_proofs);
+    const FoldTask* dt = reinterpret_cast<const FoldTask*>(ws + p->off_tasks);
+    const FoldTile* dl = reinterpret_cast<const FoldTile*>(ws + p->off_tiles);
+    vl_proof* dout = reinterpret_cast<vl_proof*>(ws + p->off_out);
+    // The accumulators keep the previous call's sums: clear them first.
+    cudaError_t ce = cudaMemsetAsync(ws + p->off_acc, 0, p->acc_bytes, st);
+    if (ce == cudaSuccess) ce = launch_prologue(dp, 1, st);
+    if (ce == cudaSuccess) ce = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, st);
+    if (ce == cudaSuccess) ce = launch_rounds(dp, 1, dout, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, dout, sizeof(vl_proof), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    e = cuda_status(ce, "vl_prove_matmul_noalloc");
+  }
+  vl_plan_destroy(p);
+  return e;
+}
