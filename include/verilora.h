@@ -117,7 +117,10 @@ typedef struct vl_batch_opts {
   int32_t persistent;    /* 1: one persistent launch; 2: phase launches       */
   int32_t use_graph;     /* 1: capture vl_plan_run in a CUDA graph; 2: never   */
   int32_t timing_runs;   /* runs kept by vl_plan_phase_ms (0: 64)             */
-  int32_t reserved[3];
+  int32_t wait_limit_us; /* bound on any single device-side wait, in us (0: 2 s);
+                            a wait that runs out sets the proof's status to
+                            VL_ETIMEOUT and its CTA returns                  */
+  int32_t reserved[2];
 } vl_batch_opts;
 
 typedef struct vl_plan vl_plan; /* opaque batched-step plan */
@@ -167,7 +170,7 @@ int32_t vl_prove_batch(const vl_job* jobs, int32_t njobs, void* workspace, size_
 int32_t vl_plan_create(const vl_job* jobs, int32_t njobs, const vl_batch_opts* opts, vl_plan** plan);
 size_t vl_plan_workspace_bytes(const vl_plan* plan);
 /* Enqueue one proving pass; out: njobs proofs in `out_space` memory (VL_HOST
- * synchronises).  Host-space operands are copied in on every run.  The first
+ * synchronises, and returns the first non-OK proof status, e.g. VL_ETIMEOUT).  Host-space operands are copied in on every run.  The first
  * run on a workspace uploads the plan's descriptor tables into it (a
  * synchronous copy); later runs reuse them.  Several plans may take turns on
  * one workspace (same base pointer): a plan re-uploads its tables when

@@ -49,6 +49,8 @@ struct FoldTask {
   int32_t rows, cols;
   int32_t mode, dtype;
   int32_t proof, side;  // side 0: weights E_u, output accA; side 1: E_v, accB
+  int32_t bulk;         // 1: int16 tiles staged by bulk async copies (alignment checked on the host)
+  int32_t pad;
 };
 
 struct FoldTile {
@@ -64,13 +66,32 @@ static constexpr int COLSUM_VEC = 4;                              // int16 colum
 static constexpr int COLSUM_TILE_COLS = FOLD_THREADS * COLSUM_VEC;  // 1024
 static constexpr int ROWDOT_ROWS_PER_WARP = 4;
 static constexpr int ROWDOT_TILE_ROWS = (FOLD_THREADS / 32) * ROWDOT_ROWS_PER_WARP;  // 32
+static constexpr int ROWDOT_TILE_COLS = 1024;
 static constexpr int FR_COLSUM_TILE_COLS = FOLD_THREADS;          // Montgomery operands: 1 col/thread
+// Bulk-copy pipeline: NSTAGE shared-memory stages of STAGE_BYTES each; a
+// row-dot stage holds ROWDOT_STAGE_COLS columns of all 32 tile rows.
+static constexpr int NSTAGE = 4;
+static constexpr int STAGE_BYTES = 16384;
+static constexpr int ROWDOT_STAGE_COLS = STAGE_BYTES / (ROWDOT_TILE_ROWS * 2);  // 256
+static constexpr int FOLD_SMEM_HEAD = 128;  // mbarriers
+// Default bound on any single wait for a bulk copy (ns of %globaltimer).
+static constexpr unsigned long long FOLD_WAIT_NS = 2000000000ull;
+
+// Dynamic shared memory a fold tile needs (bytes).
+inline int fold_tile_smem(int mode, int dtype, int tile_rows, int tile_cols) {
+  if (mode == MODE_COLSUM) {
+    const int e = tile_rows * 32;
+    return FOLD_SMEM_HEAD + e + (dtype == VL_I16 ? NSTAGE * STAGE_BYTES : 0);
+  }
+  const int pitch = (tile_cols + 3) & ~3;
+  return FOLD_SMEM_HEAD + pitch * 32 + (dtype == VL_I16 ? NSTAGE * STAGE_BYTES : 0);
+}
 
 cudaError_t launch_prologue(const DevProof* proofs, int nproofs, cudaStream_t st);
 // Raise the fold kernel's dynamic shared-memory limit (call before capture).
 cudaError_t fold_set_smem(int smem_bytes);
 cudaError_t launch_fold(const FoldTask* tasks, const FoldTile* tiles, int ntiles,
-                        const DevProof* proofs, int smem_bytes, cudaStream_t st);
+                        const DevProof* proofs, int smem_bytes, unsigned long long wait_ns, cudaStream_t st);
 cudaError_t launch_rounds(const DevProof* proofs, int nproofs, vl_proof* out, cudaStream_t st);
 cudaError_t launch_encode(const int16_t* src, int64_t rows, int64_t cols, int64_t ld, Fr* dst,
                           cudaStream_t st);

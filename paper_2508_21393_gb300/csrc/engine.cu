@@ -134,11 +134,11 @@ void add_fold_task(vl_plan* p, const vl_mat& M, int32_t mode, int proof, int sid
         ft.c0 = c0;
         ft.c1 = std::min<int>(t.cols, c0 + tc);
         p->tiles.push_back(ft);
-        p->fold_smem = std::max(p->fold_smem, (ft.r1 - ft.r0) * 32);
+        p->fold_smem = std::max(p->fold_smem, fold_tile_smem(mode, M.dtype, ft.r1 - ft.r0, ft.c1 - ft.c0));
       }
   } else {
-    int tcmax = p->opts.rowdot_cols > 0 ? p->opts.rowdot_cols : 2048;
-    tcmax = (tcmax + 3) & ~3;
+    int tcmax = p->opts.rowdot_cols > 0 ? p->opts.rowdot_cols : ROWDOT_TILE_COLS;
+    tcmax = (tcmax + 7) & ~7;
     for (int c0 = 0; c0 < t.cols; c0 += tcmax)
       for (int r0 = 0; r0 < t.rows; r0 += ROWDOT_TILE_ROWS) {
         FoldTile ft{};
@@ -148,8 +148,7 @@ void add_fold_task(vl_plan* p, const vl_mat& M, int32_t mode, int proof, int sid
         ft.c0 = c0;
         ft.c1 = std::min<int>(t.cols, c0 + tcmax);
         p->tiles.push_back(ft);
-        const int pitch = ((ft.c1 - ft.c0) + 3) & ~3;
-        p->fold_smem = std::max(p->fold_smem, pitch * 32);
+        p->fold_smem = std::max(p->fold_smem, fold_tile_smem(mode, M.dtype, ft.r1 - ft.r0, ft.c1 - ft.c0));
       }
   }
 }
@@ -290,6 +289,10 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
   for (FoldTask& t : p->tasks) {
     const vl_job& j = p->jobs[t.proof];
     t.mat = operand_ptr(p, t.side ? j.Q : j.P, ws);
+    // Bulk copies need 16-byte aligned row starts and row lengths: aligned
+    // base, ld and cols multiples of 8 int16 (tile edges are multiples of 8).
+    t.bulk = t.dtype == VL_I16 && (reinterpret_cast<uintptr_t>(t.mat) & 15) == 0 && (t.ld & 7) == 0 &&
+             (t.cols & 7) == 0;
   }
   cudaError_t e = cudaMemcpyAsync(ws + p->off_proofs, p->proofs.data(), sizeof(DevProof) * np,
                                   cudaMemcpyHostToDevice, st);
@@ -303,6 +306,10 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess && p->fold_smem > 0) e = fold_set_smem(p->fold_smem);
   return cuda_status(e, "bind_workspace");
+}
+
+unsigned long long wait_ns(const vl_plan* p) {
+  return p->opts.wait_limit_us > 0 ? 1000ull * (unsigned long long)p->opts.wait_limit_us : FOLD_WAIT_NS;
 }
 
 cudaError_t ensure_events(vl_plan* p) {
@@ -338,7 +345,7 @@ cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t s
   if (e == cudaSuccess) e = cudaMemsetAsync(ws + p->off_acc, 0, p->acc_bytes, st);
   if (e == cudaSuccess) e = launch_prologue(dp, np, st);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[1], st, flags);
-  if (e == cudaSuccess) e = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, st);
+  if (e == cudaSuccess) e = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, wait_ns(p), st);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2], st, flags);
   if (e == cudaSuccess) e = launch_rounds(dp, np, dout, st);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[3], st, flags);
@@ -444,6 +451,8 @@ int run_plan(vl_plan* p, void* workspace, size_t ws_bytes, vl_proof* out, int32_
     if ((ce = cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
       return cuda_status(ce, "proof copy-out");
     if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_status(ce, "cudaStreamSynchronize");
+    for (size_t i = 0; i < p->jobs.size(); i++)
+      if (out[i].status != VL_OK) return out[i].status;
   }
   return VL_OK;
 }
@@ -634,11 +643,12 @@ extern "C" int32_t vl_prove_matmul_noalloc(const vl_mat* P, const vl_mat* Q, con
     // The accumulators keep the previous call's sums: clear them first.
     cudaError_t ce = cudaMemsetAsync(ws + p->off_acc, 0, p->acc_bytes, st);
     if (ce == cudaSuccess) ce = launch_prologue(dp, 1, st);
-    if (ce == cudaSuccess) ce = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, st);
+    if (ce == cudaSuccess) ce = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, FOLD_WAIT_NS, st);
     if (ce == cudaSuccess) ce = launch_rounds(dp, 1, dout, st);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, dout, sizeof(vl_proof), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     e = cuda_status(ce, "vl_prove_matmul_noalloc");
+    if (e == VL_OK && out->status != VL_OK) e = out->status;
   }
   vl_plan_destroy(p);
   return e;

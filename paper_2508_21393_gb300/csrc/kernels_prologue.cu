@@ -17,7 +17,7 @@
 
 namespace vl {
 
-static constexpr int PRO_THREADS = 256;
+static constexpr int PRO_THREADS = 128;
 static constexpr int MAX_VARS = 16;      // log2 of VL_MAX_REDUCE
 static constexpr int MAX_HALF = 1 << 8;  // 2^(MAX_VARS / 2)
 
@@ -58,7 +58,7 @@ __device__ static Fr build_eq(const Fr* x, int d, int size, Fr* out, Fr* lo, Fr*
   return mont_mul(sum[0], fr_small(1u << 15));
 }
 
-__global__ void __launch_bounds__(PRO_THREADS) prologue_kernel(const DevProof* __restrict__ proofs) {
+__global__ void __launch_bounds__(PRO_THREADS, 8) prologue_kernel(const DevProof* __restrict__ proofs) {
   const DevProof& P = proofs[blockIdx.x];
   __shared__ uint8_t S0[32], S1[32], S2[32];
   __shared__ Fr u[MAX_VARS], v[MAX_VARS];

@@ -15,7 +15,7 @@
 
 namespace vl {
 
-static constexpr int RND_THREADS = 256;
+static constexpr int RND_THREADS = 128;
 
 __device__ __forceinline__ Fr load_acc_fr(const unsigned long long* acc, int w, const Fr& corr) {
   uint64_t a[8];
@@ -29,7 +29,7 @@ __device__ __forceinline__ void store_fr(vl_fr* dst, const Fr& x) {
   for (int l = 0; l < 8; l++) dst->limb[l] = x.v[l];
 }
 
-__global__ void __launch_bounds__(RND_THREADS) rounds_kernel(const DevProof* __restrict__ proofs,
+__global__ void __launch_bounds__(RND_THREADS, 7) rounds_kernel(const DevProof* __restrict__ proofs,
                                                              vl_proof* __restrict__ out) {
   const DevProof& P = proofs[blockIdx.x];
   vl_proof* pf = out + blockIdx.x;

@@ -75,6 +75,44 @@ def test_ragged_and_transposed(m, k, n, tp, tq):
     assert B.proof_bytes(pf) == ref.to_bytes()
 
 
+@pytest.mark.parametrize("m,k,n,tp,tq", [
+    (600, 2056, 1032, 0, 0),   # bulk path: 3 row tiles, column tiles 1024/1024/8, 32 stages per tile
+    (600, 2056, 1032, 1, 1),   # bulk path, transposed: row dots over 600 columns, column sums of Q^T
+    (4096, 16, 40, 0, 0),      # narrow contiguous rows: one copy per stage
+    (40, 4096, 16, 0, 0),      # narrow row dots (16 columns, a 32-byte copy per row)
+    (24, 8, 8, 1, 1),          # smallest bulk-eligible shapes
+])
+def test_bulk_pipeline_shapes(m, k, n, tp, tq):
+    rng = np.random.default_rng(m + 3 * k + 7 * n + tp)
+    A, Bm, P, Q = _shapes(m, k, n, tp, tq, rng)
+    pf = gpu_prove(P, Q, tp, tq, 99)
+    assert B.proof_bytes(pf) == oracle.prove_matmul(P, Q, tp, tq, seed=99).to_bytes()
+
+
+def test_bulk_eligible_cols_with_unaligned_ld_falls_back():
+    rng = np.random.default_rng(8)
+    big = _rand(rng, (64, 1030))
+    Pd = torch.from_numpy(big).cuda()[:, :1024]      # cols % 8 == 0 but ld = 1030
+    Q = _rand(rng, (1024, 24))
+    jb = B.job(Pd, torch.from_numpy(Q).cuda(), 0, 0, 5)
+    n = B.vl_workspace_bytes([jb])
+    ws = _ws(n)
+    pf = B.vl_prove_matmul(jb.P, jb.Q, jb.fs, ws.data_ptr(), n)
+    assert B.proof_bytes(pf) == oracle.prove_matmul(big[:, :1024], Q, 0, 0, seed=5).to_bytes()
+
+
+def test_wait_limit_option_keeps_results():
+    jobs = _lora_jobs(n=32, d=256, k=256, r=8, layer=5, proj="o")
+    dj, keep = _dev_jobs(jobs)
+    opts = B.vl_batch_opts()
+    opts.wait_limit_us = 500000
+    nb = B.vl_workspace_bytes(dj, opts)
+    ws = _ws(nb)
+    proofs = B.vl_prove_batch(dj, ws.data_ptr(), nb, opts=opts)
+    for j, pf in zip(jobs, proofs):
+        assert B.proof_bytes(pf) == oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes()
+
+
 def test_extreme_values():
     """All entries at the int16 extremes (the +2^15 offset and its correction)."""
     m, k, n = 33, 70, 40
