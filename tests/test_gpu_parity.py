@@ -94,7 +94,8 @@ def test_bulk_eligible_cols_with_unaligned_ld_falls_back():
     big = _rand(rng, (64, 1030))
     Pd = torch.from_numpy(big).cuda()[:, :1024]      # cols % 8 == 0 but ld = 1030
     Q = _rand(rng, (1024, 24))
-    jb = B.job(Pd, torch.from_numpy(Q).cuda(), 0, 0, 5)
+    Qd = torch.from_numpy(Q).cuda()  # kept alive: the job holds only its address
+    jb = B.job(Pd, Qd, 0, 0, 5)
     n = B.vl_workspace_bytes([jb])
     ws = _ws(n)
     pf = B.vl_prove_matmul(jb.P, jb.Q, jb.fs, ws.data_ptr(), n)
