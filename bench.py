@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-projections", type=int, default=2)
+    ap.add_argument("--rounds-variant", type=int, default=0, choices=[0, 4, 7],
+                    help="rounds kernel register budget (CTAs per SM); 0 = library default")
     ap.add_argument("--layers", type=int, default=0,
                     help="prove only the first L layers of the step (profiling captures); 0 = all")
     return ap.parse_args()
@@ -185,6 +187,7 @@ def main():
     stream = torch.cuda.current_stream()
     opts = B.vl_batch_opts()
     opts.timing_runs = max(args.steps, 1)
+    opts.rounds_variant = args.rounds_variant
     plan = B.vl_plan_create(djobs, opts)
     nws = B.vl_plan_workspace_bytes(plan)
     ws = torch.empty(nws, dtype=torch.uint8, device="cuda")

@@ -120,7 +120,9 @@ typedef struct vl_batch_opts {
   int32_t wait_limit_us; /* bound on any single device-side wait, in us (0: 2 s);
                             a wait that runs out sets the proof's status to
                             VL_ETIMEOUT and its CTA returns                  */
-  int32_t reserved[2];
+  int32_t rounds_variant; /* rounds kernel register budget: 7 or 4 CTAs per SM
+                            (0: 7)                                           */
+  int32_t reserved[1];
 } vl_batch_opts;
 
 typedef struct vl_plan vl_plan; /* opaque batched-step plan */

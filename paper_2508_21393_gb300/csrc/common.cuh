@@ -92,7 +92,7 @@ cudaError_t launch_prologue(const DevProof* proofs, int nproofs, cudaStream_t st
 cudaError_t fold_set_smem(int smem_bytes);
 cudaError_t launch_fold(const FoldTask* tasks, const FoldTile* tiles, int ntiles,
                         const DevProof* proofs, int smem_bytes, unsigned long long wait_ns, cudaStream_t st);
-cudaError_t launch_rounds(const DevProof* proofs, int nproofs, vl_proof* out, cudaStream_t st);
+cudaError_t launch_rounds(const DevProof* proofs, int nproofs, vl_proof* out, int variant, cudaStream_t st);
 cudaError_t launch_encode(const int16_t* src, int64_t rows, int64_t cols, int64_t ld, Fr* dst,
                           cudaStream_t st);
 

@@ -347,7 +347,7 @@ cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t s
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[1], st, flags);
   if (e == cudaSuccess) e = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, wait_ns(p), st);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2], st, flags);
-  if (e == cudaSuccess) e = launch_rounds(dp, np, dout, st);
+  if (e == cudaSuccess) e = launch_rounds(dp, np, dout, p->opts.rounds_variant, st);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[3], st, flags);
   return e;
 }
@@ -644,7 +644,7 @@ extern "C" int32_t vl_prove_matmul_noalloc(const vl_mat* P, const vl_mat* Q, con
     cudaError_t ce = cudaMemsetAsync(ws + p->off_acc, 0, p->acc_bytes, st);
     if (ce == cudaSuccess) ce = launch_prologue(dp, 1, st);
     if (ce == cudaSuccess) ce = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, FOLD_WAIT_NS, st);
-    if (ce == cudaSuccess) ce = launch_rounds(dp, 1, dout, st);
+    if (ce == cudaSuccess) ce = launch_rounds(dp, 1, dout, 0, st);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, dout, sizeof(vl_proof), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     e = cuda_status(ce, "vl_prove_matmul_noalloc");

@@ -14,6 +14,7 @@
 #include "common.cuh"
 #include "reduce.cuh"
 #include "transcript.cuh"
+#include "transcript_dev.cuh"
 
 namespace vl {
 
@@ -58,29 +59,51 @@ __device__ static Fr build_eq(const Fr* x, int d, int size, Fr* out, Fr* lo, Fr*
   return mont_mul(sum[0], fr_small(1u << 15));
 }
 
+// Squeeze `count` challenges with `label` from the state Sw (big-endian
+// words): thread 2t + h hashes half h of challenge t, thread 2 count the
+// closing update.  Writes the challenges (Montgomery) to x and the new state
+// to Sn.  Block-wide (two barriers).
+__device__ static void squeeze_dev(const uint32_t* Sw, uint32_t label, int count, Fr* x, uint32_t* Sn,
+                                   uint32_t (*dig)[8]) {
+  const int tid = threadIdx.x;
+  if (tid <= 2 * count) {
+    uint32_t st[8], d[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) st[i] = Sw[i];
+    if (tid < 2 * count) {
+      dev_squeeze_block(st, label, (uint32_t)(tid >> 1), tid & 1, d);
+#pragma unroll
+      for (int i = 0; i < 8; i++) dig[tid][i] = d[i];
+    } else {
+      dev_squeeze_block(st, label, (uint32_t)count, 2, d);
+#pragma unroll
+      for (int i = 0; i < 8; i++) Sn[i] = d[i];
+    }
+  }
+  __syncthreads();
+  if (tid < count) x[tid] = to_mont(reduce_512(digest_le(dig[2 * tid]), digest_le(dig[2 * tid + 1])));
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(PRO_THREADS, 8) prologue_kernel(const DevProof* __restrict__ proofs) {
   const DevProof& P = proofs[blockIdx.x];
-  __shared__ uint8_t S0[32], S1[32], S2[32];
+  __shared__ uint32_t S0[8], S1[8], S2[8];
+  __shared__ uint32_t dig[2 * MAX_VARS][8];
   __shared__ Fr u[MAX_VARS], v[MAX_VARS];
   __shared__ Fr lo[MAX_HALF], hi[MAX_HALF];
   __shared__ Fr red[PRO_THREADS / 32];
   const int tid = threadIdx.x;
 
-  if (tid == 0) ts_start(S0, P.seed, P.m, P.k, P.n, P.tp, P.tq, P.binds);
-  __syncthreads();
-  if (tid < P.d0) u[tid] = to_mont(ts_challenge(S0, LBL_U, tid));
-  if (tid == 64) {
-    for (int i = 0; i < 32; i++) S1[i] = S0[i];
-    ts_squeeze_done(S1, LBL_U, P.d0);
+  if (tid == 0) {
+    uint8_t b[32];
+    ts_start(b, P.seed, P.m, P.k, P.n, P.tp, P.tq, P.binds);
+    for (int i = 0; i < 8; i++)
+      S0[i] = ((uint32_t)b[4 * i] << 24) | ((uint32_t)b[4 * i + 1] << 16) | ((uint32_t)b[4 * i + 2] << 8) | b[4 * i + 3];
   }
   __syncthreads();
-  if (tid < P.d2) v[tid] = to_mont(ts_challenge(S1, LBL_V, tid));
-  if (tid == 64) {
-    for (int i = 0; i < 32; i++) S2[i] = S1[i];
-    ts_squeeze_done(S2, LBL_V, P.d2);
-  }
-  __syncthreads();
-  if (tid < 32) P.scr->state[tid] = S2[tid];
+  squeeze_dev(S0, LBL_U, P.d0, u, S1, dig);
+  squeeze_dev(S1, LBL_V, P.d2, v, S2, dig);
+  if (tid < 32) P.scr->state[tid] = (uint8_t)(S2[tid >> 2] >> (24 - 8 * (tid & 3)));
 
   Fr ca = build_eq(u, P.d0, P.m, P.eqA, lo, hi, red);
   __syncthreads();
