@@ -106,11 +106,6 @@ __device__ __forceinline__ uint2 lds_u2(uint32_t addr) {
   return r;
 }
 
-// acc += a * b as one 32x32->64 multiply-add.
-__device__ __forceinline__ void madw(u64& acc, uint32_t a, uint32_t b) {
-  asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
-}
-
 // Offset int16 -> [0, 2^16).
 __device__ __forceinline__ uint32_t off16(int16_t x) { return (uint32_t)(uint16_t)x ^ 0x8000u; }
 
@@ -191,7 +186,7 @@ __device__ void colsum_i16(const FoldTask& T, const FoldTile& t, const Fr* __res
 #pragma unroll
     for (int q = 0; q < 4; q++)
 #pragma unroll
-      for (int l = 0; l < 8; l++) madw(a[q][l], e[l], p[q]);
+      for (int l = 0; l < 8; l++) a[q][l] += (u64)e[l] * p[q];
   }
 #pragma unroll
   for (int q = 0; q < 4; q++) {
@@ -248,7 +243,7 @@ __device__ void rowdot_i16(const FoldTask& T, const FoldTile& t, const Fr* __res
 #pragma unroll
         for (int q = 0; q < 4; q++)
 #pragma unroll
-          for (int l = 0; l < 8; l++) madw(a[rr * 8 + l], e[q][l], p[q]);
+          for (int l = 0; l < 8; l++) a[rr * 8 + l] += (u64)e[q][l] * p[q];
       }
     }
   }
@@ -355,7 +350,7 @@ __device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, const Fr* 
 #pragma unroll
         for (int q = 0; q < 4; q++)
 #pragma unroll
-          for (int l = 0; l < 8; l++) madw(a[q][l], e[l], pv[q]);
+          for (int l = 0; l < 8; l++) a[q][l] += (u64)e[l] * pv[q];
       }
     }
     if (!__syncthreads_and(ok)) {
@@ -453,7 +448,7 @@ __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, const Fr* 
 #pragma unroll
               for (int q = 0; q < 4; q++)
 #pragma unroll
-                for (int l = 0; l < 8; l++) madw(a[rr * 8 + l], e[q][l], pv[q]);
+                for (int l = 0; l < 8; l++) a[rr * 8 + l] += (u64)e[q][l] * pv[q];
             }
           }
         }
