@@ -14,6 +14,7 @@
 #include "common.cuh"
 #include "reduce.cuh"
 #include "transcript.cuh"
+#include "fr_dev.cuh"
 #include "transcript_dev.cuh"
 
 namespace vl {
@@ -33,7 +34,7 @@ __device__ static Fr build_eq(const Fr* x, int d, int size, Fr* out, Fr* lo, Fr*
     for (int t = 0; t < s; t++) {
       const Fr& xt = x[dh + t];
       int b = (j >> (s - 1 - t)) & 1;
-      acc = mont_mul(acc, b ? xt : fr_sub(fr_r1(), xt));
+      acc = mont_mul_ni(acc, b ? xt : fr_sub(fr_r1(), xt));
     }
     lo[j] = acc;
   }
@@ -42,21 +43,21 @@ __device__ static Fr build_eq(const Fr* x, int d, int size, Fr* out, Fr* lo, Fr*
     for (int t = 0; t < dh; t++) {
       const Fr& xt = x[t];
       int b = (j >> (dh - 1 - t)) & 1;
-      acc = mont_mul(acc, b ? xt : fr_sub(fr_r1(), xt));
+      acc = mont_mul_ni(acc, b ? xt : fr_sub(fr_r1(), xt));
     }
     hi[j] = acc;
   }
   __syncthreads();
   Fr sum[1] = {fr_zero()};
   for (int i = tid; i < size; i += blockDim.x) {
-    Fr e = mont_mul(hi[i >> s], lo[i & (nlo - 1)]);
+    Fr e = mont_mul_ni(hi[i >> s], lo[i & (nlo - 1)]);
     out[i] = e;
     sum[0] = fr_add(sum[0], e);
   }
   block_sum_fr<1>(sum, red);
   // sum = sum_i E_i . R^2; one Montgomery product with the plain integer 2^15
   // gives 2^15 . sum_i E_i . R.
-  return mont_mul(sum[0], fr_small(1u << 15));
+  return mont_mul_ni(sum[0], fr_small(1u << 15));
 }
 
 // Squeeze `count` challenges with `label` from the state Sw (big-endian
@@ -81,7 +82,7 @@ __device__ static void squeeze_dev(const uint32_t* Sw, uint32_t label, int count
     }
   }
   __syncthreads();
-  if (tid < count) x[tid] = to_mont(reduce_512(digest_le(dig[2 * tid]), digest_le(dig[2 * tid + 1])));
+  if (tid < count) x[tid] = to_mont_ni(reduce_512_ni(digest_le(dig[2 * tid]), digest_le(dig[2 * tid + 1])));
   __syncthreads();
 }
 

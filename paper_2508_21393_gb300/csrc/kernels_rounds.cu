@@ -22,6 +22,7 @@
 //    independent hashes done by three lanes at once.
 #include "common.cuh"
 #include "reduce.cuh"
+#include "fr_dev.cuh"
 #include "transcript_dev.cuh"
 
 namespace vl {
@@ -29,10 +30,10 @@ namespace vl {
 static constexpr int RND_THREADS = 128;
 
 __device__ __forceinline__ Fr load_acc_fr(const unsigned long long* acc, int w, const Fr& corr) {
-  uint64_t a[8];
+  U64x8 a;
 #pragma unroll
-  for (int l = 0; l < 8; l++) a[l] = acc[(size_t)w * 8 + l];
-  return fr_sub(redc_columns(a), corr);
+  for (int l = 0; l < 8; l++) a.v[l] = acc[(size_t)w * 8 + l];
+  return fr_sub(redc_columns_ni(a), corr);
 }
 
 __device__ __forceinline__ void store_fr(vl_fr* dst, const Fr& x) {
@@ -41,13 +42,13 @@ __device__ __forceinline__ void store_fr(vl_fr* dst, const Fr& x) {
 }
 
 __device__ __forceinline__ Fr fold1(const Fr& x0, const Fr& x1, const Fr& r) {
-  return fr_add(x0, mont_mul(r, fr_sub(x1, x0)));
+  return fr_add(x0, mont_mul_ni(r, fr_sub(x1, x0)));
 }
 
 __device__ __forceinline__ void accum_g(Fr (&g)[3], const Fr& a0, const Fr& a1, const Fr& b0, const Fr& b1) {
-  g[0] = fr_add(g[0], mont_mul(a0, b0));
-  g[1] = fr_add(g[1], mont_mul(a1, b1));
-  g[2] = fr_add(g[2], mont_mul(fr_sub(fr_dbl(a1), a0), fr_sub(fr_dbl(b1), b0)));
+  g[0] = fr_add(g[0], mont_mul_ni(a0, b0));
+  g[1] = fr_add(g[1], mont_mul_ni(a1, b1));
+  g[2] = fr_add(g[2], mont_mul_ni(fr_sub(fr_dbl(a1), a0), fr_sub(fr_dbl(b1), b0)));
 }
 
 __device__ __forceinline__ Fr select3(const Fr (&g)[3], int q) {
@@ -60,7 +61,7 @@ __device__ __forceinline__ Fr select3(const Fr (&g)[3], int q) {
 // Warp 0, after block_sum_fr: lanes 0..2 convert g[lane] to canonical form in gsh.
 __device__ __forceinline__ void publish_g(const Fr (&g)[3], Fr* gsh) {
   const int lane = threadIdx.x & 31;
-  if (lane < 3) gsh[lane] = from_mont(select3(g, lane));
+  if (lane < 3) gsh[lane] = from_mont_ni(select3(g, lane));
   __syncwarp();
 }
 
@@ -102,7 +103,7 @@ __device__ __forceinline__ Fr round_transcript(uint32_t* S, const Fr* gsh, bool 
     for (int i = 0; i < 8; i++) S[i] = d[i];
   }
   Fr r = fr_zero();
-  if (lane == 0) r = to_mont(reduce_512(digest_le(d), digest_le(d1)));
+  if (lane == 0) r = to_mont_ni(reduce_512_ni(digest_le(d), digest_le(d1)));
   __syncwarp();
   return r;
 }
@@ -136,8 +137,8 @@ __global__ void __launch_bounds__(RND_THREADS, MINB) rounds_kernel(const DevProo
   if (d1 == 0) {  // k = 1: no rounds, c = a_r . b_r
     if (tid == 0) {
       const Fr a = load_acc_fr(P.accA, 0, corrA), b = load_acc_fr(P.accB, 0, corrB);
-      const Fr fin[2] = {from_mont(a), from_mont(b)};
-      const Fr c[1] = {from_mont(mont_mul(a, b))};
+      const Fr fin[2] = {from_mont_ni(a), from_mont_ni(b)};
+      const Fr c[1] = {from_mont_ni(mont_mul_ni(a, b))};
       store_fr(&pf->c, c[0]);
       store_fr(&pf->a_r, fin[0]);
       store_fr(&pf->b_r, fin[1]);
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(RND_THREADS, MINB) rounds_kernel(const DevProo
       if (warp == 0) publish_g(gn, gsh);
     } else if (tid == 0) {
       // Last fold: a_r, b_r; absorb them and write the proof.
-      const Fr fin[2] = {from_mont(fold1(fA[0], fA[1], r)), from_mont(fold1(fB[0], fB[1], r))};
+      const Fr fin[2] = {from_mont_ni(fold1(fA[0], fA[1], r)), from_mont_ni(fold1(fB[0], fB[1], r))};
       store_fr(&pf->a_r, fin[0]);
       store_fr(&pf->b_r, fin[1]);
       uint32_t st[8];
