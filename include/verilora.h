@@ -122,7 +122,10 @@ typedef struct vl_batch_opts {
                             VL_ETIMEOUT and its CTA returns                  */
   int32_t rounds_variant; /* rounds kernel register budget: 7 or 4 CTAs per SM
                             (0: 7)                                           */
-  int32_t reserved[1];
+  int32_t test_never_ready; /* fault injection for tests: 1 + index of a proof
+                            whose prologue never signals ready, so that its
+                            fold tiles exhaust their bounded wait and report
+                            VL_ETIMEOUT (persistent mode); 0: off            */
 } vl_batch_opts;
 
 typedef struct vl_plan vl_plan; /* opaque batched-step plan */

@@ -19,7 +19,9 @@ Readings of the paper taken here (it is silent or garbled on these points):
   from the matrices in place of polynomial-commitment openings.
 
 Transcript order: squeeze u (d0), squeeze v (d2), absorb c, then per round
-absorb (g0, g1, g2) and squeeze r_i, then absorb (a_r, b_r).
+absorb (g0, g2) and squeeze r_i, then absorb (a_r, b_r).  A round absorbs
+g(0) and g(2) only: g(1) is fixed by the running claim (the verifier checks
+g(0) + g(1) = claim), so it would bind nothing new.
 
 Pins (tests/test_oracle_sumcheck.py): brute-force round polynomials on the
 hypercube, g_i(0) + g_i(1) = claim_{i-1}, degree <= 2, the final claim equal to
@@ -123,7 +125,7 @@ def prove_matmul(P, Q, trans_p=0, trans_q=0, seed=0, binds=(bytes(32),) * 3, ove
         g1 = sum(fa[j + h] * fb[j + h] for j in range(h)) % R_MOD
         g2 = sum((2 * fa[j + h] - fa[j]) * (2 * fb[j + h] - fb[j]) for j in range(h)) % R_MOD
         g_all.append((g0, g1, g2))
-        T.absorb_fr(b"g", [g0, g1, g2])
+        T.absorb_fr(b"g", [g0, g2])
         r = T.squeeze(b"r", 1)[0]
         if "r" in ov:
             r = ov["r"][i] % R_MOD
@@ -171,7 +173,7 @@ def verify_matmul(P, Q, C, proof, trans_p=0, trans_q=0, seed=0, binds=(bytes(32)
     for i, (g0, g1, g2) in enumerate(proof.g):
         if (g0 + g1) % R_MOD != claim:
             return False, f"round {i + 1}: g(0) + g(1) != claim"
-        T.absorb_fr(b"g", [g0, g1, g2])
+        T.absorb_fr(b"g", [g0, g2])
         r = T.squeeze(b"r", 1)[0]
         rs.append(r)
         claim = round_poly_eval(g0, g1, g2, r)

@@ -19,7 +19,8 @@ fixes no hash, byte layout or sampling rule; this project's convention is:
 
 Labels: squeeze 'u' (d0 row challenges), 'v' (d2 column challenges),
 'r' (one per sumcheck round); absorb 'c' (the claim), 'g' (a round message
-g(0)||g(1)||g(2)), 'f' (the final evaluations a_r||b_r).
+g(0)||g(2); g(1) is implied by the running claim), 'f' (the final
+evaluations a_r||b_r).
 
 Parity status: SHA-256 is ``hashlib`` (pinned by the FIPS 180-4 vectors in the
 tests); the byte format above is our own convention: parity unpinned.

@@ -41,7 +41,25 @@ struct DevProof {
   Fr* fA;                  // 2^d1 working vector for the rounds (Montgomery)
   Fr* fB;
   ProofScratch* scr;
+  int32_t ntiles;          // fold tiles of this proof (both tasks)
+  int32_t pad2[3];
 };
+
+// Persistent step: work items in queue order.
+enum : int32_t { STEP_PROLOGUE = 0, STEP_FOLD = 1 };
+struct StepItem {
+  int32_t kind;
+  int32_t idx;  // proof (prologue) or fold tile
+};
+// Dynamic shared memory of the prologue and rounds block functions.
+static constexpr int PRO_SMEM = 18816;
+static constexpr int RND_SMEM = 1792;
+// Prologue items run this many proofs ahead of their fold tiles in the queue.
+static constexpr int STEP_LOOKAHEAD = 256;
+
+// Control block of a persistent step (zeroed every pass): the queue head
+// padded to its own 128 bytes, then ready[nproofs], done[nproofs].
+static constexpr int STEP_CTL_HEAD_INTS = 32;
 
 struct FoldTask {
   const void* mat;  // stored matrix (device)
@@ -92,6 +110,11 @@ cudaError_t launch_prologue(const DevProof* proofs, int nproofs, cudaStream_t st
 cudaError_t fold_set_smem(int smem_bytes);
 cudaError_t launch_fold(const FoldTask* tasks, const FoldTile* tiles, int ntiles,
                         const DevProof* proofs, int smem_bytes, unsigned long long wait_ns, cudaStream_t st);
+cudaError_t step_set_smem(int smem_bytes);
+cudaError_t step_grid(int smem_bytes, int* grid);
+cudaError_t launch_step(const StepItem* items, int nitems, const FoldTask* tasks, const FoldTile* tiles,
+                        const DevProof* proofs, int nproofs, vl_proof* out, int* ctl, int grid, int smem_bytes,
+                        unsigned long long wait_ns, int never_ready, cudaStream_t st);
 cudaError_t launch_rounds(const DevProof* proofs, int nproofs, vl_proof* out, int variant, cudaStream_t st);
 cudaError_t launch_encode(const int16_t* src, int64_t rows, int64_t cols, int64_t ld, Fr* dst,
                           cudaStream_t st);

@@ -81,7 +81,11 @@ struct vl_plan {
   std::vector<DevProof> proofs;
   std::vector<FoldTask> tasks;
   std::vector<FoldTile> tiles;
+  std::vector<StepItem> items;  // persistent step: queue order
   int fold_smem = 0;
+  int step_smem = 0;
+  int step_grid = 0;            // CTAs of the persistent launch (set at bind time)
+  size_t off_ctl = 0, off_items = 0;
   // workspace layout (offsets from the workspace base)
   size_t off_proofs = 0, off_scr = 0, off_tasks = 0, off_tiles = 0;
   size_t off_acc = 0, acc_bytes = 0, off_out = 0, total = 0;
@@ -109,6 +113,9 @@ struct vl_plan {
 
 namespace {
 
+// Persistent single launch unless the options ask for phase launches.
+bool persistent(const vl_plan* p) { return p->opts.persistent != 2; }
+
 void add_fold_task(vl_plan* p, const vl_mat& M, int32_t mode, int proof, int side) {
   FoldTask t{};
   t.mat = nullptr;  // bound at run time
@@ -121,6 +128,7 @@ void add_fold_task(vl_plan* p, const vl_mat& M, int32_t mode, int proof, int sid
   t.side = side;
   const int task = (int)p->tasks.size();
   p->tasks.push_back(t);
+  const size_t tiles_before = p->tiles.size();
   const bool fr = M.dtype == VL_FR_MONT;
   if (mode == MODE_COLSUM) {
     const int tc = fr ? FR_COLSUM_TILE_COLS : COLSUM_TILE_COLS;
@@ -150,6 +158,27 @@ void add_fold_task(vl_plan* p, const vl_mat& M, int32_t mode, int proof, int sid
         p->tiles.push_back(ft);
         p->fold_smem = std::max(p->fold_smem, fold_tile_smem(mode, M.dtype, ft.r1 - ft.r0, ft.c1 - ft.c0));
       }
+  }
+  p->proofs[proof].ntiles += (int32_t)(p->tiles.size() - tiles_before);
+}
+
+// Queue order of the persistent step.  Proofs go by k descending (their
+// rounds are the longest, and they should finish early); each proof's
+// prologue is queued STEP_LOOKAHEAD proofs ahead of its fold tiles.
+void build_items(vl_plan* p) {
+  const int np = (int)p->proofs.size();
+  std::vector<int> order(np);
+  for (int i = 0; i < np; i++) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return p->proofs[a].k > p->proofs[b].k; });
+  std::vector<std::vector<int>> tiles_of(np);
+  for (size_t t = 0; t < p->tiles.size(); t++) tiles_of[p->tasks[p->tiles[t].task].proof].push_back((int)t);
+  p->items.clear();
+  p->items.reserve(np + p->tiles.size());
+  const int look = std::min(np, STEP_LOOKAHEAD);
+  for (int i = 0; i < look; i++) p->items.push_back(StepItem{STEP_PROLOGUE, order[i]});
+  for (int i = 0; i < np; i++) {
+    if (i + look < np) p->items.push_back(StepItem{STEP_PROLOGUE, order[i + look]});
+    for (int t : tiles_of[order[i]]) p->items.push_back(StepItem{STEP_FOLD, t});
   }
 }
 
@@ -189,11 +218,16 @@ int build_plan(vl_plan* p) {
     // f_B: op(Q) over its n columns.  Stored k x n -> row dots; stored n x k -> column sums.
     add_fold_task(p, j.Q, j.Q.trans ? MODE_COLSUM : MODE_ROWDOT, i, 1);
   }
+  build_items(p);
   p->off_tasks = off;
   off = align_up(off + sizeof(FoldTask) * p->tasks.size());
   p->off_tiles = off;
   off = align_up(off + sizeof(FoldTile) * p->tiles.size());
-  // accumulators: one contiguous region, zeroed each pass
+  p->off_items = off;
+  off = align_up(off + sizeof(StepItem) * p->items.size());
+  // step control block and accumulators: one contiguous region, zeroed each pass
+  p->off_ctl = off;
+  off = align_up(off + sizeof(int) * (STEP_CTL_HEAD_INTS + 2 * (size_t)np));
   p->off_acc = off;
   for (int i = 0; i < np; i++) {
     const size_t kb = (size_t)p->proofs[i].k * 8 * sizeof(unsigned long long);
@@ -203,6 +237,7 @@ int build_plan(vl_plan* p) {
     off = align_up(off + kb);
   }
   p->acc_bytes = off - p->off_acc;
+  p->step_smem = std::max(p->fold_smem, std::max(PRO_SMEM, RND_SMEM));
   for (int i = 0; i < np; i++) {
     const DevProof& P = p->proofs[i];
     p->pp[i].eqA = off;
@@ -302,9 +337,14 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
   if (e == cudaSuccess && !p->tiles.empty())
     e = cudaMemcpyAsync(ws + p->off_tiles, p->tiles.data(), sizeof(FoldTile) * p->tiles.size(),
                         cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !p->items.empty())
+    e = cudaMemcpyAsync(ws + p->off_items, p->items.data(), sizeof(StepItem) * p->items.size(),
+                        cudaMemcpyHostToDevice, st);
   // The host vectors must outlive the copies: wait for them.
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess && p->fold_smem > 0) e = fold_set_smem(p->fold_smem);
+  if (e == cudaSuccess && persistent(p)) e = step_set_smem(p->step_smem);
+  if (e == cudaSuccess && persistent(p) && !p->step_grid) e = step_grid(p->step_smem, &p->step_grid);
   return cuda_status(e, "bind_workspace");
 }
 
@@ -342,6 +382,20 @@ cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t s
   // (the flag is only valid while capturing).
   const unsigned flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   cudaError_t e = cudaEventRecordWithFlags(ev[0], st, flags);
+  if (persistent(p)) {
+    // One launch: [0] clear, [1] the persistent step (prologues, folds and
+    // rounds interleaved), [2] empty.
+    int* ctl = reinterpret_cast<int*>(ws + p->off_ctl);
+    const StepItem* di = reinterpret_cast<const StepItem*>(ws + p->off_items);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + p->off_ctl, 0, p->off_acc - p->off_ctl + p->acc_bytes, st);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[1], st, flags);
+    if (e == cudaSuccess)
+      e = launch_step(di, (int)p->items.size(), dt, dl, dp, np, dout, ctl, p->step_grid, p->step_smem, wait_ns(p),
+                      p->opts.test_never_ready - 1, st);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2], st, flags);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[3], st, flags);
+    return e;
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(ws + p->off_acc, 0, p->acc_bytes, st);
   if (e == cudaSuccess) e = launch_prologue(dp, np, st);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[1], st, flags);
@@ -506,7 +560,7 @@ int32_t vl_plan_create(const vl_job* jobs, int32_t njobs, const vl_batch_opts* o
 
 size_t vl_plan_workspace_bytes(const vl_plan* plan) { return plan ? plan->total : 0; }
 
-int32_t vl_plan_launches(const vl_plan* plan) { return plan ? 3 : 0; }
+int32_t vl_plan_launches(const vl_plan* plan) { return plan ? (persistent(plan) ? 1 : 3) : 0; }
 
 int32_t vl_plan_run(vl_plan* plan, void* workspace, size_t workspace_bytes, vl_proof* out, int32_t out_space,
                     void* stream) {

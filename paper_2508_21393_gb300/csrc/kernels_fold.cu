@@ -1,542 +1,7 @@
-// Fold kernels: the restrictions of the operand MLEs to the sumcheck cube,
-//   f_A[w] = A~(u, w) = sum_i E_u[i] . op(P)[i, w]
-//   f_B[w] = B~(w, v) = sum_j op(Q)[w, j] . E_v[j]
-// (Eq. eq:zk-mle-matmul, Sec. II-C).  This reads every operand entry once and
-// is the bulk of the prover's work.
-//
-// int16 operands (fixed point).  An entry x is the field element x mod r.
-// With p = x + 2^15 in [0, 2^16) and weights e = E.R^2 (8 limbs of 32 bits),
-//   sum_i e_i . p_i = sum_l 2^(32 l) . (sum_i e_i[l] . p_i)
-// and each limb column sum is an exact unsigned 64-bit integer for up to 2^16
-// terms ((2^32 - 1)(2^16 - 1) 2^16 < 2^64).  So one entry costs 8 32x32->64
-// multiply-adds and no modular reduction; a tile adds its eight column sums
-// per output into global 64-bit accumulators (integer adds are exact, so the
-// order of tiles does not matter), and the rounds kernel reduces each
-// output once: REDC(sum e.p) = (sum E.p).R is the Montgomery form, minus the
-// offset correction 2^15 . sum E (written by the prologue).
-//
-// Feeding the multipliers: for int16 operands whose rows are 16-byte aligned,
-// a CTA streams its tile through NSTAGE shared-memory stages filled by bulk
-// asynchronous copies (cp.async.bulk, completion counted on an mbarrier per
-// stage), so loads of later stages are in flight while earlier stages are
-// multiplied.  Every wait is bounded (FOLD_WAIT_NS of the global timer by
-// default); a CTA whose wait runs out marks its proof VL_ETIMEOUT, waits
-// (again bounded) for its own copies still in flight, and returns.  Operands
-// that are not aligned take a register-load path.
-//
-// Montgomery operands (32 bytes per entry): one Montgomery product per entry,
-// mont_mul(E.R^2, x.R) = E.x.R^2, summed mod r per thread; partial sums are
-// added limb-wise into the same 64-bit accumulators, whose REDC again gives
-// the Montgomery form.
-#include "common.cuh"
+// Fold kernel: one CTA per fold tile (see fold_dev.cuh).
+#include "fold_dev.cuh"
 
 namespace vl {
-
-typedef unsigned long long u64;
-
-__device__ __forceinline__ uint2 ld_nc_u2(const void* p) {
-  uint2 r;
-  asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
-  return r;
-}
-
-__device__ __forceinline__ uint4 ld_nc_u4(const void* p) {
-  uint4 r;
-  asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
-  return r;
-}
-
-__device__ __forceinline__ void red_add_u64(u64* p, u64 v) {
-  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Wait for phase `parity` of an mbarrier, giving up at `deadline` (global ns).
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t deadline) {
-  while (!mbar_try_wait(bar, parity))
-    if (global_ns() > deadline) return false;
-  return true;
-}
-
-// Global -> shared bulk copy of `bytes` (multiple of 16, both addresses 16-byte
-// aligned), completion counted on mbarrier `bar`.
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-
-// Order earlier generic-proxy accesses to shared memory before later
-// async-proxy (bulk copy) writes into it.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ uint2 lds_u2(uint32_t addr) {
-  uint2 r;
-  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "r"(addr));
-  return r;
-}
-
-// Offset int16 -> [0, 2^16).
-__device__ __forceinline__ uint32_t off16(int16_t x) { return (uint32_t)(uint16_t)x ^ 0x8000u; }
-
-// Four consecutive int16 entries starting at `p` (offset form); entries at
-// column >= limit read as 2^15 (value zero).  `vec`: p is 8-byte aligned.
-__device__ __forceinline__ void load4_i16(const int16_t* p, int avail, bool vec, uint32_t out[4]) {
-  if (vec && avail >= 4) {
-    uint2 q = ld_nc_u2(p);
-    q.x ^= 0x80008000u;
-    q.y ^= 0x80008000u;
-    out[0] = q.x & 0xffffu;
-    out[1] = q.x >> 16;
-    out[2] = q.y & 0xffffu;
-    out[3] = q.y >> 16;
-  } else {
-#pragma unroll
-    for (int c = 0; c < 4; c++) out[c] = c < avail ? off16(p[c]) : 0x8000u;
-  }
-}
-
-// Sum a[32] over the 32 lanes of a warp; lane L returns the total of a[L].
-__device__ __forceinline__ u64 warp_transpose_sum(u64 (&a)[32]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
-    const bool upper = (lane & off) != 0;
-#pragma unroll
-    for (int i = 0; i < off; i++) {
-      u64 send = upper ? a[i] : a[i + off];
-      u64 keep = upper ? a[i + off] : a[i];
-      u64 recv = __shfl_xor_sync(0xffffffffu, send, off);
-      a[i] = keep + recv;
-    }
-  }
-  return a[0];
-}
-
-// ---------------------------------------------------------------- int16 ---
-
-// COLSUM over stored rows [r0, r1) and columns [c0, c1) (c1 - c0 <= 1024).
-// Thread layout: G column groups of 4 columns (G a power of two covering the
-// tile) times 256 / G row lanes.  Weights E[r] are staged in shared memory and
-// read as a broadcast.
-__device__ void colsum_i16(const FoldTask& T, const FoldTile& t, const Fr* __restrict__ E,
-                           u64* __restrict__ acc, uint4* sm) {
-  const int tid = threadIdx.x;
-  const int nrows = t.r1 - t.r0;
-  const uint4* Eg = reinterpret_cast<const uint4*>(E + t.r0);
-  for (int i = tid; i < 2 * nrows; i += FOLD_THREADS) sm[i] = Eg[i];
-  __syncthreads();
-
-  const int ncols = t.c1 - t.c0;
-  const int ngroups = (ncols + 3) >> 2;
-  int G = 1;
-  while (G < ngroups) G <<= 1;
-  const int RL = FOLD_THREADS / G;
-  const int grp = tid & (G - 1);
-  const int lr = tid / G;
-  if (grp >= ngroups) return;
-
-  const int c = t.c0 + 4 * grp;
-  const int avail = t.c1 - c;
-  const int16_t* base = static_cast<const int16_t*>(T.mat) + c;
-  const bool vec = ((reinterpret_cast<uintptr_t>(base) & 7) == 0) && ((T.ld & 3) == 0);
-
-  u64 a[4][8];
-#pragma unroll
-  for (int q = 0; q < 4; q++)
-#pragma unroll
-    for (int l = 0; l < 8; l++) a[q][l] = 0;
-
-#pragma unroll 2
-  for (int r = lr; r < nrows; r += RL) {
-    uint32_t p[4];
-    load4_i16(base + (int64_t)(t.r0 + r) * T.ld, avail, vec, p);
-    const uint4 e0 = sm[2 * r], e1 = sm[2 * r + 1];
-    const uint32_t e[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
-#pragma unroll
-    for (int q = 0; q < 4; q++)
-#pragma unroll
-      for (int l = 0; l < 8; l++) a[q][l] += (u64)e[l] * p[q];
-  }
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    if (q < avail) {
-      u64* dst = acc + (size_t)(c + q) * 8;
-#pragma unroll
-      for (int l = 0; l < 8; l++) red_add_u64(dst + l, a[q][l]);
-    }
-  }
-}
-
-// ROWDOT over stored rows [r0, r1) (<= 32: 4 per warp) and columns [c0, c1).
-// Lanes stride over columns, 4 per lane; the weights of the tile's columns are
-// staged in shared memory limb-major (conflict-free 16-byte reads).  At the
-// end a transpose-reduction leaves lane L with (row L / 8, limb L % 8).
-__device__ void rowdot_i16(const FoldTask& T, const FoldTile& t, const Fr* __restrict__ E,
-                           u64* __restrict__ acc, uint32_t* sm) {
-  const int tid = threadIdx.x;
-  const int ncols = t.c1 - t.c0;
-  const int pitch = (ncols + 3) & ~3;
-  for (int j = tid; j < pitch; j += FOLD_THREADS) {
-    Fr e = j < ncols ? E[t.c0 + j] : fr_zero();
-#pragma unroll
-    for (int l = 0; l < 8; l++) sm[l * pitch + j] = e.v[l];
-  }
-  __syncthreads();
-
-  const int warp = tid >> 5, lane = tid & 31;
-  const int rb = t.r0 + warp * ROWDOT_ROWS_PER_WARP;
-  const int16_t* M = static_cast<const int16_t*>(T.mat);
-  const bool vec = ((reinterpret_cast<uintptr_t>(M) & 7) == 0) && ((T.ld & 3) == 0) && ((t.c0 & 3) == 0);
-
-  u64 a[32];
-#pragma unroll
-  for (int i = 0; i < 32; i++) a[i] = 0;
-
-  for (int j = 4 * lane; j < ncols; j += 128) {
-    uint32_t e[4][8];
-#pragma unroll
-    for (int l = 0; l < 8; l++) {
-      const uint4 q = *reinterpret_cast<const uint4*>(sm + l * pitch + j);
-      e[0][l] = q.x;
-      e[1][l] = q.y;
-      e[2][l] = q.z;
-      e[3][l] = q.w;
-    }
-    const int avail = ncols - j;
-#pragma unroll
-    for (int rr = 0; rr < ROWDOT_ROWS_PER_WARP; rr++) {
-      const int r = rb + rr;
-      if (r < t.r1) {
-        uint32_t p[4];
-        load4_i16(M + (int64_t)r * T.ld + t.c0 + j, avail, vec, p);
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-#pragma unroll
-          for (int l = 0; l < 8; l++) a[rr * 8 + l] += (u64)e[q][l] * p[q];
-      }
-    }
-  }
-  const u64 s = warp_transpose_sum(a);
-  const int r = rb + (lane >> 3);
-  if (r < t.r1) red_add_u64(acc + (size_t)r * 8 + (lane & 7), s);
-}
-
-
-// ------------------------------------------------- int16, bulk pipeline ---
-
-struct Pipe {
-  uint32_t bar0;    // shared address of mbarrier 0 (NSTAGE consecutive 8-byte barriers)
-  uint32_t stage0;  // shared address of stage 0
-};
-
-__device__ __forceinline__ uint32_t pipe_bar(const Pipe& p, int s) { return p.bar0 + 8u * (uint32_t)(s % NSTAGE); }
-__device__ __forceinline__ uint32_t pipe_slot(const Pipe& p, int s) {
-  return p.stage0 + (uint32_t)(s % NSTAGE) * (uint32_t)STAGE_BYTES;
-}
-
-// Give up after a timed-out wait: mark the proof, then wait for this CTA's
-// copies still in flight (stages [from, to)) so that none lands in shared
-// memory after the CTA has exited.  This drain has its own fixed bound
-// (FOLD_WAIT_NS), independent of the caller's (possibly very short) limit.
-__device__ void pipe_abort(const Pipe& p, int from, int to, int* status) {
-  if (threadIdx.x == 0) {
-    atomicExch(status, VL_ETIMEOUT);
-    const uint64_t deadline = global_ns() + FOLD_WAIT_NS;
-    for (int s = from; s < to; s++) mbar_wait_bounded(pipe_bar(p, s), (uint32_t)(s / NSTAGE) & 1u, deadline);
-  }
-  __syncthreads();
-}
-
-// Stage s of a COLSUM tile: stored rows [r0 + s*SR, ...) x columns [c0, c1).
-__device__ __forceinline__ void colsum_issue(const Pipe& p, const FoldTask& T, const FoldTile& t, int s, int SR) {
-  const int lane = threadIdx.x & 31;
-  const int nrows = t.r1 - t.r0, ncols = t.c1 - t.c0;
-  const int rb = s * SR, rc = min(SR, nrows - rb);
-  const uint32_t row_bytes = (uint32_t)ncols * 2u;
-  const uint32_t bar = pipe_bar(p, s), slot = pipe_slot(p, s);
-  const int16_t* src = static_cast<const int16_t*>(T.mat) + (int64_t)(t.r0 + rb) * T.ld + t.c0;
-  if (lane == 0) {
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(bar, (uint32_t)rc * row_bytes);
-  }
-  __syncwarp();
-  if (T.ld == ncols) {  // whole rows, contiguous: one copy
-    if (lane == 0) bulk_g2s(slot, src, (uint32_t)rc * row_bytes, bar);
-  } else {
-    for (int rr = lane; rr < rc; rr += 32) bulk_g2s(slot + (uint32_t)rr * row_bytes, src + (int64_t)rr * T.ld, row_bytes, bar);
-  }
-}
-
-__device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, const Fr* __restrict__ E, u64* __restrict__ acc,
-                                uint8_t* smem, int* status, uint64_t wait_ns) {
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int nrows = t.r1 - t.r0, ncols = t.c1 - t.c0;
-  const uint32_t row_bytes = (uint32_t)ncols * 2u;
-  const int SR = min(nrows, max(1, STAGE_BYTES / (int)row_bytes));
-  const int nst = (nrows + SR - 1) / SR;
-  uint4* Es = reinterpret_cast<uint4*>(smem + FOLD_SMEM_HEAD);
-  Pipe p;
-  p.bar0 = smem_addr(smem);
-  p.stage0 = smem_addr(smem + FOLD_SMEM_HEAD + nrows * 32);
-  if (tid == 0) {
-    for (int q = 0; q < NSTAGE; q++) mbar_init(p.bar0 + 8u * q, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  if (warp == 0)
-    for (int s = 0; s < min(nst, NSTAGE - 1); s++) colsum_issue(p, T, t, s, SR);
-  // Weights of the tile's rows, broadcast later from shared memory.
-  const uint4* Eg = reinterpret_cast<const uint4*>(E + t.r0);
-  for (int i = tid; i < 2 * nrows; i += FOLD_THREADS) Es[i] = Eg[i];
-  __syncthreads();
-
-  const int ngroups = ncols >> 2;  // ncols is a multiple of 8 on this path
-  int G = 1;
-  while (G < ngroups) G <<= 1;
-  const int RL = FOLD_THREADS / G;
-  const int grp = tid & (G - 1), lr = tid / G;
-  const bool active = grp < ngroups;
-
-  u64 a[4][8];
-#pragma unroll
-  for (int q = 0; q < 4; q++)
-#pragma unroll
-    for (int l = 0; l < 8; l++) a[q][l] = 0;
-
-  for (int s = 0; s < nst; s++) {
-    if (warp == 0 && s + NSTAGE - 1 < nst) colsum_issue(p, T, t, s + NSTAGE - 1, SR);
-    const bool ok = mbar_wait_bounded(pipe_bar(p, s), (uint32_t)(s / NSTAGE) & 1u, global_ns() + wait_ns);
-    if (ok && active) {
-      const int rb = s * SR, rc = min(SR, nrows - rb);
-      const uint32_t slot = pipe_slot(p, s) + 8u * (uint32_t)grp;
-      for (int rr = lr; rr < rc; rr += RL) {
-        uint2 q2 = lds_u2(slot + (uint32_t)rr * row_bytes);
-        q2.x ^= 0x80008000u;
-        q2.y ^= 0x80008000u;
-        const uint32_t pv[4] = {q2.x & 0xffffu, q2.x >> 16, q2.y & 0xffffu, q2.y >> 16};
-        const uint4 e0 = Es[2 * (rb + rr)], e1 = Es[2 * (rb + rr) + 1];
-        const uint32_t e[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-#pragma unroll
-          for (int l = 0; l < 8; l++) a[q][l] += (u64)e[l] * pv[q];
-      }
-    }
-    if (!__syncthreads_and(ok)) {
-      pipe_abort(p, s, min(nst, s + NSTAGE), status);
-      return;
-    }
-  }
-  if (active) {
-    const int c = t.c0 + 4 * grp;
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      u64* dst = acc + (size_t)(c + q) * 8;
-#pragma unroll
-      for (int l = 0; l < 8; l++) red_add_u64(dst + l, a[q][l]);
-    }
-  }
-}
-
-// Stage s of a ROWDOT tile: columns [c0 + s*SC, ...) of all tile rows, one
-// copy per row (lane rr of warp 0 copies row rr).
-__device__ __forceinline__ void rowdot_issue(const Pipe& p, const FoldTask& T, const FoldTile& t, int s) {
-  const int lane = threadIdx.x & 31;
-  const int nrows = t.r1 - t.r0, ncols = t.c1 - t.c0;
-  const int cb = s * ROWDOT_STAGE_COLS, cc = min(ROWDOT_STAGE_COLS, ncols - cb);
-  const uint32_t bytes = (uint32_t)cc * 2u;
-  const uint32_t bar = pipe_bar(p, s), slot = pipe_slot(p, s);
-  if (lane == 0) {
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(bar, (uint32_t)nrows * bytes);
-  }
-  __syncwarp();
-  if (lane < nrows) {
-    const int16_t* src = static_cast<const int16_t*>(T.mat) + (int64_t)(t.r0 + lane) * T.ld + t.c0 + cb;
-    bulk_g2s(slot + (uint32_t)lane * (ROWDOT_STAGE_COLS * 2u), src, bytes, bar);
-  }
-}
-
-__device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, const Fr* __restrict__ E, u64* __restrict__ acc,
-                                uint8_t* smem, int* status, uint64_t wait_ns) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nrows = t.r1 - t.r0, ncols = t.c1 - t.c0;
-  const int pitch = (ncols + 3) & ~3;
-  const int nst = (ncols + ROWDOT_STAGE_COLS - 1) / ROWDOT_STAGE_COLS;
-  uint32_t* Es = reinterpret_cast<uint32_t*>(smem + FOLD_SMEM_HEAD);
-  Pipe p;
-  p.bar0 = smem_addr(smem);
-  p.stage0 = smem_addr(smem + FOLD_SMEM_HEAD + pitch * 32);
-  if (tid == 0) {
-    for (int q = 0; q < NSTAGE; q++) mbar_init(p.bar0 + 8u * q, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  if (warp == 0)
-    for (int s = 0; s < min(nst, NSTAGE - 1); s++) rowdot_issue(p, T, t, s);
-  // Weights of the tile's columns, limb-major (conflict-free 16-byte reads).
-  for (int j = tid; j < pitch; j += FOLD_THREADS) {
-    Fr e = j < ncols ? E[t.c0 + j] : fr_zero();
-#pragma unroll
-    for (int l = 0; l < 8; l++) Es[l * pitch + j] = e.v[l];
-  }
-  __syncthreads();
-
-  const int rb = warp * ROWDOT_ROWS_PER_WARP;  // tile-local first row of this warp
-  u64 a[32];
-#pragma unroll
-  for (int i = 0; i < 32; i++) a[i] = 0;
-
-  for (int s = 0; s < nst; s++) {
-    if (warp == 0 && s + NSTAGE - 1 < nst) rowdot_issue(p, T, t, s + NSTAGE - 1);
-    const bool ok = mbar_wait_bounded(pipe_bar(p, s), (uint32_t)(s / NSTAGE) & 1u, global_ns() + wait_ns);
-    if (ok) {
-      const int cb = s * ROWDOT_STAGE_COLS;
-      const uint32_t slot = pipe_slot(p, s);
-#pragma unroll 1
-      for (int half = 0; half < ROWDOT_STAGE_COLS / 128; half++) {
-        const int jl = half * 128 + 4 * lane;  // stage-local column
-        const int j = cb + jl;                 // tile-local column
-        if (j < ncols) {
-          uint32_t e[4][8];
-#pragma unroll
-          for (int l = 0; l < 8; l++) {
-            const uint4 q = *reinterpret_cast<const uint4*>(Es + l * pitch + j);
-            e[0][l] = q.x;
-            e[1][l] = q.y;
-            e[2][l] = q.z;
-            e[3][l] = q.w;
-          }
-#pragma unroll
-          for (int rr = 0; rr < ROWDOT_ROWS_PER_WARP; rr++) {
-            if (rb + rr < nrows) {
-              uint2 q2 = lds_u2(slot + (uint32_t)(rb + rr) * (ROWDOT_STAGE_COLS * 2u) + 2u * (uint32_t)jl);
-              q2.x ^= 0x80008000u;
-              q2.y ^= 0x80008000u;
-              const uint32_t pv[4] = {q2.x & 0xffffu, q2.x >> 16, q2.y & 0xffffu, q2.y >> 16};
-#pragma unroll
-              for (int q = 0; q < 4; q++)
-#pragma unroll
-                for (int l = 0; l < 8; l++) a[rr * 8 + l] += (u64)e[q][l] * pv[q];
-            }
-          }
-        }
-      }
-    }
-    if (!__syncthreads_and(ok)) {
-      pipe_abort(p, s, min(nst, s + NSTAGE), status);
-      return;
-    }
-  }
-  const u64 sum = warp_transpose_sum(a);
-  const int r = t.r0 + rb + (lane >> 3);
-  if (r < t.r1) red_add_u64(acc + (size_t)r * 8 + (lane & 7), sum);
-}
-
-// ------------------------------------------------------------ Montgomery ---
-
-__device__ __forceinline__ Fr load_fr(const Fr* p) {
-  const uint4 a = ld_nc_u4(p), b = ld_nc_u4(reinterpret_cast<const uint4*>(p) + 1);
-  Fr x;
-  x.v[0] = a.x; x.v[1] = a.y; x.v[2] = a.z; x.v[3] = a.w;
-  x.v[4] = b.x; x.v[5] = b.y; x.v[6] = b.z; x.v[7] = b.w;
-  return x;
-}
-
-// COLSUM of a Montgomery matrix: one column per thread (c1 - c0 <= 256).
-__device__ void colsum_fr(const FoldTask& T, const FoldTile& t, const Fr* __restrict__ E,
-                          u64* __restrict__ acc, uint4* sm) {
-  const int tid = threadIdx.x;
-  const int nrows = t.r1 - t.r0;
-  const uint4* Eg = reinterpret_cast<const uint4*>(E + t.r0);
-  for (int i = tid; i < 2 * nrows; i += FOLD_THREADS) sm[i] = Eg[i];
-  __syncthreads();
-  const int ncols = t.c1 - t.c0;
-  int G = 1;
-  while (G < ncols) G <<= 1;
-  const int RL = FOLD_THREADS / G;
-  const int col = tid & (G - 1), lr = tid / G;
-  if (col >= ncols) return;
-  const Fr* M = static_cast<const Fr*>(T.mat) + t.c0 + col;
-  Fr s = fr_zero();
-  for (int r = lr; r < nrows; r += RL) {
-    const Fr x = load_fr(M + (int64_t)(t.r0 + r) * T.ld);
-    const Fr* e = reinterpret_cast<const Fr*>(sm + 2 * r);
-    s = fr_add(s, mont_mul(x, *e));
-  }
-  u64* dst = acc + (size_t)(t.c0 + col) * 8;
-#pragma unroll
-  for (int l = 0; l < 8; l++) red_add_u64(dst + l, s.v[l]);
-}
-
-// ROWDOT of a Montgomery matrix: 4 rows per warp, lanes over columns.
-__device__ void rowdot_fr(const FoldTask& T, const FoldTile& t, const Fr* __restrict__ E,
-                          u64* __restrict__ acc, uint32_t* sm) {
-  const int tid = threadIdx.x;
-  const int ncols = t.c1 - t.c0;
-  const int pitch = ncols;
-  for (int j = tid; j < ncols; j += FOLD_THREADS) {
-    Fr e = E[t.c0 + j];
-#pragma unroll
-    for (int l = 0; l < 8; l++) sm[l * pitch + j] = e.v[l];
-  }
-  __syncthreads();
-  const int warp = tid >> 5, lane = tid & 31;
-  const int rb = t.r0 + warp * ROWDOT_ROWS_PER_WARP;
-  const Fr* M = static_cast<const Fr*>(T.mat);
-  Fr s[ROWDOT_ROWS_PER_WARP];
-#pragma unroll
-  for (int rr = 0; rr < ROWDOT_ROWS_PER_WARP; rr++) s[rr] = fr_zero();
-  for (int j = lane; j < ncols; j += 32) {
-    Fr e;
-#pragma unroll
-    for (int l = 0; l < 8; l++) e.v[l] = sm[l * pitch + j];
-#pragma unroll
-    for (int rr = 0; rr < ROWDOT_ROWS_PER_WARP; rr++) {
-      const int r = rb + rr;
-      if (r < t.r1) s[rr] = fr_add(s[rr], mont_mul(load_fr(M + (int64_t)r * T.ld + t.c0 + j), e));
-    }
-  }
-  u64 a[32];
-#pragma unroll
-  for (int rr = 0; rr < ROWDOT_ROWS_PER_WARP; rr++)
-#pragma unroll
-    for (int l = 0; l < 8; l++) a[rr * 8 + l] = s[rr].v[l];
-  const u64 tot = warp_transpose_sum(a);
-  const int r = rb + (lane >> 3);
-  if (r < t.r1) red_add_u64(acc + (size_t)r * 8 + (lane & 7), tot);
-}
 
 __global__ void __launch_bounds__(FOLD_THREADS, 2) fold_kernel(const FoldTask* __restrict__ tasks,
                                                                const FoldTile* __restrict__ tiles,
@@ -545,22 +10,7 @@ __global__ void __launch_bounds__(FOLD_THREADS, 2) fold_kernel(const FoldTask* _
   extern __shared__ __align__(128) uint8_t fold_smem[];
   const FoldTile t = tiles[blockIdx.x];
   const FoldTask T = tasks[t.task];
-  const DevProof& P = proofs[T.proof];
-  const Fr* E = T.side ? P.eqB : P.eqA;
-  u64* acc = T.side ? P.accB : P.accA;
-  uint4* sm4 = reinterpret_cast<uint4*>(fold_smem + FOLD_SMEM_HEAD);
-  if (T.dtype == VL_I16) {
-    if (T.bulk) {
-      if (T.mode == MODE_COLSUM) colsum_i16_bulk(T, t, E, acc, fold_smem, &P.scr->status, wait_ns);
-      else rowdot_i16_bulk(T, t, E, acc, fold_smem, &P.scr->status, wait_ns);
-    } else {
-      if (T.mode == MODE_COLSUM) colsum_i16(T, t, E, acc, sm4);
-      else rowdot_i16(T, t, E, acc, reinterpret_cast<uint32_t*>(sm4));
-    }
-  } else {
-    if (T.mode == MODE_COLSUM) colsum_fr(T, t, E, acc, sm4);
-    else rowdot_fr(T, t, E, acc, reinterpret_cast<uint32_t*>(sm4));
-  }
+  fold_tile(T, t, proofs[T.proof], fold_smem, wait_ns);
 }
 
 // The limit is per kernel and process-wide, so it only ever grows: a plan

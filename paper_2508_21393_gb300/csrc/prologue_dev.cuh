@@ -1,0 +1,128 @@
+// Prologue of each proof: transcript start, the squeezes of u (d0 row
+// challenges) and v (d2 column challenges), and the eq tables
+//   E_u[i] = eq(u, bits(i)),  E_v[j] = eq(v, bits(j))
+// of Eq. eq:MLE (Sec. II-B), written only for the real (unpadded) indices.
+//
+// eq(x, bits(i)) = prod_t (x_t if b_t else 1 - x_t), b_1 the MSB.  Split the d
+// variables into a high block (first d - s) and a low block (last s): then
+// E[i] = E_hi[i >> s] . E_lo[i mod 2^s], each factor table small enough for
+// shared memory, and every output entry costs one Montgomery product.
+// E_hi is kept in Montgomery form, E_lo in double-Montgomery form, so the
+// product lands in double-Montgomery form (x.R^2), the weight format the
+// int16 fold needs.  The kernel also writes 2^15 . sum_i E[i] (Montgomery),
+// the correction for the +2^15 offset that the int16 fold applies.
+#pragma once
+#include "common.cuh"
+#include "reduce.cuh"
+#include "transcript.cuh"
+#include "fr_dev.cuh"
+#include "transcript_dev.cuh"
+
+namespace vl {
+
+static constexpr int MAX_VARS = 16;      // log2 of VL_MAX_REDUCE
+static constexpr int MAX_HALF = 1 << 8;  // 2^(MAX_VARS / 2)
+
+__device__ static Fr build_eq(const Fr* x, int d, int size, Fr* out, Fr* lo, Fr* hi, Fr* red) {
+  const int tid = threadIdx.x;
+  const int s = (d + 1) >> 1;          // low-block variables
+  const int dh = d - s;                // high-block variables
+  const int nlo = 1 << s;
+  const int nhi = (size + nlo - 1) >> s;
+  for (int j = tid; j < nlo; j += blockDim.x) {
+    Fr acc = fr_r2();  // 1 in double-Montgomery form
+    for (int t = 0; t < s; t++) {
+      const Fr& xt = x[dh + t];
+      int b = (j >> (s - 1 - t)) & 1;
+      acc = mont_mul_ni(acc, b ? xt : fr_sub(fr_r1(), xt));
+    }
+    lo[j] = acc;
+  }
+  for (int j = tid; j < nhi; j += blockDim.x) {
+    Fr acc = fr_r1();  // 1 in Montgomery form
+    for (int t = 0; t < dh; t++) {
+      const Fr& xt = x[t];
+      int b = (j >> (dh - 1 - t)) & 1;
+      acc = mont_mul_ni(acc, b ? xt : fr_sub(fr_r1(), xt));
+    }
+    hi[j] = acc;
+  }
+  __syncthreads();
+  Fr sum[1] = {fr_zero()};
+  for (int i = tid; i < size; i += blockDim.x) {
+    Fr e = mont_mul_ni(hi[i >> s], lo[i & (nlo - 1)]);
+    out[i] = e;
+    sum[0] = fr_add(sum[0], e);
+  }
+  block_sum_fr<1>(sum, red);
+  // sum = sum_i E_i . R^2; one Montgomery product with the plain integer 2^15
+  // gives 2^15 . sum_i E_i . R.
+  return mont_mul_ni(sum[0], fr_small(1u << 15));
+}
+
+// Squeeze `count` challenges with `label` from the state Sw (big-endian
+// words): thread 2t + h hashes half h of challenge t, thread 2 count the
+// closing update.  Writes the challenges (Montgomery) to x and the new state
+// to Sn.  Block-wide (two barriers).
+__device__ static void squeeze_dev(const uint32_t* Sw, uint32_t label, int count, Fr* x, uint32_t* Sn,
+                                   uint32_t (*dig)[8]) {
+  const int tid = threadIdx.x;
+  if (tid <= 2 * count) {
+    uint32_t st[8], d[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) st[i] = Sw[i];
+    if (tid < 2 * count) {
+      dev_squeeze_block(st, label, (uint32_t)(tid >> 1), tid & 1, d);
+#pragma unroll
+      for (int i = 0; i < 8; i++) dig[tid][i] = d[i];
+    } else {
+      dev_squeeze_block(st, label, (uint32_t)count, 2, d);
+#pragma unroll
+      for (int i = 0; i < 8; i++) Sn[i] = d[i];
+    }
+  }
+  __syncthreads();
+  if (tid < count) x[tid] = to_mont_ni(reduce_512_ni(digest_le(dig[2 * tid]), digest_le(dig[2 * tid + 1])));
+  __syncthreads();
+}
+
+// Shared memory the prologue needs (PRO_SMEM bytes), laid out below.
+static_assert(PRO_SMEM == 128 + 2 * MAX_VARS * 32 + 2 * MAX_VARS * 32 + 2 * MAX_HALF * 32 + 8 * 32, "layout");
+
+// Prologue of one proof by the whole block (any multiple of 32 threads, at
+// least 64): transcript start, squeezes of u and v, eq tables, corrections.
+static __device__ void prologue_block(const DevProof& P, uint8_t* smem) {
+  uint32_t* S0 = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* S1 = S0 + 8;
+  uint32_t* S2 = S0 + 16;
+  uint32_t(*dig)[8] = reinterpret_cast<uint32_t(*)[8]>(smem + 128);
+  Fr* u = reinterpret_cast<Fr*>(smem + 128 + 2 * MAX_VARS * 32);
+  Fr* v = u + MAX_VARS;
+  Fr* lo = v + MAX_VARS;
+  Fr* hi = lo + MAX_HALF;
+  Fr* red = hi + MAX_HALF;
+  const int tid = threadIdx.x;
+
+  if (tid == 0) {
+    uint8_t b[32];
+    ts_start(b, P.seed, P.m, P.k, P.n, P.tp, P.tq, P.binds);
+    for (int i = 0; i < 8; i++)
+      S0[i] = ((uint32_t)b[4 * i] << 24) | ((uint32_t)b[4 * i + 1] << 16) | ((uint32_t)b[4 * i + 2] << 8) | b[4 * i + 3];
+  }
+  __syncthreads();
+  squeeze_dev(S0, LBL_U, P.d0, u, S1, dig);
+  squeeze_dev(S1, LBL_V, P.d2, v, S2, dig);
+  if (tid < 32) P.scr->state[tid] = (uint8_t)(S2[tid >> 2] >> (24 - 8 * (tid & 3)));
+
+  Fr ca = build_eq(u, P.d0, P.m, P.eqA, lo, hi, red);
+  __syncthreads();
+  Fr cb = build_eq(v, P.d2, P.n, P.eqB, lo, hi, red);
+  if (tid == 0) {
+    P.scr->corrA = P.dtypeA == VL_I16 ? ca : fr_zero();
+    P.scr->corrB = P.dtypeB == VL_I16 ? cb : fr_zero();
+    P.scr->status = VL_OK;
+  }
+  __syncthreads();
+}
+
+}  // namespace vl

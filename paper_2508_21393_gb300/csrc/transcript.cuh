@@ -9,7 +9,8 @@
 //   squeeze : x_t = LE512(SHA256(S||label||t u32le||0x00) ||
 //                         SHA256(S||label||t u32le||0x01)) mod r, t < count,
 //             then S <- SHA256(S || label || count u32le)
-// Field elements are serialised canonical, 32 bytes little-endian.
+// Field elements are serialised canonical, 32 bytes little-endian.  A
+// sumcheck round absorbs g(0) || g(2): g(1) is fixed by the running claim.
 // Squeezed challenges of one label depend only on the state before the
 // squeeze, so they can be derived in parallel (one thread per t).
 #pragma once

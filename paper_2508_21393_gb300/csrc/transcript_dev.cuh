@@ -19,17 +19,6 @@ namespace vl {
 
 __device__ __forceinline__ uint32_t rotr_dev(uint32_t x, int n) { return __funnelshift_r(x, x, n); }
 
-// Round constants of SHA-256 in constant memory (read as a broadcast).
-static __constant__ uint32_t SHA_K_DEV[64] = {
-    0x428a2f98u, 0x71374491u, 0xb5c0fbcfu, 0xe9b5dba5u, 0x3956c25bu, 0x59f111f1u, 0x923f82a4u, 0xab1c5ed5u,
-    0xd807aa98u, 0x12835b01u, 0x243185beu, 0x550c7dc3u, 0x72be5d74u, 0x80deb1feu, 0x9bdc06a7u, 0xc19bf174u,
-    0xe49b69c1u, 0xefbe4786u, 0x0fc19dc6u, 0x240ca1ccu, 0x2de92c6fu, 0x4a7484aau, 0x5cb0a9dcu, 0x76f988dau,
-    0x983e5152u, 0xa831c66du, 0xb00327c8u, 0xbf597fc7u, 0xc6e00bf3u, 0xd5a79147u, 0x06ca6351u, 0x14292967u,
-    0x27b70a85u, 0x2e1b2138u, 0x4d2c6dfcu, 0x53380d13u, 0x650a7354u, 0x766a0abbu, 0x81c2c92eu, 0x92722c85u,
-    0xa2bfe8a1u, 0xa81a664bu, 0xc24b8b70u, 0xc76c51a3u, 0xd192e819u, 0xd6990624u, 0xf40e3585u, 0x106aa070u,
-    0x19a4c116u, 0x1e376c08u, 0x2748774cu, 0x34b0bcb5u, 0x391c0cb3u, 0x4ed8aa4au, 0x5b9cca4fu, 0x682e6ff3u,
-    0x748f82eeu, 0x78a5636fu, 0x84c87814u, 0x8cc70208u, 0x90befffau, 0xa4506cebu, 0xbef9a3f7u, 0xc67178f2u};
-
 struct ShaState {
   uint32_t h[8];
 };
@@ -37,30 +26,28 @@ struct ShaBlock {
   uint32_t w[16];
 };
 
-// One SHA-256 compression.  Kept out of line (one copy per kernel module)
-// and rolled into four 16-round passes: the transcript is a serial chain of
-// compressions, and a fully unrolled compression inlined at every call site
-// makes the rounds kernel too large for the instruction cache.
+// One SHA-256 compression, fully unrolled with the round constants as
+// immediates, kept out of line (one copy per kernel module): the transcript
+// is a serial chain of compressions, and an inlined copy at every call site
+// makes the latency-bound kernels larger than the instruction cache.  h + K +
+// W is formed off the e-chain, Ch and Maj use their two-operation forms.
 static __device__ __noinline__ ShaState sha256_block_ni(ShaState st, ShaBlock m) {
   uint32_t a = st.h[0], b = st.h[1], c = st.h[2], d = st.h[3], e = st.h[4], f = st.h[5], g = st.h[6],
            h = st.h[7];
-#pragma unroll 1
-  for (int base = 0; base < 64; base += 16) {
 #pragma unroll
-    for (int i = 0; i < 16; i++) {
-      if (base > 0) {
-        const uint32_t x = m.w[(i + 1) & 15], y = m.w[(i + 14) & 15];
-        const uint32_t s0 = rotr_dev(x, 7) ^ rotr_dev(x, 18) ^ (x >> 3);
-        const uint32_t s1 = rotr_dev(y, 17) ^ rotr_dev(y, 19) ^ (y >> 10);
-        m.w[i] = m.w[i] + s0 + m.w[(i + 9) & 15] + s1;
-      }
-      const uint32_t S1 = rotr_dev(e, 6) ^ rotr_dev(e, 11) ^ rotr_dev(e, 25);
-      const uint32_t ch = (e & f) ^ (~e & g);
-      const uint32_t t1 = h + S1 + ch + SHA_K_DEV[base + i] + m.w[i];
-      const uint32_t S0 = rotr_dev(a, 2) ^ rotr_dev(a, 13) ^ rotr_dev(a, 22);
-      const uint32_t mj = (a & b) ^ (a & c) ^ (b & c);
-      h = g; g = f; f = e; e = d + t1; d = c; c = b; b = a; a = t1 + S0 + mj;
+  for (int i = 0; i < 64; i++) {
+    if (i >= 16) {
+      const uint32_t x = m.w[(i - 15) & 15], y = m.w[(i - 2) & 15];
+      m.w[i & 15] += (rotr_dev(x, 7) ^ rotr_dev(x, 18) ^ (x >> 3)) + m.w[(i - 7) & 15] +
+                     (rotr_dev(y, 17) ^ rotr_dev(y, 19) ^ (y >> 10));
     }
+    const uint32_t hkw = h + (sha_k(i) + m.w[i & 15]);
+    const uint32_t s1 = rotr_dev(e, 6) ^ rotr_dev(e, 11) ^ rotr_dev(e, 25);
+    const uint32_t ch = g ^ (e & (f ^ g));
+    const uint32_t t1 = hkw + ch + s1;
+    const uint32_t s0 = rotr_dev(a, 2) ^ rotr_dev(a, 13) ^ rotr_dev(a, 22);
+    const uint32_t mj = (a & b) | (c & (a | b));
+    h = g; g = f; f = e; e = d + t1; d = c; c = b; b = a; a = t1 + (s0 + mj);
   }
   st.h[0] += a; st.h[1] += b; st.h[2] += c; st.h[3] += d;
   st.h[4] += e; st.h[5] += f; st.h[6] += g; st.h[7] += h;

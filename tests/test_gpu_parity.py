@@ -274,3 +274,45 @@ def test_plans_taking_turns_on_one_workspace():
     finally:
         B.vl_plan_destroy(pa)
         B.vl_plan_destroy(pb)
+
+
+def test_phase_launch_mode_matches_persistent():
+    jobs = _lora_jobs(n=40, d=128, k=96, r=8, layer=6, proj="q")
+    dj, keep = _dev_jobs(jobs)
+    refs = [oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes() for j in jobs]
+    for mode in (0, 2):
+        opts = B.vl_batch_opts()
+        opts.persistent = mode
+        nb = B.vl_workspace_bytes(dj, opts)
+        ws = _ws(nb)
+        proofs = B.vl_prove_batch(dj, ws.data_ptr(), nb, opts=opts)
+        assert [B.proof_bytes(p) for p in proofs] == refs
+
+
+def test_wait_that_runs_out_reports_timeout_and_context_survives():
+    """A prologue that never signals ready (host-injected): the proof's fold
+    tiles give up after the bounded wait, the proof reports VL_ETIMEOUT, the
+    other proofs are unaffected, and the next run on the context is clean."""
+    jobs = _lora_jobs(n=24, d=64, k=64, r=8, layer=7, proj="v")
+    dj, keep = _dev_jobs(jobs)
+    refs = [oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes() for j in jobs]
+    bad = 3
+    opts = B.vl_batch_opts()
+    opts.wait_limit_us = 20000
+    opts.test_never_ready = bad + 1
+    plan = B.vl_plan_create(dj, opts)
+    try:
+        nb = B.vl_plan_workspace_bytes(plan)
+        ws = _ws(nb)
+        out = (B.vl_proof * len(dj))()
+        with pytest.raises(B.VLError) as e:
+            B.vl_plan_run(plan, ws.data_ptr(), nb, out, B.VL_HOST)
+        assert e.value.code == B.VL_ETIMEOUT
+        assert out[bad].status == B.VL_ETIMEOUT
+        for i, (pf, ref) in enumerate(zip(out, refs)):
+            if i != bad:
+                assert pf.status == 0 and B.proof_bytes(pf) == ref
+    finally:
+        B.vl_plan_destroy(plan)
+    proofs = B.vl_prove_batch(dj, ws.data_ptr(), nb)
+    assert [B.proof_bytes(p) for p in proofs] == refs
