@@ -33,15 +33,11 @@ namespace vl {
 // 8 warps (3 x 8 x 8 x 8 bytes at offset 256).
 static_assert(RND_SMEM == 256 + 3 * 8 * 8 * 8, "layout");
 
-__device__ __forceinline__ U64x8 load_acc(const unsigned long long* acc, int w) {
+__device__ __forceinline__ Fr load_acc_fr(const unsigned long long* acc, int w, const Fr& corr) {
   U64x8 a;
 #pragma unroll
   for (int l = 0; l < 8; l++) a.v[l] = acc[(size_t)w * 8 + l];
-  return a;
-}
-
-__device__ __forceinline__ Fr load_acc_fr(const unsigned long long* acc, int w, const Fr& corr) {
-  return fr_sub(redc_columns_ni(load_acc(acc, w)), corr);
+  return fr_sub(redc_columns_ni(a), corr);
 }
 
 __device__ __forceinline__ void store_fr(vl_fr* dst, const Fr& x) {
@@ -53,29 +49,10 @@ __device__ __forceinline__ Fr fold1(const Fr& x0, const Fr& x1, const Fr& r) {
   return fr_add(x0, mont_mul_ni(r, fr_sub(x1, x0)));
 }
 
-// g(0), g(2), g(1) terms of one pair of pairs: three independent products in one call.
 __device__ __forceinline__ void accum_g(Fr (&g)[3], const Fr& a0, const Fr& a1, const Fr& b0, const Fr& b1) {
-  FrN<3> x, y;
-  x.x[0] = a0; y.x[0] = b0;
-  x.x[1] = a1; y.x[1] = b1;
-  x.x[2] = fr_sub(fr_dbl(a1), a0); y.x[2] = fr_sub(fr_dbl(b1), b0);
-  const FrN<3> p = mont_mul_batch<3>(x, y);
-  g[0] = fr_add(g[0], p.x[0]);
-  g[1] = fr_add(g[1], p.x[1]);
-  g[2] = fr_add(g[2], p.x[2]);
-}
-
-// Four folds with the same challenge in one call: out[q] = x0[q] + r (x1[q] - x0[q]).
-__device__ __forceinline__ void fold4(const Fr (&x0)[4], const Fr (&x1)[4], const Fr& r, Fr (&out)[4]) {
-  FrN<4> d, rr;
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    d.x[q] = fr_sub(x1[q], x0[q]);
-    rr.x[q] = r;
-  }
-  const FrN<4> p = mont_mul_batch<4>(rr, d);
-#pragma unroll
-  for (int q = 0; q < 4; q++) out[q] = fr_add(x0[q], p.x[q]);
+  g[0] = fr_add(g[0], mont_mul_ni(a0, b0));
+  g[1] = fr_add(g[1], mont_mul_ni(a1, b1));
+  g[2] = fr_add(g[2], mont_mul_ni(fr_sub(fr_dbl(a1), a0), fr_sub(fr_dbl(b1), b0)));
 }
 
 // Warp 0: absorb the round message in gsh (lane 0), then squeeze one
@@ -176,20 +153,13 @@ static __device__ void rounds_block(const DevProof& P, vl_proof* pf, uint8_t* sm
   {
     const int h = K >> 1;
     for (int j = tid; j < h; j += nthr) {
-      // K/2 < k <= K, so j < k always; j + h may be padding (zero sums).
-      U64x8N<4> acc4;
-      acc4.x[0] = load_acc(P.accA, j);
-      acc4.x[1] = load_acc(P.accB, j);
-      const bool hi = j + h < P.k;
-#pragma unroll
-      for (int l = 0; l < 8; l++) acc4.x[2].v[l] = acc4.x[3].v[l] = 0;
-      if (hi) {
-        acc4.x[2] = load_acc(P.accA, j + h);
-        acc4.x[3] = load_acc(P.accB, j + h);
+      // K/2 < k <= K, so j < k always; j + h may be padding.
+      const Fr a0 = load_acc_fr(P.accA, j, corrA), b0 = load_acc_fr(P.accB, j, corrB);
+      Fr a1 = fr_zero(), b1 = fr_zero();
+      if (j + h < P.k) {
+        a1 = load_acc_fr(P.accA, j + h, corrA);
+        b1 = load_acc_fr(P.accB, j + h, corrB);
       }
-      const FrN<4> f = redc_batch<4>(acc4);
-      const Fr a0 = fr_sub(f.x[0], corrA), b0 = fr_sub(f.x[1], corrB);
-      const Fr a1 = hi ? fr_sub(f.x[2], corrA) : fr_zero(), b1 = hi ? fr_sub(f.x[3], corrB) : fr_zero();
       fA[j] = a0; fA[j + h] = a1;
       fB[j] = b0; fB[j + h] = b1;
       accum_g(g, a0, a1, b0, b1);
@@ -210,13 +180,11 @@ static __device__ void rounds_block(const DevProof& P, vl_proof* pf, uint8_t* sm
       const int hh = h >> 1;
       Fr gn[3] = {fr_zero(), fr_zero(), fr_zero()};
       for (int j = tid; j < hh; j += nthr) {
-        const Fr lo4[4] = {fA[j], fA[j + hh], fB[j], fB[j + hh]};
-        const Fr hi4[4] = {fA[j + h], fA[j + hh + h], fB[j + h], fB[j + hh + h]};
-        Fr nf[4];
-        fold4(lo4, hi4, r, nf);
-        fA[j] = nf[0]; fA[j + hh] = nf[1];
-        fB[j] = nf[2]; fB[j + hh] = nf[3];
-        accum_g(gn, nf[0], nf[1], nf[2], nf[3]);
+        const Fr a0 = fold1(fA[j], fA[j + h], r), a1 = fold1(fA[j + hh], fA[j + hh + h], r);
+        const Fr b0 = fold1(fB[j], fB[j + h], r), b1 = fold1(fB[j + hh], fB[j + hh + h], r);
+        fA[j] = a0; fA[j + hh] = a1;
+        fB[j] = b0; fB[j + hh] = b1;
+        accum_g(gn, a0, a1, b0, b1);
       }
       block_sum_canonical<3>(gn, gsh, red);
     } else if (tid == 0) {
