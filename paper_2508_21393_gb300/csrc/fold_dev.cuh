@@ -243,37 +243,79 @@ static __device__ void rowdot_i16(const FoldTask& T, const FoldTile& t, const Fr
 
 
 // ------------------------------------------------- int16, bulk pipeline ---
+//
+// NSTAGE shared-memory slots.  Slot q has a "full" mbarrier (one arrival with
+// the expected byte count; the bulk copies complete it) and an "empty"
+// mbarrier (one arrival per warp once the warp has read the slot).  Warp 0
+// also produces: before refilling a slot it waits until every warp has
+// released it, so warps drift apart by up to NSTAGE stages and no block-wide
+// barrier is needed per stage.  Every wait is bounded; the block votes once,
+// after its last stage, and drains on failure.
+
+static constexpr int FOLD_WARPS = FOLD_THREADS / 32;
 
 struct Pipe {
-  uint32_t bar0;    // shared address of mbarrier 0 (NSTAGE consecutive 8-byte barriers)
+  uint32_t full0;   // shared address of full barrier 0 (NSTAGE consecutive 8-byte barriers)
+  uint32_t empty0;  // shared address of empty barrier 0
   uint32_t stage0;  // shared address of stage 0
 };
 
-__device__ __forceinline__ uint32_t pipe_bar(const Pipe& p, int s) { return p.bar0 + 8u * (uint32_t)(s % NSTAGE); }
+__device__ __forceinline__ uint32_t pipe_full(const Pipe& p, int s) { return p.full0 + 8u * (uint32_t)(s % NSTAGE); }
+__device__ __forceinline__ uint32_t pipe_empty(const Pipe& p, int s) { return p.empty0 + 8u * (uint32_t)(s % NSTAGE); }
 __device__ __forceinline__ uint32_t pipe_slot(const Pipe& p, int s) {
   return p.stage0 + (uint32_t)(s % NSTAGE) * (uint32_t)STAGE_BYTES;
 }
+__device__ __forceinline__ uint32_t pipe_parity(int s) { return (uint32_t)(s / NSTAGE) & 1u; }
 
-// After the last stage (all threads past their final wait): invalidate the
-// stage barriers so that the shared memory can serve other purposes (the
-// persistent step reuses it for the next work item).
-__device__ __forceinline__ void pipe_release(const Pipe& p) {
-  if (threadIdx.x == 0)
-    for (int q = 0; q < NSTAGE; q++) mbar_inval(p.bar0 + 8u * q);
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Give up after a timed-out wait: mark the proof, then wait for this CTA's
-// copies still in flight (stages [from, to)) so that none lands in shared
-// memory after the CTA has exited.  This drain has its own fixed bound
-// (FOLD_WAIT_NS), independent of the caller's (possibly very short) limit.
-static __device__ void pipe_abort(const Pipe& p, int from, int to, int* status) {
+__device__ __forceinline__ Pipe pipe_init(uint8_t* smem, uint32_t stage_offset) {
+  Pipe p;
+  p.full0 = smem_addr(smem);
+  p.empty0 = p.full0 + 8u * NSTAGE;
+  p.stage0 = smem_addr(smem + stage_offset);
   if (threadIdx.x == 0) {
-    atomicExch(status, VL_ETIMEOUT);
-    const uint64_t deadline = global_ns() + FOLD_WAIT_NS;
-    for (int s = from; s < to; s++) mbar_wait_bounded(pipe_bar(p, s), (uint32_t)(s / NSTAGE) & 1u, deadline);
+    for (int q = 0; q < NSTAGE; q++) {
+      mbar_init(p.full0 + 8u * q, 1);
+      mbar_init(p.empty0 + 8u * q, FOLD_WARPS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  pipe_release(p);
+  return p;
+}
+
+// Producer (warp 0, all lanes): before filling the slot of stage s >= NSTAGE,
+// wait until every warp has released stage s - NSTAGE.
+__device__ __forceinline__ bool pipe_acquire_slot(const Pipe& p, int s, uint64_t wait_ns) {
+  if (s < NSTAGE) return true;
+  return mbar_wait_bounded(pipe_empty(p, s), pipe_parity(s - NSTAGE), global_ns() + wait_ns);
+}
+
+// Consumer warp: done reading stage s.
+__device__ __forceinline__ void pipe_release_slot(const Pipe& p, int s) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(pipe_empty(p, s));
+}
+
+// End of a tile: block-wide vote; on failure mark the proof and wait
+// (bounded by FOLD_WAIT_NS, independent of the caller's limit) for the last
+// copy issued into each slot, so none lands after the CTA moves on.  Then the
+// barriers are invalidated so that the shared memory can serve other
+// purposes (the persistent step reuses it for the next work item).
+__device__ __forceinline__ bool pipe_finish(const Pipe& p, bool ok, int issued, int* status) {
+  const bool all_ok = __syncthreads_and(ok);
+  if (!all_ok && threadIdx.x == 0) {
+    atomicExch(status, VL_ETIMEOUT);
+    const uint64_t deadline = global_ns() + FOLD_WAIT_NS;
+    for (int s = max(0, issued - NSTAGE); s < issued; s++) mbar_wait_bounded(pipe_full(p, s), pipe_parity(s), deadline);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 2 * NSTAGE; q++) mbar_inval(p.full0 + 8u * q);
+  return all_ok;
 }
 
 // Stage s of a COLSUM tile: stored rows [r0 + s*SR, ...) x columns [c0, c1).
@@ -282,7 +324,7 @@ __device__ __forceinline__ void colsum_issue(const Pipe& p, const FoldTask& T, c
   const int nrows = t.r1 - t.r0, ncols = t.c1 - t.c0;
   const int rb = s * SR, rc = min(SR, nrows - rb);
   const uint32_t row_bytes = (uint32_t)ncols * 2u;
-  const uint32_t bar = pipe_bar(p, s), slot = pipe_slot(p, s);
+  const uint32_t bar = pipe_full(p, s), slot = pipe_slot(p, s);
   const int16_t* src = static_cast<const int16_t*>(T.mat) + (int64_t)(t.r0 + rb) * T.ld + t.c0;
   if (lane == 0) {
     fence_proxy_async_smem();
@@ -296,24 +338,30 @@ __device__ __forceinline__ void colsum_issue(const Pipe& p, const FoldTask& T, c
   }
 }
 
-static __device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, const Fr* __restrict__ E, u64* __restrict__ acc,
-                                uint8_t* smem, int* status, uint64_t wait_ns) {
+__device__ __forceinline__ void unpack4(uint2 q2, uint32_t (&pv)[4]) {
+  q2.x ^= 0x80008000u;
+  q2.y ^= 0x80008000u;
+  pv[0] = q2.x & 0xffffu;
+  pv[1] = q2.x >> 16;
+  pv[2] = q2.y & 0xffffu;
+  pv[3] = q2.y >> 16;
+}
+
+static __device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, const Fr* __restrict__ E,
+                                       u64* __restrict__ acc, uint8_t* smem, int* status, uint64_t wait_ns) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const int nrows = t.r1 - t.r0, ncols = t.c1 - t.c0;
   const uint32_t row_bytes = (uint32_t)ncols * 2u;
   const int SR = min(nrows, max(1, STAGE_BYTES / (int)row_bytes));
   const int nst = (nrows + SR - 1) / SR;
   uint4* Es = reinterpret_cast<uint4*>(smem + FOLD_SMEM_HEAD);
-  Pipe p;
-  p.bar0 = smem_addr(smem);
-  p.stage0 = smem_addr(smem + FOLD_SMEM_HEAD + nrows * 32);
-  if (tid == 0) {
-    for (int q = 0; q < NSTAGE; q++) mbar_init(p.bar0 + 8u * q, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const Pipe p = pipe_init(smem, FOLD_SMEM_HEAD + nrows * 32);
+  int issued = 0;
+  bool ok = true;
+  if (warp == 0) {
+    issued = min(nst, NSTAGE - 1);
+    for (int s = 0; s < issued; s++) colsum_issue(p, T, t, s, SR);
   }
-  __syncthreads();
-  if (warp == 0)
-    for (int s = 0; s < min(nst, NSTAGE - 1); s++) colsum_issue(p, T, t, s, SR);
   // Weights of the tile's rows, broadcast later from shared memory.
   const uint4* Eg = reinterpret_cast<const uint4*>(E + t.r0);
   for (int i = tid; i < 2 * nrows; i += FOLD_THREADS) Es[i] = Eg[i];
@@ -333,30 +381,49 @@ static __device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, con
     for (int l = 0; l < 8; l++) a[q][l] = 0;
 
   for (int s = 0; s < nst; s++) {
-    if (warp == 0 && s + NSTAGE - 1 < nst) colsum_issue(p, T, t, s + NSTAGE - 1, SR);
-    const bool ok = mbar_wait_bounded(pipe_bar(p, s), (uint32_t)(s / NSTAGE) & 1u, global_ns() + wait_ns);
-    if (ok && active) {
+    if (ok && warp == 0 && s + NSTAGE - 1 < nst) {
+      const int sn = s + NSTAGE - 1;
+      if (pipe_acquire_slot(p, sn, wait_ns)) {
+        colsum_issue(p, T, t, sn, SR);
+        issued = sn + 1;
+      } else {
+        ok = false;
+      }
+    }
+    const bool got = ok && mbar_wait_bounded(pipe_full(p, s), pipe_parity(s), global_ns() + wait_ns);
+    ok = got;
+    if (got && active) {
       const int rb = s * SR, rc = min(SR, nrows - rb);
       const uint32_t slot = pipe_slot(p, s) + 8u * (uint32_t)grp;
-      for (int rr = lr; rr < rc; rr += RL) {
-        uint2 q2 = lds_u2(slot + (uint32_t)rr * row_bytes);
-        q2.x ^= 0x80008000u;
-        q2.y ^= 0x80008000u;
-        const uint32_t pv[4] = {q2.x & 0xffffu, q2.x >> 16, q2.y & 0xffffu, q2.y >> 16};
-        const uint4 e0 = Es[2 * (rb + rr)], e1 = Es[2 * (rb + rr) + 1];
-        const uint32_t e[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+      // Software-pipelined rows: the next row's weights and data are loaded
+      // while the current row is multiplied.
+      int rr = lr;
+      uint2 dn = make_uint2(0u, 0u);
+      uint4 e0n = make_uint4(0u, 0u, 0u, 0u), e1n = e0n;
+      if (rr < rc) {
+        dn = lds_u2(slot + (uint32_t)rr * row_bytes);
+        e0n = Es[2 * (rb + rr)];
+        e1n = Es[2 * (rb + rr) + 1];
+      }
+      for (; rr < rc; rr += RL) {
+        const uint2 d = dn;
+        const uint32_t e[8] = {e0n.x, e0n.y, e0n.z, e0n.w, e1n.x, e1n.y, e1n.z, e1n.w};
+        if (rr + RL < rc) {
+          dn = lds_u2(slot + (uint32_t)(rr + RL) * row_bytes);
+          e0n = Es[2 * (rb + rr + RL)];
+          e1n = Es[2 * (rb + rr + RL) + 1];
+        }
+        uint32_t pv[4];
+        unpack4(d, pv);
 #pragma unroll
         for (int q = 0; q < 4; q++)
 #pragma unroll
           for (int l = 0; l < 8; l++) a[q][l] += (u64)e[l] * pv[q];
       }
     }
-    if (!__syncthreads_and(ok)) {
-      pipe_abort(p, s, min(nst, s + NSTAGE), status);
-      return;
-    }
+    pipe_release_slot(p, s);
   }
-  pipe_release(p);
+  if (!pipe_finish(p, ok, warp == 0 ? issued : 0, status)) return;
   if (active) {
     const int c = t.c0 + 4 * grp;
 #pragma unroll
@@ -375,7 +442,7 @@ __device__ __forceinline__ void rowdot_issue(const Pipe& p, const FoldTask& T, c
   const int nrows = t.r1 - t.r0, ncols = t.c1 - t.c0;
   const int cb = s * ROWDOT_STAGE_COLS, cc = min(ROWDOT_STAGE_COLS, ncols - cb);
   const uint32_t bytes = (uint32_t)cc * 2u;
-  const uint32_t bar = pipe_bar(p, s), slot = pipe_slot(p, s);
+  const uint32_t bar = pipe_full(p, s), slot = pipe_slot(p, s);
   if (lane == 0) {
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(bar, (uint32_t)nrows * bytes);
@@ -387,23 +454,20 @@ __device__ __forceinline__ void rowdot_issue(const Pipe& p, const FoldTask& T, c
   }
 }
 
-static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, const Fr* __restrict__ E, u64* __restrict__ acc,
-                                uint8_t* smem, int* status, uint64_t wait_ns) {
+static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, const Fr* __restrict__ E,
+                                       u64* __restrict__ acc, uint8_t* smem, int* status, uint64_t wait_ns) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nrows = t.r1 - t.r0, ncols = t.c1 - t.c0;
   const int pitch = (ncols + 3) & ~3;
   const int nst = (ncols + ROWDOT_STAGE_COLS - 1) / ROWDOT_STAGE_COLS;
   uint32_t* Es = reinterpret_cast<uint32_t*>(smem + FOLD_SMEM_HEAD);
-  Pipe p;
-  p.bar0 = smem_addr(smem);
-  p.stage0 = smem_addr(smem + FOLD_SMEM_HEAD + pitch * 32);
-  if (tid == 0) {
-    for (int q = 0; q < NSTAGE; q++) mbar_init(p.bar0 + 8u * q, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const Pipe p = pipe_init(smem, FOLD_SMEM_HEAD + pitch * 32);
+  int issued = 0;
+  bool ok = true;
+  if (warp == 0) {
+    issued = min(nst, NSTAGE - 1);
+    for (int s = 0; s < issued; s++) rowdot_issue(p, T, t, s);
   }
-  __syncthreads();
-  if (warp == 0)
-    for (int s = 0; s < min(nst, NSTAGE - 1); s++) rowdot_issue(p, T, t, s);
   // Weights of the tile's columns, limb-major (conflict-free 16-byte reads).
   for (int j = tid; j < pitch; j += FOLD_THREADS) {
     Fr e = j < ncols ? E[t.c0 + j] : fr_zero();
@@ -418,9 +482,18 @@ static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, con
   for (int i = 0; i < 32; i++) a[i] = 0;
 
   for (int s = 0; s < nst; s++) {
-    if (warp == 0 && s + NSTAGE - 1 < nst) rowdot_issue(p, T, t, s + NSTAGE - 1);
-    const bool ok = mbar_wait_bounded(pipe_bar(p, s), (uint32_t)(s / NSTAGE) & 1u, global_ns() + wait_ns);
-    if (ok) {
+    if (ok && warp == 0 && s + NSTAGE - 1 < nst) {
+      const int sn = s + NSTAGE - 1;
+      if (pipe_acquire_slot(p, sn, wait_ns)) {
+        rowdot_issue(p, T, t, sn);
+        issued = sn + 1;
+      } else {
+        ok = false;
+      }
+    }
+    const bool got = ok && mbar_wait_bounded(pipe_full(p, s), pipe_parity(s), global_ns() + wait_ns);
+    ok = got;
+    if (got) {
       const int cb = s * ROWDOT_STAGE_COLS;
       const uint32_t slot = pipe_slot(p, s);
 #pragma unroll 1
@@ -440,10 +513,8 @@ static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, con
 #pragma unroll
           for (int rr = 0; rr < ROWDOT_ROWS_PER_WARP; rr++) {
             if (rb + rr < nrows) {
-              uint2 q2 = lds_u2(slot + (uint32_t)(rb + rr) * (ROWDOT_STAGE_COLS * 2u) + 2u * (uint32_t)jl);
-              q2.x ^= 0x80008000u;
-              q2.y ^= 0x80008000u;
-              const uint32_t pv[4] = {q2.x & 0xffffu, q2.x >> 16, q2.y & 0xffffu, q2.y >> 16};
+              uint32_t pv[4];
+              unpack4(lds_u2(slot + (uint32_t)(rb + rr) * (ROWDOT_STAGE_COLS * 2u) + 2u * (uint32_t)jl), pv);
 #pragma unroll
               for (int q = 0; q < 4; q++)
 #pragma unroll
@@ -453,12 +524,9 @@ static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, con
         }
       }
     }
-    if (!__syncthreads_and(ok)) {
-      pipe_abort(p, s, min(nst, s + NSTAGE), status);
-      return;
-    }
+    pipe_release_slot(p, s);
   }
-  pipe_release(p);
+  if (!pipe_finish(p, ok, warp == 0 ? issued : 0, status)) return;
   const u64 sum = warp_transpose_sum(a);
   const int r = t.r0 + rb + (lane >> 3);
   if (r < t.r1) red_add_u64(acc + (size_t)r * 8 + (lane & 7), sum);
