@@ -435,12 +435,15 @@ static __device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, con
   }
 }
 
-// Stage s of a ROWDOT tile: columns [c0 + s*SC, ...) of all tile rows, one
-// copy per row (lane rr of warp 0 copies row rr).
-__device__ __forceinline__ void rowdot_issue(const Pipe& p, const FoldTask& T, const FoldTile& t, int s) {
+// Stage s of a ROWDOT tile: row block s / SPB (32 rows), columns
+// [c0 + (s % SPB) * SC, ...) of that block, one copy per row (lane rr of
+// warp 0 copies row rr of the block).
+__device__ __forceinline__ void rowdot_issue(const Pipe& p, const FoldTask& T, const FoldTile& t, int s, int spb) {
   const int lane = threadIdx.x & 31;
-  const int nrows = t.r1 - t.r0, ncols = t.c1 - t.c0;
-  const int cb = s * ROWDOT_STAGE_COLS, cc = min(ROWDOT_STAGE_COLS, ncols - cb);
+  const int ncols = t.c1 - t.c0;
+  const int rb0 = t.r0 + (s / spb) * ROWDOT_BLOCK_ROWS;
+  const int nrows = min(ROWDOT_BLOCK_ROWS, t.r1 - rb0);
+  const int cb = (s % spb) * ROWDOT_STAGE_COLS, cc = min(ROWDOT_STAGE_COLS, ncols - cb);
   const uint32_t bytes = (uint32_t)cc * 2u;
   const uint32_t bar = pipe_full(p, s), slot = pipe_slot(p, s);
   if (lane == 0) {
@@ -449,7 +452,7 @@ __device__ __forceinline__ void rowdot_issue(const Pipe& p, const FoldTask& T, c
   }
   __syncwarp();
   if (lane < nrows) {
-    const int16_t* src = static_cast<const int16_t*>(T.mat) + (int64_t)(t.r0 + lane) * T.ld + t.c0 + cb;
+    const int16_t* src = static_cast<const int16_t*>(T.mat) + (int64_t)(rb0 + lane) * T.ld + t.c0 + cb;
     bulk_g2s(slot + (uint32_t)lane * (ROWDOT_STAGE_COLS * 2u), src, bytes, bar);
   }
 }
@@ -457,18 +460,21 @@ __device__ __forceinline__ void rowdot_issue(const Pipe& p, const FoldTask& T, c
 static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, const Fr* __restrict__ E,
                                        u64* __restrict__ acc, uint8_t* smem, int* status, uint64_t wait_ns) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nrows = t.r1 - t.r0, ncols = t.c1 - t.c0;
+  const int ncols = t.c1 - t.c0;
   const int pitch = (ncols + 3) & ~3;
-  const int nst = (ncols + ROWDOT_STAGE_COLS - 1) / ROWDOT_STAGE_COLS;
+  const int spb = (ncols + ROWDOT_STAGE_COLS - 1) / ROWDOT_STAGE_COLS;      // stages per row block
+  const int nblk = (t.r1 - t.r0 + ROWDOT_BLOCK_ROWS - 1) / ROWDOT_BLOCK_ROWS;
+  const int nst = spb * nblk;
   uint32_t* Es = reinterpret_cast<uint32_t*>(smem + FOLD_SMEM_HEAD);
   const Pipe p = pipe_init(smem, FOLD_SMEM_HEAD + pitch * 32);
   int issued = 0;
   bool ok = true;
   if (warp == 0) {
     issued = min(nst, NSTAGE - 1);
-    for (int s = 0; s < issued; s++) rowdot_issue(p, T, t, s);
+    for (int s = 0; s < issued; s++) rowdot_issue(p, T, t, s, spb);
   }
-  // Weights of the tile's columns, limb-major (conflict-free 16-byte reads).
+  // Weights of the tile's columns, limb-major (conflict-free 16-byte reads),
+  // shared by all row blocks of the tile.
   for (int j = tid; j < pitch; j += FOLD_THREADS) {
     Fr e = j < ncols ? E[t.c0 + j] : fr_zero();
 #pragma unroll
@@ -476,7 +482,7 @@ static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, con
   }
   __syncthreads();
 
-  const int rb = warp * ROWDOT_ROWS_PER_WARP;  // tile-local first row of this warp
+  const int wr = warp * ROWDOT_ROWS_PER_WARP;  // first row of this warp within a block
   u64 a[32];
 #pragma unroll
   for (int i = 0; i < 32; i++) a[i] = 0;
@@ -485,16 +491,19 @@ static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, con
     if (ok && warp == 0 && s + NSTAGE - 1 < nst) {
       const int sn = s + NSTAGE - 1;
       if (pipe_acquire_slot(p, sn, wait_ns)) {
-        rowdot_issue(p, T, t, sn);
+        rowdot_issue(p, T, t, sn, spb);
         issued = sn + 1;
       } else {
         ok = false;
       }
     }
+    const int blk = s / spb, chunk = s - blk * spb;
+    const int rb0 = t.r0 + blk * ROWDOT_BLOCK_ROWS;
+    const int nrows = min(ROWDOT_BLOCK_ROWS, t.r1 - rb0);
     const bool got = ok && mbar_wait_bounded(pipe_full(p, s), pipe_parity(s), global_ns() + wait_ns);
     ok = got;
     if (got) {
-      const int cb = s * ROWDOT_STAGE_COLS;
+      const int cb = chunk * ROWDOT_STAGE_COLS;
       const uint32_t slot = pipe_slot(p, s);
 #pragma unroll 1
       for (int half = 0; half < ROWDOT_STAGE_COLS / 128; half++) {
@@ -512,9 +521,9 @@ static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, con
           }
 #pragma unroll
           for (int rr = 0; rr < ROWDOT_ROWS_PER_WARP; rr++) {
-            if (rb + rr < nrows) {
+            if (wr + rr < nrows) {
               uint32_t pv[4];
-              unpack4(lds_u2(slot + (uint32_t)(rb + rr) * (ROWDOT_STAGE_COLS * 2u) + 2u * (uint32_t)jl), pv);
+              unpack4(lds_u2(slot + (uint32_t)(wr + rr) * (ROWDOT_STAGE_COLS * 2u) + 2u * (uint32_t)jl), pv);
 #pragma unroll
               for (int q = 0; q < 4; q++)
 #pragma unroll
@@ -525,11 +534,16 @@ static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, con
       }
     }
     pipe_release_slot(p, s);
+    if (chunk == spb - 1) {
+      // Row block done: lane L adds (row L / 8, limb L % 8) to the accumulators.
+      const u64 sum = warp_transpose_sum(a);
+      const int r = rb0 + wr + (lane >> 3);
+      if (got && r < rb0 + nrows) red_add_u64(acc + (size_t)r * 8 + (lane & 7), sum);
+#pragma unroll
+      for (int i = 0; i < 32; i++) a[i] = 0;
+    }
   }
-  if (!pipe_finish(p, ok, warp == 0 ? issued : 0, status)) return;
-  const u64 sum = warp_transpose_sum(a);
-  const int r = t.r0 + rb + (lane >> 3);
-  if (r < t.r1) red_add_u64(acc + (size_t)r * 8 + (lane & 7), sum);
+  pipe_finish(p, ok, warp == 0 ? issued : 0, status);
 }
 
 // ------------------------------------------------------------ Montgomery ---
@@ -616,13 +630,27 @@ __device__ __forceinline__ void fold_tile(const FoldTask& T, const FoldTile& t, 
     if (T.bulk) {
       if (T.mode == MODE_COLSUM) colsum_i16_bulk(T, t, E, acc, smem, &P.scr->status, wait_ns);
       else rowdot_i16_bulk(T, t, E, acc, smem, &P.scr->status, wait_ns);
+    } else if (T.mode == MODE_COLSUM) {
+      colsum_i16(T, t, E, acc, sm4);
     } else {
-      if (T.mode == MODE_COLSUM) colsum_i16(T, t, E, acc, sm4);
-      else rowdot_i16(T, t, E, acc, reinterpret_cast<uint32_t*>(sm4));
+      for (int r0 = t.r0; r0 < t.r1; r0 += ROWDOT_BLOCK_ROWS) {  // 32-row blocks
+        FoldTile b = t;
+        b.r0 = r0;
+        b.r1 = min(t.r1, r0 + ROWDOT_BLOCK_ROWS);
+        rowdot_i16(T, b, E, acc, reinterpret_cast<uint32_t*>(sm4));
+        __syncthreads();
+      }
     }
+  } else if (T.mode == MODE_COLSUM) {
+    colsum_fr(T, t, E, acc, sm4);
   } else {
-    if (T.mode == MODE_COLSUM) colsum_fr(T, t, E, acc, sm4);
-    else rowdot_fr(T, t, E, acc, reinterpret_cast<uint32_t*>(sm4));
+    for (int r0 = t.r0; r0 < t.r1; r0 += ROWDOT_BLOCK_ROWS) {
+      FoldTile b = t;
+      b.r0 = r0;
+      b.r1 = min(t.r1, r0 + ROWDOT_BLOCK_ROWS);
+      rowdot_fr(T, b, E, acc, reinterpret_cast<uint32_t*>(sm4));
+      __syncthreads();
+    }
   }
 }
 
