@@ -82,16 +82,21 @@ struct FoldTile {
 static constexpr int FOLD_THREADS = 256;
 static constexpr int COLSUM_VEC = 4;                              // int16 columns per thread
 static constexpr int COLSUM_TILE_COLS = FOLD_THREADS * COLSUM_VEC;  // 1024
+// Register-load and Montgomery row-dot paths: 4 rows per warp, 32-row blocks.
 static constexpr int ROWDOT_ROWS_PER_WARP = 4;
-static constexpr int ROWDOT_BLOCK_ROWS = (FOLD_THREADS / 32) * ROWDOT_ROWS_PER_WARP;  // 32 rows per block
-static constexpr int ROWDOT_TILE_ROWS = 4 * ROWDOT_BLOCK_ROWS;  // a tile = 4 blocks sharing its weights
+static constexpr int FB_BLOCK_ROWS = (FOLD_THREADS / 32) * ROWDOT_ROWS_PER_WARP;  // 32
+// Bulk row-dot path: 8 rows per warp, 64-row blocks; a tile is 2 blocks
+// sharing its staged weights.
+static constexpr int BULK_ROWS_PER_WARP = 8;
+static constexpr int ROWDOT_BLOCK_ROWS = (FOLD_THREADS / 32) * BULK_ROWS_PER_WARP;  // 64
+static constexpr int ROWDOT_TILE_ROWS = 2 * ROWDOT_BLOCK_ROWS;                      // 128
 static constexpr int ROWDOT_TILE_COLS = 1024;
 static constexpr int FR_COLSUM_TILE_COLS = FOLD_THREADS;          // Montgomery operands: 1 col/thread
 // Bulk-copy pipeline: NSTAGE shared-memory stages of STAGE_BYTES each; a
 // row-dot stage holds ROWDOT_STAGE_COLS columns of all 32 tile rows.
 static constexpr int NSTAGE = 4;
 static constexpr int STAGE_BYTES = 16384;
-static constexpr int ROWDOT_STAGE_COLS = STAGE_BYTES / (ROWDOT_BLOCK_ROWS * 2);  // 256
+static constexpr int ROWDOT_STAGE_COLS = STAGE_BYTES / (ROWDOT_BLOCK_ROWS * 2);  // 128
 static constexpr int FOLD_SMEM_HEAD = 128;  // mbarriers
 // Default bound on any single wait for a bulk copy (ns of %globaltimer).
 static constexpr unsigned long long FOLD_WAIT_NS = 2000000000ull;

@@ -92,6 +92,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   return true;
 }
 
+// The same with a budget of `wait_ns` from the first failed attempt: the
+// global timer is only read when the phase is not complete at once.
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, uint64_t wait_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  return mbar_wait_bounded(bar, parity, global_ns() + wait_ns);
+}
+
 // Global -> shared bulk copy of `bytes` (multiple of 16, both addresses 16-byte
 // aligned), completion counted on mbarrier `bar`.
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -104,6 +111,12 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 // async-proxy (bulk copy) writes into it.
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ uint4 lds_u4(uint32_t addr) {
+  uint4 r;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "r"(addr));
+  return r;
 }
 
 __device__ __forceinline__ uint2 lds_u2(uint32_t addr) {
@@ -291,7 +304,7 @@ __device__ __forceinline__ Pipe pipe_init(uint8_t* smem, uint32_t stage_offset) 
 // wait until every warp has released stage s - NSTAGE.
 __device__ __forceinline__ bool pipe_acquire_slot(const Pipe& p, int s, uint64_t wait_ns) {
   if (s < NSTAGE) return true;
-  return mbar_wait_bounded(pipe_empty(p, s), pipe_parity(s - NSTAGE), global_ns() + wait_ns);
+  return mbar_wait_for(pipe_empty(p, s), pipe_parity(s - NSTAGE), wait_ns);
 }
 
 // Consumer warp: done reading stage s.
@@ -338,15 +351,12 @@ __device__ __forceinline__ void colsum_issue(const Pipe& p, const FoldTask& T, c
   }
 }
 
-__device__ __forceinline__ void unpack4(uint2 q2, uint32_t (&pv)[4]) {
-  q2.x ^= 0x80008000u;
-  q2.y ^= 0x80008000u;
-  pv[0] = q2.x & 0xffffu;
-  pv[1] = q2.x >> 16;
-  pv[2] = q2.y & 0xffffu;
-  pv[3] = q2.y >> 16;
-}
-
+// Column sums, bulk path.  Thread layout: G groups of 8 columns (G a power of
+// two covering the tile) x 2 limb halves x 128 / G row lanes.  A thread keeps
+// 8 columns x 4 limbs of 64-bit sums; per row it reads its 4 weight limbs
+// (16 bytes) and its 8 int16 entries (16 bytes) from shared memory and does
+// 32 multiply-adds.  Splitting the limbs between two threads (rather than 4
+// columns x 8 limbs per thread) measured markedly faster on GB300.
 static __device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, const Fr* __restrict__ E,
                                        u64* __restrict__ acc, uint8_t* smem, int* status, uint64_t wait_ns) {
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -362,23 +372,23 @@ static __device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, con
     issued = min(nst, NSTAGE - 1);
     for (int s = 0; s < issued; s++) colsum_issue(p, T, t, s, SR);
   }
-  // Weights of the tile's rows, broadcast later from shared memory.
+  // Weights of the tile's rows (two 16-byte halves per row).
   const uint4* Eg = reinterpret_cast<const uint4*>(E + t.r0);
   for (int i = tid; i < 2 * nrows; i += FOLD_THREADS) Es[i] = Eg[i];
   __syncthreads();
 
-  const int ngroups = ncols >> 2;  // ncols is a multiple of 8 on this path
+  const int ngroups = ncols >> 3;  // ncols is a multiple of 8 on this path
   int G = 1;
   while (G < ngroups) G <<= 1;
-  const int RL = FOLD_THREADS / G;
-  const int grp = tid & (G - 1), lr = tid / G;
+  const int RL = (FOLD_THREADS / 2) / G;
+  const int h = tid & 1, grp = (tid >> 1) & (G - 1), lr = tid / (2 * G);
   const bool active = grp < ngroups;
 
-  u64 a[4][8];
+  u64 a[8][4];
 #pragma unroll
-  for (int q = 0; q < 4; q++)
+  for (int q = 0; q < 8; q++)
 #pragma unroll
-    for (int l = 0; l < 8; l++) a[q][l] = 0;
+    for (int l = 0; l < 4; l++) a[q][l] = 0;
 
   for (int s = 0; s < nst; s++) {
     if (ok && warp == 0 && s + NSTAGE - 1 < nst) {
@@ -390,54 +400,54 @@ static __device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, con
         ok = false;
       }
     }
-    const bool got = ok && mbar_wait_bounded(pipe_full(p, s), pipe_parity(s), global_ns() + wait_ns);
+    const bool got = ok && mbar_wait_for(pipe_full(p, s), pipe_parity(s), wait_ns);
     ok = got;
     if (got && active) {
       const int rb = s * SR, rc = min(SR, nrows - rb);
-      const uint32_t slot = pipe_slot(p, s) + 8u * (uint32_t)grp;
-      // Software-pipelined rows: the next row's weights and data are loaded
-      // while the current row is multiplied.
+      const uint32_t slot = pipe_slot(p, s) + 16u * (uint32_t)grp;
       int rr = lr;
-      uint2 dn = make_uint2(0u, 0u);
-      uint4 e0n = make_uint4(0u, 0u, 0u, 0u), e1n = e0n;
+      uint4 dn = make_uint4(0u, 0u, 0u, 0u), en = dn;
       if (rr < rc) {
-        dn = lds_u2(slot + (uint32_t)rr * row_bytes);
-        e0n = Es[2 * (rb + rr)];
-        e1n = Es[2 * (rb + rr) + 1];
+        dn = lds_u4(slot + (uint32_t)rr * row_bytes);
+        en = Es[2 * (rb + rr) + h];
       }
       for (; rr < rc; rr += RL) {
-        const uint2 d = dn;
-        const uint32_t e[8] = {e0n.x, e0n.y, e0n.z, e0n.w, e1n.x, e1n.y, e1n.z, e1n.w};
-        if (rr + RL < rc) {
-          dn = lds_u2(slot + (uint32_t)(rr + RL) * row_bytes);
-          e0n = Es[2 * (rb + rr + RL)];
-          e1n = Es[2 * (rb + rr + RL) + 1];
+        uint4 d = dn;
+        const uint4 ev = en;
+        if (rr + RL < rc) {  // the next row's data and weights, one row ahead
+          dn = lds_u4(slot + (uint32_t)(rr + RL) * row_bytes);
+          en = Es[2 * (rb + rr + RL) + h];
         }
-        uint32_t pv[4];
-        unpack4(d, pv);
+        d.x ^= 0x80008000u;
+        d.y ^= 0x80008000u;
+        d.z ^= 0x80008000u;
+        d.w ^= 0x80008000u;
+        const uint32_t pv[8] = {d.x & 0xffffu, d.x >> 16, d.y & 0xffffu, d.y >> 16,
+                                d.z & 0xffffu, d.z >> 16, d.w & 0xffffu, d.w >> 16};
+        const uint32_t e[4] = {ev.x, ev.y, ev.z, ev.w};
 #pragma unroll
-        for (int q = 0; q < 4; q++)
+        for (int q = 0; q < 8; q++)
 #pragma unroll
-          for (int l = 0; l < 8; l++) a[q][l] += (u64)e[l] * pv[q];
+          for (int l = 0; l < 4; l++) a[q][l] += (u64)e[l] * pv[q];
       }
     }
     pipe_release_slot(p, s);
   }
   if (!pipe_finish(p, ok, warp == 0 ? issued : 0, status)) return;
   if (active) {
-    const int c = t.c0 + 4 * grp;
+    const int c = t.c0 + 8 * grp;
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      u64* dst = acc + (size_t)(c + q) * 8;
+    for (int q = 0; q < 8; q++) {
+      u64* dst = acc + (size_t)(c + q) * 8 + 4 * h;
 #pragma unroll
-      for (int l = 0; l < 8; l++) red_add_u64(dst + l, a[q][l]);
+      for (int l = 0; l < 4; l++) red_add_u64(dst + l, a[q][l]);
     }
   }
 }
 
-// Stage s of a ROWDOT tile: row block s / SPB (32 rows), columns
-// [c0 + (s % SPB) * SC, ...) of that block, one copy per row (lane rr of
-// warp 0 copies row rr of the block).
+// Stage s of a ROWDOT tile: row block s / SPB (64 rows), columns
+// [c0 + (s % SPB) * SC, ...) of that block, one copy per row (lane L of
+// warp 0 copies rows L and L + 32 of the block).
 __device__ __forceinline__ void rowdot_issue(const Pipe& p, const FoldTask& T, const FoldTile& t, int s, int spb) {
   const int lane = threadIdx.x & 31;
   const int ncols = t.c1 - t.c0;
@@ -451,18 +461,25 @@ __device__ __forceinline__ void rowdot_issue(const Pipe& p, const FoldTask& T, c
     mbar_arrive_expect_tx(bar, (uint32_t)nrows * bytes);
   }
   __syncwarp();
-  if (lane < nrows) {
-    const int16_t* src = static_cast<const int16_t*>(T.mat) + (int64_t)(rb0 + lane) * T.ld + t.c0 + cb;
-    bulk_g2s(slot + (uint32_t)lane * (ROWDOT_STAGE_COLS * 2u), src, bytes, bar);
+  for (int r = lane; r < nrows; r += 32) {
+    const int16_t* src = static_cast<const int16_t*>(T.mat) + (int64_t)(rb0 + r) * T.ld + t.c0 + cb;
+    bulk_g2s(slot + (uint32_t)r * (ROWDOT_STAGE_COLS * 2u), src, bytes, bar);
   }
 }
 
+// Row dots, bulk path.  Lane L of a warp owns 8 consecutive columns of a
+// stage (L / 2) and one limb half (L % 2); the warp owns 8 rows of the 64-row
+// block.  Per stage a lane reads 8 columns x 4 limbs of weights (limb-major
+// in shared memory), then per row its 8 int16 entries, 32 multiply-adds.
+// At the end of a row block the 64-bit sums of the 16 lanes of each limb
+// half are added with a 4-level transpose-reduction (offsets 16, 8, 4, 2):
+// lane L ends with (row, limb) pairs v = (L & 30) | j, j < 2, v = row*4 + l.
 static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, const Fr* __restrict__ E,
                                        u64* __restrict__ acc, uint8_t* smem, int* status, uint64_t wait_ns) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ncols = t.c1 - t.c0;
   const int pitch = (ncols + 3) & ~3;
-  const int spb = (ncols + ROWDOT_STAGE_COLS - 1) / ROWDOT_STAGE_COLS;      // stages per row block
+  const int spb = (ncols + ROWDOT_STAGE_COLS - 1) / ROWDOT_STAGE_COLS;  // stages per row block
   const int nblk = (t.r1 - t.r0 + ROWDOT_BLOCK_ROWS - 1) / ROWDOT_BLOCK_ROWS;
   const int nst = spb * nblk;
   uint32_t* Es = reinterpret_cast<uint32_t*>(smem + FOLD_SMEM_HEAD);
@@ -473,8 +490,7 @@ static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, con
     issued = min(nst, NSTAGE - 1);
     for (int s = 0; s < issued; s++) rowdot_issue(p, T, t, s, spb);
   }
-  // Weights of the tile's columns, limb-major (conflict-free 16-byte reads),
-  // shared by all row blocks of the tile.
+  // Weights of the tile's columns, limb-major, shared by all row blocks.
   for (int j = tid; j < pitch; j += FOLD_THREADS) {
     Fr e = j < ncols ? E[t.c0 + j] : fr_zero();
 #pragma unroll
@@ -482,10 +498,13 @@ static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, con
   }
   __syncthreads();
 
-  const int wr = warp * ROWDOT_ROWS_PER_WARP;  // first row of this warp within a block
-  u64 a[32];
+  const int h = lane & 1, g = lane >> 1;
+  const int wr = warp * BULK_ROWS_PER_WARP;  // first row of this warp within a block
+  u64 a[BULK_ROWS_PER_WARP][4];
 #pragma unroll
-  for (int i = 0; i < 32; i++) a[i] = 0;
+  for (int r = 0; r < BULK_ROWS_PER_WARP; r++)
+#pragma unroll
+    for (int l = 0; l < 4; l++) a[r][l] = 0;
 
   for (int s = 0; s < nst; s++) {
     if (ok && warp == 0 && s + NSTAGE - 1 < nst) {
@@ -500,47 +519,65 @@ static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, con
     const int blk = s / spb, chunk = s - blk * spb;
     const int rb0 = t.r0 + blk * ROWDOT_BLOCK_ROWS;
     const int nrows = min(ROWDOT_BLOCK_ROWS, t.r1 - rb0);
-    const bool got = ok && mbar_wait_bounded(pipe_full(p, s), pipe_parity(s), global_ns() + wait_ns);
+    const bool got = ok && mbar_wait_for(pipe_full(p, s), pipe_parity(s), wait_ns);
     ok = got;
-    if (got) {
-      const int cb = chunk * ROWDOT_STAGE_COLS;
-      const uint32_t slot = pipe_slot(p, s);
-#pragma unroll 1
-      for (int half = 0; half < ROWDOT_STAGE_COLS / 128; half++) {
-        const int jl = half * 128 + 4 * lane;  // stage-local column
-        const int j = cb + jl;                 // tile-local column
-        if (j < ncols) {
-          uint32_t e[4][8];
+    const int j = chunk * ROWDOT_STAGE_COLS + 8 * g;  // tile-local first column of this lane
+    if (got && j < ncols) {
+      uint32_t e[8][4];
 #pragma unroll
-          for (int l = 0; l < 8; l++) {
-            const uint4 q = *reinterpret_cast<const uint4*>(Es + l * pitch + j);
-            e[0][l] = q.x;
-            e[1][l] = q.y;
-            e[2][l] = q.z;
-            e[3][l] = q.w;
-          }
+      for (int l = 0; l < 4; l++) {
+        const uint4 q0 = *reinterpret_cast<const uint4*>(Es + (4 * h + l) * pitch + j);
+        const uint4 q1 = *reinterpret_cast<const uint4*>(Es + (4 * h + l) * pitch + j + 4);
+        e[0][l] = q0.x; e[1][l] = q0.y; e[2][l] = q0.z; e[3][l] = q0.w;
+        e[4][l] = q1.x; e[5][l] = q1.y; e[6][l] = q1.z; e[7][l] = q1.w;
+      }
+      const uint32_t slot = pipe_slot(p, s) + 16u * (uint32_t)g;
 #pragma unroll
-          for (int rr = 0; rr < ROWDOT_ROWS_PER_WARP; rr++) {
-            if (wr + rr < nrows) {
-              uint32_t pv[4];
-              unpack4(lds_u2(slot + (uint32_t)(wr + rr) * (ROWDOT_STAGE_COLS * 2u) + 2u * (uint32_t)jl), pv);
+      for (int rr = 0; rr < BULK_ROWS_PER_WARP; rr++) {
+        if (wr + rr < nrows) {
+          uint4 d = lds_u4(slot + (uint32_t)(wr + rr) * (ROWDOT_STAGE_COLS * 2u));
+          d.x ^= 0x80008000u;
+          d.y ^= 0x80008000u;
+          d.z ^= 0x80008000u;
+          d.w ^= 0x80008000u;
+          const uint32_t pv[8] = {d.x & 0xffffu, d.x >> 16, d.y & 0xffffu, d.y >> 16,
+                                  d.z & 0xffffu, d.z >> 16, d.w & 0xffffu, d.w >> 16};
 #pragma unroll
-              for (int q = 0; q < 4; q++)
+          for (int q = 0; q < 8; q++)
 #pragma unroll
-                for (int l = 0; l < 8; l++) a[rr * 8 + l] += (u64)e[q][l] * pv[q];
-            }
-          }
+            for (int l = 0; l < 4; l++) a[rr][l] += (u64)e[q][l] * pv[q];
         }
       }
     }
     pipe_release_slot(p, s);
     if (chunk == spb - 1) {
-      // Row block done: lane L adds (row L / 8, limb L % 8) to the accumulators.
-      const u64 sum = warp_transpose_sum(a);
-      const int r = rb0 + wr + (lane >> 3);
-      if (got && r < rb0 + nrows) red_add_u64(acc + (size_t)r * 8 + (lane & 7), sum);
+      // Row block done: reduce over the 16 lanes of each limb half.
+      u64 v[32];
 #pragma unroll
-      for (int i = 0; i < 32; i++) a[i] = 0;
+      for (int i = 0; i < 32; i++) v[i] = a[i >> 2][i & 3];
+#pragma unroll
+      for (int off = 16; off >= 2; off >>= 1) {
+        const bool upper = (lane & off) != 0;
+        const int half = off;  // values still held: 2 * off
+#pragma unroll
+        for (int i = 0; i < half; i++) {
+          const u64 send = upper ? v[i] : v[i + half];
+          const u64 keep = upper ? v[i + half] : v[i];
+          v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+      }
+      if (got) {
+#pragma unroll
+        for (int jj = 0; jj < 2; jj++) {
+          const int vi = (lane & 30) | jj;
+          const int row = rb0 + wr + (vi >> 2);
+          if (row < rb0 + nrows) red_add_u64(acc + (size_t)row * 8 + 4 * h + (vi & 3), v[jj]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < BULK_ROWS_PER_WARP; r++)
+#pragma unroll
+        for (int l = 0; l < 4; l++) a[r][l] = 0;
     }
   }
   pipe_finish(p, ok, warp == 0 ? issued : 0, status);
@@ -633,10 +670,10 @@ __device__ __forceinline__ void fold_tile(const FoldTask& T, const FoldTile& t, 
     } else if (T.mode == MODE_COLSUM) {
       colsum_i16(T, t, E, acc, sm4);
     } else {
-      for (int r0 = t.r0; r0 < t.r1; r0 += ROWDOT_BLOCK_ROWS) {  // 32-row blocks
+      for (int r0 = t.r0; r0 < t.r1; r0 += FB_BLOCK_ROWS) {  // 32-row blocks
         FoldTile b = t;
         b.r0 = r0;
-        b.r1 = min(t.r1, r0 + ROWDOT_BLOCK_ROWS);
+        b.r1 = min(t.r1, r0 + FB_BLOCK_ROWS);
         rowdot_i16(T, b, E, acc, reinterpret_cast<uint32_t*>(sm4));
         __syncthreads();
       }
@@ -644,10 +681,10 @@ __device__ __forceinline__ void fold_tile(const FoldTask& T, const FoldTile& t, 
   } else if (T.mode == MODE_COLSUM) {
     colsum_fr(T, t, E, acc, sm4);
   } else {
-    for (int r0 = t.r0; r0 < t.r1; r0 += ROWDOT_BLOCK_ROWS) {
+    for (int r0 = t.r0; r0 < t.r1; r0 += FB_BLOCK_ROWS) {
       FoldTile b = t;
       b.r0 = r0;
-      b.r1 = min(t.r1, r0 + ROWDOT_BLOCK_ROWS);
+      b.r1 = min(t.r1, r0 + FB_BLOCK_ROWS);
       rowdot_fr(T, b, E, acc, reinterpret_cast<uint32_t*>(sm4));
       __syncthreads();
     }
