@@ -67,8 +67,11 @@ struct FoldTask {
   int32_t rows, cols;
   int32_t mode, dtype;
   int32_t proof, side;  // side 0: weights E_u, output accA; side 1: E_v, accB
-  int32_t bulk;         // 1: int16 tiles staged by bulk async copies (alignment checked on the host)
+  int32_t bulk;         // 1: int16 tiles staged by TMA tensor copies (alignment checked on the host)
+  int32_t box_w;        // TMA box: columns (a multiple of 8)
+  int32_t box_h;        //          rows
   int32_t pad;
+  const void* tmap;     // TMA tensor map of the stored matrix (device, 64-byte aligned)
 };
 
 struct FoldTile {
@@ -104,7 +107,7 @@ static constexpr unsigned long long FOLD_WAIT_NS = 2000000000ull;
 // Dynamic shared memory a fold tile needs (bytes).
 inline int fold_tile_smem(int mode, int dtype, int tile_rows, int tile_cols) {
   if (mode == MODE_COLSUM) {
-    const int e = tile_rows * 32;
+    const int e = (tile_rows * 32 + 127) & ~127;
     return FOLD_SMEM_HEAD + e + (dtype == VL_I16 ? NSTAGE * STAGE_BYTES : 0);
   }
   const int pitch = (tile_cols + 3) & ~3;

@@ -7,6 +7,8 @@
 // (transcripts, challenges, eq tables), the fold kernel over all tiles of all
 // jobs, and the rounds kernel (claims, sumcheck rounds, proofs).  A plan can
 // capture that pass in a CUDA graph and replay it.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -82,6 +84,8 @@ struct vl_plan {
   std::vector<FoldTask> tasks;
   std::vector<FoldTile> tiles;
   std::vector<StepItem> items;  // persistent step: queue order
+  std::vector<CUtensorMap> tmaps;  // one per fold task (TMA operands), built at bind time
+  size_t off_tmaps = 0;
   int fold_smem = 0;
   int step_smem = 0;
   int step_grid = 0;            // CTAs of the persistent launch (set at bind time)
@@ -126,6 +130,16 @@ void add_fold_task(vl_plan* p, const vl_mat& M, int32_t mode, int proof, int sid
   t.dtype = M.dtype;
   t.proof = proof;
   t.side = side;
+  // TMA box of the stored matrix (used when the operand qualifies at bind time).
+  auto round8 = [](int64_t x) { return (int)((x + 7) & ~int64_t(7)); };
+  if (mode == MODE_COLSUM) {
+    t.box_w = std::min(256, round8(std::min<int64_t>(M.cols, COLSUM_TILE_COLS)));
+    const int nsub = (int)((std::min<int64_t>(M.cols, COLSUM_TILE_COLS) + t.box_w - 1) / t.box_w);
+    t.box_h = std::max(1, std::min(256, STAGE_BYTES / (nsub * t.box_w * 2)));
+  } else {
+    t.box_w = std::min(ROWDOT_STAGE_COLS, round8(std::min<int64_t>(M.cols, ROWDOT_TILE_COLS)));
+    t.box_h = ROWDOT_BLOCK_ROWS;
+  }
   const int task = (int)p->tasks.size();
   p->tasks.push_back(t);
   const size_t tiles_before = p->tiles.size();
@@ -223,6 +237,8 @@ int build_plan(vl_plan* p) {
   off = align_up(off + sizeof(FoldTask) * p->tasks.size());
   p->off_tiles = off;
   off = align_up(off + sizeof(FoldTile) * p->tiles.size());
+  p->off_tmaps = off;
+  off = align_up(off + sizeof(CUtensorMap) * p->tasks.size());
   p->off_items = off;
   off = align_up(off + sizeof(StepItem) * p->items.size());
   // step control block and accumulators: one contiguous region, zeroed each pass
@@ -308,6 +324,38 @@ int cuda_status(cudaError_t e, const char* where = "cuda") {
   return VL_ECUDA;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+// TMA descriptor of an int16 task's stored matrix; false if the operand does
+// not qualify (16-byte aligned base, rows a multiple of 16 bytes apart,
+// a multiple of 8 columns) or encoding fails.
+bool encode_task_map(const FoldTask& t, CUtensorMap* map) {
+  if (t.dtype != VL_I16 || (reinterpret_cast<uintptr_t>(t.mat) & 15) || (t.ld & 7) || (t.cols & 7)) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)t.cols, (cuuint64_t)t.rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)t.ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)t.box_w, (cuuint32_t)t.box_h};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(t.mat), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Fill device pointers for this workspace and upload the descriptor tables.
 int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
   const int np = (int)p->jobs.size();
@@ -321,13 +369,14 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
     P.fB = reinterpret_cast<Fr*>(ws + p->pp[i].fB);
     P.scr = reinterpret_cast<ProofScratch*>(ws + p->off_scr) + i;
   }
-  for (FoldTask& t : p->tasks) {
+  p->tmaps.resize(p->tasks.size());
+  for (size_t i = 0; i < p->tasks.size(); i++) {
+    FoldTask& t = p->tasks[i];
     const vl_job& j = p->jobs[t.proof];
     t.mat = operand_ptr(p, t.side ? j.Q : j.P, ws);
-    // Bulk copies need 16-byte aligned row starts and row lengths: aligned
-    // base, ld and cols multiples of 8 int16 (tile edges are multiples of 8).
-    t.bulk = t.dtype == VL_I16 && (reinterpret_cast<uintptr_t>(t.mat) & 15) == 0 && (t.ld & 7) == 0 &&
-             (t.cols & 7) == 0;
+    std::memset(&p->tmaps[i], 0, sizeof(CUtensorMap));
+    t.bulk = encode_task_map(t, &p->tmaps[i]) ? 1 : 0;
+    t.tmap = ws + p->off_tmaps + i * sizeof(CUtensorMap);
   }
   cudaError_t e = cudaMemcpyAsync(ws + p->off_proofs, p->proofs.data(), sizeof(DevProof) * np,
                                   cudaMemcpyHostToDevice, st);
@@ -336,6 +385,9 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
                         cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !p->tiles.empty())
     e = cudaMemcpyAsync(ws + p->off_tiles, p->tiles.data(), sizeof(FoldTile) * p->tiles.size(),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !p->tmaps.empty())
+    e = cudaMemcpyAsync(ws + p->off_tmaps, p->tmaps.data(), sizeof(CUtensorMap) * p->tmaps.size(),
                         cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !p->items.empty())
     e = cudaMemcpyAsync(ws + p->off_items, p->items.data(), sizeof(StepItem) * p->items.size(),

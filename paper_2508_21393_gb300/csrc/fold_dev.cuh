@@ -107,6 +107,16 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
+// 2D TMA load of one box of the tensor map at (x = column, y = row) into
+// shared memory, completion counted on mbarrier `bar`.  x must be a multiple
+// of 8 (16 bytes of int16); out-of-range rows and columns read as zero.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
 // Order earlier generic-proxy accesses to shared memory before later
 // async-proxy (bulk copy) writes into it.
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -331,27 +341,20 @@ __device__ __forceinline__ bool pipe_finish(const Pipe& p, bool ok, int issued, 
   return all_ok;
 }
 
-// Stage s of a COLSUM tile: stored rows [r0 + s*SR, ...) x columns [c0, c1).
-__device__ __forceinline__ void colsum_issue(const Pipe& p, const FoldTask& T, const FoldTile& t, int s, int SR) {
-  const int lane = threadIdx.x & 31;
-  const int nrows = t.r1 - t.r0, ncols = t.c1 - t.c0;
-  const int rb = s * SR, rc = min(SR, nrows - rb);
-  const uint32_t row_bytes = (uint32_t)ncols * 2u;
+// Stage s of a COLSUM tile: stored rows [r0 + s*BH, ...) of the tile's
+// columns, as ceil(ncols / BW) boxes of BH x BW side by side in the slot.
+__device__ __forceinline__ void colsum_issue(const Pipe& p, const FoldTask& T, const FoldTile& t, int s) {
+  if ((threadIdx.x & 31) != 0) return;
+  const int ncols = t.c1 - t.c0, bw = T.box_w, bh = T.box_h;
+  const int nsub = (ncols + bw - 1) / bw;
+  const uint32_t box_bytes = (uint32_t)bw * (uint32_t)bh * 2u;
   const uint32_t bar = pipe_full(p, s), slot = pipe_slot(p, s);
-  const int16_t* src = static_cast<const int16_t*>(T.mat) + (int64_t)(t.r0 + rb) * T.ld + t.c0;
-  if (lane == 0) {
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(bar, (uint32_t)rc * row_bytes);
-  }
-  __syncwarp();
-  if (T.ld == ncols) {  // whole rows, contiguous: one copy
-    if (lane == 0) bulk_g2s(slot, src, (uint32_t)rc * row_bytes, bar);
-  } else {
-    for (int rr = lane; rr < rc; rr += 32) bulk_g2s(slot + (uint32_t)rr * row_bytes, src + (int64_t)rr * T.ld, row_bytes, bar);
-  }
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(bar, (uint32_t)nsub * box_bytes);
+  for (int q = 0; q < nsub; q++) tma_load_2d(slot + (uint32_t)q * box_bytes, T.tmap, t.c0 + q * bw, t.r0 + s * bh, bar);
 }
 
-// Column sums, bulk path.  Thread layout: G groups of 8 columns (G a power of
+// Column sums, TMA path.  Thread layout: G groups of 8 columns (G a power of
 // two covering the tile) x 2 limb halves x 128 / G row lanes.  A thread keeps
 // 8 columns x 4 limbs of 64-bit sums; per row it reads its 4 weight limbs
 // (16 bytes) and its 8 int16 entries (16 bytes) from shared memory and does
@@ -361,16 +364,16 @@ static __device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, con
                                        u64* __restrict__ acc, uint8_t* smem, int* status, uint64_t wait_ns) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const int nrows = t.r1 - t.r0, ncols = t.c1 - t.c0;
-  const uint32_t row_bytes = (uint32_t)ncols * 2u;
-  const int SR = min(nrows, max(1, STAGE_BYTES / (int)row_bytes));
+  const int bw = T.box_w, SR = T.box_h;
+  const uint32_t box_bytes = (uint32_t)bw * (uint32_t)SR * 2u;
   const int nst = (nrows + SR - 1) / SR;
   uint4* Es = reinterpret_cast<uint4*>(smem + FOLD_SMEM_HEAD);
-  const Pipe p = pipe_init(smem, FOLD_SMEM_HEAD + nrows * 32);
+  const Pipe p = pipe_init(smem, FOLD_SMEM_HEAD + ((nrows * 32 + 127) & ~127));  // TMA wants 128-byte aligned stages
   int issued = 0;
   bool ok = true;
   if (warp == 0) {
     issued = min(nst, NSTAGE - 1);
-    for (int s = 0; s < issued; s++) colsum_issue(p, T, t, s, SR);
+    for (int s = 0; s < issued; s++) colsum_issue(p, T, t, s);
   }
   // Weights of the tile's rows (two 16-byte halves per row).
   const uint4* Eg = reinterpret_cast<const uint4*>(E + t.r0);
@@ -394,7 +397,7 @@ static __device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, con
     if (ok && warp == 0 && s + NSTAGE - 1 < nst) {
       const int sn = s + NSTAGE - 1;
       if (pipe_acquire_slot(p, sn, wait_ns)) {
-        colsum_issue(p, T, t, sn, SR);
+        colsum_issue(p, T, t, sn);
         issued = sn + 1;
       } else {
         ok = false;
@@ -404,7 +407,10 @@ static __device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, con
     ok = got;
     if (got && active) {
       const int rb = s * SR, rc = min(SR, nrows - rb);
-      const uint32_t slot = pipe_slot(p, s) + 16u * (uint32_t)grp;
+      // this thread's 8 columns: box q = 8 grp / bw, column 8 grp - q bw within it
+      const int q0 = (8 * grp) / bw;
+      const uint32_t row_bytes = (uint32_t)bw * 2u;
+      const uint32_t slot = pipe_slot(p, s) + (uint32_t)q0 * box_bytes + 2u * (uint32_t)(8 * grp - q0 * bw);
       int rr = lr;
       uint4 dn = make_uint4(0u, 0u, 0u, 0u), en = dn;
       if (rr < rc) {
@@ -445,29 +451,18 @@ static __device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, con
   }
 }
 
-// Stage s of a ROWDOT tile: row block s / SPB (64 rows), columns
-// [c0 + (s % SPB) * SC, ...) of that block, one copy per row (lane L of
-// warp 0 copies rows L and L + 32 of the block).
+// Stage s of a ROWDOT tile: row block s / SPB (64 rows) x columns
+// [c0 + (s % SPB) * BW, ...): one box of 64 x BW.
 __device__ __forceinline__ void rowdot_issue(const Pipe& p, const FoldTask& T, const FoldTile& t, int s, int spb) {
-  const int lane = threadIdx.x & 31;
-  const int ncols = t.c1 - t.c0;
-  const int rb0 = t.r0 + (s / spb) * ROWDOT_BLOCK_ROWS;
-  const int nrows = min(ROWDOT_BLOCK_ROWS, t.r1 - rb0);
-  const int cb = (s % spb) * ROWDOT_STAGE_COLS, cc = min(ROWDOT_STAGE_COLS, ncols - cb);
-  const uint32_t bytes = (uint32_t)cc * 2u;
+  if ((threadIdx.x & 31) != 0) return;
+  const int bw = T.box_w;
   const uint32_t bar = pipe_full(p, s), slot = pipe_slot(p, s);
-  if (lane == 0) {
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(bar, (uint32_t)nrows * bytes);
-  }
-  __syncwarp();
-  for (int r = lane; r < nrows; r += 32) {
-    const int16_t* src = static_cast<const int16_t*>(T.mat) + (int64_t)(rb0 + r) * T.ld + t.c0 + cb;
-    bulk_g2s(slot + (uint32_t)r * (ROWDOT_STAGE_COLS * 2u), src, bytes, bar);
-  }
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(bar, (uint32_t)ROWDOT_BLOCK_ROWS * (uint32_t)bw * 2u);
+  tma_load_2d(slot, T.tmap, t.c0 + (s % spb) * bw, t.r0 + (s / spb) * ROWDOT_BLOCK_ROWS, bar);
 }
 
-// Row dots, bulk path.  Lane L of a warp owns 8 consecutive columns of a
+// Row dots, TMA path.  Lane L of a warp owns 8 consecutive columns of a
 // stage (L / 2) and one limb half (L % 2); the warp owns 8 rows of the 64-row
 // block.  Per stage a lane reads 8 columns x 4 limbs of weights (limb-major
 // in shared memory), then per row its 8 int16 entries, 32 multiply-adds.
@@ -479,7 +474,8 @@ static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, con
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ncols = t.c1 - t.c0;
   const int pitch = (ncols + 3) & ~3;
-  const int spb = (ncols + ROWDOT_STAGE_COLS - 1) / ROWDOT_STAGE_COLS;  // stages per row block
+  const int bw = T.box_w;                 // columns per stage
+  const int spb = (ncols + bw - 1) / bw;  // stages per row block
   const int nblk = (t.r1 - t.r0 + ROWDOT_BLOCK_ROWS - 1) / ROWDOT_BLOCK_ROWS;
   const int nst = spb * nblk;
   uint32_t* Es = reinterpret_cast<uint32_t*>(smem + FOLD_SMEM_HEAD);
@@ -521,8 +517,8 @@ static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, con
     const int nrows = min(ROWDOT_BLOCK_ROWS, t.r1 - rb0);
     const bool got = ok && mbar_wait_for(pipe_full(p, s), pipe_parity(s), wait_ns);
     ok = got;
-    const int j = chunk * ROWDOT_STAGE_COLS + 8 * g;  // tile-local first column of this lane
-    if (got && j < ncols) {
+    const int j = chunk * bw + 8 * g;  // tile-local first column of this lane
+    if (got && 8 * g < bw && j < ncols) {
       uint32_t e[8][4];
 #pragma unroll
       for (int l = 0; l < 4; l++) {
@@ -535,7 +531,7 @@ static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, con
 #pragma unroll
       for (int rr = 0; rr < BULK_ROWS_PER_WARP; rr++) {
         if (wr + rr < nrows) {
-          uint4 d = lds_u4(slot + (uint32_t)(wr + rr) * (ROWDOT_STAGE_COLS * 2u));
+          uint4 d = lds_u4(slot + (uint32_t)(wr + rr) * (uint32_t)bw * 2u);
           d.x ^= 0x80008000u;
           d.y ^= 0x80008000u;
           d.z ^= 0x80008000u;
