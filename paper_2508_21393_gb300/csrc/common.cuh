@@ -36,6 +36,9 @@ struct DevProof {
   uint8_t binds[96];
   Fr* eqA;                 // m entries, E_u in double-Montgomery form (x.R^2)
   Fr* eqB;                 // n entries, E_v
+  uint32_t* eqA_soa;       // the same tables limb-major: [8][pitch] words (row-dot
+  uint32_t* eqB_soa;       //   weights are fetched as [8 x box] tensor boxes)
+  int32_t soa_pitchA, soa_pitchB;  // words per limb row, multiples of 4
   unsigned long long* accA;  // k x 8 column sums (f_A numerators)
   unsigned long long* accB;  // k x 8
   Fr* fA;                  // 2^d1 working vector for the rounds (Montgomery)
@@ -72,6 +75,7 @@ struct FoldTask {
   int32_t box_h;        //          rows
   int32_t pad;
   const void* tmap;     // TMA tensor map of the stored matrix (device, 64-byte aligned)
+  const void* etmap;    // TMA tensor map of the limb-major weights (row dots)
 };
 
 struct FoldTile {
@@ -95,23 +99,25 @@ static constexpr int ROWDOT_BLOCK_ROWS = (FOLD_THREADS / 32) * BULK_ROWS_PER_WAR
 static constexpr int ROWDOT_TILE_ROWS = 2 * ROWDOT_BLOCK_ROWS;                      // 128
 static constexpr int ROWDOT_TILE_COLS = 1024;
 static constexpr int FR_COLSUM_TILE_COLS = FOLD_THREADS;          // Montgomery operands: 1 col/thread
-// Bulk-copy pipeline: NSTAGE shared-memory stages of STAGE_BYTES each; a
-// row-dot stage holds ROWDOT_STAGE_COLS columns of all 32 tile rows.
+// TMA pipeline: NSTAGE shared-memory slots of SLOT_BYTES; a slot holds up to
+// STAGE_BYTES of operand entries followed by the weights those entries need
+// (column sums: the stage's rows, 32 bytes each; row dots: 8 limb rows of the
+// stage's columns).
 static constexpr int NSTAGE = 4;
 static constexpr int STAGE_BYTES = 16384;
+static constexpr int SLOT_BYTES = 24576;
 static constexpr int ROWDOT_STAGE_COLS = STAGE_BYTES / (ROWDOT_BLOCK_ROWS * 2);  // 128
 static constexpr int FOLD_SMEM_HEAD = 128;  // mbarriers
 // Default bound on any single wait for a bulk copy (ns of %globaltimer).
 static constexpr unsigned long long FOLD_WAIT_NS = 2000000000ull;
 
-// Dynamic shared memory a fold tile needs (bytes).
+// Dynamic shared memory a fold tile needs (bytes): the TMA pipeline for
+// int16 operands, or the staged weights of the register-load and Montgomery
+// paths, whichever is larger.
 inline int fold_tile_smem(int mode, int dtype, int tile_rows, int tile_cols) {
-  if (mode == MODE_COLSUM) {
-    const int e = (tile_rows * 32 + 127) & ~127;
-    return FOLD_SMEM_HEAD + e + (dtype == VL_I16 ? NSTAGE * STAGE_BYTES : 0);
-  }
-  const int pitch = (tile_cols + 3) & ~3;
-  return FOLD_SMEM_HEAD + pitch * 32 + (dtype == VL_I16 ? NSTAGE * STAGE_BYTES : 0);
+  const int staged = mode == MODE_COLSUM ? tile_rows * 32 : ((tile_cols + 3) & ~3) * 32;
+  const int pipe = dtype == VL_I16 ? NSTAGE * SLOT_BYTES : 0;
+  return FOLD_SMEM_HEAD + (staged > pipe ? staged : pipe);
 }
 
 cudaError_t launch_prologue(const DevProof* proofs, int nproofs, cudaStream_t st);

@@ -84,8 +84,9 @@ struct vl_plan {
   std::vector<FoldTask> tasks;
   std::vector<FoldTile> tiles;
   std::vector<StepItem> items;  // persistent step: queue order
-  std::vector<CUtensorMap> tmaps;  // one per fold task (TMA operands), built at bind time
-  size_t off_tmaps = 0;
+  std::vector<CUtensorMap> tmaps;   // one per fold task (TMA operands), built at bind time
+  std::vector<CUtensorMap> etmaps;  // limb-major weights of each row-dot task
+  size_t off_tmaps = 0, off_etmaps = 0;
   int fold_smem = 0;
   int step_smem = 0;
   int step_grid = 0;            // CTAs of the persistent launch (set at bind time)
@@ -94,7 +95,7 @@ struct vl_plan {
   size_t off_proofs = 0, off_scr = 0, off_tasks = 0, off_tiles = 0;
   size_t off_acc = 0, acc_bytes = 0, off_out = 0, total = 0;
   struct PerProof {
-    size_t eqA, eqB, accA, accB, fA, fB;
+    size_t eqA, eqB, soaA, soaB, accA, accB, fA, fB;
   };
   std::vector<PerProof> pp;
   std::map<const void*, Staged> staging;  // host operand -> device copy
@@ -239,6 +240,8 @@ int build_plan(vl_plan* p) {
   off = align_up(off + sizeof(FoldTile) * p->tiles.size());
   p->off_tmaps = off;
   off = align_up(off + sizeof(CUtensorMap) * p->tasks.size());
+  p->off_etmaps = off;
+  off = align_up(off + sizeof(CUtensorMap) * p->tasks.size());
   p->off_items = off;
   off = align_up(off + sizeof(StepItem) * p->items.size());
   // step control block and accumulators: one contiguous region, zeroed each pass
@@ -260,6 +263,12 @@ int build_plan(vl_plan* p) {
     off = align_up(off + sizeof(Fr) * P.m);
     p->pp[i].eqB = off;
     off = align_up(off + sizeof(Fr) * P.n);
+    p->proofs[i].soa_pitchA = (P.m + 3) & ~3;
+    p->proofs[i].soa_pitchB = (P.n + 3) & ~3;
+    p->pp[i].soaA = off;
+    off = align_up(off + 32 * (size_t)p->proofs[i].soa_pitchA);
+    p->pp[i].soaB = off;
+    off = align_up(off + 32 * (size_t)p->proofs[i].soa_pitchB);
     p->pp[i].fA = off;
     off = align_up(off + sizeof(Fr) * ((size_t)1 << P.d1));
     p->pp[i].fB = off;
@@ -356,6 +365,20 @@ bool encode_task_map(const FoldTask& t, CUtensorMap* map) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// TMA descriptor of the limb-major weights a row-dot task reads: 8 rows of
+// `pitch` words, boxes of [8 x BW].
+bool encode_weight_map(const FoldTask& t, const uint32_t* soa, int pitch, CUtensorMap* map) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)t.cols, 8};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)t.box_w, 8};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(soa), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Fill device pointers for this workspace and upload the descriptor tables.
 int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
   const int np = (int)p->jobs.size();
@@ -363,6 +386,8 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
     DevProof& P = p->proofs[i];
     P.eqA = reinterpret_cast<Fr*>(ws + p->pp[i].eqA);
     P.eqB = reinterpret_cast<Fr*>(ws + p->pp[i].eqB);
+    P.eqA_soa = reinterpret_cast<uint32_t*>(ws + p->pp[i].soaA);
+    P.eqB_soa = reinterpret_cast<uint32_t*>(ws + p->pp[i].soaB);
     P.accA = reinterpret_cast<unsigned long long*>(ws + p->pp[i].accA);
     P.accB = reinterpret_cast<unsigned long long*>(ws + p->pp[i].accB);
     P.fA = reinterpret_cast<Fr*>(ws + p->pp[i].fA);
@@ -370,13 +395,21 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
     P.scr = reinterpret_cast<ProofScratch*>(ws + p->off_scr) + i;
   }
   p->tmaps.resize(p->tasks.size());
+  p->etmaps.resize(p->tasks.size());
   for (size_t i = 0; i < p->tasks.size(); i++) {
     FoldTask& t = p->tasks[i];
     const vl_job& j = p->jobs[t.proof];
+    const DevProof& P = p->proofs[t.proof];
     t.mat = operand_ptr(p, t.side ? j.Q : j.P, ws);
     std::memset(&p->tmaps[i], 0, sizeof(CUtensorMap));
-    t.bulk = encode_task_map(t, &p->tmaps[i]) ? 1 : 0;
+    std::memset(&p->etmaps[i], 0, sizeof(CUtensorMap));
+    bool ok = encode_task_map(t, &p->tmaps[i]);
+    if (ok && t.mode == MODE_ROWDOT)
+      ok = encode_weight_map(t, t.side ? P.eqB_soa : P.eqA_soa, t.side ? P.soa_pitchB : P.soa_pitchA,
+                             &p->etmaps[i]);
+    t.bulk = ok ? 1 : 0;
     t.tmap = ws + p->off_tmaps + i * sizeof(CUtensorMap);
+    t.etmap = ws + p->off_etmaps + i * sizeof(CUtensorMap);
   }
   cudaError_t e = cudaMemcpyAsync(ws + p->off_proofs, p->proofs.data(), sizeof(DevProof) * np,
                                   cudaMemcpyHostToDevice, st);
@@ -388,6 +421,9 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
                         cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !p->tmaps.empty())
     e = cudaMemcpyAsync(ws + p->off_tmaps, p->tmaps.data(), sizeof(CUtensorMap) * p->tmaps.size(),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !p->etmaps.empty())
+    e = cudaMemcpyAsync(ws + p->off_etmaps, p->etmaps.data(), sizeof(CUtensorMap) * p->etmaps.size(),
                         cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !p->items.empty())
     e = cudaMemcpyAsync(ws + p->off_items, p->items.data(), sizeof(StepItem) * p->items.size(),

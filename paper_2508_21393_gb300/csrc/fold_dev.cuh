@@ -286,7 +286,7 @@ struct Pipe {
 __device__ __forceinline__ uint32_t pipe_full(const Pipe& p, int s) { return p.full0 + 8u * (uint32_t)(s % NSTAGE); }
 __device__ __forceinline__ uint32_t pipe_empty(const Pipe& p, int s) { return p.empty0 + 8u * (uint32_t)(s % NSTAGE); }
 __device__ __forceinline__ uint32_t pipe_slot(const Pipe& p, int s) {
-  return p.stage0 + (uint32_t)(s % NSTAGE) * (uint32_t)STAGE_BYTES;
+  return p.stage0 + (uint32_t)(s % NSTAGE) * (uint32_t)SLOT_BYTES;
 }
 __device__ __forceinline__ uint32_t pipe_parity(int s) { return (uint32_t)(s / NSTAGE) & 1u; }
 
@@ -342,16 +342,19 @@ __device__ __forceinline__ bool pipe_finish(const Pipe& p, bool ok, int issued, 
 }
 
 // Stage s of a COLSUM tile: stored rows [r0 + s*BH, ...) of the tile's
-// columns, as ceil(ncols / BW) boxes of BH x BW side by side in the slot.
-__device__ __forceinline__ void colsum_issue(const Pipe& p, const FoldTask& T, const FoldTile& t, int s) {
+// columns, as ceil(ncols / BW) boxes of BH x BW side by side in the slot,
+// then the weights of the stage's rows (32 bytes each, one bulk copy).
+__device__ __forceinline__ void colsum_issue(const Pipe& p, const FoldTask& T, const FoldTile& t, const Fr* E, int s) {
   if ((threadIdx.x & 31) != 0) return;
   const int ncols = t.c1 - t.c0, bw = T.box_w, bh = T.box_h;
   const int nsub = (ncols + bw - 1) / bw;
+  const int erows = min(bh, t.r1 - t.r0 - s * bh);
   const uint32_t box_bytes = (uint32_t)bw * (uint32_t)bh * 2u;
   const uint32_t bar = pipe_full(p, s), slot = pipe_slot(p, s);
   fence_proxy_async_smem();
-  mbar_arrive_expect_tx(bar, (uint32_t)nsub * box_bytes);
+  mbar_arrive_expect_tx(bar, (uint32_t)nsub * box_bytes + 32u * (uint32_t)erows);
   for (int q = 0; q < nsub; q++) tma_load_2d(slot + (uint32_t)q * box_bytes, T.tmap, t.c0 + q * bw, t.r0 + s * bh, bar);
+  bulk_g2s(slot + (uint32_t)nsub * box_bytes, E + t.r0 + s * bh, 32u * (uint32_t)erows, bar);
 }
 
 // Column sums, TMA path.  Thread layout: G groups of 8 columns (G a power of
@@ -366,19 +369,16 @@ static __device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, con
   const int nrows = t.r1 - t.r0, ncols = t.c1 - t.c0;
   const int bw = T.box_w, SR = T.box_h;
   const uint32_t box_bytes = (uint32_t)bw * (uint32_t)SR * 2u;
+  const int nsub = (ncols + bw - 1) / bw;
+  const uint32_t e_off = (uint32_t)nsub * box_bytes;  // weights follow the boxes in a slot
   const int nst = (nrows + SR - 1) / SR;
-  uint4* Es = reinterpret_cast<uint4*>(smem + FOLD_SMEM_HEAD);
-  const Pipe p = pipe_init(smem, FOLD_SMEM_HEAD + ((nrows * 32 + 127) & ~127));  // TMA wants 128-byte aligned stages
+  const Pipe p = pipe_init(smem, FOLD_SMEM_HEAD);
   int issued = 0;
   bool ok = true;
   if (warp == 0) {
     issued = min(nst, NSTAGE - 1);
-    for (int s = 0; s < issued; s++) colsum_issue(p, T, t, s);
+    for (int s = 0; s < issued; s++) colsum_issue(p, T, t, E, s);
   }
-  // Weights of the tile's rows (two 16-byte halves per row).
-  const uint4* Eg = reinterpret_cast<const uint4*>(E + t.r0);
-  for (int i = tid; i < 2 * nrows; i += FOLD_THREADS) Es[i] = Eg[i];
-  __syncthreads();
 
   const int ngroups = ncols >> 3;  // ncols is a multiple of 8 on this path
   int G = 1;
@@ -397,7 +397,7 @@ static __device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, con
     if (ok && warp == 0 && s + NSTAGE - 1 < nst) {
       const int sn = s + NSTAGE - 1;
       if (pipe_acquire_slot(p, sn, wait_ns)) {
-        colsum_issue(p, T, t, sn);
+        colsum_issue(p, T, t, E, sn);
         issued = sn + 1;
       } else {
         ok = false;
@@ -410,19 +410,24 @@ static __device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, con
       // this thread's 8 columns: box q = 8 grp / bw, column 8 grp - q bw within it
       const int q0 = (8 * grp) / bw;
       const uint32_t row_bytes = (uint32_t)bw * 2u;
-      const uint32_t slot = pipe_slot(p, s) + (uint32_t)q0 * box_bytes + 2u * (uint32_t)(8 * grp - q0 * bw);
+      const uint32_t dstep = (uint32_t)RL * row_bytes, estep = 32u * (uint32_t)RL;
+      uint32_t da = pipe_slot(p, s) + (uint32_t)q0 * box_bytes + 2u * (uint32_t)(8 * grp - q0 * bw) +
+                    (uint32_t)lr * row_bytes;
+      uint32_t ea = pipe_slot(p, s) + e_off + 32u * (uint32_t)lr + 16u * (uint32_t)h;
       int rr = lr;
       uint4 dn = make_uint4(0u, 0u, 0u, 0u), en = dn;
       if (rr < rc) {
-        dn = lds_u4(slot + (uint32_t)rr * row_bytes);
-        en = Es[2 * (rb + rr) + h];
+        dn = lds_u4(da);
+        en = lds_u4(ea);
       }
       for (; rr < rc; rr += RL) {
         uint4 d = dn;
         const uint4 ev = en;
+        da += dstep;
+        ea += estep;
         if (rr + RL < rc) {  // the next row's data and weights, one row ahead
-          dn = lds_u4(slot + (uint32_t)(rr + RL) * row_bytes);
-          en = Es[2 * (rb + rr + RL) + h];
+          dn = lds_u4(da);
+          en = lds_u4(ea);
         }
         d.x ^= 0x80008000u;
         d.y ^= 0x80008000u;
@@ -452,14 +457,18 @@ static __device__ void colsum_i16_bulk(const FoldTask& T, const FoldTile& t, con
 }
 
 // Stage s of a ROWDOT tile: row block s / SPB (64 rows) x columns
-// [c0 + (s % SPB) * BW, ...): one box of 64 x BW.
+// [c0 + (s % SPB) * BW, ...): one box of 64 x BW entries, then a box of the
+// weights of those columns, 8 limb rows x BW words.
 __device__ __forceinline__ void rowdot_issue(const Pipe& p, const FoldTask& T, const FoldTile& t, int s, int spb) {
   if ((threadIdx.x & 31) != 0) return;
   const int bw = T.box_w;
+  const int x = t.c0 + (s % spb) * bw;
   const uint32_t bar = pipe_full(p, s), slot = pipe_slot(p, s);
+  const uint32_t data_bytes = (uint32_t)ROWDOT_BLOCK_ROWS * (uint32_t)bw * 2u;
   fence_proxy_async_smem();
-  mbar_arrive_expect_tx(bar, (uint32_t)ROWDOT_BLOCK_ROWS * (uint32_t)bw * 2u);
-  tma_load_2d(slot, T.tmap, t.c0 + (s % spb) * bw, t.r0 + (s / spb) * ROWDOT_BLOCK_ROWS, bar);
+  mbar_arrive_expect_tx(bar, data_bytes + 8u * (uint32_t)bw * 4u);
+  tma_load_2d(slot, T.tmap, x, t.r0 + (s / spb) * ROWDOT_BLOCK_ROWS, bar);
+  tma_load_2d(slot + data_bytes, T.etmap, x, 0, bar);  // [8 limbs x BW] of the weights
 }
 
 // Row dots, TMA path.  Lane L of a warp owns 8 consecutive columns of a
@@ -473,26 +482,18 @@ static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, con
                                        u64* __restrict__ acc, uint8_t* smem, int* status, uint64_t wait_ns) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ncols = t.c1 - t.c0;
-  const int pitch = (ncols + 3) & ~3;
   const int bw = T.box_w;                 // columns per stage
   const int spb = (ncols + bw - 1) / bw;  // stages per row block
   const int nblk = (t.r1 - t.r0 + ROWDOT_BLOCK_ROWS - 1) / ROWDOT_BLOCK_ROWS;
   const int nst = spb * nblk;
-  uint32_t* Es = reinterpret_cast<uint32_t*>(smem + FOLD_SMEM_HEAD);
-  const Pipe p = pipe_init(smem, FOLD_SMEM_HEAD + pitch * 32);
+  const uint32_t e_off = (uint32_t)ROWDOT_BLOCK_ROWS * (uint32_t)bw * 2u;  // weights follow the entries
+  const Pipe p = pipe_init(smem, FOLD_SMEM_HEAD);
   int issued = 0;
   bool ok = true;
   if (warp == 0) {
     issued = min(nst, NSTAGE - 1);
     for (int s = 0; s < issued; s++) rowdot_issue(p, T, t, s, spb);
   }
-  // Weights of the tile's columns, limb-major, shared by all row blocks.
-  for (int j = tid; j < pitch; j += FOLD_THREADS) {
-    Fr e = j < ncols ? E[t.c0 + j] : fr_zero();
-#pragma unroll
-    for (int l = 0; l < 8; l++) Es[l * pitch + j] = e.v[l];
-  }
-  __syncthreads();
 
   const int h = lane & 1, g = lane >> 1;
   const int wr = warp * BULK_ROWS_PER_WARP;  // first row of this warp within a block
@@ -520,10 +521,11 @@ static __device__ void rowdot_i16_bulk(const FoldTask& T, const FoldTile& t, con
     const int j = chunk * bw + 8 * g;  // tile-local first column of this lane
     if (got && 8 * g < bw && j < ncols) {
       uint32_t e[8][4];
+      const uint32_t eb = pipe_slot(p, s) + e_off + 32u * (uint32_t)g;
 #pragma unroll
       for (int l = 0; l < 4; l++) {
-        const uint4 q0 = *reinterpret_cast<const uint4*>(Es + (4 * h + l) * pitch + j);
-        const uint4 q1 = *reinterpret_cast<const uint4*>(Es + (4 * h + l) * pitch + j + 4);
+        const uint4 q0 = lds_u4(eb + (uint32_t)(4 * h + l) * (uint32_t)bw * 4u);
+        const uint4 q1 = lds_u4(eb + (uint32_t)(4 * h + l) * (uint32_t)bw * 4u + 16u);
         e[0][l] = q0.x; e[1][l] = q0.y; e[2][l] = q0.z; e[3][l] = q0.w;
         e[4][l] = q1.x; e[5][l] = q1.y; e[6][l] = q1.z; e[7][l] = q1.w;
       }

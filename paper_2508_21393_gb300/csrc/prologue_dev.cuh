@@ -23,7 +23,8 @@ namespace vl {
 static constexpr int MAX_VARS = 16;      // log2 of VL_MAX_REDUCE
 static constexpr int MAX_HALF = 1 << 8;  // 2^(MAX_VARS / 2)
 
-__device__ static Fr build_eq(const Fr* x, int d, int size, Fr* out, Fr* lo, Fr* hi, Fr* red) {
+__device__ static Fr build_eq(const Fr* x, int d, int size, Fr* out, uint32_t* out_soa, int pitch, Fr* lo, Fr* hi,
+                              Fr* red) {
   const int tid = threadIdx.x;
   const int s = (d + 1) >> 1;          // low-block variables
   const int dh = d - s;                // high-block variables
@@ -52,6 +53,8 @@ __device__ static Fr build_eq(const Fr* x, int d, int size, Fr* out, Fr* lo, Fr*
   for (int i = tid; i < size; i += blockDim.x) {
     Fr e = mont_mul_ni(hi[i >> s], lo[i & (nlo - 1)]);
     out[i] = e;
+#pragma unroll
+    for (int l = 0; l < 8; l++) out_soa[l * pitch + i] = e.v[l];
     sum[0] = fr_add(sum[0], e);
   }
   block_sum_fr<1>(sum, red);
@@ -114,9 +117,9 @@ static __device__ void prologue_block(const DevProof& P, uint8_t* smem) {
   squeeze_dev(S1, LBL_V, P.d2, v, S2, dig);
   if (tid < 32) P.scr->state[tid] = (uint8_t)(S2[tid >> 2] >> (24 - 8 * (tid & 3)));
 
-  Fr ca = build_eq(u, P.d0, P.m, P.eqA, lo, hi, red);
+  Fr ca = build_eq(u, P.d0, P.m, P.eqA, P.eqA_soa, P.soa_pitchA, lo, hi, red);
   __syncthreads();
-  Fr cb = build_eq(v, P.d2, P.n, P.eqB, lo, hi, red);
+  Fr cb = build_eq(v, P.d2, P.n, P.eqB, P.eqB_soa, P.soa_pitchB, lo, hi, red);
   if (tid == 0) {
     P.scr->corrA = P.dtypeA == VL_I16 ? ca : fr_zero();
     P.scr->corrB = P.dtypeB == VL_I16 ? cb : fr_zero();
