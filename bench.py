@@ -62,8 +62,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-projections", type=int, default=2)
-    ap.add_argument("--phases", action="store_true",
-                    help="three launches per step (prologue, fold, rounds) instead of one persistent launch")
+    ap.add_argument("--persistent", action="store_true",
+                    help="one persistent launch per step (CUDA-core fold) instead of phase launches")
+    ap.add_argument("--fold-engine", type=int, default=0, choices=[0, 1],
+                    help="phase launches: 0 tensor-core fold where TMA can address the operand, 1 CUDA cores only")
+    ap.add_argument("--groups", type=int, default=0,
+                    help="phase launches: proof groups pipelined over three streams (0: library default)")
     ap.add_argument("--rounds-variant", type=int, default=0, choices=[0, 4, 7],
                     help="rounds kernel register budget (CTAs per SM); 0 = library default")
     ap.add_argument("--layers", type=int, default=0,
@@ -190,7 +194,9 @@ def main():
     opts = B.vl_batch_opts()
     opts.timing_runs = max(args.steps, 1)
     opts.rounds_variant = args.rounds_variant
-    opts.persistent = 2 if args.phases else 0
+    opts.persistent = 1 if args.persistent else 2
+    opts.fold_engine = args.fold_engine
+    opts.groups = args.groups
     plan = B.vl_plan_create(djobs, opts)
     nws = B.vl_plan_workspace_bytes(plan)
     ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
@@ -227,21 +233,35 @@ def main():
     fold_ms = statistics.mean(p[1] for p in phases)
     pro_ms = statistics.mean(p[0] for p in phases)
     rnd_ms = statistics.mean(p[2] for p in phases)
-    if args.phases:
-        kernel, phase_ms = "fold_kernel", {"clear+prologue": pro_ms, "fold": fold_ms, "rounds": rnd_ms}
-    else:
-        # One persistent launch does prologues, folds and rounds; its time is
-        # the dominant kernel's, and only the fold's multiply-adds are counted.
-        kernel, phase_ms = "step_kernel (persistent)", {"clear": pro_ms, "step_kernel": fold_ms}
-    madw = 8 * entries  # eight 32x32->64 multiply-adds per int16 entry
-    peak = SMS * MADWIDE_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = madw / (fold_ms / 1e3) / 1e12
-    hbm_gbs = 2 * entries / (fold_ms / 1e3) / 1e9
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
+    hbm_peak, hbm_note = (peaks["hbm_gbs"], "measured") if "hbm_gbs" in peaks else (6800.0, "fallback")
+    hbm_gbs = 2 * entries / (fold_ms / 1e3) / 1e9  # each int16 operand entry read once
+    if args.persistent or args.fold_engine == 1:
+        # CUDA-core fold: bound by 32x32->64 multiply-adds (eight per entry).
+        if args.persistent:
+            kernel, phase_ms = "step_kernel (persistent)", {"clear": pro_ms, "step_kernel": fold_ms}
+        else:
+            kernel, phase_ms = "fold_kernel", {"clear+prologue": pro_ms, "fold": fold_ms, "rounds": rnd_ms}
+        peak = SMS * MADWIDE_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+        achieved = 8 * entries / (fold_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "Tmadwide/s",
+                "frac": achieved / peak, "traffic": None, "hbm_gbs_algorithmic": hbm_gbs,
+                "peak_note": "152 SMs x 32 IMAD.WIDE/clk x 2070 MHz (derived)"}
+    else:
+        # Tensor-core fold: streams every operand entry once from HBM.
+        kernel, phase_ms = "fold_tc_kernel", {"clear+prologue": pro_ms, "fold": fold_ms, "rounds": rnd_ms}
+        # 64 fp16 MACs per entry (two bytes x 32 weight bytes) plus the init
+        # MMA of each 64-entry stage (2048 MACs per 128 x 64 entries)
+        tflops = 2 * (64 + 0.25) * entries / (fold_ms / 1e3) / 1e12
+        roof = {"bound": "hbm", "kernel": kernel, "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": hbm_gbs / hbm_peak, "traffic": None,
+                "peak_note": f"{hbm_note} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": 2 * entries,
+                "tensor_tflops_fp16": tflops}
 
     # Unbatched per-matmul path: each product proved by its own plan (graph),
     # one after another on the same stream.
@@ -317,13 +337,10 @@ def main():
                    "input_bytes_per_step": in_bytes, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas{world}" if world > 1 else "single GPU",
                    "batched_ms_per_step": ms_max, "unbatched_ms_per_step": unbatched_ms,
-                   "launch_mode": "three phase launches" if args.phases else "one persistent launch",
+                   "launch_mode": "one persistent launch" if args.persistent else "phase launches (CUDA graph)",
+                   "fold_engine": "CUDA cores" if (args.persistent or args.fold_engine == 1) else "tensor cores",
                    "phase_ms": phase_ms},
-        "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
-                     "unit": "Tmadwide/s", "frac": achieved / peak, "traffic": None,
-                     "hbm_gbs_algorithmic": hbm_gbs,
-                     "hbm_frac_of_measured": hbm_gbs / peaks["hbm_gbs"] if "hbm_gbs" in peaks else None,
-                     "peak_note": "152 SMs x 32 IMAD.WIDE/clk x 2070 MHz (derived)"},
+        "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,

@@ -114,7 +114,14 @@ typedef struct vl_job {
 typedef struct vl_batch_opts {
   int32_t colsum_rows;   /* stored rows per column-sum fold tile              */
   int32_t rowdot_cols;   /* stored columns per row-dot fold tile              */
-  int32_t persistent;    /* 1: one persistent launch; 2: phase launches       */
+  int32_t persistent;    /* 1: one persistent launch (CUDA-core fold);
+                            0 or 2: phase launches (prologue, fold, rounds)  */
+  int32_t groups;        /* phase launches: proof groups pipelined across
+                            three streams (0: 1, no overlap)                 */
+  int32_t fold_engine;   /* phase launches: 0 tensor cores for every int16
+                            operand that TMA can address (16-byte aligned
+                            base, rows and columns multiples of 8 entries),
+                            CUDA cores for the rest; 1 CUDA cores only      */
   int32_t use_graph;     /* 1: capture vl_plan_run in a CUDA graph; 2: never   */
   int32_t timing_runs;   /* runs kept by vl_plan_phase_ms (0: 64)             */
   int32_t wait_limit_us; /* bound on any single device-side wait, in us (0: 2 s);
@@ -122,7 +129,7 @@ typedef struct vl_batch_opts {
                             VL_ETIMEOUT and its CTA returns                  */
   int32_t rounds_variant; /* rounds kernel register budget: 7 or 4 CTAs per SM
                             (0: 7)                                           */
-  int32_t test_never_ready; /* fault injection for tests: 1 + index of a proof
+  int32_t test_never_ready; /* fault injection for tests: 1 + index of a job
                             whose prologue never signals ready, so that its
                             fold tiles exhaust their bounded wait and report
                             VL_ETIMEOUT (persistent mode); 0: off            */

@@ -62,7 +62,8 @@ class vl_job(ctypes.Structure):
 
 class vl_batch_opts(ctypes.Structure):
     _fields_ = [("colsum_rows", ctypes.c_int32), ("rowdot_cols", ctypes.c_int32),
-                ("persistent", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("persistent", ctypes.c_int32), ("groups", ctypes.c_int32), ("fold_engine", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32),
                 ("timing_runs", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
                 ("rounds_variant", ctypes.c_int32), ("test_never_ready", ctypes.c_int32)]
 

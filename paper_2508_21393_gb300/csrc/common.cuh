@@ -45,8 +45,19 @@ struct DevProof {
   Fr* fB;
   ProofScratch* scr;
   int32_t ntiles;          // fold tiles of this proof (both tasks)
-  int32_t pad2[3];
+  int32_t job;             // index of the proof in the caller's job list (output slot)
+  int32_t tabA, tabB;      // weight tables each side needs: TAB_LIMBS and/or TAB_BYTES
+  uint32_t* w8A;           // tensor-core weights: E_u bytes as fp16, [m / 64 chunks] x 4 KB
+  uint32_t* w8B;           // E_v bytes
 };
+
+// Weight tables of one side of a proof.
+//   TAB_LIMBS: E in Montgomery limbs, entry-major (eqA) and limb-major (soa)
+//   TAB_BYTES: the 32 bytes of each E entry as fp16 values, in the shared-
+//              memory operand layout of the tensor-core fold (per 64-entry
+//              chunk: [8 entry groups][4 byte groups][8 entries][8 bytes]),
+//              zero past the last entry up to the chunk boundary
+enum : int32_t { TAB_LIMBS = 1, TAB_BYTES = 2 };
 
 // Persistent step: work items in queue order.
 enum : int32_t { STEP_PROLOGUE = 0, STEP_FOLD = 1 };
@@ -77,6 +88,23 @@ struct FoldTask {
   const void* tmap;     // TMA tensor map of the stored matrix (device, 64-byte aligned)
   const void* etmap;    // TMA tensor map of the limb-major weights (row dots)
 };
+
+// Tensor-core fold tile: stored lines [w0, w0 + nw) (columns for COLSUM,
+// rows for ROWDOT; nw <= 128), reduced over [k0, k0 + nk) (k0 a multiple of
+// 64, nk <= TC_SEG).
+struct TcTile {
+  int32_t task;
+  int32_t w0, nw;
+  int32_t k0, nk;
+  int32_t pad[3];
+};
+static constexpr int TC_M = 128;        // lines per tile (MMA M)
+static constexpr int TC_KS = 64;        // reduction entries per pipeline stage
+static constexpr int TC_SEG = 16384;    // reduction entries per tile at most
+static constexpr int TC_THREADS = 320;  // producer warp, MMA warp, 8 worker warps
+static constexpr int TC_NR = 4;         // raw (TMA) stages
+static constexpr int TC_NC = 2;         // converted-operand stages
+static constexpr int TC_SMEM = 1024 + TC_NC * 32768 + TC_NR * 20480 + 4096 + 1024 + 512;
 
 struct FoldTile {
   int32_t task;
@@ -125,6 +153,11 @@ cudaError_t launch_prologue(const DevProof* proofs, int nproofs, cudaStream_t st
 cudaError_t fold_set_smem(int smem_bytes);
 cudaError_t launch_fold(const FoldTask* tasks, const FoldTile* tiles, int ntiles,
                         const DevProof* proofs, int smem_bytes, unsigned long long wait_ns, cudaStream_t st);
+// Tensor-core fold of int16 operands (fold_tc.cuh); `counter` is a zeroed
+// int the CTAs take tiles from.
+cudaError_t fold_tc_prepare();
+cudaError_t launch_fold_tc(const TcTile* tiles, int ntiles, const FoldTask* tasks, const DevProof* proofs,
+                           int* counter, unsigned long long wait_ns, cudaStream_t st);
 cudaError_t step_set_smem(int smem_bytes);
 cudaError_t step_grid(int smem_bytes, int* grid);
 cudaError_t launch_step(const StepItem* items, int nitems, const FoldTask* tasks, const FoldTile* tiles,

@@ -83,7 +83,19 @@ struct vl_plan {
   std::vector<DevProof> proofs;
   std::vector<FoldTask> tasks;
   std::vector<FoldTile> tiles;
+  std::vector<TcTile> tc_tiles;  // tensor-core fold (phase launches)
   std::vector<StepItem> items;  // persistent step: queue order
+  // Phase launches: proofs in groups (k descending); the graph folds group g
+  // while group g+1's prologue and group g-1's rounds run on other streams.
+  struct Group {
+    int p0, p1;  // proofs [p0, p1)
+    int t0, t1;  // CUDA-core fold tiles [t0, t1)
+    int c0, c1;  // tensor-core fold tiles [c0, c1)
+  };
+  std::vector<Group> groups;
+  std::vector<int> slot_of_job;  // DevProof index of each job
+  cudaStream_t side[2] = {nullptr, nullptr};  // rounds stream, prologue stream
+  std::vector<cudaEvent_t> gev;               // dependency events (no timing)
   std::vector<CUtensorMap> tmaps;   // one per fold task (TMA operands), built at bind time
   std::vector<CUtensorMap> etmaps;  // limb-major weights of each row-dot task
   size_t off_tmaps = 0, off_etmaps = 0;
@@ -92,10 +104,10 @@ struct vl_plan {
   int step_grid = 0;            // CTAs of the persistent launch (set at bind time)
   size_t off_ctl = 0, off_items = 0;
   // workspace layout (offsets from the workspace base)
-  size_t off_proofs = 0, off_scr = 0, off_tasks = 0, off_tiles = 0;
+  size_t off_proofs = 0, off_scr = 0, off_tasks = 0, off_tiles = 0, off_tc_tiles = 0;
   size_t off_acc = 0, acc_bytes = 0, off_out = 0, total = 0;
   struct PerProof {
-    size_t eqA, eqB, soaA, soaB, accA, accB, fA, fB;
+    size_t eqA, eqB, soaA, soaB, w8A, w8B, accA, accB, fA, fB;
   };
   std::vector<PerProof> pp;
   std::map<const void*, Staged> staging;  // host operand -> device copy
@@ -118,8 +130,16 @@ struct vl_plan {
 
 namespace {
 
-// Persistent single launch unless the options ask for phase launches.
-bool persistent(const vl_plan* p) { return p->opts.persistent != 2; }
+// Phase launches unless the options ask for the persistent single launch.
+bool persistent(const vl_plan* p) { return p->opts.persistent == 1; }
+
+// An int16 operand goes to the tensor-core fold when TMA can address it:
+// 16-byte aligned base (host operands are staged at 256-byte offsets of a
+// workspace aligned to 256 bytes) and rows a multiple of 16 bytes apart.
+bool tc_eligible(const vl_plan* p, const vl_mat& M) {
+  if (persistent(p) || p->opts.fold_engine == 1 || M.dtype != VL_I16 || (M.ld & 7)) return false;
+  return M.space == VL_HOST || (reinterpret_cast<uintptr_t>(M.data) & 15) == 0;
+}
 
 void add_fold_task(vl_plan* p, const vl_mat& M, int32_t mode, int proof, int side) {
   FoldTask t{};
@@ -142,6 +162,21 @@ void add_fold_task(vl_plan* p, const vl_mat& M, int32_t mode, int proof, int sid
     t.box_h = ROWDOT_BLOCK_ROWS;
   }
   const int task = (int)p->tasks.size();
+  int32_t& tabs = side ? p->proofs[proof].tabB : p->proofs[proof].tabA;
+  if (tc_eligible(p, M)) {
+    // Tensor-core tiles: 128 lines by at most TC_SEG reduced entries.
+    t.bulk = 2;
+    t.box_w = TC_KS;
+    t.box_h = mode == MODE_ROWDOT ? TC_M : TC_KS;
+    p->tasks.push_back(t);
+    tabs |= TAB_BYTES;
+    const int lines = mode == MODE_COLSUM ? t.cols : t.rows, red = mode == MODE_COLSUM ? t.rows : t.cols;
+    for (int w0 = 0; w0 < lines; w0 += TC_M)
+      for (int k0 = 0; k0 < red; k0 += TC_SEG)
+        p->tc_tiles.push_back(TcTile{task, w0, std::min(TC_M, lines - w0), k0, std::min(TC_SEG, red - k0), {}});
+    return;
+  }
+  tabs |= TAB_LIMBS;
   p->tasks.push_back(t);
   const size_t tiles_before = p->tiles.size();
   const bool fr = M.dtype == VL_FR_MONT;
@@ -177,14 +212,58 @@ void add_fold_task(vl_plan* p, const vl_mat& M, int32_t mode, int proof, int sid
   p->proofs[proof].ntiles += (int32_t)(p->tiles.size() - tiles_before);
 }
 
-// Queue order of the persistent step.  Proofs go by k descending (their
-// rounds are the longest, and they should finish early); each proof's
-// prologue is queued STEP_LOOKAHEAD proofs ahead of its fold tiles.
+// Groups of consecutive proofs with about equal fold work (tiles are laid
+// out proof by proof, so each group's tiles are contiguous too).
+void build_groups(vl_plan* p) {
+  const int np = (int)p->proofs.size();
+  int ng = p->opts.groups > 0 ? p->opts.groups : 1;
+  ng = std::max(1, std::min(std::min(ng, np), STEP_CTL_HEAD_INTS));  // one tile counter per group
+  std::vector<int64_t> work(np, 0);
+  std::vector<int> first_tile(np + 1, (int)p->tiles.size()), first_tc(np + 1, (int)p->tc_tiles.size());
+  for (int t = (int)p->tiles.size() - 1; t >= 0; t--) {
+    const FoldTile& ft = p->tiles[t];
+    const int pi = p->tasks[ft.task].proof;
+    work[pi] += (int64_t)(ft.r1 - ft.r0) * (ft.c1 - ft.c0);
+    first_tile[pi] = t;
+  }
+  for (int t = (int)p->tc_tiles.size() - 1; t >= 0; t--) {
+    const TcTile& ft = p->tc_tiles[t];
+    const int pi = p->tasks[ft.task].proof;
+    work[pi] += (int64_t)ft.nw * ft.nk;
+    first_tc[pi] = t;
+  }
+  for (int i = np - 1; i >= 0; i--) {
+    first_tile[i] = std::min(first_tile[i], first_tile[i + 1]);
+    first_tc[i] = std::min(first_tc[i], first_tc[i + 1]);
+  }
+  int64_t total = 0;
+  for (int64_t w : work) total += w;
+  p->groups.clear();
+  int64_t acc = 0;
+  int start = 0;
+  for (int i = 0; i < np; i++) {
+    acc += work[i];
+    const bool cut = (int)p->groups.size() < ng - 1 && acc * ng >= total * (int64_t)(p->groups.size() + 1);
+    if (cut || i == np - 1) {
+      p->groups.push_back(
+          vl_plan::Group{start, i + 1, first_tile[start], first_tile[i + 1], first_tc[start], first_tc[i + 1]});
+      start = i + 1;
+    }
+  }
+  // Within a group, tensor-core tiles go longest first (the CTAs take them
+  // from a counter in this order).
+  for (const vl_plan::Group& G : p->groups)
+    std::stable_sort(p->tc_tiles.begin() + G.c0, p->tc_tiles.begin() + G.c1,
+                     [](const TcTile& a, const TcTile& b) { return a.nk > b.nk; });
+}
+
+// Queue order of the persistent step: proofs in layout order (k descending);
+// each proof's prologue is queued STEP_LOOKAHEAD proofs ahead of its fold
+// tiles.
 void build_items(vl_plan* p) {
   const int np = (int)p->proofs.size();
   std::vector<int> order(np);
-  for (int i = 0; i < np; i++) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return p->proofs[a].k > p->proofs[b].k; });
+  for (int i = 0; i < np; i++) order[i] = i;  // proofs are already laid out by k descending
   std::vector<std::vector<int>> tiles_of(np);
   for (size_t t = 0; t < p->tiles.size(); t++) tiles_of[p->tasks[p->tiles[t].task].proof].push_back((int)t);
   p->items.clear();
@@ -209,11 +288,24 @@ int build_plan(vl_plan* p) {
   p->off_out = off;
   off = align_up(off + sizeof(vl_proof) * np);
 
+  // Proofs are laid out by k descending (their rounds take longest, so they
+  // should finish first); DevProof.job maps back to the caller's order.
+  std::vector<int> order(np);
+  std::vector<int64_t> kk(np);
   for (int i = 0; i < np; i++) {
-    const vl_job& j = p->jobs[i];
     Dims d;
-    int e = job_dims(j, &d);
+    int e = job_dims(p->jobs[i], &d);
     if (e != VL_OK) return e;
+    order[i] = i;
+    kk[i] = d.k;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return kk[a] > kk[b]; });
+  p->slot_of_job.assign(np, 0);
+  for (int i = 0; i < np; i++) {
+    const vl_job& j = p->jobs[order[i]];
+    Dims d;
+    job_dims(j, &d);
+    p->slot_of_job[order[i]] = i;
     DevProof& P = p->proofs[i];
     std::memset(&P, 0, sizeof(P));
     P.m = (int32_t)d.m;
@@ -227,6 +319,7 @@ int build_plan(vl_plan* p) {
     P.dtypeA = j.P.dtype;
     P.dtypeB = j.Q.dtype;
     P.seed = j.fs.seed;
+    P.job = order[i];
     std::memcpy(P.binds, j.fs.bind, 96);
     // f_A: op(P) over its m rows.  Stored m x k -> column sums; stored k x m -> row dots.
     add_fold_task(p, j.P, j.P.trans ? MODE_ROWDOT : MODE_COLSUM, i, 0);
@@ -234,10 +327,13 @@ int build_plan(vl_plan* p) {
     add_fold_task(p, j.Q, j.Q.trans ? MODE_COLSUM : MODE_ROWDOT, i, 1);
   }
   build_items(p);
+  build_groups(p);
   p->off_tasks = off;
   off = align_up(off + sizeof(FoldTask) * p->tasks.size());
   p->off_tiles = off;
   off = align_up(off + sizeof(FoldTile) * p->tiles.size());
+  p->off_tc_tiles = off;
+  off = align_up(off + sizeof(TcTile) * p->tc_tiles.size());
   p->off_tmaps = off;
   off = align_up(off + sizeof(CUtensorMap) * p->tasks.size());
   p->off_etmaps = off;
@@ -258,17 +354,30 @@ int build_plan(vl_plan* p) {
   p->acc_bytes = off - p->off_acc;
   p->step_smem = std::max(p->fold_smem, std::max(PRO_SMEM, RND_SMEM));
   for (int i = 0; i < np; i++) {
-    const DevProof& P = p->proofs[i];
-    p->pp[i].eqA = off;
-    off = align_up(off + sizeof(Fr) * P.m);
-    p->pp[i].eqB = off;
-    off = align_up(off + sizeof(Fr) * P.n);
-    p->proofs[i].soa_pitchA = (P.m + 3) & ~3;
-    p->proofs[i].soa_pitchB = (P.n + 3) & ~3;
-    p->pp[i].soaA = off;
-    off = align_up(off + 32 * (size_t)p->proofs[i].soa_pitchA);
-    p->pp[i].soaB = off;
-    off = align_up(off + 32 * (size_t)p->proofs[i].soa_pitchB);
+    DevProof& P = p->proofs[i];
+    P.soa_pitchA = (P.m + 3) & ~3;
+    P.soa_pitchB = (P.n + 3) & ~3;
+    p->pp[i].eqA = p->pp[i].eqB = p->pp[i].soaA = p->pp[i].soaB = p->pp[i].w8A = p->pp[i].w8B = 0;
+    if (P.tabA & TAB_LIMBS) {
+      p->pp[i].eqA = off;
+      off = align_up(off + sizeof(Fr) * P.m);
+      p->pp[i].soaA = off;
+      off = align_up(off + 32 * (size_t)P.soa_pitchA);
+    }
+    if (P.tabB & TAB_LIMBS) {
+      p->pp[i].eqB = off;
+      off = align_up(off + sizeof(Fr) * P.n);
+      p->pp[i].soaB = off;
+      off = align_up(off + 32 * (size_t)P.soa_pitchB);
+    }
+    if (P.tabA & TAB_BYTES) {
+      p->pp[i].w8A = off;
+      off = align_up(off + 4096 * (size_t)((P.m + TC_KS - 1) / TC_KS));
+    }
+    if (P.tabB & TAB_BYTES) {
+      p->pp[i].w8B = off;
+      off = align_up(off + 4096 * (size_t)((P.n + TC_KS - 1) / TC_KS));
+    }
     p->pp[i].fA = off;
     off = align_up(off + sizeof(Fr) * ((size_t)1 << P.d1));
     p->pp[i].fB = off;
@@ -365,6 +474,22 @@ bool encode_task_map(const FoldTask& t, CUtensorMap* map) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// TMA descriptor of a tensor-core task's stored matrix: uint16 boxes of 64
+// columns (128 bytes, 128-byte swizzle) by 128 rows (row dots) or 64 rows
+// (column sums); out-of-range entries read as zero.
+bool encode_tc_map(const FoldTask& t, CUtensorMap* map) {
+  if ((reinterpret_cast<uintptr_t>(t.mat) & 15) || (t.ld & 7)) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)t.cols, (cuuint64_t)t.rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)t.ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)t.box_w, (cuuint32_t)t.box_h};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(t.mat), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // TMA descriptor of the limb-major weights a row-dot task reads: 8 rows of
 // `pitch` words, boxes of [8 x BW].
 bool encode_weight_map(const FoldTask& t, const uint32_t* soa, int pitch, CUtensorMap* map) {
@@ -384,10 +509,13 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
   const int np = (int)p->jobs.size();
   for (int i = 0; i < np; i++) {
     DevProof& P = p->proofs[i];
-    P.eqA = reinterpret_cast<Fr*>(ws + p->pp[i].eqA);
-    P.eqB = reinterpret_cast<Fr*>(ws + p->pp[i].eqB);
-    P.eqA_soa = reinterpret_cast<uint32_t*>(ws + p->pp[i].soaA);
-    P.eqB_soa = reinterpret_cast<uint32_t*>(ws + p->pp[i].soaB);
+    const bool la = P.tabA & TAB_LIMBS, lb = P.tabB & TAB_LIMBS;
+    P.eqA = la ? reinterpret_cast<Fr*>(ws + p->pp[i].eqA) : nullptr;
+    P.eqB = lb ? reinterpret_cast<Fr*>(ws + p->pp[i].eqB) : nullptr;
+    P.eqA_soa = la ? reinterpret_cast<uint32_t*>(ws + p->pp[i].soaA) : nullptr;
+    P.eqB_soa = lb ? reinterpret_cast<uint32_t*>(ws + p->pp[i].soaB) : nullptr;
+    P.w8A = (P.tabA & TAB_BYTES) ? reinterpret_cast<uint32_t*>(ws + p->pp[i].w8A) : nullptr;
+    P.w8B = (P.tabB & TAB_BYTES) ? reinterpret_cast<uint32_t*>(ws + p->pp[i].w8B) : nullptr;
     P.accA = reinterpret_cast<unsigned long long*>(ws + p->pp[i].accA);
     P.accB = reinterpret_cast<unsigned long long*>(ws + p->pp[i].accB);
     P.fA = reinterpret_cast<Fr*>(ws + p->pp[i].fA);
@@ -398,18 +526,25 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
   p->etmaps.resize(p->tasks.size());
   for (size_t i = 0; i < p->tasks.size(); i++) {
     FoldTask& t = p->tasks[i];
-    const vl_job& j = p->jobs[t.proof];
     const DevProof& P = p->proofs[t.proof];
+    const vl_job& j = p->jobs[P.job];
     t.mat = operand_ptr(p, t.side ? j.Q : j.P, ws);
     std::memset(&p->tmaps[i], 0, sizeof(CUtensorMap));
     std::memset(&p->etmaps[i], 0, sizeof(CUtensorMap));
+    t.tmap = ws + p->off_tmaps + i * sizeof(CUtensorMap);
+    t.etmap = ws + p->off_etmaps + i * sizeof(CUtensorMap);
+    if (t.bulk == 2) {
+      if (!encode_tc_map(t, &p->tmaps[i])) {
+        snprintf(g_last_error, sizeof(g_last_error), "tensor map of fold task %zu could not be encoded", i);
+        return VL_EINVAL;
+      }
+      continue;
+    }
     bool ok = encode_task_map(t, &p->tmaps[i]);
     if (ok && t.mode == MODE_ROWDOT)
       ok = encode_weight_map(t, t.side ? P.eqB_soa : P.eqA_soa, t.side ? P.soa_pitchB : P.soa_pitchA,
                              &p->etmaps[i]);
     t.bulk = ok ? 1 : 0;
-    t.tmap = ws + p->off_tmaps + i * sizeof(CUtensorMap);
-    t.etmap = ws + p->off_etmaps + i * sizeof(CUtensorMap);
   }
   cudaError_t e = cudaMemcpyAsync(ws + p->off_proofs, p->proofs.data(), sizeof(DevProof) * np,
                                   cudaMemcpyHostToDevice, st);
@@ -418,6 +553,9 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
                         cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !p->tiles.empty())
     e = cudaMemcpyAsync(ws + p->off_tiles, p->tiles.data(), sizeof(FoldTile) * p->tiles.size(),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !p->tc_tiles.empty())
+    e = cudaMemcpyAsync(ws + p->off_tc_tiles, p->tc_tiles.data(), sizeof(TcTile) * p->tc_tiles.size(),
                         cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !p->tmaps.empty())
     e = cudaMemcpyAsync(ws + p->off_tmaps, p->tmaps.data(), sizeof(CUtensorMap) * p->tmaps.size(),
@@ -431,9 +569,16 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
   // The host vectors must outlive the copies: wait for them.
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess && p->fold_smem > 0) e = fold_set_smem(p->fold_smem);
+  if (e == cudaSuccess && !p->tc_tiles.empty()) e = fold_tc_prepare();
   if (e == cudaSuccess && persistent(p)) e = step_set_smem(p->step_smem);
   if (e == cudaSuccess && persistent(p) && !p->step_grid) e = step_grid(p->step_smem, &p->step_grid);
   return cuda_status(e, "bind_workspace");
+}
+
+// DevProof index of the test hook's proof (given as 1 + job index), or -1.
+int never_ready_slot(const vl_plan* p) {
+  const int j = p->opts.test_never_ready - 1;
+  return (j >= 0 && j < (int)p->slot_of_job.size()) ? p->slot_of_job[j] : -1;
 }
 
 unsigned long long wait_ns(const vl_plan* p) {
@@ -441,6 +586,17 @@ unsigned long long wait_ns(const vl_plan* p) {
 }
 
 cudaError_t ensure_events(vl_plan* p) {
+  if (p->gev.empty()) {
+    p->gev.resize(2 * p->groups.size() + 2);
+    for (cudaEvent_t& ev : p->gev) {
+      cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) return e;
+    }
+    for (cudaStream_t& s2 : p->side) {
+      cudaError_t e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return e;
+    }
+  }
   if (!p->ring.empty()) return cudaSuccess;
   p->ring.resize((size_t)p->ring_runs * vl_plan::NEV);
   for (cudaEvent_t& ev : p->ring) {
@@ -465,6 +621,7 @@ cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t s
   const DevProof* dp = reinterpret_cast<const DevProof*>(ws + p->off_proofs);
   const FoldTask* dt = reinterpret_cast<const FoldTask*>(ws + p->off_tasks);
   const FoldTile* dl = reinterpret_cast<const FoldTile*>(ws + p->off_tiles);
+  const TcTile* dc = reinterpret_cast<const TcTile*>(ws + p->off_tc_tiles);
   const int np = (int)p->jobs.size();
   // Under capture, external records become event-record nodes of the graph
   // (the flag is only valid while capturing).
@@ -479,17 +636,47 @@ cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t s
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[1], st, flags);
     if (e == cudaSuccess)
       e = launch_step(di, (int)p->items.size(), dt, dl, dp, np, dout, ctl, p->step_grid, p->step_smem, wait_ns(p),
-                      p->opts.test_never_ready - 1, st);
+                      never_ready_slot(p), st);
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2], st, flags);
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[3], st, flags);
     return e;
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(ws + p->off_acc, 0, p->acc_bytes, st);
-  if (e == cudaSuccess) e = launch_prologue(dp, np, st);
+  // Phase launches in groups: stream st folds group g while the rounds stream
+  // runs group g-1's rounds and the prologue stream group g+1's prologue.
+  // Dependencies are graph edges (events); no kernel waits for another.
+  // Phases: [0] clear + first prologue, [1] folds (rounds and prologues of
+  // other groups overlap them), [2] rounds left after the last fold.
+  const int ng = (int)p->groups.size();
+  cudaStream_t rs = p->side[0], ps = p->side[1];
+  cudaEvent_t* gev = p->gev.data();  // [0, ng): prologue g done; [ng, 2ng): fold g done; 2ng: start; 2ng+1: rounds done
+  // tile counters (one per group) and accumulators: one contiguous region
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws + p->off_ctl, 0, p->off_acc + p->acc_bytes - p->off_ctl, st);
+  if (e == cudaSuccess) e = cudaEventRecord(gev[2 * ng], st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ps, gev[2 * ng], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(rs, gev[2 * ng], 0);
+  const vl_plan::Group& g0 = p->groups[0];
+  if (e == cudaSuccess) e = launch_prologue(dp + g0.p0, g0.p1 - g0.p0, st);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[1], st, flags);
-  if (e == cudaSuccess) e = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, wait_ns(p), st);
+  for (int g = 1; g < ng && e == cudaSuccess; g++) {
+    const vl_plan::Group& G = p->groups[g];
+    e = launch_prologue(dp + G.p0, G.p1 - G.p0, ps);
+    if (e == cudaSuccess) e = cudaEventRecord(gev[g], ps);
+  }
+  for (int g = 0; g < ng && e == cudaSuccess; g++) {
+    const vl_plan::Group& G = p->groups[g];
+    if (g > 0) e = cudaStreamWaitEvent(st, gev[g], 0);
+    if (e == cudaSuccess)
+      e = launch_fold_tc(dc + G.c0, G.c1 - G.c0, dt, dp, reinterpret_cast<int*>(ws + p->off_ctl) + g, wait_ns(p), st);
+    if (e == cudaSuccess) e = launch_fold(dt, dl + G.t0, G.t1 - G.t0, dp, p->fold_smem, wait_ns(p), st);
+    if (e == cudaSuccess) e = cudaEventRecord(gev[ng + g], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(rs, gev[ng + g], 0);
+    if (e == cudaSuccess) e = launch_rounds(dp + G.p0, G.p1 - G.p0, dout, p->opts.rounds_variant, rs);
+  }
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2], st, flags);
-  if (e == cudaSuccess) e = launch_rounds(dp, np, dout, p->opts.rounds_variant, st);
+  if (e == cudaSuccess) e = cudaEventRecord(gev[2 * ng + 1], rs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, gev[2 * ng + 1], 0);
+  if (e == cudaSuccess) e = cudaEventRecord(gev[0], ps);  // join the prologue stream too
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, gev[0], 0);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[3], st, flags);
   return e;
 }
@@ -648,7 +835,14 @@ int32_t vl_plan_create(const vl_job* jobs, int32_t njobs, const vl_batch_opts* o
 
 size_t vl_plan_workspace_bytes(const vl_plan* plan) { return plan ? plan->total : 0; }
 
-int32_t vl_plan_launches(const vl_plan* plan) { return plan ? (persistent(plan) ? 1 : 3) : 0; }
+int32_t vl_plan_launches(const vl_plan* plan) {
+  if (!plan) return 0;
+  if (persistent(plan)) return 1;
+  int32_t n = 0;
+  for (const vl_plan::Group& G : plan->groups)
+    n += 2 + (G.c1 > G.c0 ? 1 : 0) + (G.t1 > G.t0 ? 1 : 0);  // prologue, folds, rounds
+  return n;
+}
 
 int32_t vl_plan_run(vl_plan* plan, void* workspace, size_t workspace_bytes, vl_proof* out, int32_t out_space,
                     void* stream) {
@@ -679,6 +873,10 @@ void vl_plan_destroy(vl_plan* plan) {
   release_workspaces(plan);
   drop_graph(plan);
   if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
+  for (cudaStream_t s2 : plan->side)
+    if (s2) cudaStreamDestroy(s2);
+  for (cudaEvent_t ev : plan->gev)
+    if (ev) cudaEventDestroy(ev);
   for (cudaEvent_t ev : plan->ring) cudaEventDestroy(ev);
   for (cudaEvent_t ev : plan->cap_ev)
     if (ev) cudaEventDestroy(ev);
@@ -762,7 +960,10 @@ extern "C" int32_t vl_prove_matmul_noalloc(const vl_mat* P, const vl_mat* Q, con
   j.Q = *Q;
   j.fs = *fs;
   vl_plan* p = nullptr;
-  int e = make_plan(&j, 1, nullptr, &p);
+  vl_batch_opts o{};
+  o.persistent = 2;
+  o.fold_engine = 1;  // the launches below run the CUDA-core fold
+  int e = make_plan(&j, 1, &o, &p);
   if (e != VL_OK) return e;
   if (p->total > VL_NOALLOC_SCRATCH_BYTES) {
     snprintf(g_last_error, sizeof(g_last_error),

@@ -9,7 +9,8 @@ template <int MINB>
 __global__ void __launch_bounds__(RND_THREADS, MINB) rounds_kernel(const DevProof* __restrict__ proofs,
                                                                    vl_proof* __restrict__ out) {
   extern __shared__ __align__(128) uint8_t rnd_smem[];
-  rounds_block(proofs[blockIdx.x], out + blockIdx.x, rnd_smem);
+  const DevProof& P = proofs[blockIdx.x];
+  rounds_block(P, out + P.job, rnd_smem);
 }
 
 // variant: CTAs per SM the register allocation targets (7: one wave of 1064

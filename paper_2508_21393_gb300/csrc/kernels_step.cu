@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(FOLD_THREADS, 2) step_kernel(const StepItem* _
     __syncthreads();
     if (flag_sh) {
       __threadfence();
-      rounds_block(P, out + p, step_smem);
+      rounds_block(P, out + P.job, step_smem);
     }
   }
 }

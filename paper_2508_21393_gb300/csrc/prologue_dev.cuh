@@ -23,8 +23,30 @@ namespace vl {
 static constexpr int MAX_VARS = 16;      // log2 of VL_MAX_REDUCE
 static constexpr int MAX_HALF = 1 << 8;  // 2^(MAX_VARS / 2)
 
-__device__ static Fr build_eq(const Fr* x, int d, int size, Fr* out, uint32_t* out_soa, int pitch, Fr* lo, Fr* hi,
-                              Fr* red) {
+// Two fp16 values from bytes of w selected by `sel` (0x64bb is 1024 + bb).
+__device__ __forceinline__ uint32_t pro_bytes_f16x2(uint32_t w, uint32_t sel) {
+  const uint32_t v = __byte_perm(w, 0x64646464u, sel);
+  uint32_t r;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(0x64006400u));
+  return r;
+}
+
+// Entry i of the tensor-core weight table: the 32 bytes of e as fp16 values,
+// at row i % 64 of its 4 KB chunk (MN-major core matrices: [i / 8 % 8][byte
+// group][i % 8][8 bytes]).
+__device__ __forceinline__ void store_w8(uint32_t* w8, int i, const Fr& e) {
+  uint4* chunk = reinterpret_cast<uint4*>(w8) + (size_t)(i >> 6) * 256;
+  const int kk = i & 63;
+#pragma unroll
+  for (int g = 0; g < 4; g++) {
+    const uint32_t a = e.v[2 * g], b = e.v[2 * g + 1];
+    chunk[(kk >> 3) * 32 + g * 8 + (kk & 7)] = make_uint4(pro_bytes_f16x2(a, 0x4140), pro_bytes_f16x2(a, 0x4342),
+                                                          pro_bytes_f16x2(b, 0x4140), pro_bytes_f16x2(b, 0x4342));
+  }
+}
+
+__device__ static Fr build_eq(const Fr* x, int d, int size, int tabs, Fr* out, uint32_t* out_soa, int pitch,
+                              uint32_t* w8, Fr* lo, Fr* hi, Fr* red) {
   const int tid = threadIdx.x;
   const int s = (d + 1) >> 1;          // low-block variables
   const int dh = d - s;                // high-block variables
@@ -52,10 +74,17 @@ __device__ static Fr build_eq(const Fr* x, int d, int size, Fr* out, uint32_t* o
   Fr sum[1] = {fr_zero()};
   for (int i = tid; i < size; i += blockDim.x) {
     Fr e = mont_mul_ni(hi[i >> s], lo[i & (nlo - 1)]);
-    out[i] = e;
+    if (tabs & TAB_LIMBS) {
+      out[i] = e;
 #pragma unroll
-    for (int l = 0; l < 8; l++) out_soa[l * pitch + i] = e.v[l];
+      for (int l = 0; l < 8; l++) out_soa[l * pitch + i] = e.v[l];
+    }
+    if (tabs & TAB_BYTES) store_w8(w8, i, e);
     sum[0] = fr_add(sum[0], e);
+  }
+  if (tabs & TAB_BYTES) {
+    const int end = (size + 63) & ~63;
+    for (int i = size + tid; i < end; i += blockDim.x) store_w8(w8, i, fr_zero());
   }
   block_sum_fr<1>(sum, red);
   // sum = sum_i E_i . R^2; one Montgomery product with the plain integer 2^15
@@ -117,9 +146,9 @@ static __device__ void prologue_block(const DevProof& P, uint8_t* smem) {
   squeeze_dev(S1, LBL_V, P.d2, v, S2, dig);
   if (tid < 32) P.scr->state[tid] = (uint8_t)(S2[tid >> 2] >> (24 - 8 * (tid & 3)));
 
-  Fr ca = build_eq(u, P.d0, P.m, P.eqA, P.eqA_soa, P.soa_pitchA, lo, hi, red);
+  Fr ca = build_eq(u, P.d0, P.m, P.tabA, P.eqA, P.eqA_soa, P.soa_pitchA, P.w8A, lo, hi, red);
   __syncthreads();
-  Fr cb = build_eq(v, P.d2, P.n, P.eqB, P.eqB_soa, P.soa_pitchB, lo, hi, red);
+  Fr cb = build_eq(v, P.d2, P.n, P.tabB, P.eqB, P.eqB_soa, P.soa_pitchB, P.w8B, lo, hi, red);
   if (tid == 0) {
     P.scr->corrA = P.dtypeA == VL_I16 ? ca : fr_zero();
     P.scr->corrB = P.dtypeB == VL_I16 ? cb : fr_zero();

@@ -276,13 +276,16 @@ def test_plans_taking_turns_on_one_workspace():
         B.vl_plan_destroy(pb)
 
 
-def test_phase_launch_mode_matches_persistent():
+def test_launch_modes_and_fold_engines_agree():
+    """Persistent launch, phase launches with the tensor-core fold, phase
+    launches with the CUDA-core fold: the same proofs."""
     jobs = _lora_jobs(n=40, d=128, k=96, r=8, layer=6, proj="q")
     dj, keep = _dev_jobs(jobs)
     refs = [oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes() for j in jobs]
-    for mode in (0, 2):
+    for mode, engine in ((1, 0), (2, 0), (2, 1), (0, 0)):
         opts = B.vl_batch_opts()
         opts.persistent = mode
+        opts.fold_engine = engine
         nb = B.vl_workspace_bytes(dj, opts)
         ws = _ws(nb)
         proofs = B.vl_prove_batch(dj, ws.data_ptr(), nb, opts=opts)
@@ -298,6 +301,7 @@ def test_wait_that_runs_out_reports_timeout_and_context_survives():
     refs = [oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes() for j in jobs]
     bad = 3
     opts = B.vl_batch_opts()
+    opts.persistent = 1  # the hook delays a prologue inside the persistent step
     opts.wait_limit_us = 20000
     opts.test_never_ready = bad + 1
     plan = B.vl_plan_create(dj, opts)
@@ -314,5 +318,67 @@ def test_wait_that_runs_out_reports_timeout_and_context_survives():
                 assert pf.status == 0 and B.proof_bytes(pf) == ref
     finally:
         B.vl_plan_destroy(plan)
-    proofs = B.vl_prove_batch(dj, ws.data_ptr(), nb)
+    nb2 = B.vl_workspace_bytes(dj)
+    ws2 = _ws(nb2)
+    proofs = B.vl_prove_batch(dj, ws2.data_ptr(), nb2)
     assert [B.proof_bytes(p) for p in proofs] == refs
+
+
+TC_SHAPES = [
+    # (m, k, n, transP, transQ): ragged lines and reductions, both fold modes,
+    # one or two TMA boxes per column-sum stage, reductions over one segment
+    (1, 8, 1, 0, 0),
+    (70, 200, 33, 0, 0),
+    (64, 128, 64, 1, 1),
+    (130, 136, 72, 0, 1),
+    (200, 64, 300, 1, 0),
+    (3, 512, 5, 0, 0),
+    (129, 8, 257, 1, 1),
+    (16500, 16, 8, 0, 0),
+    (8, 24, 17000, 0, 0),
+]
+
+
+@pytest.mark.parametrize("shape", TC_SHAPES)
+def test_tensor_core_fold_matches_oracle_and_cuda_core_fold(shape):
+    m, k, n, tp, tq = shape
+    rng = np.random.default_rng(1000 + m + 7 * k + 13 * n)
+    P = _rand(rng, (k, m) if tp else (m, k))
+    Q = _rand(rng, (n, k) if tq else (k, n))
+    ref = oracle.prove_matmul(P, Q, tp, tq, seed=m * 31 + n).to_bytes()
+    Pd, Qd = torch.from_numpy(P).cuda(), torch.from_numpy(Q).cuda()
+    jb = [B.job(Pd, Qd, tp, tq, m * 31 + n)]
+    for engine in (0, 1):
+        opts = B.vl_batch_opts()
+        opts.fold_engine = engine
+        plan = B.vl_plan_create(jb, opts)
+        try:
+            ltc = B.vl_plan_launches(plan)
+            nb = B.vl_plan_workspace_bytes(plan)
+            ws = _ws(nb)
+            out = (B.vl_proof * 1)()
+            B.vl_plan_run(plan, ws.data_ptr(), nb, out, B.VL_HOST)
+            assert B.proof_bytes(out[0]) == ref, f"engine {engine}"
+        finally:
+            B.vl_plan_destroy(plan)
+        # both operands are TMA-addressable (ld a multiple of 8) only when so
+        tc_ok = (P.shape[1] % 8 == 0) and (Q.shape[1] % 8 == 0)
+        if engine == 0 and tc_ok:
+            assert ltc == 3  # prologue, tensor-core fold, rounds
+
+
+def test_tensor_core_fold_extreme_entries():
+    """Entries at the int16 extremes: every byte of p = x + 2^15 at 0 or 255,
+    the largest per-stage accumulator values."""
+    m, k, n = 200, 136, 72
+    for pv, qv in ((-(1 << 15), (1 << 15) - 1), ((1 << 15) - 1, (1 << 15) - 1), (-(1 << 15), -(1 << 15))):
+        P = np.full((m, k), pv, np.int16)
+        Q = np.full((k, n), qv, np.int16)
+        Pd, Qd = torch.from_numpy(P).cuda(), torch.from_numpy(Q).cuda()
+        opts = B.vl_batch_opts()
+        jb = [B.job(Pd, Qd, 0, 0, 9), B.job(Qd, Pd, 1, 1, 10)]
+        nb = B.vl_workspace_bytes(jb, opts)
+        ws = _ws(nb)
+        proofs = B.vl_prove_batch(jb, ws.data_ptr(), nb, opts=opts)
+        assert B.proof_bytes(proofs[0]) == oracle.prove_matmul(P, Q, 0, 0, seed=9).to_bytes()
+        assert B.proof_bytes(proofs[1]) == oracle.prove_matmul(Q, P, 1, 1, seed=10).to_bytes()
