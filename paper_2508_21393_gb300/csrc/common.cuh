@@ -101,10 +101,14 @@ struct TcTile {
 static constexpr int TC_M = 128;        // lines per tile (MMA M)
 static constexpr int TC_KS = 64;        // reduction entries per pipeline stage
 static constexpr int TC_SEG = 16384;    // reduction entries per tile at most
-static constexpr int TC_THREADS = 320;  // producer warp, MMA warp, 8 worker warps
-static constexpr int TC_NR = 4;         // raw (TMA) stages
-static constexpr int TC_NC = 2;         // converted-operand stages
-static constexpr int TC_SMEM = 1024 + TC_NC * 32768 + TC_NR * 20480 + 4096 + 1024 + 512;
+static constexpr int TC_CONV_WARPS = 8;   // int16 -> fp16 byte operands
+static constexpr int TC_DRAIN_WARPS = 8;  // TMEM -> digit sums (two groups of four lane quarters)
+static constexpr int TC_THREADS = 64 + 32 * (TC_CONV_WARPS + TC_DRAIN_WARPS);  // + producer, MMA warps
+static constexpr int TC_NR = 5;         // raw (TMA) stages
+static constexpr int TC_NC = 3;         // converted-operand stages
+static constexpr int TC_NA = 4;         // TMEM accumulator buffers
+static constexpr int TC_HR = 16;        // stage-header ring (> TC_NR + TC_NC + TC_NA)
+static constexpr int TC_SMEM = 1024 + TC_NC * 32768 + TC_NR * 20480 + 4096 + 1024 + 1024;
 
 struct FoldTile {
   int32_t task;

@@ -21,15 +21,20 @@
 // rounds reduce them unchanged (Montgomery reduction, minus 2^15 . sum E).
 //
 // Roles in a CTA (one CTA per SM; tiles come from a global counter, longest
-// first):
-//   warp 0     producer: per stage one 128B-swizzled TMA box of the operand
-//              (or two for column sums) and the 4 KB of fp16 weight bytes
-//   warp 1     owns TMEM; issues per stage one init MMA and 4 + 4 MMAs
-//              (K = 16) into one of two accumulator buffers
-//   warps 2-9  workers: convert the int16 box into fp16 lo/hi operand tiles
-//              (canonical core-matrix layout, no swizzle; K-major for row
-//              dots, MN-major for column sums), then drain the previous
-//              stage's accumulator from TMEM into per-line digit sums
+// first), each running at its own pace and linked only by mbarriers:
+//   warp 0       producer: per stage one 128B-swizzled TMA box of the operand
+//                (two for column sums) and the stage's 4 KB of fp16 weight
+//                bytes, into one of TC_NR raw slots
+//   warp 1       owns TMEM; per stage one init MMA and 4 + 4 MMAs (K = 16)
+//                into one of TC_NA accumulator buffers
+//   warps 2-9    converters: int16 box -> fp16 lo/hi operand tiles in one of
+//                TC_NC slots (canonical core-matrix layout, no swizzle;
+//                K-major for row dots, MN-major for column sums)
+//   warps 10-17  drainers: accumulator buffer -> per-line digit sums (two
+//                groups of four warps, one warp per TMEM lane quarter, each
+//                group half of the 33 digits); tile epilogue
+// Stage headers (tile, stage) sit in a ring of TC_HR entries, longer than
+// the stages any role can be ahead of another.
 // Every wait is bounded; a wait that runs out marks the proof VL_ETIMEOUT, and
 // the CTA drains its copies and MMAs before it frees TMEM and returns.
 #include "fold_dev.cuh"
@@ -41,12 +46,13 @@ constexpr int SM_CONV = 0;                         // TC_NC x 32 KB: [lo 16 KB |
 constexpr int SM_RAW = SM_CONV + TC_NC * 32768;    // TC_NR x 20 KB: [operand 16 KB | weights 4 KB]
 constexpr int SM_ACONST = SM_RAW + TC_NR * 20480;  // 128 x 16 fp16, K-major
 constexpr int SM_BCONST = SM_ACONST + 4096;        // 16 x 32 fp16, MN-major
-constexpr int SM_HDR = SM_BCONST + 1024;           // TC_NR stage headers
-constexpr int SM_BAR = SM_HDR + TC_NR * 16;
-constexpr int NBAR = 2 * TC_NR + 2 * TC_NC + 4 + 1;
+constexpr int SM_HDR = SM_BCONST + 1024;           // TC_HR stage headers
+constexpr int SM_BAR = SM_HDR + TC_HR * 16;
+constexpr int NBAR = 2 * TC_NR + 2 * TC_NC + 2 * TC_NA + 1;
 constexpr int SM_TMEM = SM_BAR + NBAR * 8;
 static_assert(SM_TMEM + 16 <= TC_SMEM - 1024, "shared-memory layout");
-constexpr uint32_t TMEM_COLS = 128;  // two buffers of [lo 32 | hi 32] fp32 columns
+constexpr uint32_t TMEM_COLS = 64 * TC_NA;  // TC_NA buffers of [lo 32 | hi 32] fp32 columns
+static_assert(TMEM_COLS == 256, "TMEM allocation is a power of two");
 
 // Instruction descriptor of kind::f16: fp32 accumulator, fp16 A and B,
 // B MN-major, N = 32, M = 128; bit 15 selects an MN-major A.
@@ -78,19 +84,12 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 #define TC_R8(b) "=r"(r[b + 0]), "=r"(r[b + 1]), "=r"(r[b + 2]), "=r"(r[b + 3]), "=r"(r[b + 4]), "=r"(r[b + 5]), \
                  "=r"(r[b + 6]), "=r"(r[b + 7])
 
-// 32 lanes x 16 / 32 consecutive fp32 columns of TMEM (this warp's lane quarter).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : TC_R8(0), TC_R8(8)
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : TC_R8(0), TC_R8(8), TC_R8(16), TC_R8(24)
-      : "r"(taddr));
+// 8 columns into r[OFF .. OFF + 7].
+template <int OFF>
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : TC_R8(OFF)
+               : "r"(taddr));
 }
 #undef TC_R8
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -128,8 +127,8 @@ struct TcBars {
   __device__ uint32_t conv_full(int c) const { return b + 8 * (2 * TC_NR + c); }
   __device__ uint32_t conv_empty(int c) const { return b + 8 * (2 * TC_NR + TC_NC + c); }
   __device__ uint32_t acc_full(int a) const { return b + 8 * (2 * TC_NR + 2 * TC_NC + a); }
-  __device__ uint32_t acc_empty(int a) const { return b + 8 * (2 * TC_NR + 2 * TC_NC + 2 + a); }
-  __device__ uint32_t fin() const { return b + 8 * (2 * TC_NR + 2 * TC_NC + 4); }
+  __device__ uint32_t acc_empty(int a) const { return b + 8 * (2 * TC_NR + 2 * TC_NC + TC_NA + a); }
+  __device__ uint32_t fin() const { return b + 8 * (2 * TC_NR + 2 * TC_NC + 2 * TC_NA); }
 };
 
 __device__ __forceinline__ void mark_timeout(const DevProof* proofs, const FoldTask* tasks, const TcTile* tiles,
@@ -137,28 +136,55 @@ __device__ __forceinline__ void mark_timeout(const DevProof* proofs, const FoldT
   atomicExch(&proofs[tasks[tiles[tile < 0 ? 0 : tile].task].proof].scr->status, VL_ETIMEOUT);
 }
 
-// Combine a tile's digit sums into column sums and add them to the proof's
-// accumulators (group 0 holds s_0..s_16, group 1 s_17..s_32).
-__device__ __forceinline__ void tc_epilogue(int grp, uint32_t (&dg)[17], int nst, unsigned long long* acc) {
+// Drain one stage's accumulator columns (lo at ta, hi at ta + 32) into the
+// digit sums s_t, t in [T0, T1]:  dg[t - T0] += bits(2^23 + s_t), with
+// s_t = lo_t + hi_{t-1} (the lo accumulator starts at 2^23).
+template <int T0, int T1>
+__device__ __forceinline__ void drain_digits(uint32_t ta, uint32_t (&dg)[17], uint32_t acc_empty) {
+  constexpr int LA = T0, LB = T1 < 31 ? T1 : 31;           // lo columns used
+  constexpr int HA = T0 > 0 ? T0 - 1 : 0, HB = T1 - 1;      // hi columns used
+  uint32_t L[32], H[32];
+  if (LA <= 7 && LB >= 0) tmem_ld8<0>(ta + 0, L);
+  if (LA <= 15 && LB >= 8) tmem_ld8<8>(ta + 8, L);
+  if (LA <= 23 && LB >= 16) tmem_ld8<16>(ta + 16, L);
+  if (LA <= 31 && LB >= 24) tmem_ld8<24>(ta + 24, L);
+  if (HA <= 7 && HB >= 0) tmem_ld8<0>(ta + 32, H);
+  if (HA <= 15 && HB >= 8) tmem_ld8<8>(ta + 40, H);
+  if (HA <= 23 && HB >= 16) tmem_ld8<16>(ta + 48, H);
+  if (HA <= 31 && HB >= 24) tmem_ld8<24>(ta + 56, H);
+  tmem_wait_ld();
+  tc_fence_before();
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(acc_empty);
+#pragma unroll
+  for (int t = T0; t <= T1; t++) {
+    uint32_t v;
+    if (t == 0) v = L[0];
+    else if (t == 32) v = fbits_add(H[31], 0x4B000000u);
+    else v = fbits_add(L[t], H[t - 1]);
+    dg[t - T0] += v;
+  }
+}
+
+// Combine a tile's digit sums s_t, t in [T0, T1], into the column sums
+// col_j = sum_q 2^(8q) s_{4j+q} and add them to the proof's accumulators;
+// s_32 goes to col_7 as s_32 . 2^32 (2^256 = 2^32 . 2^224).
+template <int T0, int T1>
+__device__ __forceinline__ void tc_epilogue(uint32_t (&dg)[17], int nst, unsigned long long* acc) {
   const uint32_t off = (uint32_t)nst * 0x4B000000u;
-  uint64_t s[17];
 #pragma unroll
-  for (int t = 0; t < 17; t++) s[t] = (uint64_t)(dg[t] - off);
-  if (grp == 0) {
+  for (int j = 0; j < 8; j++) {
+    uint64_t c = 0;
+    bool any = false;
 #pragma unroll
-    for (int j = 0; j < 4; j++)
-      red_add_u64(acc + j, s[4 * j] + (s[4 * j + 1] << 8) + (s[4 * j + 2] << 16) + (s[4 * j + 3] << 24));
-    red_add_u64(acc + 4, s[16]);
-  } else {
-    // s[i] holds s_{17+i}
-    red_add_u64(acc + 4, (s[0] << 8) + (s[1] << 16) + (s[2] << 24));
-#pragma unroll
-    for (int j = 5; j < 8; j++) {
-      const int b = 4 * j - 17;
-      uint64_t c = s[b] + (s[b + 1] << 8) + (s[b + 2] << 16) + (s[b + 3] << 24);
-      if (j == 7) c += s[15] << 32;  // s_32 . 2^256 = (s_32 . 2^32) . 2^224
-      red_add_u64(acc + j, c);
+    for (int t = T0; t <= T1; t++) {
+      const int col = t < 32 ? t >> 2 : 7, sh = t < 32 ? 8 * (t & 3) : 32;
+      if (col == j) {
+        c += (uint64_t)(dg[t - T0] - off) << sh;
+        any = true;
+      }
     }
+    if (any) red_add_u64(acc + j, c);
   }
 }
 
@@ -179,15 +205,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (tid == 0) {
     for (int s = 0; s < TC_NR; s++) {
       mbar_init(bars.raw_full(s), 1);
-      mbar_init(bars.raw_empty(s), 8 + 1);  // 8 worker warps + the MMA commit (weights)
+      mbar_init(bars.raw_empty(s), TC_CONV_WARPS + 1);  // converters + the MMA commit (weights)
     }
     for (int c = 0; c < TC_NC; c++) {
-      mbar_init(bars.conv_full(c), 8);
+      mbar_init(bars.conv_full(c), TC_CONV_WARPS);
       mbar_init(bars.conv_empty(c), 1);
     }
-    for (int a = 0; a < 2; a++) {
+    for (int a = 0; a < TC_NA; a++) {
       mbar_init(bars.acc_full(a), 1);
-      mbar_init(bars.acc_empty(a), 8);
+      mbar_init(bars.acc_empty(a), TC_DRAIN_WARPS);
     }
     mbar_init(bars.fin(), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -197,17 +223,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                  "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (warp >= 2) {
+  if (warp >= 2 && warp < 2 + TC_CONV_WARPS) {
     // Constant operands of the init MMA: A[m][0] = 256, B[0][n] = 32768, so
     // D = 2^23 everywhere; every other entry 0.
-    const int wi = tid - 64;
+    const int wi = tid - 64, nw = 32 * TC_CONV_WARPS;
     uint32_t* ac = reinterpret_cast<uint32_t*>(sm + SM_ACONST);
     // A K-major: entry (m, k = 0) at byte m * 16 of the first 2 KB (k < 8).
-    for (int i = wi; i < 1024; i += 256) ac[i] = (i < 512 && (i & 3) == 0) ? 0x5C00u : 0u;
+    for (int i = wi; i < 1024; i += nw) ac[i] = (i < 512 && (i & 3) == 0) ? 0x5C00u : 0u;
     // B MN-major: row k = 0 is bytes [0, 16) of each 128-byte core matrix of
     // the first 512 bytes (k < 8).
     uint32_t* bc = reinterpret_cast<uint32_t*>(sm + SM_BCONST);
-    for (int i = wi; i < 256; i += 256) bc[i] = (i < 128 && (i & 31) < 4) ? 0x78007800u : 0u;
+    for (int i = wi; i < 256; i += nw) bc[i] = (i < 128 && (i & 31) < 4) ? 0x78007800u : 0u;
     fence_proxy_async_smem();
   }
   tc_fence_before();
@@ -242,7 +268,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             ok = false;
             break;
           }
-          hdr[slot] = StageHdr{done ? -1 : tile, st, nst, K.mode};
+          hdr[s % TC_HR] = StageHdr{done ? -1 : tile, st, nst, K.mode};
           last_use[slot] = use;
           const uint32_t raw = base + SM_RAW + slot * 20480;
           if (done) {
@@ -273,16 +299,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       bool issued = false;
       for (int s = 0;; s++) {
-        const int c = s % TC_NC, slot = s % TC_NR, a = s & 1;
+        const int c = s % TC_NC, slot = s % TC_NR, a = s % TC_NA;
         if (!mbar_wait_for(bars.conv_full(c), (s / TC_NC) & 1, wait_ns)) {
           ok = false;
           break;
         }
-        const StageHdr h = hdr[slot];
-        if (h.tile < 0) break;
-        if (s >= 2 && !mbar_wait_for(bars.acc_empty(a), ((s >> 1) - 1) & 1, wait_ns)) {
+        const StageHdr h = hdr[s % TC_HR];
+        if (s >= TC_NA && !mbar_wait_for(bars.acc_empty(a), ((s / TC_NA) - 1) & 1, wait_ns)) {
           ok = false;
           mark_timeout(proofs, tasks, tiles, h.tile);
+          break;
+        }
+        if (h.tile < 0) {
+          umma_commit(bars.acc_full(a));  // tells the drainers: no more stages
           break;
         }
         tc_fence_after();
@@ -307,76 +336,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_wait_for(bars.fin(), 0, wait_ns);
       }
     }
-  } else {
-    // ---------------------------------------------------------------- workers
-    const int wi = tid - 64, grp = (warp - 2) >> 2, quarter = warp & 3;
-    const int line = 32 * quarter + lane;
-    const uint32_t tq = tmem + ((uint32_t)(32 * quarter) << 16);
-    uint32_t dg[17];
-#pragma unroll
-    for (int t = 0; t < 17; t++) dg[t] = 0;
-    StageHdr prev{-1, 0, 0, 0};
-    int s = 0;
-    // Drain stage sd's accumulator into the digit sums; finish the tile after
-    // its last stage.
-    auto drain = [&](int sd, const StageHdr& h) -> bool {
-      const int a = sd & 1;
-      if (!warp_wait(bars.acc_full(a), (sd >> 1) & 1, wait_ns)) return false;
-      tc_fence_after();
-      const uint32_t ta = tq + 64 * a;
-      if (grp == 0) {
-        uint32_t L[32], H[16];
-        tmem_ld32(ta, L);
-        tmem_ld16(ta + 32, H);
-        tmem_wait_ld();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bars.acc_empty(a));
-        dg[0] += L[0];
-#pragma unroll
-        for (int t = 1; t < 17; t++) dg[t] += fbits_add(L[t], H[t - 1]);
-      } else {
-        uint32_t L[16], H[16];
-        tmem_ld16(ta + 16, L);
-        tmem_ld16(ta + 48, H);
-        tmem_wait_ld();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bars.acc_empty(a));
-#pragma unroll
-        for (int t = 17; t < 32; t++) dg[t - 17] += fbits_add(L[t - 16], H[t - 17]);
-        dg[15] += fbits_add(H[15], 0x4B000000u);  // s_32 + 2^23
-      }
-      if (h.stage == h.nst - 1) {
-        const TcTile T = tiles[h.tile];
-        if (line < T.nw) {
-          const FoldTask& K = tasks[T.task];
-          const DevProof& P = proofs[K.proof];
-          unsigned long long* acc = (K.side ? P.accB : P.accA) + (size_t)(T.w0 + line) * 8;
-          tc_epilogue(grp, dg, h.nst, acc);
-        }
-#pragma unroll
-        for (int t = 0; t < 17; t++) dg[t] = 0;
-      }
-      return true;
-    };
-    for (;; s++) {
+  } else if (warp < 2 + TC_CONV_WARPS) {
+    // ---------------------------------------------------------------- converters
+    constexpr int NCT = 32 * TC_CONV_WARPS;
+    const int wi = tid - 64;
+    for (int s = 0;; s++) {
       const int slot = s % TC_NR, c = s % TC_NC;
       if (!warp_wait(bars.raw_full(slot), (s / TC_NR) & 1, wait_ns)) {
         ok = false;
         break;
       }
-      const StageHdr h = hdr[slot];
+      const StageHdr h = hdr[s % TC_HR];
       if (s >= TC_NC && !warp_wait(bars.conv_empty(c), ((s / TC_NC) - 1) & 1, wait_ns)) {
         ok = false;
+        mark_timeout(proofs, tasks, tiles, h.tile);
         break;
       }
       if (h.tile >= 0) {
         const uint8_t* raw = sm + SM_RAW + slot * 20480;
         uint8_t* lo = sm + SM_CONV + c * 32768;
 #pragma unroll
-        for (int it = 0; it < 4; it++) {
-          const int q = it * 256 + wi, r8 = q & 7, rest = q >> 3;
+        for (int it = 0; it < 1024 / NCT; it++) {
+          const int q = it * NCT + wi, r8 = q & 7, rest = q >> 3;
           int src, dst;
           if (h.mode == MODE_ROWDOT) {
             const int kc = rest & 7, mg = rest >> 3, m = mg * 8 + r8;
@@ -403,14 +384,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (h.tile >= 0) mbar_arrive(bars.raw_empty(slot));
       }
       if (h.tile < 0) break;
-      if (s > 0 && !drain(s - 1, prev)) {
+    }
+  } else {
+    // ---------------------------------------------------------------- drainers
+    const int grp = (warp - 2 - TC_CONV_WARPS) >> 2, quarter = warp & 3;
+    const int line = 32 * quarter + lane;
+    const uint32_t tq = tmem + ((uint32_t)(32 * quarter) << 16);
+    uint32_t dg[17];
+#pragma unroll
+    for (int t = 0; t < 17; t++) dg[t] = 0;
+    for (int s = 0;; s++) {
+      const int a = s % TC_NA;
+      if (!warp_wait(bars.acc_full(a), (s / TC_NA) & 1, wait_ns)) {
         ok = false;
-        mark_timeout(proofs, tasks, tiles, prev.tile);
         break;
       }
-      prev = h;
+      const StageHdr h = hdr[s % TC_HR];
+      if (h.tile < 0) break;
+      tc_fence_after();
+      const uint32_t ta = tq + 64 * a;
+      if (grp == 0) drain_digits<0, 16>(ta, dg, bars.acc_empty(a));
+      else drain_digits<17, 32>(ta, dg, bars.acc_empty(a));
+      if (h.stage == h.nst - 1) {
+        const TcTile T = tiles[h.tile];
+        if (line < T.nw) {
+          const FoldTask& K = tasks[T.task];
+          const DevProof& P = proofs[K.proof];
+          unsigned long long* acc = (K.side ? P.accB : P.accA) + (size_t)(T.w0 + line) * 8;
+          if (grp == 0) tc_epilogue<0, 16>(dg, h.nst, acc);
+          else tc_epilogue<17, 32>(dg, h.nst, acc);
+        }
+#pragma unroll
+        for (int t = 0; t < 17; t++) dg[t] = 0;
+      }
     }
-    if (ok && s > 0 && !drain(s - 1, prev)) mark_timeout(proofs, tasks, tiles, prev.tile);
+    if (!ok) mark_timeout(proofs, tasks, tiles, -1);
   }
 
   tc_fence_before();
