@@ -3,6 +3,8 @@
 Each translation unit in csrc/ is compiled by its own nvcc process (in
 parallel), then linked into paper_2508_21393_gb300/_lib/libverilora.so.
 Usage: python -m paper_2508_21393_gb300.build [--ptxas-verbose] [--debug]
+Extra nvcc flags (e.g. -DTC_NR=6 to size a pipeline ring) may be given in
+the environment variable VL_NVCC_FLAGS.
 """
 
 import argparse
@@ -48,6 +50,7 @@ def build(ptxas_verbose=False, debug=False, quiet=False):
         extra += ["-Xptxas", "-v"]
     if debug:
         extra += ["-DVL_DEBUG=1"]
+    extra += os.environ.get("VL_NVCC_FLAGS", "").split()
     srcs = sources()
     with ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         results = list(ex.map(lambda s: compile_one(s, extra), srcs))

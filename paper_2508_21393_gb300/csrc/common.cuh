@@ -103,12 +103,21 @@ static constexpr int TC_KS = 64;        // reduction entries per pipeline stage
 static constexpr int TC_SEG = 16384;    // reduction entries per tile at most
 static constexpr int TC_CONV_WARPS = 8;   // int16 -> fp16 byte operands
 static constexpr int TC_DRAIN_WARPS = 8;  // TMEM -> digit sums (two groups of four lane quarters)
-static constexpr int TC_THREADS = 64 + 32 * (TC_CONV_WARPS + TC_DRAIN_WARPS);  // + producer, MMA warps
-static constexpr int TC_NR = 5;         // raw (TMA) stages
-static constexpr int TC_NC = 3;         // converted-operand stages
-static constexpr int TC_NA = 4;         // TMEM accumulator buffers
-static constexpr int TC_HR = 16;        // stage-header ring (> TC_NR + TC_NC + TC_NA)
-static constexpr int TC_SMEM = 1024 + TC_NC * 32768 + TC_NR * 20480 + 4096 + 1024 + 1024;
+// warp 0 producer, warp 1 lo-MMA issuer (TMEM owner), then converters,
+// drainers, and the hi-MMA issuer last
+static constexpr int TC_THREADS = 96 + 32 * (TC_CONV_WARPS + TC_DRAIN_WARPS);
+// Ring depths (overridable at build time for tuning sweeps).
+#ifndef TC_NR
+#define TC_NR 8  // operand (TMA) stages, 16 KB of shared memory each
+#endif
+#ifndef TC_NW
+#define TC_NW 8  // weight stages, 4 KB each
+#endif
+static constexpr int TC_NC = 4;   // converted-operand stages (TMEM, 64 columns each)
+static constexpr int TC_NA = 4;   // accumulator buffers (TMEM, 64 columns each)
+static constexpr int TC_HR = 32;  // stage-header ring (> TC_NR + TC_NC + TC_NA)
+static_assert(TC_HR > TC_NR + TC_NC + TC_NA, "header ring");
+static constexpr int TC_SMEM = 1024 + TC_NR * 16384 + TC_NW * 4096 + 1024 + 1024;
 
 struct FoldTile {
   int32_t task;

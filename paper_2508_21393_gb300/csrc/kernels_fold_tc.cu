@@ -1,61 +1,66 @@
-// Tensor-core fold of int16 operands (tcgen05.mma with TMEM accumulators,
-// TMA tensor copies, mbarrier pipelines).
+// Tensor-core fold of int16 operands (tcgen05.mma with TMEM operands and
+// accumulators, TMA tensor copies, mbarrier pipelines).
 //
 // The fold f[w] = sum_i E_i . x[i, w] (Sec. II-C: A~(u, w) is the eq-weighted
 // sum of column w; row dots likewise) is an integer matrix-vector product with
 // 255-bit weights.  Write each weight as 32 bytes, E_i = sum_b 2^(8b) e[i, b],
 // and each offset entry p = x + 2^15 (in [0, 2^16)) as two bytes,
 // p = lo + 2^8 hi.  Then
-//     D_lo[w, b] = sum_i lo[i, w] e[i, b],   D_hi[w, b] = sum_i hi[i, w] e[i, b]
+//     D_lo[w, b] = sum_i lo[w, i] e[i, b],   D_hi[w, b] = sum_i hi[w, i] e[i, b]
 // are two dense products (M = 128 lines w, N = 32 bytes b, K = the reduced
 // index i), and
-//     sum_i E_i p[i, w] = sum_{t=0}^{32} 2^(8t) s_t,  s_t = D_lo[w, t] + D_hi[w, t-1].
+//     sum_i E_i p[w, i] = sum_{t=0}^{32} 2^(8t) s_t,  s_t = D_lo[w, t] + D_hi[w, t-1].
 // All operands are integers in [0, 255] (exact in fp16); a product is at most
-// 255^2, so one 64-entry stage sums to less than 2^22 and fp32 accumulation is
-// exact.  The lo accumulator of each stage starts at 2^23 (one MMA of
-// constants), so D_lo + D_hi = 2^23 + s_t lies in [2^23, 2^24) and its fp32 bit
-// pattern is 0x4B000000 + s_t: workers add the bit patterns as 32-bit integers
-// and remove the offsets once per tile.  At the end of a tile the 33 digit
-// sums become the eight 64-bit column sums sum_j 2^(32j) col_j of the
+// 255^2, so over one 64-entry stage D_lo + D_hi < 2^23 and fp32 accumulation
+// is exact.  Adding 2^23 puts the sum in [2^23, 2^24), where the fp32 bit
+// pattern is 0x4B000000 + s_t: the drainers add bit patterns as 32-bit
+// integers and remove the offsets once per tile.  At the end of a tile the 33
+// digit sums become the eight 64-bit column sums sum_j 2^(32j) col_j of the
 // CUDA-core fold (col_7 also takes s_32 . 2^32), added with red.add, so the
 // rounds reduce them unchanged (Montgomery reduction, minus 2^15 . sum E).
 //
 // Roles in a CTA (one CTA per SM; tiles come from a global counter, longest
 // first), each running at its own pace and linked only by mbarriers:
 //   warp 0       producer: per stage one 128B-swizzled TMA box of the operand
-//                (two for column sums) and the stage's 4 KB of fp16 weight
-//                bytes, into one of TC_NR raw slots
-//   warp 1       owns TMEM; per stage one init MMA and 4 + 4 MMAs (K = 16)
-//                into one of TC_NA accumulator buffers
-//   warps 2-9    converters: int16 box -> fp16 lo/hi operand tiles in one of
-//                TC_NC slots (canonical core-matrix layout, no swizzle;
-//                K-major for row dots, MN-major for column sums)
+//                (two for column sums) into one of TC_NR shared-memory slots,
+//                and the stage's 4 KB of fp16 weight bytes into one of TC_NW
+//   warps 1, 18 MMA issuers (warp 1 also owns TMEM, 512 columns): per stage
+//                each issues 4 MMAs (K = 16), warp 1 the lo and warp 18 the
+//                hi products, with A read from TMEM and B (weights) from
+//                shared memory, into one of TC_NA accumulator buffers (one
+//                thread issues an MMA only every ~60 cycles, two keep the
+//                tensor core busy)
+//   warps 2-9    converters: one thread per (line, half of the stage's 64
+//                entries) reads its entries from the swizzled box, forms the
+//                fp16 lo/hi operand rows and stores them to TMEM (one of
+//                TC_NC operand buffers) with tcgen05.st
 //   warps 10-17  drainers: accumulator buffer -> per-line digit sums (two
 //                groups of four warps, one warp per TMEM lane quarter, each
 //                group half of the 33 digits); tile epilogue
-// Stage headers (tile, stage) sit in a ring of TC_HR entries, longer than
-// the stages any role can be ahead of another.
-// Every wait is bounded; a wait that runs out marks the proof VL_ETIMEOUT, and
-// the CTA drains its copies and MMAs before it frees TMEM and returns.
+// TMEM columns: accumulator a at 64a ([lo 32 | hi 32]), operand buffer c at
+// 256 + 64c ([lo 32 | hi 32], two fp16 per column).  Stage headers (tile,
+// stage) sit in a ring of TC_HR entries, longer than the stages any role can
+// be ahead of another.  Every wait is bounded; a wait that runs out marks the
+// proof VL_ETIMEOUT, and the CTA drains its copies and MMAs before it frees
+// TMEM and returns.
 #include "fold_dev.cuh"
 
 namespace vl {
 namespace {
 
-constexpr int SM_CONV = 0;                         // TC_NC x 32 KB: [lo 16 KB | hi 16 KB]
-constexpr int SM_RAW = SM_CONV + TC_NC * 32768;    // TC_NR x 20 KB: [operand 16 KB | weights 4 KB]
-constexpr int SM_ACONST = SM_RAW + TC_NR * 20480;  // 128 x 16 fp16, K-major
-constexpr int SM_BCONST = SM_ACONST + 4096;        // 16 x 32 fp16, MN-major
-constexpr int SM_HDR = SM_BCONST + 1024;           // TC_HR stage headers
+constexpr int SM_RAW = 0;                          // TC_NR x 16 KB of int16 operand
+constexpr int SM_W = SM_RAW + TC_NR * 16384;       // TC_NW x 4 KB of fp16 weight bytes
+constexpr int SM_HDR = SM_W + TC_NW * 4096;        // TC_HR stage headers
 constexpr int SM_BAR = SM_HDR + TC_HR * 16;
-constexpr int NBAR = 2 * TC_NR + 2 * TC_NC + 2 * TC_NA + 1;
+constexpr int NBAR = 2 * TC_NR + 2 * TC_NC + 2 * TC_NA + 2 * TC_NW + 1;
 constexpr int SM_TMEM = SM_BAR + NBAR * 8;
 static_assert(SM_TMEM + 16 <= TC_SMEM - 1024, "shared-memory layout");
-constexpr uint32_t TMEM_COLS = 64 * TC_NA;  // TC_NA buffers of [lo 32 | hi 32] fp32 columns
-static_assert(TMEM_COLS == 256, "TMEM allocation is a power of two");
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t ACONV_COL = 64 * TC_NA;
+static_assert(ACONV_COL + 64 * TC_NC <= TMEM_COLS, "TMEM columns");
 
 // Instruction descriptor of kind::f16: fp32 accumulator, fp16 A and B,
-// B MN-major, N = 32, M = 128; bit 15 selects an MN-major A.
+// A K-major (from TMEM), B MN-major, N = 32, M = 128.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 16) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 
 // Shared-memory matrix descriptor, no swizzle: core matrices of 8 x 16 bytes
@@ -66,11 +71,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
          ((uint64_t)((sbo >> 4) & 0x3fff) << 32) | (1ull << 46);
 }
 
-__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+// D (TMEM) (+)= A (TMEM, 128 lanes x 8 columns) . B (shared memory).
+__device__ __forceinline__ void umma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d),
+      "r"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
 // Arrive on `bar` once every MMA this thread issued so far has completed.
@@ -93,6 +99,17 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[32]) {
 }
 #undef TC_R8
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 16 consecutive columns of this warp's lane quarter from r[0..15].
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Two fp16 values from bytes of t selected by `sel` (bytes 0x64 fill the
 // high halves): 0x64bb is 1024 + bb exactly, minus 1024 leaves bb.
@@ -128,7 +145,9 @@ struct TcBars {
   __device__ uint32_t conv_empty(int c) const { return b + 8 * (2 * TC_NR + TC_NC + c); }
   __device__ uint32_t acc_full(int a) const { return b + 8 * (2 * TC_NR + 2 * TC_NC + a); }
   __device__ uint32_t acc_empty(int a) const { return b + 8 * (2 * TC_NR + 2 * TC_NC + TC_NA + a); }
-  __device__ uint32_t fin() const { return b + 8 * (2 * TC_NR + 2 * TC_NC + 2 * TC_NA); }
+  __device__ uint32_t w_full(int w) const { return b + 8 * (2 * TC_NR + 2 * TC_NC + 2 * TC_NA + w); }
+  __device__ uint32_t w_empty(int w) const { return b + 8 * (2 * TC_NR + 2 * TC_NC + 2 * TC_NA + TC_NW + w); }
+  __device__ uint32_t fin() const { return b + 8 * (2 * TC_NR + 2 * TC_NC + 2 * TC_NA + 2 * TC_NW); }
 };
 
 __device__ __forceinline__ void mark_timeout(const DevProof* proofs, const FoldTask* tasks, const TcTile* tiles,
@@ -138,7 +157,7 @@ __device__ __forceinline__ void mark_timeout(const DevProof* proofs, const FoldT
 
 // Drain one stage's accumulator columns (lo at ta, hi at ta + 32) into the
 // digit sums s_t, t in [T0, T1]:  dg[t - T0] += bits(2^23 + s_t), with
-// s_t = lo_t + hi_{t-1} (the lo accumulator starts at 2^23).
+// s_t = lo_t + hi_{t-1}.
 template <int T0, int T1>
 __device__ __forceinline__ void drain_digits(uint32_t ta, uint32_t (&dg)[17], uint32_t acc_empty) {
   constexpr int LA = T0, LB = T1 < 31 ? T1 : 31;           // lo columns used
@@ -159,9 +178,9 @@ __device__ __forceinline__ void drain_digits(uint32_t ta, uint32_t (&dg)[17], ui
 #pragma unroll
   for (int t = T0; t <= T1; t++) {
     uint32_t v;
-    if (t == 0) v = L[0];
+    if (t == 0) v = fbits_add(L[0], 0x4B000000u);
     else if (t == 32) v = fbits_add(H[31], 0x4B000000u);
-    else v = fbits_add(L[t], H[t - 1]);
+    else v = fbits_add(fbits_add(L[t], H[t - 1]), 0x4B000000u);  // both sums exact below 2^24
     dg[t - T0] += v;
   }
 }
@@ -205,36 +224,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (tid == 0) {
     for (int s = 0; s < TC_NR; s++) {
       mbar_init(bars.raw_full(s), 1);
-      mbar_init(bars.raw_empty(s), TC_CONV_WARPS + 1);  // converters + the MMA commit (weights)
+      mbar_init(bars.raw_empty(s), TC_CONV_WARPS);
     }
+    // operand, weight and accumulator releases wait for both MMA issuers
     for (int c = 0; c < TC_NC; c++) {
       mbar_init(bars.conv_full(c), TC_CONV_WARPS);
-      mbar_init(bars.conv_empty(c), 1);
+      mbar_init(bars.conv_empty(c), 2);
     }
     for (int a = 0; a < TC_NA; a++) {
-      mbar_init(bars.acc_full(a), 1);
+      mbar_init(bars.acc_full(a), 2);
       mbar_init(bars.acc_empty(a), TC_DRAIN_WARPS);
     }
-    mbar_init(bars.fin(), 1);
+    for (int w = 0; w < TC_NW; w++) {
+      mbar_init(bars.w_full(w), 1);
+      mbar_init(bars.w_empty(w), 2);
+    }
+    mbar_init(bars.fin(), 2);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(base + SM_TMEM),
                  "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (warp >= 2 && warp < 2 + TC_CONV_WARPS) {
-    // Constant operands of the init MMA: A[m][0] = 256, B[0][n] = 32768, so
-    // D = 2^23 everywhere; every other entry 0.
-    const int wi = tid - 64, nw = 32 * TC_CONV_WARPS;
-    uint32_t* ac = reinterpret_cast<uint32_t*>(sm + SM_ACONST);
-    // A K-major: entry (m, k = 0) at byte m * 16 of the first 2 KB (k < 8).
-    for (int i = wi; i < 1024; i += nw) ac[i] = (i < 512 && (i & 3) == 0) ? 0x5C00u : 0u;
-    // B MN-major: row k = 0 is bytes [0, 16) of each 128-byte core matrix of
-    // the first 512 bytes (k < 8).
-    uint32_t* bc = reinterpret_cast<uint32_t*>(sm + SM_BCONST);
-    for (int i = wi; i < 256; i += nw) bc[i] = (i < 128 && (i & 31) < 4) ? 0x78007800u : 0u;
-    fence_proxy_async_smem();
   }
   tc_fence_before();
   __syncthreads();
@@ -245,9 +256,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
     if (lane == 0) {
-      int last_use[TC_NR];
+      int last_use[TC_NR], last_wuse[TC_NW];
 #pragma unroll
       for (int i = 0; i < TC_NR; i++) last_use[i] = -1;
+#pragma unroll
+      for (int i = 0; i < TC_NW; i++) last_wuse[i] = -1;
       int s = 0, tile = -1;
       for (bool done = false; !done && ok;) {
         tile = atomicAdd(counter, 1);
@@ -263,43 +276,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         const int nst = done ? 1 : (T.nk + TC_KS - 1) / TC_KS;
         for (int st = 0; st < nst; st++, s++) {
-          const int slot = s % TC_NR, use = s / TC_NR;
+          const int slot = s % TC_NR, use = s / TC_NR, ws = s % TC_NW, wuse = s / TC_NW;
           if (use > 0 && !mbar_wait_for(bars.raw_empty(slot), (use - 1) & 1, wait_ns)) {
             ok = false;
             break;
           }
           hdr[s % TC_HR] = StageHdr{done ? -1 : tile, st, nst, K.mode};
           last_use[slot] = use;
-          const uint32_t raw = base + SM_RAW + slot * 20480;
+          const uint32_t raw = base + SM_RAW + slot * 16384;
           if (done) {
             mbar_arrive(bars.raw_full(slot));
             break;
           }
+          if (wuse > 0 && !mbar_wait_for(bars.w_empty(ws), (wuse - 1) & 1, wait_ns)) {
+            ok = false;
+            break;
+          }
           const int kk = T.k0 + st * TC_KS;
+          mbar_arrive_expect_tx(bars.w_full(ws), 4096);
+          bulk_g2s(base + SM_W + ws * 4096, reinterpret_cast<const uint8_t*>(w8) + (size_t)(kk / TC_KS) * 4096, 4096,
+                   bars.w_full(ws));
+          last_wuse[ws] = wuse;
           if (K.mode == MODE_ROWDOT) {
-            mbar_arrive_expect_tx(bars.raw_full(slot), 16384 + 4096);
+            mbar_arrive_expect_tx(bars.raw_full(slot), 16384);
             tma_load_2d(raw, K.tmap, kk, T.w0, bars.raw_full(slot));
           } else {
             const bool two = T.nw > 64;
-            mbar_arrive_expect_tx(bars.raw_full(slot), (two ? 16384 : 8192) + 4096);
+            mbar_arrive_expect_tx(bars.raw_full(slot), two ? 16384 : 8192);
             tma_load_2d(raw, K.tmap, T.w0, kk, bars.raw_full(slot));
             if (two) tma_load_2d(raw + 8192, K.tmap, T.w0 + 64, kk, bars.raw_full(slot));
           }
-          bulk_g2s(raw + 16384, reinterpret_cast<const uint8_t*>(w8) + (size_t)(kk / TC_KS) * 4096, 4096,
-                   bars.raw_full(slot));
         }
       }
       if (!ok) mark_timeout(proofs, tasks, tiles, tile < ntiles ? tile : -1);
       // Copies still in flight must land before the CTA leaves.
       for (int i = 0; i < TC_NR; i++)
         if (last_use[i] >= 0) mbar_wait_for(bars.raw_full(i), last_use[i] & 1, wait_ns);
+      for (int i = 0; i < TC_NW; i++)
+        if (last_wuse[i] >= 0) mbar_wait_for(bars.w_full(i), last_wuse[i] & 1, wait_ns);
     }
-  } else if (warp == 1) {
-    // ---------------------------------------------------------------- MMA
+  } else if (warp == 1 || warp == TC_THREADS / 32 - 1) {
+    // ---------------------------------------------------------------- MMA issuers
     if (lane == 0) {
-      bool issued = false;
+      const uint32_t half = warp == 1 ? 0 : 32;  // lo or hi: A and D column offset
       for (int s = 0;; s++) {
-        const int c = s % TC_NC, slot = s % TC_NR, a = s % TC_NA;
+        const int c = s % TC_NC, a = s % TC_NA;
         if (!mbar_wait_for(bars.conv_full(c), (s / TC_NC) & 1, wait_ns)) {
           ok = false;
           break;
@@ -314,32 +335,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           umma_commit(bars.acc_full(a));  // tells the drainers: no more stages
           break;
         }
+        const int ws = s % TC_NW;
+        if (!mbar_wait_for(bars.w_full(ws), (s / TC_NW) & 1, wait_ns)) {
+          ok = false;
+          mark_timeout(proofs, tasks, tiles, h.tile);
+          break;
+        }
         tc_fence_after();
-        const uint32_t idesc = IDESC | (h.mode == MODE_COLSUM ? (1u << 15) : 0u);
-        const uint32_t conv = base + SM_CONV + c * 32768;
-        const uint32_t wts = base + SM_RAW + slot * 20480 + 16384;
-        const uint32_t dlo = tmem + 64 * a, dhi = dlo + 32;
-        umma(dlo, sdesc(base + SM_ACONST, 2048, 128), sdesc(base + SM_BCONST, 512, 128), IDESC, 0);
+        const uint32_t wts = base + SM_W + ws * 4096;
+        const uint32_t d = tmem + 64 * a + half, av = tmem + ACONV_COL + 64 * c + half;
 #pragma unroll
-        for (int ks = 0; ks < 4; ks++)
-          umma(dlo, sdesc(conv + ks * 4096, 2048, 128), sdesc(wts + ks * 1024, 512, 128), idesc, 1);
-#pragma unroll
-        for (int ks = 0; ks < 4; ks++)
-          umma(dhi, sdesc(conv + 16384 + ks * 4096, 2048, 128), sdesc(wts + ks * 1024, 512, 128), idesc, ks > 0);
+        for (int ks = 0; ks < 4; ks++) umma_ts(d, av + 8 * ks, sdesc(wts + ks * 1024, 512, 128), IDESC, ks > 0);
         umma_commit(bars.conv_empty(c));
-        umma_commit(bars.raw_empty(slot));
+        umma_commit(bars.w_empty(ws));
         umma_commit(bars.acc_full(a));
-        issued = true;
       }
-      if (issued) {
-        umma_commit(bars.fin());
-        mbar_wait_for(bars.fin(), 0, wait_ns);
-      }
+      // every MMA this thread issued has completed before TMEM is freed
+      umma_commit(bars.fin());
+      mbar_wait_for(bars.fin(), 0, wait_ns);
     }
   } else if (warp < 2 + TC_CONV_WARPS) {
     // ---------------------------------------------------------------- converters
-    constexpr int NCT = 32 * TC_CONV_WARPS;
-    const int wi = tid - 64;
+    // Thread = line m (its TMEM lane) x half kh of the stage's 64 entries.
+    const int quarter = warp & 3, kh = (warp - 2) >> 2;
+    const int m = 32 * quarter + lane;
+    const uint32_t tq = tmem + ((uint32_t)(32 * quarter) << 16) + ACONV_COL + 16 * kh;
     for (int s = 0;; s++) {
       const int slot = s % TC_NR, c = s % TC_NC;
       if (!warp_wait(bars.raw_full(slot), (s / TC_NR) & 1, wait_ns)) {
@@ -353,31 +373,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       if (h.tile >= 0) {
-        const uint8_t* raw = sm + SM_RAW + slot * 20480;
-        uint8_t* lo = sm + SM_CONV + c * 32768;
+        const uint8_t* raw = sm + SM_RAW + slot * 16384;
+        uint32_t w[16];  // entries 32 kh + 2i, 32 kh + 2i + 1 of line m
+        if (h.mode == MODE_ROWDOT) {
+          // box [128 lines][64 entries]: chunk j of line m at 16 (j ^ (m % 8))
 #pragma unroll
-        for (int it = 0; it < 1024 / NCT; it++) {
-          const int q = it * NCT + wi, r8 = q & 7, rest = q >> 3;
-          int src, dst;
-          if (h.mode == MODE_ROWDOT) {
-            const int kc = rest & 7, mg = rest >> 3, m = mg * 8 + r8;
-            src = m * 128 + ((kc ^ r8) << 4);
-            dst = kc * 2048 + mg * 128 + r8 * 16;
-          } else {
-            const int mc = rest & 15, kg = rest >> 4, k = kg * 8 + r8;
-            src = (mc >> 3) * 8192 + k * 128 + (((mc & 7) ^ r8) << 4);
-            dst = kg * 2048 + mc * 128 + r8 * 16;
+          for (int j = 0; j < 4; j++) {
+            const uint4 v = *reinterpret_cast<const uint4*>(raw + m * 128 + (((4 * kh + j) ^ (m & 7)) << 4));
+            w[4 * j] = v.x; w[4 * j + 1] = v.y; w[4 * j + 2] = v.z; w[4 * j + 3] = v.w;
           }
-          const uint4 x = *reinterpret_cast<const uint4*>(raw + src);
-          const uint32_t t0 = x.x ^ 0x80008000u, t1 = x.y ^ 0x80008000u, t2 = x.z ^ 0x80008000u,
-                         t3 = x.w ^ 0x80008000u;
-          *reinterpret_cast<uint4*>(lo + dst) = make_uint4(bytes_f16x2(t0, 0x4240), bytes_f16x2(t1, 0x4240),
-                                                           bytes_f16x2(t2, 0x4240), bytes_f16x2(t3, 0x4240));
-          *reinterpret_cast<uint4*>(lo + 16384 + dst) = make_uint4(
-              bytes_f16x2(t0, 0x4341), bytes_f16x2(t1, 0x4341), bytes_f16x2(t2, 0x4341), bytes_f16x2(t3, 0x4341));
+        } else {
+          // two boxes [64 entries][64 lines]: line m of entry k at
+          // 8192 (m / 64) + 128 k + 16 ((m % 64 / 8) ^ (k % 8)) + 2 (m % 8)
+          const uint8_t* col = raw + (m >> 6) * 8192 + (m & 7) * 2;
+          const int mc = (m & 63) >> 3;
+#pragma unroll
+          for (int i = 0; i < 16; i++) {
+            const int k = 32 * kh + 2 * i;
+            const uint32_t a = *reinterpret_cast<const uint16_t*>(col + k * 128 + ((mc ^ (k & 7)) << 4));
+            const uint32_t b = *reinterpret_cast<const uint16_t*>(col + (k + 1) * 128 + ((mc ^ ((k + 1) & 7)) << 4));
+            w[i] = a | (b << 16);
+          }
         }
-        fence_proxy_async_smem();
+        uint32_t lo[16], hi[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+          const uint32_t t = w[i] ^ 0x80008000u;  // p = x + 2^15, per entry
+          lo[i] = bytes_f16x2(t, 0x4240);
+          hi[i] = bytes_f16x2(t, 0x4341);
+        }
+        tmem_st16(tq + 64 * c, lo);
+        tmem_st16(tq + 64 * c + 32, hi);
+        tmem_wait_st();
       }
+      tc_fence_before();
       __syncwarp();
       if (lane == 0) {
         mbar_arrive(bars.conv_full(c));
