@@ -52,7 +52,13 @@ constexpr int SM_RAW = 0;                          // TC_NR x 16 KB of int16 ope
 constexpr int SM_W = SM_RAW + TC_NR * 16384;       // TC_NW x 4 KB of fp16 weight bytes
 constexpr int SM_HDR = SM_W + TC_NW * 4096;        // TC_HR stage headers
 constexpr int SM_BAR = SM_HDR + TC_HR * 16;
-constexpr int NBAR = 2 * TC_NR + 2 * TC_NC + 2 * TC_NA + 2 * TC_NW + 1;
+// Completion of stage s's MMAs (both issuers) is one barrier of a ring of
+// TC_ND: the converters (TMEM operand reuse), the producer (weight slot
+// reuse) and the drainers (accumulator ready) all wait on it.  TC_ND exceeds
+// the lead any waiter can have, so no phase is lapped.
+constexpr int TC_ND = 16;
+static_assert(TC_ND > TC_NW && TC_ND > TC_NC && TC_ND >= TC_NA, "stage-done ring");
+constexpr int NBAR = 2 * TC_NR + TC_NC + TC_NA + TC_NW + TC_ND + 1;
 constexpr int SM_TMEM = SM_BAR + NBAR * 8;
 static_assert(SM_TMEM + 16 <= TC_SMEM - 1024, "shared-memory layout");
 constexpr uint32_t TMEM_COLS = 512;
@@ -142,13 +148,13 @@ struct TcBars {
   __device__ uint32_t raw_full(int s) const { return b + 8 * s; }
   __device__ uint32_t raw_empty(int s) const { return b + 8 * (TC_NR + s); }
   __device__ uint32_t conv_full(int c) const { return b + 8 * (2 * TC_NR + c); }
-  __device__ uint32_t conv_empty(int c) const { return b + 8 * (2 * TC_NR + TC_NC + c); }
-  __device__ uint32_t acc_full(int a) const { return b + 8 * (2 * TC_NR + 2 * TC_NC + a); }
-  __device__ uint32_t acc_empty(int a) const { return b + 8 * (2 * TC_NR + 2 * TC_NC + TC_NA + a); }
-  __device__ uint32_t w_full(int w) const { return b + 8 * (2 * TC_NR + 2 * TC_NC + 2 * TC_NA + w); }
-  __device__ uint32_t w_empty(int w) const { return b + 8 * (2 * TC_NR + 2 * TC_NC + 2 * TC_NA + TC_NW + w); }
-  __device__ uint32_t fin() const { return b + 8 * (2 * TC_NR + 2 * TC_NC + 2 * TC_NA + 2 * TC_NW); }
+  __device__ uint32_t acc_empty(int a) const { return b + 8 * (2 * TC_NR + TC_NC + a); }
+  __device__ uint32_t w_full(int w) const { return b + 8 * (2 * TC_NR + TC_NC + TC_NA + w); }
+  __device__ uint32_t done(int s) const { return b + 8 * (2 * TC_NR + TC_NC + TC_NA + TC_NW + s % TC_ND); }
+  __device__ uint32_t fin() const { return b + 8 * (2 * TC_NR + TC_NC + TC_NA + TC_NW + TC_ND); }
 };
+// parity of stage s's phase on its done barrier
+__device__ __forceinline__ uint32_t done_parity(int s) { return (uint32_t)(s / TC_ND) & 1; }
 
 __device__ __forceinline__ void mark_timeout(const DevProof* proofs, const FoldTask* tasks, const TcTile* tiles,
                                              int tile) {
@@ -226,19 +232,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(bars.raw_full(s), 1);
       mbar_init(bars.raw_empty(s), TC_CONV_WARPS);
     }
-    // operand, weight and accumulator releases wait for both MMA issuers
-    for (int c = 0; c < TC_NC; c++) {
-      mbar_init(bars.conv_full(c), TC_CONV_WARPS);
-      mbar_init(bars.conv_empty(c), 2);
-    }
-    for (int a = 0; a < TC_NA; a++) {
-      mbar_init(bars.acc_full(a), 2);
-      mbar_init(bars.acc_empty(a), TC_DRAIN_WARPS);
-    }
-    for (int w = 0; w < TC_NW; w++) {
-      mbar_init(bars.w_full(w), 1);
-      mbar_init(bars.w_empty(w), 2);
-    }
+    for (int c = 0; c < TC_NC; c++) mbar_init(bars.conv_full(c), TC_CONV_WARPS);
+    for (int a = 0; a < TC_NA; a++) mbar_init(bars.acc_empty(a), TC_DRAIN_WARPS);
+    for (int w = 0; w < TC_NW; w++) mbar_init(bars.w_full(w), 1);
+    for (int d = 0; d < TC_ND; d++) mbar_init(bars.done(d), 2);  // both MMA issuers commit
     mbar_init(bars.fin(), 2);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -288,7 +285,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_arrive(bars.raw_full(slot));
             break;
           }
-          if (wuse > 0 && !mbar_wait_for(bars.w_empty(ws), (wuse - 1) & 1, wait_ns)) {
+          if (wuse > 0 && !mbar_wait_for(bars.done(s - TC_NW), done_parity(s - TC_NW), wait_ns)) {
             ok = false;
             break;
           }
@@ -332,7 +329,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           break;
         }
         if (h.tile < 0) {
-          umma_commit(bars.acc_full(a));  // tells the drainers: no more stages
+          umma_commit(bars.done(s));  // tells the drainers: no more stages
           break;
         }
         const int ws = s % TC_NW;
@@ -346,9 +343,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t d = tmem + 64 * a + half, av = tmem + ACONV_COL + 64 * c + half;
 #pragma unroll
         for (int ks = 0; ks < 4; ks++) umma_ts(d, av + 8 * ks, sdesc(wts + ks * 1024, 512, 128), IDESC, ks > 0);
-        umma_commit(bars.conv_empty(c));
-        umma_commit(bars.w_empty(ws));
-        umma_commit(bars.acc_full(a));
+        umma_commit(bars.done(s));
       }
       // every MMA this thread issued has completed before TMEM is freed
       umma_commit(bars.fin());
@@ -367,7 +362,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       const StageHdr h = hdr[s % TC_HR];
-      if (s >= TC_NC && !warp_wait(bars.conv_empty(c), ((s / TC_NC) - 1) & 1, wait_ns)) {
+      if (s >= TC_NC && !warp_wait(bars.done(s - TC_NC), done_parity(s - TC_NC), wait_ns)) {
         ok = false;
         mark_timeout(proofs, tasks, tiles, h.tile);
         break;
@@ -424,7 +419,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int t = 0; t < 17; t++) dg[t] = 0;
     for (int s = 0;; s++) {
       const int a = s % TC_NA;
-      if (!warp_wait(bars.acc_full(a), (s / TC_NA) & 1, wait_ns)) {
+      if (!warp_wait(bars.done(s), done_parity(s), wait_ns)) {
         ok = false;
         break;
       }
