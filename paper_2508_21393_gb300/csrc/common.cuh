@@ -91,21 +91,28 @@ struct FoldTask {
 
 // Tensor-core fold tile: stored lines [w0, w0 + nw) (columns for COLSUM,
 // rows for ROWDOT; nw <= 128), reduced over [k0, k0 + nk) (k0 a multiple of
-// 64, nk <= TC_SEG).
+// 64, nk <= TC_SEG).  Everything a CTA needs to stream the tile is resolved
+// at bind time, so taking a tile is one 64-byte load.
 struct TcTile {
-  int32_t task;
+  const void* tmap;         // TMA tensor map of the stored matrix (device)
+  const uint32_t* w8;       // fp16 weight-byte table of the task's side
+  unsigned long long* acc;  // accumulator rows of lines w0.. (8 per line)
+  int32_t mode;
   int32_t w0, nw;
   int32_t k0, nk;
+  int32_t proof;            // for status reports
+  int32_t task;             // host bookkeeping
   int32_t pad[3];
 };
+static_assert(sizeof(TcTile) == 64, "one 64-byte tile descriptor");
 static constexpr int TC_M = 128;        // lines per tile (MMA M)
 static constexpr int TC_KS = 64;        // reduction entries per pipeline stage
 static constexpr int TC_SEG = 16384;    // reduction entries per tile at most
 static constexpr int TC_CONV_WARPS = 8;   // int16 -> fp16 byte operands
 static constexpr int TC_DRAIN_WARPS = 8;  // TMEM -> digit sums (two groups of four lane quarters)
-// warp 0 producer, warp 1 lo-MMA issuer (TMEM owner), then converters,
-// drainers, and the hi-MMA issuer last
-static constexpr int TC_THREADS = 96 + 32 * (TC_CONV_WARPS + TC_DRAIN_WARPS);
+// warp 0 producer, warp 1 first MMA issuer (TMEM owner), then converters,
+// drainers, and the other three MMA issuers last
+static constexpr int TC_THREADS = 32 * (5 + TC_CONV_WARPS + TC_DRAIN_WARPS);
 // Ring depths (overridable at build time for tuning sweeps).
 #ifndef TC_NR
 #define TC_NR 8  // operand (TMA) stages, 16 KB of shared memory each
@@ -169,8 +176,8 @@ cudaError_t launch_fold(const FoldTask* tasks, const FoldTile* tiles, int ntiles
 // Tensor-core fold of int16 operands (fold_tc.cuh); `counter` is a zeroed
 // int the CTAs take tiles from.
 cudaError_t fold_tc_prepare();
-cudaError_t launch_fold_tc(const TcTile* tiles, int ntiles, const FoldTask* tasks, const DevProof* proofs,
-                           int* counter, unsigned long long wait_ns, cudaStream_t st);
+cudaError_t launch_fold_tc(const TcTile* tiles, int ntiles, const DevProof* proofs, int* counter,
+                           unsigned long long wait_ns, cudaStream_t st);
 cudaError_t step_set_smem(int smem_bytes);
 cudaError_t step_grid(int smem_bytes, int* grid);
 cudaError_t launch_step(const StepItem* items, int nitems, const FoldTask* tasks, const FoldTile* tiles,

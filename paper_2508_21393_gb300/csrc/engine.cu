@@ -173,7 +173,17 @@ void add_fold_task(vl_plan* p, const vl_mat& M, int32_t mode, int proof, int sid
     const int lines = mode == MODE_COLSUM ? t.cols : t.rows, red = mode == MODE_COLSUM ? t.rows : t.cols;
     for (int w0 = 0; w0 < lines; w0 += TC_M)
       for (int k0 = 0; k0 < red; k0 += TC_SEG)
-        p->tc_tiles.push_back(TcTile{task, w0, std::min(TC_M, lines - w0), k0, std::min(TC_SEG, red - k0), {}});
+      {
+        TcTile tt{};
+        tt.mode = mode;
+        tt.w0 = w0;
+        tt.nw = std::min(TC_M, lines - w0);
+        tt.k0 = k0;
+        tt.nk = std::min(TC_SEG, red - k0);
+        tt.proof = proof;
+        tt.task = task;
+        p->tc_tiles.push_back(tt);  // device pointers are filled in at bind time
+      }
     return;
   }
   tabs |= TAB_LIMBS;
@@ -546,6 +556,13 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
                              &p->etmaps[i]);
     t.bulk = ok ? 1 : 0;
   }
+  for (TcTile& tt : p->tc_tiles) {
+    const FoldTask& t = p->tasks[tt.task];
+    const DevProof& P = p->proofs[t.proof];
+    tt.tmap = t.tmap;
+    tt.w8 = t.side ? P.w8B : P.w8A;
+    tt.acc = (t.side ? P.accB : P.accA) + (size_t)tt.w0 * 8;
+  }
   cudaError_t e = cudaMemcpyAsync(ws + p->off_proofs, p->proofs.data(), sizeof(DevProof) * np,
                                   cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !p->tasks.empty())
@@ -666,7 +683,7 @@ cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t s
     const vl_plan::Group& G = p->groups[g];
     if (g > 0) e = cudaStreamWaitEvent(st, gev[g], 0);
     if (e == cudaSuccess)
-      e = launch_fold_tc(dc + G.c0, G.c1 - G.c0, dt, dp, reinterpret_cast<int*>(ws + p->off_ctl) + g, wait_ns(p), st);
+      e = launch_fold_tc(dc + G.c0, G.c1 - G.c0, dp, reinterpret_cast<int*>(ws + p->off_ctl) + g, wait_ns(p), st);
     if (e == cudaSuccess) e = launch_fold(dt, dl + G.t0, G.t1 - G.t0, dp, p->fold_smem, wait_ns(p), st);
     if (e == cudaSuccess) e = cudaEventRecord(gev[ng + g], st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(rs, gev[ng + g], 0);

@@ -24,12 +24,12 @@
 //   warp 0       producer: per stage one 128B-swizzled TMA box of the operand
 //                (two for column sums) into one of TC_NR shared-memory slots,
 //                and the stage's 4 KB of fp16 weight bytes into one of TC_NW
-//   warps 1, 18 MMA issuers (warp 1 also owns TMEM, 512 columns): per stage
-//                each issues 4 MMAs (K = 16), warp 1 the lo and warp 18 the
-//                hi products, with A read from TMEM and B (weights) from
-//                shared memory, into one of TC_NA accumulator buffers (one
-//                thread issues an MMA only every ~60 cycles, two keep the
-//                tensor core busy)
+//   warps 1, 18-20  MMA issuers (warp 1 also owns TMEM, 512 columns): a
+//                pair per stage parity, in each pair one thread for the lo
+//                and one for the hi products; 4 MMAs (K = 16) per stage and
+//                issuer, A read from TMEM and B (weights) from shared memory,
+//                into one of TC_NA accumulator buffers (one thread issues an
+//                MMA only every ~60-120 cycles; four keep the tensor core fed)
 //   warps 2-9    converters: one thread per (line, half of the stage's 64
 //                entries) reads its entries from the swizzled box, forms the
 //                fp16 lo/hi operand rows and stores them to TMEM (one of
@@ -57,6 +57,9 @@ constexpr int SM_BAR = SM_HDR + TC_HR * 16;
 // reuse) and the drainers (accumulator ready) all wait on it.  TC_ND exceeds
 // the lead any waiter can have, so no phase is lapped.
 constexpr int TC_ND = 16;
+// Issuer pairs take alternate stages: stages that share an operand, weight or
+// accumulator barrier (TC_NC, TC_NW, TC_NA apart) must belong to one pair.
+static_assert(TC_NC % 2 == 0 && TC_NW % 2 == 0 && TC_NA % 2 == 0, "ring sizes even");
 static_assert(TC_ND > TC_NW && TC_ND > TC_NC && TC_ND >= TC_NA, "stage-done ring");
 constexpr int NBAR = 2 * TC_NR + TC_NC + TC_NA + TC_NW + TC_ND + 1;
 constexpr int SM_TMEM = SM_BAR + NBAR * 8;
@@ -156,9 +159,8 @@ struct TcBars {
 // parity of stage s's phase on its done barrier
 __device__ __forceinline__ uint32_t done_parity(int s) { return (uint32_t)(s / TC_ND) & 1; }
 
-__device__ __forceinline__ void mark_timeout(const DevProof* proofs, const FoldTask* tasks, const TcTile* tiles,
-                                             int tile) {
-  atomicExch(&proofs[tasks[tiles[tile < 0 ? 0 : tile].task].proof].scr->status, VL_ETIMEOUT);
+__device__ __forceinline__ void mark_timeout(const DevProof* proofs, const TcTile* tiles, int tile) {
+  atomicExch(&proofs[tiles[tile < 0 ? 0 : tile].proof].scr->status, VL_ETIMEOUT);
 }
 
 // Drain one stage's accumulator columns (lo at ta, hi at ta + 32) into the
@@ -216,8 +218,8 @@ __device__ __forceinline__ void tc_epilogue(uint32_t (&dg)[17], int nst, unsigne
 }  // namespace
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    fold_tc_kernel(const TcTile* __restrict__ tiles, int ntiles, const FoldTask* __restrict__ tasks,
-                   const DevProof* __restrict__ proofs, int* counter, unsigned long long wait_ns) {
+    fold_tc_kernel(const TcTile* __restrict__ tiles, int ntiles, const DevProof* __restrict__ proofs, int* counter,
+                   unsigned long long wait_ns) {
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   const uint32_t raw_addr = smem_addr(tc_smem_raw);
   const uint32_t pad = ((raw_addr + 1023u) & ~1023u) - raw_addr;
@@ -235,8 +237,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int c = 0; c < TC_NC; c++) mbar_init(bars.conv_full(c), TC_CONV_WARPS);
     for (int a = 0; a < TC_NA; a++) mbar_init(bars.acc_empty(a), TC_DRAIN_WARPS);
     for (int w = 0; w < TC_NW; w++) mbar_init(bars.w_full(w), 1);
-    for (int d = 0; d < TC_ND; d++) mbar_init(bars.done(d), 2);  // both MMA issuers commit
-    mbar_init(bars.fin(), 2);
+    for (int d = 0; d < TC_ND; d++) mbar_init(bars.done(d), 2);  // the lo and hi issuers of the stage commit
+    mbar_init(bars.fin(), 4);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -258,32 +260,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int i = 0; i < TC_NR; i++) last_use[i] = -1;
 #pragma unroll
       for (int i = 0; i < TC_NW; i++) last_wuse[i] = -1;
-      int s = 0, tile = -1;
+      int s = 0;
+      int tile = atomicAdd(counter, 1);
+      TcTile T = tile < ntiles ? tiles[tile] : TcTile{};
       for (bool done = false; !done && ok;) {
-        tile = atomicAdd(counter, 1);
         done = tile >= ntiles;
-        TcTile T{};
-        FoldTask K{};
-        const uint32_t* w8 = nullptr;
-        if (!done) {
-          T = tiles[tile];
-          K = tasks[T.task];
-          const DevProof& P = proofs[K.proof];
-          w8 = K.side ? P.w8B : P.w8A;
-        }
-        const int nst = done ? 1 : (T.nk + TC_KS - 1) / TC_KS;
+        // take the next tile now: its atomic and descriptor load overlap this
+        // tile's stages
+        const int next = done ? tile : atomicAdd(counter, 1);
+        TcTile Tn{};
+        if (!done && next < ntiles) Tn = tiles[next];
+        // after the last tile, two end markers: one for each issuer pair
+        const int nst = done ? 2 : (T.nk + TC_KS - 1) / TC_KS;
         for (int st = 0; st < nst; st++, s++) {
           const int slot = s % TC_NR, use = s / TC_NR, ws = s % TC_NW, wuse = s / TC_NW;
           if (use > 0 && !mbar_wait_for(bars.raw_empty(slot), (use - 1) & 1, wait_ns)) {
             ok = false;
             break;
           }
-          hdr[s % TC_HR] = StageHdr{done ? -1 : tile, st, nst, K.mode};
+          hdr[s % TC_HR] = StageHdr{done ? -1 : tile, st, nst, T.mode};
           last_use[slot] = use;
           const uint32_t raw = base + SM_RAW + slot * 16384;
           if (done) {
             mbar_arrive(bars.raw_full(slot));
-            break;
+            continue;
           }
           if (wuse > 0 && !mbar_wait_for(bars.done(s - TC_NW), done_parity(s - TC_NW), wait_ns)) {
             ok = false;
@@ -291,32 +291,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           const int kk = T.k0 + st * TC_KS;
           mbar_arrive_expect_tx(bars.w_full(ws), 4096);
-          bulk_g2s(base + SM_W + ws * 4096, reinterpret_cast<const uint8_t*>(w8) + (size_t)(kk / TC_KS) * 4096, 4096,
-                   bars.w_full(ws));
+          bulk_g2s(base + SM_W + ws * 4096, reinterpret_cast<const uint8_t*>(T.w8) + (size_t)(kk / TC_KS) * 4096,
+                   4096, bars.w_full(ws));
           last_wuse[ws] = wuse;
-          if (K.mode == MODE_ROWDOT) {
+          if (T.mode == MODE_ROWDOT) {
             mbar_arrive_expect_tx(bars.raw_full(slot), 16384);
-            tma_load_2d(raw, K.tmap, kk, T.w0, bars.raw_full(slot));
+            tma_load_2d(raw, T.tmap, kk, T.w0, bars.raw_full(slot));
           } else {
             const bool two = T.nw > 64;
             mbar_arrive_expect_tx(bars.raw_full(slot), two ? 16384 : 8192);
-            tma_load_2d(raw, K.tmap, T.w0, kk, bars.raw_full(slot));
-            if (two) tma_load_2d(raw + 8192, K.tmap, T.w0 + 64, kk, bars.raw_full(slot));
+            tma_load_2d(raw, T.tmap, T.w0, kk, bars.raw_full(slot));
+            if (two) tma_load_2d(raw + 8192, T.tmap, T.w0 + 64, kk, bars.raw_full(slot));
           }
         }
+        if (!done) {
+          tile = next;
+          T = Tn;
+        }
       }
-      if (!ok) mark_timeout(proofs, tasks, tiles, tile < ntiles ? tile : -1);
+      if (!ok) mark_timeout(proofs, tiles, tile < ntiles ? tile : -1);
       // Copies still in flight must land before the CTA leaves.
       for (int i = 0; i < TC_NR; i++)
         if (last_use[i] >= 0) mbar_wait_for(bars.raw_full(i), last_use[i] & 1, wait_ns);
       for (int i = 0; i < TC_NW; i++)
         if (last_wuse[i] >= 0) mbar_wait_for(bars.w_full(i), last_wuse[i] & 1, wait_ns);
     }
-  } else if (warp == 1 || warp == TC_THREADS / 32 - 1) {
+  } else if (warp == 1 || warp >= TC_THREADS / 32 - 3) {
     // ---------------------------------------------------------------- MMA issuers
     if (lane == 0) {
-      const uint32_t half = warp == 1 ? 0 : 32;  // lo or hi: A and D column offset
-      for (int s = 0;; s++) {
+      const int j = warp == 1 ? 0 : warp - (TC_THREADS / 32 - 3) + 1;  // 0..3
+      const uint32_t half = (j & 1) ? 32 : 0;  // lo or hi: A and D column offset
+      for (int s = j >> 1;; s += 2) {
         const int c = s % TC_NC, a = s % TC_NA;
         if (!mbar_wait_for(bars.conv_full(c), (s / TC_NC) & 1, wait_ns)) {
           ok = false;
@@ -325,17 +330,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const StageHdr h = hdr[s % TC_HR];
         if (s >= TC_NA && !mbar_wait_for(bars.acc_empty(a), ((s / TC_NA) - 1) & 1, wait_ns)) {
           ok = false;
-          mark_timeout(proofs, tasks, tiles, h.tile);
+          mark_timeout(proofs, tiles, h.tile);
           break;
         }
         if (h.tile < 0) {
-          umma_commit(bars.done(s));  // tells the drainers: no more stages
+          umma_commit(bars.done(s));  // end marker: the drainers stop at the first one
           break;
         }
         const int ws = s % TC_NW;
         if (!mbar_wait_for(bars.w_full(ws), (s / TC_NW) & 1, wait_ns)) {
           ok = false;
-          mark_timeout(proofs, tasks, tiles, h.tile);
+          mark_timeout(proofs, tiles, h.tile);
           break;
         }
         tc_fence_after();
@@ -355,6 +360,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int quarter = warp & 3, kh = (warp - 2) >> 2;
     const int m = 32 * quarter + lane;
     const uint32_t tq = tmem + ((uint32_t)(32 * quarter) << 16) + ACONV_COL + 16 * kh;
+    int ends = 0;
     for (int s = 0;; s++) {
       const int slot = s % TC_NR, c = s % TC_NC;
       if (!warp_wait(bars.raw_full(slot), (s / TC_NR) & 1, wait_ns)) {
@@ -364,7 +370,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const StageHdr h = hdr[s % TC_HR];
       if (s >= TC_NC && !warp_wait(bars.done(s - TC_NC), done_parity(s - TC_NC), wait_ns)) {
         ok = false;
-        mark_timeout(proofs, tasks, tiles, h.tile);
+        mark_timeout(proofs, tiles, h.tile);
         break;
       }
       if (h.tile >= 0) {
@@ -407,7 +413,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_arrive(bars.conv_full(c));
         if (h.tile >= 0) mbar_arrive(bars.raw_empty(slot));
       }
-      if (h.tile < 0) break;
+      if (h.tile < 0 && ++ends == 2) break;
     }
   } else {
     // ---------------------------------------------------------------- drainers
@@ -430,11 +436,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (grp == 0) drain_digits<0, 16>(ta, dg, bars.acc_empty(a));
       else drain_digits<17, 32>(ta, dg, bars.acc_empty(a));
       if (h.stage == h.nst - 1) {
-        const TcTile T = tiles[h.tile];
-        if (line < T.nw) {
-          const FoldTask& K = tasks[T.task];
-          const DevProof& P = proofs[K.proof];
-          unsigned long long* acc = (K.side ? P.accB : P.accA) + (size_t)(T.w0 + line) * 8;
+        const int nw = tiles[h.tile].nw;
+        if (line < nw) {
+          unsigned long long* acc = tiles[h.tile].acc + (size_t)line * 8;
           if (grp == 0) tc_epilogue<0, 16>(dg, h.nst, acc);
           else tc_epilogue<17, 32>(dg, h.nst, acc);
         }
@@ -442,7 +446,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int t = 0; t < 17; t++) dg[t] = 0;
       }
     }
-    if (!ok) mark_timeout(proofs, tasks, tiles, -1);
+    if (!ok) mark_timeout(proofs, tiles, -1);
   }
 
   tc_fence_before();
@@ -464,8 +468,8 @@ cudaError_t fold_tc_prepare() {
   return e;
 }
 
-cudaError_t launch_fold_tc(const TcTile* tiles, int ntiles, const FoldTask* tasks, const DevProof* proofs,
-                           int* counter, unsigned long long wait_ns, cudaStream_t st) {
+cudaError_t launch_fold_tc(const TcTile* tiles, int ntiles, const DevProof* proofs, int* counter,
+                           unsigned long long wait_ns, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   static int sms = 0;
   if (!sms) {
@@ -475,7 +479,7 @@ cudaError_t launch_fold_tc(const TcTile* tiles, int ntiles, const FoldTask* task
     if (e != cudaSuccess) return e;
   }
   const int grid = ntiles < sms ? ntiles : sms;
-  fold_tc_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(tiles, ntiles, tasks, proofs, counter, wait_ns);
+  fold_tc_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(tiles, ntiles, proofs, counter, wait_ns);
   return cudaGetLastError();
 }
 
