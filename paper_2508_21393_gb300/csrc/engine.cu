@@ -166,8 +166,8 @@ void add_fold_task(vl_plan* p, const vl_mat& M, int32_t mode, int proof, int sid
   if (tc_eligible(p, M)) {
     // Tensor-core tiles: 128 lines by at most TC_SEG reduced entries.
     t.bulk = 2;
-    t.box_w = TC_KS;
-    t.box_h = mode == MODE_ROWDOT ? TC_M : TC_KS;
+    t.box_w = mode == MODE_ROWDOT ? TC_KS : TC_M;  // row dots: 64 entries x 128 lines (128B-swizzled)
+    t.box_h = mode == MODE_ROWDOT ? TC_M : TC_KS;  // column sums: 128 lines x 64 entries (no swizzle)
     p->tasks.push_back(t);
     tabs |= TAB_BYTES;
     const int lines = mode == MODE_COLSUM ? t.cols : t.rows, red = mode == MODE_COLSUM ? t.rows : t.cols;
@@ -485,8 +485,9 @@ bool encode_task_map(const FoldTask& t, CUtensorMap* map) {
 }
 
 // TMA descriptor of a tensor-core task's stored matrix: uint16 boxes of 64
-// columns (128 bytes, 128-byte swizzle) by 128 rows (row dots) or 64 rows
-// (column sums); out-of-range entries read as zero.
+// columns (128 bytes, 128-byte swizzle) by 128 rows for row dots, 128 columns
+// by 64 rows (no swizzle: rows of 256 contiguous bytes stream better) for
+// column sums; out-of-range entries read as zero.
 bool encode_tc_map(const FoldTask& t, CUtensorMap* map) {
   if ((reinterpret_cast<uintptr_t>(t.mat) & 15) || (t.ld & 7)) return false;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
@@ -496,8 +497,9 @@ bool encode_tc_map(const FoldTask& t, CUtensorMap* map) {
   const cuuint32_t box[2] = {(cuuint32_t)t.box_w, (cuuint32_t)t.box_h};
   const cuuint32_t estr[2] = {1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(t.mat), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+             CU_TENSOR_MAP_INTERLEAVE_NONE,
+             t.mode == MODE_ROWDOT ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // TMA descriptor of the limb-major weights a row-dot task reads: 8 rows of

@@ -21,8 +21,9 @@
 //
 // Roles in a CTA (one CTA per SM; tiles come from a global counter, longest
 // first), each running at its own pace and linked only by mbarriers:
-//   warp 0       producer: per stage one 128B-swizzled TMA box of the operand
-//                (two for column sums) into one of TC_NR shared-memory slots,
+//   warp 0       producer: per stage one TMA box of the operand (row dots:
+//                64 entries x 128 lines, 128B-swizzled; column sums: 128 lines
+//                x 64 entries) into one of TC_NR shared-memory slots,
 //                and the stage's 4 KB of fp16 weight bytes into one of TC_NW
 //   warps 1, 18-20  MMA issuers (warp 1 also owns TMEM, 512 columns): a
 //                pair per stage parity, in each pair one thread for the lo
@@ -298,10 +299,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_arrive_expect_tx(bars.raw_full(slot), 16384);
             tma_load_2d(raw, T.tmap, kk, T.w0, bars.raw_full(slot));
           } else {
-            const bool two = T.nw > 64;
-            mbar_arrive_expect_tx(bars.raw_full(slot), two ? 16384 : 8192);
+            mbar_arrive_expect_tx(bars.raw_full(slot), 16384);
             tma_load_2d(raw, T.tmap, T.w0, kk, bars.raw_full(slot));
-            if (two) tma_load_2d(raw + 8192, T.tmap, T.w0 + 64, kk, bars.raw_full(slot));
           }
         }
         if (!done) {
@@ -384,16 +383,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             w[4 * j] = v.x; w[4 * j + 1] = v.y; w[4 * j + 2] = v.z; w[4 * j + 3] = v.w;
           }
         } else {
-          // two boxes [64 entries][64 lines]: line m of entry k at
-          // 8192 (m / 64) + 128 k + 16 ((m % 64 / 8) ^ (k % 8)) + 2 (m % 8)
-          const uint8_t* col = raw + (m >> 6) * 8192 + (m & 7) * 2;
-          const int mc = (m & 63) >> 3;
+          // box [64 entries][128 lines], no swizzle: line m of entry k at 256 k + 2 m
+          const uint8_t* col = raw + 2 * m + 32 * kh * 256;
 #pragma unroll
           for (int i = 0; i < 16; i++) {
-            const int k = 32 * kh + 2 * i;
-            const uint32_t a = *reinterpret_cast<const uint16_t*>(col + k * 128 + ((mc ^ (k & 7)) << 4));
-            const uint32_t b = *reinterpret_cast<const uint16_t*>(col + (k + 1) * 128 + ((mc ^ ((k + 1) & 7)) << 4));
-            w[i] = a | (b << 16);
+            const uint32_t a = *reinterpret_cast<const uint16_t*>(col + (2 * i) * 256);
+            const uint32_t b = *reinterpret_cast<const uint16_t*>(col + (2 * i + 1) * 256);
+            w[i] = __byte_perm(a, b, 0x5410);
           }
         }
         uint32_t lo[16], hi[16];
