@@ -124,7 +124,7 @@ static constexpr int TC_NC = 4;   // converted-operand stages (TMEM, 64 columns 
 static constexpr int TC_NA = 4;   // accumulator buffers (TMEM, 64 columns each)
 static constexpr int TC_HR = 32;  // stage-header ring (> TC_NR + TC_NC + TC_NA)
 static_assert(TC_HR > TC_NR + TC_NC + TC_NA, "header ring");
-static constexpr int TC_SMEM = 1024 + TC_NR * 16384 + TC_NW * 4096 + 1024 + 1024;
+static constexpr int TC_SMEM = 1024 + TC_NR * 16384 + TC_NW * 4096 + 3072;
 
 struct FoldTile {
   int32_t task;
@@ -173,11 +173,11 @@ cudaError_t launch_prologue(const DevProof* proofs, int nproofs, cudaStream_t st
 cudaError_t fold_set_smem(int smem_bytes);
 cudaError_t launch_fold(const FoldTask* tasks, const FoldTile* tiles, int ntiles,
                         const DevProof* proofs, int smem_bytes, unsigned long long wait_ns, cudaStream_t st);
-// Tensor-core fold of int16 operands (fold_tc.cuh); `counter` is a zeroed
-// int the CTAs take tiles from.
+// Tensor-core fold of int16 operands (kernels_fold_tc.cu): CTA b of the
+// grid takes tiles b, b + grid, b + 2 grid, ... (tiles sorted longest first).
 cudaError_t fold_tc_prepare();
-cudaError_t launch_fold_tc(const TcTile* tiles, int ntiles, const DevProof* proofs, int* counter,
-                           unsigned long long wait_ns, cudaStream_t st);
+cudaError_t launch_fold_tc(const TcTile* tiles, int ntiles, const DevProof* proofs, unsigned long long wait_ns,
+                           cudaStream_t st);
 cudaError_t step_set_smem(int smem_bytes);
 cudaError_t step_grid(int smem_bytes, int* grid);
 cudaError_t launch_step(const StepItem* items, int nitems, const FoldTask* tasks, const FoldTile* tiles,

@@ -261,7 +261,7 @@ void build_groups(vl_plan* p) {
     }
   }
   // Within a group, tensor-core tiles go longest first (the CTAs take them
-  // from a counter in this order).
+  // round robin in this order).
   for (const vl_plan::Group& G : p->groups)
     std::stable_sort(p->tc_tiles.begin() + G.c0, p->tc_tiles.begin() + G.c1,
                      [](const TcTile& a, const TcTile& b) { return a.nk > b.nk; });
@@ -685,7 +685,7 @@ cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t s
     const vl_plan::Group& G = p->groups[g];
     if (g > 0) e = cudaStreamWaitEvent(st, gev[g], 0);
     if (e == cudaSuccess)
-      e = launch_fold_tc(dc + G.c0, G.c1 - G.c0, dp, reinterpret_cast<int*>(ws + p->off_ctl) + g, wait_ns(p), st);
+      e = launch_fold_tc(dc + G.c0, G.c1 - G.c0, dp, wait_ns(p), st);
     if (e == cudaSuccess) e = launch_fold(dt, dl + G.t0, G.t1 - G.t0, dp, p->fold_smem, wait_ns(p), st);
     if (e == cudaSuccess) e = cudaEventRecord(gev[ng + g], st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(rs, gev[ng + g], 0);

@@ -19,8 +19,9 @@
 // CUDA-core fold (col_7 also takes s_32 . 2^32), added with red.add, so the
 // rounds reduce them unchanged (Montgomery reduction, minus 2^15 . sum E).
 //
-// Roles in a CTA (one CTA per SM; tiles come from a global counter, longest
-// first), each running at its own pace and linked only by mbarriers:
+// Roles in a CTA (one CTA per SM; CTA b takes tiles b, b + grid, ... of a
+// list sorted longest first), each running at its own pace and linked only by
+// mbarriers:
 //   warp 0       producer: per stage one TMA box of the operand (row dots:
 //                64 entries x 128 lines, 128B-swizzled; column sums: 128 lines
 //                x 64 entries) into one of TC_NR shared-memory slots,
@@ -52,7 +53,7 @@ namespace {
 constexpr int SM_RAW = 0;                          // TC_NR x 16 KB of int16 operand
 constexpr int SM_W = SM_RAW + TC_NR * 16384;       // TC_NW x 4 KB of fp16 weight bytes
 constexpr int SM_HDR = SM_W + TC_NW * 4096;        // TC_HR stage headers
-constexpr int SM_BAR = SM_HDR + TC_HR * 16;
+constexpr int SM_BAR = SM_HDR + TC_HR * 32;
 // Completion of stage s's MMAs (both issuers) is one barrier of a ring of
 // TC_ND: the converters (TMEM operand reuse), the producer (weight slot
 // reuse) and the drainers (accumulator ready) all wait on it.  TC_ND exceeds
@@ -140,12 +141,17 @@ __device__ __forceinline__ uint32_t fbits_add(uint32_t a, uint32_t b) {
   return __float_as_uint(__fadd_rn(__uint_as_float(a), __uint_as_float(b)));
 }
 
+// One pipeline stage as every role sees it (written by the producer).
 struct StageHdr {
-  int32_t tile;   // -1: no more tiles
+  int32_t tile;   // -1: end marker
   int32_t stage;  // stage within the tile
   int32_t nst;    // stages of the tile
   int32_t mode;
+  int32_t nw;     // lines of the tile
+  int32_t pad;
+  unsigned long long* acc;  // accumulator rows of the tile's first line
 };
+static_assert(sizeof(StageHdr) == 32, "stage header");
 
 struct TcBars {
   uint32_t b;
@@ -219,7 +225,7 @@ __device__ __forceinline__ void tc_epilogue(uint32_t (&dg)[17], int nst, unsigne
 }  // namespace
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    fold_tc_kernel(const TcTile* __restrict__ tiles, int ntiles, const DevProof* __restrict__ proofs, int* counter,
+    fold_tc_kernel(const TcTile* __restrict__ tiles, int ntiles, const DevProof* __restrict__ proofs,
                    unsigned long long wait_ns) {
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   const uint32_t raw_addr = smem_addr(tc_smem_raw);
@@ -262,15 +268,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
       for (int i = 0; i < TC_NW; i++) last_wuse[i] = -1;
       int s = 0;
-      int tile = atomicAdd(counter, 1);
+      const int G = gridDim.x;
+      int tile = blockIdx.x;
+      // descriptors of this tile and the next are in registers; the one after
+      // is loaded while this tile streams
       TcTile T = tile < ntiles ? tiles[tile] : TcTile{};
+      TcTile Tn = tile + G < ntiles ? tiles[tile + G] : TcTile{};
       for (bool done = false; !done && ok;) {
         done = tile >= ntiles;
-        // take the next tile now: its atomic and descriptor load overlap this
-        // tile's stages
-        const int next = done ? tile : atomicAdd(counter, 1);
-        TcTile Tn{};
-        if (!done && next < ntiles) Tn = tiles[next];
+        TcTile Tnn{};
+        if (!done && tile + 2 * G < ntiles) Tnn = tiles[tile + 2 * G];
         // after the last tile, two end markers: one for each issuer pair
         const int nst = done ? 2 : (T.nk + TC_KS - 1) / TC_KS;
         for (int st = 0; st < nst; st++, s++) {
@@ -279,7 +286,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             ok = false;
             break;
           }
-          hdr[s % TC_HR] = StageHdr{done ? -1 : tile, st, nst, T.mode};
+          hdr[s % TC_HR] = StageHdr{done ? -1 : tile, st, nst, T.mode, T.nw, 0, T.acc};
           last_use[slot] = use;
           const uint32_t raw = base + SM_RAW + slot * 16384;
           if (done) {
@@ -295,17 +302,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           bulk_g2s(base + SM_W + ws * 4096, reinterpret_cast<const uint8_t*>(T.w8) + (size_t)(kk / TC_KS) * 4096,
                    4096, bars.w_full(ws));
           last_wuse[ws] = wuse;
-          if (T.mode == MODE_ROWDOT) {
-            mbar_arrive_expect_tx(bars.raw_full(slot), 16384);
-            tma_load_2d(raw, T.tmap, kk, T.w0, bars.raw_full(slot));
-          } else {
-            mbar_arrive_expect_tx(bars.raw_full(slot), 16384);
-            tma_load_2d(raw, T.tmap, T.w0, kk, bars.raw_full(slot));
-          }
+          mbar_arrive_expect_tx(bars.raw_full(slot), 16384);
+          if (T.mode == MODE_ROWDOT) tma_load_2d(raw, T.tmap, kk, T.w0, bars.raw_full(slot));
+          else tma_load_2d(raw, T.tmap, T.w0, kk, bars.raw_full(slot));
         }
         if (!done) {
-          tile = next;
+          tile += G;
           T = Tn;
+          Tn = Tnn;
         }
       }
       if (!ok) mark_timeout(proofs, tiles, tile < ntiles ? tile : -1);
@@ -432,9 +436,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (grp == 0) drain_digits<0, 16>(ta, dg, bars.acc_empty(a));
       else drain_digits<17, 32>(ta, dg, bars.acc_empty(a));
       if (h.stage == h.nst - 1) {
-        const int nw = tiles[h.tile].nw;
-        if (line < nw) {
-          unsigned long long* acc = tiles[h.tile].acc + (size_t)line * 8;
+        if (line < h.nw) {
+          unsigned long long* acc = h.acc + (size_t)line * 8;
           if (grp == 0) tc_epilogue<0, 16>(dg, h.nst, acc);
           else tc_epilogue<17, 32>(dg, h.nst, acc);
         }
@@ -464,8 +467,8 @@ cudaError_t fold_tc_prepare() {
   return e;
 }
 
-cudaError_t launch_fold_tc(const TcTile* tiles, int ntiles, const DevProof* proofs, int* counter,
-                           unsigned long long wait_ns, cudaStream_t st) {
+cudaError_t launch_fold_tc(const TcTile* tiles, int ntiles, const DevProof* proofs, unsigned long long wait_ns,
+                           cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   static int sms = 0;
   if (!sms) {
@@ -475,7 +478,7 @@ cudaError_t launch_fold_tc(const TcTile* tiles, int ntiles, const DevProof* proo
     if (e != cudaSuccess) return e;
   }
   const int grid = ntiles < sms ? ntiles : sms;
-  fold_tc_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(tiles, ntiles, proofs, counter, wait_ns);
+  fold_tc_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(tiles, ntiles, proofs, wait_ns);
   return cudaGetLastError();
 }
 
