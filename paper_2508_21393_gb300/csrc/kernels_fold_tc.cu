@@ -131,10 +131,33 @@ __device__ __forceinline__ uint32_t bytes_f16x2(uint32_t t, uint32_t sel) {
   return r;
 }
 
+// try_wait with a suspend-time hint: a thread whose phase is not complete is
+// suspended in hardware (woken when the phase completes, or after ~1 us)
+// instead of polling, which would take issue slots from the working warps.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(1000u)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after wait_ns of %globaltimer (read only when the
+// first attempt fails).
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity, unsigned long long wait_ns) {
+  if (mbar_try_wait_sleep(bar, parity)) return true;
+  const uint64_t deadline = global_ns() + wait_ns;
+  while (!mbar_try_wait_sleep(bar, parity))
+    if (global_ns() > deadline) return false;
+  return true;
+}
+
 // A bounded wait taken by a whole warp: it succeeds only if every lane's did,
 // so the warp never splits before a .sync.aligned instruction.
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, unsigned long long wait_ns) {
-  return __all_sync(0xffffffffu, mbar_wait_for(bar, parity, wait_ns));
+  return __all_sync(0xffffffffu, tc_wait(bar, parity, wait_ns));
 }
 
 __device__ __forceinline__ uint32_t fbits_add(uint32_t a, uint32_t b) {
@@ -282,7 +305,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int nst = done ? 2 : (T.nk + TC_KS - 1) / TC_KS;
         for (int st = 0; st < nst; st++, s++) {
           const int slot = s % TC_NR, use = s / TC_NR, ws = s % TC_NW, wuse = s / TC_NW;
-          if (use > 0 && !mbar_wait_for(bars.raw_empty(slot), (use - 1) & 1, wait_ns)) {
+          if (use > 0 && !tc_wait(bars.raw_empty(slot), (use - 1) & 1, wait_ns)) {
             ok = false;
             break;
           }
@@ -293,7 +316,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_arrive(bars.raw_full(slot));
             continue;
           }
-          if (wuse > 0 && !mbar_wait_for(bars.done(s - TC_NW), done_parity(s - TC_NW), wait_ns)) {
+          if (wuse > 0 && !tc_wait(bars.done(s - TC_NW), done_parity(s - TC_NW), wait_ns)) {
             ok = false;
             break;
           }
@@ -315,9 +338,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!ok) mark_timeout(proofs, tiles, tile < ntiles ? tile : -1);
       // Copies still in flight must land before the CTA leaves.
       for (int i = 0; i < TC_NR; i++)
-        if (last_use[i] >= 0) mbar_wait_for(bars.raw_full(i), last_use[i] & 1, wait_ns);
+        if (last_use[i] >= 0) tc_wait(bars.raw_full(i), last_use[i] & 1, wait_ns);
       for (int i = 0; i < TC_NW; i++)
-        if (last_wuse[i] >= 0) mbar_wait_for(bars.w_full(i), last_wuse[i] & 1, wait_ns);
+        if (last_wuse[i] >= 0) tc_wait(bars.w_full(i), last_wuse[i] & 1, wait_ns);
     }
   } else if (warp == 1 || warp >= TC_THREADS / 32 - 3) {
     // ---------------------------------------------------------------- MMA issuers
@@ -326,12 +349,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const uint32_t half = (j & 1) ? 32 : 0;  // lo or hi: A and D column offset
       for (int s = j >> 1;; s += 2) {
         const int c = s % TC_NC, a = s % TC_NA;
-        if (!mbar_wait_for(bars.conv_full(c), (s / TC_NC) & 1, wait_ns)) {
+        if (!tc_wait(bars.conv_full(c), (s / TC_NC) & 1, wait_ns)) {
           ok = false;
           break;
         }
         const StageHdr h = hdr[s % TC_HR];
-        if (s >= TC_NA && !mbar_wait_for(bars.acc_empty(a), ((s / TC_NA) - 1) & 1, wait_ns)) {
+        if (s >= TC_NA && !tc_wait(bars.acc_empty(a), ((s / TC_NA) - 1) & 1, wait_ns)) {
           ok = false;
           mark_timeout(proofs, tiles, h.tile);
           break;
@@ -341,7 +364,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           break;
         }
         const int ws = s % TC_NW;
-        if (!mbar_wait_for(bars.w_full(ws), (s / TC_NW) & 1, wait_ns)) {
+        if (!tc_wait(bars.w_full(ws), (s / TC_NW) & 1, wait_ns)) {
           ok = false;
           mark_timeout(proofs, tiles, h.tile);
           break;
@@ -355,7 +378,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       // every MMA this thread issued has completed before TMEM is freed
       umma_commit(bars.fin());
-      mbar_wait_for(bars.fin(), 0, wait_ns);
+      tc_wait(bars.fin(), 0, wait_ns);
     }
   } else if (warp < 2 + TC_CONV_WARPS) {
     // ---------------------------------------------------------------- converters
