@@ -43,11 +43,13 @@ SM_MAX_MHZ = 2070.0
 # the ALU roofline of the int16 fold: 64 32-bit integer multiply-adds per SM
 # per clock, a wide (64-bit result) one taking two of them.
 MADWIDE_PER_SM_CLK = 32
-STEP_KIND = {"7b-step": "7b", "7b-proj": "7b-proj", "13b-step": "13b"}
+STEP_KIND = {"7b-step": "7b", "7b-proj": "7b-proj", "13b-step": "13b", "serve": "7b-proj"}
 WORKLOADS = {
     "7b-step": "batched 7B-shaped LoRA step: 32 layers x {q,k,v,o}, hidden 4096, seq 512, ranks {8,16,64}",
     "7b-proj": "one 7B-shaped LoRA projection, n=1024, d=k=4096, r=16, eight products",
     "13b-step": "batched 13B-shaped LoRA step: 40 layers x {q,k,v,o}, hidden 5120, seq 2048, rank 16",
+    "serve": "serving stream: Poisson arrivals (20 jobs/s) of single-layer jobs (one projection's 8 products), "
+             "hidden {4096, 5120}, seq {256, 512, 1024, 2048}, rank {8, 16, 64}, 120 GB admission budget",
 }
 
 
@@ -70,6 +72,9 @@ def parse():
                     help="phase launches: proof groups pipelined over three streams (0: library default)")
     ap.add_argument("--rounds-variant", type=int, default=0, choices=[0, 4, 7],
                     help="rounds kernel register budget (CTAs per SM); 0 = library default")
+    ap.add_argument("--serve-jobs", type=int, default=200, help="serve workload: requests in the timed stream")
+    ap.add_argument("--serve-rate", type=float, default=20.0, help="serve workload: mean arrivals per second")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0, help="serve workload: arena (admission budget)")
     ap.add_argument("--layers", type=int, default=0,
                     help="prove only the first L layers of the step (profiling captures); 0 = all")
     return ap.parse_args()
@@ -156,11 +161,118 @@ def run_reference(args, rank, world):
     }))
 
 
+def serve_main(args, rank, world, local):
+    """Serving stream through vl_server_*: Poisson arrivals, continuous batching
+    under the admission budget; frozen W resident on the device, activations
+    copied from pinned host memory per request.  Reports proofs/s and p50/p99
+    submit-to-completion latency."""
+    import torch
+    from paper_2508_21393_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    B.lib()
+    arrivals = W.serving_jobs(args.serve_jobs, W.GLOBAL_SEED + rank, rate=args.serve_rate)
+    shapes = sorted({sh for _, sh in arrivals})
+    pool = {}
+    for i, (h, n, r) in enumerate(shapes):  # job pool: generated before timing
+        t = W.lora_projection(W.GLOBAL_SEED, 100 + i, "q", n, h, h, r)
+        jobs = W.projection_products(t, W.GLOBAL_SEED)
+        hold = {}
+        for key in ("X", "W", "A", "B", "dY", "H", "dH"):
+            x = torch.from_numpy(np.ascontiguousarray(t[key]))
+            if key == "W":
+                hold[key] = x.cuda()  # frozen weight: resident
+            else:
+                hp = torch.empty(x.shape, dtype=torch.int16, pin_memory=True)
+                hp.copy_(x)
+                hold[key] = hp
+        by_id = {id(t[k]): hold[k] for k in hold}
+        vj = [B.job(by_id[id(j["P"])], by_id[id(j["Q"])], j["tp"], j["tq"], j["seed"]) for j in jobs]
+        h2d = sum(v.numel() * 2 for k, v in hold.items() if k != "W")
+        pool[(h, n, r)] = (vj, sum(W.macs(j) for j in jobs), h2d, hold)
+    budget = int(args.serve_budget_gb * (1 << 30))
+    arena = torch.empty(budget, dtype=torch.uint8, device="cuda")
+    server = B.vl_server_create(arena.data_ptr(), budget)
+
+    def submit(vj, seed):
+        jobs = []
+        for j in vj:
+            c = B.vl_job.from_buffer_copy(j)
+            c.fs.seed = seed
+            jobs.append(c)
+        out = (B.vl_proof * len(jobs))()
+        return B.vl_server_submit(server, jobs, out), out
+
+    done = {}
+    # warm-up: one request of each shape (plan building, attribute setup)
+    warm_outs = [submit(pool[sh][0], 7 + i) for i, sh in enumerate(shapes)]  # outputs live until done
+    warm = [tk for tk, _ in warm_outs]
+    while len(done) < len(warm):
+        for tk, st, b, lat in B.vl_server_poll(server):
+            done[tk] = (st, b, lat)
+        time.sleep(0.001)
+    torch.cuda.synchronize()
+    done.clear()
+    clocks = Clocks(local)
+    time.sleep(0.6)
+    sub = {}
+    outs = []
+    t0 = time.perf_counter()
+    for i, (ta, sh) in enumerate(arrivals):
+        while True:
+            now = time.perf_counter() - t0
+            if now >= ta:
+                break
+            for tk, st, b, lat in B.vl_server_poll(server):
+                done[tk] = (st, b, lat, time.perf_counter() - t0)
+            time.sleep(min(0.0005, ta - now))
+        tk, out = submit(pool[sh][0], 1000003 * (i + 1))
+        sub[tk] = (time.perf_counter() - t0, sh)
+        outs.append(out)
+    while len(done) < len(sub):
+        for tk, st, b, lat in B.vl_server_poll(server):
+            done[tk] = (st, b, lat, time.perf_counter() - t0)
+        time.sleep(0.0005)
+    clk = clocks.stop()
+    stats = B.vl_server_stats_get(server)
+    B.vl_server_destroy(server)
+    lat = sorted(v[2] for v in done.values())
+    assert all(v[0] == 0 for v in done.values()), "a request failed"
+    end = max(sub[tk][0] + done[tk][2] / 1e3 for tk in sub)
+    nproofs = sum(len(pool[sh][0]) for _, sh in sub.values())
+    macs = sum(pool[sh][1] for _, sh in sub.values())
+    h2d = sum(pool[sh][2] for _, sh in sub.values())
+    pct = lambda q: float(np.percentile(lat, q))
+    if rank != 0:
+        return
+    line = {
+        "metric": "serving: proofs/s with p50/p99 proof latency (continuous batching, bit-exact)",
+        "value": nproofs / end, "unit": "proofs/s", "n_gpus": world, "steps": len(sub), "warmup": len(warm),
+        "ms_per_step": 1e3 * end / len(sub), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int16 operands, Fr (255-bit) arithmetic", "data": "synthetic",
+        "config": {"workload": WORKLOADS["serve"].replace("(20 jobs/s)", f"({args.serve_rate:g} jobs/s)"),
+                   "requests": len(sub), "proofs": nproofs,
+                   "distinct_shapes": len(shapes), "admission_budget_gb": args.serve_budget_gb,
+                   "batches": stats["batches"], "l2": "inputs larger than L2 (no flush)"},
+        "latency_ms": {"p50": pct(50), "p99": pct(99), "mean": float(np.mean(lat)), "max": lat[-1]},
+        "macs_per_s": macs / end,
+        "roofline": None,
+        "cpu_baseline": None,
+        "e2e": {"value": nproofs / end, "unit": "proofs/s", "h2d_bytes_per_step": h2d // len(sub),
+                "d2h_bytes_per_step": int(ctypes.sizeof(B.vl_proof) * nproofs // len(sub))},
+        "clocks": clk,
+        "gpu_launches": None,
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "serve":
+        return serve_main(args, rank, world, local)
 
     # The oracle CPU baseline runs before any CUDA work (no forked pools after it).
     cpu = None

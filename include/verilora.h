@@ -254,6 +254,63 @@ int32_t vl_prove_matmul_noalloc(const vl_mat* P, const vl_mat* Q, const vl_fs_in
  */
 int32_t vl_encode(const vl_mat* src, void* dst, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Proving server: continuous batching under a device-memory budget.  The
+ * paper proves one step at a time and has no counterpart; this is the
+ * serving pattern around its prover.
+ *
+ * The caller gives the server a device arena (its admission budget, any
+ * alignment; the server sub-allocates plan workspaces and proof outputs from
+ * it and allocates no device memory).  Requests are submitted as job lists
+ * (e.g. one projection's products) and proved in arrival order: a worker
+ * thread merges the queued requests that fit the largest free arena block
+ * (at most max_batch_requests) into one batch whenever one of max_inflight
+ * streams is free, runs it as one plan on that stream (batches overlap on
+ * the device), and when it completes copies each request's proofs to its
+ * `out` (host memory, njobs proofs) and reports the request as done with its
+ * submit-to-completion latency.  Operands may be device matrices (resident,
+ * e.g. frozen weights) or host matrices (staged into the batch's arena block;
+ * pinned host memory keeps the copies asynchronous); they must stay unchanged
+ * until the request is done.  A request that cannot fit even an empty arena
+ * is done with VL_ENOMEM; one the library rejects is done with that status.
+ * Proofs are identical to proving the same jobs alone.
+ * ------------------------------------------------------------------------- */
+typedef struct vl_server vl_server;
+
+typedef struct vl_server_opts {
+  void* arena;                /* device buffer owned by the caller          */
+  size_t arena_bytes;         /* admission budget                            */
+  int32_t max_inflight;       /* batches on the device at once (0: 4)        */
+  int32_t max_batch_requests; /* requests merged into one batch (0: 64)     */
+  int32_t wait_limit_us;      /* as vl_batch_opts.wait_limit_us              */
+  int32_t reserved[4];        /* must be 0                                   */
+} vl_server_opts;
+
+typedef struct vl_server_done {
+  uint64_t ticket;
+  int32_t status;     /* VL_OK, or the first non-OK proof / launch status   */
+  int32_t batch;      /* batch the request ran in (-1: never admitted)      */
+  double latency_ms;  /* submit to completion seen by the server            */
+} vl_server_done;
+
+typedef struct vl_server_stats {
+  int64_t submitted, completed, failed, batches, proofs, queued;
+} vl_server_stats;
+
+/* Start a server (and its worker thread) on the current device. */
+int32_t vl_server_create(const vl_server_opts* opts, vl_server** out);
+/* Queue one request; *ticket identifies it in vl_server_poll. */
+int32_t vl_server_submit(vl_server* server, const vl_job* jobs, int32_t njobs, vl_proof* out,
+                         uint64_t* ticket);
+/* Move up to `max` completed requests into done[]; *ndone = how many.
+ * Non-blocking. */
+int32_t vl_server_poll(vl_server* server, vl_server_done* done, int32_t max, int32_t* ndone);
+/* Counters (queued = requests waiting for admission). */
+int32_t vl_server_stats_get(vl_server* server, vl_server_stats* out);
+/* Finish the batches on the device, stop the worker, free host resources.
+ * Queued requests that were never admitted are dropped. */
+int32_t vl_server_destroy(vl_server* server);
+
 #ifdef __cplusplus
 }
 #endif

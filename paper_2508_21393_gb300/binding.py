@@ -27,7 +27,8 @@ VL_MAX_REDUCE = 1 << 16
 # Every symbol include/verilora.h declares.
 EXPORTS = ("vl_version", "vl_strerror", "vl_last_error", "vl_workspace_bytes", "vl_prove_matmul", "vl_prove_batch",
            "vl_plan_create", "vl_plan_workspace_bytes", "vl_plan_run", "vl_plan_launches", "vl_plan_phase_ms",
-           "vl_plan_destroy", "vl_verify_matmul", "vl_encode", "vl_prove_matmul_noalloc")
+           "vl_plan_destroy", "vl_verify_matmul", "vl_encode", "vl_prove_matmul_noalloc",
+           "vl_server_create", "vl_server_submit", "vl_server_poll", "vl_server_stats_get", "vl_server_destroy")
 VL_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -58,6 +59,22 @@ class vl_proof(ctypes.Structure):
 
 class vl_job(ctypes.Structure):
     _fields_ = [("P", vl_mat), ("Q", vl_mat), ("fs", vl_fs_init)]
+
+
+class vl_server_opts(ctypes.Structure):
+    _fields_ = [("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32),
+                ("max_batch_requests", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class vl_server_done(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("latency_ms", ctypes.c_double)]
+
+
+class vl_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("proofs", ctypes.c_int64), ("queued", ctypes.c_int64)]
 
 
 class vl_batch_opts(ctypes.Structure):
@@ -112,6 +129,16 @@ def lib():
     L.vl_plan_phase_ms.restype = ctypes.c_int32
     L.vl_plan_destroy.argtypes = [ctypes.c_void_p]
     L.vl_plan_destroy.restype = None
+    L.vl_server_create.argtypes = [P(vl_server_opts), P(ctypes.c_void_p)]
+    L.vl_server_create.restype = ctypes.c_int32
+    L.vl_server_submit.argtypes = [ctypes.c_void_p, P(vl_job), ctypes.c_int32, P(vl_proof), P(ctypes.c_uint64)]
+    L.vl_server_submit.restype = ctypes.c_int32
+    L.vl_server_poll.argtypes = [ctypes.c_void_p, P(vl_server_done), ctypes.c_int32, P(ctypes.c_int32)]
+    L.vl_server_poll.restype = ctypes.c_int32
+    L.vl_server_stats_get.argtypes = [ctypes.c_void_p, P(vl_server_stats)]
+    L.vl_server_stats_get.restype = ctypes.c_int32
+    L.vl_server_destroy.argtypes = [ctypes.c_void_p]
+    L.vl_server_destroy.restype = ctypes.c_int32
     L.vl_verify_matmul.argtypes = [P(vl_mat), P(vl_mat), P(vl_mat), P(vl_fs_init), P(vl_proof)]
     L.vl_verify_matmul.restype = ctypes.c_int32
     L.vl_prove_matmul_noalloc.argtypes = [P(vl_mat), P(vl_mat), P(vl_fs_init), P(vl_proof), ctypes.c_void_p]
@@ -299,6 +326,45 @@ def vl_plan_phase_ms(plan, max_runs, reset=1):
 
 def vl_plan_destroy(plan):
     lib().vl_plan_destroy(plan)
+
+
+def vl_server_create(arena_ptr, arena_bytes, max_inflight=0, max_batch_requests=0, wait_limit_us=0):
+    """Start a proving server over the caller's device arena (its admission budget)."""
+    o = vl_server_opts()
+    o.arena = arena_ptr
+    o.arena_bytes = arena_bytes
+    o.max_inflight = max_inflight
+    o.max_batch_requests = max_batch_requests
+    o.wait_limit_us = wait_limit_us
+    s = ctypes.c_void_p()
+    _check(lib().vl_server_create(ctypes.byref(o), ctypes.byref(s)), "vl_server_create")
+    return s
+
+
+def vl_server_submit(server, jobs, out):
+    """Queue one request (a list of vl_job); `out` receives len(jobs) proofs. Returns its ticket."""
+    arr = jobs_array(jobs)
+    t = ctypes.c_uint64()
+    _check(lib().vl_server_submit(server, arr, len(jobs), out, ctypes.byref(t)), "vl_server_submit")
+    return t.value
+
+
+def vl_server_poll(server, max_done=1024):
+    """Completed requests since the last poll: list of (ticket, status, batch, latency_ms)."""
+    buf = (vl_server_done * max_done)()
+    n = ctypes.c_int32()
+    _check(lib().vl_server_poll(server, buf, max_done, ctypes.byref(n)), "vl_server_poll")
+    return [(buf[i].ticket, buf[i].status, buf[i].batch, buf[i].latency_ms) for i in range(n.value)]
+
+
+def vl_server_stats_get(server):
+    st = vl_server_stats()
+    _check(lib().vl_server_stats_get(server, ctypes.byref(st)), "vl_server_stats_get")
+    return {k: getattr(st, k) for k, _ in vl_server_stats._fields_}
+
+
+def vl_server_destroy(server):
+    _check(lib().vl_server_destroy(server), "vl_server_destroy")
 
 
 def vl_verify_matmul(P, Q, C, fs, proof):

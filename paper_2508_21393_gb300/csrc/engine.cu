@@ -605,7 +605,7 @@ unsigned long long wait_ns(const vl_plan* p) {
 }
 
 cudaError_t ensure_events(vl_plan* p) {
-  if (p->gev.empty()) {
+  if (p->gev.empty() && !persistent(p) && p->groups.size() > 1) {
     p->gev.resize(2 * p->groups.size() + 2);
     for (cudaEvent_t& ev : p->gev) {
       cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -666,6 +666,18 @@ cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t s
   // Phases: [0] clear + first prologue, [1] folds (rounds and prologues of
   // other groups overlap them), [2] rounds left after the last fold.
   const int ng = (int)p->groups.size();
+  if (ng == 1) {
+    // One group: everything in order on the caller's stream.
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + p->off_ctl, 0, p->off_acc + p->acc_bytes - p->off_ctl, st);
+    if (e == cudaSuccess) e = launch_prologue(dp, np, st);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[1], st, flags);
+    if (e == cudaSuccess) e = launch_fold_tc(dc, (int)p->tc_tiles.size(), dp, wait_ns(p), st);
+    if (e == cudaSuccess) e = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, wait_ns(p), st);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2], st, flags);
+    if (e == cudaSuccess) e = launch_rounds(dp, np, dout, p->opts.rounds_variant, st);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[3], st, flags);
+    return e;
+  }
   cudaStream_t rs = p->side[0], ps = p->side[1];
   cudaEvent_t* gev = p->gev.data();  // [0, ng): prologue g done; [ng, 2ng): fold g done; 2ng: start; 2ng+1: rounds done
   // tile counters (one per group) and accumulators: one contiguous region

@@ -149,3 +149,16 @@ def test_host_verifier_rejects_perturbations(L):
     A2[0, 0] ^= 1
     assert not B.vl_verify_matmul(B.mat(A2), B.mat(Bm), B.mat(C), fs, _to_vl_proof(pf))
     assert not B.vl_verify_matmul(B.mat(A), B.mat(Bm), B.mat(C), B.fs_init(10), _to_vl_proof(pf))
+
+
+def test_server_rejects_bad_options_before_cuda():
+    L = B.lib()
+    s = ctypes.c_void_p()
+    o = B.vl_server_opts()
+    assert L.vl_server_create(ctypes.byref(o), ctypes.byref(s)) == B.VL_EINVAL  # no arena
+    o.arena = 4096
+    o.arena_bytes = 1 << 20
+    o.reserved[1] = 1
+    assert L.vl_server_create(ctypes.byref(o), ctypes.byref(s)) == B.VL_EINVAL  # reserved field set
+    assert L.vl_server_submit(None, None, 0, None, None) == B.VL_EINVAL
+    assert L.vl_server_destroy(None) == B.VL_EINVAL
