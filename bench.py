@@ -72,6 +72,8 @@ def parse():
                     help="phase launches: proof groups pipelined over three streams (0: library default)")
     ap.add_argument("--rounds-variant", type=int, default=0, choices=[0, 4, 7],
                     help="rounds kernel register budget (CTAs per SM); 0 = library default")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the autotuner (it also stays off when launch or tile options are given)")
     ap.add_argument("--serve-jobs", type=int, default=200, help="serve workload: requests in the timed stream")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="serve workload: mean arrivals per second")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0, help="serve workload: arena (admission budget)")
@@ -304,11 +306,30 @@ def main():
 
     stream = torch.cuda.current_stream()
     opts = B.vl_batch_opts()
-    opts.timing_runs = max(args.steps, 1)
     opts.rounds_variant = args.rounds_variant
     opts.persistent = 1 if args.persistent else 2
     opts.fold_engine = args.fold_engine
     opts.groups = args.groups
+    forced = args.persistent or args.fold_engine or args.rounds_variant or args.groups
+    tuned = None
+    if not args.no_autotune and not forced:
+        # Launch and tile options by timing candidates on this workload (not timed).
+        need = 0
+        for eng, pers, seg in ((0, 2, 0), (1, 2, 0), (0, 1, 0), (0, 2, 2048)):
+            o = B.vl_batch_opts()
+            o.fold_engine, o.persistent, o.tc_seg = eng, pers, seg
+            need = max(need, B.vl_workspace_bytes(djobs, o))
+        need += len(djobs) * ctypes.sizeof(B.vl_proof) + (1 << 20)
+        tws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        t0 = time.perf_counter()
+        opts, tune_ms = B.vl_autotune(djobs, tws.data_ptr(), need, base=opts, stream=stream, runs=3)
+        tuned = {"seconds": time.perf_counter() - t0, "ms_per_step_at_tuning": tune_ms,
+                 **{k: getattr(opts, k) for k in ("fold_engine", "tc_seg", "rounds_variant", "persistent",
+                                                  "colsum_rows", "rowdot_cols", "groups")}}
+        del tws
+    cuda_core = opts.persistent == 1 or opts.fold_engine == 1
+    persistent = opts.persistent == 1
+    opts.timing_runs = max(args.steps, 1)
     plan = B.vl_plan_create(djobs, opts)
     nws = B.vl_plan_workspace_bytes(plan)
     ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
@@ -352,9 +373,9 @@ def main():
         pass
     hbm_peak, hbm_note = (peaks["hbm_gbs"], "measured") if "hbm_gbs" in peaks else (6800.0, "fallback")
     hbm_gbs = 2 * entries / (fold_ms / 1e3) / 1e9  # each int16 operand entry read once
-    if args.persistent or args.fold_engine == 1:
+    if cuda_core:
         # CUDA-core fold: bound by 32x32->64 multiply-adds (eight per entry).
-        if args.persistent:
+        if persistent:
             kernel, phase_ms = "step_kernel (persistent)", {"clear": pro_ms, "step_kernel": fold_ms}
         else:
             kernel, phase_ms = "fold_kernel", {"clear+prologue": pro_ms, "fold": fold_ms, "rounds": rnd_ms}
@@ -410,7 +431,7 @@ def main():
                 h.copy_(torch.from_numpy(t[key]))
                 host[id(t[key])] = h
         hjobs = [B.job(host[id(j["P"])], host[id(j["Q"])], j["tp"], j["tq"], j["seed"]) for j in jobs]
-        hopts = B.vl_batch_opts()
+        hopts = B.vl_batch_opts.from_buffer_copy(opts)  # the same (tuned) options
         hopts.timing_runs = 1
         hplan = B.vl_plan_create(hjobs, hopts)
         hn = B.vl_plan_workspace_bytes(hplan)
@@ -449,8 +470,9 @@ def main():
                    "input_bytes_per_step": in_bytes, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas{world}" if world > 1 else "single GPU",
                    "batched_ms_per_step": ms_max, "unbatched_ms_per_step": unbatched_ms,
-                   "launch_mode": "one persistent launch" if args.persistent else "phase launches (CUDA graph)",
-                   "fold_engine": "CUDA cores" if (args.persistent or args.fold_engine == 1) else "tensor cores",
+                   "launch_mode": "one persistent launch" if persistent else "phase launches (CUDA graph)",
+                   "fold_engine": "CUDA cores" if cuda_core else "tensor cores",
+                   "autotuned": tuned,
                    "phase_ms": phase_ms},
         "roofline": roof,
         "cpu_baseline": cpu,

@@ -129,6 +129,9 @@ typedef struct vl_batch_opts {
                             VL_ETIMEOUT and its CTA returns                  */
   int32_t rounds_variant; /* rounds kernel register budget: 7 or 4 CTAs per SM
                             (0: 7)                                           */
+  int32_t tc_seg;        /* tensor-core fold: reduced entries per tile, a
+                            multiple of 64 up to 32768 (0: 16384); shorter
+                            segments spread narrow operands over more SMs */
   int32_t test_never_ready; /* fault injection for tests: 1 + index of a job
                             whose prologue never signals ready, so that its
                             fold tiles exhaust their bounded wait and report
@@ -253,6 +256,23 @@ int32_t vl_prove_matmul_noalloc(const vl_mat* P, const vl_mat* Q, const vl_fs_in
  * `stream`.  The output can be proved with dtype VL_FR_MONT.
  */
 int32_t vl_encode(const vl_mat* src, void* dst, void* stream);
+
+/* Autotuner (the paper has no counterpart): picks the launch and tile
+ * options for `jobs` by timing candidate plans on the caller's workspace and
+ * stream — coordinate descent from `base` (NULL: defaults) over the fold
+ * engine, tc_seg, rounds_variant, the launch mode and, where CUDA-core fold
+ * tiles run, colsum_rows / rowdot_cols; each candidate is run once untimed
+ * and `runs` times timed (0: 3), its time the median.  Candidates needing more
+ * workspace than workspace_bytes (which must also hold njobs proofs at its
+ * end) are skipped.  The result is cached per shape signature (dimensions,
+ * transposes, dtypes, memory spaces, TMA addressability of every operand) for
+ * the process: a later call with the same shapes returns the cached options
+ * without running.  *best receives the options, *best_ms (optional) the time
+ * of one run.  Synchronises `stream`.  Proofs do not depend on the options. */
+int32_t vl_autotune(const vl_job* jobs, int32_t njobs, const vl_batch_opts* base, void* workspace,
+                    size_t workspace_bytes, void* stream, int32_t runs, vl_batch_opts* best, float* best_ms);
+/* Forget every cached autotuning result. */
+void vl_autotune_clear(void);
 
 /* ---------------------------------------------------------------------------
  * Proving server: continuous batching under a device-memory budget.  The

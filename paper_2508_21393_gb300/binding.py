@@ -28,7 +28,8 @@ VL_MAX_REDUCE = 1 << 16
 EXPORTS = ("vl_version", "vl_strerror", "vl_last_error", "vl_workspace_bytes", "vl_prove_matmul", "vl_prove_batch",
            "vl_plan_create", "vl_plan_workspace_bytes", "vl_plan_run", "vl_plan_launches", "vl_plan_phase_ms",
            "vl_plan_destroy", "vl_verify_matmul", "vl_encode", "vl_prove_matmul_noalloc",
-           "vl_server_create", "vl_server_submit", "vl_server_poll", "vl_server_stats_get", "vl_server_destroy")
+           "vl_server_create", "vl_server_submit", "vl_server_poll", "vl_server_stats_get", "vl_server_destroy",
+           "vl_autotune", "vl_autotune_clear")
 VL_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -82,7 +83,8 @@ class vl_batch_opts(ctypes.Structure):
                 ("persistent", ctypes.c_int32), ("groups", ctypes.c_int32), ("fold_engine", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32),
                 ("timing_runs", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
-                ("rounds_variant", ctypes.c_int32), ("test_never_ready", ctypes.c_int32)]
+                ("rounds_variant", ctypes.c_int32), ("tc_seg", ctypes.c_int32),
+                ("test_never_ready", ctypes.c_int32)]
 
 
 class VLError(RuntimeError):
@@ -129,6 +131,11 @@ def lib():
     L.vl_plan_phase_ms.restype = ctypes.c_int32
     L.vl_plan_destroy.argtypes = [ctypes.c_void_p]
     L.vl_plan_destroy.restype = None
+    L.vl_autotune.argtypes = [P(vl_job), ctypes.c_int32, P(vl_batch_opts), ctypes.c_void_p, ctypes.c_size_t,
+                              ctypes.c_void_p, ctypes.c_int32, P(vl_batch_opts), P(ctypes.c_float)]
+    L.vl_autotune.restype = ctypes.c_int32
+    L.vl_autotune_clear.argtypes = []
+    L.vl_autotune_clear.restype = None
     L.vl_server_create.argtypes = [P(vl_server_opts), P(ctypes.c_void_p)]
     L.vl_server_create.restype = ctypes.c_int32
     L.vl_server_submit.argtypes = [ctypes.c_void_p, P(vl_job), ctypes.c_int32, P(vl_proof), P(ctypes.c_uint64)]
@@ -326,6 +333,21 @@ def vl_plan_phase_ms(plan, max_runs, reset=1):
 
 def vl_plan_destroy(plan):
     lib().vl_plan_destroy(plan)
+
+
+def vl_autotune(jobs, ws_ptr, ws_bytes, base=None, stream=None, runs=0):
+    """Options for `jobs` chosen by timing candidate plans (cached per shape signature).
+    Returns (vl_batch_opts, ms per run)."""
+    arr = jobs_array(jobs)
+    best = vl_batch_opts()
+    ms = ctypes.c_float()
+    _check(lib().vl_autotune(arr, len(jobs), ctypes.byref(base) if base is not None else None, ws_ptr, ws_bytes,
+                             _stream_ptr(stream), runs, ctypes.byref(best), ctypes.byref(ms)), "vl_autotune")
+    return best, ms.value
+
+
+def vl_autotune_clear():
+    lib().vl_autotune_clear()
 
 
 def vl_server_create(arena_ptr, arena_bytes, max_inflight=0, max_batch_requests=0, wait_limit_us=0):

@@ -107,7 +107,7 @@ struct TcTile {
 static_assert(sizeof(TcTile) == 64, "one 64-byte tile descriptor");
 static constexpr int TC_M = 128;        // lines per tile (MMA M)
 static constexpr int TC_KS = 64;        // reduction entries per pipeline stage
-static constexpr int TC_SEG = 16384;    // reduction entries per tile at most
+static constexpr int TC_SEG = 16384;    // reduction entries per tile (default; at most 32768)
 static constexpr int TC_CONV_WARPS = 8;   // int16 -> fp16 byte operands
 static constexpr int TC_DRAIN_WARPS = 8;  // TMEM -> digit sums (two groups of four lane quarters)
 // warp 0 producer, warp 1 first MMA issuer (TMEM owner), then converters,

@@ -171,15 +171,16 @@ void add_fold_task(vl_plan* p, const vl_mat& M, int32_t mode, int proof, int sid
     p->tasks.push_back(t);
     tabs |= TAB_BYTES;
     const int lines = mode == MODE_COLSUM ? t.cols : t.rows, red = mode == MODE_COLSUM ? t.rows : t.cols;
+    const int seg = p->opts.tc_seg > 0 ? p->opts.tc_seg : TC_SEG;
     for (int w0 = 0; w0 < lines; w0 += TC_M)
-      for (int k0 = 0; k0 < red; k0 += TC_SEG)
+      for (int k0 = 0; k0 < red; k0 += seg)
       {
         TcTile tt{};
         tt.mode = mode;
         tt.w0 = w0;
         tt.nw = std::min(TC_M, lines - w0);
         tt.k0 = k0;
-        tt.nk = std::min(TC_SEG, red - k0);
+        tt.nk = std::min(seg, red - k0);
         tt.proof = proof;
         tt.task = task;
         p->tc_tiles.push_back(tt);  // device pointers are filled in at bind time
@@ -288,6 +289,8 @@ void build_items(vl_plan* p) {
 
 int build_plan(vl_plan* p) {
   const int np = (int)p->jobs.size();
+  // u32 digit sums hold at most 512 stages of 64 entries
+  if (p->opts.tc_seg < 0 || p->opts.tc_seg % TC_KS || p->opts.tc_seg > 32768) return VL_EINVAL;
   p->proofs.resize(np);
   p->pp.resize(np);
   size_t off = 0;

@@ -382,3 +382,31 @@ def test_tensor_core_fold_extreme_entries():
         proofs = B.vl_prove_batch(jb, ws.data_ptr(), nb, opts=opts)
         assert B.proof_bytes(proofs[0]) == oracle.prove_matmul(P, Q, 0, 0, seed=9).to_bytes()
         assert B.proof_bytes(proofs[1]) == oracle.prove_matmul(Q, P, 1, 1, seed=10).to_bytes()
+
+
+def test_autotuned_options_prove_the_same_and_are_cached():
+    jobs = _lora_jobs(n=64, d=256, k=512, r=16, layer=8, proj="k")
+    dj, keep = _dev_jobs(jobs)
+    refs = [oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes() for j in jobs]
+    # room for the largest candidate plan plus the proofs
+    need = max(B.vl_workspace_bytes(dj, o) for o in _opt_variants())
+    nb = need + 64 * 1024
+    ws = _ws(nb)
+    B.vl_autotune_clear()
+    best, ms = B.vl_autotune(dj, ws.data_ptr(), nb, runs=2)
+    assert ms > 0
+    again, ms2 = B.vl_autotune(dj, ws.data_ptr(), nb, runs=2)
+    assert bytes(again) == bytes(best) and ms2 == ms  # cached
+    nbb = B.vl_workspace_bytes(dj, best)
+    ws2 = _ws(nbb)
+    proofs = B.vl_prove_batch(dj, ws2.data_ptr(), nbb, opts=best)
+    assert [B.proof_bytes(p) for p in proofs] == refs
+
+
+def _opt_variants():
+    out = []
+    for eng, pers, seg in ((0, 2, 0), (1, 2, 0), (0, 1, 0), (0, 2, 2048)):
+        o = B.vl_batch_opts()
+        o.fold_engine, o.persistent, o.tc_seg = eng, pers, seg
+        out.append(o)
+    return out

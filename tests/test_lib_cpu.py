@@ -162,3 +162,12 @@ def test_server_rejects_bad_options_before_cuda():
     assert L.vl_server_create(ctypes.byref(o), ctypes.byref(s)) == B.VL_EINVAL  # reserved field set
     assert L.vl_server_submit(None, None, 0, None, None) == B.VL_EINVAL
     assert L.vl_server_destroy(None) == B.VL_EINVAL
+
+
+def test_autotune_rejects_bad_arguments_before_cuda():
+    L = B.lib()
+    best = B.vl_batch_opts()
+    assert L.vl_autotune(None, 1, None, 4096, 1 << 20, None, 0, ctypes.byref(best), None) == B.VL_EINVAL
+    jb = (B.vl_job * 1)()
+    assert L.vl_autotune(jb, 1, None, 4096 + 8, 1 << 20, None, 0, ctypes.byref(best), None) == B.VL_EINVAL  # unaligned
+    assert L.vl_autotune(jb, 0, None, 4096, 1 << 20, None, 0, ctypes.byref(best), None) == B.VL_EINVAL
