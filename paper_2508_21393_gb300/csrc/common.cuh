@@ -124,7 +124,7 @@ static constexpr int TC_NC = 4;   // converted-operand stages (TMEM, 64 columns 
 static constexpr int TC_NA = 4;   // accumulator buffers (TMEM, 64 columns each)
 static constexpr int TC_HR = 32;  // stage-header ring (> TC_NR + TC_NC + TC_NA)
 static_assert(TC_HR > TC_NR + TC_NC + TC_NA, "header ring");
-static constexpr int TC_SMEM = 1024 + TC_NR * 16384 + TC_NW * 4096 + 3072;
+static constexpr int TC_SMEM = 1024 + TC_NR * 16384 + TC_NW * 4096 + 5120 + 3072;
 
 struct FoldTile {
   int32_t task;

@@ -12,7 +12,8 @@
 //     sum_i E_i p[w, i] = sum_{t=0}^{32} 2^(8t) s_t,  s_t = D_lo[w, t] + D_hi[w, t-1].
 // All operands are integers in [0, 255] (exact in fp16); a product is at most
 // 255^2, so over one 64-entry stage D_lo + D_hi < 2^23 and fp32 accumulation
-// is exact.  Adding 2^23 puts the sum in [2^23, 2^24), where the fp32 bit
+// is exact.  The lo accumulator of each stage starts at 2^23 (one MMA of
+// constants), which puts D_lo + D_hi in [2^23, 2^24), where the fp32 bit
 // pattern is 0x4B000000 + s_t: the drainers add bit patterns as 32-bit
 // integers and remove the offsets once per tile.  At the end of a tile the 33
 // digit sums become the eight 64-bit column sums sum_j 2^(32j) col_j of the
@@ -52,7 +53,9 @@ namespace {
 
 constexpr int SM_RAW = 0;                          // TC_NR x 16 KB of int16 operand
 constexpr int SM_W = SM_RAW + TC_NR * 16384;       // TC_NW x 4 KB of fp16 weight bytes
-constexpr int SM_HDR = SM_W + TC_NW * 4096;        // TC_HR stage headers
+constexpr int SM_ACONST = SM_W + TC_NW * 4096;    // 128 x 16 fp16, K-major: column 0 = 256
+constexpr int SM_BCONST = SM_ACONST + 4096;        // 16 x 32 fp16, MN-major: row 0 = 32768
+constexpr int SM_HDR = SM_BCONST + 1024;           // TC_HR stage headers
 constexpr int SM_BAR = SM_HDR + TC_HR * 32;
 // Completion of stage s's MMAs (both issuers) is one barrier of a ring of
 // TC_ND: the converters (TMEM operand reuse), the producer (weight slot
@@ -82,6 +85,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
          ((uint64_t)((sbo >> 4) & 0x3fff) << 32) | (1ull << 46);
 }
 
+// D (TMEM) (+)= A (shared memory) . B (shared memory).
+__device__ __forceinline__ void umma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
 // D (TMEM) (+)= A (TMEM, 128 lanes x 8 columns) . B (shared memory).
 __device__ __forceinline__ void umma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
@@ -101,6 +112,22 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 #define TC_R8(b) "=r"(r[b + 0]), "=r"(r[b + 1]), "=r"(r[b + 2]), "=r"(r[b + 3]), "=r"(r[b + 4]), "=r"(r[b + 5]), \
                  "=r"(r[b + 6]), "=r"(r[b + 7])
 
+// 16 columns into r[OFF .. OFF + 15].
+template <int OFF>
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : TC_R8(OFF), TC_R8(OFF + 8)
+      : "r"(taddr));
+}
+// 32 columns into r[0 .. 31].
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : TC_R8(0), TC_R8(8), TC_R8(16), TC_R8(24)
+      : "r"(taddr));
+}
 // 8 columns into r[OFF .. OFF + 7].
 template <int OFF>
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[32]) {
@@ -195,20 +222,19 @@ __device__ __forceinline__ void mark_timeout(const DevProof* proofs, const TcTil
 
 // Drain one stage's accumulator columns (lo at ta, hi at ta + 32) into the
 // digit sums s_t, t in [T0, T1]:  dg[t - T0] += bits(2^23 + s_t), with
-// s_t = lo_t + hi_{t-1}.
+// s_t = lo_t + hi_{t-1}; the lo accumulator starts at 2^23 (init MMA), so
+// one fp32 add gives 2^23 + s_t, exact below 2^24.
 template <int T0, int T1>
 __device__ __forceinline__ void drain_digits(uint32_t ta, uint32_t (&dg)[17], uint32_t acc_empty) {
-  constexpr int LA = T0, LB = T1 < 31 ? T1 : 31;           // lo columns used
-  constexpr int HA = T0 > 0 ? T0 - 1 : 0, HB = T1 - 1;      // hi columns used
+  static_assert((T0 == 0 && T1 == 16) || (T0 == 17 && T1 == 32), "digit groups");
   uint32_t L[32], H[32];
-  if (LA <= 7 && LB >= 0) tmem_ld8<0>(ta + 0, L);
-  if (LA <= 15 && LB >= 8) tmem_ld8<8>(ta + 8, L);
-  if (LA <= 23 && LB >= 16) tmem_ld8<16>(ta + 16, L);
-  if (LA <= 31 && LB >= 24) tmem_ld8<24>(ta + 24, L);
-  if (HA <= 7 && HB >= 0) tmem_ld8<0>(ta + 32, H);
-  if (HA <= 15 && HB >= 8) tmem_ld8<8>(ta + 40, H);
-  if (HA <= 23 && HB >= 16) tmem_ld8<16>(ta + 48, H);
-  if (HA <= 31 && HB >= 24) tmem_ld8<24>(ta + 56, H);
+  if (T0 == 0) {
+    tmem_ld32(ta, L);            // lo 0..31 (0..16 used)
+    tmem_ld16<0>(ta + 32, H);    // hi 0..15
+  } else {
+    tmem_ld16<16>(ta + 16, L);   // lo 16..31 (17..31 used)
+    tmem_ld16<16>(ta + 48, H);   // hi 16..31
+  }
   tmem_wait_ld();
   tc_fence_before();
   __syncwarp();
@@ -216,9 +242,9 @@ __device__ __forceinline__ void drain_digits(uint32_t ta, uint32_t (&dg)[17], ui
 #pragma unroll
   for (int t = T0; t <= T1; t++) {
     uint32_t v;
-    if (t == 0) v = fbits_add(L[0], 0x4B000000u);
+    if (t == 0) v = L[0];
     else if (t == 32) v = fbits_add(H[31], 0x4B000000u);
-    else v = fbits_add(fbits_add(L[t], H[t - 1]), 0x4B000000u);  // both sums exact below 2^24
+    else v = fbits_add(L[t], H[t - 1]);
     dg[t - T0] += v;
   }
 }
@@ -275,6 +301,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(base + SM_TMEM),
                  "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (warp >= 2 && warp < 2 + TC_CONV_WARPS) {
+    // Constant operands of the init MMA: A[m][0] = 256, B[0][n] = 32768, so
+    // the lo accumulator starts at 2^23; every other entry 0.
+    const int wi = tid - 64, nw = 32 * TC_CONV_WARPS;
+    uint32_t* ac = reinterpret_cast<uint32_t*>(sm + SM_ACONST);
+    // A K-major: entry (m, k = 0) at byte m * 16 of the first 2 KB (k < 8).
+    for (int i = wi; i < 1024; i += nw) ac[i] = (i < 512 && (i & 3) == 0) ? 0x5C00u : 0u;
+    // B MN-major: row k = 0 is bytes [0, 16) of each 128-byte core matrix of
+    // the first 512 bytes (k < 8).
+    uint32_t* bc = reinterpret_cast<uint32_t*>(sm + SM_BCONST);
+    for (int i = wi; i < 256; i += nw) bc[i] = (i < 128 && (i & 31) < 4) ? 0x78007800u : 0u;
+    fence_proxy_async_smem();
   }
   tc_fence_before();
   __syncthreads();
@@ -372,8 +411,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_fence_after();
         const uint32_t wts = base + SM_W + ws * 4096;
         const uint32_t d = tmem + 64 * a + half, av = tmem + ACONV_COL + 64 * c + half;
+        if (half == 0)  // lo accumulator := 2^23 (A, B constants in shared memory)
+          umma_ss(d, sdesc(base + SM_ACONST, 2048, 128), sdesc(base + SM_BCONST, 512, 128), IDESC, 0);
 #pragma unroll
-        for (int ks = 0; ks < 4; ks++) umma_ts(d, av + 8 * ks, sdesc(wts + ks * 1024, 512, 128), IDESC, ks > 0);
+        for (int ks = 0; ks < 4; ks++)
+          umma_ts(d, av + 8 * ks, sdesc(wts + ks * 1024, 512, 128), IDESC, half == 0 || ks > 0);
         umma_commit(bars.done(s));
       }
       // every MMA this thread issued has completed before TMEM is freed
