@@ -130,7 +130,7 @@ typedef struct vl_batch_opts {
   int32_t rounds_variant; /* rounds kernel register budget: 7 or 4 CTAs per SM
                             (0: 7)                                           */
   int32_t tc_seg;        /* tensor-core fold: reduced entries per tile, a
-                            multiple of 64 up to 32768 (0: 16384); shorter
+                            multiple of 128 up to 32768 (0: 16384); shorter
                             segments spread narrow operands over more SMs */
   int32_t test_never_ready; /* fault injection for tests: 1 + index of a job
                             whose prologue never signals ready, so that its

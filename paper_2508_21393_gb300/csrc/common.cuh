@@ -47,7 +47,7 @@ struct DevProof {
   int32_t ntiles;          // fold tiles of this proof (both tasks)
   int32_t job;             // index of the proof in the caller's job list (output slot)
   int32_t tabA, tabB;      // weight tables each side needs: TAB_LIMBS and/or TAB_BYTES
-  uint32_t* w8A;           // tensor-core weights: E_u bytes as fp16, [m / 64 chunks] x 4 KB
+  uint32_t* w8A;           // tensor-core weights: E_u bytes as fp16, [ceil(m / 128) x 2 chunks] x 4 KB
   uint32_t* w8B;           // E_v bytes
 };
 
@@ -56,7 +56,7 @@ struct DevProof {
 //   TAB_BYTES: the 32 bytes of each E entry as fp16 values, in the shared-
 //              memory operand layout of the tensor-core fold (per 64-entry
 //              chunk: [8 entry groups][4 byte groups][8 entries][8 bytes]),
-//              zero past the last entry up to the chunk boundary
+//              zero past the last entry up to a multiple of 128 entries
 enum : int32_t { TAB_LIMBS = 1, TAB_BYTES = 2 };
 
 // Persistent step: work items in queue order.
@@ -91,7 +91,7 @@ struct FoldTask {
 
 // Tensor-core fold tile: stored lines [w0, w0 + nw) (columns for COLSUM,
 // rows for ROWDOT; nw <= 128), reduced over [k0, k0 + nk) (k0 a multiple of
-// 64, nk <= TC_SEG).  Everything a CTA needs to stream the tile is resolved
+// 128, nk <= 32768).  Everything a CTA needs to stream the tile is resolved
 // at bind time, so taking a tile is one 64-byte load.
 struct TcTile {
   const void* tmap;         // TMA tensor map of the stored matrix (device)
@@ -106,8 +106,9 @@ struct TcTile {
 };
 static_assert(sizeof(TcTile) == 64, "one 64-byte tile descriptor");
 static constexpr int TC_M = 128;        // lines per tile (MMA M)
-static constexpr int TC_KS = 64;        // reduction entries per pipeline stage
-static constexpr int TC_SEG = 16384;    // reduction entries per tile (default; at most 32768)
+static constexpr int TC_KS = 128;       // reduction entries per pipeline stage
+static constexpr int TC_KP = 64;        // entries per exact fp32 accumulation period (two per stage)
+static constexpr int TC_SEG = 16384;    // reduction entries per tile (default; a multiple of TC_KS, at most 32768)
 static constexpr int TC_CONV_WARPS = 8;   // int16 -> fp16 byte operands
 static constexpr int TC_DRAIN_WARPS = 8;  // TMEM -> digit sums (two groups of four lane quarters)
 // warp 0 producer, warp 1 first MMA issuer (TMEM owner), then converters,
@@ -115,16 +116,16 @@ static constexpr int TC_DRAIN_WARPS = 8;  // TMEM -> digit sums (two groups of f
 static constexpr int TC_THREADS = 32 * (5 + TC_CONV_WARPS + TC_DRAIN_WARPS);
 // Ring depths (overridable at build time for tuning sweeps).
 #ifndef TC_NR
-#define TC_NR 8  // operand (TMA) stages, 16 KB of shared memory each
+#define TC_NR 5  // operand (TMA) stages, 32 KB of shared memory each
 #endif
 #ifndef TC_NW
-#define TC_NW 8  // weight stages, 4 KB each
+#define TC_NW 4  // weight stages, 8 KB each
 #endif
-static constexpr int TC_NC = 4;   // converted-operand stages (TMEM, 64 columns each)
-static constexpr int TC_NA = 4;   // accumulator buffers (TMEM, 64 columns each)
+static constexpr int TC_NC = 2;   // converted-operand stages (TMEM, 128 columns each)
+static constexpr int TC_NA = 2;   // accumulator buffers (TMEM, 128 columns each: two periods)
 static constexpr int TC_HR = 32;  // stage-header ring (> TC_NR + TC_NC + TC_NA)
 static_assert(TC_HR > TC_NR + TC_NC + TC_NA, "header ring");
-static constexpr int TC_SMEM = 1024 + TC_NR * 16384 + TC_NW * 4096 + 5120 + 3072;
+static constexpr int TC_SMEM = 1024 + TC_NR * 32768 + TC_NW * 8192 + 5120 + 3072;
 
 struct FoldTile {
   int32_t task;

@@ -166,8 +166,8 @@ void add_fold_task(vl_plan* p, const vl_mat& M, int32_t mode, int proof, int sid
   if (tc_eligible(p, M)) {
     // Tensor-core tiles: 128 lines by at most TC_SEG reduced entries.
     t.bulk = 2;
-    t.box_w = mode == MODE_ROWDOT ? TC_KS : TC_M;  // row dots: 64 entries x 128 lines (128B-swizzled)
-    t.box_h = mode == MODE_ROWDOT ? TC_M : TC_KS;  // column sums: 128 lines x 64 entries (no swizzle)
+    t.box_w = mode == MODE_ROWDOT ? TC_KP : TC_M;  // row dots: 64 entries x 128 lines (128B-swizzled), two per stage
+    t.box_h = mode == MODE_ROWDOT ? TC_M : TC_KS;  // column sums: 128 lines x 128 entries (no swizzle)
     p->tasks.push_back(t);
     tabs |= TAB_BYTES;
     const int lines = mode == MODE_COLSUM ? t.cols : t.rows, red = mode == MODE_COLSUM ? t.rows : t.cols;
@@ -385,11 +385,11 @@ int build_plan(vl_plan* p) {
     }
     if (P.tabA & TAB_BYTES) {
       p->pp[i].w8A = off;
-      off = align_up(off + 4096 * (size_t)((P.m + TC_KS - 1) / TC_KS));
+      off = align_up(off + 8192 * (size_t)((P.m + TC_KS - 1) / TC_KS));
     }
     if (P.tabB & TAB_BYTES) {
       p->pp[i].w8B = off;
-      off = align_up(off + 4096 * (size_t)((P.n + TC_KS - 1) / TC_KS));
+      off = align_up(off + 8192 * (size_t)((P.n + TC_KS - 1) / TC_KS));
     }
     p->pp[i].fA = off;
     off = align_up(off + sizeof(Fr) * ((size_t)1 << P.d1));
@@ -489,7 +489,7 @@ bool encode_task_map(const FoldTask& t, CUtensorMap* map) {
 
 // TMA descriptor of a tensor-core task's stored matrix: uint16 boxes of 64
 // columns (128 bytes, 128-byte swizzle) by 128 rows for row dots, 128 columns
-// by 64 rows (no swizzle: rows of 256 contiguous bytes stream better) for
+// by 128 rows (no swizzle: rows of 256 contiguous bytes stream better) for
 // column sums; out-of-range entries read as zero.
 bool encode_tc_map(const FoldTask& t, CUtensorMap* map) {
   if ((reinterpret_cast<uintptr_t>(t.mat) & 15) || (t.ld & 7)) return false;

@@ -11,9 +11,9 @@
 // index i), and
 //     sum_i E_i p[w, i] = sum_{t=0}^{32} 2^(8t) s_t,  s_t = D_lo[w, t] + D_hi[w, t-1].
 // All operands are integers in [0, 255] (exact in fp16); a product is at most
-// 255^2, so over one 64-entry stage D_lo + D_hi < 2^23 and fp32 accumulation
-// is exact.  The lo accumulator of each stage starts at 2^23 (one MMA of
-// constants), which puts D_lo + D_hi in [2^23, 2^24), where the fp32 bit
+// 255^2, so over one 64-entry accumulation period D_lo + D_hi < 2^23 and fp32
+// accumulation is exact.  The lo accumulator of each period starts at 2^23
+// (one MMA of constants), which puts D_lo + D_hi in [2^23, 2^24), where the fp32 bit
 // pattern is 0x4B000000 + s_t: the drainers add bit patterns as 32-bit
 // integers and remove the offsets once per tile.  At the end of a tile the 33
 // digit sums become the eight 64-bit column sums sum_j 2^(32j) col_j of the
@@ -23,25 +23,27 @@
 // Roles in a CTA (one CTA per SM; CTA b takes tiles b, b + grid, ... of a
 // list sorted longest first), each running at its own pace and linked only by
 // mbarriers:
-//   warp 0       producer: per stage one TMA box of the operand (row dots:
-//                64 entries x 128 lines, 128B-swizzled; column sums: 128 lines
-//                x 64 entries) into one of TC_NR shared-memory slots,
-//                and the stage's 4 KB of fp16 weight bytes into one of TC_NW
+// A pipeline stage is 128 lines x 128 entries: two accumulation periods.
+//   warp 0       producer: per stage the operand (row dots: two boxes of 64
+//                entries x 128 lines, 128B-swizzled; column sums: one box of
+//                128 lines x 128 entries) into one of TC_NR shared-memory
+//                slots, and the stage's 8 KB of fp16 weight bytes into one of TC_NW
 //   warps 1, 18-20  MMA issuers (warp 1 also owns TMEM, 512 columns): a
 //                pair per stage parity, in each pair one thread for the lo
-//                and one for the hi products; 4 MMAs (K = 16) per stage and
-//                issuer, A read from TMEM and B (weights) from shared memory,
-//                into one of TC_NA accumulator buffers (one thread issues an
+//                and one for the hi products; per period 4 MMAs (K = 16) with
+//                A read from TMEM and B (weights) from shared memory, into one
+//                of TC_NA accumulator buffers (one thread issues an
 //                MMA only every ~60-120 cycles; four keep the tensor core fed)
-//   warps 2-9    converters: one thread per (line, half of the stage's 64
-//                entries) reads its entries from the swizzled box, forms the
+//   warps 2-9    converters: one thread per (line, half of the stage's 128
+//                entries) reads its entries from the box, forms the
 //                fp16 lo/hi operand rows and stores them to TMEM (one of
 //                TC_NC operand buffers) with tcgen05.st
 //   warps 10-17  drainers: accumulator buffer -> per-line digit sums (two
 //                groups of four warps, one warp per TMEM lane quarter, each
 //                group half of the 33 digits); tile epilogue
-// TMEM columns: accumulator a at 64a ([lo 32 | hi 32]), operand buffer c at
-// 256 + 64c ([lo 32 | hi 32], two fp16 per column).  Stage headers (tile,
+// TMEM columns: accumulator buffer a at 128a (period p at +64p: [lo 32 |
+// hi 32]), operand buffer c at 256 + 128c ([lo 64 | hi 64], two fp16 per
+// column).  Stage headers (tile,
 // stage) sit in a ring of TC_HR entries, longer than the stages any role can
 // be ahead of another.  Every wait is bounded; a wait that runs out marks the
 // proof VL_ETIMEOUT, and the CTA drains its copies and MMAs before it frees
@@ -51,9 +53,9 @@
 namespace vl {
 namespace {
 
-constexpr int SM_RAW = 0;                          // TC_NR x 16 KB of int16 operand
-constexpr int SM_W = SM_RAW + TC_NR * 16384;       // TC_NW x 4 KB of fp16 weight bytes
-constexpr int SM_ACONST = SM_W + TC_NW * 4096;    // 128 x 16 fp16, K-major: column 0 = 256
+constexpr int SM_RAW = 0;                          // TC_NR x 32 KB of int16 operand
+constexpr int SM_W = SM_RAW + TC_NR * 32768;       // TC_NW x 8 KB of fp16 weight bytes
+constexpr int SM_ACONST = SM_W + TC_NW * 8192;    // 128 x 16 fp16, K-major: column 0 = 256
 constexpr int SM_BCONST = SM_ACONST + 4096;        // 16 x 32 fp16, MN-major: row 0 = 32768
 constexpr int SM_HDR = SM_BCONST + 1024;           // TC_HR stage headers
 constexpr int SM_BAR = SM_HDR + TC_HR * 32;
@@ -70,8 +72,8 @@ constexpr int NBAR = 2 * TC_NR + TC_NC + TC_NA + TC_NW + TC_ND + 1;
 constexpr int SM_TMEM = SM_BAR + NBAR * 8;
 static_assert(SM_TMEM + 16 <= TC_SMEM - 1024, "shared-memory layout");
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t ACONV_COL = 64 * TC_NA;
-static_assert(ACONV_COL + 64 * TC_NC <= TMEM_COLS, "TMEM columns");
+constexpr uint32_t ACONV_COL = 128 * TC_NA;
+static_assert(ACONV_COL + 128 * TC_NC <= TMEM_COLS, "TMEM columns");
 
 // Instruction descriptor of kind::f16: fp32 accumulator, fp16 A and B,
 // A K-major (from TMEM), B MN-major, N = 32, M = 128.
@@ -236,9 +238,11 @@ __device__ __forceinline__ void drain_digits(uint32_t ta, uint32_t (&dg)[17], ui
     tmem_ld16<16>(ta + 48, H);   // hi 16..31
   }
   tmem_wait_ld();
-  tc_fence_before();
-  __syncwarp();
-  if ((threadIdx.x & 31) == 0) mbar_arrive(acc_empty);
+  if (acc_empty) {  // last period of the stage: the buffer is free
+    tc_fence_before();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(acc_empty);
+  }
 #pragma unroll
   for (int t = T0; t <= T1; t++) {
     uint32_t v;
@@ -254,7 +258,7 @@ __device__ __forceinline__ void drain_digits(uint32_t ta, uint32_t (&dg)[17], ui
 // s_32 goes to col_7 as s_32 . 2^32 (2^256 = 2^32 . 2^224).
 template <int T0, int T1>
 __device__ __forceinline__ void tc_epilogue(uint32_t (&dg)[17], int nst, unsigned long long* acc) {
-  const uint32_t off = (uint32_t)nst * 0x4B000000u;
+  const uint32_t off = (uint32_t)(2 * nst) * 0x4B000000u;  // two drains per stage
 #pragma unroll
   for (int j = 0; j < 8; j++) {
     uint64_t c = 0;
@@ -350,7 +354,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           hdr[s % TC_HR] = StageHdr{done ? -1 : tile, st, nst, T.mode, T.nw, 0, T.acc};
           last_use[slot] = use;
-          const uint32_t raw = base + SM_RAW + slot * 16384;
+          const uint32_t raw = base + SM_RAW + slot * 32768;
           if (done) {
             mbar_arrive(bars.raw_full(slot));
             continue;
@@ -360,13 +364,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             break;
           }
           const int kk = T.k0 + st * TC_KS;
-          mbar_arrive_expect_tx(bars.w_full(ws), 4096);
-          bulk_g2s(base + SM_W + ws * 4096, reinterpret_cast<const uint8_t*>(T.w8) + (size_t)(kk / TC_KS) * 4096,
-                   4096, bars.w_full(ws));
+          mbar_arrive_expect_tx(bars.w_full(ws), 8192);
+          bulk_g2s(base + SM_W + ws * 8192, reinterpret_cast<const uint8_t*>(T.w8) + (size_t)(kk / TC_KP) * 4096,
+                   8192, bars.w_full(ws));
           last_wuse[ws] = wuse;
-          mbar_arrive_expect_tx(bars.raw_full(slot), 16384);
-          if (T.mode == MODE_ROWDOT) tma_load_2d(raw, T.tmap, kk, T.w0, bars.raw_full(slot));
-          else tma_load_2d(raw, T.tmap, T.w0, kk, bars.raw_full(slot));
+          mbar_arrive_expect_tx(bars.raw_full(slot), 32768);
+          if (T.mode == MODE_ROWDOT) {
+            tma_load_2d(raw, T.tmap, kk, T.w0, bars.raw_full(slot));
+            tma_load_2d(raw + 16384, T.tmap, kk + TC_KP, T.w0, bars.raw_full(slot));
+          } else {
+            tma_load_2d(raw, T.tmap, T.w0, kk, bars.raw_full(slot));
+          }
         }
         if (!done) {
           tile += G;
@@ -409,13 +417,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t wts = base + SM_W + ws * 4096;
-        const uint32_t d = tmem + 64 * a + half, av = tmem + ACONV_COL + 64 * c + half;
-        if (half == 0)  // lo accumulator := 2^23 (A, B constants in shared memory)
-          umma_ss(d, sdesc(base + SM_ACONST, 2048, 128), sdesc(base + SM_BCONST, 512, 128), IDESC, 0);
+        const uint32_t wts = base + SM_W + ws * 8192;
 #pragma unroll
-        for (int ks = 0; ks < 4; ks++)
-          umma_ts(d, av + 8 * ks, sdesc(wts + ks * 1024, 512, 128), IDESC, half == 0 || ks > 0);
+        for (int p = 0; p < 2; p++) {  // the stage's two accumulation periods
+          const uint32_t d = tmem + 128 * a + 64 * p + half;
+          const uint32_t av = tmem + ACONV_COL + 128 * c + 2 * half + 32 * p;  // lo at +0, hi at +64
+          if (half == 0)  // lo accumulator := 2^23 (A, B constants in shared memory)
+            umma_ss(d, sdesc(base + SM_ACONST, 2048, 128), sdesc(base + SM_BCONST, 512, 128), IDESC, 0);
+#pragma unroll
+          for (int ks = 0; ks < 4; ks++)
+            umma_ts(d, av + 8 * ks, sdesc(wts + (4 * p + ks) * 1024, 512, 128), IDESC, half == 0 || ks > 0);
+        }
         umma_commit(bars.done(s));
       }
       // every MMA this thread issued has completed before TMEM is freed
@@ -425,9 +437,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp < 2 + TC_CONV_WARPS) {
     // ---------------------------------------------------------------- converters
     // Thread = line m (its TMEM lane) x half kh of the stage's 64 entries.
-    const int quarter = warp & 3, kh = (warp - 2) >> 2;
+    const int quarter = warp & 3, kh = (warp - 2) >> 2;  // entries [64 kh, 64 kh + 64) of each stage
     const int m = 32 * quarter + lane;
-    const uint32_t tq = tmem + ((uint32_t)(32 * quarter) << 16) + ACONV_COL + 16 * kh;
+    const uint32_t tq = tmem + ((uint32_t)(32 * quarter) << 16) + ACONV_COL + 32 * kh;
     int ends = 0;
     for (int s = 0;; s++) {
       const int slot = s % TC_NR, c = s % TC_NC;
@@ -442,34 +454,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       if (h.tile >= 0) {
-        const uint8_t* raw = sm + SM_RAW + slot * 16384;
-        uint32_t w[16];  // entries 32 kh + 2i, 32 kh + 2i + 1 of line m
-        if (h.mode == MODE_ROWDOT) {
-          // box [128 lines][64 entries]: chunk j of line m at 16 (j ^ (m % 8))
+        const uint8_t* raw = sm + SM_RAW + slot * 32768;
 #pragma unroll
-          for (int j = 0; j < 4; j++) {
-            const uint4 v = *reinterpret_cast<const uint4*>(raw + m * 128 + (((4 * kh + j) ^ (m & 7)) << 4));
-            w[4 * j] = v.x; w[4 * j + 1] = v.y; w[4 * j + 2] = v.z; w[4 * j + 3] = v.w;
+        for (int j2 = 0; j2 < 2; j2++) {  // 32 entries at a time: e0 = 64 kh + 32 j2
+          uint32_t w[16];  // entry pairs (e0 + 2i, e0 + 2i + 1) of line m
+          if (h.mode == MODE_ROWDOT) {
+            // box kh [128 lines][64 entries]: chunk j of line m at 16 (j ^ (m % 8))
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+              const uint4 v = *reinterpret_cast<const uint4*>(raw + 16384 * kh + m * 128 +
+                                                              (((4 * j2 + j) ^ (m & 7)) << 4));
+              w[4 * j] = v.x; w[4 * j + 1] = v.y; w[4 * j + 2] = v.z; w[4 * j + 3] = v.w;
+            }
+          } else {
+            // box [128 entries][128 lines], no swizzle: line m of entry k at 256 k + 2 m
+            const uint8_t* col = raw + 2 * m + (64 * kh + 32 * j2) * 256;
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+              const uint32_t a = *reinterpret_cast<const uint16_t*>(col + (2 * i) * 256);
+              const uint32_t b = *reinterpret_cast<const uint16_t*>(col + (2 * i + 1) * 256);
+              w[i] = __byte_perm(a, b, 0x5410);
+            }
           }
-        } else {
-          // box [64 entries][128 lines], no swizzle: line m of entry k at 256 k + 2 m
-          const uint8_t* col = raw + 2 * m + 32 * kh * 256;
+          uint32_t lo[16], hi[16];
 #pragma unroll
           for (int i = 0; i < 16; i++) {
-            const uint32_t a = *reinterpret_cast<const uint16_t*>(col + (2 * i) * 256);
-            const uint32_t b = *reinterpret_cast<const uint16_t*>(col + (2 * i + 1) * 256);
-            w[i] = __byte_perm(a, b, 0x5410);
+            const uint32_t t = w[i] ^ 0x80008000u;  // p = x + 2^15, per entry
+            lo[i] = bytes_f16x2(t, 0x4240);
+            hi[i] = bytes_f16x2(t, 0x4341);
           }
+          tmem_st16(tq + 128 * c + 16 * j2, lo);
+          tmem_st16(tq + 128 * c + 64 + 16 * j2, hi);
         }
-        uint32_t lo[16], hi[16];
-#pragma unroll
-        for (int i = 0; i < 16; i++) {
-          const uint32_t t = w[i] ^ 0x80008000u;  // p = x + 2^15, per entry
-          lo[i] = bytes_f16x2(t, 0x4240);
-          hi[i] = bytes_f16x2(t, 0x4341);
-        }
-        tmem_st16(tq + 64 * c, lo);
-        tmem_st16(tq + 64 * c + 32, hi);
         tmem_wait_st();
       }
       tc_fence_before();
@@ -497,9 +513,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const StageHdr h = hdr[s % TC_HR];
       if (h.tile < 0) break;
       tc_fence_after();
-      const uint32_t ta = tq + 64 * a;
-      if (grp == 0) drain_digits<0, 16>(ta, dg, bars.acc_empty(a));
-      else drain_digits<17, 32>(ta, dg, bars.acc_empty(a));
+      const uint32_t ta = tq + 128 * a;
+      if (grp == 0) {
+        drain_digits<0, 16>(ta, dg, 0);
+        drain_digits<0, 16>(ta + 64, dg, bars.acc_empty(a));
+      } else {
+        drain_digits<17, 32>(ta, dg, 0);
+        drain_digits<17, 32>(ta + 64, dg, bars.acc_empty(a));
+      }
       if (h.stage == h.nst - 1) {
         if (line < h.nw) {
           unsigned long long* acc = h.acc + (size_t)line * 8;

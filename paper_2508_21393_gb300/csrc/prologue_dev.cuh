@@ -83,7 +83,7 @@ __device__ static Fr build_eq(const Fr* x, int d, int size, int tabs, Fr* out, u
     sum[0] = fr_add(sum[0], e);
   }
   if (tabs & TAB_BYTES) {
-    const int end = (size + 63) & ~63;
+    const int end = (size + 127) & ~127;  // whole 128-entry stages of the tensor-core fold
     for (int i = size + tid; i < end; i += blockDim.x) store_w8(w8, i, fr_zero());
   }
   block_sum_fr<1>(sum, red);
