@@ -70,7 +70,7 @@ def parse():
                     help="phase launches: 0 tensor-core fold where TMA can address the operand, 1 CUDA cores only")
     ap.add_argument("--groups", type=int, default=0,
                     help="phase launches: proof groups pipelined over three streams (0: library default)")
-    ap.add_argument("--rounds-variant", type=int, default=0, choices=[0, 4, 7],
+    ap.add_argument("--rounds-variant", type=int, default=0, choices=[0, 2, 3, 4, 7],
                     help="rounds kernel register budget (CTAs per SM); 0 = library default")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (it also stays off when launch or tile options are given)")

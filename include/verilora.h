@@ -127,8 +127,9 @@ typedef struct vl_batch_opts {
   int32_t wait_limit_us; /* bound on any single device-side wait, in us (0: 2 s);
                             a wait that runs out sets the proof's status to
                             VL_ETIMEOUT and its CTA returns                  */
-  int32_t rounds_variant; /* rounds kernel register budget: 7 or 4 CTAs per SM
-                            (0: 7)                                           */
+  int32_t rounds_variant; /* rounds kernel: CTAs per SM, 7, 4, 3 or 2 (0: 7);
+                            7 and 4 set the register budget, 3 and 2 also
+                            cap residency (fewer proofs share an SM)        */
   int32_t tc_seg;        /* tensor-core fold: reduced entries per tile, a
                             multiple of 128 up to 32768 (0: 16384); shorter
                             segments spread narrow operands over more SMs */

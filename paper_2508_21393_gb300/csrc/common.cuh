@@ -47,6 +47,7 @@ struct DevProof {
   int32_t ntiles;          // fold tiles of this proof (both tasks)
   int32_t job;             // index of the proof in the caller's job list (output slot)
   int32_t tabA, tabB;      // weight tables each side needs: TAB_LIMBS and/or TAB_BYTES
+  int32_t fdirA, fdirB;    // 1: the fold writes f_A (f_B) itself, reduced (no accumulators)
   uint32_t* w8A;           // tensor-core weights: E_u bytes as fp16, [ceil(m / 128) x 2 chunks] x 4 KB
   uint32_t* w8B;           // E_v bytes
 };
@@ -96,15 +97,17 @@ struct FoldTask {
 struct TcTile {
   const void* tmap;         // TMA tensor map of the stored matrix (device)
   const uint32_t* w8;       // fp16 weight-byte table of the task's side
-  unsigned long long* acc;  // accumulator rows of lines w0.. (8 per line)
+  unsigned long long* acc;  // accumulator rows of lines w0.. (8 per line), or
+  Fr* f;                    //   when the tile covers the whole reduction: f[w0..] written reduced
+  const Fr* corr;           //   minus this offset correction (Montgomery)
   int32_t mode;
   int32_t w0, nw;
   int32_t k0, nk;
   int32_t proof;            // for status reports
   int32_t task;             // host bookkeeping
-  int32_t pad[3];
+  int32_t pad;
 };
-static_assert(sizeof(TcTile) == 64, "one 64-byte tile descriptor");
+static_assert(sizeof(TcTile) == 72, "tile descriptor");
 static constexpr int TC_M = 128;        // lines per tile (MMA M)
 static constexpr int TC_KS = 128;       // reduction entries per pipeline stage
 static constexpr int TC_KP = 64;        // entries per exact fp32 accumulation period (two per stage)
@@ -116,7 +119,7 @@ static constexpr int TC_DRAIN_WARPS = 8;  // TMEM -> digit sums (two groups of f
 static constexpr int TC_THREADS = 32 * (5 + TC_CONV_WARPS + TC_DRAIN_WARPS);
 // Ring depths (overridable at build time for tuning sweeps).
 #ifndef TC_NR
-#define TC_NR 5  // operand (TMA) stages, 32 KB of shared memory each
+#define TC_NR 4  // operand (TMA) stages, 32 KB of shared memory each
 #endif
 #ifndef TC_NW
 #define TC_NW 4  // weight stages, 8 KB each
@@ -125,7 +128,7 @@ static constexpr int TC_NC = 2;   // converted-operand stages (TMEM, 128 columns
 static constexpr int TC_NA = 2;   // accumulator buffers (TMEM, 128 columns each: two periods)
 static constexpr int TC_HR = 32;  // stage-header ring (> TC_NR + TC_NC + TC_NA)
 static_assert(TC_HR > TC_NR + TC_NC + TC_NA, "header ring");
-static constexpr int TC_SMEM = 1024 + TC_NR * 32768 + TC_NW * 8192 + 5120 + 3072;
+static constexpr int TC_SMEM = 1024 + TC_NR * 32768 + TC_NW * 8192 + 5120 + 4096 + 3072;
 
 struct FoldTile {
   int32_t task;

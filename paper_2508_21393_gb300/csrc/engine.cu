@@ -172,6 +172,8 @@ void add_fold_task(vl_plan* p, const vl_mat& M, int32_t mode, int proof, int sid
     tabs |= TAB_BYTES;
     const int lines = mode == MODE_COLSUM ? t.cols : t.rows, red = mode == MODE_COLSUM ? t.rows : t.cols;
     const int seg = p->opts.tc_seg > 0 ? p->opts.tc_seg : TC_SEG;
+    // One segment: each tile holds its lines' whole sums and writes f reduced.
+    (side ? p->proofs[proof].fdirB : p->proofs[proof].fdirA) = red <= seg ? 1 : 0;
     for (int w0 = 0; w0 < lines; w0 += TC_M)
       for (int k0 = 0; k0 < red; k0 += seg)
       {
@@ -359,10 +361,15 @@ int build_plan(vl_plan* p) {
   p->off_acc = off;
   for (int i = 0; i < np; i++) {
     const size_t kb = (size_t)p->proofs[i].k * 8 * sizeof(unsigned long long);
-    p->pp[i].accA = off;
-    off = align_up(off + kb);
-    p->pp[i].accB = off;
-    off = align_up(off + kb);
+    p->pp[i].accA = p->pp[i].accB = 0;
+    if (!p->proofs[i].fdirA) {
+      p->pp[i].accA = off;
+      off = align_up(off + kb);
+    }
+    if (!p->proofs[i].fdirB) {
+      p->pp[i].accB = off;
+      off = align_up(off + kb);
+    }
   }
   p->acc_bytes = off - p->off_acc;
   p->step_smem = std::max(p->fold_smem, std::max(PRO_SMEM, RND_SMEM));
@@ -531,8 +538,8 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
     P.eqB_soa = lb ? reinterpret_cast<uint32_t*>(ws + p->pp[i].soaB) : nullptr;
     P.w8A = (P.tabA & TAB_BYTES) ? reinterpret_cast<uint32_t*>(ws + p->pp[i].w8A) : nullptr;
     P.w8B = (P.tabB & TAB_BYTES) ? reinterpret_cast<uint32_t*>(ws + p->pp[i].w8B) : nullptr;
-    P.accA = reinterpret_cast<unsigned long long*>(ws + p->pp[i].accA);
-    P.accB = reinterpret_cast<unsigned long long*>(ws + p->pp[i].accB);
+    P.accA = P.fdirA ? nullptr : reinterpret_cast<unsigned long long*>(ws + p->pp[i].accA);
+    P.accB = P.fdirB ? nullptr : reinterpret_cast<unsigned long long*>(ws + p->pp[i].accB);
     P.fA = reinterpret_cast<Fr*>(ws + p->pp[i].fA);
     P.fB = reinterpret_cast<Fr*>(ws + p->pp[i].fB);
     P.scr = reinterpret_cast<ProofScratch*>(ws + p->off_scr) + i;
@@ -566,7 +573,10 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
     const DevProof& P = p->proofs[t.proof];
     tt.tmap = t.tmap;
     tt.w8 = t.side ? P.w8B : P.w8A;
-    tt.acc = (t.side ? P.accB : P.accA) + (size_t)tt.w0 * 8;
+    const bool direct = t.side ? P.fdirB : P.fdirA;
+    tt.acc = direct ? nullptr : (t.side ? P.accB : P.accA) + (size_t)tt.w0 * 8;
+    tt.f = direct ? (t.side ? P.fB : P.fA) + tt.w0 : nullptr;
+    tt.corr = direct ? (t.side ? &P.scr->corrB : &P.scr->corrA) : nullptr;
   }
   cudaError_t e = cudaMemcpyAsync(ws + p->off_proofs, p->proofs.data(), sizeof(DevProof) * np,
                                   cudaMemcpyHostToDevice, st);

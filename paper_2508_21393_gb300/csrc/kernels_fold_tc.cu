@@ -49,6 +49,7 @@
 // proof VL_ETIMEOUT, and the CTA drains its copies and MMAs before it frees
 // TMEM and returns.
 #include "fold_dev.cuh"
+#include "fr_dev.cuh"
 
 namespace vl {
 namespace {
@@ -57,8 +58,9 @@ constexpr int SM_RAW = 0;                          // TC_NR x 32 KB of int16 ope
 constexpr int SM_W = SM_RAW + TC_NR * 32768;       // TC_NW x 8 KB of fp16 weight bytes
 constexpr int SM_ACONST = SM_W + TC_NW * 8192;    // 128 x 16 fp16, K-major: column 0 = 256
 constexpr int SM_BCONST = SM_ACONST + 4096;        // 16 x 32 fp16, MN-major: row 0 = 32768
-constexpr int SM_HDR = SM_BCONST + 1024;           // TC_HR stage headers
-constexpr int SM_BAR = SM_HDR + TC_HR * 32;
+constexpr int SM_XCH = SM_BCONST + 1024;           // 128 lines x 4 u64: drainer groups' column exchange
+constexpr int SM_HDR = SM_XCH + 4096;              // TC_HR stage headers
+constexpr int SM_BAR = SM_HDR + TC_HR * 48;
 // Completion of stage s's MMAs (both issuers) is one barrier of a ring of
 // TC_ND: the converters (TMEM operand reuse), the producer (weight slot
 // reuse) and the drainers (accumulator ready) all wait on it.  TC_ND exceeds
@@ -68,10 +70,11 @@ constexpr int TC_ND = 16;
 // accumulator barrier (TC_NC, TC_NW, TC_NA apart) must belong to one pair.
 static_assert(TC_NC % 2 == 0 && TC_NW % 2 == 0 && TC_NA % 2 == 0, "ring sizes even");
 static_assert(TC_ND > TC_NW && TC_ND > TC_NC && TC_ND >= TC_NA, "stage-done ring");
-constexpr int NBAR = 2 * TC_NR + TC_NC + TC_NA + TC_NW + TC_ND + 1;
+constexpr int NBAR = 2 * TC_NR + TC_NC + TC_NA + TC_NW + TC_ND + 3;
 constexpr int SM_TMEM = SM_BAR + NBAR * 8;
 static_assert(SM_TMEM + 16 <= TC_SMEM - 1024, "shared-memory layout");
 constexpr uint32_t TMEM_COLS = 512;
+
 constexpr uint32_t ACONV_COL = 128 * TC_NA;
 static_assert(ACONV_COL + 128 * TC_NC <= TMEM_COLS, "TMEM columns");
 
@@ -201,9 +204,11 @@ struct StageHdr {
   int32_t mode;
   int32_t nw;     // lines of the tile
   int32_t pad;
-  unsigned long long* acc;  // accumulator rows of the tile's first line
+  unsigned long long* acc;  // accumulator rows of the tile's first line, or
+  Fr* f;                    //   f entries of the tile's first line (whole-reduction tiles)
+  const Fr* corr;
 };
-static_assert(sizeof(StageHdr) == 32, "stage header");
+static_assert(sizeof(StageHdr) == 48, "stage header");
 
 struct TcBars {
   uint32_t b;
@@ -214,6 +219,9 @@ struct TcBars {
   __device__ uint32_t w_full(int w) const { return b + 8 * (2 * TC_NR + TC_NC + TC_NA + w); }
   __device__ uint32_t done(int s) const { return b + 8 * (2 * TC_NR + TC_NC + TC_NA + TC_NW + s % TC_ND); }
   __device__ uint32_t fin() const { return b + 8 * (2 * TC_NR + TC_NC + TC_NA + TC_NW + TC_ND); }
+  // drainer groups' column exchange for whole-reduction tiles
+  __device__ uint32_t xch_full() const { return b + 8 * (2 * TC_NR + TC_NC + TC_NA + TC_NW + TC_ND + 1); }
+  __device__ uint32_t xch_empty() const { return b + 8 * (2 * TC_NR + TC_NC + TC_NA + TC_NW + TC_ND + 2); }
 };
 // parity of stage s's phase on its done barrier
 __device__ __forceinline__ uint32_t done_parity(int s) { return (uint32_t)(s / TC_ND) & 1; }
@@ -250,6 +258,20 @@ __device__ __forceinline__ void drain_digits(uint32_t ta, uint32_t (&dg)[17], ui
     else if (t == 32) v = fbits_add(H[31], 0x4B000000u);
     else v = fbits_add(L[t], H[t - 1]);
     dg[t - T0] += v;
+  }
+}
+
+// Column sums col_j = sum_q 2^(8q) s_{4j+q} of the digits s_t, t in [T0, T1]
+// (s_32 into col_7 as s_32 . 2^32); columns outside the range are 0.
+template <int T0, int T1>
+__device__ __forceinline__ void digit_columns(const uint32_t (&dg)[17], int nst, uint64_t (&col)[8]) {
+  const uint32_t off = (uint32_t)(2 * nst) * 0x4B000000u;  // two drains per stage
+#pragma unroll
+  for (int j = 0; j < 8; j++) col[j] = 0;
+#pragma unroll
+  for (int t = T0; t <= T1; t++) {
+    const int c = t < 32 ? t >> 2 : 7, sh = t < 32 ? 8 * (t & 3) : 32;
+    col[c] += (uint64_t)(dg[t - T0] - off) << sh;
   }
 }
 
@@ -299,6 +321,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int w = 0; w < TC_NW; w++) mbar_init(bars.w_full(w), 1);
     for (int d = 0; d < TC_ND; d++) mbar_init(bars.done(d), 2);  // the lo and hi issuers of the stage commit
     mbar_init(bars.fin(), 4);
+    mbar_init(bars.xch_full(), TC_DRAIN_WARPS / 2);
+    mbar_init(bars.xch_empty(), TC_DRAIN_WARPS / 2);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -352,7 +376,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             ok = false;
             break;
           }
-          hdr[s % TC_HR] = StageHdr{done ? -1 : tile, st, nst, T.mode, T.nw, 0, T.acc};
+          hdr[s % TC_HR] = StageHdr{done ? -1 : tile, st, nst, T.mode, T.nw, 0, T.acc, T.f, T.corr};
           last_use[slot] = use;
           const uint32_t raw = base + SM_RAW + slot * 32768;
           if (done) {
@@ -504,6 +528,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint32_t dg[17];
 #pragma unroll
     for (int t = 0; t < 17; t++) dg[t] = 0;
+    int nx = 0;  // whole-reduction epilogues done (exchange barrier phases)
     for (int s = 0;; s++) {
       const int a = s % TC_NA;
       if (!warp_wait(bars.done(s), done_parity(s), wait_ns)) {
@@ -522,7 +547,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         drain_digits<17, 32>(ta + 64, dg, bars.acc_empty(a));
       }
       if (h.stage == h.nst - 1) {
-        if (line < h.nw) {
+        if (h.f) {
+          // Whole-reduction tile: group 1 hands its columns (4..7) to group 0
+          // through shared memory; group 0 reduces the line's sum and stores
+          // f = REDC(sum) - 2^15 . sum E (Montgomery).  The hand-over is an
+          // mbarrier pair with bounded waits.
+          uint64_t* xch = reinterpret_cast<uint64_t*>(sm + SM_XCH) + line * 4;
+          uint64_t col[8];
+          if (grp == 1) {
+            if (nx > 0 && !warp_wait(bars.xch_empty(), (nx - 1) & 1, wait_ns)) {
+              ok = false;
+              break;
+            }
+            digit_columns<17, 32>(dg, h.nst, col);
+#pragma unroll
+            for (int j = 0; j < 4; j++) xch[j] = col[4 + j];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bars.xch_full());
+          } else {
+            if (!warp_wait(bars.xch_full(), nx & 1, wait_ns)) {
+              ok = false;
+              break;
+            }
+            digit_columns<0, 16>(dg, h.nst, col);
+            if (line < h.nw) {
+              U64x8 a;
+#pragma unroll
+              for (int j = 0; j < 8; j++) a.v[j] = col[j] + (j >= 4 ? xch[j - 4] : 0ull);
+              h.f[line] = fr_sub(redc_columns_ni(a), *h.corr);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bars.xch_empty());
+          }
+          nx++;
+        } else if (line < h.nw) {
           unsigned long long* acc = h.acc + (size_t)line * 8;
           if (grp == 0) tc_epilogue<0, 16>(dg, h.nst, acc);
           else tc_epilogue<17, 32>(dg, h.nst, acc);

@@ -13,12 +13,26 @@ __global__ void __launch_bounds__(RND_THREADS, MINB) rounds_kernel(const DevProo
   rounds_block(P, out + P.job, rnd_smem);
 }
 
-// variant: CTAs per SM the register allocation targets (7: one wave of 1064
-// proofs, tighter registers; 4: more registers per thread, more waves).
+// variant: CTAs per SM.  7 and 4 set the register allocation (7: one wave of
+// 1064 proofs, tighter registers; 4: more registers per thread).  3 and 2
+// use the variant-4 code and cap residency by reserving shared memory, for
+// fewer co-resident proofs competing for issue slots.
 cudaError_t launch_rounds(const DevProof* proofs, int nproofs, vl_proof* out, int variant, cudaStream_t st) {
   if (nproofs <= 0) return cudaSuccess;
-  if (variant == 4) rounds_kernel<4><<<nproofs, RND_THREADS, RND_SMEM, st>>>(proofs, out);
-  else rounds_kernel<7><<<nproofs, RND_THREADS, RND_SMEM, st>>>(proofs, out);
+  if (variant == 2 || variant == 3) {
+    static int set = 0;
+    const int smem = variant == 2 ? 100 * 1024 : 70 * 1024;
+    if (set < smem) {
+      cudaError_t e = cudaFuncSetAttribute(rounds_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+      if (e != cudaSuccess) return e;
+      set = 100 * 1024;
+    }
+    rounds_kernel<4><<<nproofs, RND_THREADS, smem, st>>>(proofs, out);
+  } else if (variant == 4) {
+    rounds_kernel<4><<<nproofs, RND_THREADS, RND_SMEM, st>>>(proofs, out);
+  } else {
+    rounds_kernel<7><<<nproofs, RND_THREADS, RND_SMEM, st>>>(proofs, out);
+  }
   return cudaGetLastError();
 }
 

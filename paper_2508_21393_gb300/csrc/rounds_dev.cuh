@@ -124,7 +124,8 @@ static __device__ void rounds_block(const DevProof& P, vl_proof* pf, uint8_t* sm
 
   if (d1 == 0) {  // k = 1: no rounds, c = a_r . b_r
     if (tid == 0) {
-      const Fr a = load_acc_fr(P.accA, 0, corrA), b = load_acc_fr(P.accB, 0, corrB);
+      const Fr a = P.fdirA ? fA[0] : load_acc_fr(P.accA, 0, corrA);
+      const Fr b = P.fdirB ? fB[0] : load_acc_fr(P.accB, 0, corrB);
       const Fr fin[2] = {from_mont_ni(a), from_mont_ni(b)};
       const Fr c[1] = {from_mont_ni(mont_mul_ni(a, b))};
       store_fr(&pf->c, c[0]);
@@ -154,11 +155,13 @@ static __device__ void rounds_block(const DevProof& P, vl_proof* pf, uint8_t* sm
     const int h = K >> 1;
     for (int j = tid; j < h; j += nthr) {
       // K/2 < k <= K, so j < k always; j + h may be padding.
-      const Fr a0 = load_acc_fr(P.accA, j, corrA), b0 = load_acc_fr(P.accB, j, corrB);
+      // f_A, f_B come reduced from the fold (fdir) or as column sums to reduce here
+      const Fr a0 = P.fdirA ? fA[j] : load_acc_fr(P.accA, j, corrA);
+      const Fr b0 = P.fdirB ? fB[j] : load_acc_fr(P.accB, j, corrB);
       Fr a1 = fr_zero(), b1 = fr_zero();
       if (j + h < P.k) {
-        a1 = load_acc_fr(P.accA, j + h, corrA);
-        b1 = load_acc_fr(P.accB, j + h, corrB);
+        a1 = P.fdirA ? fA[j + h] : load_acc_fr(P.accA, j + h, corrA);
+        b1 = P.fdirB ? fB[j + h] : load_acc_fr(P.accB, j + h, corrB);
       }
       fA[j] = a0; fA[j + h] = a1;
       fB[j] = b0; fB[j + h] = b1;
