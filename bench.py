@@ -86,6 +86,28 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def rank_seed(rank):
+    """Seed of rank `rank`'s replica: each rank proves its own step (weak scaling)."""
+    return W.GLOBAL_SEED + 1000003 * rank
+
+
+def max_over_ranks(x, world, device):
+    """Maximum of a per-rank float over the process group (the job takes as
+    long as its slowest rank)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, seconds_max):
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 def step_jobs(kind, seed, layers=0):
     projs = W.make_step(STEP_KIND[kind], seed, layers=range(layers) if layers > 0 else None)
     jobs = [j for t in projs for j in W.projection_products(t, seed)]
@@ -292,7 +314,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.lib()
-    seed = W.GLOBAL_SEED + 1000003 * rank
+    seed = rank_seed(rank)
     projs, jobs = step_jobs(args.workload, seed, args.layers)
     macs_step = sum(W.macs(j) for j in jobs)
     entries = sum(W.fold_entries(j) for j in jobs)
@@ -357,11 +379,8 @@ def main():
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     phases = B.vl_plan_phase_ms(plan, args.steps, reset=1)
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = macs_step * world / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = job_value(macs_step, world, ms_max / 1e3)
 
     fold_ms = statistics.mean(p[1] for p in phases)
     pro_ms = statistics.mean(p[0] for p in phases)
@@ -447,13 +466,11 @@ def main():
         for _ in range(ksteps):
             B.vl_plan_run(hplan, hws.data_ptr(), hn, hout, B.VL_HOST, stream)
         e2e_s = (time.perf_counter() - t0) / ksteps
-        et = torch.tensor([e2e_s], device="cuda")
-        if world > 1:
-            dist.all_reduce(et, op=dist.ReduceOp.MAX)
-        e2e = {"value": macs_step * world / float(et.item()), "unit": UNIT,
+        e2e_max = max_over_ranks(e2e_s, world, "cuda")
+        e2e = {"value": job_value(macs_step, world, e2e_max), "unit": UNIT,
                "h2d_bytes_per_step": int(sum(h.numel() * 2 for h in host.values())),
                "d2h_bytes_per_step": int(ctypes.sizeof(B.vl_proof) * len(hjobs)),
-               "ms_per_step": 1e3 * float(et.item()), "steps": ksteps}
+               "ms_per_step": 1e3 * e2e_max, "steps": ksteps}
         B.vl_plan_destroy(hplan)
 
     launches = args.steps * B.vl_plan_launches(plan)
