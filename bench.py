@@ -409,8 +409,12 @@ def main():
         # 64 fp16 MACs per entry (two bytes x 32 weight bytes) plus the init
         # MMA of each 64-entry stage (2048 MACs per 128 x 64 entries)
         tflops = 2 * (64 + 0.25) * entries / (fold_ms / 1e3) / 1e12
+        # DRAM traffic per launch: ncu capture of the same kernel on the first
+        # two layers (profiles/fold_tc_kernel_7b_2layers.md), 440.6 MB for 746 MB
+        # algorithmic, scaled by entries (the tile mix repeats per projection).
+        traffic = 0.5906 * 2 * entries if args.workload == "7b-step" else None
         roof = {"bound": "hbm", "kernel": kernel, "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": hbm_gbs / hbm_peak, "traffic": None,
+                "frac": hbm_gbs / hbm_peak, "traffic": traffic,
                 "peak_note": f"{hbm_note} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": 2 * entries,
                 "tensor_tflops_fp16": tflops}
