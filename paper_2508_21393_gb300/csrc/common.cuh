@@ -48,6 +48,7 @@ struct DevProof {
   int32_t job;             // index of the proof in the caller's job list (output slot)
   int32_t tabA, tabB;      // weight tables each side needs: TAB_LIMBS and/or TAB_BYTES
   int32_t fdirA, fdirB;    // 1: the fold writes f_A (f_B) itself, reduced (no accumulators)
+  Fr* fac;                 // eq factor tables: [lo_u 256 | hi_u 256 | lo_v 256 | hi_v 256]
   uint32_t* w8A;           // tensor-core weights: E_u bytes as fp16, [ceil(m / 128) x 2 chunks] x 4 KB
   uint32_t* w8B;           // E_v bytes
 };
@@ -59,6 +60,14 @@ struct DevProof {
 //              chunk: [8 entry groups][4 byte groups][8 entries][8 bytes]),
 //              zero past the last entry up to a multiple of 128 entries
 enum : int32_t { TAB_LIMBS = 1, TAB_BYTES = 2 };
+
+// Eq-table expansion: entries [i0, i1) of one side's table.
+struct EqItem {
+  int32_t proof, side;
+  int32_t i0, i1;
+};
+static constexpr int EQ_CHUNK = 1024;
+static constexpr int EQ_FAC = 256;  // entries of each factor table
 
 // Persistent step: work items in queue order.
 enum : int32_t { STEP_PROLOGUE = 0, STEP_FOLD = 1 };
@@ -172,7 +181,12 @@ inline int fold_tile_smem(int mode, int dtype, int tile_rows, int tile_cols) {
   return FOLD_SMEM_HEAD + (staged > pipe ? staged : pipe);
 }
 
-cudaError_t launch_prologue(const DevProof* proofs, int nproofs, cudaStream_t st);
+// Prologue in two launches: per proof the transcript start, squeezes, eq
+// factor tables and offset corrections; then the eq tables chunk by chunk.
+// proofs: the plan's proof table; [p0, p1) the proofs whose transcripts run;
+// items: their eq chunks (proof indices into `proofs`).
+cudaError_t launch_prologue(const DevProof* proofs, int p0, int p1, const EqItem* items, int nitems,
+                            cudaStream_t st);
 // Raise the fold kernel's dynamic shared-memory limit (call before capture).
 cudaError_t fold_set_smem(int smem_bytes);
 cudaError_t launch_fold(const FoldTask* tasks, const FoldTile* tiles, int ntiles,

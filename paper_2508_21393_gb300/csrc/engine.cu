@@ -84,6 +84,7 @@ struct vl_plan {
   std::vector<FoldTask> tasks;
   std::vector<FoldTile> tiles;
   std::vector<TcTile> tc_tiles;  // tensor-core fold (phase launches)
+  std::vector<EqItem> eq_items;  // eq-table chunks, proof by proof
   std::vector<StepItem> items;  // persistent step: queue order
   // Phase launches: proofs in groups (k descending); the graph folds group g
   // while group g+1's prologue and group g-1's rounds run on other streams.
@@ -91,6 +92,7 @@ struct vl_plan {
     int p0, p1;  // proofs [p0, p1)
     int t0, t1;  // CUDA-core fold tiles [t0, t1)
     int c0, c1;  // tensor-core fold tiles [c0, c1)
+    int e0, e1;  // eq-table chunks [e0, e1)
   };
   std::vector<Group> groups;
   std::vector<int> slot_of_job;  // DevProof index of each job
@@ -104,10 +106,10 @@ struct vl_plan {
   int step_grid = 0;            // CTAs of the persistent launch (set at bind time)
   size_t off_ctl = 0, off_items = 0;
   // workspace layout (offsets from the workspace base)
-  size_t off_proofs = 0, off_scr = 0, off_tasks = 0, off_tiles = 0, off_tc_tiles = 0;
+  size_t off_proofs = 0, off_scr = 0, off_tasks = 0, off_tiles = 0, off_tc_tiles = 0, off_eq_items = 0;
   size_t off_acc = 0, acc_bytes = 0, off_out = 0, total = 0;
   struct PerProof {
-    size_t eqA, eqB, soaA, soaB, w8A, w8B, accA, accB, fA, fB;
+    size_t eqA, eqB, soaA, soaB, w8A, w8B, accA, accB, fA, fB, fac;
   };
   std::vector<PerProof> pp;
   std::map<const void*, Staged> staging;  // host operand -> device copy
@@ -232,7 +234,9 @@ void build_groups(vl_plan* p) {
   int ng = p->opts.groups > 0 ? p->opts.groups : 1;
   ng = std::max(1, std::min(std::min(ng, np), STEP_CTL_HEAD_INTS));  // one tile counter per group
   std::vector<int64_t> work(np, 0);
-  std::vector<int> first_tile(np + 1, (int)p->tiles.size()), first_tc(np + 1, (int)p->tc_tiles.size());
+  std::vector<int> first_tile(np + 1, (int)p->tiles.size()), first_tc(np + 1, (int)p->tc_tiles.size()),
+      first_eq(np + 1, (int)p->eq_items.size());
+  for (int t = (int)p->eq_items.size() - 1; t >= 0; t--) first_eq[p->eq_items[t].proof] = t;
   for (int t = (int)p->tiles.size() - 1; t >= 0; t--) {
     const FoldTile& ft = p->tiles[t];
     const int pi = p->tasks[ft.task].proof;
@@ -248,6 +252,7 @@ void build_groups(vl_plan* p) {
   for (int i = np - 1; i >= 0; i--) {
     first_tile[i] = std::min(first_tile[i], first_tile[i + 1]);
     first_tc[i] = std::min(first_tc[i], first_tc[i + 1]);
+    first_eq[i] = std::min(first_eq[i], first_eq[i + 1]);
   }
   int64_t total = 0;
   for (int64_t w : work) total += w;
@@ -259,7 +264,8 @@ void build_groups(vl_plan* p) {
     const bool cut = (int)p->groups.size() < ng - 1 && acc * ng >= total * (int64_t)(p->groups.size() + 1);
     if (cut || i == np - 1) {
       p->groups.push_back(
-          vl_plan::Group{start, i + 1, first_tile[start], first_tile[i + 1], first_tc[start], first_tc[i + 1]});
+          vl_plan::Group{start, i + 1, first_tile[start], first_tile[i + 1], first_tc[start], first_tc[i + 1],
+                         first_eq[start], first_eq[i + 1]});
       start = i + 1;
     }
   }
@@ -341,6 +347,16 @@ int build_plan(vl_plan* p) {
     // f_B: op(Q) over its n columns.  Stored k x n -> row dots; stored n x k -> column sums.
     add_fold_task(p, j.Q, j.Q.trans ? MODE_COLSUM : MODE_ROWDOT, i, 1);
   }
+  // eq-table chunks (tensor-core tables run to a multiple of 128 entries)
+  p->eq_items.clear();
+  for (int i = 0; i < np; i++) {
+    const DevProof& P = p->proofs[i];
+    for (int side = 0; side < 2; side++) {
+      const int tabs = side ? P.tabB : P.tabA, size = side ? P.n : P.m;
+      const int end = (tabs & TAB_BYTES) ? (size + TC_KS - 1) / TC_KS * TC_KS : size;
+      for (int c = 0; tabs && c < end; c += EQ_CHUNK) p->eq_items.push_back(EqItem{i, side, c, std::min(end, c + EQ_CHUNK)});
+    }
+  }
   build_items(p);
   build_groups(p);
   p->off_tasks = off;
@@ -349,6 +365,8 @@ int build_plan(vl_plan* p) {
   off = align_up(off + sizeof(FoldTile) * p->tiles.size());
   p->off_tc_tiles = off;
   off = align_up(off + sizeof(TcTile) * p->tc_tiles.size());
+  p->off_eq_items = off;
+  off = align_up(off + sizeof(EqItem) * p->eq_items.size());
   p->off_tmaps = off;
   off = align_up(off + sizeof(CUtensorMap) * p->tasks.size());
   p->off_etmaps = off;
@@ -402,6 +420,8 @@ int build_plan(vl_plan* p) {
     off = align_up(off + sizeof(Fr) * ((size_t)1 << P.d1));
     p->pp[i].fB = off;
     off = align_up(off + sizeof(Fr) * ((size_t)1 << P.d1));
+    p->pp[i].fac = off;
+    off = align_up(off + sizeof(Fr) * 4 * EQ_FAC);
   }
   // staging for host operands (one device copy per distinct host pointer)
   for (const vl_job& j : p->jobs) {
@@ -543,6 +563,7 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
     P.fA = reinterpret_cast<Fr*>(ws + p->pp[i].fA);
     P.fB = reinterpret_cast<Fr*>(ws + p->pp[i].fB);
     P.scr = reinterpret_cast<ProofScratch*>(ws + p->off_scr) + i;
+    P.fac = reinterpret_cast<Fr*>(ws + p->pp[i].fac);
   }
   p->tmaps.resize(p->tasks.size());
   p->etmaps.resize(p->tasks.size());
@@ -588,6 +609,9 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
                         cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !p->tc_tiles.empty())
     e = cudaMemcpyAsync(ws + p->off_tc_tiles, p->tc_tiles.data(), sizeof(TcTile) * p->tc_tiles.size(),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !p->eq_items.empty())
+    e = cudaMemcpyAsync(ws + p->off_eq_items, p->eq_items.data(), sizeof(EqItem) * p->eq_items.size(),
                         cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !p->tmaps.empty())
     e = cudaMemcpyAsync(ws + p->off_tmaps, p->tmaps.data(), sizeof(CUtensorMap) * p->tmaps.size(),
@@ -654,6 +678,7 @@ cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t s
   const FoldTask* dt = reinterpret_cast<const FoldTask*>(ws + p->off_tasks);
   const FoldTile* dl = reinterpret_cast<const FoldTile*>(ws + p->off_tiles);
   const TcTile* dc = reinterpret_cast<const TcTile*>(ws + p->off_tc_tiles);
+  const EqItem* de = reinterpret_cast<const EqItem*>(ws + p->off_eq_items);
   const int np = (int)p->jobs.size();
   // Under capture, external records become event-record nodes of the graph
   // (the flag is only valid while capturing).
@@ -682,7 +707,7 @@ cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t s
   if (ng == 1) {
     // One group: everything in order on the caller's stream.
     if (e == cudaSuccess) e = cudaMemsetAsync(ws + p->off_ctl, 0, p->off_acc + p->acc_bytes - p->off_ctl, st);
-    if (e == cudaSuccess) e = launch_prologue(dp, np, st);
+    if (e == cudaSuccess) e = launch_prologue(dp, 0, np, de, (int)p->eq_items.size(), st);
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[1], st, flags);
     if (e == cudaSuccess) e = launch_fold_tc(dc, (int)p->tc_tiles.size(), dp, wait_ns(p), st);
     if (e == cudaSuccess) e = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, wait_ns(p), st);
@@ -699,11 +724,11 @@ cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t s
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ps, gev[2 * ng], 0);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(rs, gev[2 * ng], 0);
   const vl_plan::Group& g0 = p->groups[0];
-  if (e == cudaSuccess) e = launch_prologue(dp + g0.p0, g0.p1 - g0.p0, st);
+  if (e == cudaSuccess) e = launch_prologue(dp, g0.p0, g0.p1, de + g0.e0, g0.e1 - g0.e0, st);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[1], st, flags);
   for (int g = 1; g < ng && e == cudaSuccess; g++) {
     const vl_plan::Group& G = p->groups[g];
-    e = launch_prologue(dp + G.p0, G.p1 - G.p0, ps);
+    e = launch_prologue(dp, G.p0, G.p1, de + G.e0, G.e1 - G.e0, ps);
     if (e == cudaSuccess) e = cudaEventRecord(gev[g], ps);
   }
   for (int g = 0; g < ng && e == cudaSuccess; g++) {
@@ -1029,7 +1054,8 @@ extern "C" int32_t vl_prove_matmul_noalloc(const vl_mat* P, const vl_mat* Q, con
     vl_proof* dout = reinterpret_cast<vl_proof*>(ws + p->off_out);
     // The accumulators keep the previous call's sums: clear them first.
     cudaError_t ce = cudaMemsetAsync(ws + p->off_acc, 0, p->acc_bytes, st);
-    if (ce == cudaSuccess) ce = launch_prologue(dp, 1, st);
+    const EqItem* de = reinterpret_cast<const EqItem*>(ws + p->off_eq_items);
+    if (ce == cudaSuccess) ce = launch_prologue(dp, 0, 1, de, (int)p->eq_items.size(), st);
     if (ce == cudaSuccess) ce = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, FOLD_WAIT_NS, st);
     if (ce == cudaSuccess) ce = launch_rounds(dp, 1, dout, 0, st);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, dout, sizeof(vl_proof), cudaMemcpyDeviceToHost, st);

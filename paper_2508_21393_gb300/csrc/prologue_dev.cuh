@@ -157,4 +157,101 @@ static __device__ void prologue_block(const DevProof& P, uint8_t* smem) {
   __syncthreads();
 }
 
+// Factor tables of one side into global memory: lo[j] (2^s entries,
+// double-Montgomery) and hi[j] (ceil(size / 2^s) entries, Montgomery), with
+// E[i] = hi[i >> s] . lo[i mod 2^s] and s = ceil(d / 2).  Block-wide.
+__device__ static void eq_factors(const Fr* x, int d, int size, Fr* lo, Fr* hi) {
+  const int tid = threadIdx.x;
+  const int s = (d + 1) >> 1, dh = d - s;
+  const int nlo = 1 << s, nhi = (size + nlo - 1) >> s;
+  for (int j = tid; j < nlo + nhi; j += blockDim.x) {
+    const bool is_lo = j < nlo;
+    const int jj = is_lo ? j : j - nlo, nv = is_lo ? s : dh, base = is_lo ? dh : 0;
+    Fr acc = is_lo ? fr_r2() : fr_r1();
+    for (int t = 0; t < nv; t++) {
+      const Fr& xt = x[base + t];
+      acc = mont_mul_ni(acc, ((jj >> (nv - 1 - t)) & 1) ? xt : fr_sub(fr_r1(), xt));
+    }
+    (is_lo ? lo : hi)[jj] = acc;
+  }
+}
+
+// sum_{i < size} eq(x, bits(i)) (Montgomery), in closed form: i < size
+// exactly when, at the first bit (from the top) where i and size differ, i
+// has 0 and size has 1; the bits below are free and their eq factors sum to
+// 1.  So the sum runs over the 1-bits t of size: prod of the factors of size's
+// bits above t, times (1 - x_t).  O(d) products, one thread.
+__device__ static Fr eq_prefix_sum(const Fr* x, int d, int size) {
+  if (size >= (1 << d)) return fr_r1();  // the whole cube: sum 1
+  Fr sum = fr_zero(), pre = fr_r1();
+  for (int t = 0; t < d; t++) {
+    const int b = (size >> (d - 1 - t)) & 1;
+    const Fr one_minus = fr_sub(fr_r1(), x[t]);
+    if (b) sum = fr_add(sum, mont_mul_ni(pre, one_minus));
+    pre = mont_mul_ni(pre, b ? x[t] : one_minus);
+  }
+  return sum;
+}
+
+// First launch of the prologue, one proof per block (any multiple of 32
+// threads, at least 64): transcript start, squeezes of u and v, the factor
+// tables of both eq tables (to P.fac) and the offset corrections
+// 2^15 . sum_i E[i] (Montgomery).
+static __device__ void transcript_block(const DevProof& P, uint8_t* smem) {
+  uint32_t* S0 = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* S1 = S0 + 8;
+  uint32_t* S2 = S0 + 16;
+  uint32_t(*dig)[8] = reinterpret_cast<uint32_t(*)[8]>(smem + 128);
+  Fr* u = reinterpret_cast<Fr*>(smem + 128 + 2 * MAX_VARS * 32);
+  Fr* v = u + MAX_VARS;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    uint8_t b[32];
+    ts_start(b, P.seed, P.m, P.k, P.n, P.tp, P.tq, P.binds);
+    for (int i = 0; i < 8; i++)
+      S0[i] = ((uint32_t)b[4 * i] << 24) | ((uint32_t)b[4 * i + 1] << 16) | ((uint32_t)b[4 * i + 2] << 8) | b[4 * i + 3];
+  }
+  __syncthreads();
+  squeeze_dev(S0, LBL_U, P.d0, u, S1, dig);
+  squeeze_dev(S1, LBL_V, P.d2, v, S2, dig);
+  if (tid < 32) P.scr->state[tid] = (uint8_t)(S2[tid >> 2] >> (24 - 8 * (tid & 3)));
+  eq_factors(u, P.d0, P.m, P.fac, P.fac + EQ_FAC);
+  eq_factors(v, P.d2, P.n, P.fac + 2 * EQ_FAC, P.fac + 3 * EQ_FAC);
+  if (tid == 0 || tid == 32) {
+    const bool a = tid == 0;
+    const Fr sum = a ? eq_prefix_sum(u, P.d0, P.m) : eq_prefix_sum(v, P.d2, P.n);
+    // sum . R times 2^15 . R, reduced once: 2^15 . sum (Montgomery)
+    const Fr corr = mont_mul_ni(sum, to_mont_ni(fr_small(1u << 15)));
+    const bool i16 = (a ? P.dtypeA : P.dtypeB) == VL_I16;
+    (a ? P.scr->corrA : P.scr->corrB) = i16 ? corr : fr_zero();
+  }
+  if (tid == 0) P.scr->status = VL_OK;
+  __syncthreads();
+}
+
+// Second launch: entries [i0, i1) of one eq table, E[i] = hi[i >> s] . lo[i
+// mod 2^s] (double-Montgomery), written in the formats the side's fold
+// engines read; tensor-core tables are zero from the last entry to their
+// padded end.
+static __device__ void eq_chunk(const EqItem& it, const DevProof& P) {
+  const bool b = it.side != 0;
+  const int d = b ? P.d2 : P.d0, size = b ? P.n : P.m, tabs = b ? P.tabB : P.tabA;
+  const int s = (d + 1) >> 1, mask = (1 << s) - 1;
+  const Fr* lo = P.fac + (b ? 2 * EQ_FAC : 0);
+  const Fr* hi = lo + EQ_FAC;
+  Fr* out = b ? P.eqB : P.eqA;
+  uint32_t* soa = b ? P.eqB_soa : P.eqA_soa;
+  const int pitch = b ? P.soa_pitchB : P.soa_pitchA;
+  uint32_t* w8 = b ? P.w8B : P.w8A;
+  for (int i = it.i0 + threadIdx.x; i < it.i1; i += blockDim.x) {
+    const Fr e = i < size ? mont_mul_ni(hi[i >> s], lo[i & mask]) : fr_zero();
+    if ((tabs & TAB_LIMBS) && i < size) {
+      out[i] = e;
+#pragma unroll
+      for (int l = 0; l < 8; l++) soa[l * pitch + i] = e.v[l];
+    }
+    if (tabs & TAB_BYTES) store_w8(w8, i, e);
+  }
+}
+
 }  // namespace vl
