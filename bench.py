@@ -346,7 +346,7 @@ def main():
         t0 = time.perf_counter()
         opts, tune_ms = B.vl_autotune(djobs, tws.data_ptr(), need, base=opts, stream=stream, runs=3)
         tuned = {"seconds": time.perf_counter() - t0, "ms_per_step_at_tuning": tune_ms,
-                 **{k: getattr(opts, k) for k in ("fold_engine", "tc_seg", "rounds_variant", "persistent",
+                 **{k: getattr(opts, k) for k in ("fold_engine", "tc_seg", "rounds_variant", "rounds_threads", "persistent",
                                                   "colsum_rows", "rowdot_cols", "groups")}}
         del tws
     cuda_core = opts.persistent == 1 or opts.fold_engine == 1

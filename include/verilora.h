@@ -130,6 +130,8 @@ typedef struct vl_batch_opts {
   int32_t rounds_variant; /* rounds kernel: CTAs per SM, 7, 4, 3 or 2 (0: 7);
                             7 and 4 set the register budget, 3 and 2 also
                             cap residency (fewer proofs share an SM)        */
+  int32_t rounds_threads; /* rounds kernel threads per proof: 128, 192 or 256
+                            (0: 128)                                         */
   int32_t tc_seg;        /* tensor-core fold: reduced entries per tile, a
                             multiple of 128 up to 32768 (0: 16384); shorter
                             segments spread narrow operands over more SMs */

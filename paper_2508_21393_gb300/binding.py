@@ -83,7 +83,7 @@ class vl_batch_opts(ctypes.Structure):
                 ("persistent", ctypes.c_int32), ("groups", ctypes.c_int32), ("fold_engine", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32),
                 ("timing_runs", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
-                ("rounds_variant", ctypes.c_int32), ("tc_seg", ctypes.c_int32),
+                ("rounds_variant", ctypes.c_int32), ("rounds_threads", ctypes.c_int32), ("tc_seg", ctypes.c_int32),
                 ("test_never_ready", ctypes.c_int32)]
 
 

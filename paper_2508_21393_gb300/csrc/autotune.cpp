@@ -1,7 +1,7 @@
 // Autotuner: launch and tile options for a job list, chosen by timing.
 //
 // Coordinate descent from the caller's options: for each knob in turn (fold
-// engine, tensor-core segment length, rounds kernel variant, launch mode,
+// engine, tensor-core segment length, rounds kernel variant and threads, launch mode,
 // CUDA-core tile shapes when CUDA-core tiles exist) every listed value is
 // tried with the other knobs fixed, and the fastest kept.  A candidate is a
 // real plan run on the caller's workspace and stream: one untimed run (bind,
@@ -130,6 +130,7 @@ extern "C" int32_t vl_autotune(const vl_job* jobs, int32_t njobs, const vl_batch
       {&vl_batch_opts::fold_engine, {0, 1}},
       {&vl_batch_opts::tc_seg, {0, 8192, 4096, 2048}},
       {&vl_batch_opts::rounds_variant, {7, 4, 3, 2}},
+      {&vl_batch_opts::rounds_threads, {0, 192, 256}},
       {&vl_batch_opts::persistent, {2, 1}},
       {&vl_batch_opts::colsum_rows, {0, 128, 512}},
       {&vl_batch_opts::rowdot_cols, {0, 512, 2048}},

@@ -201,7 +201,8 @@ cudaError_t step_grid(int smem_bytes, int* grid);
 cudaError_t launch_step(const StepItem* items, int nitems, const FoldTask* tasks, const FoldTile* tiles,
                         const DevProof* proofs, int nproofs, vl_proof* out, int* ctl, int grid, int smem_bytes,
                         unsigned long long wait_ns, int never_ready, cudaStream_t st);
-cudaError_t launch_rounds(const DevProof* proofs, int nproofs, vl_proof* out, int variant, cudaStream_t st);
+cudaError_t launch_rounds(const DevProof* proofs, int nproofs, vl_proof* out, int variant, int threads,
+                          cudaStream_t st);
 cudaError_t launch_encode(const int16_t* src, int64_t rows, int64_t cols, int64_t ld, Fr* dst,
                           cudaStream_t st);
 

@@ -712,7 +712,7 @@ cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t s
     if (e == cudaSuccess) e = launch_fold_tc(dc, (int)p->tc_tiles.size(), dp, wait_ns(p), st);
     if (e == cudaSuccess) e = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, wait_ns(p), st);
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2], st, flags);
-    if (e == cudaSuccess) e = launch_rounds(dp, np, dout, p->opts.rounds_variant, st);
+    if (e == cudaSuccess) e = launch_rounds(dp, np, dout, p->opts.rounds_variant, p->opts.rounds_threads, st);
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[3], st, flags);
     return e;
   }
@@ -739,7 +739,7 @@ cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t s
     if (e == cudaSuccess) e = launch_fold(dt, dl + G.t0, G.t1 - G.t0, dp, p->fold_smem, wait_ns(p), st);
     if (e == cudaSuccess) e = cudaEventRecord(gev[ng + g], st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(rs, gev[ng + g], 0);
-    if (e == cudaSuccess) e = launch_rounds(dp + G.p0, G.p1 - G.p0, dout, p->opts.rounds_variant, rs);
+    if (e == cudaSuccess) e = launch_rounds(dp + G.p0, G.p1 - G.p0, dout, p->opts.rounds_variant, p->opts.rounds_threads, rs);
   }
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2], st, flags);
   if (e == cudaSuccess) e = cudaEventRecord(gev[2 * ng + 1], rs);
@@ -1057,7 +1057,7 @@ extern "C" int32_t vl_prove_matmul_noalloc(const vl_mat* P, const vl_mat* Q, con
     const EqItem* de = reinterpret_cast<const EqItem*>(ws + p->off_eq_items);
     if (ce == cudaSuccess) ce = launch_prologue(dp, 0, 1, de, (int)p->eq_items.size(), st);
     if (ce == cudaSuccess) ce = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, FOLD_WAIT_NS, st);
-    if (ce == cudaSuccess) ce = launch_rounds(dp, 1, dout, 0, st);
+    if (ce == cudaSuccess) ce = launch_rounds(dp, 1, dout, 0, 0, st);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, dout, sizeof(vl_proof), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     e = cuda_status(ce, "vl_prove_matmul_noalloc");

@@ -278,14 +278,18 @@ def test_plans_taking_turns_on_one_workspace():
 
 def test_launch_modes_and_fold_engines_agree():
     """Persistent launch, phase launches with the tensor-core fold, phase
-    launches with the CUDA-core fold: the same proofs."""
+    launches with the CUDA-core fold, every rounds variant and thread count:
+    the same proofs."""
     jobs = _lora_jobs(n=40, d=128, k=96, r=8, layer=6, proj="q")
     dj, keep = _dev_jobs(jobs)
     refs = [oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes() for j in jobs]
-    for mode, engine in ((1, 0), (2, 0), (2, 1), (0, 0)):
+    for mode, engine, rv, rt in ((1, 0, 0, 0), (2, 0, 0, 0), (2, 1, 0, 0), (0, 0, 0, 0), (2, 0, 4, 192),
+                                 (2, 0, 3, 256), (2, 0, 2, 0), (2, 0, 4, 0)):
         opts = B.vl_batch_opts()
         opts.persistent = mode
         opts.fold_engine = engine
+        opts.rounds_variant = rv
+        opts.rounds_threads = rt
         nb = B.vl_workspace_bytes(dj, opts)
         ws = _ws(nb)
         proofs = B.vl_prove_batch(dj, ws.data_ptr(), nb, opts=opts)
