@@ -260,6 +260,55 @@ int32_t vl_prove_matmul_noalloc(const vl_mat* P, const vl_mat* Q, const vl_fs_in
  */
 int32_t vl_encode(const vl_mat* src, void* dst, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Linear zkMat (Sec. IV: zkMat proves matrix additions as well as products):
+ * a proof that sum_q coeffs[q] * op(mats[q]) = 0 entrywise over F, by MLE
+ * linearity and no sumcheck.  The transcript (domain "verilora-gb300/zklin/v1",
+ * seed u64le, rows, cols, q u32le, the coefficients, one 32-byte bind per
+ * matrix) gives a point (x, y), x in F^d0 over the row bits and y in F^d1 over
+ * the column bits (d0 = ceil log2 rows, d1 = ceil log2 cols); the proof
+ * carries e_q = M_q~(x, y) of Eq. eq:MLE (absorbed under label 'e') and the
+ * final transcript state.  The verifier checks sum_q c_q e_q = 0 and
+ * evaluates each M_q~(x, y) from the matrices.  The LoRA parameter update of
+ * Eq. eq:grad_update_ab, A' = A - eta dA, is one such relation.
+ * ------------------------------------------------------------------------- */
+#define VL_LIN_MAX 16
+
+typedef struct vl_lin_job {
+  const vl_mat* mats;    /* nmats operands of one logical shape (after transposes) */
+  const vl_fr* coeffs;   /* nmats canonical coefficients                           */
+  const uint8_t* binds;  /* nmats x 32 bytes, or NULL for zeros                    */
+  uint64_t seed;
+  int32_t nmats;         /* 1 .. VL_LIN_MAX                                        */
+  int32_t reserved;      /* must be 0                                              */
+} vl_lin_job;
+
+typedef struct vl_lin_proof {
+  int32_t rows, cols, d0, d1, nmats;
+  int32_t status;
+  vl_fr evals[VL_LIN_MAX]; /* canonical; the first nmats are used              */
+  uint8_t state[32];
+} vl_lin_proof;
+
+/* Device workspace vl_prove_linear needs for this batch (0 on invalid
+ * arguments: see vl_prove_linear). */
+size_t vl_linear_workspace_bytes(const vl_lin_job* jobs, int32_t njobs);
+/* Prove a batch of linear relations on the GPU, one independent transcript
+ * each.  Operands: int16 (VL_EINVAL otherwise), logical rows and columns at
+ * most VL_MAX_REDUCE (VL_ESHAPE), on the device or the host; device operands
+ * with a 16-byte aligned base and a leading dimension of a multiple of 8
+ * entries are read in place, all others are first copied into the
+ * workspace.  workspace: device memory, 256-byte aligned, at least
+ * vl_linear_workspace_bytes (VL_ENOMEM).  out: host memory for njobs proofs.
+ * Synchronises `stream`.  Returns VL_OK, or the first proof's non-OK status
+ * (VL_ETIMEOUT from a bounded device wait).  The prover does not check the
+ * relation: a false one yields a proof that the verifier rejects. */
+int32_t vl_prove_linear(const vl_lin_job* jobs, int32_t njobs, void* workspace, size_t workspace_bytes,
+                        vl_lin_proof* out, void* stream);
+/* Verify one proof on the host against host operands (int16, int64 or
+ * Montgomery): VL_OK (accept), VL_REJECT, or an argument error. */
+int32_t vl_verify_linear(const vl_lin_job* job, const vl_lin_proof* proof);
+
 /* Autotuner (the paper has no counterpart): picks the launch and tile
  * options for `jobs` by timing candidate plans on the caller's workspace and
  * stream — coordinate descent from `base` (NULL: defaults) over the fold

@@ -29,8 +29,10 @@ EXPORTS = ("vl_version", "vl_strerror", "vl_last_error", "vl_workspace_bytes", "
            "vl_plan_create", "vl_plan_workspace_bytes", "vl_plan_run", "vl_plan_launches", "vl_plan_phase_ms",
            "vl_plan_destroy", "vl_verify_matmul", "vl_encode", "vl_prove_matmul_noalloc",
            "vl_server_create", "vl_server_submit", "vl_server_poll", "vl_server_stats_get", "vl_server_destroy",
-           "vl_autotune", "vl_autotune_clear")
+           "vl_autotune", "vl_autotune_clear", "vl_linear_workspace_bytes", "vl_prove_linear", "vl_verify_linear")
 VL_NOALLOC_SCRATCH_BYTES = 8 << 20
+VL_LIN_MAX = 16
+R_MOD = 0x73EDA753299D7D483339D80809A1D80553BDA402FFFE5BFEFFFFFFFF00000001
 
 
 class vl_fr(ctypes.Structure):
@@ -55,6 +57,18 @@ class vl_proof(ctypes.Structure):
                 ("d0", ctypes.c_int32), ("d1", ctypes.c_int32), ("d2", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("c", vl_fr), ("g", (vl_fr * 3) * VL_MAX_ROUNDS), ("a_r", vl_fr), ("b_r", vl_fr),
+                ("state", ctypes.c_uint8 * 32)]
+
+
+class vl_lin_job(ctypes.Structure):
+    _fields_ = [("mats", ctypes.POINTER(vl_mat)), ("coeffs", ctypes.POINTER(vl_fr)),
+                ("binds", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("nmats", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class vl_lin_proof(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int32), ("cols", ctypes.c_int32), ("d0", ctypes.c_int32), ("d1", ctypes.c_int32),
+                ("nmats", ctypes.c_int32), ("status", ctypes.c_int32), ("evals", vl_fr * VL_LIN_MAX),
                 ("state", ctypes.c_uint8 * 32)]
 
 
@@ -151,6 +165,13 @@ def lib():
     L.vl_prove_matmul_noalloc.argtypes = [P(vl_mat), P(vl_mat), P(vl_fs_init), P(vl_proof), ctypes.c_void_p]
     L.vl_prove_matmul_noalloc.restype = ctypes.c_int32
     L.vl_encode.argtypes = [P(vl_mat), ctypes.c_void_p, ctypes.c_void_p]
+    L.vl_linear_workspace_bytes.argtypes = [P(vl_lin_job), ctypes.c_int32]
+    L.vl_linear_workspace_bytes.restype = ctypes.c_size_t
+    L.vl_prove_linear.argtypes = [P(vl_lin_job), ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                                  P(vl_lin_proof), ctypes.c_void_p]
+    L.vl_prove_linear.restype = ctypes.c_int32
+    L.vl_verify_linear.argtypes = [P(vl_lin_job), P(vl_lin_proof)]
+    L.vl_verify_linear.restype = ctypes.c_int32
     L.vl_encode.restype = ctypes.c_int32
     _lib = L
     return L
@@ -181,7 +202,8 @@ def mat(a, trans=0, dtype=None):
             assert a.shape[2] == 8 and a.dtype.itemsize == 4 and a.flags["C_CONTIGUOUS"]
             m.dtype, m.ld = VL_FR_MONT, a.shape[1]
         else:
-            assert a.ndim == 2 and a.strides[1] == a.itemsize, "unit column stride required"
+            # a single column may report any column stride
+            assert a.ndim == 2 and (a.strides[1] == a.itemsize or a.shape[1] == 1), "unit column stride required"
             m.dtype = {np.dtype(np.int16): VL_I16, np.dtype(np.int64): VL_I64}[a.dtype]
             m.ld = a.strides[0] // a.itemsize
         m.data = a.ctypes.data
@@ -192,7 +214,7 @@ def mat(a, trans=0, dtype=None):
             assert a.shape[2] == 8 and a.element_size() == 4 and a.is_contiguous()
             m.dtype, m.ld = VL_FR_MONT, a.shape[1]
         else:
-            assert a.dim() == 2 and a.stride(1) == 1, "unit column stride required"
+            assert a.dim() == 2 and (a.stride(1) == 1 or a.shape[1] == 1), "unit column stride required"
             m.dtype = {torch.int16: VL_I16, torch.int64: VL_I64}[a.dtype]
             m.ld = a.stride(0)
         m.data = a.data_ptr()
@@ -241,6 +263,53 @@ def proof_bytes(p):
             out += bytes(p.g[i][q])
     out += bytes(p.a_r) + bytes(p.b_r) + bytes(p.state)
     return out
+
+
+def fr(x):
+    """vl_fr holding the canonical residue of the integer x (negative allowed)."""
+    v = vl_fr()
+    x = int(x) % R_MOD
+    for i in range(8):
+        v.limb[i] = (x >> (32 * i)) & 0xFFFFFFFF
+    return v
+
+
+def lin_proof_bytes(p):
+    """Linear proof serialisation (same layout as the oracle's LinearProof.to_bytes)."""
+    out = b"".join(int(x).to_bytes(4, "little") for x in (p.rows, p.cols, p.d0, p.d1, p.nmats))
+    return out + b"".join(bytes(p.evals[q]) for q in range(p.nmats)) + bytes(p.state)
+
+
+def lin_job(mats, coeffs, seed=0, binds=None):
+    """vl_lin_job for sum_q coeffs[q] * op(mats[q]) = 0.  mats: vl_mat list;
+    coeffs: Python ints (reduced mod r); binds: None or one 32-byte string per
+    matrix.  The returned structure keeps its arrays alive."""
+    if len(mats) != len(coeffs):
+        raise ValueError("one coefficient per matrix")
+    j = vl_lin_job()
+    j._mats = (vl_mat * len(mats))(*mats)
+    j._coeffs = (vl_fr * len(coeffs))(*[fr(c) for c in coeffs])
+    j.mats = ctypes.cast(j._mats, ctypes.POINTER(vl_mat))
+    j.coeffs = ctypes.cast(j._coeffs, ctypes.POINTER(vl_fr))
+    j._binds = None
+    if binds is not None:
+        raw = b"".join(bytes(b) for b in binds)
+        if len(raw) != 32 * len(mats):
+            raise ValueError("one 32-byte bind per matrix")
+        j._binds = ctypes.create_string_buffer(raw, len(raw))
+        j.binds = ctypes.addressof(j._binds)
+    j.seed = int(seed) & ((1 << 64) - 1)
+    j.nmats = len(mats)
+    j.reserved = 0
+    return j
+
+
+def lin_jobs_array(jobs):
+    arr = (vl_lin_job * len(jobs))()
+    for i, j in enumerate(jobs):
+        arr[i] = j
+    arr._keep = list(jobs)  # the copies point at the jobs' arrays
+    return arr
 
 
 def _stream_ptr(stream):
@@ -396,6 +465,29 @@ def vl_verify_matmul(P, Q, C, fs, proof):
     if code == VL_REJECT:
         return False
     _check(code, "vl_verify_matmul")
+    return True
+
+
+def vl_linear_workspace_bytes(jobs):
+    """Workspace bytes vl_prove_linear needs for these vl_lin_job (0 if invalid)."""
+    return lib().vl_linear_workspace_bytes(lin_jobs_array(jobs), len(jobs))
+
+
+def vl_prove_linear(jobs, workspace, workspace_bytes, stream=None):
+    """Prove a batch of linear relations; returns the ctypes array of host proofs."""
+    arr = lin_jobs_array(jobs)
+    out = (vl_lin_proof * len(jobs))()
+    _check(lib().vl_prove_linear(arr, len(jobs), workspace, workspace_bytes, out, _stream_ptr(stream)),
+           "vl_prove_linear")
+    return out
+
+
+def vl_verify_linear(job, proof):
+    """Host verifier of a linear proof: True / False; raises on input errors."""
+    code = lib().vl_verify_linear(ctypes.byref(job), ctypes.byref(proof))
+    if code == VL_REJECT:
+        return False
+    _check(code, "vl_verify_linear")
     return True
 
 

@@ -519,17 +519,7 @@ bool encode_task_map(const FoldTask& t, CUtensorMap* map) {
 // by 128 rows (no swizzle: rows of 256 contiguous bytes stream better) for
 // column sums; out-of-range entries read as zero.
 bool encode_tc_map(const FoldTask& t, CUtensorMap* map) {
-  if ((reinterpret_cast<uintptr_t>(t.mat) & 15) || (t.ld & 7)) return false;
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)t.cols, (cuuint64_t)t.rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)t.ld * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)t.box_w, (cuuint32_t)t.box_h};
-  const cuuint32_t estr[2] = {1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(t.mat), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE,
-             t.mode == MODE_ROWDOT ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return vl::encode_tc_operand(t.mat, t.rows, t.cols, t.ld, t.mode, map);
 }
 
 // TMA descriptor of the limb-major weights a row-dot task reads: 8 rows of
@@ -1066,3 +1056,29 @@ extern "C" int32_t vl_prove_matmul_noalloc(const vl_mat* P, const vl_mat* Q, con
   vl_plan_destroy(p);
   return e;
 }
+
+namespace vl {
+
+// TMA descriptor of an int16 operand of the tensor-core fold: uint16 boxes of
+// 64 columns (128 bytes, 128-byte swizzle) by 128 rows for row dots, 128
+// columns by 128 rows (no swizzle: rows of 256 contiguous bytes stream
+// better) for column sums; out-of-range entries read as zero.  False unless
+// the base is 16-byte aligned and rows are a multiple of 16 bytes apart.
+bool encode_tc_operand(const void* base, int64_t rows, int64_t cols, int64_t ld, int32_t mode, void* out) {
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld & 7)) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)(mode == MODE_ROWDOT ? TC_KP : TC_M),
+                             (cuuint32_t)(mode == MODE_ROWDOT ? TC_M : TC_KS)};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(static_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dims,
+             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             mode == MODE_ROWDOT ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+void set_last_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
+}  // namespace vl

@@ -1,0 +1,309 @@
+// Host engine and C ABI of the linear zkMat prover: sum_q c_q op(M_q) = 0
+// entrywise, by MLE linearity at a transcript point (Sec. IV: zkMat covers
+// matrix additions; the LoRA parameter update of Eq. eq:grad_update_ab is one
+// such relation).
+//
+// One call proves a batch of relations with five launches on a caller-owned
+// workspace: the start kernel (per proof: transcript, x and y, eq factors,
+// offset correction), the eq-table kernel (chunks of every proof), the
+// tensor-core fold of every matrix over its shorter logical dimension, the
+// partial dot products against the other dimension's eq table, and the
+// finish kernel (per proof: evaluations, absorb, proof); then one copy of the
+// proofs to the host.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace vl;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
+
+int ceil_log2(int64_t x) {
+  int d = 0;
+  while ((int64_t(1) << d) < x) d++;
+  return d;
+}
+
+// Fold tiles the segment choice aims for: two per SM of a 152-SM GB300.
+constexpr int LIN_TILE_TARGET = 304;
+// Shortest reduction segment worth a tile of its own.
+constexpr int LIN_MIN_SEG = 1024;
+// Longest segment whose digit sums stay exact (256 stages).
+constexpr int LIN_MAX_SEG = 32768;
+// Proofs per call (the partial-dot launch has one grid z index per proof).
+constexpr int LIN_MAX_JOBS = 65535;
+
+// Shape and fold plan of one proof.
+struct LinShape {
+  int rows = 0, cols = 0, d0 = 0, d1 = 0, q = 0;
+  bool red_rows = true;
+  int red = 0, lines = 0, seg = 0, nsplit = 0, nblk = 0, ntiles = 0;
+};
+
+// Workspace offsets of one proof's buffers.
+struct LinBufs {
+  size_t fac = 0, w8 = 0, el = 0, f = 0, part = 0;
+};
+
+struct LinLayout {
+  int np = 0, nmats = 0, ntiles = 0, max_nblk = 1, max_q = 1;
+  std::vector<LinShape> shape;
+  std::vector<LinBufs> buf;
+  std::vector<EqItem> items;
+  size_t off_L = 0, off_scr = 0, off_dp = 0, off_tiles = 0, off_maps = 0, off_items = 0, off_out = 0, total = 0;
+  std::vector<size_t> off_stage;  // per operand (flattened job by job); unused unless staged
+  std::vector<int64_t> stage_ld;
+  std::vector<char> staged;
+};
+
+int64_t lrows(const vl_mat& M) { return M.trans ? M.cols : M.rows; }
+int64_t lcols(const vl_mat& M) { return M.trans ? M.rows : M.cols; }
+
+// The fold reads the stored matrix with TMA: a device operand qualifies with
+// a 16-byte aligned base and a leading dimension of a multiple of 8 entries;
+// anything else is copied into the workspace first.
+bool tma_ready(const vl_mat& M) {
+  return M.space == VL_DEVICE && (reinterpret_cast<uintptr_t>(M.data) & 15) == 0 && (M.ld & 7) == 0;
+}
+
+int lin_shape(const vl_lin_job& J, LinShape* S) {
+  if (!J.mats || !J.coeffs || J.nmats < 1 || J.nmats > VL_LIN_MAX || J.reserved != 0) return VL_EINVAL;
+  const vl_mat* mats = J.mats;
+  for (int q = 0; q < J.nmats; q++) {
+    const vl_mat& M = mats[q];
+    if (!M.data || M.dtype != VL_I16 || (M.trans != 0 && M.trans != 1) || M.reserved != 0) return VL_EINVAL;
+    if (M.space != VL_DEVICE && M.space != VL_HOST) return VL_EINVAL;
+    if (M.rows < 1 || M.cols < 1) return VL_ESHAPE;
+    if (M.ld < M.cols) return VL_EINVAL;
+    if (lrows(M) != lrows(mats[0]) || lcols(M) != lcols(mats[0])) return VL_ESHAPE;
+  }
+  const int64_t rows = lrows(mats[0]), cols = lcols(mats[0]);
+  if (rows > VL_MAX_REDUCE || cols > VL_MAX_REDUCE) return VL_ESHAPE;
+  S->rows = (int)rows;
+  S->cols = (int)cols;
+  S->d0 = ceil_log2(rows);
+  S->d1 = ceil_log2(cols);
+  S->q = J.nmats;
+  // Reduce over the shorter dimension: the longer one gives the most tiles.
+  S->red_rows = rows <= cols;
+  S->red = (int)std::min(rows, cols);
+  S->lines = (int)std::max(rows, cols);
+  const int ntl = (S->lines + TC_M - 1) / TC_M;
+  const int want = (LIN_TILE_TARGET + ntl - 1) / ntl;
+  const int most = std::max(1, (S->red + LIN_MIN_SEG - 1) / LIN_MIN_SEG);
+  const int least = (S->red + LIN_MAX_SEG - 1) / LIN_MAX_SEG;
+  const int split = std::max(least, std::min(want, most));
+  S->seg = ((S->red + split - 1) / split + TC_KS - 1) / TC_KS * TC_KS;
+  S->nsplit = (S->red + S->seg - 1) / S->seg;
+  S->ntiles = J.nmats * ntl * S->nsplit;
+  S->nblk = (S->lines + LIN_DOT - 1) / LIN_DOT;
+  return VL_OK;
+}
+
+int lin_layout(const vl_lin_job* jobs, int32_t njobs, LinLayout* L) {
+  if (!jobs || njobs < 1 || njobs > LIN_MAX_JOBS) return VL_EINVAL;
+  L->np = njobs;
+  L->shape.resize(njobs);
+  L->buf.resize(njobs);
+  for (int i = 0; i < njobs; i++) {
+    const int e = lin_shape(jobs[i], &L->shape[i]);
+    if (e != VL_OK) return e;
+    const LinShape& S = L->shape[i];
+    L->nmats += S.q;
+    L->ntiles += S.ntiles;
+    L->max_nblk = std::max(L->max_nblk, S.nblk);
+    L->max_q = std::max(L->max_q, S.q);
+    // eq-table chunks: the reduced side (padded to whole stages), then the lines side
+    const int rend = (S.red + TC_KS - 1) / TC_KS * TC_KS;
+    for (int i0 = 0; i0 < rend; i0 += EQ_CHUNK) L->items.push_back(EqItem{i, 1, i0, std::min(rend, i0 + EQ_CHUNK)});
+    for (int i0 = 0; i0 < S.lines; i0 += EQ_CHUNK)
+      L->items.push_back(EqItem{i, 0, i0, std::min(S.lines, i0 + EQ_CHUNK)});
+  }
+  size_t off = 0;
+  auto take = [&off](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  L->off_L = take(sizeof(LinDev) * njobs);
+  L->off_scr = take(sizeof(ProofScratch) * njobs);
+  L->off_dp = take(sizeof(DevProof) * njobs);
+  L->off_tiles = take(sizeof(TcTile) * (size_t)L->ntiles);
+  L->off_maps = take(sizeof(CUtensorMap) * (size_t)L->nmats);
+  L->off_items = take(sizeof(EqItem) * L->items.size());
+  L->off_out = take(sizeof(vl_lin_proof) * njobs);
+  for (int i = 0; i < njobs; i++) {
+    const LinShape& S = L->shape[i];
+    LinBufs& b = L->buf[i];
+    b.fac = take(sizeof(Fr) * 4 * EQ_FAC);
+    b.w8 = take((size_t)8192 * ((S.red + TC_KS - 1) / TC_KS));
+    b.el = take(sizeof(Fr) * (size_t)S.lines);
+    // f (one segment per tile) or the column-sum accumulators (several)
+    b.f = take((S.nsplit == 1 ? sizeof(Fr) : 8 * sizeof(unsigned long long)) * (size_t)S.q * S.lines);
+    b.part = take(sizeof(Fr) * (size_t)S.q * S.nblk);
+  }
+  L->off_stage.assign(L->nmats, 0);
+  L->stage_ld.assign(L->nmats, 0);
+  L->staged.assign(L->nmats, 0);
+  int g = 0;
+  for (int i = 0; i < njobs; i++)
+    for (int q = 0; q < jobs[i].nmats; q++, g++) {
+      const vl_mat& M = jobs[i].mats[q];
+      if (tma_ready(M)) continue;
+      L->staged[g] = 1;
+      L->stage_ld[g] = (M.cols + 7) & ~int64_t(7);
+      L->off_stage[g] = take((size_t)M.rows * L->stage_ld[g] * 2);
+    }
+  L->total = off;
+  return VL_OK;
+}
+
+int cuda_fail(const char* where, cudaError_t e) {
+  char msg[256];
+  snprintf(msg, sizeof(msg), "%s: %s", where, cudaGetErrorString(e));
+  set_last_error(msg);
+  return VL_ECUDA;
+}
+
+}  // namespace
+
+extern "C" size_t vl_linear_workspace_bytes(const vl_lin_job* jobs, int32_t njobs) {
+  LinLayout L;
+  return lin_layout(jobs, njobs, &L) == VL_OK ? L.total : 0;
+}
+
+extern "C" int32_t vl_prove_linear(const vl_lin_job* jobs, int32_t njobs, void* workspace, size_t workspace_bytes,
+                                   vl_lin_proof* out, void* stream) {
+  LinLayout lay;
+  int e = lin_layout(jobs, njobs, &lay);
+  if (e != VL_OK) return e;
+  if (!workspace || !out) return VL_EINVAL;
+  if (reinterpret_cast<uintptr_t>(workspace) & (ALIGN - 1)) return VL_EINVAL;
+  if (workspace_bytes < lay.total) return VL_ENOMEM;
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LinDev* dL = reinterpret_cast<LinDev*>(ws + lay.off_L);
+  std::vector<LinDev> Ls(njobs);
+  std::vector<DevProof> dps(njobs);
+  for (int i = 0; i < njobs; i++) {
+    const vl_lin_job& J = jobs[i];
+    const LinShape& S = lay.shape[i];
+    const LinBufs& b = lay.buf[i];
+    LinDev& L = Ls[i];
+    std::memset(&L, 0, sizeof(L));
+    for (int q = 0; q < J.nmats; q++) {
+      for (int l = 0; l < 8; l++) L.coeffs[q].v[l] = J.coeffs[q].limb[l];
+      if (!lt_r(L.coeffs[q])) return VL_EINVAL;  // coefficients are canonical
+      if (J.binds) std::memcpy(L.binds[q], J.binds + 32 * q, 32);
+    }
+    L.rows = S.rows;
+    L.cols = S.cols;
+    L.d0 = S.d0;
+    L.d1 = S.d1;
+    L.nmats = S.q;
+    L.red_rows = S.red_rows ? 1 : 0;
+    L.lines = S.lines;
+    L.nblk = S.nblk;
+    L.seed = J.seed;
+    L.fac = reinterpret_cast<Fr*>(ws + b.fac);
+    L.w8 = reinterpret_cast<uint32_t*>(ws + b.w8);
+    L.el = reinterpret_cast<Fr*>(ws + b.el);
+    L.f = S.nsplit == 1 ? reinterpret_cast<Fr*>(ws + b.f) : nullptr;
+    L.acc = S.nsplit == 1 ? nullptr : reinterpret_cast<unsigned long long*>(ws + b.f);
+    L.part = reinterpret_cast<Fr*>(ws + b.part);
+    L.scr = reinterpret_cast<ProofScratch*>(ws + lay.off_scr) + i;
+    std::memset(&dps[i], 0, sizeof(DevProof));
+    dps[i].scr = L.scr;  // the fold reports a timeout through this proof's status
+  }
+
+  // Operands (the caller's device matrix, or a TMA-addressable copy) and
+  // fold tiles, proof by proof.
+  cudaError_t ce = cudaSuccess;
+  std::vector<CUtensorMap> maps(lay.nmats);
+  std::vector<TcTile> tiles;
+  tiles.reserve(lay.ntiles);
+  int g = 0;
+  for (int i = 0; i < njobs && ce == cudaSuccess; i++) {
+    const LinShape& S = lay.shape[i];
+    const LinDev& L = Ls[i];
+    const int ntl = (S.lines + TC_M - 1) / TC_M;
+    for (int q = 0; q < S.q && ce == cudaSuccess; q++, g++) {
+      const vl_mat& M = jobs[i].mats[q];
+      const void* base = M.data;
+      int64_t ld = M.ld;
+      if (lay.staged[g]) {
+        ld = lay.stage_ld[g];
+        ce = cudaMemcpy2DAsync(ws + lay.off_stage[g], ld * 2, M.data, M.ld * 2, M.cols * 2, M.rows,
+                               M.space == VL_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
+        base = ws + lay.off_stage[g];
+      }
+      // Column sums reduce over stored rows, row dots over stored columns.
+      const int32_t mode = (S.red_rows != (M.trans != 0)) ? MODE_COLSUM : MODE_ROWDOT;
+      std::memset(&maps[g], 0, sizeof(CUtensorMap));
+      if (!encode_tc_operand(base, M.rows, M.cols, ld, mode, &maps[g])) {
+        char msg[128];
+        snprintf(msg, sizeof(msg), "vl_prove_linear: tensor map of job %d matrix %d could not be encoded", i, q);
+        set_last_error(msg);
+        return VL_EINVAL;
+      }
+      for (int t = 0; t < ntl; t++)
+        for (int k = 0; k < S.nsplit; k++) {
+          TcTile tt{};
+          tt.tmap = ws + lay.off_maps + (size_t)g * sizeof(CUtensorMap);
+          tt.w8 = L.w8;
+          tt.mode = mode;
+          tt.w0 = t * TC_M;
+          tt.nw = std::min(TC_M, S.lines - tt.w0);
+          tt.k0 = k * S.seg;
+          tt.nk = std::min(S.seg, S.red - tt.k0);
+          tt.proof = i;
+          tt.task = g;
+          const size_t line = (size_t)q * S.lines + tt.w0;
+          tt.acc = L.acc ? L.acc + line * 8 : nullptr;
+          tt.f = L.acc ? nullptr : L.f + line;
+          tt.corr = L.acc ? nullptr : &dL[i].corr;
+          tiles.push_back(tt);
+        }
+    }
+  }
+  // Longest tiles first: the fold deals tiles to CTAs round robin.
+  std::stable_sort(tiles.begin(), tiles.end(), [](const TcTile& a, const TcTile& b) { return a.nk > b.nk; });
+  auto up = [&](size_t off, const void* src, size_t bytes) {
+    if (ce == cudaSuccess && bytes) ce = cudaMemcpyAsync(ws + off, src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  up(lay.off_L, Ls.data(), sizeof(LinDev) * njobs);
+  up(lay.off_dp, dps.data(), sizeof(DevProof) * njobs);
+  up(lay.off_tiles, tiles.data(), sizeof(TcTile) * tiles.size());
+  up(lay.off_maps, maps.data(), sizeof(CUtensorMap) * maps.size());
+  up(lay.off_items, lay.items.data(), sizeof(EqItem) * lay.items.size());
+  for (int i = 0; i < njobs && ce == cudaSuccess; i++)
+    if (Ls[i].acc)
+      ce = cudaMemsetAsync(Ls[i].acc, 0, sizeof(unsigned long long) * 8 * (size_t)Ls[i].nmats * Ls[i].lines, st);
+  vl_lin_proof* dout = reinterpret_cast<vl_lin_proof*>(ws + lay.off_out);
+  if (ce == cudaSuccess)
+    ce = launch_linear_start(dL, njobs, reinterpret_cast<const EqItem*>(ws + lay.off_items), (int)lay.items.size(),
+                             st);
+  if (ce == cudaSuccess) ce = fold_tc_prepare();
+  if (ce == cudaSuccess)
+    ce = launch_fold_tc(reinterpret_cast<const TcTile*>(ws + lay.off_tiles), lay.ntiles,
+                        reinterpret_cast<const DevProof*>(ws + lay.off_dp), FOLD_WAIT_NS, st);
+  if (ce == cudaSuccess) ce = launch_linear_finish(dL, njobs, lay.max_nblk, lay.max_q, dout, st);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(out, dout, sizeof(vl_lin_proof) * njobs, cudaMemcpyDeviceToHost, st);
+  // The host tables above must outlive their copies, and the proofs are read now.
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return cuda_fail("vl_prove_linear", ce);
+  for (int i = 0; i < njobs; i++)
+    if (out[i].status != VL_OK) return out[i].status;
+  return VL_OK;
+}

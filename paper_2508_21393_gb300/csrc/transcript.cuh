@@ -59,6 +59,30 @@ VL_HD void ts_start(uint8_t S[32], uint64_t seed, uint32_t m, uint32_t k, uint32
   h.finish(S);
 }
 
+// Start of a linear zkMat transcript:
+//   S0 = SHA256("verilora-gb300/zklin/v1" || seed u64le || rows, cols, q u32le
+//               || coeffs (q x 32 B, canonical) || binds (q x 32 B))
+VL_HD void ts_start_linear(uint8_t S[32], uint64_t seed, uint32_t rows, uint32_t cols, int q, const Fr* coeffs,
+                           const uint8_t (*binds)[32]) {
+  const uint8_t dom[23] = {'v', 'e', 'r', 'i', 'l', 'o', 'r', 'a', '-', 'g', 'b', '3',
+                           '0', '0', '/', 'z', 'k', 'l', 'i', 'n', '/', 'v', '1'};
+  Sha256 h;
+  h.init();
+  h.update(dom, 23);
+  h.u32le((uint32_t)seed);
+  h.u32le((uint32_t)(seed >> 32));
+  h.u32le(rows);
+  h.u32le(cols);
+  h.u32le((uint32_t)q);
+  for (int i = 0; i < q; i++) {
+    uint8_t b[32];
+    fr_to_le_bytes(coeffs[i], b);
+    h.update(b, 32);
+  }
+  for (int i = 0; i < q; i++) h.update(binds[i], 32);
+  h.finish(S);
+}
+
 // absorb(label, canonical field elements)
 VL_HD void ts_absorb_fr(uint8_t S[32], uint8_t label, const Fr* vals, int count) {
   Sha256 h;

@@ -162,3 +162,54 @@ extern "C" int32_t vl_verify_matmul(const vl_mat* P, const vl_mat* Q, const vl_m
   if (!fr_eq(to_mont(br), mle_eval(B, rs, v))) return VL_REJECT;
   return VL_OK;
 }
+
+// Host verifier of a linear zkMat proof (sum_q c_q op(M_q) = 0, Sec. IV):
+// replays the transcript from the statement, checks sum_q c_q e_q = 0 and the
+// final state, and evaluates every M_q~(x, y) from the matrices.
+extern "C" int32_t vl_verify_linear(const vl_lin_job* job, const vl_lin_proof* proof) {
+  if (!job || !proof || !job->mats || !job->coeffs || job->nmats < 1 || job->nmats > VL_LIN_MAX || job->reserved)
+    return VL_EINVAL;
+  const vl_mat* mats = job->mats;
+  const int nmats = job->nmats;
+  const uint8_t* binds = job->binds;
+  const uint64_t seed = job->seed;
+  const vl_fr* coeffs = job->coeffs;
+  int e;
+  for (int q = 0; q < nmats; q++)
+    if ((e = check_host_mat(&mats[q])) != VL_OK) return e;
+  const int64_t rows = HostMat{&mats[0]}.rows(), cols = HostMat{&mats[0]}.cols();
+  for (int q = 1; q < nmats; q++)
+    if (HostMat{&mats[q]}.rows() != rows || HostMat{&mats[q]}.cols() != cols) return VL_ESHAPE;
+  if (rows > VL_MAX_REDUCE || cols > VL_MAX_REDUCE) return VL_ESHAPE;
+  std::vector<Fr> c(nmats);
+  uint8_t bind[VL_LIN_MAX][32] = {};
+  for (int q = 0; q < nmats; q++) {
+    c[q] = fr_from_api(coeffs[q]);
+    if (!lt_r(c[q])) return VL_EINVAL;
+    if (binds) std::memcpy(bind[q], binds + 32 * q, 32);
+  }
+  const int d0 = ceil_log2(rows), d1 = ceil_log2(cols);
+  if (proof->rows != rows || proof->cols != cols || proof->d0 != d0 || proof->d1 != d1 || proof->nmats != nmats)
+    return VL_REJECT;
+  if (proof->status != VL_OK) return VL_REJECT;
+  std::vector<Fr> ev(nmats);
+  for (int q = 0; q < nmats; q++) {
+    ev[q] = fr_from_api(proof->evals[q]);
+    if (!lt_r(ev[q])) return VL_REJECT;
+  }
+  uint8_t S[32];
+  ts_start_linear(S, seed, (uint32_t)rows, (uint32_t)cols, nmats, c.data(), bind);
+  std::vector<Fr> x(d0), y(d1);
+  for (int t = 0; t < d0; t++) x[t] = to_mont(ts_challenge(S, 'x', t));
+  ts_squeeze_done(S, 'x', d0);
+  for (int t = 0; t < d1; t++) y[t] = to_mont(ts_challenge(S, 'y', t));
+  ts_squeeze_done(S, 'y', d1);
+  Fr sum = fr_zero();
+  for (int q = 0; q < nmats; q++) sum = fr_add(sum, mont_mul(to_mont(c[q]), to_mont(ev[q])));
+  if (!fr_is_zero(sum)) return VL_REJECT;
+  ts_absorb_fr(S, 'e', ev.data(), nmats);
+  if (std::memcmp(S, proof->state, 32) != 0) return VL_REJECT;
+  for (int q = 0; q < nmats; q++)
+    if (!fr_eq(to_mont(ev[q]), mle_eval(HostMat{&mats[q]}, x, y))) return VL_REJECT;
+  return VL_OK;
+}

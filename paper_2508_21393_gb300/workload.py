@@ -24,6 +24,14 @@ transpose flag.
 
 Rescale (workload only; it is a lookup-proved step in the paper, Sec. IV-A,
 zkSwiGLU quantisation): z' = floor((z + 2^7) / 2^8), clamped to int16.
+
+Parameter update (Eq. eq:grad_update_ab, in fixed point): the learning rate
+is eta = 2^-UPDATE_SHIFT at the tensor scale, so the step of a LoRA factor is
+G = rescale(dFactor, UPDATE_SHIFT) (the exact gradient product, rounded half
+up, clamped to +-2^14) and the updated factor is Factor' = Factor - G.  The
+update is then the linear relation Factor' - Factor + G = 0, proved by the
+linear zkMat with coefficients (1, -1, 1); the rescale itself is a
+lookup-proved step.
 """
 
 import hashlib
@@ -122,6 +130,26 @@ def projection_products(t, seed=GLOBAL_SEED):
         P, Q, tp, tq = spec[name]
         out.append({"P": P, "Q": Q, "tp": tp, "tq": tq, "name": f"L{t['layer']}.{t['proj']}.{name}",
                     "seed": proof_seed(seed, t["layer"], t["proj"], name)})
+    return out
+
+
+UPDATE_SHIFT = 12
+UPDATE_CLAMP = 1 << 14
+
+
+def update_statements(t, seed=GLOBAL_SEED):
+    """The two parameter-update relations of one projection: A' = A - G_A
+    (d x r) and B' = B - G_B (r x k), with G = rescale(gradient) as above.
+    Each is {"mats": (A', A, G), "coeffs": (1, -1, 1), "seed", "name"}."""
+    X, A, B, dY, H, dH = (t[x] for x in ("X", "A", "B", "dY", "H", "dH"))
+    out = []
+    for name, F, grad in (("A", A, lambda: exact_matmul(X.T, dH)), ("B", B, lambda: exact_matmul(H.T, dY))):
+        G = np.clip(rescale(grad(), UPDATE_SHIFT), -UPDATE_CLAMP, UPDATE_CLAMP).astype(np.int16)
+        F2 = (F.astype(np.int32) - G.astype(np.int32))
+        assert F2.min() >= I16_MIN and F2.max() <= I16_MAX
+        out.append({"mats": (F2.astype(np.int16), F, G), "coeffs": (1, -1, 1),
+                    "seed": proof_seed(seed, t["layer"], t["proj"], "U" + name),
+                    "name": f"L{t['layer']}.{t['proj']}.U{name}"})
     return out
 
 
