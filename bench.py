@@ -43,11 +43,13 @@ SM_MAX_MHZ = 2070.0
 # the ALU roofline of the int16 fold: 64 32-bit integer multiply-adds per SM
 # per clock, a wide (64-bit result) one taking two of them.
 MADWIDE_PER_SM_CLK = 32
-STEP_KIND = {"7b-step": "7b", "7b-proj": "7b-proj", "13b-step": "13b", "serve": "7b-proj"}
+STEP_KIND = {"7b-step": "7b", "7b-proj": "7b-proj", "13b-step": "13b", "serve": "7b-proj", "7b-update": "7b"}
 WORKLOADS = {
     "7b-step": "batched 7B-shaped LoRA step: 32 layers x {q,k,v,o}, hidden 4096, seq 512, ranks {8,16,64}",
     "7b-proj": "one 7B-shaped LoRA projection, n=1024, d=k=4096, r=16, eight products",
     "13b-step": "batched 13B-shaped LoRA step: 40 layers x {q,k,v,o}, hidden 5120, seq 2048, rank 16",
+    "7b-update": "parameter updates of the 7B-shaped LoRA step (Eq. eq:grad_update_ab): 32 layers x {q,k,v,o} x "
+                 "{A' = A - G_A (4096 x r), B' = B - G_B (r x 4096)}, ranks {8,16,64}, linear zkMat, one batched call",
     "serve": "serving stream: Poisson arrivals (20 jobs/s) of single-layer jobs (one projection's 8 products), "
              "hidden {4096, 5120}, seq {256, 512, 1024, 2048}, rank {8, 16, 64}, 120 GB admission budget",
 }
@@ -164,6 +166,26 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     cores = 1
+    if args.workload == "7b-update":
+        nproj = 8
+        per_step = []
+        for _ in range(args.warmup):
+            oracle_update_sample(W.GLOBAL_SEED, nproj)
+        for _ in range(args.steps):
+            rate, dt, nj, ent = oracle_update_sample(W.GLOBAL_SEED, nproj)
+            per_step.append(dt)
+        total = sum(per_step)
+        value = ent * args.steps / total
+        sample = f"update relations of the first {nproj} projections ({nj} proofs, {ent} entries) per step"
+        print(json.dumps({
+            "impl": "reference", "metric": LIN_METRIC, "value": value, "unit": LIN_UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int (Fr, 255-bit)",
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "sample": sample},
+            "cpu_baseline": {"value": value, "unit": LIN_UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": LIN_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
     per_step = []
     macs_step = None
     for _ in range(args.warmup):
@@ -290,6 +312,133 @@ def serve_main(args, rank, world, local):
     print(json.dumps(line))
 
 
+LIN_METRIC = "linear-relation matrix entries proved/sec (parameter-update proofs of a LoRA step), bit-exact"
+LIN_UNIT = "entries/s"
+
+
+def update_statements(seed, layers=0, nproj=None):
+    spec = W.step_layers("7b", seed)
+    if layers > 0:
+        spec = [s for s in spec if s[0] < layers]
+    if nproj is not None:
+        spec = spec[:nproj]
+    stmts = []
+    for s in spec:
+        stmts += W.update_statements(W.lora_projection(seed, *s), seed)
+    return stmts
+
+
+def oracle_update_sample(seed, nproj):
+    """Time the oracle on the update relations of the first `nproj` projections."""
+    import oracle
+    stmts = update_statements(seed, nproj=nproj)
+    entries = sum(m.size for st in stmts for m in st["mats"])
+    t0 = time.perf_counter()
+    for st in stmts:
+        oracle.prove_linear(list(st["mats"]), list(st["coeffs"]), seed=st["seed"])
+    dt = time.perf_counter() - t0
+    return entries / dt, dt, len(stmts), entries
+
+
+def update_main(args, rank, world, local, cpu):
+    """Parameter-update proofs of the 7B step: 256 linear relations (three
+    int16 matrices each) proved by one plan run (five launches) per step."""
+    import torch
+    from paper_2508_21393_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.lib()
+    stmts = update_statements(rank_seed(rank), args.layers)
+    entries = sum(m.size for st in stmts for m in st["mats"])
+    dev = [[torch.from_numpy(m).cuda() for m in st["mats"]] for st in stmts]
+    jobs = [B.lin_job([B.mat(t) for t in d], list(st["coeffs"]), st["seed"]) for d, st in zip(dev, stmts)]
+    plan = B.LinPlan(jobs)
+    n = plan.workspace_bytes()
+    ws = torch.empty(n, dtype=torch.uint8, device="cuda")
+    dout = torch.empty(len(jobs) * ctypes.sizeof(B.vl_lin_proof), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):  # the first run binds the plan to the workspace
+        plan.run(ws.data_ptr(), n, dout.data_ptr(), B.VL_DEVICE, stream)
+    torch.cuda.synchronize()
+    raw = dout.cpu().numpy().tobytes()
+    out = [B.vl_lin_proof.from_buffer_copy(raw, i * ctypes.sizeof(B.vl_lin_proof)) for i in range(len(jobs))]
+    assert all(p.status == 0 for p in out)
+    # every warm-up proof verifies in the library's host verifier (not timed)
+    hj = [B.lin_job([B.mat(m) for m in st["mats"]], list(st["coeffs"]), st["seed"]) for st in stmts]
+    assert all(B.vl_verify_linear(j, p) for j, p in zip(hj, out))
+    # a buffer larger than L2 written between steps: the operands (~0.2 GB) would otherwise stay in L2
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    time.sleep(0.6)
+    total_ms, phases = 0.0, []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.run(ws.data_ptr(), n, dout.data_ptr(), B.VL_DEVICE, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        phases.append(plan.phase_ms())
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = total_ms / args.steps
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = job_value(entries, world, ms_max / 1e3)
+    fold_ms = statistics.mean(p[1] for p in phases)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak, hbm_note = (peaks["hbm_gbs"], "measured") if "hbm_gbs" in peaks else (6800.0, "fallback")
+    hbm_gbs = 2 * entries / (fold_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "fold_tc_kernel", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
+            "frac": hbm_gbs / hbm_peak, "traffic": None,
+            "peak_note": f"{hbm_note} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "algorithmic_bytes_per_launch": 2 * entries}
+    # End to end: pinned host operands in (staged by the library), host proofs out.
+    host = [[torch.from_numpy(m).pin_memory() for m in st["mats"]] for st in stmts]
+    hjobs = [B.lin_job([B.mat(t) for t in h], list(st["coeffs"]), st["seed"]) for h, st in zip(host, stmts)]
+    hplan = B.LinPlan(hjobs)
+    hn = hplan.workspace_bytes()
+    plan.destroy()
+    del ws
+    hws = torch.empty(hn, dtype=torch.uint8, device="cuda")
+    hplan.run(hws.data_ptr(), hn, stream=stream)
+    ksteps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(ksteps):
+        hplan.run(hws.data_ptr(), hn, stream=stream)  # operands copied in, proofs read back, every run
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / ksteps, world, "cuda")
+    hplan.destroy()
+    e2e = {"value": job_value(entries, world, e2e_s), "unit": LIN_UNIT,
+           "h2d_bytes_per_step": int(2 * entries), "d2h_bytes_per_step": int(ctypes.sizeof(B.vl_lin_proof) * len(jobs)),
+           "ms_per_step": 1e3 * e2e_s, "steps": ksteps}
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": LIN_METRIC, "value": value, "unit": LIN_UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int16 operands, Fr (255-bit) arithmetic", "data": "synthetic",
+        "config": {"workload": WORKLOADS["7b-update"] + (f", first {args.layers} layers" if args.layers else ""),
+                   "proofs_per_step": len(jobs), "matrices_per_step": 3 * len(jobs), "entries_per_step": entries,
+                   "l2": "256 MB buffer written between steps (operands smaller than L2)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single GPU",
+                   "phase_ms": {"start+eq": statistics.mean(p[0] for p in phases), "fold": fold_ms,
+                                "dots+proofs": statistics.mean(p[2] for p in phases)}},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+        "gpu_launches": 5 * args.steps,
+    }))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -297,6 +446,14 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "serve":
         return serve_main(args, rank, world, local)
+    if args.workload == "7b-update":
+        cpu = None
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            rate, dt, nj, ent = oracle_update_sample(W.GLOBAL_SEED, args.cpu_sample_projections)
+            cpu = {"value": rate, "unit": LIN_UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"update relations of the first {args.cpu_sample_projections} projections "
+                             f"({nj} proofs, {ent} entries), single process, {dt:.1f} s"}
+        return update_main(args, rank, world, local, cpu)
 
     # The oracle CPU baseline runs before any CUDA work (no forked pools after it).
     cpu = None

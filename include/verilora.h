@@ -305,6 +305,23 @@ size_t vl_linear_workspace_bytes(const vl_lin_job* jobs, int32_t njobs);
  * relation: a false one yields a proof that the verifier rejects. */
 int32_t vl_prove_linear(const vl_lin_job* jobs, int32_t njobs, void* workspace, size_t workspace_bytes,
                         vl_lin_proof* out, void* stream);
+/* Plans: the same batch proved repeatedly (a training loop's updates).  A
+ * plan copies the statements (the operand descriptors, not their data: the
+ * matrices are read at every run) and, on its first run with a workspace,
+ * uploads its tables there (synchronising `stream`); later runs with that
+ * workspace only enqueue the host-operand copies and five kernels.  The
+ * workspace must not be used by anything else between runs.  out_space
+ * VL_DEVICE: `out` is device memory and the run is asynchronous (each
+ * proof's status field reports its outcome); VL_HOST: as vl_prove_linear. */
+typedef struct vl_lin_plan vl_lin_plan;
+int32_t vl_lin_plan_create(const vl_lin_job* jobs, int32_t njobs, vl_lin_plan** plan);
+size_t vl_lin_plan_workspace_bytes(const vl_lin_plan* plan);
+int32_t vl_lin_plan_run(vl_lin_plan* plan, void* workspace, size_t workspace_bytes, vl_lin_proof* out,
+                        int32_t out_space, void* stream);
+/* Device times (ms) of the plan's last run (waits for it): ms[0] start and eq
+ * tables, ms[1] the tensor-core fold, ms[2] partial dot products and proofs. */
+int32_t vl_lin_plan_phase_ms(vl_lin_plan* plan, float ms[3]);
+void vl_lin_plan_destroy(vl_lin_plan* plan);
 /* Verify one proof on the host against host operands (int16, int64 or
  * Montgomery): VL_OK (accept), VL_REJECT, or an argument error. */
 int32_t vl_verify_linear(const vl_lin_job* job, const vl_lin_proof* proof);

@@ -29,7 +29,9 @@ EXPORTS = ("vl_version", "vl_strerror", "vl_last_error", "vl_workspace_bytes", "
            "vl_plan_create", "vl_plan_workspace_bytes", "vl_plan_run", "vl_plan_launches", "vl_plan_phase_ms",
            "vl_plan_destroy", "vl_verify_matmul", "vl_encode", "vl_prove_matmul_noalloc",
            "vl_server_create", "vl_server_submit", "vl_server_poll", "vl_server_stats_get", "vl_server_destroy",
-           "vl_autotune", "vl_autotune_clear", "vl_linear_workspace_bytes", "vl_prove_linear", "vl_verify_linear")
+           "vl_autotune", "vl_autotune_clear", "vl_linear_workspace_bytes", "vl_prove_linear", "vl_verify_linear",
+           "vl_lin_plan_create", "vl_lin_plan_workspace_bytes", "vl_lin_plan_run", "vl_lin_plan_phase_ms",
+           "vl_lin_plan_destroy")
 VL_NOALLOC_SCRATCH_BYTES = 8 << 20
 VL_LIN_MAX = 16
 R_MOD = 0x73EDA753299D7D483339D80809A1D80553BDA402FFFE5BFEFFFFFFFF00000001
@@ -171,6 +173,17 @@ def lib():
                                   P(vl_lin_proof), ctypes.c_void_p]
     L.vl_prove_linear.restype = ctypes.c_int32
     L.vl_verify_linear.argtypes = [P(vl_lin_job), P(vl_lin_proof)]
+    L.vl_lin_plan_create.argtypes = [P(vl_lin_job), ctypes.c_int32, P(ctypes.c_void_p)]
+    L.vl_lin_plan_create.restype = ctypes.c_int32
+    L.vl_lin_plan_workspace_bytes.argtypes = [ctypes.c_void_p]
+    L.vl_lin_plan_workspace_bytes.restype = ctypes.c_size_t
+    L.vl_lin_plan_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                  ctypes.c_int32, ctypes.c_void_p]
+    L.vl_lin_plan_run.restype = ctypes.c_int32
+    L.vl_lin_plan_phase_ms.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]
+    L.vl_lin_plan_phase_ms.restype = ctypes.c_int32
+    L.vl_lin_plan_destroy.argtypes = [ctypes.c_void_p]
+    L.vl_lin_plan_destroy.restype = None
     L.vl_verify_linear.restype = ctypes.c_int32
     L.vl_encode.restype = ctypes.c_int32
     _lib = L
@@ -480,6 +493,41 @@ def vl_prove_linear(jobs, workspace, workspace_bytes, stream=None):
     _check(lib().vl_prove_linear(arr, len(jobs), workspace, workspace_bytes, out, _stream_ptr(stream)),
            "vl_prove_linear")
     return out
+
+
+class LinPlan:
+    """A vl_lin_plan (keeps the jobs' arrays alive as long as the plan)."""
+
+    def __init__(self, jobs):
+        self.arr = lin_jobs_array(jobs)
+        self.ptr = ctypes.c_void_p()
+        _check(lib().vl_lin_plan_create(self.arr, len(jobs), ctypes.byref(self.ptr)), "vl_lin_plan_create")
+        self.n = len(jobs)
+
+    def workspace_bytes(self):
+        return lib().vl_lin_plan_workspace_bytes(self.ptr)
+
+    def run(self, workspace, workspace_bytes, out=None, out_space=VL_HOST, stream=None):
+        """VL_HOST: returns the ctypes array of proofs; VL_DEVICE: `out` is a
+        device pointer (int) to n proofs and the run is asynchronous."""
+        if out_space == VL_HOST:
+            res = (vl_lin_proof * self.n)()
+            ptr = ctypes.addressof(res)
+        else:
+            res, ptr = None, int(out)
+        _check(lib().vl_lin_plan_run(self.ptr, workspace, workspace_bytes, ptr, out_space, _stream_ptr(stream)),
+               "vl_lin_plan_run")
+        return res
+
+    def phase_ms(self):
+        ms = (ctypes.c_float * 3)()
+        _check(lib().vl_lin_plan_phase_ms(self.ptr, ms), "vl_lin_plan_phase_ms")
+        return tuple(ms)
+
+    def destroy(self):
+        if self.ptr:
+            lib().vl_lin_plan_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p()
 
 
 def vl_verify_linear(job, proof):

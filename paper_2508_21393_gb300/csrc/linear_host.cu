@@ -177,44 +177,38 @@ int cuda_fail(const char* where, cudaError_t e) {
 
 }  // namespace
 
-extern "C" size_t vl_linear_workspace_bytes(const vl_lin_job* jobs, int32_t njobs) {
-  LinLayout L;
-  return lin_layout(jobs, njobs, &L) == VL_OK ? L.total : 0;
-}
-
-extern "C" int32_t vl_prove_linear(const vl_lin_job* jobs, int32_t njobs, void* workspace, size_t workspace_bytes,
-                                   vl_lin_proof* out, void* stream) {
+// A batch of linear relations: the statements (copied), the workspace
+// layout, and the device tables of the workspace it was last bound to.
+struct vl_lin_plan {
   LinLayout lay;
-  int e = lin_layout(jobs, njobs, &lay);
-  if (e != VL_OK) return e;
-  if (!workspace || !out) return VL_EINVAL;
-  if (reinterpret_cast<uintptr_t>(workspace) & (ALIGN - 1)) return VL_EINVAL;
-  if (workspace_bytes < lay.total) return VL_ENOMEM;
-  uint8_t* ws = static_cast<uint8_t*>(workspace);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<std::vector<vl_mat>> mats;
+  std::vector<LinDev> Ls;  // statements; device pointers filled at bind time
+  std::vector<DevProof> dps;
+  std::vector<CUtensorMap> maps;
+  std::vector<TcTile> tiles;
+  uint8_t* bound_ws = nullptr;
+  int device = -1;
+  cudaEvent_t ev[4] = {};
+  bool timed = false;  // the events hold a run
+  ~vl_lin_plan() {
+    for (cudaEvent_t& x : ev)
+      if (x) cudaEventDestroy(x);
+  }
+};
+
+namespace {
+
+// Device pointers of workspace `ws` into the tables, tensor maps of the
+// operands, fold tiles; uploaded on `st` (synchronised: the host tables
+// must outlive the copies).
+int lin_bind(vl_lin_plan* P, uint8_t* ws, cudaStream_t st) {
+  const LinLayout& lay = P->lay;
+  const int np = lay.np;
   LinDev* dL = reinterpret_cast<LinDev*>(ws + lay.off_L);
-  std::vector<LinDev> Ls(njobs);
-  std::vector<DevProof> dps(njobs);
-  for (int i = 0; i < njobs; i++) {
-    const vl_lin_job& J = jobs[i];
+  for (int i = 0; i < np; i++) {
     const LinShape& S = lay.shape[i];
     const LinBufs& b = lay.buf[i];
-    LinDev& L = Ls[i];
-    std::memset(&L, 0, sizeof(L));
-    for (int q = 0; q < J.nmats; q++) {
-      for (int l = 0; l < 8; l++) L.coeffs[q].v[l] = J.coeffs[q].limb[l];
-      if (!lt_r(L.coeffs[q])) return VL_EINVAL;  // coefficients are canonical
-      if (J.binds) std::memcpy(L.binds[q], J.binds + 32 * q, 32);
-    }
-    L.rows = S.rows;
-    L.cols = S.cols;
-    L.d0 = S.d0;
-    L.d1 = S.d1;
-    L.nmats = S.q;
-    L.red_rows = S.red_rows ? 1 : 0;
-    L.lines = S.lines;
-    L.nblk = S.nblk;
-    L.seed = J.seed;
+    LinDev& L = P->Ls[i];
     L.fac = reinterpret_cast<Fr*>(ws + b.fac);
     L.w8 = reinterpret_cast<uint32_t*>(ws + b.w8);
     L.el = reinterpret_cast<Fr*>(ws + b.el);
@@ -222,37 +216,26 @@ extern "C" int32_t vl_prove_linear(const vl_lin_job* jobs, int32_t njobs, void* 
     L.acc = S.nsplit == 1 ? nullptr : reinterpret_cast<unsigned long long*>(ws + b.f);
     L.part = reinterpret_cast<Fr*>(ws + b.part);
     L.scr = reinterpret_cast<ProofScratch*>(ws + lay.off_scr) + i;
-    std::memset(&dps[i], 0, sizeof(DevProof));
-    dps[i].scr = L.scr;  // the fold reports a timeout through this proof's status
+    std::memset(&P->dps[i], 0, sizeof(DevProof));
+    P->dps[i].scr = L.scr;  // the fold reports a timeout through this proof's status
   }
-
-  // Operands (the caller's device matrix, or a TMA-addressable copy) and
-  // fold tiles, proof by proof.
-  cudaError_t ce = cudaSuccess;
-  std::vector<CUtensorMap> maps(lay.nmats);
-  std::vector<TcTile> tiles;
-  tiles.reserve(lay.ntiles);
+  P->maps.assign(lay.nmats, CUtensorMap{});
+  P->tiles.clear();
+  P->tiles.reserve(lay.ntiles);
   int g = 0;
-  for (int i = 0; i < njobs && ce == cudaSuccess; i++) {
+  for (int i = 0; i < np; i++) {
     const LinShape& S = lay.shape[i];
-    const LinDev& L = Ls[i];
+    const LinDev& L = P->Ls[i];
     const int ntl = (S.lines + TC_M - 1) / TC_M;
-    for (int q = 0; q < S.q && ce == cudaSuccess; q++, g++) {
-      const vl_mat& M = jobs[i].mats[q];
-      const void* base = M.data;
-      int64_t ld = M.ld;
-      if (lay.staged[g]) {
-        ld = lay.stage_ld[g];
-        ce = cudaMemcpy2DAsync(ws + lay.off_stage[g], ld * 2, M.data, M.ld * 2, M.cols * 2, M.rows,
-                               M.space == VL_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
-        base = ws + lay.off_stage[g];
-      }
+    for (int q = 0; q < S.q; q++, g++) {
+      const vl_mat& M = P->mats[i][q];
+      const void* base = lay.staged[g] ? ws + lay.off_stage[g] : M.data;
+      const int64_t ld = lay.staged[g] ? lay.stage_ld[g] : M.ld;
       // Column sums reduce over stored rows, row dots over stored columns.
       const int32_t mode = (S.red_rows != (M.trans != 0)) ? MODE_COLSUM : MODE_ROWDOT;
-      std::memset(&maps[g], 0, sizeof(CUtensorMap));
-      if (!encode_tc_operand(base, M.rows, M.cols, ld, mode, &maps[g])) {
+      if (!encode_tc_operand(base, M.rows, M.cols, ld, mode, &P->maps[g])) {
         char msg[128];
-        snprintf(msg, sizeof(msg), "vl_prove_linear: tensor map of job %d matrix %d could not be encoded", i, q);
+        snprintf(msg, sizeof(msg), "linear proofs: tensor map of job %d matrix %d could not be encoded", i, q);
         set_last_error(msg);
         return VL_EINVAL;
       }
@@ -272,38 +255,163 @@ extern "C" int32_t vl_prove_linear(const vl_lin_job* jobs, int32_t njobs, void* 
           tt.acc = L.acc ? L.acc + line * 8 : nullptr;
           tt.f = L.acc ? nullptr : L.f + line;
           tt.corr = L.acc ? nullptr : &dL[i].corr;
-          tiles.push_back(tt);
+          P->tiles.push_back(tt);
         }
     }
   }
   // Longest tiles first: the fold deals tiles to CTAs round robin.
-  std::stable_sort(tiles.begin(), tiles.end(), [](const TcTile& a, const TcTile& b) { return a.nk > b.nk; });
+  std::stable_sort(P->tiles.begin(), P->tiles.end(), [](const TcTile& a, const TcTile& b) { return a.nk > b.nk; });
+  cudaError_t ce = cudaSuccess;
   auto up = [&](size_t off, const void* src, size_t bytes) {
     if (ce == cudaSuccess && bytes) ce = cudaMemcpyAsync(ws + off, src, bytes, cudaMemcpyHostToDevice, st);
   };
-  up(lay.off_L, Ls.data(), sizeof(LinDev) * njobs);
-  up(lay.off_dp, dps.data(), sizeof(DevProof) * njobs);
-  up(lay.off_tiles, tiles.data(), sizeof(TcTile) * tiles.size());
-  up(lay.off_maps, maps.data(), sizeof(CUtensorMap) * maps.size());
+  up(lay.off_L, P->Ls.data(), sizeof(LinDev) * np);
+  up(lay.off_dp, P->dps.data(), sizeof(DevProof) * np);
+  up(lay.off_tiles, P->tiles.data(), sizeof(TcTile) * P->tiles.size());
+  up(lay.off_maps, P->maps.data(), sizeof(CUtensorMap) * P->maps.size());
   up(lay.off_items, lay.items.data(), sizeof(EqItem) * lay.items.size());
-  for (int i = 0; i < njobs && ce == cudaSuccess; i++)
-    if (Ls[i].acc)
-      ce = cudaMemsetAsync(Ls[i].acc, 0, sizeof(unsigned long long) * 8 * (size_t)Ls[i].nmats * Ls[i].lines, st);
-  vl_lin_proof* dout = reinterpret_cast<vl_lin_proof*>(ws + lay.off_out);
-  if (ce == cudaSuccess)
-    ce = launch_linear_start(dL, njobs, reinterpret_cast<const EqItem*>(ws + lay.off_items), (int)lay.items.size(),
-                             st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
   if (ce == cudaSuccess) ce = fold_tc_prepare();
+  if (ce != cudaSuccess) return cuda_fail("linear proofs: bind", ce);
+  P->bound_ws = ws;
+  return VL_OK;
+}
+
+cudaError_t lin_events(vl_lin_plan* P) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev == P->device) return e;
+  for (cudaEvent_t& x : P->ev)
+    if (x) cudaEventDestroy(x), x = nullptr;  // events of the previous device
+  for (cudaEvent_t& x : P->ev)
+    if ((e = cudaEventCreate(&x)) != cudaSuccess) return e;
+  P->device = dev;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" size_t vl_linear_workspace_bytes(const vl_lin_job* jobs, int32_t njobs) {
+  LinLayout L;
+  return lin_layout(jobs, njobs, &L) == VL_OK ? L.total : 0;
+}
+
+extern "C" int32_t vl_lin_plan_create(const vl_lin_job* jobs, int32_t njobs, vl_lin_plan** plan) {
+  if (!plan) return VL_EINVAL;
+  *plan = nullptr;
+  vl_lin_plan* P = new (std::nothrow) vl_lin_plan;
+  if (!P) return VL_ENOMEM;
+  int e = lin_layout(jobs, njobs, &P->lay);
+  if (e != VL_OK) {
+    delete P;
+    return e;
+  }
+  P->mats.resize(njobs);
+  P->Ls.assign(njobs, LinDev{});
+  P->dps.assign(njobs, DevProof{});
+  for (int i = 0; i < njobs; i++) {
+    const vl_lin_job& J = jobs[i];
+    const LinShape& S = P->lay.shape[i];
+    LinDev& L = P->Ls[i];
+    std::memset(&L, 0, sizeof(L));
+    P->mats[i].assign(J.mats, J.mats + J.nmats);
+    for (int q = 0; q < J.nmats; q++) {
+      for (int l = 0; l < 8; l++) L.coeffs[q].v[l] = J.coeffs[q].limb[l];
+      if (!lt_r(L.coeffs[q])) {  // coefficients are canonical
+        delete P;
+        return VL_EINVAL;
+      }
+      if (J.binds) std::memcpy(L.binds[q], J.binds + 32 * q, 32);
+    }
+    L.rows = S.rows;
+    L.cols = S.cols;
+    L.d0 = S.d0;
+    L.d1 = S.d1;
+    L.nmats = S.q;
+    L.red_rows = S.red_rows ? 1 : 0;
+    L.lines = S.lines;
+    L.nblk = S.nblk;
+    L.seed = J.seed;
+  }
+  *plan = P;
+  return VL_OK;
+}
+
+extern "C" size_t vl_lin_plan_workspace_bytes(const vl_lin_plan* plan) { return plan ? plan->lay.total : 0; }
+
+extern "C" int32_t vl_lin_plan_run(vl_lin_plan* P, void* workspace, size_t workspace_bytes, vl_lin_proof* out,
+                                   int32_t out_space, void* stream) {
+  if (!P || !workspace || !out || (out_space != VL_DEVICE && out_space != VL_HOST)) return VL_EINVAL;
+  if (reinterpret_cast<uintptr_t>(workspace) & (ALIGN - 1)) return VL_EINVAL;
+  const LinLayout& lay = P->lay;
+  if (workspace_bytes < lay.total) return VL_ENOMEM;
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  P->timed = false;
+  if (P->bound_ws != ws) {
+    const int e = lin_bind(P, ws, st);
+    if (e != VL_OK) return e;
+  }
+  cudaError_t ce = lin_events(P);
+  // Operands that are not TMA-addressable in place: copied every run.
+  int g = 0;
+  for (int i = 0; i < lay.np && ce == cudaSuccess; i++)
+    for (const vl_mat& M : P->mats[i]) {
+      if (lay.staged[g] && ce == cudaSuccess)
+        ce = cudaMemcpy2DAsync(ws + lay.off_stage[g], lay.stage_ld[g] * 2, M.data, M.ld * 2, M.cols * 2, M.rows,
+                               M.space == VL_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
+      g++;
+    }
+  for (int i = 0; i < lay.np && ce == cudaSuccess; i++) {
+    const LinDev& L = P->Ls[i];
+    if (L.acc) ce = cudaMemsetAsync(L.acc, 0, sizeof(unsigned long long) * 8 * (size_t)L.nmats * L.lines, st);
+  }
+  LinDev* dL = reinterpret_cast<LinDev*>(ws + lay.off_L);
+  vl_lin_proof* dout = out_space == VL_DEVICE ? out : reinterpret_cast<vl_lin_proof*>(ws + lay.off_out);
+  cudaEvent_t* ev = P->ev;
+  if (ce == cudaSuccess) ce = cudaEventRecord(ev[0], st);
+  if (ce == cudaSuccess)
+    ce = launch_linear_start(dL, lay.np, reinterpret_cast<const EqItem*>(ws + lay.off_items), (int)lay.items.size(),
+                             st);
+  if (ce == cudaSuccess) ce = cudaEventRecord(ev[1], st);
   if (ce == cudaSuccess)
     ce = launch_fold_tc(reinterpret_cast<const TcTile*>(ws + lay.off_tiles), lay.ntiles,
                         reinterpret_cast<const DevProof*>(ws + lay.off_dp), FOLD_WAIT_NS, st);
-  if (ce == cudaSuccess) ce = launch_linear_finish(dL, njobs, lay.max_nblk, lay.max_q, dout, st);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(out, dout, sizeof(vl_lin_proof) * njobs, cudaMemcpyDeviceToHost, st);
-  // The host tables above must outlive their copies, and the proofs are read now.
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-  if (ce != cudaSuccess) return cuda_fail("vl_prove_linear", ce);
-  for (int i = 0; i < njobs; i++)
-    if (out[i].status != VL_OK) return out[i].status;
+  if (ce == cudaSuccess) ce = cudaEventRecord(ev[2], st);
+  if (ce == cudaSuccess) ce = launch_linear_finish(dL, lay.np, lay.max_nblk, lay.max_q, dout, st);
+  if (ce == cudaSuccess) ce = cudaEventRecord(ev[3], st);
+  if (ce == cudaSuccess && out_space == VL_HOST) {
+    ce = cudaMemcpyAsync(out, dout, sizeof(vl_lin_proof) * lay.np, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  }
+  if (ce != cudaSuccess) return cuda_fail("vl_lin_plan_run", ce);
+  P->timed = true;
+  if (out_space == VL_HOST)
+    for (int i = 0; i < lay.np; i++)
+      if (out[i].status != VL_OK) return out[i].status;
   return VL_OK;
+}
+
+extern "C" int32_t vl_lin_plan_phase_ms(vl_lin_plan* P, float ms[3]) {
+  if (!P || !ms || !P->timed) return VL_EINVAL;
+  cudaError_t ce = cudaEventSynchronize(P->ev[3]);
+  for (int i = 0; i < 3 && ce == cudaSuccess; i++) ce = cudaEventElapsedTime(&ms[i], P->ev[i], P->ev[i + 1]);
+  return ce == cudaSuccess ? VL_OK : cuda_fail("vl_lin_plan_phase_ms", ce);
+}
+
+extern "C" void vl_lin_plan_destroy(vl_lin_plan* plan) { delete plan; }
+
+extern "C" int32_t vl_prove_linear(const vl_lin_job* jobs, int32_t njobs, void* workspace, size_t workspace_bytes,
+                                   vl_lin_proof* out, void* stream) {
+  if (!workspace || !out) {
+    LinLayout L;  // argument errors of the jobs first, as a plan would report them
+    const int e = lin_layout(jobs, njobs, &L);
+    return e != VL_OK ? e : VL_EINVAL;
+  }
+  vl_lin_plan* P = nullptr;
+  int e = vl_lin_plan_create(jobs, njobs, &P);
+  if (e != VL_OK) return e;
+  e = vl_lin_plan_run(P, workspace, workspace_bytes, out, VL_HOST, stream);
+  vl_lin_plan_destroy(P);
+  return e;
 }

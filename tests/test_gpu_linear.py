@@ -8,6 +8,8 @@ stages, several reduction segments per line (accumulator path), transposed,
 host, unaligned and odd-pitch operands, extreme entries, batches of mixed
 shapes, and the full-size parameter updates of a 7B LoRA step.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -184,3 +186,39 @@ def test_linear_repeat_is_deterministic():
     _, a = gpu_prove([s])
     _, b = gpu_prove([s])
     assert B.lin_proof_bytes(a[0]) == B.lin_proof_bytes(b[0])
+
+
+def test_linear_plan_reruns_rebinds_and_device_output():
+    """A plan proves its batch at every run: the same proofs on repeated runs,
+    after moving to another workspace, and with proofs left on the device;
+    host operands are re-read at every run."""
+    rng = np.random.default_rng(15)
+    stmts = [Stmt([_rand(rng, (300, 40)) for _ in range(3)], [1, -2, 3], seed=4, where=["dev", "host", "pitch"]),
+             Stmt([_rand(rng, (64, 2000)) for _ in range(2)], [5, 6], seed=5, trans=[1, 0])]
+    jobs = [s.job() for s in stmts]
+    plan = B.LinPlan(jobs)
+    n = plan.workspace_bytes()
+    ws1, ws2 = _ws(n), _ws(n)
+    want = [s.oracle_bytes() for s in stmts]
+    for ws in (ws1, ws1, ws2, ws1):
+        out = plan.run(ws.data_ptr(), n)
+        assert [B.lin_proof_bytes(p) for p in out] == want
+    dout = torch.empty(2 * ctypes_sizeof_lin(), dtype=torch.uint8, device="cuda")
+    plan.run(ws2.data_ptr(), n, dout.data_ptr(), B.VL_DEVICE)
+    torch.cuda.synchronize()
+    raw = dout.cpu().numpy().tobytes()
+    got = [B.lin_proof_bytes(B.vl_lin_proof.from_buffer_copy(raw, i * ctypes_sizeof_lin())) for i in range(2)]
+    assert got == want
+    ms = plan.phase_ms()
+    assert all(x >= 0 for x in ms)
+    # the host operand changes in place: the next run proves the new matrix
+    host = stmts[0].keep[1]  # operand 1 of the first statement is the host array
+    host[0, 0] ^= 1
+    stmts[0].mats[1] = np.array(host)
+    out = plan.run(ws1.data_ptr(), n)
+    assert B.lin_proof_bytes(out[0]) == stmts[0].oracle_bytes()
+    plan.destroy()
+
+
+def ctypes_sizeof_lin():
+    return ctypes.sizeof(B.vl_lin_proof)

@@ -185,3 +185,17 @@ def test_update_statements_are_true_relations():
         F2, F, G = (m.astype(np.int64) for m in st["mats"])
         assert np.array_equal(F2 - F + G, np.zeros_like(F))
         assert st["coeffs"] == (1, -1, 1)
+
+
+def test_plan_create_validation(L):
+    rng = np.random.default_rng(7)
+    M = [_rand(rng, (20, 30)) for _ in range(2)]
+    j = _host_job(M, [1, 2])
+    plan = B.LinPlan([j])
+    assert plan.workspace_bytes() == B.vl_linear_workspace_bytes([j])
+    plan.destroy()
+    j._coeffs[1].limb[7] = 0xFFFFFFFF
+    with pytest.raises(B.VLError):
+        B.LinPlan([j])
+    with pytest.raises(B.VLError):
+        B.LinPlan([_host_job([M[0], _rand(rng, (20, 31))], [1, 1])])
