@@ -43,11 +43,15 @@ SM_MAX_MHZ = 2070.0
 # the ALU roofline of the int16 fold: 64 32-bit integer multiply-adds per SM
 # per clock, a wide (64-bit result) one taking two of them.
 MADWIDE_PER_SM_CLK = 32
-STEP_KIND = {"7b-step": "7b", "7b-proj": "7b-proj", "13b-step": "13b", "serve": "7b-proj", "7b-update": "7b"}
+STEP_KIND = {"7b-step": "7b", "7b-proj": "7b-proj", "13b-step": "13b", "serve": "7b-proj", "7b-update": "7b",
+             "7b-step-paper-route": "7b"}
 WORKLOADS = {
     "7b-step": "batched 7B-shaped LoRA step: 32 layers x {q,k,v,o}, hidden 4096, seq 512, ranks {8,16,64}",
     "7b-proj": "one 7B-shaped LoRA projection, n=1024, d=k=4096, r=16, eight products",
     "13b-step": "batched 13B-shaped LoRA step: 40 layers x {q,k,v,o}, hidden 5120, seq 2048, rank 16",
+    "7b-step-paper-route": "batched 7B-shaped LoRA step along the paper's backward route (Eq. eq:grad_wl, "
+                           "eq:grad_abl: full dW' = X^T.dY, then dA = dW'.B^T, dB = A^T.dW'), nine products per "
+                           "projection, 32 layers x {q,k,v,o}, hidden 4096, seq 512, ranks {8,16,64}",
     "7b-update": "parameter updates of the 7B-shaped LoRA step (Eq. eq:grad_update_ab): 32 layers x {q,k,v,o} x "
                  "{A' = A - G_A (4096 x r), B' = B - G_B (r x 4096)}, ranks {8,16,64}, linear zkMat, one batched call",
     "serve": "serving stream: Poisson arrivals (20 jobs/s) of single-layer jobs (one projection's 8 products), "
@@ -110,9 +114,17 @@ def job_value(units_per_rank, world, seconds_max):
     return units_per_rank * world / seconds_max
 
 
+def products(kind, t, seed):
+    if kind == "7b-step-paper-route":
+        jobs, dWr = W.paper_route_products(t, seed)
+        t["dWr"] = dWr
+        return jobs
+    return W.projection_products(t, seed)
+
+
 def step_jobs(kind, seed, layers=0):
     projs = W.make_step(STEP_KIND[kind], seed, layers=range(layers) if layers > 0 else None)
-    jobs = [j for t in projs for j in W.projection_products(t, seed)]
+    jobs = [j for t in projs for j in products(kind, t, seed)]
     return projs, jobs
 
 
@@ -121,7 +133,7 @@ def oracle_sample(kind, seed, nproj):
     import oracle
     spec = W.step_layers(STEP_KIND[kind], seed)[:nproj]
     projs = [W.lora_projection(seed, *s) for s in spec]
-    jobs = [j for t in projs for j in W.projection_products(t, seed)]
+    jobs = [j for t in projs for j in products(kind, t, seed)]
     macs = sum(W.macs(j) for j in jobs)
     t0 = time.perf_counter()
     for j in jobs:
@@ -196,7 +208,7 @@ def run_reference(args, rank, world):
         macs_step = macs
     total = sum(per_step)
     value = macs_step * args.steps / total
-    sample = f"1 projection (8 proofs, {macs_step} MACs) of the {args.workload} workload per step"
+    sample = f"1 projection ({nj} proofs, {macs_step} MACs) of the {args.workload} workload per step"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
@@ -478,8 +490,9 @@ def main():
 
     dev, keep = {}, []
     for t in projs:
-        for key in ("X", "W", "A", "B", "dY", "H", "dH"):
-            dev[id(t[key])] = torch.from_numpy(t[key]).cuda()
+        for key in ("X", "W", "A", "B", "dY", "H", "dH", "dWr"):
+            if key in t:
+                dev[id(t[key])] = torch.from_numpy(t[key]).cuda()
     djobs = [B.job(dev[id(j["P"])], dev[id(j["Q"])], j["tp"], j["tq"], j["seed"]) for j in jobs]
     in_bytes = sum(x.numel() * 2 for x in dev.values())
 
@@ -606,7 +619,9 @@ def main():
     if not args.no_e2e:
         host = {}
         for t in projs:
-            for key in ("X", "W", "A", "B", "dY", "H", "dH"):
+            for key in ("X", "W", "A", "B", "dY", "H", "dH", "dWr"):
+                if key not in t:
+                    continue
                 h = torch.empty(t[key].shape, dtype=torch.int16, pin_memory=True)
                 h.copy_(torch.from_numpy(t[key]))
                 host[id(t[key])] = h

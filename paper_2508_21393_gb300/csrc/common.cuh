@@ -204,26 +204,25 @@ struct LinDev {
   int32_t rows, cols, d0, d1, nmats;
   int32_t red_rows;                // 1: reduce over rows (weights E_x); 0: over columns (E_y)
   int32_t lines;                   // entries of each folded vector
-  int32_t nblk;                    // partial-sum blocks per matrix (LIN_DOT lines each)
+  int32_t nblk;                    // inner sums per matrix: ceil(lines / 2^s), s = ceil(d_lines / 2)
   uint64_t seed;
   Fr coeffs[VL_LIN_MAX];           // canonical
   uint8_t binds[VL_LIN_MAX][32];
   uint32_t S[8];                   // transcript state after the squeezes (big-endian words)
   Fr corr;                         // 2^15 . sum of the reduced side's eq table (Montgomery)
-  Fr* fac;                         // eq factors: [lo_x 256 | hi_x 256 | lo_y 256 | hi_y 256]
+  Fr* fac;                         // eq factors: [lo_x 256 | hi_x 256 | lo_y 256 | hi_y 256]; lo of the
+                                   //   reduced side double-Montgomery, all others Montgomery
   uint32_t* w8;                    // reduced side's eq table as fp16 bytes (fold weights)
-  Fr* el;                          // lines side's eq table (Montgomery)
   Fr* f;                           // one segment per tile: nmats x lines, M_q~ folded (Montgomery)
   unsigned long long* acc;         // several segments: nmats x lines x 8 column sums
-  Fr* part;                        // nmats x nblk partial dot products (Montgomery)
+  Fr* part;                        // nmats x nblk inner sums (Montgomery)
   ProofScratch* scr;               // status (the fold's DevProof points here)
 };
-static constexpr int LIN_DOT = 1024;
 // Host helpers of the engine shared with the linear prover.
 bool encode_tc_operand(const void* base, int64_t rows, int64_t cols, int64_t ld, int32_t mode, void* map);
-void set_last_error(const char* msg);  // lines per partial-sum block
-// Batches: one LinDev per proof; eq chunks as EqItem {proof, side 1 =
-// reduced table / 0 = lines table, i0, i1}.
+void set_last_error(const char* msg);
+// Batches: one LinDev per proof; chunks of the reduced side's eq table as
+// EqItem {proof, side (unused), i0, i1}.
 cudaError_t launch_linear_start(LinDev* Ls, int nproofs, const EqItem* items, int nitems, cudaStream_t st);
 cudaError_t launch_linear_finish(LinDev* Ls, int nproofs, int max_nblk, int max_nmats, vl_lin_proof* out,
                                  cudaStream_t st);

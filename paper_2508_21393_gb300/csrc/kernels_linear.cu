@@ -1,15 +1,19 @@
 // Linear zkMat: sum_q c_q M_q = 0 by MLE linearity (Sec. IV; Eq. eq:MLE).
 //
 // M~(x, y) = sum_i sum_j eq(x, i) M[i, j] eq(y, j) is computed as a fold
-// over one dimension followed by a dot product over the other:
+// over one dimension (the shorter, "reduced") followed by a dot product over
+// the other ("lines"):
 //   start:  per proof, transcript start over the statement, squeezes of x
-//           (d0) and y (d1), the eq factor tables of both, the fold's offset
-//           correction (closed form); then, in chunks, the reduced side's eq
-//           table as the tensor-core fold's fp16 byte table and the lines
-//           side's in Montgomery form;
+//           (d0) and y (d1), the eq factor tables of both sides, the fold's
+//           offset correction (closed form, in a warp of its own); then, in
+//           chunks, the reduced side's eq table as the tensor-core fold's
+//           fp16 byte table;
 //   (the tensor-core fold writes f_q = the reduced vector of every matrix)
-//   finish: e_q = sum_w f_q[w] E_lines[w] in blocks of LIN_DOT lines, then
-//           the partial sums, the absorb of 'e' and the proof.
+//   finish: the lines side's eq table is never formed: with
+//           E[w] = hi[w >> s] . lo[w mod 2^s],
+//             e_q = sum_j hi[j] . (sum_l f_q[j 2^s + l] . lo[l]),
+//           one warp per inner sum (one Montgomery product per line), then
+//           per proof the outer sums, the absorb of 'e' and the proof.
 #include "prologue_dev.cuh"
 
 namespace vl {
@@ -18,6 +22,24 @@ namespace {
 
 constexpr uint8_t LBL_X = 'x', LBL_Y = 'y', LBL_E = 'e';
 constexpr int LIN_THREADS = 256;
+constexpr int LIN_FAC_THREADS = LIN_THREADS - 32;  // the last warp computes the correction
+
+// Factor entry j of one side (lo entries first): a product of eq factors,
+// starting from 1 in double-Montgomery (lo of the reduced side) or
+// Montgomery form (everything else).
+__device__ Fr lin_factor(const Fr* x, int d, int j, bool lo_double, bool* is_lo, int* idx, int size) {
+  const int s = (d + 1) >> 1, dh = d - s, nlo = 1 << s;
+  *is_lo = j < nlo;
+  const int jj = *is_lo ? j : j - nlo, nv = *is_lo ? s : dh, base = *is_lo ? dh : 0;
+  *idx = jj;
+  (void)size;
+  Fr acc = (*is_lo && lo_double) ? fr_r2() : fr_r1();
+  for (int t = 0; t < nv; t++) {
+    const Fr& xt = x[base + t];
+    acc = mont_mul_ni(acc, ((jj >> (nv - 1 - t)) & 1) ? xt : fr_sub(fr_r1(), xt));
+  }
+  return acc;
+}
 
 // One block per proof.
 __global__ void __launch_bounds__(LIN_THREADS) lin_start_kernel(LinDev* Ls) {
@@ -36,70 +58,93 @@ __global__ void __launch_bounds__(LIN_THREADS) lin_start_kernel(LinDev* Ls) {
   squeeze_dev(S0, LBL_X, L->d0, xs, S1, dig);
   squeeze_dev(S1, LBL_Y, L->d1, ys, S2, dig);
   if (tid < 8) L->S[tid] = S2[tid];
-  eq_factors(xs, L->d0, L->rows, L->fac, L->fac + EQ_FAC);
-  eq_factors(ys, L->d1, L->cols, L->fac + 2 * EQ_FAC, L->fac + 3 * EQ_FAC);
-  if (tid == 0) {
-    const Fr sum = L->red_rows ? eq_prefix_sum(xs, L->d0, L->rows) : eq_prefix_sum(ys, L->d1, L->cols);
+  const bool rr = L->red_rows != 0;
+  if (tid < LIN_FAC_THREADS) {
+    // Both sides' factor tables in one loop: [x lo | x hi | y lo | y hi].
+    const int sx = (L->d0 + 1) >> 1, sy = (L->d1 + 1) >> 1;
+    const int nx = (1 << sx) + ((L->rows + (1 << sx) - 1) >> sx);
+    const int ny = (1 << sy) + ((L->cols + (1 << sy) - 1) >> sy);
+    for (int j = tid; j < nx + ny; j += LIN_FAC_THREADS) {
+      const bool xside = j < nx;
+      bool is_lo;
+      int idx;
+      const Fr v = xside ? lin_factor(xs, L->d0, j, rr, &is_lo, &idx, L->rows)
+                         : lin_factor(ys, L->d1, j - nx, !rr, &is_lo, &idx, L->cols);
+      L->fac[(xside ? 0 : 2 * EQ_FAC) + (is_lo ? 0 : EQ_FAC) + idx] = v;
+    }
+  } else if (tid == LIN_FAC_THREADS) {
+    const Fr sum = rr ? eq_prefix_sum(xs, L->d0, L->rows) : eq_prefix_sum(ys, L->d1, L->cols);
     L->corr = mont_mul_ni(sum, to_mont_ni(fr_small(1u << 15)));
     L->scr->status = VL_OK;
   }
 }
 
 // Entries [i0, i1) of one proof's reduced-side table (fp16 bytes, zero up
-// to a multiple of 128 entries) or lines-side table (Montgomery).
+// to a multiple of 128 entries).
 __global__ void __launch_bounds__(LIN_THREADS) lin_eq_kernel(const LinDev* Ls, const EqItem* items) {
   const EqItem it = items[blockIdx.x];
   const LinDev* L = Ls + it.proof;
-  const bool red = it.side != 0;
-  const bool xside = red == (L->red_rows != 0);
+  const bool xside = L->red_rows != 0;
   const int d = xside ? L->d0 : L->d1, size = xside ? L->rows : L->cols;
   const int s = (d + 1) >> 1, mask = (1 << s) - 1;
   const Fr* lo = L->fac + (xside ? 0 : 2 * EQ_FAC);
   const Fr* hi = lo + EQ_FAC;
   for (int i = it.i0 + threadIdx.x; i < it.i1; i += blockDim.x) {
     const Fr e = i < size ? mont_mul_ni(hi[i >> s], lo[i & mask]) : fr_zero();  // eq . R^2
-    if (red) store_w8(L->w8, i, e);
-    else L->el[i] = mont_mul_ni(e, fr_small(1));  // eq . R
+    store_w8(L->w8, i, e);
   }
 }
 
-// Block (b, q, proof): sum over lines [b LIN_DOT, (b + 1) LIN_DOT) of
-// f_q[w] E[w]; blocks past the proof's matrices or lines return at once.
+// Warp w of block (b, q, proof) sums inner block j = 8 b + w of matrix q:
+// part[q][j] = sum_l f_q[j 2^s + l] . lo[l] (Montgomery; f from the
+// accumulators when the fold ran in several segments).
 __global__ void __launch_bounds__(LIN_THREADS) lin_dot_kernel(LinDev* Ls) {
-  __shared__ Fr red[LIN_THREADS / 32];
   LinDev* L = Ls + blockIdx.z;
-  const int q = blockIdx.y, b = blockIdx.x, lines = L->lines;
-  if (q >= L->nmats || b >= L->nblk) return;
-  const int w1 = min(lines, (b + 1) * LIN_DOT);
+  const int q = blockIdx.y, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (LIN_THREADS / 32) + (threadIdx.x >> 5);
+  if (q >= L->nmats || j >= L->nblk) return;
+  const bool xside = L->red_rows == 0;  // the lines side
+  const int d = xside ? L->d0 : L->d1, lines = L->lines;
+  const int s = (d + 1) >> 1, hb = 1 << s;
+  const Fr* lo = L->fac + (xside ? 0 : 2 * EQ_FAC);
   const Fr corr = L->corr;
-  Fr acc[1] = {fr_zero()};
-  for (int w = b * LIN_DOT + threadIdx.x; w < w1; w += blockDim.x) {
+  // f_q[w] (Montgomery), from the accumulators when the fold ran in several segments
+  auto load_f = [&](int w) {
     const size_t i = (size_t)q * lines + w;
-    Fr fw;
-    if (L->acc) {
-      U64x8 a;
+    if (!L->acc) return L->f[i];
+    U64x8 a;
 #pragma unroll
-      for (int l = 0; l < 8; l++) a.v[l] = L->acc[i * 8 + l];
-      fw = fr_sub(redc_columns_ni(a), corr);
-    } else {
-      fw = L->f[i];
-    }
-    acc[0] = fr_add(acc[0], mont_mul_ni(fw, L->el[w]));
+    for (int l = 0; l < 8; l++) a.v[l] = L->acc[i * 8 + l];
+    return fr_sub(redc_columns_ni(a), corr);
+  };
+  Fr acc = fr_zero();
+  const int w1 = min(lines, (j + 1) * hb);
+  int w = j * hb + lane;
+  // Two independent inline products per step: the carry chains interleave.
+  for (; w + 32 < w1; w += 64) {
+    const Fr f0 = load_f(w), f1 = load_f(w + 32);
+    const Fr p0 = mont_mul(f0, lo[w & (hb - 1)]), p1 = mont_mul(f1, lo[(w + 32) & (hb - 1)]);
+    acc = fr_add(acc, fr_add(p0, p1));
   }
-  block_sum_fr<1>(acc, red);
-  if (threadIdx.x == 0) L->part[(size_t)q * L->nblk + b] = acc[0];
+  if (w < w1) acc = fr_add(acc, mont_mul_ni(load_f(w), lo[w & (hb - 1)]));
+  acc = warp_sum_fr(acc);
+  if (lane == 0) L->part[(size_t)q * L->nblk + j] = acc;
 }
 
-// One block per proof.
+// One block per proof: e_q = sum_j part[q][j] . hi[j], absorb, proof.
 __global__ void __launch_bounds__(LIN_THREADS) lin_finish_kernel(const LinDev* Ls, vl_lin_proof* outs) {
+  __shared__ Fr red[LIN_THREADS / 32];
   __shared__ Fr ev[VL_LIN_MAX];
   const LinDev* L = Ls + blockIdx.x;
   vl_lin_proof* out = outs + blockIdx.x;
   const int tid = threadIdx.x, nm = L->nmats;
-  if (tid < nm) {
-    Fr s = fr_zero();
-    for (int b = 0; b < L->nblk; b++) s = fr_add(s, L->part[(size_t)tid * L->nblk + b]);
-    ev[tid] = from_mont_ni(s);
+  const Fr* hi = L->fac + (L->red_rows ? 2 * EQ_FAC : 0) + EQ_FAC;  // the lines side's outer factors
+  for (int q = 0; q < nm; q++) {
+    Fr acc[1] = {fr_zero()};
+    for (int j = tid; j < L->nblk; j += blockDim.x)
+      acc[0] = fr_add(acc[0], mont_mul_ni(L->part[(size_t)q * L->nblk + j], hi[j]));
+    block_sum_fr<1>(acc, red);
+    if (tid == 0) ev[q] = from_mont_ni(acc[0]);
   }
   __syncthreads();
   if (tid == 0) {
@@ -128,7 +173,8 @@ cudaError_t launch_linear_start(LinDev* Ls, int nproofs, const EqItem* items, in
 
 cudaError_t launch_linear_finish(LinDev* Ls, int nproofs, int max_nblk, int max_nmats, vl_lin_proof* out,
                                  cudaStream_t st) {
-  lin_dot_kernel<<<dim3(max_nblk, max_nmats, nproofs), LIN_THREADS, 0, st>>>(Ls);
+  const int bx = (max_nblk + LIN_THREADS / 32 - 1) / (LIN_THREADS / 32);
+  lin_dot_kernel<<<dim3(bx, max_nmats, nproofs), LIN_THREADS, 0, st>>>(Ls);
   lin_finish_kernel<<<nproofs, LIN_THREADS, 0, st>>>(Ls, out);
   return cudaGetLastError();
 }

@@ -52,7 +52,7 @@ struct LinShape {
 
 // Workspace offsets of one proof's buffers.
 struct LinBufs {
-  size_t fac = 0, w8 = 0, el = 0, f = 0, part = 0;
+  size_t fac = 0, w8 = 0, f = 0, part = 0;
 };
 
 struct LinLayout {
@@ -106,7 +106,9 @@ int lin_shape(const vl_lin_job& J, LinShape* S) {
   S->seg = ((S->red + split - 1) / split + TC_KS - 1) / TC_KS * TC_KS;
   S->nsplit = (S->red + S->seg - 1) / S->seg;
   S->ntiles = J.nmats * ntl * S->nsplit;
-  S->nblk = (S->lines + LIN_DOT - 1) / LIN_DOT;
+  // inner sums of the lines side: blocks of 2^s lines, s = ceil(d / 2)
+  const int dl = S->red_rows ? S->d1 : S->d0, sl = (dl + 1) >> 1;
+  S->nblk = (S->lines + (1 << sl) - 1) >> sl;
   return VL_OK;
 }
 
@@ -123,11 +125,9 @@ int lin_layout(const vl_lin_job* jobs, int32_t njobs, LinLayout* L) {
     L->ntiles += S.ntiles;
     L->max_nblk = std::max(L->max_nblk, S.nblk);
     L->max_q = std::max(L->max_q, S.q);
-    // eq-table chunks: the reduced side (padded to whole stages), then the lines side
+    // chunks of the reduced side's eq table (padded to whole stages)
     const int rend = (S.red + TC_KS - 1) / TC_KS * TC_KS;
     for (int i0 = 0; i0 < rend; i0 += EQ_CHUNK) L->items.push_back(EqItem{i, 1, i0, std::min(rend, i0 + EQ_CHUNK)});
-    for (int i0 = 0; i0 < S.lines; i0 += EQ_CHUNK)
-      L->items.push_back(EqItem{i, 0, i0, std::min(S.lines, i0 + EQ_CHUNK)});
   }
   size_t off = 0;
   auto take = [&off](size_t bytes) {
@@ -147,7 +147,6 @@ int lin_layout(const vl_lin_job* jobs, int32_t njobs, LinLayout* L) {
     LinBufs& b = L->buf[i];
     b.fac = take(sizeof(Fr) * 4 * EQ_FAC);
     b.w8 = take((size_t)8192 * ((S.red + TC_KS - 1) / TC_KS));
-    b.el = take(sizeof(Fr) * (size_t)S.lines);
     // f (one segment per tile) or the column-sum accumulators (several)
     b.f = take((S.nsplit == 1 ? sizeof(Fr) : 8 * sizeof(unsigned long long)) * (size_t)S.q * S.lines);
     b.part = take(sizeof(Fr) * (size_t)S.q * S.nblk);
@@ -211,7 +210,6 @@ int lin_bind(vl_lin_plan* P, uint8_t* ws, cudaStream_t st) {
     LinDev& L = P->Ls[i];
     L.fac = reinterpret_cast<Fr*>(ws + b.fac);
     L.w8 = reinterpret_cast<uint32_t*>(ws + b.w8);
-    L.el = reinterpret_cast<Fr*>(ws + b.el);
     L.f = S.nsplit == 1 ? reinterpret_cast<Fr*>(ws + b.f) : nullptr;
     L.acc = S.nsplit == 1 ? nullptr : reinterpret_cast<unsigned long long*>(ws + b.f);
     L.part = reinterpret_cast<Fr*>(ws + b.part);

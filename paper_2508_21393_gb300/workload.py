@@ -153,6 +153,33 @@ def update_statements(t, seed=GLOBAL_SEED):
     return out
 
 
+ROUTE_PRODUCTS = ("F1", "F2", "F3", "B1", "B4", "B5", "R1", "R2", "R3")
+
+
+def paper_route_products(t, seed=GLOBAL_SEED):
+    """The products of one projection along the paper's backward route
+    (Eq. eq:grad_wl, eq:grad_abl), which forms the full d x k gradient of the
+    adapted weight W' = W + A.B and derives the LoRA gradients from it:
+        R1 dW' = X^T.dY (d x n x k),  dWr = rescale(dW')
+        R2 dA  = dWr.B^T (d x k x r)
+        R3 dB  = A^T.dWr (r x d x k)
+    replacing B2 and B3 of the eight-product set; F1-F3, B1, B4, B5 stay (the
+    input gradient needs dH).  Returns (products, dWr)."""
+    X, A, B, dY = (t[x] for x in ("X", "A", "B", "dY"))
+    dWr = rescale(exact_matmul(X.T, dY))
+    base = {j["name"].rsplit(".", 1)[1]: j for j in projection_products(t, seed)}
+    spec = {"R1": (X, dY, 1, 0), "R2": (dWr, B, 0, 1), "R3": (A, dWr, 1, 0)}
+    out = []
+    for name in ROUTE_PRODUCTS:
+        if name in base:
+            out.append(base[name])
+            continue
+        P, Q, tp, tq = spec[name]
+        out.append({"P": P, "Q": Q, "tp": tp, "tq": tq, "name": f"L{t['layer']}.{t['proj']}.{name}",
+                    "seed": proof_seed(seed, t["layer"], t["proj"], name)})
+    return out, dWr
+
+
 def op_shape(job):
     P, Q = job["P"], job["Q"]
     m, k = (P.shape[1], P.shape[0]) if job["tp"] else P.shape

@@ -414,3 +414,22 @@ def _opt_variants():
         o.fold_engine, o.persistent, o.tc_seg = eng, pers, seg
         out.append(o)
     return out
+
+
+def test_paper_backward_route_products():
+    """The paper's backward route (full dW' = X^T.dY, then dA = dW'.B^T and
+    dB = A^T.dW'), nine products of one projection, byte-equal to the oracle
+    and verified by the library's host verifier against the claimed products."""
+    t = W.lora_projection(W.GLOBAL_SEED, 3, "v", 48, 160, 96, 8)
+    jobs, dWr = W.paper_route_products(t)
+    assert [j["name"].rsplit(".", 1)[1] for j in jobs] == list(W.ROUTE_PRODUCTS)
+    assert dWr.shape == (160, 96)
+    dj, keep = _dev_jobs(jobs)
+    nb = B.vl_workspace_bytes(dj)
+    ws = _ws(nb)
+    proofs = B.vl_prove_batch(dj, ws.data_ptr(), nb)
+    for j, pf in zip(jobs, proofs):
+        ref = oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes()
+        assert B.proof_bytes(pf) == ref, j["name"]
+        C = W.claimed_product(j)
+        assert B.vl_verify_matmul(B.mat(j["P"], j["tp"]), B.mat(j["Q"], j["tq"]), B.mat(C), B.fs_init(j["seed"]), pf)

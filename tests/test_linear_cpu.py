@@ -199,3 +199,23 @@ def test_plan_create_validation(L):
         B.LinPlan([j])
     with pytest.raises(B.VLError):
         B.LinPlan([_host_job([M[0], _rand(rng, (20, 31))], [1, 1])])
+
+
+def test_paper_route_products_shapes_and_claims():
+    """The paper's backward route: R1 is the full weight gradient X^T.dY
+    (d x k), R2 and R3 take its rescaled form to the LoRA gradients
+    (d x r and r x k), the same shapes as B3 (dA) and B2 (dB) of the
+    eight-product set; a tiny claimed product is checked entry by entry."""
+    t = W.lora_projection(W.GLOBAL_SEED, 0, "q", 8, 12, 10, 4)
+    jobs, dWr = W.paper_route_products(t)
+    shapes = {j["name"].rsplit(".", 1)[1]: W.op_shape(j) for j in jobs}
+    assert shapes["R1"] == (12, 8, 10) and shapes["R2"] == (12, 10, 4) and shapes["R3"] == (4, 12, 10)
+    base = {j["name"].rsplit(".", 1)[1]: W.op_shape(j) for j in W.projection_products(t)}
+    assert (shapes["R2"][0], shapes["R2"][2]) == (base["B3"][0], base["B3"][2])  # dA: d x r
+    assert (shapes["R3"][0], shapes["R3"][2]) == (base["B2"][0], base["B2"][2])  # dB: r x k
+    X, dY = t["X"].astype(np.int64), t["dY"].astype(np.int64)
+    R1 = W.claimed_product(jobs[6])
+    for i in range(12):
+        for j in range(10):
+            assert R1[i, j] == sum(X[s, i] * dY[s, j] for s in range(8))
+    assert np.array_equal(dWr, W.rescale(R1))
