@@ -6,7 +6,8 @@ C = op(P) . op(Q) over the BLS12-381 scalar field (Sec. II-B, II-C, Eq.
 eq:MLE and eq:zk-mle-matmul), with a SHA-256 Fiat-Shamir transcript (Sec. IV,
 footnote on Fiat-Shamir), and the linear zkMat proofs of matrix additions
 (sum_q c_q M_q = 0 by MLE linearity; the parameter update of Eq.
-eq:grad_update_ab is one).  It uses Python integers and ``hashlib`` only,
+eq:grad_update_ab is one), and the lookup-argument sumcheck of Protocol 1
+(Eq. eq:lookup-sumcheck) for range tables.  It uses Python integers and ``hashlib`` only,
 with NumPy object arrays as the one library matmul step.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
@@ -26,10 +27,12 @@ from .mle import eq_table, eq_value, mle_eval_bruteforce, mle_eval_matrix, fold_
 from .sumcheck import Proof, prove_matmul, verify_matmul, round_poly_eval
 from .encode import encode_montgomery, limbs_le32
 from .linear import LinearProof, prove_linear, verify_linear
+from .lookup import LookupProof, prove_lookup, verify_lookup, cubic_eval
 
 __all__ = [
     "R_MOD", "fr", "fr_add", "fr_sub", "fr_mul", "fr_inv", "fr_to_bytes", "fr_from_bytes",
     "Transcript", "eq_table", "eq_value", "mle_eval_bruteforce", "mle_eval_matrix",
     "fold_rows", "fold_cols", "Proof", "prove_matmul", "verify_matmul", "round_poly_eval",
     "encode_montgomery", "limbs_le32", "LinearProof", "prove_linear", "verify_linear",
+    "LookupProof", "prove_lookup", "verify_lookup", "cubic_eval",
 ]
