@@ -52,6 +52,7 @@ extern "C" {
 #define VL_ECUDA 4    /* a CUDA runtime call failed                          */
 #define VL_ETIMEOUT 5 /* a bounded device-side wait gave up                  */
 #define VL_REJECT 6   /* vl_verify_matmul: the proof does not verify         */
+#define VL_ELOOKUP 7  /* vl_prove_lookup: a value lies outside its table     */
 
 /* Element types of a vl_mat. */
 #define VL_I16 1     /* int16 fixed-point, 2 bytes                            */
@@ -325,6 +326,68 @@ void vl_lin_plan_destroy(vl_lin_plan* plan);
 /* Verify one proof on the host against host operands (int16, int64 or
  * Montgomery): VL_OK (accept), VL_REJECT, or an argument error. */
 int32_t vl_verify_linear(const vl_lin_job* job, const vl_lin_proof* proof);
+
+/* ---------------------------------------------------------------------------
+ * Lookup argument (Sec. II, lookup arguments; Protocol 1; Eq.
+ * eq:lookup-sumcheck): a proof that every entry of S lies in the table
+ * T = [t0, t0 + N), N = 2^log2_n (a range check, e.g. of rescale
+ * remainders).  S (n entries, row-major) is padded with t0 to
+ * D = max(N, 2^ceil(log2 n)) entries; with A_k = 1/(beta + S_k),
+ * B_j = 1/(beta + T_j) and multiplicities m_j, a degree-3 sumcheck over the
+ * log2 D variables shows that
+ *   P(k) = alpha A(k) eq(u,k) (S(k) + beta) + A(k)
+ *          + (N/D) (alpha^2 B(j) eq(u_low,j) (T(j) + beta) - B(j) m(j))
+ * (j = k mod N, u_low the last log2 N coordinates of u) sums to
+ * alpha + alpha^2.  Transcript: domain "verilora-gb300/zklookup/v1", seed
+ * u64le, n, log2 D, log2 N u32le, t0 i64le, bind; squeeze beta ('b'),
+ * alpha ('a'), u ('u', log2 D); per round absorb g(0), g(2), g(3) ('g') and
+ * squeeze r ('r'); absorb a_r, s_r, b_r, m_r ('f').  The verifier
+ * recomputes A, B, m from S and T in place of commitment openings.
+ * ------------------------------------------------------------------------- */
+#define VL_LOOKUP_MAX_LOG_D 24
+#define VL_LOOKUP_MAX_LOG_N 16
+
+typedef struct vl_lookup_job {
+  vl_mat S;          /* int16 values, trans 0, read in row-major order      */
+  int64_t t0;        /* first table value                                    */
+  int32_t log2_n;    /* table size 2^log2_n, 0 .. VL_LOOKUP_MAX_LOG_N        */
+  int32_t reserved;  /* must be 0                                            */
+  uint64_t seed;
+  uint8_t bind[32];  /* commitment stand-in for S (zeros when unused)        */
+} vl_lookup_job;
+
+typedef struct vl_lookup_proof {
+  int32_t n, log2_d, log2_n, status;
+  int64_t t0;
+  vl_fr g[VL_LOOKUP_MAX_LOG_D][4]; /* g_t(0), g_t(1), g_t(2), g_t(3), canonical */
+  vl_fr a_r, s_r, b_r, m_r;        /* A~(r), S~(r), B~(r_low), m~(r_low)        */
+  uint8_t state[32];
+} vl_lookup_proof;
+
+typedef struct vl_lookup_plan vl_lookup_plan;
+/* Device workspace the batch needs (0 on invalid arguments: S not int16,
+ * transposed or empty; n > 2^VL_LOOKUP_MAX_LOG_D; log2_n out of range;
+ * reserved != 0). */
+size_t vl_lookup_workspace_bytes(const vl_lookup_job* jobs, int32_t njobs);
+/* Plans, as for linear proofs: the statements are copied (S's data is read
+ * at every run; host S is copied into the workspace at every run), tables
+ * are bound once per workspace; out_space VL_DEVICE runs asynchronously
+ * (each proof's status field reports VL_OK or VL_ELOOKUP), VL_HOST
+ * synchronises `stream` and returns the first non-OK status. */
+int32_t vl_lookup_plan_create(const vl_lookup_job* jobs, int32_t njobs, vl_lookup_plan** plan);
+size_t vl_lookup_plan_workspace_bytes(const vl_lookup_plan* plan);
+int32_t vl_lookup_plan_run(vl_lookup_plan* plan, void* workspace, size_t workspace_bytes, vl_lookup_proof* out,
+                           int32_t out_space, void* stream);
+/* Device times (ms) of the last run: ms[0] setup (transcript start, tables,
+ * multiplicities, inverses), ms[1] the sumcheck rounds, ms[2] the finish. */
+int32_t vl_lookup_plan_phase_ms(vl_lookup_plan* plan, float ms[3]);
+void vl_lookup_plan_destroy(vl_lookup_plan* plan);
+/* One-shot: plan, run with host output, destroy. */
+int32_t vl_prove_lookup(const vl_lookup_job* jobs, int32_t njobs, void* workspace, size_t workspace_bytes,
+                        vl_lookup_proof* out, void* stream);
+/* Host verifier against host S (int16 or int64): VL_OK, VL_REJECT or an
+ * argument error. */
+int32_t vl_verify_lookup(const vl_lookup_job* job, const vl_lookup_proof* proof);
 
 /* Autotuner (the paper has no counterpart): picks the launch and tile
  * options for `jobs` by timing candidate plans on the caller's workspace and

@@ -18,7 +18,7 @@ import numpy as np
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "_lib", "libverilora.so")
 
-VL_OK, VL_EINVAL, VL_ESHAPE, VL_ENOMEM, VL_ECUDA, VL_ETIMEOUT, VL_REJECT = range(7)
+VL_OK, VL_EINVAL, VL_ESHAPE, VL_ENOMEM, VL_ECUDA, VL_ETIMEOUT, VL_REJECT, VL_ELOOKUP = range(8)
 VL_I16, VL_I64, VL_FR_MONT = 1, 2, 3
 VL_DEVICE, VL_HOST = 0, 1
 VL_MAX_ROUNDS = 24
@@ -31,9 +31,13 @@ EXPORTS = ("vl_version", "vl_strerror", "vl_last_error", "vl_workspace_bytes", "
            "vl_server_create", "vl_server_submit", "vl_server_poll", "vl_server_stats_get", "vl_server_destroy",
            "vl_autotune", "vl_autotune_clear", "vl_linear_workspace_bytes", "vl_prove_linear", "vl_verify_linear",
            "vl_lin_plan_create", "vl_lin_plan_workspace_bytes", "vl_lin_plan_run", "vl_lin_plan_phase_ms",
-           "vl_lin_plan_destroy")
+           "vl_lin_plan_destroy", "vl_lookup_workspace_bytes", "vl_lookup_plan_create",
+           "vl_lookup_plan_workspace_bytes", "vl_lookup_plan_run", "vl_lookup_plan_phase_ms",
+           "vl_lookup_plan_destroy", "vl_prove_lookup", "vl_verify_lookup")
 VL_NOALLOC_SCRATCH_BYTES = 8 << 20
 VL_LIN_MAX = 16
+VL_LOOKUP_MAX_LOG_D = 24
+VL_LOOKUP_MAX_LOG_N = 16
 R_MOD = 0x73EDA753299D7D483339D80809A1D80553BDA402FFFE5BFEFFFFFFFF00000001
 
 
@@ -72,6 +76,18 @@ class vl_lin_proof(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int32), ("cols", ctypes.c_int32), ("d0", ctypes.c_int32), ("d1", ctypes.c_int32),
                 ("nmats", ctypes.c_int32), ("status", ctypes.c_int32), ("evals", vl_fr * VL_LIN_MAX),
                 ("state", ctypes.c_uint8 * 32)]
+
+
+class vl_lookup_job(ctypes.Structure):
+    _fields_ = [("S", vl_mat), ("t0", ctypes.c_int64), ("log2_n", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("bind", ctypes.c_uint8 * 32)]
+
+
+class vl_lookup_proof(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("log2_d", ctypes.c_int32), ("log2_n", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("t0", ctypes.c_int64),
+                ("g", (vl_fr * 4) * VL_LOOKUP_MAX_LOG_D), ("a_r", vl_fr), ("s_r", vl_fr), ("b_r", vl_fr),
+                ("m_r", vl_fr), ("state", ctypes.c_uint8 * 32)]
 
 
 class vl_job(ctypes.Structure):
@@ -184,6 +200,24 @@ def lib():
     L.vl_lin_plan_phase_ms.restype = ctypes.c_int32
     L.vl_lin_plan_destroy.argtypes = [ctypes.c_void_p]
     L.vl_lin_plan_destroy.restype = None
+    L.vl_lookup_workspace_bytes.argtypes = [P(vl_lookup_job), ctypes.c_int32]
+    L.vl_lookup_workspace_bytes.restype = ctypes.c_size_t
+    L.vl_lookup_plan_create.argtypes = [P(vl_lookup_job), ctypes.c_int32, P(ctypes.c_void_p)]
+    L.vl_lookup_plan_create.restype = ctypes.c_int32
+    L.vl_lookup_plan_workspace_bytes.argtypes = [ctypes.c_void_p]
+    L.vl_lookup_plan_workspace_bytes.restype = ctypes.c_size_t
+    L.vl_lookup_plan_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                     ctypes.c_int32, ctypes.c_void_p]
+    L.vl_lookup_plan_run.restype = ctypes.c_int32
+    L.vl_lookup_plan_phase_ms.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]
+    L.vl_lookup_plan_phase_ms.restype = ctypes.c_int32
+    L.vl_lookup_plan_destroy.argtypes = [ctypes.c_void_p]
+    L.vl_lookup_plan_destroy.restype = None
+    L.vl_prove_lookup.argtypes = [P(vl_lookup_job), ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                                  P(vl_lookup_proof), ctypes.c_void_p]
+    L.vl_prove_lookup.restype = ctypes.c_int32
+    L.vl_verify_lookup.argtypes = [P(vl_lookup_job), P(vl_lookup_proof)]
+    L.vl_verify_lookup.restype = ctypes.c_int32
     L.vl_verify_linear.restype = ctypes.c_int32
     L.vl_encode.restype = ctypes.c_int32
     _lib = L
@@ -323,6 +357,37 @@ def lin_jobs_array(jobs):
         arr[i] = j
     arr._keep = list(jobs)  # the copies point at the jobs' arrays
     return arr
+
+
+def lookup_job(S, t0, log2_n, seed=0, bind=None):
+    """vl_lookup_job: every entry of S (a vl_mat of int16, row-major) in
+    [t0, t0 + 2^log2_n)."""
+    j = vl_lookup_job()
+    j.S = S
+    j.t0 = int(t0)
+    j.log2_n = int(log2_n)
+    j.reserved = 0
+    j.seed = int(seed) & ((1 << 64) - 1)
+    b = bytes(32) if bind is None else bytes(bind)
+    for i in range(32):
+        j.bind[i] = b[i]
+    return j
+
+
+def lookup_jobs_array(jobs):
+    arr = (vl_lookup_job * len(jobs))()
+    for i, j in enumerate(jobs):
+        arr[i] = j
+    return arr
+
+
+def lookup_proof_bytes(p):
+    """Lookup proof serialisation (same layout as the oracle's LookupProof.to_bytes)."""
+    out = b"".join(int(x).to_bytes(4, "little") for x in (p.n, p.log2_d, p.log2_n))
+    out += int(p.t0).to_bytes(8, "little", signed=True)
+    for t in range(p.log2_d):
+        out += b"".join(bytes(p.g[t][q]) for q in range(4))
+    return out + bytes(p.a_r) + bytes(p.s_r) + bytes(p.b_r) + bytes(p.m_r) + bytes(p.state)
 
 
 def _stream_ptr(stream):
@@ -527,6 +592,60 @@ class LinPlan:
     def destroy(self):
         if self.ptr:
             lib().vl_lin_plan_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p()
+
+
+def vl_lookup_workspace_bytes(jobs):
+    return lib().vl_lookup_workspace_bytes(lookup_jobs_array(jobs), len(jobs))
+
+
+def vl_prove_lookup(jobs, workspace, workspace_bytes, stream=None):
+    """Prove a batch of range lookups; returns the ctypes array of host proofs."""
+    out = (vl_lookup_proof * len(jobs))()
+    _check(lib().vl_prove_lookup(lookup_jobs_array(jobs), len(jobs), workspace, workspace_bytes, out,
+                                 _stream_ptr(stream)), "vl_prove_lookup")
+    return out
+
+
+def vl_verify_lookup(job, proof):
+    """Host verifier of a lookup proof: True / False; raises on input errors."""
+    code = lib().vl_verify_lookup(ctypes.byref(job), ctypes.byref(proof))
+    if code == VL_REJECT:
+        return False
+    _check(code, "vl_verify_lookup")
+    return True
+
+
+class LookupPlan:
+    """A vl_lookup_plan."""
+
+    def __init__(self, jobs):
+        self.arr = lookup_jobs_array(jobs)
+        self.ptr = ctypes.c_void_p()
+        _check(lib().vl_lookup_plan_create(self.arr, len(jobs), ctypes.byref(self.ptr)), "vl_lookup_plan_create")
+        self.n = len(jobs)
+
+    def workspace_bytes(self):
+        return lib().vl_lookup_plan_workspace_bytes(self.ptr)
+
+    def run(self, workspace, workspace_bytes, out=None, out_space=VL_HOST, stream=None):
+        if out_space == VL_HOST:
+            res = (vl_lookup_proof * self.n)()
+            ptr = ctypes.addressof(res)
+        else:
+            res, ptr = None, int(out)
+        _check(lib().vl_lookup_plan_run(self.ptr, workspace, workspace_bytes, ptr, out_space, _stream_ptr(stream)),
+               "vl_lookup_plan_run")
+        return res
+
+    def phase_ms(self):
+        ms = (ctypes.c_float * 3)()
+        _check(lib().vl_lookup_plan_phase_ms(self.ptr, ms), "vl_lookup_plan_phase_ms")
+        return tuple(ms)
+
+    def destroy(self):
+        if self.ptr:
+            lib().vl_lookup_plan_destroy(self.ptr)
             self.ptr = ctypes.c_void_p()
 
 

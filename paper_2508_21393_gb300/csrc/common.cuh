@@ -218,6 +218,48 @@ struct LinDev {
   Fr* part;                        // nmats x nblk inner sums (Montgomery)
   ProofScratch* scr;               // status (the fold's DevProof points here)
 };
+// Lookup argument (kernels_lookup.cu): one LkDev per proof, in the workspace.
+static constexpr int LK_MAX_L = VL_LOOKUP_MAX_LOG_D;
+struct LkDev {
+  int32_t n, L, log2_n, sE;        // entries, log2 D, log2 N, low-block variables of eq(u, .)
+  int64_t t0;
+  uint64_t seed;
+  int64_t rows, cols, ld;          // S as stored (row-major, k = row . cols + col)
+  const int16_t* S;
+  uint8_t bind[32];
+  Fr beta, alpha, c_nd, Cb;        // Montgomery; c_nd = N / D; Cb = alpha^2 X1 - X2 (table side's cube sum)
+  Fr claim, half_t;                // running claim; 2^-t during the high rounds
+  Fr inv2, inv6;                   // 1/2, 1/6 (Montgomery)
+  Fr u[LK_MAX_L], r[LK_MAX_L];     // challenges (Montgomery)
+  uint32_t St[8];                  // transcript state (big-endian words)
+  int32_t pbeg[LK_MAX_L + 1], pend[LK_MAX_L + 1];  // partial-sum slots of each round (1-based)
+  int32_t xbeg, xend;              // slots of the table-side sums X1, X2
+  Fr* lo;                          // eq(u, .) low factors (2^sE, Montgomery)
+  Fr* hi;                          // eq(u, .) high factors (2^(L - sE))
+  Fr* Binv;                        // 1 / (beta + t0 + j), N (gather source, never folded)
+  Fr* Tb;                          // beta + t0 + j, N (gather source)
+  Fr* WB; Fr* WE; Fr* WT; Fr* WM;  // table-side vectors B, eq(u_low, .), T + beta, m (folded in place)
+  Fr* VA; Fr* VE; Fr* VS;          // folded A, eq(u, .), S + beta, D/2 each
+  uint32_t* counts;                // N multiplicities
+  Fr* part;                        // partial sums (12 per slot)
+  ProofScratch* scr;               // status
+};
+// A block of work of one proof: entries or pairs [k0, k1), partial slot.
+struct LkItem {
+  int32_t proof, k0, k1, slot;
+};
+static constexpr int LK_THREADS = 256;
+static constexpr int LK_PAIRS = 1024;     // pairs per round item
+static constexpr int LK_ENTRIES = 1024;   // table entries per table item (one batch inversion)
+static constexpr int LK_HIST = 8192;      // S entries per histogram item
+cudaError_t launch_lookup_setup(LkDev* Ls, int np, const LkItem* fac_items, int nfac, const LkItem* hist_items,
+                                int nhist, const LkItem* tab_items, int ntab, cudaStream_t st);
+// Round t: nhi items of proofs in their high rounds, then nlo items of
+// proofs in their table rounds.
+cudaError_t launch_lookup_round(LkDev* Ls, int np, int t, const LkItem* items, int nhi, int nlo,
+                                vl_lookup_proof* out, cudaStream_t st);
+cudaError_t launch_lookup_finish(LkDev* Ls, int np, vl_lookup_proof* out, cudaStream_t st);
+
 // Host helpers of the engine shared with the linear prover.
 bool encode_tc_operand(const void* base, int64_t rows, int64_t cols, int64_t ld, int32_t mode, void* map);
 void set_last_error(const char* msg);

@@ -876,6 +876,7 @@ const char* vl_strerror(int32_t s) {
     case VL_ECUDA: return "CUDA error";
     case VL_ETIMEOUT: return "device wait timed out";
     case VL_REJECT: return "proof rejected";
+    case VL_ELOOKUP: return "a lookup value lies outside its table";
     default: return "unknown status";
   }
 }

@@ -222,6 +222,74 @@ VL_HD Fr reduce_512(const Fr& lo, const Fr& hi) {
   return fr_add(l, h);
 }
 
+// Inverse of a canonical nonzero a (canonical result), by the binary
+// extended Euclidean algorithm on (a, r): invariants x1.a = u and x2.a = v
+// (mod r); halving keeps them (x/2 mod r = (x + r)/2 for odd x; x + r < 2^256
+// since r < 2^255), subtracting the smaller of u, v from the larger shrinks
+// them until one is 1.  Each step removes at least one bit of u or v, so at
+// most 2 . 256 steps run; the cap only guards a zero input (returns 0).
+VL_HD bool fr_is_one(const Fr& a) {
+  uint32_t acc = a.v[0] ^ 1u;
+  for (int i = 1; i < 8; i++) acc |= a.v[i];
+  return acc == 0;
+}
+VL_HD void fr_half_mod(Fr& x) {  // x <- x / 2 mod r, x < r
+  uint32_t carry = 0;
+  if (x.v[0] & 1u) {
+    uint64_t c = 0;
+    for (int i = 0; i < 8; i++) {
+      c += (uint64_t)x.v[i] + r_limb(i);
+      x.v[i] = (uint32_t)c;
+      c >>= 32;
+    }
+    carry = (uint32_t)c;  // always 0 (x + r < 2^256); kept for the shift
+  }
+  for (int i = 0; i < 7; i++) x.v[i] = (x.v[i] >> 1) | (x.v[i + 1] << 31);
+  x.v[7] = (x.v[7] >> 1) | (carry << 31);
+}
+VL_HD bool fr_geq_raw(const Fr& a, const Fr& b) {
+  for (int i = 7; i >= 0; i--)
+    if (a.v[i] != b.v[i]) return a.v[i] > b.v[i];
+  return true;
+}
+VL_HD Fr fr_sub_raw(const Fr& a, const Fr& b) {  // a - b for a >= b (integers)
+  Fr d;
+  uint64_t borrow = 0;
+  for (int i = 0; i < 8; i++) {
+    const uint64_t x = (uint64_t)a.v[i] - b.v[i] - borrow;
+    d.v[i] = (uint32_t)x;
+    borrow = (x >> 63) & 1u;
+  }
+  return d;
+}
+VL_HD Fr fr_inv_canonical(const Fr& a) {
+  if (fr_is_zero(a)) return fr_zero();
+  Fr u = a, v, x1 = fr_small(1), x2 = fr_zero();
+  for (int i = 0; i < 8; i++) v.v[i] = r_limb(i);
+  for (int step = 0; step < 4 * 256 && !fr_is_one(u) && !fr_is_one(v); step++) {
+    while (!(u.v[0] & 1u)) {
+      for (int i = 0; i < 7; i++) u.v[i] = (u.v[i] >> 1) | (u.v[i + 1] << 31);
+      u.v[7] >>= 1;
+      fr_half_mod(x1);
+    }
+    while (!(v.v[0] & 1u)) {
+      for (int i = 0; i < 7; i++) v.v[i] = (v.v[i] >> 1) | (v.v[i + 1] << 31);
+      v.v[7] >>= 1;
+      fr_half_mod(x2);
+    }
+    if (fr_geq_raw(u, v)) {
+      u = fr_sub_raw(u, v);
+      x1 = fr_sub(x1, x2);
+    } else {
+      v = fr_sub_raw(v, u);
+      x2 = fr_sub(x2, x1);
+    }
+  }
+  return fr_is_one(u) ? x1 : x2;
+}
+// Inverse in Montgomery form (x.R -> x^-1.R): from_mont, canonical inverse, to_mont.
+VL_HD Fr fr_inv_mont(const Fr& a) { return to_mont(fr_inv_canonical(from_mont(a))); }
+
 // Signed integer x (|x| < 2^63) as a canonical field element.
 VL_HD Fr fr_from_i64(int64_t x) {
   uint64_t mag = x < 0 ? (uint64_t)(-(x + 1)) + 1u : (uint64_t)x;

@@ -1,0 +1,472 @@
+// Lookup-argument sumcheck (Sec. II, lookup arguments; Protocol 1; Eq.
+// eq:lookup-sumcheck) for range tables T_j = t0 + j, j < N, over a batch of
+// proofs.
+//
+// The sumcheck runs over k = (i, j) in {0,1}^L, L = log2 D, binding the most
+// significant variable first, on
+//   P(k) = alpha A(k) E(k) S'(k) + A(k) + (N/D)(alpha^2 B(j) Ej(j) T'(j) - B(j) m(j))
+// with A = 1/(beta + S), E = eq(u, .), S' = S + beta, B = 1/(beta + T),
+// Ej = eq(u_low, .), T' = T + beta.  The table side depends on the low
+// log2 N variables only, so in the first L - log2 N rounds its contribution
+// to g_t(X) is the constant 2^-t . Cb, Cb = alpha^2 sum B Ej T' - sum B m;
+// in the last log2 N rounds its four vectors are folded like the others.
+//
+// Launches: start (per proof: transcript, beta, alpha, u, N/D, claim),
+// factors (eq(u, .) as hi x lo factor tables and eq(u_low, .)), histogram
+// (multiplicities, range check), table (batch inversion of beta + T per
+// 1024-entry block, table-side vectors, partial sums of Cb); per round a
+// pass over all proofs' pairs (fold with the previous challenge, then the
+// partial sums of g(0), g(2), g(3)) and a transcript step per proof; finish.
+// A never exists as a vector: its entries are gathered from B by value
+// (A_k = B_{S_k - t0}), and S' from T'.
+#include "prologue_dev.cuh"
+
+namespace vl {
+
+namespace {
+
+constexpr uint8_t LBL_BETA = 'b', LBL_ALPHA = 'a';
+
+__device__ __forceinline__ int lk_table_index(const LkDev& L, int k) {
+  if (k >= L.n) return 0;  // padding entries hold t0
+  const int row = k / (int)L.cols, col = k - row * (int)L.cols;
+  const int64_t v = (int64_t)L.S[(int64_t)row * L.ld + col];
+  const int64_t j = v - L.t0;
+  const int N = 1 << L.log2_n;
+  return j < 0 ? 0 : (j >= N ? N - 1 : (int)j);  // out-of-table values were reported; stay in bounds
+}
+
+// A, E, S' at entry k of the unfolded cube.
+__device__ __forceinline__ void lk_level0(const LkDev& L, int k, Fr& a, Fr& e, Fr& s) {
+  const int j = lk_table_index(L, k);
+  a = L.Binv[j];
+  s = L.Tb[j];
+  e = mont_mul(L.hi[k >> L.sE], L.lo[k & ((1 << L.sE) - 1)]);
+}
+
+__device__ __forceinline__ Fr lk_fold(const Fr& x0, const Fr& x1, const Fr& r) {
+  return fr_add(x0, mont_mul(r, fr_sub(x1, x0)));
+}
+
+// One block per proof.
+__global__ void __launch_bounds__(LK_THREADS) lk_start_kernel(LkDev* Ls) {
+  LkDev* L = Ls + blockIdx.x;
+  __shared__ uint32_t S0[8], S1[8], S2[8], S3[8];
+  __shared__ uint32_t dig[2 * LK_MAX_L + 1][8];
+  __shared__ Fr ch[LK_MAX_L];
+  __shared__ Fr beta_sh, alpha_sh;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    uint8_t b[32];
+    ts_start_lookup(b, L->seed, (uint32_t)L->n, (uint32_t)L->L, (uint32_t)L->log2_n, L->t0, L->bind);
+    for (int i = 0; i < 8; i++)
+      S0[i] = ((uint32_t)b[4 * i] << 24) | ((uint32_t)b[4 * i + 1] << 16) | ((uint32_t)b[4 * i + 2] << 8) | b[4 * i + 3];
+  }
+  __syncthreads();
+  squeeze_dev(S0, LBL_BETA, 1, ch, S1, dig);
+  if (tid == 0) beta_sh = ch[0];
+  __syncthreads();
+  squeeze_dev(S1, LBL_ALPHA, 1, ch, S2, dig);
+  if (tid == 0) alpha_sh = ch[0];
+  __syncthreads();
+  squeeze_dev(S2, LBL_U, L->L, ch, S3, dig);
+  if (tid < L->L) L->u[tid] = ch[tid];
+  if (tid < 8) L->St[tid] = S3[tid];
+  if (tid == 0) {
+    const Fr alpha = alpha_sh;
+    L->beta = beta_sh;
+    L->alpha = alpha;
+    L->claim = fr_add(alpha, mont_mul(alpha, alpha));
+    L->half_t = fr_r1();
+    Fr c = fr_r1();  // N / D = 2^-(L - log2 N)
+    for (int i = 0; i < L->L - L->log2_n; i++) c = mont_mul(c, L->inv2);
+    L->c_nd = c;
+    L->scr->status = VL_OK;
+    const uint32_t pad = (uint32_t)((1 << L->L) - L->n);  // padding entries hold t0: table index 0
+    if (pad) atomicAdd(&L->counts[0], pad);
+  }
+}
+
+// Factor tables: item.slot 0 = lo (2^sE entries over the last sE variables
+// of u), 1 = hi (over the first L - sE), 2 = eq(u_low, .) into WE (over the
+// last log2 N).  Entry j is the product of x or 1 - x per bit (MSB first).
+__global__ void __launch_bounds__(LK_THREADS) lk_factor_kernel(LkDev* Ls, const LkItem* items) {
+  const LkItem it = items[blockIdx.x];
+  LkDev* L = Ls + it.proof;
+  const int nv = it.slot == 0 ? L->sE : it.slot == 1 ? L->L - L->sE : L->log2_n;
+  const int base = it.slot == 1 ? 0 : L->L - nv;
+  Fr* out = it.slot == 0 ? L->lo : it.slot == 1 ? L->hi : L->WE;
+  for (int j = it.k0 + threadIdx.x; j < it.k1; j += blockDim.x) {
+    Fr acc = fr_r1();
+    for (int t = 0; t < nv; t++) {
+      const Fr& x = L->u[base + t];
+      acc = mont_mul_ni(acc, ((j >> (nv - 1 - t)) & 1) ? x : fr_sub(fr_r1(), x));
+    }
+    out[j] = acc;
+  }
+}
+
+// Multiplicities of entries [k0, k1) of S; a value outside the table marks
+// the proof VL_ELOOKUP.  Tables up to 4096 entries count in shared memory.
+__global__ void __launch_bounds__(LK_THREADS) lk_hist_kernel(LkDev* Ls, const LkItem* items) {
+  __shared__ uint32_t h[4096];
+  const LkItem it = items[blockIdx.x];
+  LkDev* L = Ls + it.proof;
+  const int N = 1 << L->log2_n;
+  const bool local = N <= 4096;
+  if (local)
+    for (int j = threadIdx.x; j < N; j += blockDim.x) h[j] = 0;
+  __syncthreads();
+  bool bad = false;
+  for (int k = it.k0 + threadIdx.x; k < it.k1; k += blockDim.x) {
+    const int row = k / (int)L->cols, col = k - row * (int)L->cols;
+    const int64_t j = (int64_t)L->S[(int64_t)row * L->ld + col] - L->t0;
+    if (j < 0 || j >= N) {
+      bad = true;
+      continue;
+    }
+    if (local) atomicAdd(&h[j], 1u);
+    else atomicAdd(&L->counts[j], 1u);
+  }
+  if (bad) atomicExch(&L->scr->status, VL_ELOOKUP);
+  __syncthreads();
+  if (local)
+    for (int j = threadIdx.x; j < N; j += blockDim.x)
+      if (h[j]) atomicAdd(&L->counts[j], h[j]);
+}
+
+// Table entries [k0, k1) (at most 4 per thread): x_j = beta + t0 + j, its
+// inverse by one batch inversion per block (prefix products, one field
+// inversion, back substitution), the table-side vectors, and this block's
+// share of X1 = sum B Ej T' and X2 = sum B m (slot: 12 Fr, the first two).
+__global__ void __launch_bounds__(LK_THREADS) lk_table_kernel(LkDev* Ls, const LkItem* items) {
+  __shared__ Fr pre[LK_THREADS], suf[LK_THREADS];
+  __shared__ Fr inv_tot;
+  __shared__ Fr red[2 * (LK_THREADS / 32)];
+  const LkItem it = items[blockIdx.x];
+  LkDev* L = Ls + it.proof;
+  const int tid = threadIdx.x;
+  const Fr beta = L->beta;
+  Fr x[4], p[4];
+  for (int e = 0; e < 4; e++) {
+    const int j = it.k0 + 4 * tid + e;
+    x[e] = j < it.k1 ? fr_add(beta, to_mont(fr_from_i64(L->t0 + j))) : fr_r1();
+    p[e] = e == 0 ? x[0] : mont_mul(p[e - 1], x[e]);
+  }
+  // inclusive prefix and suffix products of the thread totals (Hillis-Steele)
+  pre[tid] = p[3];
+  suf[tid] = p[3];
+  __syncthreads();
+  for (int off = 1; off < LK_THREADS; off <<= 1) {
+    const Fr a = tid >= off ? mont_mul(pre[tid - off], pre[tid]) : pre[tid];
+    const Fr b = tid + off < LK_THREADS ? mont_mul(suf[tid], suf[tid + off]) : suf[tid];
+    __syncthreads();
+    pre[tid] = a;
+    suf[tid] = b;
+    __syncthreads();
+  }
+  if (tid == 0) inv_tot = fr_inv_mont(pre[LK_THREADS - 1]);
+  __syncthreads();
+  if (fr_is_zero(inv_tot)) {  // beta + t0 + j = 0 for some j (probability ~2^-239)
+    if (tid == 0) atomicExch(&L->scr->status, VL_ELOOKUP);
+    return;
+  }
+  const Fr qprev = tid > 0 ? pre[tid - 1] : fr_r1();
+  // 1 / (prefix through this thread) = inv_tot . (product of the later threads' totals)
+  Fr inv_f = tid + 1 < LK_THREADS ? mont_mul(inv_tot, suf[tid + 1]) : inv_tot;
+  Fr inv_x[4];
+  for (int e = 3; e >= 0; e--) {
+    const Fr f_before = e > 0 ? mont_mul(qprev, p[e - 1]) : qprev;  // prefix before element e
+    inv_x[e] = mont_mul(inv_f, f_before);
+    inv_f = mont_mul(inv_f, x[e]);
+  }
+  Fr acc[2] = {fr_zero(), fr_zero()};
+  for (int e = 0; e < 4; e++) {
+    const int j = it.k0 + 4 * tid + e;
+    if (j >= it.k1) break;
+    const Fr m = to_mont(fr_small(L->counts[j]));
+    L->Binv[j] = inv_x[e];
+    L->WB[j] = inv_x[e];
+    L->Tb[j] = x[e];
+    L->WT[j] = x[e];
+    L->WM[j] = m;
+    acc[0] = fr_add(acc[0], mont_mul(mont_mul(inv_x[e], L->WE[j]), x[e]));
+    acc[1] = fr_add(acc[1], mont_mul(inv_x[e], m));
+  }
+  block_sum_fr<2>(acc, red);
+  if (tid == 0) {
+    L->part[(size_t)it.slot * 12] = acc[0];
+    L->part[(size_t)it.slot * 12 + 1] = acc[1];
+  }
+}
+
+// Round t over pairs [k0, k1) of one proof: fold the vectors with r_{t-1}
+// (the first round reads the unfolded cube, the second folds it on the
+// fly and writes the folded vectors), then the partial sums of
+//   T_X = sum A E S',  A_X = sum A   (X = 0, 2, 3)
+// and, in the table rounds (JR), U_X = sum B Ej T', V_X = sum B m.
+template <bool JR>
+__global__ void __launch_bounds__(LK_THREADS) lk_pass_kernel(LkDev* Ls, int t, const LkItem* items) {
+  __shared__ Fr red[6 * (LK_THREADS / 32)];
+  const LkItem it = items[blockIdx.x];
+  LkDev* L = Ls + it.proof;
+  const int h = 1 << (L->L - t);
+  const int tj = t - (L->L - L->log2_n);  // table round number (1-based) when JR
+  Fr acc[6];
+#pragma unroll
+  for (int i = 0; i < 6; i++) acc[i] = fr_zero();
+  Fr accb[JR ? 6 : 1];
+#pragma unroll
+  for (int i = 0; i < (JR ? 6 : 1); i++) accb[i] = fr_zero();
+  for (int k = it.k0 + threadIdx.x; k < it.k1; k += blockDim.x) {
+    Fr a0, a1, e0, e1, s0, s1;
+    if (t == 1) {
+      lk_level0(*L, k, a0, e0, s0);
+      lk_level0(*L, k + h, a1, e1, s1);
+    } else if (t == 2) {
+      const Fr r = L->r[0];
+      Fr xa, xe, xs, ya, ye, ys;
+      lk_level0(*L, k, xa, xe, xs);
+      lk_level0(*L, k + 2 * h, ya, ye, ys);
+      a0 = lk_fold(xa, ya, r);
+      e0 = lk_fold(xe, ye, r);
+      s0 = lk_fold(xs, ys, r);
+      lk_level0(*L, k + h, xa, xe, xs);
+      lk_level0(*L, k + 3 * h, ya, ye, ys);
+      a1 = lk_fold(xa, ya, r);
+      e1 = lk_fold(xe, ye, r);
+      s1 = lk_fold(xs, ys, r);
+      L->VA[k] = a0, L->VE[k] = e0, L->VS[k] = s0;
+      L->VA[k + h] = a1, L->VE[k + h] = e1, L->VS[k + h] = s1;
+    } else {
+      const Fr r = L->r[t - 2];
+      a0 = lk_fold(L->VA[k], L->VA[k + 2 * h], r);
+      e0 = lk_fold(L->VE[k], L->VE[k + 2 * h], r);
+      s0 = lk_fold(L->VS[k], L->VS[k + 2 * h], r);
+      a1 = lk_fold(L->VA[k + h], L->VA[k + 3 * h], r);
+      e1 = lk_fold(L->VE[k + h], L->VE[k + 3 * h], r);
+      s1 = lk_fold(L->VS[k + h], L->VS[k + 3 * h], r);
+      L->VA[k] = a0, L->VE[k] = e0, L->VS[k] = s0;
+      L->VA[k + h] = a1, L->VE[k + h] = e1, L->VS[k + h] = s1;
+    }
+    {
+      const Fr da = fr_sub(a1, a0), de = fr_sub(e1, e0), ds = fr_sub(s1, s0);
+      const Fr a2 = fr_add(a1, da), e2 = fr_add(e1, de), s2 = fr_add(s1, ds);
+      const Fr a3 = fr_add(a2, da), e3 = fr_add(e2, de), s3 = fr_add(s2, ds);
+      acc[0] = fr_add(acc[0], mont_mul(mont_mul(a0, e0), s0));
+      acc[1] = fr_add(acc[1], mont_mul(mont_mul(a2, e2), s2));
+      acc[2] = fr_add(acc[2], mont_mul(mont_mul(a3, e3), s3));
+      acc[3] = fr_add(acc[3], a0);
+      acc[4] = fr_add(acc[4], a2);
+      acc[5] = fr_add(acc[5], a3);
+    }
+    if constexpr (JR) {
+      Fr b0, b1, q0, q1, u0, u1, m0, m1;  // B, Ej, T', m
+      if (tj == 1) {
+        b0 = L->WB[k], b1 = L->WB[k + h];
+        q0 = L->WE[k], q1 = L->WE[k + h];
+        u0 = L->WT[k], u1 = L->WT[k + h];
+        m0 = L->WM[k], m1 = L->WM[k + h];
+      } else {
+        const Fr r = L->r[t - 2];
+        b0 = lk_fold(L->WB[k], L->WB[k + 2 * h], r);
+        q0 = lk_fold(L->WE[k], L->WE[k + 2 * h], r);
+        u0 = lk_fold(L->WT[k], L->WT[k + 2 * h], r);
+        m0 = lk_fold(L->WM[k], L->WM[k + 2 * h], r);
+        b1 = lk_fold(L->WB[k + h], L->WB[k + 3 * h], r);
+        q1 = lk_fold(L->WE[k + h], L->WE[k + 3 * h], r);
+        u1 = lk_fold(L->WT[k + h], L->WT[k + 3 * h], r);
+        m1 = lk_fold(L->WM[k + h], L->WM[k + 3 * h], r);
+        L->WB[k] = b0, L->WE[k] = q0, L->WT[k] = u0, L->WM[k] = m0;
+        L->WB[k + h] = b1, L->WE[k + h] = q1, L->WT[k + h] = u1, L->WM[k + h] = m1;
+      }
+      const Fr db = fr_sub(b1, b0), dq = fr_sub(q1, q0), du = fr_sub(u1, u0), dm = fr_sub(m1, m0);
+      const Fr b2 = fr_add(b1, db), q2 = fr_add(q1, dq), u2 = fr_add(u1, du), m2 = fr_add(m1, dm);
+      const Fr b3 = fr_add(b2, db), q3 = fr_add(q2, dq), u3 = fr_add(u2, du), m3 = fr_add(m2, dm);
+      accb[0] = fr_add(accb[0], mont_mul(mont_mul(b0, q0), u0));
+      accb[1] = fr_add(accb[1], mont_mul(mont_mul(b2, q2), u2));
+      accb[2] = fr_add(accb[2], mont_mul(mont_mul(b3, q3), u3));
+      accb[3] = fr_add(accb[3], mont_mul(b0, m0));
+      accb[4] = fr_add(accb[4], mont_mul(b2, m2));
+      accb[5] = fr_add(accb[5], mont_mul(b3, m3));
+    }
+  }
+  block_sum_fr<6>(acc, red);
+  if (threadIdx.x < 6) {
+    Fr v = acc[0];
+#pragma unroll
+    for (int i = 1; i < 6; i++)
+      if (threadIdx.x == i) v = acc[i];
+    L->part[(size_t)it.slot * 12 + threadIdx.x] = v;
+  }
+  if constexpr (JR) {
+    block_sum_fr<6>(accb, red);
+    if (threadIdx.x < 6) {
+      Fr v = accb[0];
+#pragma unroll
+      for (int i = 1; i < 6; i++)
+        if (threadIdx.x == i) v = accb[i];
+      L->part[(size_t)it.slot * 12 + 6 + threadIdx.x] = v;
+    }
+  }
+}
+
+// g(r) for the cubic through (0, g0) .. (3, g3) (Lagrange), Montgomery.
+__device__ Fr lk_cubic(const Fr (&g)[4], const Fr& r, const Fr& inv2, const Fr& inv6) {
+  const Fr one = fr_r1(), two = fr_add(one, one), three = fr_add(two, one);
+  const Fr r1 = fr_sub(r, one), r2 = fr_sub(r, two), r3 = fr_sub(r, three);
+  const Fr p12 = mont_mul_ni(r1, r2), p23 = mont_mul_ni(r2, r3), p01 = mont_mul_ni(r, r1);
+  const Fr l0 = fr_neg(mont_mul_ni(mont_mul_ni(p12, r3), inv6));
+  const Fr l1 = mont_mul_ni(mont_mul_ni(r, p23), inv2);
+  const Fr l2 = fr_neg(mont_mul_ni(mont_mul_ni(p01, r3), inv2));
+  const Fr l3 = mont_mul_ni(mont_mul_ni(p01, r2), inv6);
+  Fr s = mont_mul_ni(g[0], l0);
+  s = fr_add(s, mont_mul_ni(g[1], l1));
+  s = fr_add(s, mont_mul_ni(g[2], l2));
+  return fr_add(s, mont_mul_ni(g[3], l3));
+}
+
+// Round t of one proof (one block each): the round polynomial from the
+// partial sums, its values in the proof, absorb, squeeze r_t, new claim.
+__global__ void __launch_bounds__(LK_THREADS) lk_round_kernel(LkDev* Ls, int t, vl_lookup_proof* outs) {
+  __shared__ Fr red[6 * (LK_THREADS / 32)];
+  __shared__ uint32_t Sw[8], Sn[8];
+  __shared__ uint32_t dig[3][8];
+  __shared__ Fr rch[1];
+  __shared__ Fr gsh[4];
+  LkDev* L = Ls + blockIdx.x;
+  if (t > L->L) return;
+  const int tid = threadIdx.x;
+  const bool jr = t > L->L - L->log2_n;
+  if (t == 1) {  // the table side's cube sum, from the table kernel's partials
+    Fr x[2] = {fr_zero(), fr_zero()};
+    for (int s = L->xbeg + tid; s < L->xend; s += blockDim.x) {
+      x[0] = fr_add(x[0], L->part[(size_t)s * 12]);
+      x[1] = fr_add(x[1], L->part[(size_t)s * 12 + 1]);
+    }
+    block_sum_fr<2>(x, red);
+    if (tid == 0) L->Cb = fr_sub(mont_mul_ni(mont_mul_ni(L->alpha, L->alpha), x[0]), x[1]);
+    __syncthreads();
+  }
+  Fr acc[6], accb[6];
+  for (int i = 0; i < 6; i++) acc[i] = accb[i] = fr_zero();
+  for (int s = L->pbeg[t] + tid; s < L->pend[t]; s += blockDim.x) {
+    for (int i = 0; i < 6; i++) acc[i] = fr_add(acc[i], L->part[(size_t)s * 12 + i]);
+    if (jr)
+      for (int i = 0; i < 6; i++) accb[i] = fr_add(accb[i], L->part[(size_t)s * 12 + 6 + i]);
+  }
+  block_sum_fr<6>(acc, red);
+  if (jr) block_sum_fr<6>(accb, red);
+  if (tid == 0) {
+    const Fr alpha = L->alpha, a2 = mont_mul_ni(alpha, alpha);
+    Fr tab[3];
+    if (jr) {
+      for (int i = 0; i < 3; i++) tab[i] = mont_mul_ni(L->c_nd, fr_sub(mont_mul_ni(a2, accb[i]), accb[3 + i]));
+    } else {
+      L->half_t = mont_mul_ni(L->half_t, L->inv2);
+      const Fr c = mont_mul_ni(L->half_t, L->Cb);
+      tab[0] = tab[1] = tab[2] = c;
+    }
+    Fr g[4];
+    g[0] = fr_add(fr_add(mont_mul_ni(alpha, acc[0]), acc[3]), tab[0]);
+    g[2] = fr_add(fr_add(mont_mul_ni(alpha, acc[1]), acc[4]), tab[1]);
+    g[3] = fr_add(fr_add(mont_mul_ni(alpha, acc[2]), acc[5]), tab[2]);
+    g[1] = fr_sub(L->claim, g[0]);
+    Fr gc[3];
+    vl_lookup_proof* out = outs + blockIdx.x;
+    for (int i = 0; i < 4; i++) {
+      gsh[i] = g[i];
+      const Fr c = from_mont_ni(g[i]);
+      for (int l = 0; l < 8; l++) out->g[t - 1][i].limb[l] = c.v[l];
+      if (i != 1) gc[i == 0 ? 0 : i - 1] = c;
+    }
+    uint32_t S[8];
+    for (int i = 0; i < 8; i++) S[i] = L->St[i];
+    dev_absorb_fr<3>(S, LBL_G, gc);
+    for (int i = 0; i < 8; i++) Sw[i] = S[i];
+  }
+  __syncthreads();
+  squeeze_dev(Sw, LBL_R, 1, rch, Sn, dig);
+  if (tid == 0) {
+    const Fr r = rch[0];
+    L->r[t - 1] = r;
+    for (int i = 0; i < 8; i++) L->St[i] = Sn[i];
+    const Fr g[4] = {gsh[0], gsh[1], gsh[2], gsh[3]};
+    L->claim = lk_cubic(g, r, L->inv2, L->inv6);
+  }
+}
+
+// One block per proof: the final evaluations (the last pair folded with
+// r_L), absorb 'f', the proof.
+__global__ void __launch_bounds__(LK_THREADS) lk_finish_kernel(LkDev* Ls, vl_lookup_proof* outs) {
+  LkDev* L = Ls + blockIdx.x;
+  vl_lookup_proof* out = outs + blockIdx.x;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < (VL_LOOKUP_MAX_LOG_D - L->L) * 32; i += blockDim.x)  // unused rounds
+    out->g[L->L + i / 32][(i / 8) & 3].limb[i & 7] = 0u;
+  if (tid != 0) return;
+  Fr a, e, s, b, m;
+  const int Lp = L->L;
+  if (Lp == 0) {
+    lk_level0(*L, 0, a, e, s);
+  } else if (Lp == 1) {
+    Fr a1, e1, s1;
+    lk_level0(*L, 0, a, e, s);
+    lk_level0(*L, 1, a1, e1, s1);
+    a = lk_fold(a, a1, L->r[0]);
+    s = lk_fold(s, s1, L->r[0]);
+  } else {
+    a = lk_fold(L->VA[0], L->VA[1], L->r[Lp - 1]);
+    s = lk_fold(L->VS[0], L->VS[1], L->r[Lp - 1]);
+  }
+  if (L->log2_n == 0) {
+    b = L->WB[0];
+    m = L->WM[0];
+  } else {
+    b = lk_fold(L->WB[0], L->WB[1], L->r[Lp - 1]);
+    m = lk_fold(L->WM[0], L->WM[1], L->r[Lp - 1]);
+  }
+  s = fr_sub(s, L->beta);
+  const Fr fin[4] = {from_mont_ni(a), from_mont_ni(s), from_mont_ni(b), from_mont_ni(m)};
+  uint32_t S[8];
+  for (int i = 0; i < 8; i++) S[i] = L->St[i];
+  dev_absorb_fr<4>(S, LBL_F, fin);
+  out->n = L->n;
+  out->log2_d = Lp;
+  out->log2_n = L->log2_n;
+  out->t0 = L->t0;
+  for (int l = 0; l < 8; l++) {
+    out->a_r.limb[l] = fin[0].v[l];
+    out->s_r.limb[l] = fin[1].v[l];
+    out->b_r.limb[l] = fin[2].v[l];
+    out->m_r.limb[l] = fin[3].v[l];
+  }
+  for (int i = 0; i < 32; i++) out->state[i] = (uint8_t)(S[i >> 2] >> (24 - 8 * (i & 3)));
+  out->status = L->scr->status;
+}
+
+}  // namespace
+
+cudaError_t launch_lookup_setup(LkDev* Ls, int np, const LkItem* fac_items, int nfac, const LkItem* hist_items,
+                                int nhist, const LkItem* tab_items, int ntab, cudaStream_t st) {
+  lk_start_kernel<<<np, LK_THREADS, 0, st>>>(Ls);
+  if (nfac) lk_factor_kernel<<<nfac, LK_THREADS, 0, st>>>(Ls, fac_items);
+  if (nhist) lk_hist_kernel<<<nhist, LK_THREADS, 0, st>>>(Ls, hist_items);
+  if (ntab) lk_table_kernel<<<ntab, LK_THREADS, 0, st>>>(Ls, tab_items);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lookup_round(LkDev* Ls, int np, int t, const LkItem* items, int nhi, int nlo,
+                                vl_lookup_proof* out, cudaStream_t st) {
+  if (nhi) lk_pass_kernel<false><<<nhi, LK_THREADS, 0, st>>>(Ls, t, items);
+  if (nlo) lk_pass_kernel<true><<<nlo, LK_THREADS, 0, st>>>(Ls, t, items + nhi);
+  lk_round_kernel<<<np, LK_THREADS, 0, st>>>(Ls, t, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lookup_finish(LkDev* Ls, int np, vl_lookup_proof* out, cudaStream_t st) {
+  lk_finish_kernel<<<np, LK_THREADS, 0, st>>>(Ls, out);
+  return cudaGetLastError();
+}
+
+}  // namespace vl

@@ -83,6 +83,28 @@ VL_HD void ts_start_linear(uint8_t S[32], uint64_t seed, uint32_t rows, uint32_t
   h.finish(S);
 }
 
+// Start of a lookup transcript:
+//   S0 = SHA256("verilora-gb300/zklookup/v1" || seed u64le || n, log2 D, log2 N u32le
+//               || t0 i64le || bind (32 B))
+VL_HD void ts_start_lookup(uint8_t S[32], uint64_t seed, uint32_t n, uint32_t log2_d, uint32_t log2_n, int64_t t0,
+                           const uint8_t bind[32]) {
+  const uint8_t dom[26] = {'v', 'e', 'r', 'i', 'l', 'o', 'r', 'a', '-', 'g', 'b', '3', '0',
+                           '0', '/', 'z', 'k', 'l', 'o', 'o', 'k', 'u', 'p', '/', 'v', '1'};
+  Sha256 h;
+  h.init();
+  h.update(dom, 26);
+  h.u32le((uint32_t)seed);
+  h.u32le((uint32_t)(seed >> 32));
+  h.u32le(n);
+  h.u32le(log2_d);
+  h.u32le(log2_n);
+  const uint64_t tb = (uint64_t)t0;
+  h.u32le((uint32_t)tb);
+  h.u32le((uint32_t)(tb >> 32));
+  h.update(bind, 32);
+  h.finish(S);
+}
+
 // absorb(label, canonical field elements)
 VL_HD void ts_absorb_fr(uint8_t S[32], uint8_t label, const Fr* vals, int count) {
   Sha256 h;

@@ -7,6 +7,7 @@
 // through 0, 1, 2, checks the final claim a_r . b_r, the final transcript
 // state, and evaluates A~(u, r), B~(r, v), C~(u, v) directly from the
 // matrices (the stand-in for polynomial-commitment openings, Sec. II-A).
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -211,5 +212,136 @@ extern "C" int32_t vl_verify_linear(const vl_lin_job* job, const vl_lin_proof* p
   if (std::memcmp(S, proof->state, 32) != 0) return VL_REJECT;
   for (int q = 0; q < nmats; q++)
     if (!fr_eq(to_mont(ev[q]), mle_eval(HostMat{&mats[q]}, x, y))) return VL_REJECT;
+  return VL_OK;
+}
+
+namespace {
+
+// g(x) for the cubic through (0, g0) .. (3, g3) (Lagrange); Montgomery.
+Fr cubic_interp(const Fr (&g)[4], const Fr& x) {
+  const Fr one = fr_r1(), two = fr_add(one, one), three = fr_add(two, one);
+  const Fr inv2 = to_mont(fr_inv_canonical(fr_small(2))), inv6 = to_mont(fr_inv_canonical(fr_small(6)));
+  const Fr x1 = fr_sub(x, one), x2 = fr_sub(x, two), x3 = fr_sub(x, three);
+  const Fr l0 = fr_neg(mont_mul(mont_mul(mont_mul(x1, x2), x3), inv6));
+  const Fr l1 = mont_mul(mont_mul(mont_mul(x, x2), x3), inv2);
+  const Fr l2 = fr_neg(mont_mul(mont_mul(mont_mul(x, x1), x3), inv2));
+  const Fr l3 = mont_mul(mont_mul(mont_mul(x, x1), x2), inv6);
+  return fr_add(fr_add(mont_mul(g[0], l0), mont_mul(g[1], l1)), fr_add(mont_mul(g[2], l2), mont_mul(g[3], l3)));
+}
+
+}  // namespace
+
+// Host verifier of a lookup proof (Protocol 1, Eq. eq:lookup-sumcheck):
+// replays the transcript, checks every round against the running claim and
+// the final claim against the sent evaluations (eq(u, r), eq(u_low, r_low)
+// and T~(r_low) computed here), then checks the evaluations against A, S, B
+// and m recomputed from S and T (the stand-in for commitment openings).
+extern "C" int32_t vl_verify_lookup(const vl_lookup_job* job, const vl_lookup_proof* proof) {
+  if (!job || !proof) return VL_EINVAL;
+  const vl_mat* M = &job->S;
+  int e;
+  if ((e = check_host_mat(M)) != VL_OK) return e;
+  if (M->trans != 0 || M->dtype == VL_FR_MONT || job->reserved != 0) return VL_EINVAL;
+  if (job->log2_n < 0 || job->log2_n > VL_LOOKUP_MAX_LOG_N) return VL_EINVAL;
+  const int64_t n = M->rows * M->cols;
+  if (n > (int64_t(1) << VL_LOOKUP_MAX_LOG_D)) return VL_ESHAPE;
+  const int ln = job->log2_n, L = std::max(ln, ceil_log2(n));
+  const int64_t N = int64_t(1) << ln, D = int64_t(1) << L, t0 = job->t0;
+  if (proof->n != n || proof->log2_d != L || proof->log2_n != ln || proof->t0 != t0) return VL_REJECT;
+  if (proof->status != VL_OK) return VL_REJECT;
+  for (int t = 0; t < L; t++)
+    for (int q = 0; q < 4; q++)
+      if (!lt_r(fr_from_api(proof->g[t][q]))) return VL_REJECT;
+  const Fr a_r = fr_from_api(proof->a_r), s_r = fr_from_api(proof->s_r), b_r = fr_from_api(proof->b_r),
+           m_r = fr_from_api(proof->m_r);
+  if (!lt_r(a_r) || !lt_r(s_r) || !lt_r(b_r) || !lt_r(m_r)) return VL_REJECT;
+  // S padded with t0, as table indices; values outside the table reject
+  std::vector<int32_t> idx((size_t)D, 0);
+  std::vector<uint64_t> counts((size_t)N, 0);
+  for (int64_t k = 0; k < D; k++) {
+    int64_t v = t0;
+    if (k < n) {
+      const int64_t row = k / M->cols, col = k % M->cols, at = row * M->ld + col;
+      v = M->dtype == VL_I16 ? static_cast<const int16_t*>(M->data)[at] : static_cast<const int64_t*>(M->data)[at];
+    }
+    if (v < t0 || v - t0 >= N) return VL_REJECT;
+    idx[(size_t)k] = (int32_t)(v - t0);
+    counts[(size_t)(v - t0)]++;
+  }
+  uint8_t S[32];
+  ts_start_lookup(S, job->seed, (uint32_t)n, (uint32_t)L, (uint32_t)ln, t0, job->bind);
+  const Fr beta = to_mont(ts_challenge(S, 'b', 0));
+  ts_squeeze_done(S, 'b', 1);
+  const Fr alpha = to_mont(ts_challenge(S, 'a', 0));
+  ts_squeeze_done(S, 'a', 1);
+  std::vector<Fr> u(L), r(L);
+  for (int t = 0; t < L; t++) u[t] = to_mont(ts_challenge(S, 'u', t));
+  ts_squeeze_done(S, 'u', L);
+  Fr claim = fr_add(alpha, mont_mul(alpha, alpha));
+  for (int t = 0; t < L; t++) {
+    Fr g[4], gc[3];
+    for (int q = 0; q < 4; q++) g[q] = to_mont(fr_from_api(proof->g[t][q]));
+    if (!fr_eq(fr_add(g[0], g[1]), claim)) return VL_REJECT;
+    gc[0] = fr_from_api(proof->g[t][0]);
+    gc[1] = fr_from_api(proof->g[t][2]);
+    gc[2] = fr_from_api(proof->g[t][3]);
+    ts_absorb_fr(S, 'g', gc, 3);
+    r[t] = to_mont(ts_challenge(S, 'r', 0));
+    ts_squeeze_done(S, 'r', 1);
+    claim = cubic_interp(g, r[t]);
+  }
+  // eq(u, r), eq(u_low, r_low), T~(r_low) = t0 + sum_t 2^(ln-1-t) r_low_t
+  Fr e_r = fr_r1(), ej_r = fr_r1(), t_r = to_mont(fr_from_i64(t0)), w = fr_r1();
+  for (int t = 0; t < L; t++) {
+    const Fr f = fr_add(mont_mul(u[t], r[t]), mont_mul(fr_sub(fr_r1(), u[t]), fr_sub(fr_r1(), r[t])));
+    e_r = mont_mul(e_r, f);
+    if (t >= L - ln) ej_r = mont_mul(ej_r, f);
+  }
+  for (int t = L - 1; t >= L - ln; t--) {  // weights 1, 2, 4, .. from the least significant bit
+    t_r = fr_add(t_r, mont_mul(w, r[t]));
+    w = fr_add(w, w);
+  }
+  const Fr inv2 = to_mont(fr_inv_canonical(fr_small(2)));
+  Fr c = fr_r1();
+  for (int i = 0; i < L - ln; i++) c = mont_mul(c, inv2);
+  const Fr am = to_mont(a_r), sm = to_mont(s_r), bm = to_mont(b_r), mm = to_mont(m_r);
+  const Fr a2 = mont_mul(alpha, alpha);
+  Fr fin = fr_add(mont_mul(mont_mul(mont_mul(alpha, am), e_r), fr_add(sm, beta)), am);
+  const Fr tab = fr_sub(mont_mul(mont_mul(mont_mul(a2, bm), ej_r), fr_add(t_r, beta)), mont_mul(bm, mm));
+  fin = fr_add(fin, mont_mul(c, tab));
+  if (!fr_eq(fin, claim)) return VL_REJECT;
+  const Fr f4[4] = {a_r, s_r, b_r, m_r};
+  ts_absorb_fr(S, 'f', f4, 4);
+  if (std::memcmp(S, proof->state, 32) != 0) return VL_REJECT;
+  // Openings: B by one batch inversion, A gathered from B, eq tables by doubling.
+  std::vector<Fr> B((size_t)N), pre((size_t)N);
+  Fr acc = fr_r1();
+  for (int64_t j = 0; j < N; j++) {
+    B[(size_t)j] = fr_add(beta, to_mont(fr_from_i64(t0 + j)));
+    acc = mont_mul(acc, B[(size_t)j]);
+    pre[(size_t)j] = acc;
+  }
+  Fr inv = fr_inv_mont(acc);
+  if (fr_is_zero(inv)) return VL_REJECT;
+  for (int64_t j = N - 1; j >= 0; j--) {
+    const Fr before = j > 0 ? pre[(size_t)j - 1] : fr_r1();
+    const Fr x = B[(size_t)j];
+    B[(size_t)j] = mont_mul(inv, before);
+    inv = mont_mul(inv, x);
+  }
+  const std::vector<Fr> er = eq_table(r, D);
+  const std::vector<Fr> rl(r.begin() + (L - ln), r.end());
+  const std::vector<Fr> erl = eq_table(rl, N);
+  Fr ea = fr_zero(), es = fr_zero(), eb = fr_zero(), em = fr_zero();
+  for (int64_t k = 0; k < D; k++) {
+    const int32_t j = idx[(size_t)k];
+    ea = fr_add(ea, mont_mul(B[(size_t)j], er[(size_t)k]));
+    es = fr_add(es, mont_mul(to_mont(fr_from_i64(t0 + j)), er[(size_t)k]));
+  }
+  for (int64_t j = 0; j < N; j++) {
+    eb = fr_add(eb, mont_mul(B[(size_t)j], erl[(size_t)j]));
+    em = fr_add(em, mont_mul(to_mont(fr_from_i64((int64_t)counts[(size_t)j])), erl[(size_t)j]));
+  }
+  if (!fr_eq(ea, am) || !fr_eq(es, sm) || !fr_eq(eb, bm) || !fr_eq(em, mm)) return VL_REJECT;
   return VL_OK;
 }

@@ -180,6 +180,34 @@ def paper_route_products(t, seed=GLOBAL_SEED):
     return out, dWr
 
 
+RESCALE_SHIFT = 8
+
+
+def remainder(Z, shift):
+    """rho = (z + 2^(shift-1)) mod 2^shift, the remainder the rescale
+    z' = floor((z + 2^(shift-1)) / 2^shift) drops: z + 2^(shift-1) = 2^shift z' + rho."""
+    Z = np.asarray(Z, dtype=np.int64)
+    return ((Z + (1 << (shift - 1))) & ((1 << shift) - 1)).astype(np.int16)
+
+
+def rescale_lookups(t, seed=GLOBAL_SEED):
+    """Range checks of one projection's rescale remainders (the lookup
+    arguments that prove the fixed-point rescales, Sec. IV-A): H = rescale(X.A)
+    and dH = rescale(dY.B^T) (n x r, remainders in [0, 2^8)), and the
+    parameter-update steps G_A, G_B (d x r and r x k, remainders in
+    [0, 2^12)).  Each is {"S", "t0", "log2_n", "seed", "name"}."""
+    X, A, B, dY, H, dH = (t[x] for x in ("X", "A", "B", "dY", "H", "dH"))
+    out = []
+    for name, Z, shift in (("H", lambda: exact_matmul(X, A), RESCALE_SHIFT),
+                           ("dH", lambda: exact_matmul(dY, B.T), RESCALE_SHIFT),
+                           ("GA", lambda: exact_matmul(X.T, dH), UPDATE_SHIFT),
+                           ("GB", lambda: exact_matmul(H.T, dY), UPDATE_SHIFT)):
+        out.append({"S": remainder(Z(), shift), "t0": 0, "log2_n": shift,
+                    "seed": proof_seed(seed, t["layer"], t["proj"], "R" + name),
+                    "name": f"L{t['layer']}.{t['proj']}.R{name}"})
+    return out
+
+
 def op_shape(job):
     P, Q = job["P"], job["Q"]
     m, k = (P.shape[1], P.shape[0]) if job["tp"] else P.shape
