@@ -44,7 +44,7 @@ SM_MAX_MHZ = 2070.0
 # per clock, a wide (64-bit result) one taking two of them.
 MADWIDE_PER_SM_CLK = 32
 STEP_KIND = {"7b-step": "7b", "7b-proj": "7b-proj", "13b-step": "13b", "serve": "7b-proj", "7b-update": "7b",
-             "7b-step-paper-route": "7b"}
+             "7b-step-paper-route": "7b", "7b-lookups": "7b"}
 WORKLOADS = {
     "7b-step": "batched 7B-shaped LoRA step: 32 layers x {q,k,v,o}, hidden 4096, seq 512, ranks {8,16,64}",
     "7b-proj": "one 7B-shaped LoRA projection, n=1024, d=k=4096, r=16, eight products",
@@ -52,6 +52,9 @@ WORKLOADS = {
     "7b-step-paper-route": "batched 7B-shaped LoRA step along the paper's backward route (Eq. eq:grad_wl, "
                            "eq:grad_abl: full dW' = X^T.dY, then dA = dW'.B^T, dB = A^T.dW'), nine products per "
                            "projection, 32 layers x {q,k,v,o}, hidden 4096, seq 512, ranks {8,16,64}",
+    "7b-lookups": "range lookups of the 7B-shaped LoRA step's rescale remainders (Protocol 1, Eq. "
+                  "eq:lookup-sumcheck): 32 layers x {q,k,v,o} x {H, dH (512 x r, table 2^8), G_A (4096 x r), "
+                  "G_B (r x 4096) (table 2^12)}, ranks {8,16,64}, one batched plan run",
     "7b-update": "parameter updates of the 7B-shaped LoRA step (Eq. eq:grad_update_ab): 32 layers x {q,k,v,o} x "
                  "{A' = A - G_A (4096 x r), B' = B - G_B (r x 4096)}, ranks {8,16,64}, linear zkMat, one batched call",
     "serve": "serving stream: Poisson arrivals (20 jobs/s) of single-layer jobs (one projection's 8 products), "
@@ -178,6 +181,25 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     cores = 1
+    if args.workload == "7b-lookups":
+        per_step = []
+        for _ in range(args.warmup):
+            oracle_lookup_sample(W.GLOBAL_SEED, 1)
+        for _ in range(args.steps):
+            rate, dt, nj, ent = oracle_lookup_sample(W.GLOBAL_SEED, 1)
+            per_step.append(dt)
+        total = sum(per_step)
+        value = ent * args.steps / total
+        sample = f"the two n x r remainder lookups of the first projection ({nj} proofs, {ent} entries) per step"
+        print(json.dumps({
+            "impl": "reference", "metric": LK_METRIC, "value": value, "unit": LK_UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int (Fr, 255-bit)",
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "sample": sample},
+            "cpu_baseline": {"value": value, "unit": LK_UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": LK_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
     if args.workload == "7b-update":
         nproj = 8
         per_step = []
@@ -451,6 +473,144 @@ def update_main(args, rank, world, local, cpu):
     }))
 
 
+LK_METRIC = "lookup-argument entries proved/sec (range checks of a LoRA step's rescale remainders), bit-exact"
+LK_UNIT = "entries/s"
+# Montgomery products per second the SMs can issue: 152 SMs x 32 IMAD.WIDE
+# per clock x 2070 MHz, 128 IMAD.WIDE per 8-limb Montgomery product (64 for
+# the product, 64 for the reduction).
+MONT_PEAK = SMS * MADWIDE_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 128
+
+
+def lookup_statements(seed, layers=0, nproj=None):
+    spec = W.step_layers("7b", seed)
+    if layers > 0:
+        spec = [s for s in spec if s[0] < layers]
+    if nproj is not None:
+        spec = spec[:nproj]
+    looks = []
+    for s in spec:
+        looks += W.rescale_lookups(W.lora_projection(seed, *s), seed)
+    return looks
+
+
+def lookup_cube(x):
+    n = int(x["S"].size)
+    return 1 << max(x["log2_n"], (n - 1).bit_length())
+
+
+def oracle_lookup_sample(seed, nproj):
+    """Time the oracle on the two n x r remainder lookups of the first `nproj` projections."""
+    import oracle
+    looks = [x for x in lookup_statements(seed, nproj=nproj) if x["log2_n"] == W.RESCALE_SHIFT]
+    entries = sum(int(x["S"].size) for x in looks)
+    t0 = time.perf_counter()
+    for x in looks:
+        oracle.prove_lookup(x["S"], x["t0"], x["log2_n"], seed=x["seed"])
+    dt = time.perf_counter() - t0
+    return entries / dt, dt, len(looks), entries
+
+
+def lookups_main(args, rank, world, local, cpu):
+    """Range lookups of the 7B step's rescale remainders: 512 proofs per
+    step, one plan run (setup, three launches per round, finish)."""
+    import torch
+    from paper_2508_21393_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.lib()
+    looks = lookup_statements(rank_seed(rank), args.layers)
+    entries = sum(int(x["S"].size) for x in looks)
+    cube = sum(lookup_cube(x) for x in looks)
+    dev = [torch.from_numpy(np.ascontiguousarray(x["S"])).cuda() for x in looks]
+    jobs = [B.lookup_job(B.mat(d), x["t0"], x["log2_n"], x["seed"]) for d, x in zip(dev, looks)]
+    plan = B.LookupPlan(jobs)
+    n = plan.workspace_bytes()
+    ws = torch.empty(n, dtype=torch.uint8, device="cuda")
+    sz = ctypes.sizeof(B.vl_lookup_proof)
+    dout = torch.empty(len(jobs) * sz, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        plan.run(ws.data_ptr(), n, dout.data_ptr(), B.VL_DEVICE, stream)
+    torch.cuda.synchronize()
+    raw = dout.cpu().numpy().tobytes()
+    out = [B.vl_lookup_proof.from_buffer_copy(raw, i * sz) for i in range(len(jobs))]
+    assert all(p.status == 0 for p in out)
+    # a sample of the warm-up proofs verifies in the library's host verifier (not timed)
+    for i in range(0, len(looks), max(1, len(looks) // 16)):
+        hj = B.lookup_job(B.mat(np.ascontiguousarray(looks[i]["S"])), looks[i]["t0"], looks[i]["log2_n"],
+                          looks[i]["seed"])
+        assert B.vl_verify_lookup(hj, out[i])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    time.sleep(0.6)
+    total_ms, phases = 0.0, []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.run(ws.data_ptr(), n, dout.data_ptr(), B.VL_DEVICE, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        phases.append(plan.phase_ms())
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = total_ms / args.steps
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = job_value(entries, world, ms_max / 1e3)
+    # the sumcheck rounds: batched passes plus each proof's tail rounds
+    rounds_ms = statistics.mean(p[1] + p[2] for p in phases)
+    # algorithmic field products of the rounds: per round and pair, 3 folds +
+    # 3 evaluation points x 2 products (9 per pair; sum over rounds 9 D), plus
+    # the eq(u, .) entry (1 per cube entry): 10 per cube entry
+    achieved = 10 * cube / (rounds_ms / 1e3)
+    roof = {"bound": "alu", "kernel": "lk_pass_kernel + lk_round_kernel + lk_tail_kernel (all rounds)",
+            "achieved": achieved / 1e9,
+            "peak": MONT_PEAK / 1e9, "unit": "G Montgomery products/s", "frac": achieved / MONT_PEAK,
+            "traffic": None, "peak_note": "derived: 152 SMs x 32 IMAD.WIDE/clk x 2070 MHz / 128 per product",
+            "algorithmic_products_per_step": 10 * cube}
+    host = [torch.from_numpy(np.ascontiguousarray(x["S"])).pin_memory() for x in looks]
+    hjobs = [B.lookup_job(B.mat(h), x["t0"], x["log2_n"], x["seed"]) for h, x in zip(host, looks)]
+    hplan = B.LookupPlan(hjobs)
+    hn = hplan.workspace_bytes()
+    plan.destroy()
+    del ws
+    hws = torch.empty(hn, dtype=torch.uint8, device="cuda")
+    hplan.run(hws.data_ptr(), hn, stream=stream)
+    ksteps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(ksteps):
+        hplan.run(hws.data_ptr(), hn, stream=stream)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / ksteps, world, "cuda")
+    hplan.destroy()
+    e2e = {"value": job_value(entries, world, e2e_s), "unit": LK_UNIT, "h2d_bytes_per_step": int(2 * entries),
+           "d2h_bytes_per_step": int(sz * len(jobs)), "ms_per_step": 1e3 * e2e_s, "steps": ksteps}
+    max_l = max((lookup_cube(x) - 1).bit_length() for x in looks)
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": LK_METRIC, "value": value, "unit": LK_UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int16 values, Fr (255-bit) arithmetic", "data": "synthetic",
+        "config": {"workload": WORKLOADS["7b-lookups"] + (f", first {args.layers} layers" if args.layers else ""),
+                   "proofs_per_step": len(jobs), "entries_per_step": entries, "cube_entries_per_step": cube,
+                   "l2": "256 MB buffer written between steps",
+                   "parallelism": f"replicas{world}" if world > 1 else "single GPU",
+                   "phase_ms": {"setup": statistics.mean(p[0] for p in phases),
+                                "batched rounds": statistics.mean(p[1] for p in phases),
+                                "tail rounds + proofs": statistics.mean(p[2] for p in phases)}},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+        "gpu_launches": (5 + 3 * max_l) * args.steps,
+    }))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -458,6 +618,14 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "serve":
         return serve_main(args, rank, world, local)
+    if args.workload == "7b-lookups":
+        cpu = None
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            rate, dt, nj, ent = oracle_lookup_sample(W.GLOBAL_SEED, 1)
+            cpu = {"value": rate, "unit": LK_UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"the two n x r remainder lookups of the first projection ({nj} proofs, {ent} "
+                             f"entries), single process, {dt:.1f} s"}
+        return lookups_main(args, rank, world, local, cpu)
     if args.workload == "7b-update":
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -379,7 +379,9 @@ size_t vl_lookup_plan_workspace_bytes(const vl_lookup_plan* plan);
 int32_t vl_lookup_plan_run(vl_lookup_plan* plan, void* workspace, size_t workspace_bytes, vl_lookup_proof* out,
                            int32_t out_space, void* stream);
 /* Device times (ms) of the last run: ms[0] setup (transcript start, tables,
- * multiplicities, inverses), ms[1] the sumcheck rounds, ms[2] the finish. */
+ * multiplicities, inverses), ms[1] the sumcheck rounds run as batched passes,
+ * ms[2] every proof's last rounds (at most 2^11 pairs) in one block per proof
+ * and the proofs. */
 int32_t vl_lookup_plan_phase_ms(vl_lookup_plan* plan, float ms[3]);
 void vl_lookup_plan_destroy(vl_lookup_plan* plan);
 /* One-shot: plan, run with host output, destroy. */

@@ -221,7 +221,7 @@ struct LinDev {
 // Lookup argument (kernels_lookup.cu): one LkDev per proof, in the workspace.
 static constexpr int LK_MAX_L = VL_LOOKUP_MAX_LOG_D;
 struct LkDev {
-  int32_t n, L, log2_n, sE;        // entries, log2 D, log2 N, low-block variables of eq(u, .)
+  int32_t n, L, log2_n, sE;        // entries, log2 D, log2 N, variables of the low eq block
   int64_t t0;
   uint64_t seed;
   int64_t rows, cols, ld;          // S as stored (row-major, k = row . cols + col)
@@ -229,17 +229,19 @@ struct LkDev {
   uint8_t bind[32];
   Fr beta, alpha, c_nd, Cb;        // Montgomery; c_nd = N / D; Cb = alpha^2 X1 - X2 (table side's cube sum)
   Fr claim, half_t;                // running claim; 2^-t during the high rounds
+  Fr ct;                           // prod_{v < t} eqf(u_v, r_v): eq(u, .) folded by the bound variables
   Fr inv2, inv6;                   // 1/2, 1/6 (Montgomery)
   Fr u[LK_MAX_L], r[LK_MAX_L];     // challenges (Montgomery)
   uint32_t St[8];                  // transcript state (big-endian words)
   int32_t pbeg[LK_MAX_L + 1], pend[LK_MAX_L + 1];  // partial-sum slots of each round (1-based)
   int32_t xbeg, xend;              // slots of the table-side sums X1, X2
-  Fr* lo;                          // eq(u, .) low factors (2^sE, Montgomery)
-  Fr* hi;                          // eq(u, .) high factors (2^(L - sE))
+  int32_t tail, pad_tail;          // first round run by the per-proof tail kernel
+  Fr* loP;                         // eq over the last m variables of u, levels m = 0..sE at offset 2^m - 1
+  Fr* hiP;                         // eq over the last m variables of u_1..u_{L-sE}, levels m = 0..L-sE-1
   Fr* Binv;                        // 1 / (beta + t0 + j), N (gather source, never folded)
   Fr* Tb;                          // beta + t0 + j, N (gather source)
   Fr* WB; Fr* WE; Fr* WT; Fr* WM;  // table-side vectors B, eq(u_low, .), T + beta, m (folded in place)
-  Fr* VA; Fr* VE; Fr* VS;          // folded A, eq(u, .), S + beta, D/2 each
+  Fr* VA; Fr* VS;                  // folded A and S + beta, D/2 each
   uint32_t* counts;                // N multiplicities
   Fr* part;                        // partial sums (12 per slot)
   ProofScratch* scr;               // status
@@ -249,9 +251,12 @@ struct LkItem {
   int32_t proof, k0, k1, slot;
 };
 static constexpr int LK_THREADS = 256;
-static constexpr int LK_PAIRS = 1024;     // pairs per round item
+static constexpr int LK_PPT_LOG = 2;
+static constexpr int LK_PPT = 1 << LK_PPT_LOG;  // pairs per thread in a round pass
+static constexpr int LK_PAIRS = LK_THREADS * LK_PPT;  // pairs per round item
 static constexpr int LK_ENTRIES = 1024;   // table entries per table item (one batch inversion)
 static constexpr int LK_HIST = 8192;      // S entries per histogram item
+static constexpr int LK_TAIL_LOG = 11;    // rounds of at most 2^LK_TAIL_LOG pairs run in one block per proof
 cudaError_t launch_lookup_setup(LkDev* Ls, int np, const LkItem* fac_items, int nfac, const LkItem* hist_items,
                                 int nhist, const LkItem* tab_items, int ntab, cudaStream_t st);
 // Round t: nhi items of proofs in their high rounds, then nlo items of

@@ -11,8 +11,16 @@
 // to g_t(X) is the constant 2^-t . Cb, Cb = alpha^2 sum B Ej T' - sum B m;
 // in the last log2 N rounds its four vectors are folded like the others.
 //
+// E = eq(u, .) is never formed: folded by r_1 .. r_{t-1} it is
+//   E_t(X, k) = c_t . eqf(u_t, X) . eq(u_{t+1..L}, k),
+//   c_t = prod_{v<t} eqf(u_v, r_v), eqf(u, x) = u x + (1 - u)(1 - x),
+// so a pass sums eq(u_{t+1..L}, k) . (A S')(X, k) and the transcript step
+// multiplies by the scalar c_t eqf(u_t, X).  eq(u_{t+1..L}, k) is read from
+// suffix tables: while t binds one of the first L - sE variables it is
+// hiP[k >> sE] . loP_sE[k mod 2^sE], later loP_(L-t)[k].
+//
 // Launches: start (per proof: transcript, beta, alpha, u, N/D, claim),
-// factors (eq(u, .) as hi x lo factor tables and eq(u_low, .)), histogram
+// factors (the suffix eq tables and eq(u_low, .)), histogram
 // (multiplicities, range check), table (batch inversion of beta + T per
 // 1024-entry block, table-side vectors, partial sums of Cb); per round a
 // pass over all proofs' pairs (fold with the previous challenge, then the
@@ -26,6 +34,8 @@ namespace vl {
 namespace {
 
 constexpr uint8_t LBL_BETA = 'b', LBL_ALPHA = 'a';
+constexpr int LK_ROUND_THREADS = 64;  // transcript step: a few partial sums and one serial hash chain
+constexpr int LK_TAIL_THREADS = 128;  // a proof's last rounds: four blocks per SM
 
 __device__ __forceinline__ int lk_table_index(const LkDev& L, int k) {
   if (k >= L.n) return 0;  // padding entries hold t0
@@ -36,12 +46,11 @@ __device__ __forceinline__ int lk_table_index(const LkDev& L, int k) {
   return j < 0 ? 0 : (j >= N ? N - 1 : (int)j);  // out-of-table values were reported; stay in bounds
 }
 
-// A, E, S' at entry k of the unfolded cube.
-__device__ __forceinline__ void lk_level0(const LkDev& L, int k, Fr& a, Fr& e, Fr& s) {
+// A and S' at entry k of the unfolded cube.
+__device__ __forceinline__ void lk_level0(const LkDev& L, int k, Fr& a, Fr& s) {
   const int j = lk_table_index(L, k);
   a = L.Binv[j];
   s = L.Tb[j];
-  e = mont_mul(L.hi[k >> L.sE], L.lo[k & ((1 << L.sE) - 1)]);
 }
 
 __device__ __forceinline__ Fr lk_fold(const Fr& x0, const Fr& x1, const Fr& r) {
@@ -78,6 +87,7 @@ __global__ void __launch_bounds__(LK_THREADS) lk_start_kernel(LkDev* Ls) {
     L->alpha = alpha;
     L->claim = fr_add(alpha, mont_mul(alpha, alpha));
     L->half_t = fr_r1();
+    L->ct = fr_r1();
     Fr c = fr_r1();  // N / D = 2^-(L - log2 N)
     for (int i = 0; i < L->L - L->log2_n; i++) c = mont_mul(c, L->inv2);
     L->c_nd = c;
@@ -87,22 +97,31 @@ __global__ void __launch_bounds__(LK_THREADS) lk_start_kernel(LkDev* Ls) {
   }
 }
 
-// Factor tables: item.slot 0 = lo (2^sE entries over the last sE variables
-// of u), 1 = hi (over the first L - sE), 2 = eq(u_low, .) into WE (over the
-// last log2 N).  Entry j is the product of x or 1 - x per bit (MSB first).
+// Suffix eq tables: item.slot 0 = loP (levels m = 0..sE: eq over the last
+// m variables of u), 1 = hiP (levels m = 0..L-sE-1: eq over the last m of
+// the first L - sE variables), 2 = eq(u_low, .) into WE (the last log2 N).
+// Entry e of a pyramid is level m = floor(log2(e + 1)), index e + 1 - 2^m;
+// its value is the product of x or 1 - x per bit (MSB first).
 __global__ void __launch_bounds__(LK_THREADS) lk_factor_kernel(LkDev* Ls, const LkItem* items) {
   const LkItem it = items[blockIdx.x];
   LkDev* L = Ls + it.proof;
-  const int nv = it.slot == 0 ? L->sE : it.slot == 1 ? L->L - L->sE : L->log2_n;
-  const int base = it.slot == 1 ? 0 : L->L - nv;
-  Fr* out = it.slot == 0 ? L->lo : it.slot == 1 ? L->hi : L->WE;
-  for (int j = it.k0 + threadIdx.x; j < it.k1; j += blockDim.x) {
-    Fr acc = fr_r1();
-    for (int t = 0; t < nv; t++) {
-      const Fr& x = L->u[base + t];
-      acc = mont_mul_ni(acc, ((j >> (nv - 1 - t)) & 1) ? x : fr_sub(fr_r1(), x));
+  Fr* out = it.slot == 0 ? L->loP : it.slot == 1 ? L->hiP : L->WE;
+  const int top = it.slot == 1 ? L->L - L->sE : L->L;  // the suffixes end at variable top - 1 (0-based)
+  for (int e = it.k0 + threadIdx.x; e < it.k1; e += blockDim.x) {
+    int m, i;
+    if (it.slot == 2) {
+      m = L->log2_n;
+      i = e;
+    } else {
+      m = 31 - __clz(e + 1);
+      i = e + 1 - (1 << m);
     }
-    out[j] = acc;
+    Fr acc = fr_r1();
+    for (int t = 0; t < m; t++) {
+      const Fr& x = L->u[top - m + t];
+      acc = mont_mul_ni(acc, ((i >> (m - 1 - t)) & 1) ? x : fr_sub(fr_r1(), x));
+    }
+    out[e] = acc;
   }
 }
 
@@ -200,114 +219,162 @@ __global__ void __launch_bounds__(LK_THREADS) lk_table_kernel(LkDev* Ls, const L
   }
 }
 
-// Round t over pairs [k0, k1) of one proof: fold the vectors with r_{t-1}
-// (the first round reads the unfolded cube, the second folds it on the
-// fly and writes the folded vectors), then the partial sums of
-//   T_X = sum A E S',  A_X = sum A   (X = 0, 2, 3)
-// and, in the table rounds (JR), U_X = sum B Ej T', V_X = sum B m.
-template <bool JR>
-__global__ void __launch_bounds__(LK_THREADS) lk_pass_kernel(LkDev* Ls, int t, const LkItem* items) {
+// One pair (k, k + h) of round t, A side: fold A and S' with r_{t-1} (the
+// first round reads the unfolded cube, the second folds it on the fly and
+// writes the folded vectors, later rounds fold them in place), then add
+// f (A S')(X) to acc[0..2] and A(X) to acc[3..5] for X = 0, 2, 3, where f =
+// eq(u_{t+1..L}, k).  MODE: 0 = first round, 1 = second round, 2 = later.
+template <int MODE>
+__device__ __forceinline__ void lk_pair_a(LkDev* L, int t, int k, int h, const Fr& f, Fr (&acc)[6]) {
+  Fr a0, a1, s0, s1;
+  if constexpr (MODE == 0) {
+    lk_level0(*L, k, a0, s0);
+    lk_level0(*L, k + h, a1, s1);
+    // Unfolded entries have A . S' = 1, so along the line through them
+    // (A S')(X) = (1-X)^2 + X^2 + X(1-X) w with w = a1 s0 + a0 s1:
+    // (A S')(0) = 1, (A S')(2) = 5 - 2w, (A S')(3) = 13 - 6w.  Sum f and f w
+    // here; lk_mode0_sums forms the three sums.
+    const Fr w = fr_add(mont_mul(a1, s0), mont_mul(a0, s1));
+    acc[0] = fr_add(acc[0], f);
+    acc[1] = fr_add(acc[1], mont_mul(f, w));
+  } else {
+    if constexpr (MODE == 1) {
+      const Fr r = L->r[0];
+      Fr xa, xs, ya, ys;
+      lk_level0(*L, k, xa, xs);
+      lk_level0(*L, k + 2 * h, ya, ys);
+      a0 = lk_fold(xa, ya, r);
+      s0 = lk_fold(xs, ys, r);
+      lk_level0(*L, k + h, xa, xs);
+      lk_level0(*L, k + 3 * h, ya, ys);
+      a1 = lk_fold(xa, ya, r);
+      s1 = lk_fold(xs, ys, r);
+    } else {
+      const Fr r = L->r[t - 2];
+      a0 = lk_fold(L->VA[k], L->VA[k + 2 * h], r);
+      s0 = lk_fold(L->VS[k], L->VS[k + 2 * h], r);
+      a1 = lk_fold(L->VA[k + h], L->VA[k + 3 * h], r);
+      s1 = lk_fold(L->VS[k + h], L->VS[k + 3 * h], r);
+    }
+    L->VA[k] = a0, L->VS[k] = s0;
+    L->VA[k + h] = a1, L->VS[k + h] = s1;
+    const Fr ds = fr_sub(s1, s0), da = fr_sub(a1, a0);
+    const Fr s2 = fr_add(s1, ds), a2 = fr_add(a1, da);
+    const Fr s3 = fr_add(s2, ds), a3 = fr_add(a2, da);
+    acc[0] = fr_add(acc[0], mont_mul(f, mont_mul(a0, s0)));
+    acc[1] = fr_add(acc[1], mont_mul(f, mont_mul(a2, s2)));
+    acc[2] = fr_add(acc[2], mont_mul(f, mont_mul(a3, s3)));
+  }
+  const Fr da = fr_sub(a1, a0);
+  const Fr a2 = fr_add(a1, da), a3 = fr_add(a2, da);
+  acc[3] = fr_add(acc[3], a0);
+  acc[4] = fr_add(acc[4], a2);
+  acc[5] = fr_add(acc[5], a3);
+}
+
+// First-round sums from (sum f, sum f w): T_0 = sum f, T_2 = 5 sum f - 2 sum f w,
+// T_3 = 13 sum f - 6 sum f w (linear: valid per thread before the reduction).
+__device__ __forceinline__ void lk_mode0_sums(Fr (&acc)[6]) {
+  const Fr sf = acc[0], sw = acc[1];
+  const Fr sw2 = fr_add(sw, sw), sf4 = fr_add(fr_add(sf, sf), fr_add(sf, sf));
+  acc[1] = fr_sub(fr_add(sf4, sf), sw2);
+  acc[2] = fr_sub(fr_add(fr_add(sf4, sf4), fr_add(sf4, sf)), fr_add(sw2, fr_add(sw2, sw2)));
+}
+
+// One pair of a table round (round tj of the last log2 N): fold B, Ej, T', m
+// (in place after the first table round), add B Ej T' (X) to accb[0..2] and
+// B m (X) to accb[3..5].
+__device__ __forceinline__ void lk_pair_b(LkDev* L, int t, int tj, int k, int h, Fr (&accb)[6]) {
+  Fr b0, b1, q0, q1, u0, u1, m0, m1;  // B, Ej, T', m
+  if (tj == 1) {
+    b0 = L->WB[k], b1 = L->WB[k + h];
+    q0 = L->WE[k], q1 = L->WE[k + h];
+    u0 = L->WT[k], u1 = L->WT[k + h];
+    m0 = L->WM[k], m1 = L->WM[k + h];
+  } else {
+    const Fr r = L->r[t - 2];
+    b0 = lk_fold(L->WB[k], L->WB[k + 2 * h], r);
+    q0 = lk_fold(L->WE[k], L->WE[k + 2 * h], r);
+    u0 = lk_fold(L->WT[k], L->WT[k + 2 * h], r);
+    m0 = lk_fold(L->WM[k], L->WM[k + 2 * h], r);
+    b1 = lk_fold(L->WB[k + h], L->WB[k + 3 * h], r);
+    q1 = lk_fold(L->WE[k + h], L->WE[k + 3 * h], r);
+    u1 = lk_fold(L->WT[k + h], L->WT[k + 3 * h], r);
+    m1 = lk_fold(L->WM[k + h], L->WM[k + 3 * h], r);
+    L->WB[k] = b0, L->WE[k] = q0, L->WT[k] = u0, L->WM[k] = m0;
+    L->WB[k + h] = b1, L->WE[k + h] = q1, L->WT[k + h] = u1, L->WM[k + h] = m1;
+  }
+  const Fr db = fr_sub(b1, b0), dq = fr_sub(q1, q0), du = fr_sub(u1, u0), dm = fr_sub(m1, m0);
+  const Fr b2 = fr_add(b1, db), q2 = fr_add(q1, dq), u2 = fr_add(u1, du), m2 = fr_add(m1, dm);
+  const Fr b3 = fr_add(b2, db), q3 = fr_add(q2, dq), u3 = fr_add(u2, du), m3 = fr_add(m2, dm);
+  accb[0] = fr_add(accb[0], mont_mul(mont_mul(b0, q0), u0));
+  accb[1] = fr_add(accb[1], mont_mul(mont_mul(b2, q2), u2));
+  accb[2] = fr_add(accb[2], mont_mul(mont_mul(b3, q3), u3));
+  accb[3] = fr_add(accb[3], mont_mul(b0, m0));
+  accb[4] = fr_add(accb[4], mont_mul(b2, m2));
+  accb[5] = fr_add(accb[5], mont_mul(b3, m3));
+}
+
+// Where round t reads eq(u_{t+1..L}, k): hiP[k >> sE] . loP_sE[k mod 2^sE]
+// while t binds one of the first L - sE variables (high), loP_(L-t)[k] after.
+struct LkEq {
+  const Fr* f_tab;
+  const Fr* hi_tab;
+  int f_mask;
+  bool high;
+  __device__ LkEq(const LkDev* L, int t) {
+    high = t <= L->L - L->sE;
+    const int mask = (1 << L->sE) - 1;
+    f_tab = high ? L->loP + mask : L->loP + (1 << (L->L - t)) - 1;
+    f_mask = high ? mask : (1 << (L->L - t)) - 1;
+    hi_tab = L->hiP + (high ? (1 << (L->L - L->sE - t)) - 1 : 0);
+  }
+};
+
+// Round t over pairs [k0, k1) of one proof (the rounds before the proof's
+// tail): the partial sums of lk_pair_a (and lk_pair_b in table rounds, JR)
+// into the item's slot.  Warp w of the block takes the 32 LK_PPT pairs from
+// k0 + 32 LK_PPT w, lanes strided by one (coalesced loads).  In a high round
+// with 2^sE >= 32 LK_PPT the warp's pairs lie in one block of 2^sE pairs, so
+// the block's hiP factor multiplies each lane's sums once; with smaller
+// blocks it multiplies every pair's eq factor.
+template <bool JR, int MODE>
+__global__ void __launch_bounds__(LK_THREADS, 2) lk_pass_kernel(LkDev* Ls, int t, const LkItem* items) {
   __shared__ Fr red[6 * (LK_THREADS / 32)];
   const LkItem it = items[blockIdx.x];
   LkDev* L = Ls + it.proof;
   const int h = 1 << (L->L - t);
   const int tj = t - (L->L - L->log2_n);  // table round number (1-based) when JR
+  const LkEq q(L, t);
+  const bool lane_factor = q.high && L->sE >= LK_PPT_LOG + 5;  // the warp's pairs share one hiP entry
+  const int kw = it.k0 + (threadIdx.x >> 5) * (32 * LK_PPT);
   Fr acc[6];
 #pragma unroll
   for (int i = 0; i < 6; i++) acc[i] = fr_zero();
-  Fr accb[JR ? 6 : 1];
+  Fr accb[6];
+  if constexpr (JR) {
 #pragma unroll
-  for (int i = 0; i < (JR ? 6 : 1); i++) accb[i] = fr_zero();
-  for (int k = it.k0 + threadIdx.x; k < it.k1; k += blockDim.x) {
-    Fr a0, a1, e0, e1, s0, s1;
-    if (t == 1) {
-      lk_level0(*L, k, a0, e0, s0);
-      lk_level0(*L, k + h, a1, e1, s1);
-    } else if (t == 2) {
-      const Fr r = L->r[0];
-      Fr xa, xe, xs, ya, ye, ys;
-      lk_level0(*L, k, xa, xe, xs);
-      lk_level0(*L, k + 2 * h, ya, ye, ys);
-      a0 = lk_fold(xa, ya, r);
-      e0 = lk_fold(xe, ye, r);
-      s0 = lk_fold(xs, ys, r);
-      lk_level0(*L, k + h, xa, xe, xs);
-      lk_level0(*L, k + 3 * h, ya, ye, ys);
-      a1 = lk_fold(xa, ya, r);
-      e1 = lk_fold(xe, ye, r);
-      s1 = lk_fold(xs, ys, r);
-      L->VA[k] = a0, L->VE[k] = e0, L->VS[k] = s0;
-      L->VA[k + h] = a1, L->VE[k + h] = e1, L->VS[k + h] = s1;
-    } else {
-      const Fr r = L->r[t - 2];
-      a0 = lk_fold(L->VA[k], L->VA[k + 2 * h], r);
-      e0 = lk_fold(L->VE[k], L->VE[k + 2 * h], r);
-      s0 = lk_fold(L->VS[k], L->VS[k + 2 * h], r);
-      a1 = lk_fold(L->VA[k + h], L->VA[k + 3 * h], r);
-      e1 = lk_fold(L->VE[k + h], L->VE[k + 3 * h], r);
-      s1 = lk_fold(L->VS[k + h], L->VS[k + 3 * h], r);
-      L->VA[k] = a0, L->VE[k] = e0, L->VS[k] = s0;
-      L->VA[k + h] = a1, L->VE[k + h] = e1, L->VS[k + h] = s1;
-    }
-    {
-      const Fr da = fr_sub(a1, a0), de = fr_sub(e1, e0), ds = fr_sub(s1, s0);
-      const Fr a2 = fr_add(a1, da), e2 = fr_add(e1, de), s2 = fr_add(s1, ds);
-      const Fr a3 = fr_add(a2, da), e3 = fr_add(e2, de), s3 = fr_add(s2, ds);
-      acc[0] = fr_add(acc[0], mont_mul(mont_mul(a0, e0), s0));
-      acc[1] = fr_add(acc[1], mont_mul(mont_mul(a2, e2), s2));
-      acc[2] = fr_add(acc[2], mont_mul(mont_mul(a3, e3), s3));
-      acc[3] = fr_add(acc[3], a0);
-      acc[4] = fr_add(acc[4], a2);
-      acc[5] = fr_add(acc[5], a3);
-    }
-    if constexpr (JR) {
-      Fr b0, b1, q0, q1, u0, u1, m0, m1;  // B, Ej, T', m
-      if (tj == 1) {
-        b0 = L->WB[k], b1 = L->WB[k + h];
-        q0 = L->WE[k], q1 = L->WE[k + h];
-        u0 = L->WT[k], u1 = L->WT[k + h];
-        m0 = L->WM[k], m1 = L->WM[k + h];
-      } else {
-        const Fr r = L->r[t - 2];
-        b0 = lk_fold(L->WB[k], L->WB[k + 2 * h], r);
-        q0 = lk_fold(L->WE[k], L->WE[k + 2 * h], r);
-        u0 = lk_fold(L->WT[k], L->WT[k + 2 * h], r);
-        m0 = lk_fold(L->WM[k], L->WM[k + 2 * h], r);
-        b1 = lk_fold(L->WB[k + h], L->WB[k + 3 * h], r);
-        q1 = lk_fold(L->WE[k + h], L->WE[k + 3 * h], r);
-        u1 = lk_fold(L->WT[k + h], L->WT[k + 3 * h], r);
-        m1 = lk_fold(L->WM[k + h], L->WM[k + 3 * h], r);
-        L->WB[k] = b0, L->WE[k] = q0, L->WT[k] = u0, L->WM[k] = m0;
-        L->WB[k + h] = b1, L->WE[k + h] = q1, L->WT[k + h] = u1, L->WM[k + h] = m1;
-      }
-      const Fr db = fr_sub(b1, b0), dq = fr_sub(q1, q0), du = fr_sub(u1, u0), dm = fr_sub(m1, m0);
-      const Fr b2 = fr_add(b1, db), q2 = fr_add(q1, dq), u2 = fr_add(u1, du), m2 = fr_add(m1, dm);
-      const Fr b3 = fr_add(b2, db), q3 = fr_add(q2, dq), u3 = fr_add(u2, du), m3 = fr_add(m2, dm);
-      accb[0] = fr_add(accb[0], mont_mul(mont_mul(b0, q0), u0));
-      accb[1] = fr_add(accb[1], mont_mul(mont_mul(b2, q2), u2));
-      accb[2] = fr_add(accb[2], mont_mul(mont_mul(b3, q3), u3));
-      accb[3] = fr_add(accb[3], mont_mul(b0, m0));
-      accb[4] = fr_add(accb[4], mont_mul(b2, m2));
-      accb[5] = fr_add(accb[5], mont_mul(b3, m3));
-    }
+    for (int i = 0; i < 6; i++) accb[i] = fr_zero();
+  }
+#pragma unroll 1
+  for (int k = kw + (threadIdx.x & 31); k < min(it.k1, kw + 32 * LK_PPT); k += 32) {
+    Fr f = q.f_tab[k & q.f_mask];
+    if (q.high && !lane_factor) f = mont_mul(f, q.hi_tab[k >> L->sE]);
+    lk_pair_a<MODE>(L, t, k, h, f, acc);
+    if constexpr (JR) lk_pair_b(L, t, tj, k, h, accb);
+  }
+  if constexpr (MODE == 0) lk_mode0_sums(acc);
+  if (lane_factor && kw < it.k1) {  // the eq factor over the remaining high variables
+    const Fr hf = q.hi_tab[kw >> L->sE];
+    for (int i = 0; i < 3; i++) acc[i] = mont_mul_ni(acc[i], hf);
   }
   block_sum_fr<6>(acc, red);
-  if (threadIdx.x < 6) {
-    Fr v = acc[0];
-#pragma unroll
-    for (int i = 1; i < 6; i++)
-      if (threadIdx.x == i) v = acc[i];
-    L->part[(size_t)it.slot * 12 + threadIdx.x] = v;
-  }
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 6; i++) L->part[(size_t)it.slot * 12 + i] = acc[i];
   if constexpr (JR) {
     block_sum_fr<6>(accb, red);
-    if (threadIdx.x < 6) {
-      Fr v = accb[0];
-#pragma unroll
-      for (int i = 1; i < 6; i++)
-        if (threadIdx.x == i) v = accb[i];
-      L->part[(size_t)it.slot * 12 + 6 + threadIdx.x] = v;
-    }
+    if (threadIdx.x == 0)
+      for (int i = 0; i < 6; i++) L->part[(size_t)it.slot * 12 + 6 + i] = accb[i];
   }
 }
 
@@ -326,28 +393,77 @@ __device__ Fr lk_cubic(const Fr (&g)[4], const Fr& r, const Fr& inv2, const Fr& 
   return fr_add(s, mont_mul_ni(g[3], l3));
 }
 
-// Round t of one proof (one block each): the round polynomial from the
-// partial sums, its values in the proof, absorb, squeeze r_t, new claim.
-__global__ void __launch_bounds__(LK_THREADS) lk_round_kernel(LkDev* Ls, int t, vl_lookup_proof* outs) {
-  __shared__ Fr red[6 * (LK_THREADS / 32)];
+// The round polynomial of round t from the summed partials (thread 0):
+// g(X) = alpha c_t eqf(u_t, X) T_X + A_X + table side, g(1) = claim - g(0);
+// the values go into the proof and are absorbed ('g': g0, g2, g3) into Sw.
+__device__ void lk_step_g(LkDev* L, int t, const Fr (&acc)[6], const Fr (&accb)[6], bool jr, vl_lookup_proof* out,
+                          Fr (&g)[4], uint32_t (&Sw)[8]) {
+  const Fr alpha = L->alpha, a2 = mont_mul_ni(alpha, alpha);
+  Fr tab[3];
+  if (jr) {
+    for (int i = 0; i < 3; i++) tab[i] = mont_mul_ni(L->c_nd, fr_sub(mont_mul_ni(a2, accb[i]), accb[3 + i]));
+  } else {
+    L->half_t = mont_mul_ni(L->half_t, L->inv2);
+    const Fr c = mont_mul_ni(L->half_t, L->Cb);
+    tab[0] = tab[1] = tab[2] = c;
+  }
+  // alpha c_t eqf(u_t, X) for X = 0, 2, 3: eqf(u, X) = (1 - u) + X (2u - 1)
+  const Fr ut = L->u[t - 1], one = fr_r1();
+  const Fr e0 = fr_sub(one, ut), d = fr_sub(fr_add(ut, ut), one);
+  const Fr e2 = fr_add(e0, fr_add(d, d)), e3 = fr_add(e2, d);
+  const Fr ac = mont_mul_ni(alpha, L->ct);
+  g[0] = fr_add(fr_add(mont_mul_ni(mont_mul_ni(ac, e0), acc[0]), acc[3]), tab[0]);
+  g[2] = fr_add(fr_add(mont_mul_ni(mont_mul_ni(ac, e2), acc[1]), acc[4]), tab[1]);
+  g[3] = fr_add(fr_add(mont_mul_ni(mont_mul_ni(ac, e3), acc[2]), acc[5]), tab[2]);
+  g[1] = fr_sub(L->claim, g[0]);
+  Fr gc[3];
+  for (int i = 0; i < 4; i++) {
+    const Fr c = from_mont_ni(g[i]);
+    for (int l = 0; l < 8; l++) out->g[t - 1][i].limb[l] = c.v[l];
+    if (i != 1) gc[i == 0 ? 0 : i - 1] = c;
+  }
+  uint32_t S[8];
+  for (int i = 0; i < 8; i++) S[i] = L->St[i];
+  dev_absorb_fr<3>(S, LBL_G, gc);
+  for (int i = 0; i < 8; i++) Sw[i] = S[i];
+}
+
+// After the squeeze of r_t (thread 0): store r_t and the state, fold c_t,
+// the new claim g(r_t).
+__device__ void lk_step_r(LkDev* L, int t, const Fr& r, const uint32_t (&Sn)[8], const Fr (&g)[4]) {
+  L->r[t - 1] = r;
+  for (int i = 0; i < 8; i++) L->St[i] = Sn[i];
+  const Fr ut = L->u[t - 1], one = fr_r1();
+  L->ct = mont_mul_ni(L->ct, fr_add(mont_mul_ni(ut, r), mont_mul_ni(fr_sub(one, ut), fr_sub(one, r))));
+  L->claim = lk_cubic(g, r, L->inv2, L->inv6);
+}
+
+// The table side's cube sum Cb = alpha^2 X1 - X2 from the table kernel's
+// partials (block-wide).
+__device__ void lk_table_sum(LkDev* L, Fr* red) {
+  Fr x[2] = {fr_zero(), fr_zero()};
+  for (int s = L->xbeg + threadIdx.x; s < L->xend; s += blockDim.x) {
+    x[0] = fr_add(x[0], L->part[(size_t)s * 12]);
+    x[1] = fr_add(x[1], L->part[(size_t)s * 12 + 1]);
+  }
+  block_sum_fr<2>(x, red);
+  if (threadIdx.x == 0) L->Cb = fr_sub(mont_mul_ni(mont_mul_ni(L->alpha, L->alpha), x[0]), x[1]);
+  __syncthreads();
+}
+
+// Round t of one proof before its tail (one block each): the round
+// polynomial from the partial sums, absorb, squeeze r_t, new claim.
+__global__ void __launch_bounds__(LK_ROUND_THREADS) lk_round_kernel(LkDev* Ls, int t, vl_lookup_proof* outs) {
+  __shared__ Fr red[6 * (LK_ROUND_THREADS / 32)];
   __shared__ uint32_t Sw[8], Sn[8];
   __shared__ uint32_t dig[3][8];
   __shared__ Fr rch[1];
   __shared__ Fr gsh[4];
   LkDev* L = Ls + blockIdx.x;
-  if (t > L->L) return;
+  if (t >= L->tail) return;
   const int tid = threadIdx.x;
   const bool jr = t > L->L - L->log2_n;
-  if (t == 1) {  // the table side's cube sum, from the table kernel's partials
-    Fr x[2] = {fr_zero(), fr_zero()};
-    for (int s = L->xbeg + tid; s < L->xend; s += blockDim.x) {
-      x[0] = fr_add(x[0], L->part[(size_t)s * 12]);
-      x[1] = fr_add(x[1], L->part[(size_t)s * 12 + 1]);
-    }
-    block_sum_fr<2>(x, red);
-    if (tid == 0) L->Cb = fr_sub(mont_mul_ni(mont_mul_ni(L->alpha, L->alpha), x[0]), x[1]);
-    __syncthreads();
-  }
+  if (t == 1) lk_table_sum(L, red);
   Fr acc[6], accb[6];
   for (int i = 0; i < 6; i++) acc[i] = accb[i] = fr_zero();
   for (int s = L->pbeg[t] + tid; s < L->pend[t]; s += blockDim.x) {
@@ -358,61 +474,36 @@ __global__ void __launch_bounds__(LK_THREADS) lk_round_kernel(LkDev* Ls, int t, 
   block_sum_fr<6>(acc, red);
   if (jr) block_sum_fr<6>(accb, red);
   if (tid == 0) {
-    const Fr alpha = L->alpha, a2 = mont_mul_ni(alpha, alpha);
-    Fr tab[3];
-    if (jr) {
-      for (int i = 0; i < 3; i++) tab[i] = mont_mul_ni(L->c_nd, fr_sub(mont_mul_ni(a2, accb[i]), accb[3 + i]));
-    } else {
-      L->half_t = mont_mul_ni(L->half_t, L->inv2);
-      const Fr c = mont_mul_ni(L->half_t, L->Cb);
-      tab[0] = tab[1] = tab[2] = c;
-    }
     Fr g[4];
-    g[0] = fr_add(fr_add(mont_mul_ni(alpha, acc[0]), acc[3]), tab[0]);
-    g[2] = fr_add(fr_add(mont_mul_ni(alpha, acc[1]), acc[4]), tab[1]);
-    g[3] = fr_add(fr_add(mont_mul_ni(alpha, acc[2]), acc[5]), tab[2]);
-    g[1] = fr_sub(L->claim, g[0]);
-    Fr gc[3];
-    vl_lookup_proof* out = outs + blockIdx.x;
-    for (int i = 0; i < 4; i++) {
-      gsh[i] = g[i];
-      const Fr c = from_mont_ni(g[i]);
-      for (int l = 0; l < 8; l++) out->g[t - 1][i].limb[l] = c.v[l];
-      if (i != 1) gc[i == 0 ? 0 : i - 1] = c;
-    }
     uint32_t S[8];
-    for (int i = 0; i < 8; i++) S[i] = L->St[i];
-    dev_absorb_fr<3>(S, LBL_G, gc);
+    lk_step_g(L, t, acc, accb, jr, outs + blockIdx.x, g, S);
+    for (int i = 0; i < 4; i++) gsh[i] = g[i];
     for (int i = 0; i < 8; i++) Sw[i] = S[i];
   }
   __syncthreads();
   squeeze_dev(Sw, LBL_R, 1, rch, Sn, dig);
   if (tid == 0) {
-    const Fr r = rch[0];
-    L->r[t - 1] = r;
-    for (int i = 0; i < 8; i++) L->St[i] = Sn[i];
     const Fr g[4] = {gsh[0], gsh[1], gsh[2], gsh[3]};
-    L->claim = lk_cubic(g, r, L->inv2, L->inv6);
+    uint32_t S[8];
+    for (int i = 0; i < 8; i++) S[i] = Sn[i];
+    lk_step_r(L, t, rch[0], S, g);
   }
 }
 
-// One block per proof: the final evaluations (the last pair folded with
-// r_L), absorb 'f', the proof.
-__global__ void __launch_bounds__(LK_THREADS) lk_finish_kernel(LkDev* Ls, vl_lookup_proof* outs) {
-  LkDev* L = Ls + blockIdx.x;
-  vl_lookup_proof* out = outs + blockIdx.x;
-  const int tid = threadIdx.x;
-  for (int i = tid; i < (VL_LOOKUP_MAX_LOG_D - L->L) * 32; i += blockDim.x)  // unused rounds
+// The final evaluations (the last pair folded with r_L), absorb 'f', the
+// proof (thread 0; the other threads zero the unused rounds first).
+__device__ void lk_finish(LkDev* L, vl_lookup_proof* out) {
+  for (int i = threadIdx.x; i < (VL_LOOKUP_MAX_LOG_D - L->L) * 32; i += blockDim.x)  // unused rounds
     out->g[L->L + i / 32][(i / 8) & 3].limb[i & 7] = 0u;
-  if (tid != 0) return;
-  Fr a, e, s, b, m;
+  if (threadIdx.x != 0) return;
+  Fr a, s, b, m;
   const int Lp = L->L;
   if (Lp == 0) {
-    lk_level0(*L, 0, a, e, s);
+    lk_level0(*L, 0, a, s);
   } else if (Lp == 1) {
-    Fr a1, e1, s1;
-    lk_level0(*L, 0, a, e, s);
-    lk_level0(*L, 1, a1, e1, s1);
+    Fr a1, s1;
+    lk_level0(*L, 0, a, s);
+    lk_level0(*L, 1, a1, s1);
     a = lk_fold(a, a1, L->r[0]);
     s = lk_fold(s, s1, L->r[0]);
   } else {
@@ -445,6 +536,57 @@ __global__ void __launch_bounds__(LK_THREADS) lk_finish_kernel(LkDev* Ls, vl_loo
   out->status = L->scr->status;
 }
 
+// One block per proof: its rounds from L->tail on (at most 2^LK_TAIL_LOG
+// pairs each), each a pass over the pairs, a block reduction and the
+// transcript step in this block, then the final evaluations and the proof.
+__global__ void __launch_bounds__(LK_TAIL_THREADS, 4) lk_tail_kernel(LkDev* Ls, vl_lookup_proof* outs) {
+  __shared__ Fr red[6 * (LK_TAIL_THREADS / 32)];
+  __shared__ uint32_t Sw[8], Sn[8];
+  __shared__ uint32_t dig[3][8];
+  __shared__ Fr rch[1];
+  __shared__ Fr gsh[4];
+  LkDev* L = Ls + blockIdx.x;
+  vl_lookup_proof* out = outs + blockIdx.x;
+  const int tid = threadIdx.x;
+  if (L->tail == 1 && L->L >= 1) lk_table_sum(L, red);
+  for (int t = L->tail; t <= L->L; t++) {
+    const int h = 1 << (L->L - t);
+    const bool jr = t > L->L - L->log2_n;
+    const int tj = t - (L->L - L->log2_n);
+    const LkEq q(L, t);
+    Fr acc[6], accb[6];
+    for (int i = 0; i < 6; i++) acc[i] = accb[i] = fr_zero();
+    for (int k = tid; k < h; k += blockDim.x) {
+      Fr f = q.f_tab[k & q.f_mask];
+      if (q.high) f = mont_mul(f, q.hi_tab[k >> L->sE]);
+      if (t == 1) lk_pair_a<0>(L, t, k, h, f, acc);
+      else if (t == 2) lk_pair_a<1>(L, t, k, h, f, acc);
+      else lk_pair_a<2>(L, t, k, h, f, acc);
+      if (jr) lk_pair_b(L, t, tj, k, h, accb);
+    }
+    if (t == 1) lk_mode0_sums(acc);
+    block_sum_fr<6>(acc, red);
+    if (jr) block_sum_fr<6>(accb, red);
+    if (tid == 0) {
+      Fr g[4];
+      uint32_t S[8];
+      lk_step_g(L, t, acc, accb, jr, out, g, S);
+      for (int i = 0; i < 4; i++) gsh[i] = g[i];
+      for (int i = 0; i < 8; i++) Sw[i] = S[i];
+    }
+    __syncthreads();
+    squeeze_dev(Sw, LBL_R, 1, rch, Sn, dig);
+    if (tid == 0) {
+      const Fr g[4] = {gsh[0], gsh[1], gsh[2], gsh[3]};
+      uint32_t S[8];
+      for (int i = 0; i < 8; i++) S[i] = Sn[i];
+      lk_step_r(L, t, rch[0], S, g);
+    }
+    __syncthreads();  // r_t and the folded vectors are visible to the next round
+  }
+  lk_finish(L, out);
+}
+
 }  // namespace
 
 cudaError_t launch_lookup_setup(LkDev* Ls, int np, const LkItem* fac_items, int nfac, const LkItem* hist_items,
@@ -458,14 +600,22 @@ cudaError_t launch_lookup_setup(LkDev* Ls, int np, const LkItem* fac_items, int 
 
 cudaError_t launch_lookup_round(LkDev* Ls, int np, int t, const LkItem* items, int nhi, int nlo,
                                 vl_lookup_proof* out, cudaStream_t st) {
-  if (nhi) lk_pass_kernel<false><<<nhi, LK_THREADS, 0, st>>>(Ls, t, items);
-  if (nlo) lk_pass_kernel<true><<<nlo, LK_THREADS, 0, st>>>(Ls, t, items + nhi);
-  lk_round_kernel<<<np, LK_THREADS, 0, st>>>(Ls, t, out);
+  if (nhi) {
+    if (t == 1) lk_pass_kernel<false, 0><<<nhi, LK_THREADS, 0, st>>>(Ls, t, items);
+    else if (t == 2) lk_pass_kernel<false, 1><<<nhi, LK_THREADS, 0, st>>>(Ls, t, items);
+    else lk_pass_kernel<false, 2><<<nhi, LK_THREADS, 0, st>>>(Ls, t, items);
+  }
+  if (nlo) {
+    if (t == 1) lk_pass_kernel<true, 0><<<nlo, LK_THREADS, 0, st>>>(Ls, t, items + nhi);
+    else if (t == 2) lk_pass_kernel<true, 1><<<nlo, LK_THREADS, 0, st>>>(Ls, t, items + nhi);
+    else lk_pass_kernel<true, 2><<<nlo, LK_THREADS, 0, st>>>(Ls, t, items + nhi);
+  }
+  lk_round_kernel<<<np, LK_ROUND_THREADS, 0, st>>>(Ls, t, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_lookup_finish(LkDev* Ls, int np, vl_lookup_proof* out, cudaStream_t st) {
-  lk_finish_kernel<<<np, LK_THREADS, 0, st>>>(Ls, out);
+  lk_tail_kernel<<<np, LK_TAIL_THREADS, 0, st>>>(Ls, out);
   return cudaGetLastError();
 }
 

@@ -42,8 +42,7 @@ int check_job(const vl_lookup_job& J) {
 }
 
 struct LkBufs {
-  size_t lo = 0, hi = 0, binv = 0, tb = 0, wb = 0, we = 0, wt = 0, wm = 0, va = 0, ve = 0, vs = 0, counts = 0,
-         stage = 0;
+  size_t lop = 0, hip = 0, binv = 0, tb = 0, wb = 0, we = 0, wt = 0, wm = 0, va = 0, vs = 0, counts = 0, stage = 0;
 };
 
 int cuda_fail(const char* where, cudaError_t e) {
@@ -57,7 +56,7 @@ int cuda_fail(const char* where, cudaError_t e) {
 
 struct vl_lookup_plan {
   std::vector<vl_lookup_job> jobs;
-  int np = 0, maxL = 0, nslots = 0;
+  int np = 0, maxL = 0, nslots = 0, nrounds = 0;
   std::vector<LkDev> Ls;  // statements; device pointers filled at bind time
   std::vector<LkBufs> buf;
   std::vector<LkItem> fac, hist, tab, rounds;
@@ -105,10 +104,12 @@ int lk_build(vl_lookup_plan* P, const vl_lookup_job* jobs, int32_t njobs) {
     std::memcpy(L.bind, J.bind, 32);
     L.inv2 = inv2;
     L.inv6 = inv6;
+    L.tail = std::max(1, L.L - LK_TAIL_LOG);  // rounds with h = 2^(L-t) <= 2^LK_TAIL_LOG pairs
+    if (L.L == 0) L.tail = 1;
     P->maxL = std::max(P->maxL, L.L);
     const int N = 1 << L.log2_n;
-    // factor tables: lo, hi, eq(u_low, .)
-    const int sizes[3] = {1 << L.sE, 1 << (L.L - L.sE), N};
+    // suffix eq tables (loP: levels 0..sE; hiP: levels 0..L-sE-1) and eq(u_low, .)
+    const int sizes[3] = {(2 << L.sE) - 1, (1 << (L.L - L.sE)) - 1, N};
     for (int w = 0; w < 3; w++)
       for (int k0 = 0; k0 < sizes[w]; k0 += LK_THREADS * 4)
         P->fac.push_back(LkItem{i, k0, std::min(sizes[w], k0 + LK_THREADS * 4), w});
@@ -126,7 +127,7 @@ int lk_build(vl_lookup_plan* P, const vl_lookup_job* jobs, int32_t njobs) {
     for (int pass = 0; pass < 2; pass++)
       for (int i = 0; i < njobs; i++) {
         LkDev& L = P->Ls[i];
-        if (t > L.L) continue;
+        if (t >= L.tail) continue;  // the tail kernel runs this proof's later rounds
         const bool jr = t > L.L - L.log2_n;
         if (jr != (pass == 1)) continue;
         const int h = 1 << (L.L - t);
@@ -139,6 +140,8 @@ int lk_build(vl_lookup_plan* P, const vl_lookup_job* jobs, int32_t njobs) {
       }
   }
   P->nslots = slot;
+  P->nrounds = 0;  // rounds before the tails
+  for (const LkDev& L : P->Ls) P->nrounds = std::max(P->nrounds, L.tail - 1);
   // workspace layout
   size_t off = 0;
   auto take = [&off](size_t bytes) {
@@ -166,8 +169,8 @@ int lk_build(vl_lookup_plan* P, const vl_lookup_job* jobs, int32_t njobs) {
     const LkDev& L = P->Ls[i];
     LkBufs& b = P->buf[i];
     const size_t N = (size_t)1 << L.log2_n, half = std::max<size_t>(1, ((size_t)1 << L.L) / 2);
-    b.lo = take(sizeof(Fr) << L.sE);
-    b.hi = take(sizeof(Fr) << (L.L - L.sE));
+    b.lop = take(sizeof(Fr) * ((2u << L.sE) - 1));
+    b.hip = take(sizeof(Fr) * std::max<size_t>(1, (1u << (L.L - L.sE)) - 1));
     b.binv = take(sizeof(Fr) * N);
     b.tb = take(sizeof(Fr) * N);
     b.wb = take(sizeof(Fr) * N);
@@ -175,7 +178,6 @@ int lk_build(vl_lookup_plan* P, const vl_lookup_job* jobs, int32_t njobs) {
     b.wt = take(sizeof(Fr) * N);
     b.wm = take(sizeof(Fr) * N);
     b.va = take(sizeof(Fr) * half);
-    b.ve = take(sizeof(Fr) * half);
     b.vs = take(sizeof(Fr) * half);
     if (jobs[i].S.space == VL_HOST) b.stage = take(sizeof(int16_t) * (size_t)L.n);
   }
@@ -190,8 +192,8 @@ int lk_bind(vl_lookup_plan* P, uint8_t* ws, cudaStream_t st) {
     const vl_lookup_job& J = P->jobs[i];
     L.S = J.S.space == VL_HOST ? reinterpret_cast<const int16_t*>(ws + b.stage)
                                : static_cast<const int16_t*>(J.S.data);
-    L.lo = reinterpret_cast<Fr*>(ws + b.lo);
-    L.hi = reinterpret_cast<Fr*>(ws + b.hi);
+    L.loP = reinterpret_cast<Fr*>(ws + b.lop);
+    L.hiP = reinterpret_cast<Fr*>(ws + b.hip);
     L.Binv = reinterpret_cast<Fr*>(ws + b.binv);
     L.Tb = reinterpret_cast<Fr*>(ws + b.tb);
     L.WB = reinterpret_cast<Fr*>(ws + b.wb);
@@ -199,7 +201,6 @@ int lk_bind(vl_lookup_plan* P, uint8_t* ws, cudaStream_t st) {
     L.WT = reinterpret_cast<Fr*>(ws + b.wt);
     L.WM = reinterpret_cast<Fr*>(ws + b.wm);
     L.VA = reinterpret_cast<Fr*>(ws + b.va);
-    L.VE = reinterpret_cast<Fr*>(ws + b.ve);
     L.VS = reinterpret_cast<Fr*>(ws + b.vs);
     L.counts = reinterpret_cast<uint32_t*>(ws + P->off_counts + b.counts);
     L.part = reinterpret_cast<Fr*>(ws + P->off_part);
@@ -283,7 +284,7 @@ extern "C" int32_t vl_lookup_plan_run(vl_lookup_plan* P, void* workspace, size_t
     ce = launch_lookup_setup(dL, P->np, items(P->off_fac), (int)P->fac.size(), items(P->off_hist),
                              (int)P->hist.size(), items(P->off_tab), (int)P->tab.size(), st);
   if (ce == cudaSuccess) ce = cudaEventRecord(P->ev[1], st);
-  for (int t = 1; t <= P->maxL && ce == cudaSuccess; t++)
+  for (int t = 1; t <= P->nrounds && ce == cudaSuccess; t++)
     ce = launch_lookup_round(dL, P->np, t, items(P->off_rounds) + P->roff[t], P->nhi[t], P->nlo[t], dout, st);
   if (ce == cudaSuccess) ce = cudaEventRecord(P->ev[2], st);
   if (ce == cudaSuccess) ce = launch_lookup_finish(dL, P->np, dout, st);
