@@ -230,6 +230,7 @@ struct LkDev {
   Fr beta, alpha, c_nd, Cb;        // Montgomery; c_nd = N / D; Cb = alpha^2 X1 - X2 (table side's cube sum)
   Fr claim, half_t;                // running claim; 2^-t during the high rounds
   Fr ct;                           // prod_{v < t} eqf(u_v, r_v): eq(u, .) folded by the bound variables
+  Fr ctj;                          // the same product over the bound table variables (eq(u_low, .))
   Fr inv2, inv6;                   // 1/2, 1/6 (Montgomery)
   Fr u[LK_MAX_L], r[LK_MAX_L];     // challenges (Montgomery)
   uint32_t St[8];                  // transcript state (big-endian words)
@@ -240,7 +241,7 @@ struct LkDev {
   Fr* hiP;                         // eq over the last m variables of u_1..u_{L-sE}, levels m = 0..L-sE-1
   Fr* Binv;                        // 1 / (beta + t0 + j), N (gather source, never folded)
   Fr* Tb;                          // beta + t0 + j, N (gather source)
-  Fr* WB; Fr* WE; Fr* WT; Fr* WM;  // table-side vectors B, eq(u_low, .), T + beta, m (folded in place)
+  Fr* WB; Fr* WE; Fr* WT; Fr* WM;  // table side: B, eq(u_low, .) (for Cb only), T + beta, m (folded in place)
   Fr* VA; Fr* VS;                  // folded A and S + beta, D/2 each
   uint32_t* counts;                // N multiplicities
   Fr* part;                        // partial sums (12 per slot)

@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(LK_THREADS) lk_start_kernel(LkDev* Ls) {
     L->claim = fr_add(alpha, mont_mul(alpha, alpha));
     L->half_t = fr_r1();
     L->ct = fr_r1();
+    L->ctj = fr_r1();
     Fr c = fr_r1();  // N / D = 2^-(L - log2 N)
     for (int i = 0; i < L->L - L->log2_n; i++) c = mont_mul(c, L->inv2);
     L->c_nd = c;
@@ -281,35 +282,42 @@ __device__ __forceinline__ void lk_mode0_sums(Fr (&acc)[6]) {
   acc[2] = fr_sub(fr_add(fr_add(sf4, sf4), fr_add(sf4, sf)), fr_add(sw2, fr_add(sw2, sw2)));
 }
 
-// One pair of a table round (round tj of the last log2 N): fold B, Ej, T', m
-// (in place after the first table round), add B Ej T' (X) to accb[0..2] and
-// B m (X) to accb[3..5].
-__device__ __forceinline__ void lk_pair_b(LkDev* L, int t, int tj, int k, int h, Fr (&accb)[6]) {
-  Fr b0, b1, q0, q1, u0, u1, m0, m1;  // B, Ej, T', m
+// One pair of a table round (round tj of the last log2 N).  eq(u_low, .)
+// folded by the bound table variables is c'_t eqf(u_t, X) eq(u_{t+1..L}, k),
+// the A side's factor f times a scalar of the transcript step, so only B,
+// T' and m are folded (in place after the first table round).  Adds
+// f (B T')(X) to accb[0..2] and (B m)(X) to accb[3..5]; in the first table
+// round B T' = 1 on the unfolded entries, so as for the A side only f and
+// f w' (w' = b1 u0 + b0 u1) are summed (lk_mode0_sums forms the three).
+__device__ __forceinline__ void lk_pair_b(LkDev* L, int t, int tj, int k, int h, const Fr& f, Fr (&accb)[6]) {
+  Fr b0, b1, u0, u1, m0, m1;  // B, T', m
   if (tj == 1) {
     b0 = L->WB[k], b1 = L->WB[k + h];
-    q0 = L->WE[k], q1 = L->WE[k + h];
     u0 = L->WT[k], u1 = L->WT[k + h];
     m0 = L->WM[k], m1 = L->WM[k + h];
+    const Fr w = fr_add(mont_mul(b1, u0), mont_mul(b0, u1));
+    accb[0] = fr_add(accb[0], f);
+    accb[1] = fr_add(accb[1], mont_mul(f, w));
   } else {
     const Fr r = L->r[t - 2];
     b0 = lk_fold(L->WB[k], L->WB[k + 2 * h], r);
-    q0 = lk_fold(L->WE[k], L->WE[k + 2 * h], r);
     u0 = lk_fold(L->WT[k], L->WT[k + 2 * h], r);
     m0 = lk_fold(L->WM[k], L->WM[k + 2 * h], r);
     b1 = lk_fold(L->WB[k + h], L->WB[k + 3 * h], r);
-    q1 = lk_fold(L->WE[k + h], L->WE[k + 3 * h], r);
     u1 = lk_fold(L->WT[k + h], L->WT[k + 3 * h], r);
     m1 = lk_fold(L->WM[k + h], L->WM[k + 3 * h], r);
-    L->WB[k] = b0, L->WE[k] = q0, L->WT[k] = u0, L->WM[k] = m0;
-    L->WB[k + h] = b1, L->WE[k + h] = q1, L->WT[k + h] = u1, L->WM[k + h] = m1;
+    L->WB[k] = b0, L->WT[k] = u0, L->WM[k] = m0;
+    L->WB[k + h] = b1, L->WT[k + h] = u1, L->WM[k + h] = m1;
+    const Fr du = fr_sub(u1, u0), db = fr_sub(b1, b0);
+    const Fr u2 = fr_add(u1, du), b2 = fr_add(b1, db);
+    const Fr u3 = fr_add(u2, du), b3 = fr_add(b2, db);
+    accb[0] = fr_add(accb[0], mont_mul(f, mont_mul(b0, u0)));
+    accb[1] = fr_add(accb[1], mont_mul(f, mont_mul(b2, u2)));
+    accb[2] = fr_add(accb[2], mont_mul(f, mont_mul(b3, u3)));
   }
-  const Fr db = fr_sub(b1, b0), dq = fr_sub(q1, q0), du = fr_sub(u1, u0), dm = fr_sub(m1, m0);
-  const Fr b2 = fr_add(b1, db), q2 = fr_add(q1, dq), u2 = fr_add(u1, du), m2 = fr_add(m1, dm);
-  const Fr b3 = fr_add(b2, db), q3 = fr_add(q2, dq), u3 = fr_add(u2, du), m3 = fr_add(m2, dm);
-  accb[0] = fr_add(accb[0], mont_mul(mont_mul(b0, q0), u0));
-  accb[1] = fr_add(accb[1], mont_mul(mont_mul(b2, q2), u2));
-  accb[2] = fr_add(accb[2], mont_mul(mont_mul(b3, q3), u3));
+  const Fr db = fr_sub(b1, b0), dm = fr_sub(m1, m0);
+  const Fr b2 = fr_add(b1, db), m2 = fr_add(m1, dm);
+  const Fr b3 = fr_add(b2, db), m3 = fr_add(m2, dm);
   accb[3] = fr_add(accb[3], mont_mul(b0, m0));
   accb[4] = fr_add(accb[4], mont_mul(b2, m2));
   accb[5] = fr_add(accb[5], mont_mul(b3, m3));
@@ -361,12 +369,16 @@ __global__ void __launch_bounds__(LK_THREADS, 2) lk_pass_kernel(LkDev* Ls, int t
     Fr f = q.f_tab[k & q.f_mask];
     if (q.high && !lane_factor) f = mont_mul(f, q.hi_tab[k >> L->sE]);
     lk_pair_a<MODE>(L, t, k, h, f, acc);
-    if constexpr (JR) lk_pair_b(L, t, tj, k, h, accb);
+    if constexpr (JR) lk_pair_b(L, t, tj, k, h, f, accb);
   }
   if constexpr (MODE == 0) lk_mode0_sums(acc);
+  if constexpr (JR)
+    if (tj == 1) lk_mode0_sums(accb);
   if (lane_factor && kw < it.k1) {  // the eq factor over the remaining high variables
     const Fr hf = q.hi_tab[kw >> L->sE];
     for (int i = 0; i < 3; i++) acc[i] = mont_mul_ni(acc[i], hf);
+    if constexpr (JR)
+      for (int i = 0; i < 3; i++) accb[i] = mont_mul_ni(accb[i], hf);
   }
   block_sum_fr<6>(acc, red);
   if (threadIdx.x == 0)
@@ -399,18 +411,21 @@ __device__ Fr lk_cubic(const Fr (&g)[4], const Fr& r, const Fr& inv2, const Fr& 
 __device__ void lk_step_g(LkDev* L, int t, const Fr (&acc)[6], const Fr (&accb)[6], bool jr, vl_lookup_proof* out,
                           Fr (&g)[4], uint32_t (&Sw)[8]) {
   const Fr alpha = L->alpha, a2 = mont_mul_ni(alpha, alpha);
+  // eqf(u_t, X) for X = 0, 2, 3: eqf(u, X) = (1 - u) + X (2u - 1)
+  const Fr ut = L->u[t - 1], one = fr_r1();
+  const Fr e0 = fr_sub(one, ut), d = fr_sub(fr_add(ut, ut), one);
+  const Fr e2 = fr_add(e0, fr_add(d, d)), e3 = fr_add(e2, d);
   Fr tab[3];
-  if (jr) {
-    for (int i = 0; i < 3; i++) tab[i] = mont_mul_ni(L->c_nd, fr_sub(mont_mul_ni(a2, accb[i]), accb[3 + i]));
+  if (jr) {  // (N/D) (alpha^2 c'_t eqf(u_t, X) U_X - V_X)
+    const Fr ac2 = mont_mul_ni(a2, L->ctj);
+    const Fr ex[3] = {e0, e2, e3};
+    for (int i = 0; i < 3; i++)
+      tab[i] = mont_mul_ni(L->c_nd, fr_sub(mont_mul_ni(mont_mul_ni(ac2, ex[i]), accb[i]), accb[3 + i]));
   } else {
     L->half_t = mont_mul_ni(L->half_t, L->inv2);
     const Fr c = mont_mul_ni(L->half_t, L->Cb);
     tab[0] = tab[1] = tab[2] = c;
   }
-  // alpha c_t eqf(u_t, X) for X = 0, 2, 3: eqf(u, X) = (1 - u) + X (2u - 1)
-  const Fr ut = L->u[t - 1], one = fr_r1();
-  const Fr e0 = fr_sub(one, ut), d = fr_sub(fr_add(ut, ut), one);
-  const Fr e2 = fr_add(e0, fr_add(d, d)), e3 = fr_add(e2, d);
   const Fr ac = mont_mul_ni(alpha, L->ct);
   g[0] = fr_add(fr_add(mont_mul_ni(mont_mul_ni(ac, e0), acc[0]), acc[3]), tab[0]);
   g[2] = fr_add(fr_add(mont_mul_ni(mont_mul_ni(ac, e2), acc[1]), acc[4]), tab[1]);
@@ -434,7 +449,9 @@ __device__ void lk_step_r(LkDev* L, int t, const Fr& r, const uint32_t (&Sn)[8],
   L->r[t - 1] = r;
   for (int i = 0; i < 8; i++) L->St[i] = Sn[i];
   const Fr ut = L->u[t - 1], one = fr_r1();
-  L->ct = mont_mul_ni(L->ct, fr_add(mont_mul_ni(ut, r), mont_mul_ni(fr_sub(one, ut), fr_sub(one, r))));
+  const Fr ef = fr_add(mont_mul_ni(ut, r), mont_mul_ni(fr_sub(one, ut), fr_sub(one, r)));
+  L->ct = mont_mul_ni(L->ct, ef);
+  if (t > L->L - L->log2_n) L->ctj = mont_mul_ni(L->ctj, ef);  // a table variable
   L->claim = lk_cubic(g, r, L->inv2, L->inv6);
 }
 
@@ -562,9 +579,10 @@ __global__ void __launch_bounds__(LK_TAIL_THREADS, 4) lk_tail_kernel(LkDev* Ls, 
       if (t == 1) lk_pair_a<0>(L, t, k, h, f, acc);
       else if (t == 2) lk_pair_a<1>(L, t, k, h, f, acc);
       else lk_pair_a<2>(L, t, k, h, f, acc);
-      if (jr) lk_pair_b(L, t, tj, k, h, accb);
+      if (jr) lk_pair_b(L, t, tj, k, h, f, accb);
     }
     if (t == 1) lk_mode0_sums(acc);
+    if (jr && tj == 1) lk_mode0_sums(accb);
     block_sum_fr<6>(acc, red);
     if (jr) block_sum_fr<6>(accb, red);
     if (tid == 0) {
