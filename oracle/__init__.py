@@ -7,7 +7,9 @@ eq:MLE and eq:zk-mle-matmul), with a SHA-256 Fiat-Shamir transcript (Sec. IV,
 footnote on Fiat-Shamir), and the linear zkMat proofs of matrix additions
 (sum_q c_q M_q = 0 by MLE linearity; the parameter update of Eq.
 eq:grad_update_ab is one), and the lookup-argument sumcheck of Protocol 1
-(Eq. eq:lookup-sumcheck) for range tables.  It uses Python integers and ``hashlib`` only,
+(Eq. eq:lookup-sumcheck) for range tables, and the batched-claim sumcheck
+that proves many products with one transcript (Sec. IV, composition by
+random aggregation).  It uses Python integers and ``hashlib`` only,
 with NumPy object arrays as the one library matmul step.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
@@ -28,6 +30,7 @@ from .sumcheck import Proof, prove_matmul, verify_matmul, round_poly_eval
 from .encode import encode_montgomery, limbs_le32
 from .linear import LinearProof, prove_linear, verify_linear
 from .lookup import LookupProof, prove_lookup, verify_lookup, cubic_eval
+from .batch import BatchProof, prove_matmul_batch, verify_matmul_batch, merkle_root
 
 __all__ = [
     "R_MOD", "fr", "fr_add", "fr_sub", "fr_mul", "fr_inv", "fr_to_bytes", "fr_from_bytes",
@@ -35,4 +38,5 @@ __all__ = [
     "fold_rows", "fold_cols", "Proof", "prove_matmul", "verify_matmul", "round_poly_eval",
     "encode_montgomery", "limbs_le32", "LinearProof", "prove_linear", "verify_linear",
     "LookupProof", "prove_lookup", "verify_lookup", "cubic_eval",
+    "BatchProof", "prove_matmul_batch", "verify_matmul_batch", "merkle_root",
 ]
