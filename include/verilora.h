@@ -391,6 +391,45 @@ int32_t vl_prove_lookup(const vl_lookup_job* jobs, int32_t njobs, void* workspac
  * argument error. */
 int32_t vl_verify_lookup(const vl_lookup_job* job, const vl_lookup_proof* proof);
 
+/* ---------------------------------------------------------------------------
+ * Batched-claim sumcheck (Sec. IV, putting everything together: claims of
+ * many proving steps aggregated at random points under one Fiat-Shamir
+ * transcript).  K products C_i = op(P_i) op(Q_i) with a common inner
+ * dimension k are proved by ONE sumcheck over w in {0,1}^d1:
+ *   member transcripts  M_i = SHA256("verilora-gb300/zkbatch/v1/member" ||
+ *     seed || K, i || m_i, k, n_i || transP, transQ || three binds) give
+ *     u_i, v_i (as in a single proof); c_i = sum_w A_i~(u_i,w) B_i~(w,v_i);
+ *   the claims are bound by a Merkle root over SHA256(0x00 || S_i || c_i)
+ *     (S_i the member state, node = SHA256(0x01 || l || r)), the batch
+ *     transcript starts at SHA256("verilora-gb300/zkbatch/v1" || seed || K ||
+ *     root) and squeezes rho ('p');
+ *   rounds prove sum_w sum_i rho^i A_i~ B_i~ = sum_i rho^i c_i (g(0), g(2)
+ *     absorbed as 'g', r squeezed); finally a_i = A_i~(u_i, r),
+ *     b_i = B_i~(r, v_i), bound by a Merkle root over
+ *     SHA256(0x00 || i u32le || a_i || b_i) absorbed as 'f'.
+ * Each job's own fs.seed is not used (the batch seed is); its binds are.
+ * ------------------------------------------------------------------------- */
+typedef struct vl_batch_proof {
+  int32_t K, k, d1, status;
+  vl_fr g[VL_MAX_ROUNDS][3];       /* g_t(0), g_t(1), g_t(2), canonical        */
+  uint8_t state[32];
+} vl_batch_proof;
+
+/* Device workspace for a batch (0 on invalid arguments or inner dimensions
+ * that differ). */
+size_t vl_batch_workspace_bytes(const vl_job* jobs, int32_t njobs);
+/* Prove a batch on the GPU.  Operands as for vl_prove_batch; njobs <= 65535,
+ * all with the same inner dimension (VL_ESHAPE otherwise).  out, claims, a,
+ * b: host memory (claims, a, b hold njobs canonical elements each, in job
+ * order).  Synchronises `stream`. */
+int32_t vl_prove_matmul_batched(const vl_job* jobs, int32_t njobs, uint64_t seed, void* workspace,
+                                size_t workspace_bytes, vl_batch_proof* out, vl_fr* claims, vl_fr* a, vl_fr* b,
+                                void* stream);
+/* Host verifier: C[i] are the claimed products (host), checked through the
+ * claims; the final values are checked against the operands. */
+int32_t vl_verify_matmul_batched(const vl_job* jobs, const vl_mat* C, int32_t njobs, uint64_t seed,
+                                 const vl_batch_proof* proof, const vl_fr* claims, const vl_fr* a, const vl_fr* b);
+
 /* Autotuner (the paper has no counterpart): picks the launch and tile
  * options for `jobs` by timing candidate plans on the caller's workspace and
  * stream — coordinate descent from `base` (NULL: defaults) over the fold

@@ -33,7 +33,8 @@ EXPORTS = ("vl_version", "vl_strerror", "vl_last_error", "vl_workspace_bytes", "
            "vl_lin_plan_create", "vl_lin_plan_workspace_bytes", "vl_lin_plan_run", "vl_lin_plan_phase_ms",
            "vl_lin_plan_destroy", "vl_lookup_workspace_bytes", "vl_lookup_plan_create",
            "vl_lookup_plan_workspace_bytes", "vl_lookup_plan_run", "vl_lookup_plan_phase_ms",
-           "vl_lookup_plan_destroy", "vl_prove_lookup", "vl_verify_lookup")
+           "vl_lookup_plan_destroy", "vl_prove_lookup", "vl_verify_lookup", "vl_batch_workspace_bytes",
+           "vl_prove_matmul_batched", "vl_verify_matmul_batched")
 VL_NOALLOC_SCRATCH_BYTES = 8 << 20
 VL_LIN_MAX = 16
 VL_LOOKUP_MAX_LOG_D = 24
@@ -88,6 +89,11 @@ class vl_lookup_proof(ctypes.Structure):
                 ("status", ctypes.c_int32), ("t0", ctypes.c_int64),
                 ("g", (vl_fr * 4) * VL_LOOKUP_MAX_LOG_D), ("a_r", vl_fr), ("s_r", vl_fr), ("b_r", vl_fr),
                 ("m_r", vl_fr), ("state", ctypes.c_uint8 * 32)]
+
+
+class vl_batch_proof(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("k", ctypes.c_int32), ("d1", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("g", (vl_fr * 3) * VL_MAX_ROUNDS), ("state", ctypes.c_uint8 * 32)]
 
 
 class vl_job(ctypes.Structure):
@@ -218,6 +224,15 @@ def lib():
     L.vl_prove_lookup.restype = ctypes.c_int32
     L.vl_verify_lookup.argtypes = [P(vl_lookup_job), P(vl_lookup_proof)]
     L.vl_verify_lookup.restype = ctypes.c_int32
+    L.vl_batch_workspace_bytes.argtypes = [P(vl_job), ctypes.c_int32]
+    L.vl_batch_workspace_bytes.restype = ctypes.c_size_t
+    L.vl_prove_matmul_batched.argtypes = [P(vl_job), ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p,
+                                          ctypes.c_size_t, P(vl_batch_proof), P(vl_fr), P(vl_fr), P(vl_fr),
+                                          ctypes.c_void_p]
+    L.vl_prove_matmul_batched.restype = ctypes.c_int32
+    L.vl_verify_matmul_batched.argtypes = [P(vl_job), P(vl_mat), ctypes.c_int32, ctypes.c_uint64,
+                                           P(vl_batch_proof), P(vl_fr), P(vl_fr), P(vl_fr)]
+    L.vl_verify_matmul_batched.restype = ctypes.c_int32
     L.vl_verify_linear.restype = ctypes.c_int32
     L.vl_encode.restype = ctypes.c_int32
     _lib = L
@@ -647,6 +662,51 @@ class LookupPlan:
         if self.ptr:
             lib().vl_lookup_plan_destroy(self.ptr)
             self.ptr = ctypes.c_void_p()
+
+
+class BatchedProof:
+    """A batched-claim proof: the vl_batch_proof and the per-product claims,
+    a_i, b_i (ctypes arrays, job order)."""
+
+    def __init__(self, K):
+        self.proof = vl_batch_proof()
+        self.claims = (vl_fr * K)()
+        self.a = (vl_fr * K)()
+        self.b = (vl_fr * K)()
+
+    def to_bytes(self):
+        """Same layout as the oracle's BatchProof.to_bytes."""
+        p = self.proof
+        out = b"".join(int(x).to_bytes(4, "little") for x in (p.K, p.k, p.d1))
+        out += b"".join(bytes(c) for c in self.claims)
+        for t in range(p.d1):
+            out += b"".join(bytes(p.g[t][q]) for q in range(3))
+        for x, y in zip(self.a, self.b):
+            out += bytes(x) + bytes(y)
+        return out + bytes(p.state)
+
+
+def vl_batch_workspace_bytes(jobs):
+    return lib().vl_batch_workspace_bytes(jobs_array(jobs), len(jobs))
+
+
+def vl_prove_matmul_batched(jobs, seed, workspace, workspace_bytes, stream=None):
+    res = BatchedProof(len(jobs))
+    _check(lib().vl_prove_matmul_batched(jobs_array(jobs), len(jobs), int(seed) & ((1 << 64) - 1), workspace,
+                                         workspace_bytes, ctypes.byref(res.proof), res.claims, res.a, res.b,
+                                         _stream_ptr(stream)), "vl_prove_matmul_batched")
+    return res
+
+
+def vl_verify_matmul_batched(jobs, Cs, seed, res):
+    """Host verifier: True / False; Cs are vl_mat of the claimed products."""
+    cs = (vl_mat * len(Cs))(*Cs)
+    code = lib().vl_verify_matmul_batched(jobs_array(jobs), cs, len(jobs), int(seed) & ((1 << 64) - 1),
+                                          ctypes.byref(res.proof), res.claims, res.a, res.b)
+    if code == VL_REJECT:
+        return False
+    _check(code, "vl_verify_matmul_batched")
+    return True
 
 
 def vl_verify_linear(job, proof):

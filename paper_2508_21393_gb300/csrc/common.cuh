@@ -31,7 +31,8 @@ struct DevProof {
   int32_t m, k, n, d0, d1, d2;
   int32_t tp, tq;
   int32_t dtypeA, dtypeB;  // VL_I16 or VL_FR_MONT
-  int32_t pad0, pad1;
+  int32_t member1;         // batched proofs: 1 + the product's index in the batch (0: a proof of its own)
+  int32_t nmembers;        // batched proofs: products in the batch
   uint64_t seed;
   uint8_t binds[96];
   Fr* eqA;                 // m entries, E_u in double-Montgomery form (x.R^2)
@@ -265,6 +266,29 @@ cudaError_t launch_lookup_setup(LkDev* Ls, int np, const LkItem* fac_items, int 
 cudaError_t launch_lookup_round(LkDev* Ls, int np, int t, const LkItem* items, int nhi, int nlo,
                                 vl_lookup_proof* out, cudaStream_t st);
 cudaError_t launch_lookup_finish(LkDev* Ls, int np, vl_lookup_proof* out, cudaStream_t st);
+
+// Batched-claim sumcheck (kernels_batch.cu): the batch transcript and
+// buffers, in the workspace.
+struct BtState {
+  int32_t K, d1, status, P2;       // products, rounds, status, leaves of the Merkle trees (2^t >= K)
+  uint64_t seed;
+  Fr rho, claim, inv2;             // Montgomery
+  Fr r[VL_MAX_ROUNDS];
+  uint32_t St[8];                  // batch transcript state (big-endian words)
+  int32_t pbeg[VL_MAX_ROUNDS + 1], pend[VL_MAX_ROUNDS + 1];  // partial-sum slots of each round
+  Fr* w;                           // rho^i
+  Fr* c;                           // claims (Montgomery)
+  uint8_t* tree;                   // 2 P2 nodes of 32 bytes (leaves at [P2, 2 P2), root at 1)
+  Fr* part;                        // partial sums, 2 per slot (g(0), g(2))
+  vl_fr* c_out;                    // canonical outputs: claims, a_i, b_i
+  vl_fr* a_out;
+  vl_fr* b_out;
+  vl_batch_proof* out;
+};
+cudaError_t launch_batch_claims(const DevProof* dp, int np, BtState* B, cudaStream_t st);
+cudaError_t launch_batch_round(const DevProof* dp, BtState* B, int t, const LkItem* items, int nitems,
+                               cudaStream_t st);
+cudaError_t launch_batch_finish(const DevProof* dp, int np, BtState* B, int k, cudaStream_t st);
 
 // Host helpers of the engine shared with the linear prover.
 bool encode_tc_operand(const void* base, int64_t rows, int64_t cols, int64_t ld, int32_t mode, void* map);

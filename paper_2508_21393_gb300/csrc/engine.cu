@@ -1083,3 +1083,145 @@ bool encode_tc_operand(const void* base, int64_t rows, int64_t cols, int64_t ld,
 void set_last_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
 
 }  // namespace vl
+
+// ---------------------------------------------------------------------------
+// Batched-claim sumcheck: the products' prologues (member transcripts) and
+// folds as in a plan, then the batch kernels (kernels_batch.cu).
+
+namespace {
+
+struct BatchLayout {
+  vl_plan* p = nullptr;
+  int K = 0, d1 = 0, k = 0, P2 = 1;
+  std::vector<LkItem> items;  // round items, round by round
+  std::vector<int> roff;      // round t: items [roff[t], roff[t + 1])
+  size_t off_state = 0, off_w = 0, off_c = 0, off_tree = 0, off_part = 0, off_items = 0, off_cout = 0,
+         off_aout = 0, off_bout = 0, off_proof = 0, total = 0;
+};
+
+constexpr int BT_PAIRS = 1024;
+
+int batch_layout(const vl_job* jobs, int32_t njobs, BatchLayout* L) {
+  if (!jobs || njobs < 1 || njobs > 65535) return VL_EINVAL;
+  vl_batch_opts o{};
+  o.persistent = 2;  // phase launches: the batch kernels replace the rounds
+  int e = make_plan(jobs, njobs, &o, &L->p);
+  if (e != VL_OK) return e;
+  vl_plan* p = L->p;
+  L->K = njobs;
+  L->k = p->proofs[0].k;
+  L->d1 = p->proofs[0].d1;
+  for (DevProof& P : p->proofs) {
+    if (P.k != L->k) return VL_ESHAPE;  // one inner dimension per batch
+    P.member1 = P.job + 1;
+    P.nmembers = njobs;
+  }
+  while (L->P2 < njobs) L->P2 <<= 1;
+  // round items: each proof's pairs in chunks, round by round (slots = item index)
+  L->roff.assign(L->d1 + 2, 0);
+  for (int t = 1; t <= L->d1; t++) {
+    L->roff[t] = (int)L->items.size();
+    const int h = 1 << (L->d1 - t);
+    for (int s = 0; s < njobs; s++)
+      for (int k0 = 0; k0 < h; k0 += BT_PAIRS)
+        L->items.push_back(LkItem{s, k0, std::min(h, k0 + BT_PAIRS), (int)L->items.size()});
+  }
+  L->roff[L->d1 + 1] = (int)L->items.size();
+  size_t off = p->total;
+  auto take = [&off](size_t bytes) {
+    const size_t o2 = off;
+    off = align_up(off + bytes);
+    return o2;
+  };
+  L->off_state = take(sizeof(BtState));
+  L->off_w = take(sizeof(Fr) * njobs);
+  L->off_c = take(sizeof(Fr) * njobs);
+  L->off_tree = take(64 * (size_t)L->P2);
+  L->off_part = take(sizeof(Fr) * 2 * std::max<size_t>(1, L->items.size()));
+  L->off_items = take(sizeof(LkItem) * std::max<size_t>(1, L->items.size()));
+  L->off_cout = take(sizeof(vl_fr) * njobs);
+  L->off_aout = take(sizeof(vl_fr) * njobs);
+  L->off_bout = take(sizeof(vl_fr) * njobs);
+  L->off_proof = take(sizeof(vl_batch_proof));
+  L->total = off;
+  return VL_OK;
+}
+
+}  // namespace
+
+extern "C" size_t vl_batch_workspace_bytes(const vl_job* jobs, int32_t njobs) {
+  BatchLayout L;
+  const int e = batch_layout(jobs, njobs, &L);
+  const size_t total = e == VL_OK ? L.total : 0;
+  if (L.p) vl_plan_destroy(L.p);
+  return total;
+}
+
+extern "C" int32_t vl_prove_matmul_batched(const vl_job* jobs, int32_t njobs, uint64_t seed, void* workspace,
+                                           size_t workspace_bytes, vl_batch_proof* out, vl_fr* claims, vl_fr* a,
+                                           vl_fr* b, void* stream) {
+  BatchLayout L;
+  int e = batch_layout(jobs, njobs, &L);
+  if (e == VL_OK && (!workspace || !out || !claims || !a || !b)) e = VL_EINVAL;
+  if (e == VL_OK && (reinterpret_cast<uintptr_t>(workspace) & (ALIGN - 1))) e = VL_EINVAL;
+  if (e == VL_OK && workspace_bytes < L.total) e = VL_ENOMEM;
+  if (e != VL_OK) {
+    if (L.p) vl_plan_destroy(L.p);
+    return e;
+  }
+  vl_plan* p = L.p;
+  for (DevProof& P : p->proofs) P.seed = seed;  // member transcripts use the batch seed
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  BtState S{};
+  S.K = L.K;
+  S.d1 = L.d1;
+  S.status = VL_OK;
+  S.P2 = L.P2;
+  S.seed = seed;
+  S.inv2 = to_mont(fr_inv_canonical(fr_small(2)));
+  for (int t = 1; t <= L.d1; t++) {
+    S.pbeg[t] = L.roff[t];
+    S.pend[t] = L.roff[t + 1];
+  }
+  S.w = reinterpret_cast<Fr*>(ws + L.off_w);
+  S.c = reinterpret_cast<Fr*>(ws + L.off_c);
+  S.tree = ws + L.off_tree;
+  S.part = reinterpret_cast<Fr*>(ws + L.off_part);
+  S.c_out = reinterpret_cast<vl_fr*>(ws + L.off_cout);
+  S.a_out = reinterpret_cast<vl_fr*>(ws + L.off_aout);
+  S.b_out = reinterpret_cast<vl_fr*>(ws + L.off_bout);
+  S.out = reinterpret_cast<vl_batch_proof*>(ws + L.off_proof);
+  BtState* dS = reinterpret_cast<BtState*>(ws + L.off_state);
+  e = bind_workspace(p, ws, st);  // descriptor tables, member fields included (synchronous)
+  if (e == VL_OK) e = stage_host_operands(p, ws, st);
+  cudaError_t ce = e == VL_OK ? cudaSuccess : cudaErrorInvalidValue;
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(dS, &S, sizeof(S), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess && !L.items.empty())
+    ce = cudaMemcpyAsync(ws + L.off_items, L.items.data(), sizeof(LkItem) * L.items.size(), cudaMemcpyHostToDevice,
+                         st);
+  const DevProof* dp = reinterpret_cast<const DevProof*>(ws + p->off_proofs);
+  const FoldTask* dt = reinterpret_cast<const FoldTask*>(ws + p->off_tasks);
+  const FoldTile* dl = reinterpret_cast<const FoldTile*>(ws + p->off_tiles);
+  const TcTile* dc = reinterpret_cast<const TcTile*>(ws + p->off_tc_tiles);
+  const EqItem* de = reinterpret_cast<const EqItem*>(ws + p->off_eq_items);
+  const LkItem* di = reinterpret_cast<const LkItem*>(ws + L.off_items);
+  const int np = (int)p->jobs.size();
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(ws + p->off_ctl, 0, p->off_acc + p->acc_bytes - p->off_ctl, st);
+  if (ce == cudaSuccess) ce = launch_prologue(dp, 0, np, de, (int)p->eq_items.size(), st);
+  if (ce == cudaSuccess) ce = launch_fold_tc(dc, (int)p->tc_tiles.size(), dp, wait_ns(p), st);
+  if (ce == cudaSuccess) ce = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, wait_ns(p), st);
+  if (ce == cudaSuccess) ce = launch_batch_claims(dp, np, dS, st);
+  for (int t = 1; t <= L.d1 && ce == cudaSuccess; t++)
+    ce = launch_batch_round(dp, dS, t, di + L.roff[t], L.roff[t + 1] - L.roff[t], st);
+  if (ce == cudaSuccess) ce = launch_batch_finish(dp, np, dS, L.k, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, ws + L.off_proof, sizeof(vl_batch_proof), cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(claims, ws + L.off_cout, sizeof(vl_fr) * njobs, cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(a, ws + L.off_aout, sizeof(vl_fr) * njobs, cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(b, ws + L.off_bout, sizeof(vl_fr) * njobs, cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // the host tables above outlive their copies
+  if (e == VL_OK) e = cuda_status(ce, "vl_prove_matmul_batched");
+  vl_plan_destroy(p);
+  if (e == VL_OK && out->status != VL_OK) e = out->status;
+  return e;
+}

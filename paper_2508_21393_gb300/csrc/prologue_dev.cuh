@@ -137,7 +137,10 @@ static __device__ void prologue_block(const DevProof& P, uint8_t* smem) {
 
   if (tid == 0) {
     uint8_t b[32];
-    ts_start(b, P.seed, P.m, P.k, P.n, P.tp, P.tq, P.binds);
+    if (P.member1 > 0)
+      ts_start_member(b, P.seed, (uint32_t)P.nmembers, (uint32_t)(P.member1 - 1), P.m, P.k, P.n, P.tp, P.tq, P.binds);
+    else
+      ts_start(b, P.seed, P.m, P.k, P.n, P.tp, P.tq, P.binds);
     for (int i = 0; i < 8; i++)
       S0[i] = ((uint32_t)b[4 * i] << 24) | ((uint32_t)b[4 * i + 1] << 16) | ((uint32_t)b[4 * i + 2] << 8) | b[4 * i + 3];
   }
@@ -207,7 +210,10 @@ static __device__ void transcript_block(const DevProof& P, uint8_t* smem) {
   const int tid = threadIdx.x;
   if (tid == 0) {
     uint8_t b[32];
-    ts_start(b, P.seed, P.m, P.k, P.n, P.tp, P.tq, P.binds);
+    if (P.member1 > 0)
+      ts_start_member(b, P.seed, (uint32_t)P.nmembers, (uint32_t)(P.member1 - 1), P.m, P.k, P.n, P.tp, P.tq, P.binds);
+    else
+      ts_start(b, P.seed, P.m, P.k, P.n, P.tp, P.tq, P.binds);
     for (int i = 0; i < 8; i++)
       S0[i] = ((uint32_t)b[4 * i] << 24) | ((uint32_t)b[4 * i + 1] << 16) | ((uint32_t)b[4 * i + 2] << 8) | b[4 * i + 3];
   }

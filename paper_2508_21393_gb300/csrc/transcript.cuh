@@ -83,6 +83,53 @@ VL_HD void ts_start_linear(uint8_t S[32], uint64_t seed, uint32_t rows, uint32_t
   h.finish(S);
 }
 
+// Member transcript of a product in a batched proof:
+//   M_i = SHA256("verilora-gb300/zkbatch/v1/member" || seed u64le || K, i u32le
+//                || m, k, n u32le || transP, transQ u8 || bindP || bindQ || bindC)
+VL_HD void ts_start_member(uint8_t S[32], uint64_t seed, uint32_t K, uint32_t i, uint32_t m, uint32_t k, uint32_t n,
+                           uint32_t trans_p, uint32_t trans_q, const uint8_t binds[96]) {
+  const uint8_t dom[32] = {'v', 'e', 'r', 'i', 'l', 'o', 'r', 'a', '-', 'g', 'b', '3', '0', '0', '/', 'z',
+                           'k', 'b', 'a', 't', 'c', 'h', '/', 'v', '1', '/', 'm', 'e', 'm', 'b', 'e', 'r'};
+  Sha256 h;
+  h.init();
+  h.update(dom, 32);
+  h.u32le((uint32_t)seed);
+  h.u32le((uint32_t)(seed >> 32));
+  h.u32le(K);
+  h.u32le(i);
+  h.u32le(m);
+  h.u32le(k);
+  h.u32le(n);
+  h.byte((uint8_t)(trans_p & 1));
+  h.byte((uint8_t)(trans_q & 1));
+  h.update(binds, 96);
+  h.finish(S);
+}
+
+// Batch transcript start: SHA256("verilora-gb300/zkbatch/v1" || seed u64le || K u32le || root)
+VL_HD void ts_start_batch(uint8_t S[32], uint64_t seed, uint32_t K, const uint8_t root[32]) {
+  const uint8_t dom[25] = {'v', 'e', 'r', 'i', 'l', 'o', 'r', 'a', '-', 'g', 'b', '3', '0',
+                           '0', '/', 'z', 'k', 'b', 'a', 't', 'c', 'h', '/', 'v', '1'};
+  Sha256 h;
+  h.init();
+  h.update(dom, 25);
+  h.u32le((uint32_t)seed);
+  h.u32le((uint32_t)(seed >> 32));
+  h.u32le(K);
+  h.update(root, 32);
+  h.finish(S);
+}
+
+// Merkle nodes: leaf = SHA256(0x00 || data), node = SHA256(0x01 || left || right).
+VL_HD void merkle_node(uint8_t out[32], const uint8_t left[32], const uint8_t right[32]) {
+  Sha256 h;
+  h.init();
+  h.byte(1);
+  h.update(left, 32);
+  h.update(right, 32);
+  h.finish(out);
+}
+
 // Start of a lookup transcript:
 //   S0 = SHA256("verilora-gb300/zklookup/v1" || seed u64le || n, log2 D, log2 N u32le
 //               || t0 i64le || bind (32 B))

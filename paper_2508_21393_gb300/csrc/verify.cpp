@@ -345,3 +345,129 @@ extern "C" int32_t vl_verify_lookup(const vl_lookup_job* job, const vl_lookup_pr
   if (!fr_eq(ea, am) || !fr_eq(es, sm) || !fr_eq(eb, bm) || !fr_eq(em, mm)) return VL_REJECT;
   return VL_OK;
 }
+
+namespace {
+
+// Root of the Merkle tree over 32-byte leaves, zero-padded to a power of two.
+std::vector<uint8_t> merkle_root_host(std::vector<uint8_t> level, size_t nleaves) {
+  size_t size = 1;
+  while (size < nleaves) size <<= 1;
+  level.resize(32 * size, 0);
+  while (size > 1) {
+    std::vector<uint8_t> next(32 * (size / 2));
+    for (size_t j = 0; j < size / 2; j++) merkle_node(&next[32 * j], &level[64 * j], &level[64 * j + 32]);
+    level.swap(next);
+    size /= 2;
+  }
+  level.resize(32);
+  return level;
+}
+
+}  // namespace
+
+// Host verifier of a batched proof: member transcripts and claims (checked
+// against the claimed products), the claims' root, rho, the rounds against
+// the combined claim, the final combination, the final values' root and
+// state, and the final values against the operands.
+extern "C" int32_t vl_verify_matmul_batched(const vl_job* jobs, const vl_mat* C, int32_t njobs, uint64_t seed,
+                                            const vl_batch_proof* proof, const vl_fr* claims, const vl_fr* a,
+                                            const vl_fr* b) {
+  if (!jobs || !C || !proof || !claims || !a || !b || njobs < 1 || njobs > 65535) return VL_EINVAL;
+  int e;
+  int64_t k = -1;
+  for (int i = 0; i < njobs; i++) {
+    if ((e = check_host_mat(&jobs[i].P)) != VL_OK || (e = check_host_mat(&jobs[i].Q)) != VL_OK ||
+        (e = check_host_mat(&C[i])) != VL_OK)
+      return e;
+    const HostMat A{&jobs[i].P}, B{&jobs[i].Q}, Cm{&C[i]};
+    if (A.cols() != B.rows() || Cm.rows() != A.rows() || Cm.cols() != B.cols()) return VL_ESHAPE;
+    if (k < 0) k = A.cols();
+    if (A.cols() != k) return VL_ESHAPE;
+    if (A.rows() > VL_MAX_REDUCE || B.cols() > VL_MAX_REDUCE || k > (int64_t(1) << VL_MAX_ROUNDS)) return VL_ESHAPE;
+  }
+  const int d1 = ceil_log2(k);
+  if (proof->K != njobs || proof->k != k || proof->d1 != d1 || proof->status != VL_OK) return VL_REJECT;
+  for (int t = 0; t < d1; t++)
+    for (int q = 0; q < 3; q++)
+      if (!lt_r(fr_from_api(proof->g[t][q]))) return VL_REJECT;
+  for (int i = 0; i < njobs; i++)
+    if (!lt_r(fr_from_api(claims[i])) || !lt_r(fr_from_api(a[i])) || !lt_r(fr_from_api(b[i]))) return VL_REJECT;
+  std::vector<std::vector<Fr>> us(njobs), vs(njobs);
+  std::vector<uint8_t> leaves(32 * (size_t)njobs);
+  for (int i = 0; i < njobs; i++) {
+    const HostMat A{&jobs[i].P}, B{&jobs[i].Q};
+    const int64_t m = A.rows(), n = B.cols();
+    uint8_t S[32];
+    ts_start_member(S, seed, (uint32_t)njobs, (uint32_t)i, (uint32_t)m, (uint32_t)k, (uint32_t)n,
+                    (uint32_t)jobs[i].P.trans, (uint32_t)jobs[i].Q.trans, &jobs[i].fs.bind[0][0]);
+    const int d0 = ceil_log2(m), d2 = ceil_log2(n);
+    for (int t = 0; t < d0; t++) us[i].push_back(to_mont(ts_challenge(S, 'u', t)));
+    ts_squeeze_done(S, 'u', d0);
+    for (int t = 0; t < d2; t++) vs[i].push_back(to_mont(ts_challenge(S, 'v', t)));
+    ts_squeeze_done(S, 'v', d2);
+    const Fr c = fr_from_api(claims[i]);
+    if (!fr_eq(to_mont(c), mle_eval(HostMat{&C[i]}, us[i], vs[i]))) return VL_REJECT;
+    uint8_t cb[32];
+    fr_to_le_bytes(c, cb);
+    Sha256 h;
+    h.init();
+    h.byte(0);
+    h.update(S, 32);
+    h.update(cb, 32);
+    h.finish(&leaves[32 * (size_t)i]);
+  }
+  const std::vector<uint8_t> root = merkle_root_host(leaves, njobs);
+  uint8_t S[32];
+  ts_start_batch(S, seed, (uint32_t)njobs, root.data());
+  const Fr rho = to_mont(ts_challenge(S, 'p', 0));
+  ts_squeeze_done(S, 'p', 1);
+  std::vector<Fr> w(njobs);
+  Fr claim = fr_zero(), pw = fr_r1();
+  for (int i = 0; i < njobs; i++) {
+    w[i] = pw;
+    claim = fr_add(claim, mont_mul(pw, to_mont(fr_from_api(claims[i]))));
+    pw = mont_mul(pw, rho);
+  }
+  std::vector<Fr> r;
+  for (int t = 0; t < d1; t++) {
+    const Fr g0 = to_mont(fr_from_api(proof->g[t][0])), g1 = to_mont(fr_from_api(proof->g[t][1])),
+             g2 = to_mont(fr_from_api(proof->g[t][2]));
+    if (!fr_eq(fr_add(g0, g1), claim)) return VL_REJECT;
+    const Fr m2[2] = {fr_from_api(proof->g[t][0]), fr_from_api(proof->g[t][2])};
+    ts_absorb_fr(S, 'g', m2, 2);
+    r.push_back(to_mont(ts_challenge(S, 'r', 0)));
+    ts_squeeze_done(S, 'r', 1);
+    claim = interp(g0, g1, g2, r.back());
+  }
+  Fr fin = fr_zero();
+  for (int i = 0; i < njobs; i++)
+    fin = fr_add(fin, mont_mul(w[i], mont_mul(to_mont(fr_from_api(a[i])), to_mont(fr_from_api(b[i])))));
+  if (!fr_eq(fin, claim)) return VL_REJECT;
+  for (int i = 0; i < njobs; i++) {
+    uint8_t ab[32], bb[32];
+    fr_to_le_bytes(fr_from_api(a[i]), ab);
+    fr_to_le_bytes(fr_from_api(b[i]), bb);
+    Sha256 h;
+    h.init();
+    h.byte(0);
+    h.u32le((uint32_t)i);
+    h.update(ab, 32);
+    h.update(bb, 32);
+    h.finish(&leaves[32 * (size_t)i]);
+  }
+  const std::vector<uint8_t> root_f = merkle_root_host(leaves, njobs);
+  {
+    Sha256 h;
+    h.init();
+    h.update(S, 32);
+    h.byte('f');
+    h.update(root_f.data(), 32);
+    h.finish(S);
+  }
+  if (std::memcmp(S, proof->state, 32) != 0) return VL_REJECT;
+  for (int i = 0; i < njobs; i++) {
+    if (!fr_eq(to_mont(fr_from_api(a[i])), mle_eval(HostMat{&jobs[i].P}, us[i], r))) return VL_REJECT;
+    if (!fr_eq(to_mont(fr_from_api(b[i])), mle_eval(HostMat{&jobs[i].Q}, r, vs[i]))) return VL_REJECT;
+  }
+  return VL_OK;
+}
