@@ -44,7 +44,7 @@ SM_MAX_MHZ = 2070.0
 # per clock, a wide (64-bit result) one taking two of them.
 MADWIDE_PER_SM_CLK = 32
 STEP_KIND = {"7b-step": "7b", "7b-proj": "7b-proj", "13b-step": "13b", "serve": "7b-proj", "7b-update": "7b",
-             "7b-step-paper-route": "7b", "7b-lookups": "7b"}
+             "7b-step-paper-route": "7b", "7b-lookups": "7b", "7b-step-batched": "7b"}
 WORKLOADS = {
     "7b-step": "batched 7B-shaped LoRA step: 32 layers x {q,k,v,o}, hidden 4096, seq 512, ranks {8,16,64}",
     "7b-proj": "one 7B-shaped LoRA projection, n=1024, d=k=4096, r=16, eight products",
@@ -55,6 +55,8 @@ WORKLOADS = {
     "7b-lookups": "range lookups of the 7B-shaped LoRA step's rescale remainders (Protocol 1, Eq. "
                   "eq:lookup-sumcheck): 32 layers x {q,k,v,o} x {H, dH (512 x r, table 2^8), G_A (4096 x r), "
                   "G_B (r x 4096) (table 2^12)}, ranks {8,16,64}, one batched plan run",
+    "7b-step-batched": "the batched 7B-shaped LoRA step's 1024 products as 5 batched-claim proofs (one per inner "
+                       "dimension: 4096, 512, and the ranks 8, 16, 64), one transcript and one sumcheck each",
     "7b-update": "parameter updates of the 7B-shaped LoRA step (Eq. eq:grad_update_ab): 32 layers x {q,k,v,o} x "
                  "{A' = A - G_A (4096 x r), B' = B - G_B (r x 4096)}, ranks {8,16,64}, linear zkMat, one batched call",
     "serve": "serving stream: Poisson arrivals (20 jobs/s) of single-layer jobs (one projection's 8 products), "
@@ -139,8 +141,15 @@ def oracle_sample(kind, seed, nproj):
     jobs = [j for t in projs for j in products(kind, t, seed)]
     macs = sum(W.macs(j) for j in jobs)
     t0 = time.perf_counter()
-    for j in jobs:
-        oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"])
+    if kind == "7b-step-batched":  # one batched proof per inner dimension
+        groups = {}
+        for j in jobs:
+            groups.setdefault(W.op_shape(j)[1], []).append(j)
+        for k, g in groups.items():
+            oracle.prove_matmul_batch(g, seed=seed + k)
+    else:
+        for j in jobs:
+            oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"])
     dt = time.perf_counter() - t0
     return macs / dt, dt, len(jobs), macs
 
@@ -611,6 +620,80 @@ def lookups_main(args, rank, world, local, cpu):
     }))
 
 
+def batched_main(args, rank, world, local):
+    """The 7B step's products grouped by inner dimension, each group one
+    batched-claim proof (vl_prove_matmul_batched, synchronous per group)."""
+    import torch
+    from paper_2508_21393_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.lib()
+    seed = rank_seed(rank)
+    projs, jobs = step_jobs("7b-step", seed, args.layers)
+    macs_step = sum(W.macs(j) for j in jobs)
+    dev = {}
+    for t in projs:
+        for key in ("X", "W", "A", "B", "dY", "H", "dH"):
+            dev[id(t[key])] = torch.from_numpy(t[key]).cuda()
+    groups = {}
+    for j in jobs:
+        groups.setdefault(W.op_shape(j)[1], []).append(B.job(dev[id(j["P"])], dev[id(j["Q"])], j["tp"], j["tq"],
+                                                             j["seed"]))
+    keys = sorted(groups)
+    sizes = {k: B.vl_batch_workspace_bytes(groups[k]) for k in keys}
+    ws = torch.empty(max(sizes.values()), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return [B.vl_prove_matmul_batched(groups[k], seed + k, ws.data_ptr(), sizes[k], stream) for k in keys]
+
+    for _ in range(max(args.warmup, 3)):
+        res = step()
+    assert all(r.proof.status == 0 for r in res)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    time.sleep(0.6)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = job_value(macs_step, world, ms_max / 1e3)
+    proof_bytes = sum(len(r.to_bytes()) for r in res)
+    # the same products as separate proofs: dims, c, three values per round, a_r, b_r, state
+    separate_bytes = sum(24 + 32 + 96 * (W.op_shape(j)[1] - 1).bit_length() + 64 + 32 for j in jobs)
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int16 operands, Fr (255-bit) arithmetic", "data": "synthetic",
+        "config": {"workload": WORKLOADS["7b-step-batched"] + (f", first {args.layers} layers" if args.layers else ""),
+                   "products_per_step": len(jobs), "batched_proofs_per_step": len(keys),
+                   "products_per_batch": {str(k): len(groups[k]) for k in keys}, "macs_per_step": macs_step,
+                   "proof_bytes_per_step": proof_bytes, "separate_proofs_bytes_per_step": separate_bytes,
+                   "l2": "inputs larger than L2 (no flush)",
+                   "host_ms_per_step": 1e3 * wall,
+                   "note": "one synchronous call per batch: the plan, its tables and the proofs' copies are "
+                           "inside the timed region"},
+        "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
+        "gpu_launches": None,
+    }))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -618,6 +701,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "serve":
         return serve_main(args, rank, world, local)
+    if args.workload == "7b-step-batched":
+        return batched_main(args, rank, world, local)
     if args.workload == "7b-lookups":
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
