@@ -425,6 +425,19 @@ size_t vl_batch_workspace_bytes(const vl_job* jobs, int32_t njobs);
 int32_t vl_prove_matmul_batched(const vl_job* jobs, int32_t njobs, uint64_t seed, void* workspace,
                                 size_t workspace_bytes, vl_batch_proof* out, vl_fr* claims, vl_fr* a, vl_fr* b,
                                 void* stream);
+/* Plans, as for single proofs: the batch (operand descriptors) is copied at
+ * creation, its tables are bound to a workspace on the first run there
+ * (synchronising `stream`); a run stages host operands, enqueues the
+ * launches and copies the proof, claims, a and b to the given buffers in
+ * out_space: VL_DEVICE asynchronously (status in out->status), VL_HOST
+ * synchronously.  The workspace must not be used by anything else between
+ * runs of the plan. */
+typedef struct vl_claims_plan vl_claims_plan;
+int32_t vl_claims_plan_create(const vl_job* jobs, int32_t njobs, uint64_t seed, vl_claims_plan** plan);
+size_t vl_claims_plan_workspace_bytes(const vl_claims_plan* plan);
+int32_t vl_claims_plan_run(vl_claims_plan* plan, void* workspace, size_t workspace_bytes, vl_batch_proof* out,
+                           vl_fr* claims, vl_fr* a, vl_fr* b, int32_t out_space, void* stream);
+void vl_claims_plan_destroy(vl_claims_plan* plan);
 /* Host verifier: C[i] are the claimed products (host), checked through the
  * claims; the final values are checked against the operands. */
 int32_t vl_verify_matmul_batched(const vl_job* jobs, const vl_mat* C, int32_t njobs, uint64_t seed,

@@ -34,7 +34,8 @@ EXPORTS = ("vl_version", "vl_strerror", "vl_last_error", "vl_workspace_bytes", "
            "vl_lin_plan_destroy", "vl_lookup_workspace_bytes", "vl_lookup_plan_create",
            "vl_lookup_plan_workspace_bytes", "vl_lookup_plan_run", "vl_lookup_plan_phase_ms",
            "vl_lookup_plan_destroy", "vl_prove_lookup", "vl_verify_lookup", "vl_batch_workspace_bytes",
-           "vl_prove_matmul_batched", "vl_verify_matmul_batched")
+           "vl_prove_matmul_batched", "vl_verify_matmul_batched", "vl_claims_plan_create",
+           "vl_claims_plan_workspace_bytes", "vl_claims_plan_run", "vl_claims_plan_destroy")
 VL_NOALLOC_SCRATCH_BYTES = 8 << 20
 VL_LIN_MAX = 16
 VL_LOOKUP_MAX_LOG_D = 24
@@ -233,6 +234,16 @@ def lib():
     L.vl_verify_matmul_batched.argtypes = [P(vl_job), P(vl_mat), ctypes.c_int32, ctypes.c_uint64,
                                            P(vl_batch_proof), P(vl_fr), P(vl_fr), P(vl_fr)]
     L.vl_verify_matmul_batched.restype = ctypes.c_int32
+    L.vl_claims_plan_create.argtypes = [P(vl_job), ctypes.c_int32, ctypes.c_uint64, P(ctypes.c_void_p)]
+    L.vl_claims_plan_create.restype = ctypes.c_int32
+    L.vl_claims_plan_workspace_bytes.argtypes = [ctypes.c_void_p]
+    L.vl_claims_plan_workspace_bytes.restype = ctypes.c_size_t
+    L.vl_claims_plan_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                     ctypes.c_void_p]
+    L.vl_claims_plan_run.restype = ctypes.c_int32
+    L.vl_claims_plan_destroy.argtypes = [ctypes.c_void_p]
+    L.vl_claims_plan_destroy.restype = None
     L.vl_verify_linear.restype = ctypes.c_int32
     L.vl_encode.restype = ctypes.c_int32
     _lib = L
@@ -684,6 +695,39 @@ class BatchedProof:
         for x, y in zip(self.a, self.b):
             out += bytes(x) + bytes(y)
         return out + bytes(p.state)
+
+
+class ClaimsPlan:
+    """A vl_claims_plan (keeps its job array alive)."""
+
+    def __init__(self, jobs, seed):
+        self.arr = jobs_array(jobs)
+        self.K = len(jobs)
+        self.ptr = ctypes.c_void_p()
+        _check(lib().vl_claims_plan_create(self.arr, self.K, int(seed) & ((1 << 64) - 1), ctypes.byref(self.ptr)),
+               "vl_claims_plan_create")
+
+    def workspace_bytes(self):
+        return lib().vl_claims_plan_workspace_bytes(self.ptr)
+
+    def run(self, workspace, workspace_bytes, stream=None, device_out=None):
+        """Host outputs (a BatchedProof) by default; device_out = (proof, claims,
+        a, b) device pointers for an asynchronous run."""
+        if device_out is None:
+            res = BatchedProof(self.K)
+            ptrs = [ctypes.addressof(res.proof), ctypes.addressof(res.claims), ctypes.addressof(res.a),
+                    ctypes.addressof(res.b)]
+            space = VL_HOST
+        else:
+            res, ptrs, space = None, [int(x) for x in device_out], VL_DEVICE
+        _check(lib().vl_claims_plan_run(self.ptr, workspace, workspace_bytes, *ptrs, space, _stream_ptr(stream)),
+               "vl_claims_plan_run")
+        return res
+
+    def destroy(self):
+        if self.ptr:
+            lib().vl_claims_plan_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p()
 
 
 def vl_batch_workspace_bytes(jobs):

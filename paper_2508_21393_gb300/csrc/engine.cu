@@ -1157,49 +1157,84 @@ extern "C" size_t vl_batch_workspace_bytes(const vl_job* jobs, int32_t njobs) {
   return total;
 }
 
-extern "C" int32_t vl_prove_matmul_batched(const vl_job* jobs, int32_t njobs, uint64_t seed, void* workspace,
-                                           size_t workspace_bytes, vl_batch_proof* out, vl_fr* claims, vl_fr* a,
-                                           vl_fr* b, void* stream) {
+// A batch bound to one workspace at a time: the plan of its products, the
+// layout and the batch state template (re-uploaded every run: the kernels
+// update it).
+struct vl_claims_plan {
   BatchLayout L;
-  int e = batch_layout(jobs, njobs, &L);
-  if (e == VL_OK && (!workspace || !out || !claims || !a || !b)) e = VL_EINVAL;
-  if (e == VL_OK && (reinterpret_cast<uintptr_t>(workspace) & (ALIGN - 1))) e = VL_EINVAL;
-  if (e == VL_OK && workspace_bytes < L.total) e = VL_ENOMEM;
-  if (e != VL_OK) {
+  uint64_t seed = 0;
+  uint8_t* bound_ws = nullptr;
+  BtState S{};
+  ~vl_claims_plan() {
     if (L.p) vl_plan_destroy(L.p);
+  }
+};
+
+extern "C" int32_t vl_claims_plan_create(const vl_job* jobs, int32_t njobs, uint64_t seed, vl_claims_plan** plan) {
+  if (!plan) return VL_EINVAL;
+  *plan = nullptr;
+  vl_claims_plan* C = new (std::nothrow) vl_claims_plan;
+  if (!C) return VL_ENOMEM;
+  const int e = batch_layout(jobs, njobs, &C->L);
+  if (e != VL_OK) {
+    delete C;
     return e;
   }
-  vl_plan* p = L.p;
-  for (DevProof& P : p->proofs) P.seed = seed;  // member transcripts use the batch seed
-  uint8_t* ws = static_cast<uint8_t*>(workspace);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  BtState S{};
-  S.K = L.K;
-  S.d1 = L.d1;
+  C->seed = seed;
+  for (DevProof& P : C->L.p->proofs) P.seed = seed;  // member transcripts use the batch seed
+  BtState& S = C->S;
+  S.K = C->L.K;
+  S.d1 = C->L.d1;
   S.status = VL_OK;
-  S.P2 = L.P2;
+  S.P2 = C->L.P2;
   S.seed = seed;
   S.inv2 = to_mont(fr_inv_canonical(fr_small(2)));
-  for (int t = 1; t <= L.d1; t++) {
-    S.pbeg[t] = L.roff[t];
-    S.pend[t] = L.roff[t + 1];
+  for (int t = 1; t <= C->L.d1; t++) {
+    S.pbeg[t] = C->L.roff[t];
+    S.pend[t] = C->L.roff[t + 1];
   }
-  S.w = reinterpret_cast<Fr*>(ws + L.off_w);
-  S.c = reinterpret_cast<Fr*>(ws + L.off_c);
-  S.tree = ws + L.off_tree;
-  S.part = reinterpret_cast<Fr*>(ws + L.off_part);
-  S.c_out = reinterpret_cast<vl_fr*>(ws + L.off_cout);
-  S.a_out = reinterpret_cast<vl_fr*>(ws + L.off_aout);
-  S.b_out = reinterpret_cast<vl_fr*>(ws + L.off_bout);
-  S.out = reinterpret_cast<vl_batch_proof*>(ws + L.off_proof);
+  *plan = C;
+  return VL_OK;
+}
+
+extern "C" size_t vl_claims_plan_workspace_bytes(const vl_claims_plan* plan) { return plan ? plan->L.total : 0; }
+
+extern "C" void vl_claims_plan_destroy(vl_claims_plan* plan) { delete plan; }
+
+extern "C" int32_t vl_claims_plan_run(vl_claims_plan* C, void* workspace, size_t workspace_bytes, vl_batch_proof* out,
+                                      vl_fr* claims, vl_fr* a, vl_fr* b, int32_t out_space, void* stream) {
+  if (!C || !workspace || !out || !claims || !a || !b || (out_space != VL_DEVICE && out_space != VL_HOST))
+    return VL_EINVAL;
+  if (reinterpret_cast<uintptr_t>(workspace) & (ALIGN - 1)) return VL_EINVAL;
+  BatchLayout& L = C->L;
+  if (workspace_bytes < L.total) return VL_ENOMEM;
+  vl_plan* p = L.p;
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int e = VL_OK;
+  cudaError_t ce = cudaSuccess;
+  if (C->bound_ws != ws) {
+    BtState& S = C->S;
+    S.w = reinterpret_cast<Fr*>(ws + L.off_w);
+    S.c = reinterpret_cast<Fr*>(ws + L.off_c);
+    S.tree = ws + L.off_tree;
+    S.part = reinterpret_cast<Fr*>(ws + L.off_part);
+    S.c_out = reinterpret_cast<vl_fr*>(ws + L.off_cout);
+    S.a_out = reinterpret_cast<vl_fr*>(ws + L.off_aout);
+    S.b_out = reinterpret_cast<vl_fr*>(ws + L.off_bout);
+    S.out = reinterpret_cast<vl_batch_proof*>(ws + L.off_proof);
+    e = bind_workspace(p, ws, st);  // descriptor tables, member fields included (synchronous)
+    if (e == VL_OK && !L.items.empty())
+      ce = cudaMemcpyAsync(ws + L.off_items, L.items.data(), sizeof(LkItem) * L.items.size(), cudaMemcpyHostToDevice,
+                           st);
+    if (e == VL_OK && ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (e != VL_OK) return e;
+    if (ce != cudaSuccess) return cuda_status(ce, "vl_claims_plan_run: bind");
+    C->bound_ws = ws;
+  }
+  e = stage_host_operands(p, ws, st);
+  if (e != VL_OK) return e;
   BtState* dS = reinterpret_cast<BtState*>(ws + L.off_state);
-  e = bind_workspace(p, ws, st);  // descriptor tables, member fields included (synchronous)
-  if (e == VL_OK) e = stage_host_operands(p, ws, st);
-  cudaError_t ce = e == VL_OK ? cudaSuccess : cudaErrorInvalidValue;
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(dS, &S, sizeof(S), cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess && !L.items.empty())
-    ce = cudaMemcpyAsync(ws + L.off_items, L.items.data(), sizeof(LkItem) * L.items.size(), cudaMemcpyHostToDevice,
-                         st);
   const DevProof* dp = reinterpret_cast<const DevProof*>(ws + p->off_proofs);
   const FoldTask* dt = reinterpret_cast<const FoldTask*>(ws + p->off_tasks);
   const FoldTile* dl = reinterpret_cast<const FoldTile*>(ws + p->off_tiles);
@@ -1207,6 +1242,8 @@ extern "C" int32_t vl_prove_matmul_batched(const vl_job* jobs, int32_t njobs, ui
   const EqItem* de = reinterpret_cast<const EqItem*>(ws + p->off_eq_items);
   const LkItem* di = reinterpret_cast<const LkItem*>(ws + L.off_items);
   const int np = (int)p->jobs.size();
+  const int K = L.K;
+  ce = cudaMemcpyAsync(dS, &C->S, sizeof(BtState), cudaMemcpyHostToDevice, st);  // status, pointers (the plan keeps the source)
   if (ce == cudaSuccess) ce = cudaMemsetAsync(ws + p->off_ctl, 0, p->off_acc + p->acc_bytes - p->off_ctl, st);
   if (ce == cudaSuccess) ce = launch_prologue(dp, 0, np, de, (int)p->eq_items.size(), st);
   if (ce == cudaSuccess) ce = launch_fold_tc(dc, (int)p->tc_tiles.size(), dp, wait_ns(p), st);
@@ -1215,13 +1252,24 @@ extern "C" int32_t vl_prove_matmul_batched(const vl_job* jobs, int32_t njobs, ui
   for (int t = 1; t <= L.d1 && ce == cudaSuccess; t++)
     ce = launch_batch_round(dp, dS, t, di + L.roff[t], L.roff[t + 1] - L.roff[t], st);
   if (ce == cudaSuccess) ce = launch_batch_finish(dp, np, dS, L.k, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, ws + L.off_proof, sizeof(vl_batch_proof), cudaMemcpyDeviceToHost, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(claims, ws + L.off_cout, sizeof(vl_fr) * njobs, cudaMemcpyDeviceToHost, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(a, ws + L.off_aout, sizeof(vl_fr) * njobs, cudaMemcpyDeviceToHost, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(b, ws + L.off_bout, sizeof(vl_fr) * njobs, cudaMemcpyDeviceToHost, st);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // the host tables above outlive their copies
-  if (e == VL_OK) e = cuda_status(ce, "vl_prove_matmul_batched");
-  vl_plan_destroy(p);
-  if (e == VL_OK && out->status != VL_OK) e = out->status;
+  const cudaMemcpyKind kind = out_space == VL_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, ws + L.off_proof, sizeof(vl_batch_proof), kind, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(claims, ws + L.off_cout, sizeof(vl_fr) * K, kind, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(a, ws + L.off_aout, sizeof(vl_fr) * K, kind, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(b, ws + L.off_bout, sizeof(vl_fr) * K, kind, st);
+  if (ce == cudaSuccess && out_space == VL_HOST) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return cuda_status(ce, "vl_claims_plan_run");
+  if (out_space == VL_HOST && out->status != VL_OK) return out->status;
+  return VL_OK;
+}
+
+extern "C" int32_t vl_prove_matmul_batched(const vl_job* jobs, int32_t njobs, uint64_t seed, void* workspace,
+                                           size_t workspace_bytes, vl_batch_proof* out, vl_fr* claims, vl_fr* a,
+                                           vl_fr* b, void* stream) {
+  vl_claims_plan* C = nullptr;
+  int e = vl_claims_plan_create(jobs, njobs, seed, &C);
+  if (e != VL_OK) return e;
+  e = vl_claims_plan_run(C, workspace, workspace_bytes, out, claims, a, b, VL_HOST, stream);
+  vl_claims_plan_destroy(C);
   return e;
 }

@@ -92,3 +92,36 @@ def test_batch_of_64():
         jobs.append({"P": A, "Q": Bm, "tp": 0, "tq": 0})
     res = gpu_batch(jobs, seed=1)
     assert res.to_bytes() == OB.prove_matmul_batch(jobs, seed=1).to_bytes()
+
+
+def test_claims_plan_reruns_rebinds_device_output():
+    import ctypes
+    rng = np.random.default_rng(7)
+    jobs = _jobs(rng, 3, 40)
+    keep, cj = [], []
+    for i, j in enumerate(jobs):
+        P = j["P"] if i == 0 else torch.from_numpy(np.ascontiguousarray(j["P"])).cuda()  # one host operand
+        Q = torch.from_numpy(np.ascontiguousarray(j["Q"])).cuda()
+        keep += [P, Q]
+        cj.append(B.job(P, Q, j["tp"], j["tq"], 0, j["binds"]))
+    want = OB.prove_matmul_batch(jobs, seed=11).to_bytes()
+    plan = B.ClaimsPlan(cj, 11)
+    n = plan.workspace_bytes()
+    ws1 = torch.empty(n, dtype=torch.uint8, device="cuda")
+    ws2 = torch.empty(n, dtype=torch.uint8, device="cuda")
+    for ws in (ws1, ws1, ws2, ws1):
+        assert plan.run(ws.data_ptr(), n).to_bytes() == want
+    K = len(jobs)
+    dproof = torch.empty(ctypes.sizeof(B.vl_batch_proof), dtype=torch.uint8, device="cuda")
+    dvals = torch.empty(3 * K * 32, dtype=torch.uint8, device="cuda")
+    base = dvals.data_ptr()
+    plan.run(ws2.data_ptr(), n, device_out=(dproof.data_ptr(), base, base + K * 32, base + 2 * K * 32))
+    torch.cuda.synchronize()
+    res = B.BatchedProof(K)
+    ctypes.memmove(ctypes.addressof(res.proof), dproof.cpu().numpy().tobytes(), ctypes.sizeof(B.vl_batch_proof))
+    raw = dvals.cpu().numpy().tobytes()
+    ctypes.memmove(ctypes.addressof(res.claims), raw[:K * 32], K * 32)
+    ctypes.memmove(ctypes.addressof(res.a), raw[K * 32:2 * K * 32], K * 32)
+    ctypes.memmove(ctypes.addressof(res.b), raw[2 * K * 32:], K * 32)
+    assert res.to_bytes() == want
+    plan.destroy()
