@@ -258,7 +258,9 @@ static constexpr int LK_PPT = 1 << LK_PPT_LOG;  // pairs per thread in a round p
 static constexpr int LK_PAIRS = LK_THREADS * LK_PPT;  // pairs per round item
 static constexpr int LK_ENTRIES = 1024;   // table entries per table item (one batch inversion)
 static constexpr int LK_HIST = 8192;      // S entries per histogram item
-static constexpr int LK_TAIL_LOG = 11;    // rounds of at most 2^LK_TAIL_LOG pairs run in one block per proof
+#ifndef LK_TAIL_LOG
+#define LK_TAIL_LOG 11  // rounds of at most 2^LK_TAIL_LOG pairs run in one block per proof
+#endif
 cudaError_t launch_lookup_setup(LkDev* Ls, int np, const LkItem* fac_items, int nfac, const LkItem* hist_items,
                                 int nhist, const LkItem* tab_items, int ntab, cudaStream_t st);
 // Round t: nhi items of proofs in their high rounds, then nlo items of
