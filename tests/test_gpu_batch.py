@@ -125,3 +125,16 @@ def test_claims_plan_reruns_rebinds_device_output():
     ctypes.memmove(ctypes.addressof(res.b), raw[2 * K * 32:], K * 32)
     assert res.to_bytes() == want
     plan.destroy()
+
+
+def test_batch_long_inner_dimension():
+    """k = 2^16 + 8: 17 rounds, folds over 65544 lines, a ragged last round."""
+    rng = np.random.default_rng(8)
+    k = (1 << 16) + 8
+    jobs = []
+    for i in range(2):
+        A, Bm = _rand(rng, (3 + i, k)), _rand(rng, (k, 2 + i))
+        jobs.append({"P": A, "Q": Bm, "tp": 0, "tq": 0})
+    res = gpu_batch(jobs, seed=3)
+    assert res.proof.d1 == 17
+    assert res.to_bytes() == OB.prove_matmul_batch(jobs, seed=3).to_bytes()

@@ -222,3 +222,15 @@ def test_linear_plan_reruns_rebinds_and_device_output():
 
 def ctypes_sizeof_lin():
     return ctypes.sizeof(B.vl_lin_proof)
+
+
+def test_linear_sixteen_matrices():
+    """VL_LIN_MAX matrices in one relation (the coefficient and bind lists at
+    their longest)."""
+    rng = np.random.default_rng(16)
+    mats = [_rand(rng, (33, 47)) for _ in range(B.VL_LIN_MAX)]
+    coeffs = [int(c) for c in rng.integers(-1000, 1000, size=B.VL_LIN_MAX)]
+    binds = [bytes([i]) * 32 for i in range(B.VL_LIN_MAX)]
+    s = Stmt(mats, coeffs, seed=16, binds=binds, trans=[i % 2 for i in range(B.VL_LIN_MAX)])
+    _, out = gpu_prove([s])
+    assert B.lin_proof_bytes(out[0]) == s.oracle_bytes()
