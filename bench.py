@@ -620,7 +620,7 @@ def lookups_main(args, rank, world, local, cpu):
     }))
 
 
-def batched_main(args, rank, world, local):
+def batched_main(args, rank, world, local, cpu=None):
     """The 7B step's products grouped by inner dimension, each group one
     batched-claim proof (a vl_claims_plan per group, replayed every step)."""
     import torch
@@ -697,6 +697,37 @@ def batched_main(args, rank, world, local):
     ms = e0.elapsed_time(e1) / args.steps
     ms_max = max_over_ranks(ms, world, "cuda")
     value = job_value(macs_step, world, ms_max / 1e3)
+    # end to end: the same batches from pinned host operands, host proofs, synchronous
+    e2e = None
+    if not args.no_e2e:
+        host = {}
+        for t in projs:
+            for key in ("X", "W", "A", "B", "dY", "H", "dH"):
+                host[id(t[key])] = torch.from_numpy(t[key]).pin_memory()
+        hgroups = {}
+        for j in jobs:
+            hgroups.setdefault(W.op_shape(j)[1], []).append(
+                B.job(host[id(j["P"])], host[id(j["Q"])], j["tp"], j["tq"], j["seed"]))
+        hplans = {k: B.ClaimsPlan(hgroups[k], seed + k) for k in keys}
+        hsizes = {k: hplans[k].workspace_bytes() for k in keys}
+        del wss
+        hws = {k: torch.empty(hsizes[k], dtype=torch.uint8, device="cuda") for k in keys}
+        for k in keys:  # bind (first run on each workspace)
+            hplans[k].run(hws[k].data_ptr(), hsizes[k], stream)
+        ksteps = max(1, min(args.steps, 3))
+        t1 = time.perf_counter()
+        for _ in range(ksteps):
+            for k in keys:
+                hplans[k].run(hws[k].data_ptr(), hsizes[k], stream)
+        e2e_s = max_over_ranks((time.perf_counter() - t1) / ksteps, world, "cuda")
+        e2e = {"value": job_value(macs_step, world, e2e_s), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(h.numel() * 2 for h in host.values())),
+               "d2h_bytes_per_step": int(sum(ctypes.sizeof(B.vl_batch_proof) + 96 * len(hgroups[k]) for k in keys)),
+               "ms_per_step": 1e3 * e2e_s, "steps": ksteps,
+               "note": "one synchronous plan run per batch (host outputs), operands copied in every run"}
+        for k in keys:
+            hplans[k].destroy()
+    launches = args.steps * sum(7 + 2 * (k - 1).bit_length() for k in keys)
     proof_bytes = sum(len(r.to_bytes()) for r in res)
     # the same products as separate proofs: dims, c, three values per round, a_r, b_r, state
     separate_bytes = sum(24 + 32 + 96 * (W.op_shape(j)[1] - 1).bit_length() + 64 + 32 for j in jobs)
@@ -714,8 +745,8 @@ def batched_main(args, rank, world, local):
                    "host_ms_per_step": 1e3 * wall,
                    "note": "one plan run per batch, each batch on its own stream (plans bound to their "
                            "workspaces, proofs left on the device)"},
-        "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
-        "gpu_launches": None,
+        "roofline": None, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+        "gpu_launches": launches,
     }))
     for k in keys:
         plans[k].destroy()
@@ -729,7 +760,13 @@ def main():
     if args.workload == "serve":
         return serve_main(args, rank, world, local)
     if args.workload == "7b-step-batched":
-        return batched_main(args, rank, world, local)
+        cpu = None
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            rate, dt, nj, macs = oracle_sample(args.workload, W.GLOBAL_SEED, 1)
+            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"the first projection's {nj} products as batched proofs by inner dimension "
+                             f"({macs} MACs), single process, {dt:.1f} s"}
+        return batched_main(args, rank, world, local, cpu)
     if args.workload == "7b-lookups":
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:

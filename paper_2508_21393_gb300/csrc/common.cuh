@@ -295,6 +295,11 @@ cudaError_t launch_batch_finish(const DevProof* dp, int np, BtState* B, int k, c
 // Host helpers of the engine shared with the linear prover.
 bool encode_tc_operand(const void* base, int64_t rows, int64_t cols, int64_t ld, int32_t mode, void* map);
 void set_last_error(const char* msg);
+// Which plan's tables a workspace holds (every plan type registers here, so
+// a plan re-binds when another plan has used its workspace since).
+bool ws_owned_by(const void* owner, const void* ws);
+void ws_claim(const void* owner, const void* ws);
+void ws_release(const void* owner);
 // Batches: one LinDev per proof; chunks of the reduced side's eq table as
 // EqItem {proof, side (unused), i0, i1}.
 cudaError_t launch_linear_start(LinDev* Ls, int nproofs, const EqItem* items, int nitems, cudaStream_t st);

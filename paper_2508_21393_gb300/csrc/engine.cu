@@ -457,20 +457,20 @@ void note_error(const char* where, cudaError_t e) {
 // pointer).  A plan whose workspace was taken over by another plan re-binds
 // (re-uploads its tables) before its next run.
 std::mutex g_ws_mu;
-std::map<const void*, const vl_plan*> g_ws_owner;
+std::map<const void*, const void*> g_ws_owner;  // workspace -> the plan whose tables it holds
 
-bool owns_workspace(const vl_plan* p, const void* ws) {
+bool owns_workspace(const void* p, const void* ws) {
   std::lock_guard<std::mutex> lk(g_ws_mu);
   auto it = g_ws_owner.find(ws);
   return it != g_ws_owner.end() && it->second == p;
 }
 
-void claim_workspace(const vl_plan* p, const void* ws) {
+void claim_workspace(const void* p, const void* ws) {
   std::lock_guard<std::mutex> lk(g_ws_mu);
   g_ws_owner[ws] = p;
 }
 
-void release_workspaces(const vl_plan* p) {
+void release_workspaces(const void* p) {
   std::lock_guard<std::mutex> lk(g_ws_mu);
   for (auto it = g_ws_owner.begin(); it != g_ws_owner.end();)
     it = it->second == p ? g_ws_owner.erase(it) : std::next(it);
@@ -1082,6 +1082,10 @@ bool encode_tc_operand(const void* base, int64_t rows, int64_t cols, int64_t ld,
 
 void set_last_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
 
+bool ws_owned_by(const void* owner, const void* ws) { return owns_workspace(owner, ws); }
+void ws_claim(const void* owner, const void* ws) { claim_workspace(owner, ws); }
+void ws_release(const void* owner) { release_workspaces(owner); }
+
 }  // namespace vl
 
 // ---------------------------------------------------------------------------
@@ -1167,6 +1171,7 @@ struct vl_claims_plan {
   BtState S{};
   ~vl_claims_plan() {
     if (L.p) vl_plan_destroy(L.p);
+    vl::ws_release(this);
   }
 };
 
@@ -1213,7 +1218,7 @@ extern "C" int32_t vl_claims_plan_run(vl_claims_plan* C, void* workspace, size_t
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int e = VL_OK;
   cudaError_t ce = cudaSuccess;
-  if (C->bound_ws != ws) {
+  if (C->bound_ws != ws || !owns_workspace(C, ws)) {  // first run here, or another plan's tables replaced ours
     BtState& S = C->S;
     S.w = reinterpret_cast<Fr*>(ws + L.off_w);
     S.c = reinterpret_cast<Fr*>(ws + L.off_c);
@@ -1231,6 +1236,7 @@ extern "C" int32_t vl_claims_plan_run(vl_claims_plan* C, void* workspace, size_t
     if (e != VL_OK) return e;
     if (ce != cudaSuccess) return cuda_status(ce, "vl_claims_plan_run: bind");
     C->bound_ws = ws;
+    claim_workspace(C, ws);
   }
   e = stage_host_operands(p, ws, st);
   if (e != VL_OK) return e;

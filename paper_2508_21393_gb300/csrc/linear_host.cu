@@ -192,6 +192,7 @@ struct vl_lin_plan {
   ~vl_lin_plan() {
     for (cudaEvent_t& x : ev)
       if (x) cudaEventDestroy(x);
+    ws_release(this);
   }
 };
 
@@ -272,6 +273,7 @@ int lin_bind(vl_lin_plan* P, uint8_t* ws, cudaStream_t st) {
   if (ce == cudaSuccess) ce = fold_tc_prepare();
   if (ce != cudaSuccess) return cuda_fail("linear proofs: bind", ce);
   P->bound_ws = ws;
+  ws_claim(P, ws);
   return VL_OK;
 }
 
@@ -346,7 +348,7 @@ extern "C" int32_t vl_lin_plan_run(vl_lin_plan* P, void* workspace, size_t works
   uint8_t* ws = static_cast<uint8_t*>(workspace);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   P->timed = false;
-  if (P->bound_ws != ws) {
+  if (P->bound_ws != ws || !ws_owned_by(P, ws)) {  // first run here, or another plan used it
     const int e = lin_bind(P, ws, st);
     if (e != VL_OK) return e;
   }

@@ -70,6 +70,7 @@ struct vl_lookup_plan {
   ~vl_lookup_plan() {
     for (cudaEvent_t& x : ev)
       if (x) cudaEventDestroy(x);
+    ws_release(this);
   }
 };
 
@@ -218,6 +219,7 @@ int lk_bind(vl_lookup_plan* P, uint8_t* ws, cudaStream_t st) {
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // the host tables must outlive the copies
   if (ce != cudaSuccess) return cuda_fail("lookup proofs: bind", ce);
   P->bound_ws = ws;
+  ws_claim(P, ws);
   return VL_OK;
 }
 
@@ -264,7 +266,7 @@ extern "C" int32_t vl_lookup_plan_run(vl_lookup_plan* P, void* workspace, size_t
   uint8_t* ws = static_cast<uint8_t*>(workspace);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   P->timed = false;
-  if (P->bound_ws != ws) {
+  if (P->bound_ws != ws || !ws_owned_by(P, ws)) {  // first run here, or another plan used it
     const int e = lk_bind(P, ws, st);
     if (e != VL_OK) return e;
   }

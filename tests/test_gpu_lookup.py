@@ -173,3 +173,34 @@ def test_lookup_7b_projection_remainders_full_size():
         assert B.vl_verify_lookup(hj, p)
     for i in (0, 1):
         assert B.lookup_proof_bytes(out[i]) == looks[i].oracle_bytes()
+
+
+def test_plans_taking_turns_on_one_workspace():
+    """A lookup plan, a linear plan and a claims plan alternate on one
+    workspace: each run re-binds when another plan used the workspace since,
+    and every proof stays equal to the oracle's."""
+    rng = np.random.default_rng(21)
+    x = Look(rng.integers(0, 64, size=(10, 30)), 0, 6, seed=2)
+    lplan = B.LookupPlan([x.job()])
+    A = rng.integers(-100, 100, size=(12, 20)).astype(np.int16)
+    G = rng.integers(-100, 100, size=(12, 20)).astype(np.int16)
+    A2 = (A - G).astype(np.int16)
+    lin_t = [torch.from_numpy(m).cuda() for m in (A2, A, G)]
+    linplan = B.LinPlan([B.lin_job([B.mat(t) for t in lin_t], [1, -1, 1], 5)])
+    from oracle import prove_linear, prove_matmul_batch
+    P = rng.integers(-1000, 1000, size=(9, 16)).astype(np.int16)
+    Q = rng.integers(-1000, 1000, size=(16, 7)).astype(np.int16)
+    bt = [torch.from_numpy(P).cuda(), torch.from_numpy(Q).cuda()]
+    cplan = B.ClaimsPlan([B.job(bt[0], bt[1], 0, 0, 0)], 8)
+    n = max(lplan.workspace_bytes(), linplan.workspace_bytes(), cplan.workspace_bytes())
+    ws = _ws(n)
+    want_l = x.oracle_bytes()
+    want_lin = prove_linear([A2, A, G], [1, -1, 1], seed=5).to_bytes()
+    want_b = prove_matmul_batch([{"P": P, "Q": Q, "tp": 0, "tq": 0}], seed=8).to_bytes()
+    for _ in range(2):
+        assert B.lookup_proof_bytes(lplan.run(ws.data_ptr(), n)[0]) == want_l
+        assert B.lin_proof_bytes(linplan.run(ws.data_ptr(), n)[0]) == want_lin
+        assert cplan.run(ws.data_ptr(), n).to_bytes() == want_b
+    lplan.destroy()
+    linplan.destroy()
+    cplan.destroy()
