@@ -346,8 +346,11 @@ struct LkEq {
 // with 2^sE >= 32 LK_PPT the warp's pairs lie in one block of 2^sE pairs, so
 // the block's hiP factor multiplies each lane's sums once; with smaller
 // blocks it multiplies every pair's eq factor.
+#ifndef LK_PASS_MINB
+#define LK_PASS_MINB 2  // resident CTAs per SM the register budget of the passes allows
+#endif
 template <bool JR, int MODE>
-__global__ void __launch_bounds__(LK_THREADS, 2) lk_pass_kernel(LkDev* Ls, int t, const LkItem* items) {
+__global__ void __launch_bounds__(LK_THREADS, LK_PASS_MINB) lk_pass_kernel(LkDev* Ls, int t, const LkItem* items) {
   __shared__ Fr red[6 * (LK_THREADS / 32)];
   const LkItem it = items[blockIdx.x];
   LkDev* L = Ls + it.proof;
