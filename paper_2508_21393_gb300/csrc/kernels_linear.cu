@@ -27,12 +27,11 @@ constexpr int LIN_FAC_THREADS = LIN_THREADS - 32;  // the last warp computes the
 // Factor entry j of one side (lo entries first): a product of eq factors,
 // starting from 1 in double-Montgomery (lo of the reduced side) or
 // Montgomery form (everything else).
-__device__ Fr lin_factor(const Fr* x, int d, int j, bool lo_double, bool* is_lo, int* idx, int size) {
+__device__ Fr lin_factor(const Fr* x, int d, int j, bool lo_double, bool* is_lo, int* idx) {
   const int s = (d + 1) >> 1, dh = d - s, nlo = 1 << s;
   *is_lo = j < nlo;
   const int jj = *is_lo ? j : j - nlo, nv = *is_lo ? s : dh, base = *is_lo ? dh : 0;
   *idx = jj;
-  (void)size;
   Fr acc = (*is_lo && lo_double) ? fr_r2() : fr_r1();
   for (int t = 0; t < nv; t++) {
     const Fr& xt = x[base + t];
@@ -68,8 +67,7 @@ __global__ void __launch_bounds__(LIN_THREADS) lin_start_kernel(LinDev* Ls) {
       const bool xside = j < nx;
       bool is_lo;
       int idx;
-      const Fr v = xside ? lin_factor(xs, L->d0, j, rr, &is_lo, &idx, L->rows)
-                         : lin_factor(ys, L->d1, j - nx, !rr, &is_lo, &idx, L->cols);
+      const Fr v = xside ? lin_factor(xs, L->d0, j, rr, &is_lo, &idx) : lin_factor(ys, L->d1, j - nx, !rr, &is_lo, &idx);
       L->fac[(xside ? 0 : 2 * EQ_FAC) + (is_lo ? 0 : EQ_FAC) + idx] = v;
     }
   } else if (tid == LIN_FAC_THREADS) {
