@@ -229,17 +229,40 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": LIN_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }))
         return
-    per_step = []
-    macs_step = None
-    for _ in range(args.warmup):
-        oracle_sample(args.workload, W.GLOBAL_SEED, 1)
-    for _ in range(args.steps):
-        rate, dt, nj, macs = oracle_sample(args.workload, W.GLOBAL_SEED, 1)
-        per_step.append(dt)
-        macs_step = macs
-    total = sum(per_step)
-    value = macs_step * args.steps / total
-    sample = f"1 projection ({nj} proofs, {macs_step} MACs) of the {args.workload} workload per step"
+    if args.steps + args.warmup <= 40 or args.workload == "7b-step-batched":
+        # one whole projection per step (a few seconds each)
+        per_step = []
+        macs_step = None
+        for _ in range(args.warmup):
+            oracle_sample(args.workload, W.GLOBAL_SEED, 1)
+        for _ in range(args.steps):
+            rate, dt, nj, macs = oracle_sample(args.workload, W.GLOBAL_SEED, 1)
+            per_step.append(dt)
+            macs_step = macs
+        total = sum(per_step)
+        value = macs_step * args.steps / total
+        sample = f"1 projection ({nj} proofs, {macs_step} MACs) of the {args.workload} workload per step"
+    else:
+        # many steps: one product per step, cycling through the first
+        # projection's products, so the run stays within a few minutes
+        import oracle
+        spec = W.step_layers(STEP_KIND[args.workload], W.GLOBAL_SEED)[:1]
+        jobs = [j for t in (W.lora_projection(W.GLOBAL_SEED, *s) for s in spec)
+                for j in products(args.workload, t, W.GLOBAL_SEED)]
+
+        def one(i):
+            j = jobs[i % len(jobs)]
+            t0 = time.perf_counter()
+            oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"])
+            return time.perf_counter() - t0, W.macs(j)
+
+        for i in range(args.warmup):
+            one(i)
+        per = [one(i) for i in range(args.steps)]
+        total = sum(dt for dt, _ in per)
+        value = sum(m for _, m in per) / total
+        sample = (f"one product per step, cycling through the first projection's {len(jobs)} products "
+                  f"({sum(m for _, m in per)} MACs over the timed steps)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
