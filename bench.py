@@ -466,8 +466,12 @@ def update_main(args, rank, world, local, cpu):
         pass
     hbm_peak, hbm_note = (peaks["hbm_gbs"], "measured") if "hbm_gbs" in peaks else (6800.0, "fallback")
     hbm_gbs = 2 * entries / (fold_ms / 1e3) / 1e9
+    # DRAM bytes of one fold launch over the whole update workload, from an ncu
+    # capture of this kernel on it (profiles/fold_tc_kernel_7b_update.md:
+    # 172.4 MB read + 52.1 MB written)
+    traffic = 224.5e6 if not args.layers else None
     roof = {"bound": "hbm", "kernel": "fold_tc_kernel", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
-            "frac": hbm_gbs / hbm_peak, "traffic": None,
+            "frac": hbm_gbs / hbm_peak, "traffic": traffic,
             "peak_note": f"{hbm_note} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
             "algorithmic_bytes_per_launch": 2 * entries}
     # End to end: pinned host operands in (staged by the library), host proofs out.
