@@ -294,8 +294,8 @@ typedef struct vl_lin_proof {
 /* Device workspace vl_prove_linear needs for this batch (0 on invalid
  * arguments: see vl_prove_linear). */
 size_t vl_linear_workspace_bytes(const vl_lin_job* jobs, int32_t njobs);
-/* Prove a batch of linear relations on the GPU, one independent transcript
- * each.  Operands: int16 (VL_EINVAL otherwise), logical rows and columns at
+/* Prove a batch of 1 .. 65535 linear relations on the GPU, one independent
+ * transcript each.  Operands: int16 (VL_EINVAL otherwise), logical rows and columns at
  * most VL_MAX_REDUCE (VL_ESHAPE), on the device or the host; device operands
  * with a 16-byte aligned base and a leading dimension of a multiple of 8
  * entries are read in place, all others are first copied into the
@@ -365,9 +365,9 @@ typedef struct vl_lookup_proof {
 } vl_lookup_proof;
 
 typedef struct vl_lookup_plan vl_lookup_plan;
-/* Device workspace the batch needs (0 on invalid arguments: S not int16,
- * transposed or empty; n > 2^VL_LOOKUP_MAX_LOG_D; log2_n out of range;
- * reserved != 0). */
+/* Device workspace a batch of 1 .. 65535 lookups needs (0 on invalid
+ * arguments: S not int16, transposed or empty; n > 2^VL_LOOKUP_MAX_LOG_D;
+ * log2_n out of range; |t0| > 2^40; reserved != 0). */
 size_t vl_lookup_workspace_bytes(const vl_lookup_job* jobs, int32_t njobs);
 /* Plans, as for linear proofs: the statements are copied (S's data is read
  * at every run; host S is copied into the workspace at every run), tables
