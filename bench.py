@@ -44,7 +44,7 @@ SM_MAX_MHZ = 2070.0
 # per clock, a wide (64-bit result) one taking two of them.
 MADWIDE_PER_SM_CLK = 32
 STEP_KIND = {"7b-step": "7b", "7b-proj": "7b-proj", "13b-step": "13b", "serve": "7b-proj", "7b-update": "7b",
-             "7b-step-paper-route": "7b", "7b-lookups": "7b", "7b-step-batched": "7b"}
+             "7b-step-paper-route": "7b", "7b-lookups": "7b", "7b-step-batched": "7b", "7b-step-all": "7b"}
 WORKLOADS = {
     "7b-step": "batched 7B-shaped LoRA step: 32 layers x {q,k,v,o}, hidden 4096, seq 512, ranks {8,16,64}",
     "7b-proj": "one 7B-shaped LoRA projection, n=1024, d=k=4096, r=16, eight products",
@@ -57,6 +57,9 @@ WORKLOADS = {
                   "G_B (r x 4096) (table 2^12)}, ranks {8,16,64}, one batched plan run",
     "7b-step-batched": "the batched 7B-shaped LoRA step's 1024 products as 5 batched-claim proofs (one per inner "
                        "dimension: 4096, 512, and the ranks 8, 16, 64), one transcript and one sumcheck each",
+    "7b-step-all": "the built hot path of one 7B-shaped LoRA step: the 1024 matmul proofs (one plan, graph), the "
+                   "256 parameter-update proofs and the 512 rescale-remainder range lookups, each plan on its own "
+                   "stream",
     "7b-update": "parameter updates of the 7B-shaped LoRA step (Eq. eq:grad_update_ab): 32 layers x {q,k,v,o} x "
                  "{A' = A - G_A (4096 x r), B' = B - G_B (r x 4096)}, ranks {8,16,64}, linear zkMat, one batched call",
     "serve": "serving stream: Poisson arrivals (20 jobs/s) of single-layer jobs (one projection's 8 products), "
@@ -779,6 +782,105 @@ def batched_main(args, rank, world, local, cpu=None):
         plans[k].destroy()
 
 
+def all_main(args, rank, world, local):
+    """Matmul proofs, parameter-update proofs and remainder lookups of one 7B
+    step, each as its plan on its own stream; ms_per_step is the fork-join
+    time on the timing stream."""
+    import torch
+    from paper_2508_21393_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.lib()
+    seed = rank_seed(rank)
+    projs, jobs = step_jobs("7b-step", seed, args.layers)
+    macs_step = sum(W.macs(j) for j in jobs)
+    dev = {}
+    for t in projs:
+        for key in ("X", "W", "A", "B", "dY", "H", "dH"):
+            dev[id(t[key])] = torch.from_numpy(t[key]).cuda()
+    djobs = [B.job(dev[id(j["P"])], dev[id(j["Q"])], j["tp"], j["tq"], j["seed"]) for j in jobs]
+    opts = B.vl_batch_opts()
+    opts.persistent = 2
+    opts.timing_runs = 1
+    mplan = B.vl_plan_create(djobs, opts)
+    mn = B.vl_plan_workspace_bytes(mplan)
+    mws = torch.empty(mn, dtype=torch.uint8, device="cuda")
+    mout = torch.empty(len(djobs) * ctypes.sizeof(B.vl_proof), dtype=torch.uint8, device="cuda")
+    ustm = [st for t in projs for st in W.update_statements(t, seed)]
+    udev = [[torch.from_numpy(m).cuda() for m in st["mats"]] for st in ustm]
+    uplan = B.LinPlan([B.lin_job([B.mat(x) for x in d], list(st["coeffs"]), st["seed"]) for d, st in zip(udev, ustm)])
+    un = uplan.workspace_bytes()
+    uws = torch.empty(un, dtype=torch.uint8, device="cuda")
+    uout = torch.empty(len(ustm) * ctypes.sizeof(B.vl_lin_proof), dtype=torch.uint8, device="cuda")
+    looks = [x for t in projs for x in W.rescale_lookups(t, seed)]
+    ldev = [torch.from_numpy(np.ascontiguousarray(x["S"])).cuda() for x in looks]
+    lplan = B.LookupPlan([B.lookup_job(B.mat(d), x["t0"], x["log2_n"], x["seed"]) for d, x in zip(ldev, looks)])
+    ln = lplan.workspace_bytes()
+    lws = torch.empty(ln, dtype=torch.uint8, device="cuda")
+    lout = torch.empty(len(looks) * ctypes.sizeof(B.vl_lookup_proof), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    sm, su, sl = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    fork, jm, ju, jl = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
+
+    def step():
+        fork.record(stream)
+        for s2 in (sm, su, sl):
+            s2.wait_event(fork)
+        B.vl_plan_run(mplan, mws.data_ptr(), mn, mout.data_ptr(), B.VL_DEVICE, sm)
+        jm.record(sm)
+        uplan.run(uws.data_ptr(), un, uout.data_ptr(), B.VL_DEVICE, su)
+        ju.record(su)
+        lplan.run(lws.data_ptr(), ln, lout.data_ptr(), B.VL_DEVICE, sl)
+        jl.record(sl)
+        for e in (jm, ju, jl):
+            stream.wait_event(e)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    st_m = np.frombuffer(mout.cpu().numpy().tobytes(), dtype=np.int32).reshape(len(djobs), -1)[:, 6]
+    st_u = [B.vl_lin_proof.from_buffer_copy(uout.cpu().numpy().tobytes(), i * ctypes.sizeof(B.vl_lin_proof)).status
+            for i in range(len(ustm))]
+    st_l = [B.vl_lookup_proof.from_buffer_copy(lout.cpu().numpy().tobytes(), i * ctypes.sizeof(B.vl_lookup_proof)).status
+            for i in range(len(looks))]
+    assert (st_m == 0).all() and not any(st_u) and not any(st_l)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    time.sleep(0.6)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = job_value(macs_step, world, ms_max / 1e3)
+    uplan.destroy()
+    lplan.destroy()
+    B.vl_plan_destroy(mplan)
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int16 operands, Fr (255-bit) arithmetic", "data": "synthetic",
+        "config": {"workload": WORKLOADS["7b-step-all"] + (f", first {args.layers} layers" if args.layers else ""),
+                   "matmul_proofs": len(djobs), "update_proofs": len(ustm), "lookup_proofs": len(looks),
+                   "macs_per_step": macs_step, "l2": "inputs larger than L2 (no flush)",
+                   "note": "value counts the matmul MACs only; the update and lookup proofs ride along"},
+        "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk, "gpu_launches": None,
+    }))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -786,6 +888,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "serve":
         return serve_main(args, rank, world, local)
+    if args.workload == "7b-step-all":
+        return all_main(args, rank, world, local)
     if args.workload == "7b-step-batched":
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
