@@ -299,6 +299,7 @@ def mat(a, trans=0, dtype=None):
     m.reserved = 0
     if dtype is not None:
         m.dtype = dtype
+    m._keep = a  # the array or tensor stays alive as long as this descriptor
     return m
 
 
@@ -317,6 +318,7 @@ def job(P, Q, tp=0, tq=0, seed=0, binds=None):
     j.P = mat(P, tp)
     j.Q = mat(Q, tq)
     j.fs = fs_init(seed, binds)
+    j._keep = (P, Q)  # the operands stay alive as long as the job
     return j
 
 
@@ -360,6 +362,7 @@ def lin_job(mats, coeffs, seed=0, binds=None):
     if len(mats) != len(coeffs):
         raise ValueError("one coefficient per matrix")
     j = vl_lin_job()
+    j._keep = [getattr(m, "_keep", None) for m in mats]  # the operands stay alive as long as the job
     j._mats = (vl_mat * len(mats))(*mats)
     j._coeffs = (vl_fr * len(coeffs))(*[fr(c) for c in coeffs])
     j.mats = ctypes.cast(j._mats, ctypes.POINTER(vl_mat))
@@ -390,6 +393,7 @@ def lookup_job(S, t0, log2_n, seed=0, bind=None):
     [t0, t0 + 2^log2_n)."""
     j = vl_lookup_job()
     j.S = S
+    j._keep = getattr(S, "_keep", None)  # the values stay alive as long as the job
     j.t0 = int(t0)
     j.log2_n = int(log2_n)
     j.reserved = 0
