@@ -96,3 +96,19 @@ def test_host_verifier_rejections(L):
     bad = [j["C"].copy() for j in jobs]
     bad[2][1, 1] += 1
     assert not B.vl_verify_matmul_batched(cj, [B.mat(C) for C in bad], 2, to_c(p))
+
+
+def test_host_verifier_argument_errors(L):
+    rng = np.random.default_rng(4)
+    jobs = _jobs(rng, 2, 6)
+    Cs = [B.mat(j["C"]) for j in jobs]
+    r = B.BatchedProof(2)
+    # inner dimensions differ
+    other = _jobs(rng, 1, 7)
+    with pytest.raises(B.VLError):
+        B.vl_verify_matmul_batched(_c_jobs(jobs[:1] + other), Cs[:1] + [B.mat(other[0]["C"])], 0, r)
+    # a claimed product of the wrong shape
+    with pytest.raises(B.VLError):
+        B.vl_verify_matmul_batched(_c_jobs(jobs), [Cs[1], Cs[0]], 0, r)
+    # a zeroed proof of a valid statement is simply rejected
+    assert not B.vl_verify_matmul_batched(_c_jobs(jobs), Cs, 0, r)

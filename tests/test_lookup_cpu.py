@@ -126,3 +126,22 @@ def test_rescale_lookup_statements_hold():
     assert np.array_equal(Z + 128, ((Z + 128) >> 8) * 256 + rho)
     for x in looks:
         assert x["S"].min() >= 0 and x["S"].max() < (1 << x["log2_n"])
+
+
+def test_host_verifier_argument_errors(L):
+    S = np.zeros((3, 4), np.int16)
+    p = B.vl_lookup_proof()
+    j = _job(S, 0, 4)
+    j.S.trans = 1
+    with pytest.raises(B.VLError):
+        B.vl_verify_lookup(j, p)
+    j = _job(S, 0, 4)
+    j.log2_n = 17
+    with pytest.raises(B.VLError):
+        B.vl_verify_lookup(j, p)
+    j = _job(S, 0, 4)
+    j.reserved = 2
+    with pytest.raises(B.VLError):
+        B.vl_verify_lookup(j, p)
+    # a zeroed proof of a valid statement is simply rejected
+    assert not B.vl_verify_lookup(_job(S, 0, 4), p)
