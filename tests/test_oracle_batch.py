@@ -107,3 +107,42 @@ def test_rejections():
     assert not OB.verify_matmul_batch(jobs[::-1], Cs[::-1], p, seed=2)[0]
     with pytest.raises(ValueError):
         OB.prove_matmul_batch(jobs + _jobs(rng, 1, 13), seed=2)
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Mistakes planted in the batch oracle (rho^(i+1) weights, the round
+    message's g(1) and g(2) swapped in the interpolation) each fail the
+    rho-weighted brute-force pin or completeness."""
+    rng = np.random.default_rng(12)
+    jobs = _jobs(rng, 3, 4)
+    Cs = [_claimed(j) for j in jobs]
+
+    def ok():
+        try:
+            p = OB.prove_matmul_batch(jobs, seed=6)
+        except AssertionError:
+            return False
+        return OB.verify_matmul_batch(jobs, Cs, p, seed=6)[0]
+
+    assert ok()
+    real_pow = pow
+    monkeypatch.setattr(OB, "pow", lambda b, e, m=None: real_pow(b, e + 1, m) if m else real_pow(b, e), raising=False)
+    p = OB.prove_matmul_batch(jobs, seed=6)
+    # the shifted weights still give a self-consistent proof, but not the rho^i-weighted polynomial
+    rho = p.point["rho"]
+    monkeypatch.setattr(OB, "pow", real_pow, raising=False)
+    g0 = 0
+    for i, j in enumerate(jobs):
+        A, B_ = _op(j["P"], j["tp"]), _op(j["Q"], j["tq"])
+        u, v = p.point["u"][i], p.point["v"][i]
+        tot = 0
+        for b in range(1 << (p.d1 - 1)):
+            w = [0] + [(b >> (p.d1 - 2 - q)) & 1 for q in range(p.d1 - 1)]
+            tot += mle_eval_matrix(A, u, w) * mle_eval_matrix(B_, w, v)
+        g0 += real_pow(rho, i, R_MOD) * tot
+    assert g0 % R_MOD != p.rounds[0][0]
+    orig = OB.round_poly_eval
+    monkeypatch.setattr(OB, "round_poly_eval", lambda g0_, g1, g2, x: orig(g0_, g2, g1, x))
+    assert not ok()
+    monkeypatch.setattr(OB, "round_poly_eval", orig)
+    assert ok()

@@ -101,3 +101,29 @@ def test_row_and_column_variables_are_not_swapped():
     assert swapped != pf.evals[0]
     bad = oracle.LinearProof(pf.rows, pf.cols, pf.d0, pf.d1, [swapped, (-swapped) % R_MOD], pf.state)
     assert not oracle.verify_linear([M, -M], [1, 1], bad, seed=2)[0]
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Mistakes planted in the oracle's evaluation (the row and column points
+    swapped, the point's variables in reverse order) each fail the
+    hypercube-sum pin or completeness."""
+    from oracle import linear as OLin
+    rng = np.random.default_rng(7)
+    M = _rand(rng, (4, 4))
+    mats, coeffs = [M, -M], [1, 1]
+
+    def pinned():
+        pf = oracle.prove_linear(mats, coeffs, seed=4)
+        x, y = pf.point["x"], pf.point["y"]
+        table = [int(M[i][j]) for i in range(4) for j in range(4)]
+        ok_eval = pf.evals[0] == mle_eval_bruteforce(table, list(x) + list(y))
+        return ok_eval and oracle.verify_linear(mats, coeffs, pf, seed=4)[0]
+
+    assert pinned()
+    orig = OLin.mle_eval_matrix
+    monkeypatch.setattr(OLin, "mle_eval_matrix", lambda A, x, y: orig(A, y, x))
+    assert not pinned()
+    monkeypatch.setattr(OLin, "mle_eval_matrix", lambda A, x, y: orig(A, list(x)[::-1], list(y)[::-1]))
+    assert not pinned()
+    monkeypatch.setattr(OLin, "mle_eval_matrix", orig)
+    assert pinned()
