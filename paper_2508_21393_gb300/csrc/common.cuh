@@ -268,6 +268,7 @@ cudaError_t launch_lookup_setup(LkDev* Ls, int np, const LkItem* fac_items, int 
 cudaError_t launch_lookup_round(LkDev* Ls, int np, int t, const LkItem* items, int nhi, int nlo,
                                 vl_lookup_proof* out, cudaStream_t st);
 cudaError_t launch_lookup_finish(LkDev* Ls, int np, vl_lookup_proof* out, cudaStream_t st);
+cudaError_t launch_lookup_passes(LkDev* Ls, int t, const LkItem* items, int nhi, int nlo, cudaStream_t st);
 
 // Batched-claim sumcheck (kernels_batch.cu): the batch transcript and
 // buffers, in the workspace.
