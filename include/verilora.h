@@ -388,7 +388,8 @@ void vl_lookup_plan_destroy(vl_lookup_plan* plan);
 int32_t vl_prove_lookup(const vl_lookup_job* jobs, int32_t njobs, void* workspace, size_t workspace_bytes,
                         vl_lookup_proof* out, void* stream);
 /* Host verifier against host S (int16 or int64): VL_OK, VL_REJECT or an
- * argument error. */
+ * argument error (VL_EINVAL as for the prover, VL_ESHAPE when S has more
+ * than 2^VL_LOOKUP_MAX_LOG_D entries). */
 int32_t vl_verify_lookup(const vl_lookup_job* job, const vl_lookup_proof* proof);
 
 /* ---------------------------------------------------------------------------

@@ -37,7 +37,8 @@ int check_job(const vl_lookup_job& J) {
   if (M.space != VL_DEVICE && M.space != VL_HOST) return VL_EINVAL;
   if (M.rows < 1 || M.cols < 1) return VL_ESHAPE;
   if (M.ld < M.cols) return VL_EINVAL;
-  if (M.rows * M.cols > (int64_t(1) << VL_LOOKUP_MAX_LOG_D)) return VL_ESHAPE;
+  const int64_t maxd = int64_t(1) << VL_LOOKUP_MAX_LOG_D;
+  if (M.rows > maxd || M.cols > maxd || M.rows * M.cols > maxd) return VL_ESHAPE;  // no overflow: each <= 2^24
   return VL_OK;
 }
 

@@ -243,8 +243,10 @@ extern "C" int32_t vl_verify_lookup(const vl_lookup_job* job, const vl_lookup_pr
   if ((e = check_host_mat(M)) != VL_OK) return e;
   if (M->trans != 0 || M->dtype == VL_FR_MONT || job->reserved != 0) return VL_EINVAL;
   if (job->log2_n < 0 || job->log2_n > VL_LOOKUP_MAX_LOG_N) return VL_EINVAL;
+  if (job->t0 < -(int64_t(1) << 40) || job->t0 > (int64_t(1) << 40)) return VL_EINVAL;  // the prover's bound
+  const int64_t maxd = int64_t(1) << VL_LOOKUP_MAX_LOG_D;
+  if (M->rows > maxd || M->cols > maxd || M->rows * M->cols > maxd) return VL_ESHAPE;
   const int64_t n = M->rows * M->cols;
-  if (n > (int64_t(1) << VL_LOOKUP_MAX_LOG_D)) return VL_ESHAPE;
   const int ln = job->log2_n, L = std::max(ln, ceil_log2(n));
   const int64_t N = int64_t(1) << ln, D = int64_t(1) << L, t0 = job->t0;
   if (proof->n != n || proof->log2_d != L || proof->log2_n != ln || proof->t0 != t0) return VL_REJECT;

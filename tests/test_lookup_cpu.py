@@ -53,6 +53,11 @@ def test_workspace_sizing_and_argument_errors(L):
     big = B.vl_mat()
     big.data, big.rows, big.cols, big.ld, big.dtype, big.space = 256, 1 << 13, (1 << 11) + 1, (1 << 11) + 1, 1, 0
     assert B.vl_lookup_workspace_bytes([B.lookup_job(big, 0, 8)]) == 0  # more than 2^24 entries
+    big.rows = big.cols = big.ld = 1 << 40  # rows * cols would overflow int64
+    assert B.vl_lookup_workspace_bytes([B.lookup_job(big, 0, 8)]) == 0
+    assert B.vl_lookup_workspace_bytes([_job(S, (1 << 40) + 1, 8)]) == 0
+    assert B.vl_lookup_workspace_bytes([_job(S, -(1 << 40) - 1, 8)]) == 0
+    assert B.vl_lookup_workspace_bytes([_job(S, -(1 << 40), 8)]) > 0
     assert B.vl_lookup_workspace_bytes([]) == 0
     with pytest.raises(B.VLError):
         B.LookupPlan([_job(S, 0, 17)])
@@ -143,5 +148,14 @@ def test_host_verifier_argument_errors(L):
     j.reserved = 2
     with pytest.raises(B.VLError):
         B.vl_verify_lookup(j, p)
+    for t0 in ((1 << 40) + 1, -(1 << 40) - 1):  # the prover's bound on the table's offset
+        with pytest.raises(B.VLError) as ei:
+            B.vl_verify_lookup(_job(S, t0, 4), p)
+        assert ei.value.code == B.VL_EINVAL
+    big = B.vl_mat()
+    big.data, big.rows, big.cols, big.ld, big.dtype, big.space = 256, 1 << 40, 1 << 40, 1 << 40, B.VL_I16, B.VL_HOST
+    with pytest.raises(B.VLError) as ei:  # more than 2^24 entries; rows * cols would overflow int64
+        B.vl_verify_lookup(B.lookup_job(big, 0, 4), p)
+    assert ei.value.code == B.VL_ESHAPE
     # a zeroed proof of a valid statement is simply rejected
     assert not B.vl_verify_lookup(_job(S, 0, 4), p)
