@@ -193,10 +193,20 @@ size_t vl_plan_workspace_bytes(const vl_plan* plan);
  * run on a workspace uploads the plan's descriptor tables into it (a
  * synchronous copy); later runs reuse them.  Several plans may take turns on
  * one workspace (same base pointer): a plan re-uploads its tables when
- * another plan used the workspace since its last run.  Runs that overlap in
- * time on the GPU must use disjoint workspaces. */
+ * another plan used the workspace since its last run.  Anything else that
+ * writes to the workspace between runs must be followed by
+ * vl_workspace_forget.  Runs that overlap in time on the GPU must use
+ * disjoint workspaces. */
 int32_t vl_plan_run(vl_plan* plan, void* workspace, size_t workspace_bytes, vl_proof* out,
                     int32_t out_space, void* stream);
+/* The library records, per workspace base pointer, which plan's tables the
+ * workspace holds (for plans of every kind: matmul, linear, lookup, claims).
+ * Call this after anything other than a plan run wrote to a workspace, and
+ * before a buffer freed and reallocated at the same address is given to a
+ * plan again: it forgets the record, so the next plan run there re-uploads
+ * its tables.  Host only; no CUDA call.  Returns 1 if a record was dropped,
+ * 0 if there was none, -VL_EINVAL for a null pointer. */
+int32_t vl_workspace_forget(const void* workspace);
 /* Number of kernel launches one vl_plan_run enqueues (graph nodes included). */
 int32_t vl_plan_launches(const vl_plan* plan);
 /*
@@ -311,7 +321,8 @@ int32_t vl_prove_linear(const vl_lin_job* jobs, int32_t njobs, void* workspace, 
  * matrices are read at every run) and, on its first run with a workspace,
  * uploads its tables there (synchronising `stream`); later runs with that
  * workspace only enqueue the host-operand copies and five kernels.  The
- * workspace must not be used by anything else between runs.  out_space
+ * workspace must not be used by anything else between runs (else call
+ * vl_workspace_forget before the next run).  out_space
  * VL_DEVICE: `out` is device memory and the run is asynchronous (each
  * proof's status field reports its outcome); VL_HOST: as vl_prove_linear. */
 typedef struct vl_lin_plan vl_lin_plan;

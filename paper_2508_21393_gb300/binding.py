@@ -35,7 +35,8 @@ EXPORTS = ("vl_version", "vl_strerror", "vl_last_error", "vl_workspace_bytes", "
            "vl_lookup_plan_workspace_bytes", "vl_lookup_plan_run", "vl_lookup_plan_phase_ms",
            "vl_lookup_plan_destroy", "vl_prove_lookup", "vl_verify_lookup", "vl_batch_workspace_bytes",
            "vl_prove_matmul_batched", "vl_verify_matmul_batched", "vl_claims_plan_create",
-           "vl_claims_plan_workspace_bytes", "vl_claims_plan_run", "vl_claims_plan_destroy")
+           "vl_claims_plan_workspace_bytes", "vl_claims_plan_run", "vl_claims_plan_destroy",
+           "vl_workspace_forget")
 VL_NOALLOC_SCRATCH_BYTES = 8 << 20
 VL_LIN_MAX = 16
 VL_LOOKUP_MAX_LOG_D = 24
@@ -246,6 +247,8 @@ def lib():
     L.vl_claims_plan_destroy.restype = None
     L.vl_verify_linear.restype = ctypes.c_int32
     L.vl_encode.restype = ctypes.c_int32
+    L.vl_workspace_forget.argtypes = [ctypes.c_void_p]
+    L.vl_workspace_forget.restype = ctypes.c_int32
     _lib = L
     return L
 
@@ -440,6 +443,16 @@ def vl_strerror(code):
 
 def vl_last_error():
     return lib().vl_last_error().decode()
+
+
+def vl_workspace_forget(workspace):
+    """Forget which plan's tables a workspace (a device pointer) holds: True
+    if a record was dropped.  Call it after writing to a workspace outside a
+    plan run, or before reusing a freed buffer's address for a plan."""
+    code = lib().vl_workspace_forget(workspace)
+    if code < 0:
+        raise VLError(-code, "vl_workspace_forget")
+    return code == 1
 
 
 def vl_workspace_bytes(jobs, opts=None):

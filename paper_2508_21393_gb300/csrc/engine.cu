@@ -928,6 +928,12 @@ int32_t vl_plan_phase_ms(vl_plan* plan, float* ms, int32_t max_runs, int32_t res
 
 const char* vl_last_error(void) { return g_last_error; }
 
+int32_t vl_workspace_forget(const void* workspace) {
+  if (!workspace) return -VL_EINVAL;
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  return g_ws_owner.erase(workspace) ? 1 : 0;
+}
+
 void vl_plan_destroy(vl_plan* plan) {
   if (!plan) return;
   release_workspaces(plan);

@@ -204,3 +204,51 @@ def test_plans_taking_turns_on_one_workspace():
     lplan.destroy()
     linplan.destroy()
     cplan.destroy()
+
+
+class _MatmulPlan:
+    """A vl_plan with the other plans' method names."""
+
+    def __init__(self, jobs):
+        self.h, self.n = B.vl_plan_create(jobs), len(jobs)
+
+    def workspace_bytes(self):
+        return B.vl_plan_workspace_bytes(self.h)
+
+    def first_proof(self, w, n):
+        out = (B.vl_proof * self.n)()
+        B.vl_plan_run(self.h, w, n, out, B.VL_HOST)
+        return B.proof_bytes(out[0])
+
+    def destroy(self):
+        B.vl_plan_destroy(self.h)
+
+
+def test_forgotten_workspace_is_bound_again():
+    """vl_workspace_forget drops a workspace's record; the next run of any
+    plan kind re-uploads its tables there (the record comes back, which only
+    the binding step writes) and proves the same bytes; a destroyed plan
+    leaves no record.  The workspace is never overwritten here."""
+    rng = np.random.default_rng(22)
+    x = Look(rng.integers(0, 32, size=(6, 20)), 0, 5, seed=3)
+    A = rng.integers(-50, 50, size=(8, 12)).astype(np.int16)
+    lin_t = [torch.from_numpy(m).cuda() for m in (A, A)]
+    P = rng.integers(-100, 100, size=(5, 8)).astype(np.int16)
+    Q = rng.integers(-100, 100, size=(8, 3)).astype(np.int16)
+    bt = [torch.from_numpy(P).cuda(), torch.from_numpy(Q).cuda()]
+    plans = [(B.LookupPlan([x.job()]), lambda p, w, n: B.lookup_proof_bytes(p.run(w, n)[0])),
+             (B.LinPlan([B.lin_job([B.mat(t) for t in lin_t], [1, -1], 6)]),
+              lambda p, w, n: B.lin_proof_bytes(p.run(w, n)[0])),
+             (B.ClaimsPlan([B.job(bt[0], bt[1], 0, 0, 0)], 9), lambda p, w, n: p.run(w, n).to_bytes()),
+             (_MatmulPlan([B.job(bt[0], bt[1], 0, 0, 4)]), _MatmulPlan.first_proof)]
+    for plan, run in plans:
+        n = plan.workspace_bytes()
+        ws = _ws(n)
+        first = run(plan, ws.data_ptr(), n)
+        assert B.vl_workspace_forget(ws.data_ptr())
+        assert not B.vl_workspace_forget(ws.data_ptr())
+        assert run(plan, ws.data_ptr(), n) == first
+        assert B.vl_workspace_forget(ws.data_ptr())  # bound again by the second run
+        run(plan, ws.data_ptr(), n)
+        plan.destroy()
+        assert not B.vl_workspace_forget(ws.data_ptr())

@@ -39,6 +39,14 @@ def test_exports_every_declared_symbol(L):
         assert hasattr(L, name), name
 
 
+def test_workspace_forget_without_a_record(L):
+    # no plan ran on this address: nothing to forget; no CUDA call is made
+    assert B.vl_workspace_forget(4096) is False
+    assert L.vl_workspace_forget(None) == -B.VL_EINVAL
+    with pytest.raises(B.VLError):
+        B.vl_workspace_forget(None)
+
+
 def test_version_and_strerror(L):
     assert B.vl_version() == 100
     assert B.vl_strerror(B.VL_OK) == "ok"
