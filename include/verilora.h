@@ -199,8 +199,10 @@ size_t vl_plan_workspace_bytes(const vl_plan* plan);
  * disjoint workspaces. */
 int32_t vl_plan_run(vl_plan* plan, void* workspace, size_t workspace_bytes, vl_proof* out,
                     int32_t out_space, void* stream);
-/* The library records, per workspace base pointer, which plan's tables the
- * workspace holds (for plans of every kind: matmul, linear, lookup, claims).
+/* Workspace bookkeeping (the paper has no counterpart: plans are this
+ * library's way of replaying one step's proofs).  The library records, per
+ * workspace base pointer, which plan's tables the workspace holds (for plans
+ * of every kind: matmul, linear, lookup, claims).
  * Call this after anything other than a plan run wrote to a workspace, and
  * before a buffer freed and reallocated at the same address is given to a
  * plan again: it forgets the record, so the next plan run there re-uploads
