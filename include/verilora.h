@@ -9,8 +9,15 @@
  * v in F^d2 from the transcript and runs d1 rounds of sumcheck on
  *     sum_{w in {0,1}^d1} A~(u, w) . B~(w, v) = c   (c = C~(u, v) when C = A.B)
  * over the BLS12-381 scalar field (Sec. V), with SHA-256 Fiat-Shamir
- * challenges (Sec. IV-A footnote).  Commitments and lookups are outside this
- * library: the verifier evaluates A~, B~, C~ directly from the matrices.
+ * challenges (Sec. IV-A footnote).  Commitments are outside this library:
+ * every verifier evaluates the MLEs it needs directly from the matrices.
+ *
+ * Also proved (sections below): linear relations sum_q c_q op(M_q) = 0, the
+ * parameter updates and matrix additions of Sec. IV (vl_prove_linear);
+ * range lookups of int16 values in a table of consecutive integers
+ * (Protocol 1, Eq. eq:lookup-sumcheck; vl_prove_lookup); and K products of
+ * one inner dimension under one transcript with one random-combination
+ * sumcheck (Sec. IV, putting everything together; vl_prove_matmul_batched).
  *
  * Conventions.
  *  - Field elements (vl_fr) are canonical, 8 x 32-bit limbs, little endian.
