@@ -37,9 +37,11 @@
  * library never allocates device memory.  Operands must stay unchanged
  * until the call's stream work has finished.
  *
- * Errors.  Every call returns VL_OK (0) or one of the codes below; nothing
- * throws.  vl_strerror() names a code.  A failed call leaves outputs
- * unspecified.
+ * Errors.  Every call returns VL_OK (0) or one of the codes below; no C++
+ * exception crosses this interface (a failed host allocation inside the
+ * library returns VL_ENOMEM, or 0 from a *_workspace_bytes call, with a
+ * message in vl_last_error()).  vl_strerror() names a code.  A failed call
+ * leaves outputs unspecified.
  */
 #ifndef VERILORA_H
 #define VERILORA_H
@@ -55,7 +57,7 @@ extern "C" {
 #define VL_OK 0
 #define VL_EINVAL 1   /* null pointer, bad enum, bad leading dimension       */
 #define VL_ESHAPE 2   /* inner dimensions differ, empty or oversized dims    */
-#define VL_ENOMEM 3   /* workspace smaller than required                     */
+#define VL_ENOMEM 3   /* workspace smaller than required, or host allocation */
 #define VL_ECUDA 4    /* a CUDA runtime call failed                          */
 #define VL_ETIMEOUT 5 /* a bounded device-side wait gave up                  */
 #define VL_REJECT 6   /* vl_verify_matmul: the proof does not verify         */
@@ -157,8 +159,9 @@ int32_t vl_version(void);
 /* Name of a status code (static string). */
 const char* vl_strerror(int32_t status);
 
-/* Detail of the last VL_ECUDA failure on the calling thread: the failing
- * step and the CUDA error string ("" if none).  Valid until the next call. */
+/* Detail of the last VL_ECUDA failure on the calling thread (the failing
+ * step and the CUDA error string), or of a host-side failure reported as
+ * VL_ENOMEM; "" if none.  Valid until the next call. */
 const char* vl_last_error(void);
 
 /*

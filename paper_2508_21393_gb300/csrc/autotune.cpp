@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "verilora.h"
+#include "abi_guard.h"
 
 namespace {
 
@@ -100,6 +101,7 @@ float time_candidate(const vl_job* jobs, int32_t njobs, const vl_batch_opts& o, 
 extern "C" int32_t vl_autotune(const vl_job* jobs, int32_t njobs, const vl_batch_opts* base, void* workspace,
                                size_t workspace_bytes, void* stream, int32_t runs, vl_batch_opts* best,
                                float* best_ms) {
+  VL_ABI_TRY
   if (!jobs || njobs < 1 || !workspace || !best) return VL_EINVAL;
   if (reinterpret_cast<uintptr_t>(workspace) & (ALIGN - 1)) return VL_EINVAL;
   const std::string sig = signature(jobs, njobs);
@@ -160,6 +162,7 @@ extern "C" int32_t vl_autotune(const vl_job* jobs, int32_t njobs, const vl_batch
   *best = cur;
   if (best_ms) *best_ms = cur_ms;
   return VL_OK;
+  VL_ABI_CATCH(VL_ENOMEM)
 }
 
 extern "C" void vl_autotune_clear(void) {

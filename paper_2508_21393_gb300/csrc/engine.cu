@@ -15,11 +15,13 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
 
 #include "common.cuh"
+#include "abi_guard.h"
 
 using namespace vl;
 
@@ -847,17 +849,14 @@ int run_plan(vl_plan* p, void* workspace, size_t ws_bytes, vl_proof* out, int32_
 
 int make_plan(const vl_job* jobs, int32_t njobs, const vl_batch_opts* opts, vl_plan** out) {
   if (!jobs || njobs < 1 || !out) return VL_EINVAL;
-  vl_plan* p = new (std::nothrow) vl_plan();
+  std::unique_ptr<vl_plan> p(new (std::nothrow) vl_plan());
   if (!p) return VL_ENOMEM;
   p->jobs.assign(jobs, jobs + njobs);
   if (opts) p->opts = *opts;
   if (p->opts.timing_runs > 0) p->ring_runs = p->opts.timing_runs;
-  int e = build_plan(p);
-  if (e != VL_OK) {
-    delete p;
-    return e;
-  }
-  *out = p;
+  const int e = build_plan(p.get());
+  if (e != VL_OK) return e;
+  *out = p.release();
   return VL_OK;
 }
 
@@ -872,7 +871,7 @@ const char* vl_strerror(int32_t s) {
     case VL_OK: return "ok";
     case VL_EINVAL: return "invalid argument";
     case VL_ESHAPE: return "invalid shape";
-    case VL_ENOMEM: return "workspace too small";
+    case VL_ENOMEM: return "workspace too small or host allocation failed";
     case VL_ECUDA: return "CUDA error";
     case VL_ETIMEOUT: return "device wait timed out";
     case VL_REJECT: return "proof rejected";
@@ -882,15 +881,19 @@ const char* vl_strerror(int32_t s) {
 }
 
 size_t vl_workspace_bytes(const vl_job* jobs, int32_t njobs, const vl_batch_opts* opts) {
+  VL_ABI_TRY
   vl_plan* p = nullptr;
   if (make_plan(jobs, njobs, opts, &p) != VL_OK) return 0;
   const size_t t = p->total;
   delete p;
   return t;
+  VL_ABI_CATCH(0)
 }
 
 int32_t vl_plan_create(const vl_job* jobs, int32_t njobs, const vl_batch_opts* opts, vl_plan** plan) {
+  VL_ABI_TRY
   return make_plan(jobs, njobs, opts, plan);
+  VL_ABI_CATCH(VL_ENOMEM)
 }
 
 size_t vl_plan_workspace_bytes(const vl_plan* plan) { return plan ? plan->total : 0; }
@@ -906,9 +909,11 @@ int32_t vl_plan_launches(const vl_plan* plan) {
 
 int32_t vl_plan_run(vl_plan* plan, void* workspace, size_t workspace_bytes, vl_proof* out, int32_t out_space,
                     void* stream) {
+  VL_ABI_TRY
   if (!plan) return VL_EINVAL;
   const bool graph = plan->opts.use_graph != 2;
   return run_plan(plan, workspace, workspace_bytes, out, out_space, static_cast<cudaStream_t>(stream), graph);
+  VL_ABI_CATCH(VL_ENOMEM)
 }
 
 int32_t vl_plan_phase_ms(vl_plan* plan, float* ms, int32_t max_runs, int32_t reset) {
@@ -951,6 +956,7 @@ void vl_plan_destroy(vl_plan* plan) {
 
 int32_t vl_prove_batch(const vl_job* jobs, int32_t njobs, void* workspace, size_t workspace_bytes, vl_proof* out,
                        int32_t out_space, void* stream, const vl_batch_opts* opts) {
+  VL_ABI_TRY
   vl_plan* p = nullptr;
   int e = make_plan(jobs, njobs, opts, &p);
   if (e != VL_OK) return e;
@@ -959,6 +965,7 @@ int32_t vl_prove_batch(const vl_job* jobs, int32_t njobs, void* workspace, size_
   e = run_plan(p, workspace, workspace_bytes, out, out_space, static_cast<cudaStream_t>(stream), false);
   vl_plan_destroy(p);
   return e;
+  VL_ABI_CATCH(VL_ENOMEM)
 }
 
 int32_t vl_prove_matmul(const vl_mat* P, const vl_mat* Q, const vl_fs_init* fs, void* workspace,
@@ -1019,6 +1026,7 @@ int noalloc_scratch_ptr(void** out) {
 
 extern "C" int32_t vl_prove_matmul_noalloc(const vl_mat* P, const vl_mat* Q, const vl_fs_init* fs, vl_proof* out,
                                            void* stream) {
+  VL_ABI_TRY
   if (!P || !Q || !fs || !out) return VL_EINVAL;
   if (P->space != VL_DEVICE || Q->space != VL_DEVICE) return VL_EINVAL;
   vl_job j;
@@ -1062,6 +1070,7 @@ extern "C" int32_t vl_prove_matmul_noalloc(const vl_mat* P, const vl_mat* Q, con
   }
   vl_plan_destroy(p);
   return e;
+  VL_ABI_CATCH(VL_ENOMEM)
 }
 
 namespace vl {
@@ -1160,11 +1169,13 @@ int batch_layout(const vl_job* jobs, int32_t njobs, BatchLayout* L) {
 }  // namespace
 
 extern "C" size_t vl_batch_workspace_bytes(const vl_job* jobs, int32_t njobs) {
+  VL_ABI_TRY
   BatchLayout L;
   const int e = batch_layout(jobs, njobs, &L);
   const size_t total = e == VL_OK ? L.total : 0;
   if (L.p) vl_plan_destroy(L.p);
   return total;
+  VL_ABI_CATCH(0)
 }
 
 // A batch bound to one workspace at a time: the plan of its products, the
@@ -1182,15 +1193,13 @@ struct vl_claims_plan {
 };
 
 extern "C" int32_t vl_claims_plan_create(const vl_job* jobs, int32_t njobs, uint64_t seed, vl_claims_plan** plan) {
+  VL_ABI_TRY
   if (!plan) return VL_EINVAL;
   *plan = nullptr;
-  vl_claims_plan* C = new (std::nothrow) vl_claims_plan;
+  std::unique_ptr<vl_claims_plan> C(new (std::nothrow) vl_claims_plan);
   if (!C) return VL_ENOMEM;
   const int e = batch_layout(jobs, njobs, &C->L);
-  if (e != VL_OK) {
-    delete C;
-    return e;
-  }
+  if (e != VL_OK) return e;
   C->seed = seed;
   for (DevProof& P : C->L.p->proofs) P.seed = seed;  // member transcripts use the batch seed
   BtState& S = C->S;
@@ -1204,8 +1213,9 @@ extern "C" int32_t vl_claims_plan_create(const vl_job* jobs, int32_t njobs, uint
     S.pbeg[t] = C->L.roff[t];
     S.pend[t] = C->L.roff[t + 1];
   }
-  *plan = C;
+  *plan = C.release();
   return VL_OK;
+  VL_ABI_CATCH(VL_ENOMEM)
 }
 
 extern "C" size_t vl_claims_plan_workspace_bytes(const vl_claims_plan* plan) { return plan ? plan->L.total : 0; }
@@ -1214,6 +1224,7 @@ extern "C" void vl_claims_plan_destroy(vl_claims_plan* plan) { delete plan; }
 
 extern "C" int32_t vl_claims_plan_run(vl_claims_plan* C, void* workspace, size_t workspace_bytes, vl_batch_proof* out,
                                       vl_fr* claims, vl_fr* a, vl_fr* b, int32_t out_space, void* stream) {
+  VL_ABI_TRY
   if (!C || !workspace || !out || !claims || !a || !b || (out_space != VL_DEVICE && out_space != VL_HOST))
     return VL_EINVAL;
   if (reinterpret_cast<uintptr_t>(workspace) & (ALIGN - 1)) return VL_EINVAL;
@@ -1273,6 +1284,7 @@ extern "C" int32_t vl_claims_plan_run(vl_claims_plan* C, void* workspace, size_t
   if (ce != cudaSuccess) return cuda_status(ce, "vl_claims_plan_run");
   if (out_space == VL_HOST && out->status != VL_OK) return out->status;
   return VL_OK;
+  VL_ABI_CATCH(VL_ENOMEM)
 }
 
 extern "C" int32_t vl_prove_matmul_batched(const vl_job* jobs, int32_t njobs, uint64_t seed, void* workspace,

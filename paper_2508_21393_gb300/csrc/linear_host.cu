@@ -17,9 +17,11 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include "common.cuh"
+#include "abi_guard.h"
 
 using namespace vl;
 
@@ -292,20 +294,20 @@ cudaError_t lin_events(vl_lin_plan* P) {
 }  // namespace
 
 extern "C" size_t vl_linear_workspace_bytes(const vl_lin_job* jobs, int32_t njobs) {
+  VL_ABI_TRY
   LinLayout L;
   return lin_layout(jobs, njobs, &L) == VL_OK ? L.total : 0;
+  VL_ABI_CATCH(0)
 }
 
 extern "C" int32_t vl_lin_plan_create(const vl_lin_job* jobs, int32_t njobs, vl_lin_plan** plan) {
+  VL_ABI_TRY
   if (!plan) return VL_EINVAL;
   *plan = nullptr;
-  vl_lin_plan* P = new (std::nothrow) vl_lin_plan;
+  std::unique_ptr<vl_lin_plan> P(new (std::nothrow) vl_lin_plan);
   if (!P) return VL_ENOMEM;
-  int e = lin_layout(jobs, njobs, &P->lay);
-  if (e != VL_OK) {
-    delete P;
-    return e;
-  }
+  const int e = lin_layout(jobs, njobs, &P->lay);
+  if (e != VL_OK) return e;
   P->mats.resize(njobs);
   P->Ls.assign(njobs, LinDev{});
   P->dps.assign(njobs, DevProof{});
@@ -317,10 +319,7 @@ extern "C" int32_t vl_lin_plan_create(const vl_lin_job* jobs, int32_t njobs, vl_
     P->mats[i].assign(J.mats, J.mats + J.nmats);
     for (int q = 0; q < J.nmats; q++) {
       for (int l = 0; l < 8; l++) L.coeffs[q].v[l] = J.coeffs[q].limb[l];
-      if (!lt_r(L.coeffs[q])) {  // coefficients are canonical
-        delete P;
-        return VL_EINVAL;
-      }
+      if (!lt_r(L.coeffs[q])) return VL_EINVAL;  // coefficients are canonical
       if (J.binds) std::memcpy(L.binds[q], J.binds + 32 * q, 32);
     }
     L.rows = S.rows;
@@ -333,14 +332,16 @@ extern "C" int32_t vl_lin_plan_create(const vl_lin_job* jobs, int32_t njobs, vl_
     L.nblk = S.nblk;
     L.seed = J.seed;
   }
-  *plan = P;
+  *plan = P.release();
   return VL_OK;
+  VL_ABI_CATCH(VL_ENOMEM)
 }
 
 extern "C" size_t vl_lin_plan_workspace_bytes(const vl_lin_plan* plan) { return plan ? plan->lay.total : 0; }
 
 extern "C" int32_t vl_lin_plan_run(vl_lin_plan* P, void* workspace, size_t workspace_bytes, vl_lin_proof* out,
                                    int32_t out_space, void* stream) {
+  VL_ABI_TRY
   if (!P || !workspace || !out || (out_space != VL_DEVICE && out_space != VL_HOST)) return VL_EINVAL;
   if (reinterpret_cast<uintptr_t>(workspace) & (ALIGN - 1)) return VL_EINVAL;
   const LinLayout& lay = P->lay;
@@ -390,6 +391,7 @@ extern "C" int32_t vl_lin_plan_run(vl_lin_plan* P, void* workspace, size_t works
     for (int i = 0; i < lay.np; i++)
       if (out[i].status != VL_OK) return out[i].status;
   return VL_OK;
+  VL_ABI_CATCH(VL_ENOMEM)
 }
 
 extern "C" int32_t vl_lin_plan_phase_ms(vl_lin_plan* P, float ms[3]) {

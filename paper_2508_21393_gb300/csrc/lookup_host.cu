@@ -8,10 +8,12 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <vector>
 
 #include "common.cuh"
+#include "abi_guard.h"
 
 using namespace vl;
 
@@ -239,28 +241,30 @@ cudaError_t lk_events(vl_lookup_plan* P) {
 }  // namespace
 
 extern "C" size_t vl_lookup_workspace_bytes(const vl_lookup_job* jobs, int32_t njobs) {
+  VL_ABI_TRY
   vl_lookup_plan P;
   return lk_build(&P, jobs, njobs) == VL_OK ? P.total : 0;
+  VL_ABI_CATCH(0)
 }
 
 extern "C" int32_t vl_lookup_plan_create(const vl_lookup_job* jobs, int32_t njobs, vl_lookup_plan** plan) {
+  VL_ABI_TRY
   if (!plan) return VL_EINVAL;
   *plan = nullptr;
-  vl_lookup_plan* P = new (std::nothrow) vl_lookup_plan;
+  std::unique_ptr<vl_lookup_plan> P(new (std::nothrow) vl_lookup_plan);
   if (!P) return VL_ENOMEM;
-  const int e = lk_build(P, jobs, njobs);
-  if (e != VL_OK) {
-    delete P;
-    return e;
-  }
-  *plan = P;
+  const int e = lk_build(P.get(), jobs, njobs);
+  if (e != VL_OK) return e;
+  *plan = P.release();
   return VL_OK;
+  VL_ABI_CATCH(VL_ENOMEM)
 }
 
 extern "C" size_t vl_lookup_plan_workspace_bytes(const vl_lookup_plan* plan) { return plan ? plan->total : 0; }
 
 extern "C" int32_t vl_lookup_plan_run(vl_lookup_plan* P, void* workspace, size_t workspace_bytes,
                                       vl_lookup_proof* out, int32_t out_space, void* stream) {
+  VL_ABI_TRY
   if (!P || !workspace || !out || (out_space != VL_DEVICE && out_space != VL_HOST)) return VL_EINVAL;
   if (reinterpret_cast<uintptr_t>(workspace) & (ALIGN - 1)) return VL_EINVAL;
   if (workspace_bytes < P->total) return VL_ENOMEM;
@@ -302,6 +306,7 @@ extern "C" int32_t vl_lookup_plan_run(vl_lookup_plan* P, void* workspace, size_t
     for (int i = 0; i < P->np; i++)
       if (out[i].status != VL_OK) return out[i].status;
   return VL_OK;
+  VL_ABI_CATCH(VL_ENOMEM)
 }
 
 extern "C" int32_t vl_lookup_plan_phase_ms(vl_lookup_plan* P, float ms[3]) {

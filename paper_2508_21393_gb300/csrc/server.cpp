@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "verilora.h"
+#include "abi_guard.h"
 
 namespace {
 
@@ -333,6 +334,7 @@ void worker_main(vl_server* s) {
 }  // namespace
 
 extern "C" int32_t vl_server_create(const vl_server_opts* opts, vl_server** out) {
+  VL_ABI_TRY
   if (!opts || !out || !opts->arena || opts->arena_bytes < ARENA_ALIGN) return VL_EINVAL;
   for (int i = 0; i < 4; i++)
     if (opts->reserved[i]) return VL_EINVAL;
@@ -358,10 +360,12 @@ extern "C" int32_t vl_server_create(const vl_server_opts* opts, vl_server** out)
   s->worker = std::thread(worker_main, s);
   *out = s;
   return VL_OK;
+  VL_ABI_CATCH(VL_ENOMEM)
 }
 
 extern "C" int32_t vl_server_submit(vl_server* s, const vl_job* jobs, int32_t njobs, vl_proof* out,
                                     uint64_t* ticket) {
+  VL_ABI_TRY
   if (!s || !jobs || njobs < 1 || !out || !ticket) return VL_EINVAL;
   Request r;
   r.jobs.assign(jobs, jobs + njobs);
@@ -376,6 +380,7 @@ extern "C" int32_t vl_server_submit(vl_server* s, const vl_job* jobs, int32_t nj
   }
   s->cv.notify_one();
   return VL_OK;
+  VL_ABI_CATCH(VL_ENOMEM)
 }
 
 extern "C" int32_t vl_server_poll(vl_server* s, vl_server_done* done, int32_t max, int32_t* ndone) {

@@ -14,6 +14,7 @@
 #include "fr.cuh"
 #include "transcript.cuh"
 #include "verilora.h"
+#include "abi_guard.h"
 
 using namespace vl;
 
@@ -112,6 +113,7 @@ int check_host_mat(const vl_mat* M) {
 
 extern "C" int32_t vl_verify_matmul(const vl_mat* P, const vl_mat* Q, const vl_mat* C, const vl_fs_init* fs,
                                     const vl_proof* proof) {
+  VL_ABI_TRY
   int e;
   if ((e = check_host_mat(P)) != VL_OK || (e = check_host_mat(Q)) != VL_OK || (e = check_host_mat(C)) != VL_OK)
     return e;
@@ -162,12 +164,14 @@ extern "C" int32_t vl_verify_matmul(const vl_mat* P, const vl_mat* Q, const vl_m
   if (!fr_eq(to_mont(ar), mle_eval(A, u, rs))) return VL_REJECT;
   if (!fr_eq(to_mont(br), mle_eval(B, rs, v))) return VL_REJECT;
   return VL_OK;
+  VL_ABI_CATCH(VL_ENOMEM)
 }
 
 // Host verifier of a linear zkMat proof (sum_q c_q op(M_q) = 0, Sec. IV):
 // replays the transcript from the statement, checks sum_q c_q e_q = 0 and the
 // final state, and evaluates every M_q~(x, y) from the matrices.
 extern "C" int32_t vl_verify_linear(const vl_lin_job* job, const vl_lin_proof* proof) {
+  VL_ABI_TRY
   if (!job || !proof || !job->mats || !job->coeffs || job->nmats < 1 || job->nmats > VL_LIN_MAX || job->reserved)
     return VL_EINVAL;
   const vl_mat* mats = job->mats;
@@ -213,6 +217,7 @@ extern "C" int32_t vl_verify_linear(const vl_lin_job* job, const vl_lin_proof* p
   for (int q = 0; q < nmats; q++)
     if (!fr_eq(to_mont(ev[q]), mle_eval(HostMat{&mats[q]}, x, y))) return VL_REJECT;
   return VL_OK;
+  VL_ABI_CATCH(VL_ENOMEM)
 }
 
 namespace {
@@ -237,6 +242,7 @@ Fr cubic_interp(const Fr (&g)[4], const Fr& x) {
 // and T~(r_low) computed here), then checks the evaluations against A, S, B
 // and m recomputed from S and T (the stand-in for commitment openings).
 extern "C" int32_t vl_verify_lookup(const vl_lookup_job* job, const vl_lookup_proof* proof) {
+  VL_ABI_TRY
   if (!job || !proof) return VL_EINVAL;
   const vl_mat* M = &job->S;
   int e;
@@ -346,6 +352,7 @@ extern "C" int32_t vl_verify_lookup(const vl_lookup_job* job, const vl_lookup_pr
   }
   if (!fr_eq(ea, am) || !fr_eq(es, sm) || !fr_eq(eb, bm) || !fr_eq(em, mm)) return VL_REJECT;
   return VL_OK;
+  VL_ABI_CATCH(VL_ENOMEM)
 }
 
 namespace {
@@ -374,6 +381,7 @@ std::vector<uint8_t> merkle_root_host(std::vector<uint8_t> level, size_t nleaves
 extern "C" int32_t vl_verify_matmul_batched(const vl_job* jobs, const vl_mat* C, int32_t njobs, uint64_t seed,
                                             const vl_batch_proof* proof, const vl_fr* claims, const vl_fr* a,
                                             const vl_fr* b) {
+  VL_ABI_TRY
   if (!jobs || !C || !proof || !claims || !a || !b || njobs < 1 || njobs > 65535) return VL_EINVAL;
   int e;
   int64_t k = -1;
@@ -472,4 +480,5 @@ extern "C" int32_t vl_verify_matmul_batched(const vl_job* jobs, const vl_mat* C,
     if (!fr_eq(to_mont(fr_from_api(b[i])), mle_eval(HostMat{&jobs[i].Q}, r, vs[i]))) return VL_REJECT;
   }
   return VL_OK;
+  VL_ABI_CATCH(VL_ENOMEM)
 }
