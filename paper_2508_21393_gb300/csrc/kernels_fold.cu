@@ -1,4 +1,6 @@
 // Fold kernel: one CTA per fold tile (see fold_dev.cuh).
+#include <mutex>
+
 #include "fold_dev.cuh"
 
 namespace vl {
@@ -16,7 +18,9 @@ __global__ void __launch_bounds__(FOLD_THREADS, 2) fold_kernel(const FoldTask* _
 // The limit is per kernel and process-wide, so it only ever grows: a plan
 // bound later with smaller tiles must not lower it under an earlier plan.
 cudaError_t fold_set_smem(int smem_bytes) {
+  static std::mutex mu;  // plans are bound from several host threads
   static int current = 48 * 1024;
+  std::lock_guard<std::mutex> lk(mu);
   if (smem_bytes <= current) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e == cudaSuccess) current = smem_bytes;

@@ -48,6 +48,9 @@
 // be ahead of another.  Every wait is bounded; a wait that runs out marks the
 // proof VL_ETIMEOUT, and the CTA drains its copies and MMAs before it frees
 // TMEM and returns.
+#include <atomic>
+#include <mutex>
+
 #include "fold_dev.cuh"
 #include "fr_dev.cuh"
 
@@ -604,7 +607,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 cudaError_t fold_tc_prepare() {
+  static std::mutex mu;  // plans are bound from several host threads
   static bool done = false;
+  std::lock_guard<std::mutex> lk(mu);
   if (done) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(fold_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
   if (e == cudaSuccess) done = true;
@@ -614,12 +619,14 @@ cudaError_t fold_tc_prepare() {
 cudaError_t launch_fold_tc(const TcTile* tiles, int ntiles, const DevProof* proofs, unsigned long long wait_ns,
                            cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
-  static int sms = 0;
+  static std::atomic<int> sm_count{0};  // launches come from several host threads
+  int sms = sm_count.load(std::memory_order_relaxed);
   if (!sms) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    sm_count.store(sms, std::memory_order_relaxed);
   }
   const int grid = ntiles < sms ? ntiles : sms;
   fold_tc_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(tiles, ntiles, proofs, wait_ns);

@@ -1,4 +1,6 @@
 // Rounds kernel: one CTA per proof (see rounds_dev.cuh).
+#include <atomic>
+
 #include "rounds_dev.cuh"
 
 namespace vl {
@@ -25,13 +27,13 @@ cudaError_t launch_rounds(const DevProof* proofs, int nproofs, vl_proof* out, in
   } else if (threads == 256) {
     rounds_kernel<3, 256><<<nproofs, 256, RND_SMEM, st>>>(proofs, out);
   } else if (variant == 2 || variant == 3) {
-    static int set = 0;
+    static std::atomic<int> set{0};  // launches come from several host threads
     const int smem = variant == 2 ? 100 * 1024 : 70 * 1024;
-    if (set < smem) {
+    if (set.load(std::memory_order_acquire) < smem) {
       cudaError_t e =
           cudaFuncSetAttribute(rounds_kernel<4, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
       if (e != cudaSuccess) return e;
-      set = 100 * 1024;
+      set.store(100 * 1024, std::memory_order_release);
     }
     rounds_kernel<4, 128><<<nproofs, 128, smem, st>>>(proofs, out);
   } else if (variant == 4) {

@@ -14,6 +14,8 @@
 // runs out marks the proof VL_ETIMEOUT and skips the tile.  `never_ready`
 // (a proof index, or -1) is a test hook: that proof's ready flag is never
 // set, so its tiles exercise the timeout path.
+#include <mutex>
+
 #include "fold_dev.cuh"
 #include "prologue_dev.cuh"
 #include "rounds_dev.cuh"
@@ -89,7 +91,9 @@ __global__ void __launch_bounds__(FOLD_THREADS, 2) step_kernel(const StepItem* _
 }
 
 cudaError_t step_set_smem(int smem_bytes) {
+  static std::mutex mu;  // plans are bound from several host threads
   static int current = 48 * 1024;
+  std::lock_guard<std::mutex> lk(mu);
   if (smem_bytes <= current) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e == cudaSuccess) current = smem_bytes;
