@@ -10,7 +10,8 @@ point with probability at most (d0 + d1)/|F| (Schwartz-Zippel).  The LoRA
 parameter update A' = A - eta dA (Eq. eq:grad_update_ab) is the instance
 M = (A', A, dA), c = (1, -1, eta) over F.
 
-Protocol (Fiat-Shamir; the byte format is this project's convention):
+Protocol (Fiat-Shamir; the byte format is this project's convention, so
+parity unpinned for the format):
   S0 = SHA256(DOMAIN || seed u64le || rows, cols, q u32le
               || c_1 .. c_q (32 B each) || bind_1 .. bind_q (32 B each))
   x = squeeze('x', d0), y = squeeze('y', d1)    (d0 = ceil log2 rows, d1 for cols)

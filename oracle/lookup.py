@@ -28,7 +28,8 @@ Readings (the paper prints the identity only):
   from S and T and checks the final evaluations directly (the stand-in for
   opening proofs, as for the matmul sumcheck).
 
-Protocol (Fiat-Shamir; byte format is this project's convention):
+Protocol (Fiat-Shamir; byte format is this project's convention, so parity
+unpinned for the format):
   S0 = SHA256(DOMAIN || seed u64le || n, log2 D, log2 N u32le || t0 i64le || bind)
   beta = squeeze('b', 1); alpha = squeeze('a', 1); u = squeeze('u', log2 D)
   claim_0 = alpha + alpha^2
