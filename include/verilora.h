@@ -37,6 +37,12 @@
  * library never allocates device memory.  Operands must stay unchanged
  * until the call's stream work has finished.
  *
+ * Process-wide state (each guarded for calls from several host threads):
+ * the autotuner's cache (vl_autotune_clear), the per-workspace record of
+ * which plan's tables a workspace holds (vl_workspace_forget), the scratch
+ * array and lock of vl_prove_matmul_noalloc, and one-time kernel attribute
+ * settings.  vl_last_error() is per thread.
+ *
  * Errors.  Every call returns VL_OK (0) or one of the codes below; no C++
  * exception crosses this interface (a failed host allocation inside the
  * library returns VL_ENOMEM, or 0 from a *_workspace_bytes call, with a
