@@ -34,8 +34,11 @@
  * Ownership.  The caller owns every buffer: operand matrices, the device
  * workspace (size from vl_workspace_bytes / vl_plan_workspace_bytes, any
  * alignment >= 256 bytes), the proof outputs and the CUDA stream.  The
- * library never allocates device memory.  Operands must stay unchanged
- * until the call's stream work has finished.
+ * library never calls cudaMalloc: its only device memory of its own is the
+ * fixed scratch array of vl_prove_matmul_noalloc, part of the loaded
+ * module.  (The proving server stages proofs in pinned host buffers it
+ * allocates and frees itself.)  Operands must stay unchanged until the
+ * call's stream work has finished.
  *
  * Process-wide state (each guarded for calls from several host threads):
  * the autotuner's cache (vl_autotune_clear), the per-workspace record of
