@@ -68,6 +68,21 @@ def test_rounds_are_rho_weighted_brute_force_sums(K, k):
         assert p.d1 == 0 and all(p.claims[i] == p.a[i] * p.b[i] % R_MOD for i in range(K))
 
 
+@pytest.mark.parametrize("k,tp,tq", [(1, 0, 0), (6, 1, 0), (16, 0, 1), (21, 1, 1)])
+def test_one_product_is_the_single_sumcheck_at_the_same_point(k, tp, tq):
+    """K = 1 (rho^0 = 1): the batch's claim, rounds and final values are the
+    single-product sumcheck's, run with the batch's challenges u, v, r."""
+    rng = np.random.default_rng(50 + k)
+    jobs = _jobs(rng, 1, k, shapes=[(5, 3)], trans=[(tp, tq)])
+    p = OB.prove_matmul_batch(jobs, seed=8)
+    pt = p.point
+    from oracle.sumcheck import prove_matmul
+    s = prove_matmul(jobs[0]["P"], jobs[0]["Q"], tp, tq, override={"u": pt["u"][0], "v": pt["v"][0], "r": pt["r"]})
+    assert s.c == p.claims[0]
+    assert [tuple(g) for g in s.g] == p.rounds
+    assert (s.a_r, s.b_r) == (p.a[0], p.b[0])
+
+
 @pytest.mark.parametrize("K,k", [(1, 7), (5, 16), (3, 33)])
 def test_completeness(K, k):
     rng = np.random.default_rng(K + k)
