@@ -21,7 +21,7 @@ def _run(*args):
     return json.loads(lines[0])
 
 
-@pytest.mark.parametrize("workload", ["7b-update", "7b-lookups"])
+@pytest.mark.parametrize("workload", ["7b-step", "7b-update", "7b-lookups", "7b-step-batched"])
 def test_reference_arm_json(workload):
     d = _run("--workload", workload, "--steps", "1", "--warmup", "0")
     assert KEYS <= set(d)
