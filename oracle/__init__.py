@@ -9,7 +9,10 @@ footnote on Fiat-Shamir), and the linear zkMat proofs of matrix additions
 eq:grad_update_ab is one), and the lookup-argument sumcheck of Protocol 1
 (Eq. eq:lookup-sumcheck) for range tables, and the batched-claim sumcheck
 that proves many products with one transcript (Sec. IV, composition by
-random aggregation).  It uses Python integers and ``hashlib`` only,
+random aggregation), and the chained proof of one LoRA projection in which
+the claims on intermediate tensors are reduced through the rescale
+relations instead of being opened (Sec. IV, sequential composition).  It
+uses Python integers and ``hashlib`` only,
 with NumPy object arrays as the one library matmul step.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
@@ -25,18 +28,21 @@ SHA-256 itself is pinned by the FIPS 180-4 test vectors.
 
 from .field import R_MOD, fr, fr_add, fr_sub, fr_mul, fr_inv, fr_to_bytes, fr_from_bytes
 from .transcript import Transcript
-from .mle import eq_table, eq_value, mle_eval_bruteforce, mle_eval_matrix, fold_rows, fold_cols
+from .mle import (eq_table, eq_value, eq_eval, mle_eval_bruteforce, mle_eval_bind, mle_eval_matrix,
+                  fold_rows, fold_cols)
 from .sumcheck import Proof, prove_matmul, verify_matmul, round_poly_eval
 from .encode import encode_montgomery, limbs_le32
 from .linear import LinearProof, prove_linear, verify_linear
 from .lookup import LookupProof, prove_lookup, verify_lookup, cubic_eval
 from .batch import BatchProof, prove_matmul_batch, verify_matmul_batch, merkle_root
+from .chain import ChainProof, prove_chain, verify_chain
 
 __all__ = [
     "R_MOD", "fr", "fr_add", "fr_sub", "fr_mul", "fr_inv", "fr_to_bytes", "fr_from_bytes",
-    "Transcript", "eq_table", "eq_value", "mle_eval_bruteforce", "mle_eval_matrix",
+    "Transcript", "eq_table", "eq_value", "eq_eval", "mle_eval_bruteforce", "mle_eval_bind", "mle_eval_matrix",
     "fold_rows", "fold_cols", "Proof", "prove_matmul", "verify_matmul", "round_poly_eval",
     "encode_montgomery", "limbs_le32", "LinearProof", "prove_linear", "verify_linear",
     "LookupProof", "prove_lookup", "verify_lookup", "cubic_eval",
     "BatchProof", "prove_matmul_batch", "verify_matmul_batch", "merkle_root",
+    "ChainProof", "prove_chain", "verify_chain",
 ]

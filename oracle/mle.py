@@ -19,7 +19,10 @@ The vector-matrix product is a NumPy object-dtype matmul over Python ints
 
 Pins (tests/test_oracle_mle.py): eq at Boolean points is the indicator; the
 eq table sums to 1; the MLE agrees with the function on the cube; brute-force
-eq:MLE equals the fold-based evaluation; multilinearity along each variable.
+eq:MLE equals the fold-based evaluation; multilinearity along each variable;
+the variable-binding evaluation (mle_eval_bind) and eq at two field points
+(eq_eval) equal the brute-force sums, and a binding order reversed to LSB
+first is caught.
 """
 
 import numpy as np
@@ -100,3 +103,37 @@ def mle_eval_matrix(M, x, y) -> int:
     Ey = eq_table(y, M.shape[1])
     f = fold_rows(M, Ex)
     return sum(a * b for a, b in zip(f, Ey)) % R_MOD
+
+
+def mle_eval_bind(f, x) -> int:
+    """f~(x) for a vector f of at most 2^len(x) entries (zero-padded), by
+    binding the variables one at a time, most significant first.
+
+    eq:MLE is linear in each variable; in x_1 (the MSB) its two values are
+    the MLEs of the halves f[0:h] and f[h:2h], so
+        f~(x_1, x_2, ..) = g~(x_2, ..),  g[j] = f[j] + x_1 (f[j + h] - f[j]).
+    Repeating this l times leaves one entry.  Same value as
+    mle_eval_bruteforce with O(2^l) products instead of O(l 2^l); NumPy
+    object arrays of Python ints hold the vectors.
+    """
+    ell = len(x)
+    n = len(f)
+    assert n <= (1 << ell)
+    v = np.zeros(1 << ell, dtype=object)
+    v[:] = 0
+    v[:n] = [int(a) % R_MOD for a in f]
+    for t in range(ell):
+        h = len(v) // 2
+        v = (v[:h] + int(x[t]) * (v[h:] - v[:h])) % R_MOD
+    return int(v[0]) % R_MOD
+
+
+def eq_eval(x, y) -> int:
+    """eq(x, y) = prod_t (x_t y_t + (1 - x_t)(1 - y_t)) for two points of
+    F^l: the Lagrange basis product of eq:MLE with the Boolean b replaced by
+    a second field point (the MLE of eq_table(x) evaluated at y)."""
+    assert len(x) == len(y)
+    acc = 1
+    for a, b in zip(x, y):
+        acc = acc * ((a * b + (1 - a) * (1 - b)) % R_MOD) % R_MOD
+    return acc

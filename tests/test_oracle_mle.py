@@ -99,3 +99,48 @@ def test_eq_value_consistent():
     rng = random.Random(6)
     x = _rand_point(rng, 4)
     assert [eq_value(x, i) for i in range(16)] == eq_table(x)
+
+
+def test_mle_eval_bind_equals_bruteforce():
+    from oracle.mle import mle_eval_bind
+    rng = random.Random(11)
+    for ell in range(0, 8):
+        for n in {1, max(1, (1 << ell) - 3), 1 << ell}:
+            f = [rng.randrange(R_MOD) if rng.random() < 0.7 else rng.randrange(-(1 << 15), 1 << 15)
+                 for _ in range(n)]
+            x = _rand_point(rng, ell)
+            assert mle_eval_bind(f, x) == mle_eval_bruteforce([v % R_MOD for v in f], x)
+
+
+def test_mle_eval_bind_on_cube_and_matrix():
+    from oracle.mle import mle_eval_bind
+    rng = np.random.default_rng(12)
+    M = rng.integers(-(1 << 15), 1 << 15, size=(8, 16))
+    r = random.Random(13)
+    x, y = _rand_point(r, 3), _rand_point(r, 4)
+    # row bits are the high variables: the flat row-major vector at (x, y)
+    assert mle_eval_bind(M.reshape(-1).tolist(), x + y) == mle_eval_matrix(M, x, y)
+    for i in range(16):
+        bits = [(i >> (3 - t)) & 1 for t in range(4)]
+        assert mle_eval_bind(M[0].tolist(), bits) == int(M[0, i]) % R_MOD
+
+
+def test_mle_eval_bind_lsb_first_would_be_caught():
+    from oracle.mle import mle_eval_bind
+    rng = random.Random(14)
+    f = [rng.randrange(R_MOD) for _ in range(16)]
+    x = _rand_point(rng, 4)
+    assert mle_eval_bind(f, x) != mle_eval_bind(f, x[::-1])  # the order matters ...
+    assert mle_eval_bind(f, x) == mle_eval_bruteforce(f, x)  # ... and MSB first is eq:MLE's
+
+
+def test_eq_eval_closed_form():
+    from oracle.mle import eq_eval
+    rng = random.Random(15)
+    for ell in range(0, 7):
+        x, y = _rand_point(rng, ell), _rand_point(rng, ell)
+        assert eq_eval(x, y) == mle_eval_bruteforce(eq_table(x), y)
+        assert eq_eval(x, y) == eq_eval(y, x)
+        for i in range(1 << ell):
+            bits = [(i >> (ell - 1 - t)) & 1 for t in range(ell)]
+            assert eq_eval(x, bits) == eq_value(x, i)
