@@ -111,6 +111,19 @@ def prove_matmul(P, Q, trans_p=0, trans_q=0, seed=0, binds=(bytes(32),) * 3, ove
     if "v" in ov:
         v = [x % R_MOD for x in ov["v"]]
 
+    c, g_all, rs, a_r, b_r = sumcheck_at(A, B, u, v, T, ov.get("r"))
+    return Proof(m, k, n, d0, d1, d2, c, g_all, a_r, b_r, T.state,
+                 challenges={"u": u, "v": v, "r": rs})
+
+
+def sumcheck_at(A, B, u, v, T, r_override=None):
+    """The claim, rounds and final values for A (m x k) . B (k x n) at the
+    point (u, v), continuing transcript T (after its u, v squeezes):
+    absorb c, per round absorb (g0, g2) and squeeze r, absorb (a_r, b_r).
+    Returns (c, rounds, challenges, a_r, b_r)."""
+    m, k = A.shape
+    n = B.shape[1]
+    d1 = ceil_log2(k)
     # Restrictions A~(u, .) and B~(., v) on the Boolean cube of w.
     fa = fold_rows(A, eq_table(u, m)) + [0] * ((1 << d1) - k)
     fb = fold_cols(B, eq_table(v, n)) + [0] * ((1 << d1) - k)
@@ -127,16 +140,15 @@ def prove_matmul(P, Q, trans_p=0, trans_q=0, seed=0, binds=(bytes(32),) * 3, ove
         g_all.append((g0, g1, g2))
         T.absorb_fr(b"g", [g0, g2])
         r = T.squeeze(b"r", 1)[0]
-        if "r" in ov:
-            r = ov["r"][i] % R_MOD
+        if r_override is not None:
+            r = r_override[i] % R_MOD
         rs.append(r)
         fa = [(fa[j] + r * (fa[j + h] - fa[j])) % R_MOD for j in range(h)]
         fb = [(fb[j] + r * (fb[j + h] - fb[j])) % R_MOD for j in range(h)]
 
     a_r, b_r = fa[0], fb[0]
     T.absorb_fr(b"f", [a_r, b_r])
-    return Proof(m, k, n, d0, d1, d2, c, g_all, a_r, b_r, T.state,
-                 challenges={"u": u, "v": v, "r": rs})
+    return c, g_all, rs, a_r, b_r
 
 
 def verify_matmul(P, Q, C, proof, trans_p=0, trans_q=0, seed=0, binds=(bytes(32),) * 3):

@@ -208,6 +208,29 @@ def rescale_lookups(t, seed=GLOBAL_SEED):
     return out
 
 
+def chain_tensors(t):
+    """The projection's tensors plus the rescale remainders the chained proof
+    needs: rhoH = (X.A + 2^7) mod 2^8, rhodH = (dY.B^T + 2^7) mod 2^8, so that
+    X.A + 2^7 = 2^8 H + rhoH and dY.B^T + 2^7 = 2^8 dH + rhodH hold exactly
+    (checked: a clamped rescale would break them)."""
+    X, A, B, dY, H, dH = (t[x] for x in ("X", "A", "B", "dY", "H", "dH"))
+    out = dict(t)
+    for name, Z, Hs in (("rhoH", exact_matmul(X, A), H), ("rhodH", exact_matmul(dY, B.T), dH)):
+        rho = remainder(Z, RESCALE_SHIFT)
+        assert np.array_equal(Z + (1 << (RESCALE_SHIFT - 1)),
+                              (Hs.astype(np.int64) << RESCALE_SHIFT) + rho), "rescale clamped"
+        out[name] = rho
+    return out
+
+
+def chain_outputs(t):
+    """The claimed outputs of one projection: Y = X.W + H.B, dX = dY.W^T +
+    dH.A^T, dA = X^T.dH, dB = H^T.dY (exact int64)."""
+    X, W, A, B, dY, H, dH = (t[x] for x in ("X", "W", "A", "B", "dY", "H", "dH"))
+    return {"Y": exact_matmul(X, W) + exact_matmul(H, B), "dX": exact_matmul(dY, W.T) + exact_matmul(dH, A.T),
+            "dA": exact_matmul(X.T, dH), "dB": exact_matmul(H.T, dY)}
+
+
 def op_shape(job):
     P, Q = job["P"], job["Q"]
     m, k = (P.shape[1], P.shape[0]) if job["tp"] else P.shape
