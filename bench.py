@@ -136,14 +136,8 @@ def step_jobs(kind, seed, layers=0):
     return projs, jobs
 
 
-def oracle_sample(kind, seed, nproj):
-    """Time the oracle on the first `nproj` projections of the workload."""
+def _oracle_prove(kind, seed, jobs):
     import oracle
-    spec = W.step_layers(STEP_KIND[kind], seed)[:nproj]
-    projs = [W.lora_projection(seed, *s) for s in spec]
-    jobs = [j for t in projs for j in products(kind, t, seed)]
-    macs = sum(W.macs(j) for j in jobs)
-    t0 = time.perf_counter()
     if kind == "7b-step-batched":  # one batched proof per inner dimension
         groups = {}
         for j in jobs:
@@ -153,8 +147,93 @@ def oracle_sample(kind, seed, nproj):
     else:
         for j in jobs:
             oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"])
-    dt = time.perf_counter() - t0
-    return macs / dt, dt, len(jobs), macs
+
+
+def _oracle_projection_task(task):
+    """Worker: regenerate one projection (untimed), then prove its products
+    with the oracle; returns (seconds proving, MACs, proofs)."""
+    kind, seed, spec = task
+    t = W.lora_projection(seed, *spec)
+    jobs = products(kind, t, seed)
+    t0 = time.perf_counter()
+    _oracle_prove(kind, seed, jobs)
+    return time.perf_counter() - t0, sum(W.macs(j) for j in jobs), len(jobs)
+
+
+def _mem_available_gb():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / (1 << 20)
+    except OSError:
+        pass
+    return None
+
+
+class OracleCores:
+    """The oracle over the host's cores: one worker process per core
+    ('spawn' start: no CUDA state is inherited), each proving whole
+    projections.  A sample proves one projection per worker at once; its
+    time is the slowest worker's proving time (each worker regenerates its
+    projection from the seeded recipe first, outside the timed part)."""
+
+    def __init__(self, kind, procs=None):
+        import multiprocessing as mp
+        self.kind = kind
+        spec_n = len(W.step_layers(STEP_KIND[kind], W.GLOBAL_SEED))
+        n = procs or (os.cpu_count() or 1)
+        gb = _mem_available_gb()
+        per = 3.0 if kind == "13b-step" else 1.5  # oracle working set of one projection, GB
+        if gb is not None:
+            n = min(n, max(1, int(gb / 2 / per)))
+        self.procs = max(1, min(n, spec_n))
+        self.pool = mp.get_context("spawn").Pool(self.procs)
+
+    def sample(self, seed, first=0):
+        """(seconds, MACs, proofs) of one projection per worker, projections
+        first .. first + procs - 1 of the workload (wrapping around)."""
+        specs = W.step_layers(STEP_KIND[self.kind], seed)
+        tasks = [(self.kind, seed, specs[(first + i) % len(specs)]) for i in range(self.procs)]
+        res = self.pool.map(_oracle_projection_task, tasks, chunksize=1)
+        return max(r[0] for r in res), sum(r[1] for r in res), sum(r[2] for r in res)
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+
+def oracle_cores_baseline(kind, seed):
+    """cpu_baseline of a matmul workload: the oracle on every host core."""
+    oc = OracleCores(kind)
+    try:
+        dt, macs, nj = oc.sample(seed)
+    finally:
+        oc.close()
+    return {"value": macs / dt, "unit": UNIT, "cores": oc.procs, "kind": "oracle",
+            "sample": f"first {oc.procs} projections of the same workload, one per worker process "
+                      f"({nj} proofs, {macs} MACs), proved at once on {oc.procs} cores in {dt:.1f} s "
+                      f"(the slowest worker's proving time)"}
+
+
+def pinned_h2d_gbs(stream, nbytes=1 << 30, reps=3):
+    """Plain host-to-device copy rate of this machine: one cudaMemcpyAsync of a
+    pinned 1 GiB buffer, best of `reps`, timed with CUDA events."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h.fill_(1)
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d.copy_(h, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del d, h
+    return nbytes / (best / 1e3) / 1e9
 
 
 class Clocks:
@@ -232,40 +311,25 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": LIN_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }))
         return
-    if args.steps + args.warmup <= 40 or args.workload == "7b-step-batched":
-        # one whole projection per step (a few seconds each)
-        per_step = []
-        macs_step = None
-        for _ in range(args.warmup):
-            oracle_sample(args.workload, W.GLOBAL_SEED, 1)
-        for _ in range(args.steps):
-            rate, dt, nj, macs = oracle_sample(args.workload, W.GLOBAL_SEED, 1)
-            per_step.append(dt)
-            macs_step = macs
-        total = sum(per_step)
-        value = macs_step * args.steps / total
-        sample = f"1 projection ({nj} proofs, {macs_step} MACs) of the {args.workload} workload per step"
-    else:
-        # many steps: one product per step, cycling through the first
-        # projection's products, so the run stays within a few minutes
-        import oracle
-        spec = W.step_layers(STEP_KIND[args.workload], W.GLOBAL_SEED)[:1]
-        jobs = [j for t in (W.lora_projection(W.GLOBAL_SEED, *s) for s in spec)
-                for j in products(args.workload, t, W.GLOBAL_SEED)]
-
-        def one(i):
-            j = jobs[i % len(jobs)]
-            t0 = time.perf_counter()
-            oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"])
-            return time.perf_counter() - t0, W.macs(j)
-
+    # every host core proves one projection per step (worker processes)
+    oc = OracleCores(args.workload)
+    cores = oc.procs
+    try:
+        specs_n = len(W.step_layers(STEP_KIND[args.workload], W.GLOBAL_SEED))
         for i in range(args.warmup):
-            one(i)
-        per = [one(i) for i in range(args.steps)]
-        total = sum(dt for dt, _ in per)
-        value = sum(m for _, m in per) / total
-        sample = (f"one product per step, cycling through the first projection's {len(jobs)} products "
-                  f"({sum(m for _, m in per)} MACs over the timed steps)")
+            oc.sample(W.GLOBAL_SEED, first=(i * cores) % specs_n)
+        per_step, macs_total, nj = [], 0, 0
+        for i in range(args.steps):
+            dt, macs, nj = oc.sample(W.GLOBAL_SEED, first=((args.warmup + i) * cores) % specs_n)
+            per_step.append(dt)
+            macs_total += macs
+    finally:
+        oc.close()
+    total = sum(per_step)
+    value = macs_total / total
+    sample = (f"{cores} projections per step ({nj} proofs), one per worker process on {cores} cores, "
+              f"cycling through the {args.workload} workload's projections; a step's time is the slowest "
+              f"worker's proving time")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
@@ -893,10 +957,8 @@ def main():
     if args.workload == "7b-step-batched":
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            rate, dt, nj, macs = oracle_sample(args.workload, W.GLOBAL_SEED, 1)
-            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"the first projection's {nj} products as batched proofs by inner dimension "
-                             f"({macs} MACs), single process, {dt:.1f} s"}
+            cpu = oracle_cores_baseline(args.workload, W.GLOBAL_SEED)
+            cpu["sample"] += "; batched proofs, one per inner dimension of each projection"
         return batched_main(args, rank, world, local, cpu)
     if args.workload == "7b-lookups":
         cpu = None
@@ -918,10 +980,7 @@ def main():
     # The oracle CPU baseline runs before any CUDA work (no forked pools after it).
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt, nj, macs = oracle_sample(args.workload, W.GLOBAL_SEED, args.cpu_sample_projections)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {args.cpu_sample_projections} projections ({nj} proofs, {macs} MACs) "
-                         f"of the same workload, single process, {dt:.1f} s"}
+        cpu = oracle_cores_baseline(args.workload, W.GLOBAL_SEED)
 
     import torch
     from paper_2508_21393_gb300 import binding as B
@@ -1091,10 +1150,13 @@ def main():
             B.vl_plan_run(hplan, hws.data_ptr(), hn, hout, B.VL_HOST, stream)
         e2e_s = (time.perf_counter() - t0) / ksteps
         e2e_max = max_over_ranks(e2e_s, world, "cuda")
+        h2d = int(sum(h.numel() * 2 for h in host.values()))
+        rate = pinned_h2d_gbs(stream)
         e2e = {"value": job_value(macs_step, world, e2e_max), "unit": UNIT,
-               "h2d_bytes_per_step": int(sum(h.numel() * 2 for h in host.values())),
+               "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": int(ctypes.sizeof(B.vl_proof) * len(hjobs)),
-               "ms_per_step": 1e3 * e2e_max, "steps": ksteps}
+               "ms_per_step": 1e3 * e2e_max, "steps": ksteps,
+               "pinned_h2d_gbs": rate, "copy_bound_ms": 1e3 * h2d / (rate * 1e9)}
         B.vl_plan_destroy(hplan)
 
     launches = args.steps * B.vl_plan_launches(plan)
