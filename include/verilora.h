@@ -269,7 +269,8 @@ int32_t vl_verify_matmul(const vl_mat* P, const vl_mat* Q, const vl_mat* C, cons
  * fits; the scratch grows with k and the row/column counts).
  * Set-up: the first call on each device, with that device current, looks up
  * the array's device address; make that first call before any stream capture
- * on the device.
+ * on the device.  The address is kept for the life of the process, so this
+ * entry point must not be called on a device after cudaDeviceReset there.
  * Sharing: all calls use the same array, which keeps the previous call's
  * contents (the call clears what must start at zero).  Two calls running on
  * the GPU at the same time would race on it; within one process the entry

@@ -1065,6 +1065,9 @@ extern "C" int32_t vl_prove_matmul_noalloc(const vl_mat* P, const vl_mat* Q, con
     if (ce == cudaSuccess) ce = launch_rounds(dp, 1, dout, 0, 0, st);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, dout, sizeof(vl_proof), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    // A failed enqueue may leave earlier kernels of this call running on the
+    // array: let them finish before the lock lets the next call rebind it.
+    if (ce != cudaSuccess) (void)cudaStreamSynchronize(st);
     e = cuda_status(ce, "vl_prove_matmul_noalloc");
     if (e == VL_OK && out->status != VL_OK) e = out->status;
   }
