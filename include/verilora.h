@@ -17,7 +17,9 @@
  * range lookups of int16 values in a table of consecutive integers
  * (Protocol 1, Eq. eq:lookup-sumcheck; vl_prove_lookup); and K products of
  * one inner dimension under one transcript with one random-combination
- * sumcheck (Sec. IV, putting everything together; vl_prove_matmul_batched).
+ * sumcheck (Sec. IV, putting everything together; vl_prove_matmul_batched);
+ * and the chained proof of one LoRA projection, whose intermediate tensors
+ * are never opened (Sec. IV, sequential composition; vl_prove_chain).
  *
  * Conventions.
  *  - Field elements (vl_fr) are canonical, 8 x 32-bit limbs, little endian.
@@ -148,7 +150,10 @@ typedef struct vl_batch_opts {
                             VL_ETIMEOUT and its CTA returns                  */
   int32_t rounds_variant; /* rounds kernel: CTAs per SM, 7, 4, 3 or 2 (0: 7);
                             7 and 4 set the register budget, 3 and 2 also
-                            cap residency (fewer proofs share an SM)        */
+                            cap residency (fewer proofs share an SM); 8:
+                            batched rounds, one launch per round for the
+                            vector work of all proofs and one for their
+                            transcript steps (one-group phase launches) */
   int32_t rounds_threads; /* rounds kernel threads per proof: 128, 192 or 256
                             (0: 128)                                         */
   int32_t tc_seg;        /* tensor-core fold: reduced entries per tile, a
@@ -531,10 +536,15 @@ typedef struct vl_server_done {
   int32_t status;     /* VL_OK, or the first non-OK proof / launch status   */
   int32_t batch;      /* batch the request ran in (-1: never admitted)      */
   double latency_ms;  /* submit to completion seen by the server            */
+  double dev_start_ms; /* the batch's device interval, in ms of the GPU's   */
+  double dev_end_ms;   /*   clock since the server started (CUDA events on  */
+                       /*   the batch's stream around its work; 0 if never  */
+                       /*   admitted)                                       */
 } vl_server_done;
 
 typedef struct vl_server_stats {
   int64_t submitted, completed, failed, batches, proofs, queued;
+  int64_t launched;   /* batches put on the device so far                   */
 } vl_server_stats;
 
 /* Start a server (and its worker thread) on the current device. */
@@ -550,6 +560,81 @@ int32_t vl_server_stats_get(vl_server* server, vl_server_stats* out);
 /* Finish the batches on the device, stop the worker, free host resources.
  * Queued requests that were never admitted are dropped. */
 int32_t vl_server_destroy(vl_server* server);
+
+/* ---------------------------------------------------------------------------
+ * Chained proof of one LoRA projection (Sec. IV, putting everything together:
+ * sequential composition, where the claim a sub-proof leaves on an
+ * intermediate tensor is reduced to claims on the tensors that made it
+ * instead of being opened).  In the X.A.B convention the projection has
+ * outputs Y = X.W + H.B, dX = dY.W^T + dH.A^T, dA = X^T.dH, dB = H^T.dY and
+ * the fixed-point rescales (Sec. IV-A, quantisation z = zeta z' + r with
+ * zeta = 2^8) X.A + 2^7 = 2^8 H + rhoH and dY.B^T + 2^7 = 2^8 dH + rhodH,
+ * whose remainders rhoH, rhodH are witnesses (their range is a lookup,
+ * vl_prove_lookup).  Ten matmul sumchecks (Eq. eq:zk-mle-matmul) run under
+ * one transcript:
+ *   S0 = SHA256("verilora-gb300/zkchain/v1" || seed u64le || n, d, k, r u32le
+ *               || the seven binds);  squeeze 'p': u_Y, v_Y, u_dX, v_dX,
+ *               u_dA, v_dA, u_dB, v_dB (log2 of n, k, n, d, d, r, r, k
+ *               entries) -> S1;
+ *   stage 1, member p starting at SHA256(S1 || 'M' || p u32le), each at its
+ *     given point (no u, v squeeze; then absorb c, rounds, absorb a_r, b_r):
+ *     0 X.W and 1 H.B at (u_Y, v_Y), 2 dY.W^T and 3 dH.A^T at (u_dX, v_dX),
+ *     4 X^T.dH at (u_dA, v_dA), 5 H^T.dY at (u_dB, v_dB);
+ *   S2 = SHA256(S1 || 'L' || the six final member states); the claims left
+ *     on H and dH sit at p1 = (u_Y, r^1), p2 = (r^5, u_dB), q1 = (u_dX, r^3),
+ *     q2 = (r^4, v_dA) (r^p: member p's round challenges);
+ *     e = (rhoH~(p1), rhoH~(p2), rhodH~(q1), rhodH~(q2)) absorbed as 'e' -> S3;
+ *   stage 3, members from SHA256(S3 || 'M' || p): 6, 7 X.A at p1, p2;
+ *     8, 9 dY.B^T at q1, q2 (their claims must equal 2^8 H~ + rho~ - 2^7 J~
+ *     at the point, J the all-ones n x r matrix);
+ *   final state SHA256(S3 || 'Z' || the four stage-3 final member states).
+ * H, dH, X.A and dY.B^T are never opened; the verifier opens X, W, A, B, dY,
+ * rhoH, rhodH and checks the four output claims against the claimed outputs.
+ * ------------------------------------------------------------------------- */
+#define VL_CHAIN_MEMBERS 10
+#define VL_CHAIN_MAX_RANK 256
+typedef struct vl_chain_job {
+  /* int16 matrices, stored as named (trans = 0): X n x d, W d x k, A d x r,
+   * B r x k, dY n x k, H, dH, rhoH, rhodH n x r.  Device matrices for the
+   * prover, host matrices for the verifier.  n, d, k <= VL_MAX_REDUCE,
+   * r <= VL_CHAIN_MAX_RANK. */
+  vl_mat X, W, A, B, dY, H, dH, rhoH, rhodH;
+  uint64_t seed;
+  uint8_t bind[7][32]; /* X, W, A, B, dY, rhoH, rhodH: commitment stand-ins */
+} vl_chain_job;
+
+typedef struct vl_chain_proof {
+  int32_t n, d, k, r;
+  int32_t status;   /* VL_OK, or the first non-OK member status */
+  int32_t reserved;
+  vl_proof sub[VL_CHAIN_MEMBERS]; /* members 0..9 as above; their `state` is
+                                     the member's final transcript state */
+  vl_fr e[4];                     /* the remainder evaluations, canonical */
+  uint8_t state[32];              /* final chain state */
+} vl_chain_proof;
+
+/* Device workspace for a batch of chained proofs (0 on invalid input). */
+size_t vl_chain_workspace_bytes(const vl_chain_job* jobs, int32_t njobs);
+/* Prove `njobs` projections (independent chains, one batch of launches).
+ * out: host, njobs proofs.  Synchronises `stream`; returns the first
+ * non-OK member status. */
+int32_t vl_prove_chain(const vl_chain_job* jobs, int32_t njobs, void* workspace, size_t workspace_bytes,
+                       vl_chain_proof* out, void* stream);
+/* The same batch proved repeatedly: the member plans are built once
+ * (vl_chain_plan_create copies the jobs) and bound to a workspace on its
+ * first run there; each run synchronises `stream`. */
+typedef struct vl_chain_plan vl_chain_plan;
+int32_t vl_chain_plan_create(const vl_chain_job* jobs, int32_t njobs, vl_chain_plan** plan);
+size_t vl_chain_plan_workspace_bytes(const vl_chain_plan* plan);
+int32_t vl_chain_plan_run(vl_chain_plan* plan, void* workspace, size_t workspace_bytes, vl_chain_proof* out,
+                          void* stream);
+void vl_chain_plan_destroy(vl_chain_plan* plan);
+/* Host verifier of one chained proof: job holds HOST matrices (H and dH are
+ * not read); Y (n x k), dX (n x d), dA (d x r), dB (r x k) are the claimed
+ * outputs (VL_I64 or VL_I16 host matrices).  Returns VL_OK, VL_REJECT or an
+ * input error. */
+int32_t vl_verify_chain(const vl_chain_job* job, const vl_mat* Y, const vl_mat* dX, const vl_mat* dA,
+                        const vl_mat* dB, const vl_chain_proof* proof);
 
 #ifdef __cplusplus
 }

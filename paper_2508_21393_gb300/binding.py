@@ -36,7 +36,8 @@ EXPORTS = ("vl_version", "vl_strerror", "vl_last_error", "vl_workspace_bytes", "
            "vl_lookup_plan_destroy", "vl_prove_lookup", "vl_verify_lookup", "vl_batch_workspace_bytes",
            "vl_prove_matmul_batched", "vl_verify_matmul_batched", "vl_claims_plan_create",
            "vl_claims_plan_workspace_bytes", "vl_claims_plan_run", "vl_claims_plan_destroy",
-           "vl_workspace_forget")
+           "vl_workspace_forget", "vl_chain_workspace_bytes", "vl_prove_chain", "vl_verify_chain",
+           "vl_chain_plan_create", "vl_chain_plan_workspace_bytes", "vl_chain_plan_run", "vl_chain_plan_destroy")
 VL_NOALLOC_SCRATCH_BYTES = 8 << 20
 VL_LIN_MAX = 16
 VL_LOOKUP_MAX_LOG_D = 24
@@ -102,6 +103,22 @@ class vl_job(ctypes.Structure):
     _fields_ = [("P", vl_mat), ("Q", vl_mat), ("fs", vl_fs_init)]
 
 
+VL_CHAIN_MEMBERS = 10
+VL_CHAIN_MAX_RANK = 256
+CHAIN_MATS = ("X", "W", "A", "B", "dY", "H", "dH", "rhoH", "rhodH")
+
+
+class vl_chain_job(ctypes.Structure):
+    _fields_ = [(name, vl_mat) for name in CHAIN_MATS] + [("seed", ctypes.c_uint64),
+                                                          ("bind", (ctypes.c_uint8 * 32) * 7)]
+
+
+class vl_chain_proof(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("d", ctypes.c_int32), ("k", ctypes.c_int32), ("r", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("sub", vl_proof * VL_CHAIN_MEMBERS), ("e", vl_fr * 4), ("state", ctypes.c_uint8 * 32)]
+
+
 class vl_server_opts(ctypes.Structure):
     _fields_ = [("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32),
                 ("max_batch_requests", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
@@ -110,12 +127,13 @@ class vl_server_opts(ctypes.Structure):
 
 class vl_server_done(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("batch", ctypes.c_int32),
-                ("latency_ms", ctypes.c_double)]
+                ("latency_ms", ctypes.c_double), ("dev_start_ms", ctypes.c_double), ("dev_end_ms", ctypes.c_double)]
 
 
 class vl_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
-                ("batches", ctypes.c_int64), ("proofs", ctypes.c_int64), ("queued", ctypes.c_int64)]
+                ("batches", ctypes.c_int64), ("proofs", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("launched", ctypes.c_int64)]
 
 
 class vl_batch_opts(ctypes.Structure):
@@ -249,6 +267,22 @@ def lib():
     L.vl_encode.restype = ctypes.c_int32
     L.vl_workspace_forget.argtypes = [ctypes.c_void_p]
     L.vl_workspace_forget.restype = ctypes.c_int32
+    L.vl_chain_workspace_bytes.argtypes = [P(vl_chain_job), ctypes.c_int32]
+    L.vl_chain_workspace_bytes.restype = ctypes.c_size_t
+    L.vl_prove_chain.argtypes = [P(vl_chain_job), ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                                 P(vl_chain_proof), ctypes.c_void_p]
+    L.vl_prove_chain.restype = ctypes.c_int32
+    L.vl_verify_chain.argtypes = [P(vl_chain_job), P(vl_mat), P(vl_mat), P(vl_mat), P(vl_mat), P(vl_chain_proof)]
+    L.vl_verify_chain.restype = ctypes.c_int32
+    L.vl_chain_plan_create.argtypes = [P(vl_chain_job), ctypes.c_int32, P(ctypes.c_void_p)]
+    L.vl_chain_plan_create.restype = ctypes.c_int32
+    L.vl_chain_plan_workspace_bytes.argtypes = [ctypes.c_void_p]
+    L.vl_chain_plan_workspace_bytes.restype = ctypes.c_size_t
+    L.vl_chain_plan_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, P(vl_chain_proof),
+                                    ctypes.c_void_p]
+    L.vl_chain_plan_run.restype = ctypes.c_int32
+    L.vl_chain_plan_destroy.argtypes = [ctypes.c_void_p]
+    L.vl_chain_plan_destroy.restype = None
     _lib = L
     return L
 
@@ -562,11 +596,14 @@ def vl_server_submit(server, jobs, out):
 
 
 def vl_server_poll(server, max_done=1024):
-    """Completed requests since the last poll: list of (ticket, status, batch, latency_ms)."""
+    """Completed requests since the last poll: list of (ticket, status, batch,
+    latency_ms, (dev_start_ms, dev_end_ms)) -- the last item is the batch's
+    device interval on the GPU's clock since the server started."""
     buf = (vl_server_done * max_done)()
     n = ctypes.c_int32()
     _check(lib().vl_server_poll(server, buf, max_done, ctypes.byref(n)), "vl_server_poll")
-    return [(buf[i].ticket, buf[i].status, buf[i].batch, buf[i].latency_ms) for i in range(n.value)]
+    return [(buf[i].ticket, buf[i].status, buf[i].batch, buf[i].latency_ms, (buf[i].dev_start_ms, buf[i].dev_end_ms))
+            for i in range(n.value)]
 
 
 def vl_server_stats_get(server):
@@ -782,3 +819,85 @@ def vl_verify_linear(job, proof):
 def vl_encode(src, dst, stream=None):
     """Encode a device int16 vl_mat into dst (device pointer, rows*cols*32 bytes)."""
     _check(lib().vl_encode(ctypes.byref(src), int(dst), _stream_ptr(stream)), "vl_encode")
+
+
+# ------------------------------------------------------------ chained proofs --
+
+def chain_job(t, seed=0, binds=None):
+    """vl_chain_job of one projection: t maps X, W, A, B, dY, H, dH, rhoH,
+    rhodH to 2-D int16 torch tensors (device, for the prover) or NumPy arrays
+    (host, for the verifier); binds: None or seven 32-byte strings."""
+    j = vl_chain_job()
+    j._keep = []
+    for name in CHAIN_MATS:
+        m = mat(t[name])
+        j._keep.append(m._keep)  # the operands stay alive as long as the job
+        setattr(j, name, m)
+    j.seed = int(seed) & ((1 << 64) - 1)
+    for i in range(7):
+        b = bytes(32) if binds is None else bytes(binds[i])
+        for q in range(32):
+            j.bind[i][q] = b[q]
+    return j
+
+
+def chain_jobs_array(jobs):
+    arr = (vl_chain_job * len(jobs))()
+    for i, j in enumerate(jobs):
+        arr[i] = j
+    arr._keep = list(jobs)
+    return arr
+
+
+def chain_proof_bytes(p):
+    """Chained proof serialisation (same layout as the oracle's ChainProof.to_bytes)."""
+    out = b"".join(int(x).to_bytes(4, "little") for x in (p.n, p.d, p.k, p.r))
+    out += b"".join(proof_bytes(p.sub[i]) for i in range(VL_CHAIN_MEMBERS))
+    return out + b"".join(bytes(p.e[q]) for q in range(4)) + bytes(p.state)
+
+
+def vl_chain_workspace_bytes(jobs):
+    return lib().vl_chain_workspace_bytes(chain_jobs_array(jobs), len(jobs))
+
+
+def vl_prove_chain(jobs, workspace, workspace_bytes, stream=None):
+    """Prove a batch of chained projection proofs; returns the ctypes array of host proofs."""
+    out = (vl_chain_proof * len(jobs))()
+    _check(lib().vl_prove_chain(chain_jobs_array(jobs), len(jobs), workspace, workspace_bytes, out,
+                                _stream_ptr(stream)), "vl_prove_chain")
+    return out
+
+
+class ChainPlan:
+    """A vl_chain_plan: the same batch of chained proofs, proved repeatedly."""
+
+    def __init__(self, jobs):
+        self._jobs = chain_jobs_array(jobs)  # keeps the operands alive
+        h = ctypes.c_void_p()
+        _check(lib().vl_chain_plan_create(self._jobs, len(jobs), ctypes.byref(h)), "vl_chain_plan_create")
+        self.h, self.n = h.value, len(jobs)
+
+    def workspace_bytes(self):
+        return lib().vl_chain_plan_workspace_bytes(self.h)
+
+    def run(self, workspace, workspace_bytes, stream=None):
+        out = (vl_chain_proof * self.n)()
+        _check(lib().vl_chain_plan_run(self.h, workspace, workspace_bytes, out, _stream_ptr(stream)),
+               "vl_chain_plan_run")
+        return out
+
+    def destroy(self):
+        if self.h:
+            lib().vl_chain_plan_destroy(self.h)
+            self.h = None
+
+
+def vl_verify_chain(job, outputs, proof):
+    """Host verifier of a chained proof: job with host matrices, outputs maps
+    Y, dX, dA, dB to int64 NumPy arrays.  True / False; raises on input errors."""
+    ms = [mat(np.ascontiguousarray(outputs[k])) for k in ("Y", "dX", "dA", "dB")]
+    code = lib().vl_verify_chain(ctypes.byref(job), *[ctypes.byref(m) for m in ms], ctypes.byref(proof))
+    if code == VL_REJECT:
+        return False
+    _check(code, "vl_verify_chain")
+    return True

@@ -19,12 +19,24 @@ enum : int32_t { MODE_COLSUM = 0, MODE_ROWDOT = 1 };
 
 // Per-proof mutable state (device, in the workspace).
 struct ProofScratch {
-  uint8_t state[32];  // transcript state after the u, v squeezes
+  uint8_t state[32];  // transcript state after the u, v squeezes (then after each round)
   Fr corrA;           // 2^15 . sum E_u  (Montgomery), int16 offset correction
   Fr corrB;           // 2^15 . sum E_v
   int32_t status;
   int32_t pad[7];
+  Fr r;               // batched rounds: the latest challenge (Montgomery)
 };
+
+// Batched rounds (one launch per round over all proofs): the pairs of one
+// proof's round evaluated by one CTA.
+struct RoundItem {
+  int32_t proof;  // DevProof index
+  int32_t j0, j1; // pairs [j0, j1) of the round
+  int32_t pad;
+};
+static constexpr int RB_PAIRS = 256;    // pairs per item
+static constexpr int RB_THREADS = 128;  // threads of a pass CTA
+static constexpr int RB_WARPS = 4;      // proofs per transcript CTA (one warp each)
 
 // Per-proof read-only descriptor (device copy of the plan).
 struct DevProof {
@@ -52,6 +64,18 @@ struct DevProof {
   Fr* fac;                 // eq factor tables: [lo_u 256 | hi_u 256 | lo_v 256 | hi_v 256]
   uint32_t* w8A;           // tensor-core weights: E_u bytes as fp16, [ceil(m / 128) x 2 chunks] x 4 KB
   uint32_t* w8B;           // E_v bytes
+  const struct GivenPoint* given;  // non-null: start state and (u, v) given (chained proofs), no squeeze
+  Fr* rch;                 // non-null: the rounds store their challenges r_1..r_d1 here (Montgomery)
+};
+
+// Start of a proof whose point is fixed by an earlier proof (a member of a
+// chained proof): the transcript state the proof starts from, and u (d0
+// entries), v (d2 entries) in Montgomery form.
+static constexpr int GIVEN_VARS = 16;  // log2 of VL_MAX_REDUCE
+struct GivenPoint {
+  uint8_t state[32];
+  Fr u[GIVEN_VARS];
+  Fr v[GIVEN_VARS];
 };
 
 // Weight tables of one side of a proof.
@@ -311,6 +335,16 @@ cudaError_t step_grid(int smem_bytes, int* grid);
 cudaError_t launch_step(const StepItem* items, int nitems, const FoldTask* tasks, const FoldTile* tiles,
                         const DevProof* proofs, int nproofs, vl_proof* out, int* ctl, int grid, int smem_bytes,
                         unsigned long long wait_ns, int never_ready, cudaStream_t st);
+// Batched rounds: round t (1-based) of every proof with d1 >= t.  Pass:
+// fold with r_(t-1) (t > 1; for t = 1 the fold's output is reduced) and
+// evaluate the round over `nitems` items, one canonical partial triple per
+// item; transcript: one warp per proof of [0, nproofs) sums its items'
+// partials (items ibase[p] .. ibase[p + 1]), writes and absorbs the round
+// message, squeezes r_t, and after its last round writes the proof.
+cudaError_t launch_rounds_pass(const DevProof* proofs, const RoundItem* items, int nitems, Fr* partials, int t,
+                               cudaStream_t st);
+cudaError_t launch_rounds_hash(const DevProof* proofs, int nproofs, const int* ibase, const Fr* partials,
+                               vl_proof* out, int t, cudaStream_t st);
 cudaError_t launch_rounds(const DevProof* proofs, int nproofs, vl_proof* out, int variant, int threads,
                           cudaStream_t st);
 cudaError_t launch_encode(const int16_t* src, int64_t rows, int64_t cols, int64_t ld, Fr* dst,

@@ -98,6 +98,10 @@ struct vl_plan {
   };
   std::vector<Group> groups;
   std::vector<int> slot_of_job;  // DevProof index of each job
+  // Chained proofs (per job, caller order; empty when unused): a given start
+  // state and point, and where the rounds store their challenges.
+  std::vector<const GivenPoint*> given;
+  std::vector<Fr*> rch;
   cudaStream_t side[2] = {nullptr, nullptr};  // rounds stream, prologue stream
   std::vector<cudaEvent_t> gev;               // dependency events (no timing)
   std::vector<CUtensorMap> tmaps;   // one per fold task (TMA operands), built at bind time
@@ -110,6 +114,12 @@ struct vl_plan {
   // workspace layout (offsets from the workspace base)
   size_t off_proofs = 0, off_scr = 0, off_tasks = 0, off_tiles = 0, off_tc_tiles = 0, off_eq_items = 0;
   size_t off_acc = 0, acc_bytes = 0, off_out = 0, total = 0;
+  // batched rounds (rounds_variant 8): per round t (1-based) its items and
+  // the item range of each proof; proofs with d1 >= t are a prefix (k-descending)
+  std::vector<RoundItem> ritems;
+  std::vector<int> ibase;           // per round: np_t + 1 prefix offsets into that round's items
+  std::vector<int> r_item0, r_nitem, r_ib0, r_np;  // per round t (index t): first item, items, ibase start, proofs
+  size_t off_ritems = 0, off_ibase = 0, off_partials = 0;
   struct PerProof {
     size_t eqA, eqB, soaA, soaB, w8A, w8B, accA, accB, fA, fB, fac;
   };
@@ -425,6 +435,42 @@ int build_plan(vl_plan* p) {
     p->pp[i].fac = off;
     off = align_up(off + sizeof(Fr) * 4 * EQ_FAC);
   }
+  // batched rounds: items of RB_PAIRS pairs per proof and round
+  {
+    const int maxd1 = np ? p->proofs[0].d1 : 0;
+    p->ritems.clear();
+    p->ibase.clear();
+    p->r_item0.assign(maxd1 + 2, 0);
+    p->r_nitem.assign(maxd1 + 2, 0);
+    p->r_ib0.assign(maxd1 + 2, 0);
+    p->r_np.assign(maxd1 + 2, 0);
+    size_t max_items = 1;
+    for (int t = 1; t <= std::max(maxd1, 1); t++) {
+      p->r_item0[t] = (int)p->ritems.size();
+      p->r_ib0[t] = (int)p->ibase.size();
+      int npt = 0;
+      for (int i = 0; i < np; i++) {
+        const DevProof& P = p->proofs[i];
+        if (t > 1 && P.d1 < t) break;  // k-descending: the rest have fewer rounds
+        npt = i + 1;
+        p->ibase.push_back((int)p->ritems.size() - p->r_item0[t]);
+        if (P.d1 < t) continue;
+        const int pairs = 1 << (P.d1 - t);
+        for (int j0 = 0; j0 < pairs; j0 += RB_PAIRS)
+          p->ritems.push_back(RoundItem{i, j0, std::min(pairs, j0 + RB_PAIRS), 0});
+      }
+      p->ibase.push_back((int)p->ritems.size() - p->r_item0[t]);
+      p->r_np[t] = npt;
+      p->r_nitem[t] = (int)p->ritems.size() - p->r_item0[t];
+      max_items = std::max(max_items, (size_t)p->r_nitem[t]);
+    }
+    p->off_ritems = off;
+    off = align_up(off + sizeof(RoundItem) * std::max<size_t>(p->ritems.size(), 1));
+    p->off_ibase = off;
+    off = align_up(off + sizeof(int) * std::max<size_t>(p->ibase.size(), 1));
+    p->off_partials = off;
+    off = align_up(off + 3 * sizeof(Fr) * max_items);
+  }
   // staging for host operands (one device copy per distinct host pointer)
   for (const vl_job& j : p->jobs) {
     for (const vl_mat* M : {&j.P, &j.Q}) {
@@ -556,6 +602,8 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
     P.fB = reinterpret_cast<Fr*>(ws + p->pp[i].fB);
     P.scr = reinterpret_cast<ProofScratch*>(ws + p->off_scr) + i;
     P.fac = reinterpret_cast<Fr*>(ws + p->pp[i].fac);
+    P.given = p->given.empty() ? nullptr : p->given[P.job];
+    P.rch = p->rch.empty() ? nullptr : p->rch[P.job];
   }
   p->tmaps.resize(p->tasks.size());
   p->etmaps.resize(p->tasks.size());
@@ -614,6 +662,12 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
   if (e == cudaSuccess && !p->items.empty())
     e = cudaMemcpyAsync(ws + p->off_items, p->items.data(), sizeof(StepItem) * p->items.size(),
                         cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !p->ritems.empty())
+    e = cudaMemcpyAsync(ws + p->off_ritems, p->ritems.data(), sizeof(RoundItem) * p->ritems.size(),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !p->ibase.empty())
+    e = cudaMemcpyAsync(ws + p->off_ibase, p->ibase.data(), sizeof(int) * p->ibase.size(), cudaMemcpyHostToDevice,
+                        st);
   // The host vectors must outlive the copies: wait for them.
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess && p->fold_smem > 0) e = fold_set_smem(p->fold_smem);
@@ -662,6 +716,34 @@ cudaEvent_t* slot_events(vl_plan* p, long run) {
   return &p->ring[(size_t)(run % p->ring_runs) * vl_plan::NEV];
 }
 
+// Claims and rounds of every proof: one CTA per proof (rounds_kernel), or
+// with rounds_variant 8 one launch per round for the round's vector work of
+// all proofs and one for its transcript steps.
+cudaError_t enqueue_rounds(vl_plan* p, uint8_t* ws, const DevProof* dp, vl_proof* dout, cudaStream_t st) {
+  const int np = (int)p->jobs.size();
+  if (p->opts.rounds_variant != 8)
+    return launch_rounds(dp, np, dout, p->opts.rounds_variant, p->opts.rounds_threads, st);
+  const RoundItem* items = reinterpret_cast<const RoundItem*>(ws + p->off_ritems);
+  const int* ibase = reinterpret_cast<const int*>(ws + p->off_ibase);
+  Fr* partials = reinterpret_cast<Fr*>(ws + p->off_partials);
+  const int maxd1 = np ? p->proofs[0].d1 : 0;
+  cudaError_t e = cudaSuccess;
+  for (int t = 1; t <= std::max(maxd1, 1) && e == cudaSuccess; t++) {
+    e = launch_rounds_pass(dp, items + p->r_item0[t], p->r_nitem[t], partials, t, st);
+    if (e == cudaSuccess)
+      e = launch_rounds_hash(dp, t == 1 ? np : p->r_np[t], ibase + p->r_ib0[t], partials, dout, t, st);
+  }
+  return e;
+}
+
+int rounds_launches(const vl_plan* p) {
+  if (p->opts.rounds_variant != 8) return 1;
+  int n = 0;
+  for (size_t t = 1; t < p->r_nitem.size(); t++)
+    n += (p->r_nitem[t] > 0 ? 1 : 0) + ((t == 1 || p->r_np[t] > 0) ? 1 : 0);
+  return n;
+}
+
 // The device part of one proving pass (graph-capturable).  `ev`: the four
 // phase-boundary events to record.
 cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t st, cudaEvent_t* ev,
@@ -704,7 +786,7 @@ cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t s
     if (e == cudaSuccess) e = launch_fold_tc(dc, (int)p->tc_tiles.size(), dp, wait_ns(p), st);
     if (e == cudaSuccess) e = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, wait_ns(p), st);
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2], st, flags);
-    if (e == cudaSuccess) e = launch_rounds(dp, np, dout, p->opts.rounds_variant, p->opts.rounds_threads, st);
+    if (e == cudaSuccess) e = enqueue_rounds(p, ws, dp, dout, st);
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[3], st, flags);
     return e;
   }
@@ -862,6 +944,26 @@ int make_plan(const vl_job* jobs, int32_t njobs, const vl_batch_opts* opts, vl_p
 
 }  // namespace
 
+namespace vl {
+// Plans as building blocks of composite proofs (chained proofs).
+int plan_make(const vl_job* jobs, int32_t njobs, const vl_batch_opts* opts, vl_plan** out) {
+  return make_plan(jobs, njobs, opts, out);
+}
+size_t plan_bytes(const vl_plan* p) { return p->total; }
+void plan_set_points(vl_plan* p, const std::vector<const GivenPoint*>& given, const std::vector<Fr*>& rch) {
+  if (p->given != given || p->rch != rch) {
+    p->given = given;
+    p->rch = rch;
+    drop_graph(p);
+    p->bound_ws = nullptr;  // the descriptors change: bind again on the next run
+  }
+}
+// Enqueue one pass (no graph), proofs to device memory in job order.
+int plan_enqueue(vl_plan* p, uint8_t* ws, size_t bytes, vl_proof* dout, cudaStream_t st) {
+  return run_plan(p, ws, bytes, dout, VL_DEVICE, st, false);
+}
+}  // namespace vl
+
 extern "C" {
 
 int32_t vl_version(void) { return 100; }
@@ -902,8 +1004,9 @@ int32_t vl_plan_launches(const vl_plan* plan) {
   if (!plan) return 0;
   if (persistent(plan)) return 1;
   int32_t n = 0;
-  for (const vl_plan::Group& G : plan->groups)
-    n += 2 + (G.c1 > G.c0 ? 1 : 0) + (G.t1 > G.t0 ? 1 : 0);  // prologue, folds, rounds
+  for (const vl_plan::Group& G : plan->groups)  // prologue (transcripts, eq chunks), folds, rounds
+    n += 1 + (G.e1 > G.e0 ? 1 : 0) + (G.c1 > G.c0 ? 1 : 0) + (G.t1 > G.t0 ? 1 : 0) +
+         (plan->groups.size() == 1 ? rounds_launches(plan) : 1);
   return n;
 }
 

@@ -45,3 +45,166 @@ cudaError_t launch_rounds(const DevProof* proofs, int nproofs, vl_proof* out, in
 }
 
 }  // namespace vl
+
+// ----------------------------------------------------------- batched rounds --
+//
+// The same claim and rounds as rounds_block, organised by round instead of by
+// proof: a round's vector work (fold with the previous challenge, evaluation
+// of g(0), g(1), g(2)) for all proofs is one launch of many CTAs, each on a
+// range of one proof's pairs, and the round's transcript step is one launch
+// with one warp per proof.  A proof's chain of hashes is then never slowed by
+// another proof's vector work sharing its SM, and the vector work of the
+// first rounds spreads over the whole GPU.
+
+namespace vl {
+namespace {
+
+__global__ void __launch_bounds__(RB_THREADS) rounds_pass_kernel(const DevProof* __restrict__ proofs,
+                                                                 const RoundItem* __restrict__ items,
+                                                                 Fr* __restrict__ partials, int t) {
+  __shared__ Fr gsh[4];
+  __shared__ unsigned long long red[3 * 8 * (RB_THREADS / 32)];
+  const RoundItem it = items[blockIdx.x];
+  const DevProof& P = proofs[it.proof];
+  const int tid = threadIdx.x, K = 1 << P.d1;
+  Fr* fA = P.fA;
+  Fr* fB = P.fB;
+  Fr g[3] = {fr_zero(), fr_zero(), fr_zero()};
+  if (t == 1) {
+    // f from the fold (reduced, or column sums to reduce here), round 1 on
+    // pairs (j, j + K/2); j + K/2 may be padding
+    const int h = K >> 1;
+    const Fr corrA = P.scr->corrA, corrB = P.scr->corrB;
+    for (int j = it.j0 + tid; j < it.j1; j += RB_THREADS) {
+      const Fr a0 = P.fdirA ? fA[j] : load_acc_fr(P.accA, j, corrA);
+      const Fr b0 = P.fdirB ? fB[j] : load_acc_fr(P.accB, j, corrB);
+      Fr a1 = fr_zero(), b1 = fr_zero();
+      if (j + h < P.k) {
+        a1 = P.fdirA ? fA[j + h] : load_acc_fr(P.accA, j + h, corrA);
+        b1 = P.fdirB ? fB[j + h] : load_acc_fr(P.accB, j + h, corrB);
+      }
+      fA[j] = a0; fA[j + h] = a1;
+      fB[j] = b0; fB[j + h] = b1;
+      accum_g(g, a0, a1, b0, b1);
+    }
+  } else {
+    // fold with r_(t-1) (vectors of 2h entries) and evaluate round t on the
+    // folded pairs (j, j + hh)
+    const Fr r = P.scr->r;
+    const int h = K >> (t - 1), hh = h >> 1;
+    for (int j = it.j0 + tid; j < it.j1; j += RB_THREADS) {
+      const Fr a0 = fold1(fA[j], fA[j + h], r), a1 = fold1(fA[j + hh], fA[j + hh + h], r);
+      const Fr b0 = fold1(fB[j], fB[j + h], r), b1 = fold1(fB[j + hh], fB[j + hh + h], r);
+      fA[j] = a0; fA[j + hh] = a1;
+      fB[j] = b0; fB[j + hh] = b1;
+      accum_g(g, a0, a1, b0, b1);
+    }
+  }
+  block_sum_canonical<3>(g, gsh, red);
+  if (tid < 3) partials[3 * (size_t)blockIdx.x + tid] = gsh[tid];
+}
+
+__device__ __forceinline__ void state_to_bytes(const uint32_t* S, uint8_t* out, int lane) {
+  out[lane] = (uint8_t)(S[lane >> 2] >> (24 - 8 * (lane & 3)));
+}
+
+__global__ void __launch_bounds__(32 * RB_WARPS) rounds_hash_kernel(const DevProof* __restrict__ proofs, int np,
+                                                                    const int* __restrict__ ibase,
+                                                                    const Fr* __restrict__ partials,
+                                                                    vl_proof* __restrict__ out, int t) {
+  __shared__ uint32_t Ssh[RB_WARPS][8];
+  __shared__ Fr gsh_all[RB_WARPS][4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.x * RB_WARPS + warp;
+  if (p >= np) return;  // whole warps leave together
+  const DevProof& P = proofs[p];
+  vl_proof* pf = out + P.job;
+  uint32_t* S = Ssh[warp];
+  Fr* gsh = gsh_all[warp];
+  if (lane < 8) {
+    const uint8_t* b = P.scr->state + 4 * lane;
+    S[lane] = ((uint32_t)b[0] << 24) | ((uint32_t)b[1] << 16) | ((uint32_t)b[2] << 8) | (uint32_t)b[3];
+  }
+  if (t == 1) {
+    if (lane == 0) {
+      pf->m = P.m; pf->k = P.k; pf->n = P.n;
+      pf->d0 = P.d0; pf->d1 = P.d1; pf->d2 = P.d2;
+      pf->reserved = 0;
+    }
+    for (int i = P.d1 * 3 + lane; i < VL_MAX_ROUNDS * 3; i += 32) store_fr(&pf->g[i / 3][i % 3], fr_zero());
+  }
+  __syncwarp();
+  if (P.d1 == 0) {  // k = 1: no rounds, c = a_r . b_r (first launch only)
+    if (t != 1) return;
+    if (lane == 0) {
+      const Fr a = P.fdirA ? P.fA[0] : load_acc_fr(P.accA, 0, P.scr->corrA);
+      const Fr b = P.fdirB ? P.fB[0] : load_acc_fr(P.accB, 0, P.scr->corrB);
+      const Fr fin[2] = {from_mont_ni(a), from_mont_ni(b)};
+      const Fr c[1] = {from_mont_ni(mont_mul_ni(a, b))};
+      store_fr(&pf->c, c[0]);
+      store_fr(&pf->a_r, fin[0]);
+      store_fr(&pf->b_r, fin[1]);
+      uint32_t st[8];
+#pragma unroll
+      for (int i = 0; i < 8; i++) st[i] = S[i];
+      dev_absorb_fr<1>(st, LBL_C, c);
+      dev_absorb_fr<2>(st, LBL_F, fin);
+#pragma unroll
+      for (int i = 0; i < 8; i++) S[i] = st[i];
+      pf->status = P.scr->status;
+    }
+    __syncwarp();
+    state_to_bytes(S, pf->state, lane);
+    return;
+  }
+  if (P.d1 < t) return;
+  if (lane == 0) {
+    Fr g[3] = {fr_zero(), fr_zero(), fr_zero()};
+    for (int i = ibase[p]; i < ibase[p + 1]; i++)
+#pragma unroll
+      for (int q = 0; q < 3; q++) g[q] = fr_add(g[q], partials[3 * (size_t)i + q]);
+#pragma unroll
+    for (int q = 0; q < 3; q++) gsh[q] = g[q];
+  }
+  __syncwarp();
+  const Fr r = round_transcript(S, gsh, t == 1, pf, t - 1);
+  if (lane == 0) {
+    P.scr->r = r;
+    if (P.rch) P.rch[t - 1] = r;  // chained proofs continue from this point
+    if (t == P.d1) {
+      // last round: a_r, b_r by the last fold; absorb them, write the proof
+      const Fr fin[2] = {from_mont_ni(fold1(P.fA[0], P.fA[1], r)), from_mont_ni(fold1(P.fB[0], P.fB[1], r))};
+      store_fr(&pf->a_r, fin[0]);
+      store_fr(&pf->b_r, fin[1]);
+      uint32_t st[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) st[q] = S[q];
+      dev_absorb_fr<2>(st, LBL_F, fin);
+#pragma unroll
+      for (int q = 0; q < 8; q++) S[q] = st[q];
+      pf->status = P.scr->status;
+    }
+  }
+  __syncwarp();
+  if (t == P.d1) state_to_bytes(S, pf->state, lane);
+  else state_to_bytes(S, P.scr->state, lane);
+}
+
+}  // namespace
+
+cudaError_t launch_rounds_pass(const DevProof* proofs, const RoundItem* items, int nitems, Fr* partials, int t,
+                               cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  rounds_pass_kernel<<<nitems, RB_THREADS, 0, st>>>(proofs, items, partials, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rounds_hash(const DevProof* proofs, int nproofs, const int* ibase, const Fr* partials,
+                               vl_proof* out, int t, cudaStream_t st) {
+  if (nproofs <= 0) return cudaSuccess;
+  rounds_hash_kernel<<<(nproofs + RB_WARPS - 1) / RB_WARPS, 32 * RB_WARPS, 0, st>>>(proofs, nproofs, ibase,
+                                                                                    partials, out, t);
+  return cudaGetLastError();
+}
+
+}  // namespace vl

@@ -118,6 +118,36 @@ __device__ static void squeeze_dev(const uint32_t* Sw, uint32_t label, int count
   __syncthreads();
 }
 
+// Transcript start and the squeezes of u, v into shared memory, or, for a
+// proof with a given point, the given start state and point; the state after
+// them goes to P.scr->state.  Block-wide.
+__device__ static void start_or_given(const DevProof& P, uint32_t* S0, uint32_t* S1, uint32_t* S2,
+                                      uint32_t (*dig)[8], Fr* u, Fr* v) {
+  const int tid = threadIdx.x;
+  if (P.given) {
+    for (int i = tid; i < P.d0 + P.d2; i += blockDim.x) {
+      if (i < P.d0) u[i] = P.given->u[i];
+      else v[i - P.d0] = P.given->v[i - P.d0];
+    }
+    if (tid < 32) P.scr->state[tid] = P.given->state[tid];
+    __syncthreads();
+    return;
+  }
+  if (tid == 0) {
+    uint8_t b[32];
+    if (P.member1 > 0)
+      ts_start_member(b, P.seed, (uint32_t)P.nmembers, (uint32_t)(P.member1 - 1), P.m, P.k, P.n, P.tp, P.tq, P.binds);
+    else
+      ts_start(b, P.seed, P.m, P.k, P.n, P.tp, P.tq, P.binds);
+    for (int i = 0; i < 8; i++)
+      S0[i] = ((uint32_t)b[4 * i] << 24) | ((uint32_t)b[4 * i + 1] << 16) | ((uint32_t)b[4 * i + 2] << 8) | b[4 * i + 3];
+  }
+  __syncthreads();
+  squeeze_dev(S0, LBL_U, P.d0, u, S1, dig);
+  squeeze_dev(S1, LBL_V, P.d2, v, S2, dig);
+  if (tid < 32) P.scr->state[tid] = (uint8_t)(S2[tid >> 2] >> (24 - 8 * (tid & 3)));
+}
+
 // Shared memory the prologue needs (PRO_SMEM bytes), laid out below.
 static_assert(PRO_SMEM == 128 + 2 * MAX_VARS * 32 + 2 * MAX_VARS * 32 + 2 * MAX_HALF * 32 + 8 * 32, "layout");
 
@@ -135,19 +165,7 @@ static __device__ void prologue_block(const DevProof& P, uint8_t* smem) {
   Fr* red = hi + MAX_HALF;
   const int tid = threadIdx.x;
 
-  if (tid == 0) {
-    uint8_t b[32];
-    if (P.member1 > 0)
-      ts_start_member(b, P.seed, (uint32_t)P.nmembers, (uint32_t)(P.member1 - 1), P.m, P.k, P.n, P.tp, P.tq, P.binds);
-    else
-      ts_start(b, P.seed, P.m, P.k, P.n, P.tp, P.tq, P.binds);
-    for (int i = 0; i < 8; i++)
-      S0[i] = ((uint32_t)b[4 * i] << 24) | ((uint32_t)b[4 * i + 1] << 16) | ((uint32_t)b[4 * i + 2] << 8) | b[4 * i + 3];
-  }
-  __syncthreads();
-  squeeze_dev(S0, LBL_U, P.d0, u, S1, dig);
-  squeeze_dev(S1, LBL_V, P.d2, v, S2, dig);
-  if (tid < 32) P.scr->state[tid] = (uint8_t)(S2[tid >> 2] >> (24 - 8 * (tid & 3)));
+  start_or_given(P, S0, S1, S2, dig, u, v);
 
   Fr ca = build_eq(u, P.d0, P.m, P.tabA, P.eqA, P.eqA_soa, P.soa_pitchA, P.w8A, lo, hi, red);
   __syncthreads();
@@ -208,19 +226,7 @@ static __device__ void transcript_block(const DevProof& P, uint8_t* smem) {
   Fr* u = reinterpret_cast<Fr*>(smem + 128 + 2 * MAX_VARS * 32);
   Fr* v = u + MAX_VARS;
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    uint8_t b[32];
-    if (P.member1 > 0)
-      ts_start_member(b, P.seed, (uint32_t)P.nmembers, (uint32_t)(P.member1 - 1), P.m, P.k, P.n, P.tp, P.tq, P.binds);
-    else
-      ts_start(b, P.seed, P.m, P.k, P.n, P.tp, P.tq, P.binds);
-    for (int i = 0; i < 8; i++)
-      S0[i] = ((uint32_t)b[4 * i] << 24) | ((uint32_t)b[4 * i + 1] << 16) | ((uint32_t)b[4 * i + 2] << 8) | b[4 * i + 3];
-  }
-  __syncthreads();
-  squeeze_dev(S0, LBL_U, P.d0, u, S1, dig);
-  squeeze_dev(S1, LBL_V, P.d2, v, S2, dig);
-  if (tid < 32) P.scr->state[tid] = (uint8_t)(S2[tid >> 2] >> (24 - 8 * (tid & 3)));
+  start_or_given(P, S0, S1, S2, dig, u, v);
   eq_factors(u, P.d0, P.m, P.fac, P.fac + EQ_FAC);
   eq_factors(v, P.d2, P.n, P.fac + 2 * EQ_FAC, P.fac + 3 * EQ_FAC);
   if (tid == 0 || tid == 32) {

@@ -173,7 +173,10 @@ static __device__ void rounds_block(const DevProof& P, vl_proof* pf, uint8_t* sm
   for (int i = 0; i < d1; i++) {
     if (warp == 0) {
       const Fr r = round_transcript(S, gsh, i == 0, pf, i);
-      if ((tid & 31) == 0) r_sh = r;
+      if ((tid & 31) == 0) {
+        r_sh = r;
+        if (P.rch) P.rch[i] = r;  // chained proofs continue from this point
+      }
     }
     __syncthreads();
     const Fr r = r_sh;

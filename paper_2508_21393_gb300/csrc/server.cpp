@@ -109,7 +109,8 @@ struct Batch {
   vl_proof* hout = nullptr;   // pinned staging
   size_t nproofs = 0;
   int stream = -1;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t start = nullptr;  // recorded before the batch's work on its stream
+  cudaEvent_t done = nullptr;   // after its proofs reach the host
   int id = 0;
 };
 
@@ -130,6 +131,7 @@ struct vl_server {
   vl_server_stats stats{};
   uint64_t next_ticket = 1;
   int next_batch = 0;
+  cudaEvent_t base = nullptr;  // device clock origin of the batches' intervals
   std::atomic<bool> stop{false};
   std::thread worker;
   int32_t fatal = VL_OK;
@@ -153,6 +155,12 @@ void give_pinned(vl_server* s, vl_proof* p, size_t n) { s->pinned.emplace_back(p
 
 void finish_batch(vl_server* s, Batch* b, int32_t status) {
   const auto now = std::chrono::steady_clock::now();
+  float t0 = 0.f, t1 = 0.f;
+  if (status == VL_OK && b->start && b->done) {
+    if (cudaEventElapsedTime(&t0, s->base, b->start) != cudaSuccess ||
+        cudaEventElapsedTime(&t1, s->base, b->done) != cudaSuccess)
+      t0 = t1 = 0.f;
+  }
   size_t k = 0;
   std::lock_guard<std::mutex> lk(s->mu);
   for (Request& r : b->reqs) {
@@ -168,6 +176,8 @@ void finish_batch(vl_server* s, Batch* b, int32_t status) {
     d.status = st;
     d.batch = b->id;
     d.latency_ms = std::chrono::duration<double, std::milli>(now - r.submitted).count();
+    d.dev_start_ms = t0;
+    d.dev_end_ms = t1;
     s->done.push_back(d);
     s->stats.completed++;
     s->stats.proofs += (int64_t)r.jobs.size();
@@ -180,6 +190,7 @@ void release_batch(vl_server* s, Batch* b) {
   if (b->block) s->arena.release(b->block, b->block_bytes);
   if (b->hout) give_pinned(s, b->hout, b->nproofs);
   if (b->done) cudaEventDestroy(b->done);
+  if (b->start) cudaEventDestroy(b->start);
   if (b->stream >= 0) s->stream_busy[b->stream] = false;
   delete b;
 }
@@ -281,11 +292,13 @@ bool admit(vl_server* s) {
   b->hout = take_pinned(s, b->nproofs);
   cudaStream_t st = s->streams[stream];
   int32_t e = b->hout ? VL_OK : VL_ECUDA;
+  if (e == VL_OK && (cudaEventCreate(&b->start) != cudaSuccess || cudaEventRecord(b->start, st) != cudaSuccess))
+    e = VL_ECUDA;
   if (e == VL_OK) e = vl_plan_run(plan, b->block, wsb, b->dout, VL_DEVICE, st);
   if (e == VL_OK &&
       cudaMemcpyAsync(b->hout, b->dout, sizeof(vl_proof) * b->nproofs, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     e = VL_ECUDA;
-  if (e == VL_OK && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) e = VL_ECUDA;
+  if (e == VL_OK && cudaEventCreate(&b->done) != cudaSuccess) e = VL_ECUDA;
   if (e == VL_OK && cudaEventRecord(b->done, st) != cudaSuccess) e = VL_ECUDA;
   if (e != VL_OK) {
     cudaStreamSynchronize(st);
@@ -294,6 +307,10 @@ bool admit(vl_server* s) {
     return true;
   }
   s->inflight.push_back(b);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stats.launched++;
+  }
   return true;
 }
 
@@ -357,6 +374,13 @@ extern "C" int32_t vl_server_create(const vl_server_opts* opts, vl_server** out)
       delete s;
       return VL_ECUDA;
     }
+  if (cudaEventCreate(&s->base) != cudaSuccess || cudaEventRecord(s->base, s->streams[0]) != cudaSuccess ||
+      cudaEventSynchronize(s->base) != cudaSuccess) {
+    for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+    if (s->base) cudaEventDestroy(s->base);
+    delete s;
+    return VL_ECUDA;
+  }
   s->worker = std::thread(worker_main, s);
   *out = s;
   return VL_OK;
@@ -408,6 +432,7 @@ extern "C" int32_t vl_server_destroy(vl_server* s) {
   if (s->worker.joinable()) s->worker.join();
   for (auto& pb : s->pinned) cudaFreeHost(pb.first);
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+  if (s->base) cudaEventDestroy(s->base);
   delete s;
   return VL_OK;
 }

@@ -482,3 +482,184 @@ extern "C" int32_t vl_verify_matmul_batched(const vl_job* jobs, const vl_mat* C,
   return VL_OK;
   VL_ABI_CATCH(VL_ENOMEM)
 }
+
+// Host verifier of a chained projection proof (Sec. IV, sequential
+// composition; the protocol is written out in include/verilora.h): replays
+// the chain transcript and every member's rounds, checks the output claims
+// against the claimed outputs, each stage-3 claim against the claim the
+// rescale relation derives from the claims on H and dH, and opens only X, W,
+// A, B, dY and the remainders (evaluated directly from the matrices).
+namespace {
+
+int check_host_i16(const vl_mat& M, int64_t rows, int64_t cols) {
+  const int e = check_host_mat(&M);
+  if (e != VL_OK) return e;
+  if (M.dtype == VL_FR_MONT || M.trans != 0) return VL_EINVAL;
+  return (M.rows == rows && M.cols == cols) ? VL_OK : VL_ESHAPE;
+}
+
+void member_start_host(const uint8_t S[32], uint32_t p, uint8_t out[32]) {
+  Sha256 h;
+  h.init();
+  h.update(S, 32);
+  h.byte('M');
+  h.u32le(p);
+  h.finish(out);
+}
+
+// Replay one member's rounds from its start state; returns false on any
+// failed check, the challenges in rs (Montgomery).
+bool replay_member(const vl_proof& pf, const uint8_t start[32], int64_t m, int64_t k, int64_t n,
+                   std::vector<Fr>* rs) {
+  const int d0 = ceil_log2(m), d1 = ceil_log2(k), d2 = ceil_log2(n);
+  if (pf.m != m || pf.k != k || pf.n != n || pf.d0 != d0 || pf.d1 != d1 || pf.d2 != d2) return false;
+  if (pf.status != VL_OK) return false;
+  if (!lt_r(fr_from_api(pf.c)) || !lt_r(fr_from_api(pf.a_r)) || !lt_r(fr_from_api(pf.b_r))) return false;
+  for (int i = 0; i < d1; i++)
+    for (int q = 0; q < 3; q++)
+      if (!lt_r(fr_from_api(pf.g[i][q]))) return false;
+  uint8_t S[32];
+  std::memcpy(S, start, 32);
+  const Fr c = fr_from_api(pf.c);
+  ts_absorb_fr(S, LBL_C, &c, 1);
+  Fr claim = to_mont(c);
+  rs->clear();
+  for (int i = 0; i < d1; i++) {
+    const Fr g[3] = {fr_from_api(pf.g[i][0]), fr_from_api(pf.g[i][1]), fr_from_api(pf.g[i][2])};
+    if (!fr_eq(fr_add(g[0], g[1]), from_mont(claim))) return false;
+    const Fr g02[2] = {g[0], g[2]};
+    ts_absorb_fr(S, LBL_G, g02, 2);
+    const Fr r = to_mont(ts_challenge(S, LBL_R, 0));
+    ts_squeeze_done(S, LBL_R, 1);
+    rs->push_back(r);
+    claim = interp(to_mont(g[0]), to_mont(g[1]), to_mont(g[2]), r);
+  }
+  const Fr ar = fr_from_api(pf.a_r), br = fr_from_api(pf.b_r);
+  if (!fr_eq(claim, mont_mul(to_mont(ar), to_mont(br)))) return false;
+  const Fr fin[2] = {ar, br};
+  ts_absorb_fr(S, LBL_F, fin, 2);
+  return std::memcmp(S, pf.state, 32) == 0;
+}
+
+// sum_{i < size} eq(x, i) (Montgomery)
+Fr eq_sum(const std::vector<Fr>& x, int64_t size) {
+  Fr s = fr_zero();
+  for (const Fr& e : eq_table(x, size)) s = fr_add(s, e);
+  return s;
+}
+
+bool opens(const vl_fr& val, const vl_mat& M, const std::vector<Fr>& x, const std::vector<Fr>& y) {
+  return fr_eq(to_mont(fr_from_api(val)), mle_eval(HostMat{&M}, x, y));
+}
+
+}  // namespace
+
+extern "C" int32_t vl_verify_chain(const vl_chain_job* job, const vl_mat* Y, const vl_mat* dX, const vl_mat* dA,
+                                   const vl_mat* dB, const vl_chain_proof* proof) {
+  VL_ABI_TRY
+  if (!job || !Y || !dX || !dA || !dB || !proof) return VL_EINVAL;
+  const vl_chain_job& J = *job;
+  const int64_t n = J.X.rows, d = J.X.cols, k = J.W.cols, r = J.A.cols;
+  if (n < 1 || d < 1 || k < 1 || r < 1) return VL_ESHAPE;
+  if (n > VL_MAX_REDUCE || d > VL_MAX_REDUCE || k > VL_MAX_REDUCE || r > VL_CHAIN_MAX_RANK) return VL_ESHAPE;
+  int e;
+  if ((e = check_host_i16(J.X, n, d)) || (e = check_host_i16(J.W, d, k)) || (e = check_host_i16(J.A, d, r)) ||
+      (e = check_host_i16(J.B, r, k)) || (e = check_host_i16(J.dY, n, k)) || (e = check_host_i16(J.rhoH, n, r)) ||
+      (e = check_host_i16(J.rhodH, n, r)))
+    return e;
+  for (const vl_mat* M : {Y, dX, dA, dB})
+    if ((e = check_host_mat(M)) != VL_OK) return e;
+  if (Y->rows != n || Y->cols != k || dX->rows != n || dX->cols != d || dA->rows != d || dA->cols != r ||
+      dB->rows != r || dB->cols != k || Y->trans || dX->trans || dA->trans || dB->trans)
+    return VL_ESHAPE;
+  if (proof->n != n || proof->d != d || proof->k != k || proof->r != r || proof->status != VL_OK) return VL_REJECT;
+  for (int q = 0; q < 4; q++)
+    if (!lt_r(fr_from_api(proof->e[q]))) return VL_REJECT;
+  const int ln = ceil_log2(n), ld = ceil_log2(d), lk = ceil_log2(k), lr = ceil_log2(r);
+
+  uint8_t S[32];
+  {
+    const uint8_t dom[25] = {'v', 'e', 'r', 'i', 'l', 'o', 'r', 'a', '-', 'g', 'b', '3', '0',
+                             '0', '/', 'z', 'k', 'c', 'h', 'a', 'i', 'n', '/', 'v', '1'};
+    Sha256 h;
+    h.init();
+    h.update(dom, 25);
+    h.u32le((uint32_t)J.seed);
+    h.u32le((uint32_t)(J.seed >> 32));
+    for (int64_t v : {n, d, k, r}) h.u32le((uint32_t)v);
+    h.update(&J.bind[0][0], 7 * 32);
+    h.finish(S);
+  }
+  const int sz[8] = {ln, lk, ln, ld, ld, lr, lr, lk};
+  std::vector<Fr> pt[8];
+  uint32_t t = 0;
+  for (int s = 0; s < 8; s++)
+    for (int i = 0; i < sz[s]; i++) pt[s].push_back(to_mont(ts_challenge(S, 'p', t++)));
+  ts_squeeze_done(S, 'p', t);
+  const std::vector<Fr>&uY = pt[0], &vY = pt[1], &udX = pt[2], &vdX = pt[3], &udA = pt[4], &vdA = pt[5],
+                      &udB = pt[6], &vdB = pt[7];
+  // members: (m, k, n) of op(P) . op(Q)
+  const int64_t shape[VL_CHAIN_MEMBERS][3] = {{n, d, k}, {n, r, k}, {n, k, d}, {n, r, d}, {d, n, r},
+                                              {r, n, k}, {n, d, r}, {n, d, r}, {n, k, r}, {n, k, r}};
+  std::vector<Fr> rs[VL_CHAIN_MEMBERS];
+  uint8_t start[32];
+  for (int p = 0; p < 6; p++) {
+    member_start_host(S, (uint32_t)p, start);
+    if (!replay_member(proof->sub[p], start, shape[p][0], shape[p][1], shape[p][2], &rs[p])) return VL_REJECT;
+  }
+  const vl_proof* sp = proof->sub;
+  // output claims
+  if (!fr_eq(to_mont(fr_add(fr_from_api(sp[0].c), fr_from_api(sp[1].c))), mle_eval(HostMat{Y}, uY, vY)))
+    return VL_REJECT;
+  if (!fr_eq(to_mont(fr_add(fr_from_api(sp[2].c), fr_from_api(sp[3].c))), mle_eval(HostMat{dX}, udX, vdX)))
+    return VL_REJECT;
+  if (!fr_eq(to_mont(fr_from_api(sp[4].c)), mle_eval(HostMat{dA}, udA, vdA))) return VL_REJECT;
+  if (!fr_eq(to_mont(fr_from_api(sp[5].c)), mle_eval(HostMat{dB}, udB, vdB))) return VL_REJECT;
+  // openings of the inputs where the stage-1 members end
+  if (!opens(sp[0].a_r, J.X, uY, rs[0]) || !opens(sp[0].b_r, J.W, rs[0], vY) || !opens(sp[1].b_r, J.B, rs[1], vY) ||
+      !opens(sp[2].a_r, J.dY, udX, rs[2]) || !opens(sp[2].b_r, J.W, vdX, rs[2]) ||
+      !opens(sp[3].b_r, J.A, vdX, rs[3]) || !opens(sp[4].a_r, J.X, rs[4], udA) ||
+      !opens(sp[5].b_r, J.dY, rs[5], vdB))
+    return VL_REJECT;
+  {
+    Sha256 h;
+    h.init();
+    h.update(S, 32);
+    h.byte('L');
+    for (int p = 0; p < 6; p++) h.update(sp[p].state, 32);
+    h.finish(S);
+  }
+  // the claims on H (p1, p2) and dH (q1, q2), and the remainders there
+  const std::vector<Fr>* px[4] = {&uY, &rs[5], &udX, &rs[4]};
+  const std::vector<Fr>* py[4] = {&rs[1], &udB, &rs[3], &vdA};
+  const vl_fr* onH[4] = {&sp[1].a_r, &sp[5].a_r, &sp[3].a_r, &sp[4].b_r};
+  Fr ev[4];
+  for (int q = 0; q < 4; q++) {
+    ev[q] = fr_from_api(proof->e[q]);
+    if (!opens(proof->e[q], q < 2 ? J.rhoH : J.rhodH, *px[q], *py[q])) return VL_REJECT;
+  }
+  ts_absorb_fr(S, 'e', ev, 4);
+  const Fr z = to_mont(fr_small(256)), half = to_mont(fr_small(128));
+  for (int q = 0; q < 4; q++) {
+    // (X.A)~ or (dY.B^T)~ at the point = 2^8 H~ + rho~ - 2^7 J~
+    const Fr ones = mont_mul(eq_sum(*px[q], n), eq_sum(*py[q], r));
+    const Fr want = fr_sub(fr_add(mont_mul(z, to_mont(fr_from_api(*onH[q]))), to_mont(ev[q])), mont_mul(half, ones));
+    const vl_proof& m3 = sp[6 + q];
+    if (!fr_eq(to_mont(fr_from_api(m3.c)), want)) return VL_REJECT;
+    member_start_host(S, (uint32_t)(6 + q), start);
+    if (!replay_member(m3, start, shape[6 + q][0], shape[6 + q][1], shape[6 + q][2], &rs[6 + q])) return VL_REJECT;
+    const bool ok = q < 2 ? opens(m3.a_r, J.X, *px[q], rs[6 + q]) && opens(m3.b_r, J.A, rs[6 + q], *py[q])
+                          : opens(m3.a_r, J.dY, *px[q], rs[6 + q]) && opens(m3.b_r, J.B, *py[q], rs[6 + q]);
+    if (!ok) return VL_REJECT;
+  }
+  {
+    Sha256 h;
+    h.init();
+    h.update(S, 32);
+    h.byte('Z');
+    for (int p = 6; p < VL_CHAIN_MEMBERS; p++) h.update(sp[p].state, 32);
+    h.finish(S);
+  }
+  return std::memcmp(S, proof->state, 32) == 0 ? VL_OK : VL_REJECT;
+  VL_ABI_CATCH(VL_ENOMEM)
+}

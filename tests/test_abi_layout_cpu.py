@@ -15,7 +15,7 @@ from paper_2508_21393_gb300 import binding as B
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STRUCTS = ["vl_fr", "vl_mat", "vl_fs_init", "vl_proof", "vl_job", "vl_batch_opts", "vl_lin_job", "vl_lin_proof",
            "vl_lookup_job", "vl_lookup_proof", "vl_batch_proof", "vl_server_opts", "vl_server_done",
-           "vl_server_stats"]
+           "vl_server_stats", "vl_chain_job", "vl_chain_proof"]
 
 
 def _ctypes_layout():

@@ -278,13 +278,13 @@ def test_plans_taking_turns_on_one_workspace():
 
 def test_launch_modes_and_fold_engines_agree():
     """Persistent launch, phase launches with the tensor-core fold, phase
-    launches with the CUDA-core fold, every rounds variant and thread count:
-    the same proofs."""
+    launches with the CUDA-core fold, every rounds variant and thread count
+    (8: batched rounds, one launch per round): the same proofs."""
     jobs = _lora_jobs(n=40, d=128, k=96, r=8, layer=6, proj="q")
     dj, keep = _dev_jobs(jobs)
     refs = [oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes() for j in jobs]
     for mode, engine, rv, rt in ((1, 0, 0, 0), (2, 0, 0, 0), (2, 1, 0, 0), (0, 0, 0, 0), (2, 0, 4, 192),
-                                 (2, 0, 3, 256), (2, 0, 2, 0), (2, 0, 4, 0)):
+                                 (2, 0, 3, 256), (2, 0, 2, 0), (2, 0, 4, 0), (2, 0, 8, 0), (2, 1, 8, 0)):
         opts = B.vl_batch_opts()
         opts.persistent = mode
         opts.fold_engine = engine
@@ -368,7 +368,7 @@ def test_tensor_core_fold_matches_oracle_and_cuda_core_fold(shape):
         # both operands are TMA-addressable (ld a multiple of 8) only when so
         tc_ok = (P.shape[1] % 8 == 0) and (Q.shape[1] % 8 == 0)
         if engine == 0 and tc_ok:
-            assert ltc == 3  # prologue, tensor-core fold, rounds
+            assert ltc == 4  # prologue (transcripts, eq tables), tensor-core fold, rounds
 
 
 def test_tensor_core_fold_extreme_entries():

@@ -3,7 +3,10 @@
 Requests of mixed shapes are submitted together into an arena too small to
 hold them all, so admission waits for memory to free up and several batches
 share the device; every request's proofs must equal the proofs of the same
-jobs proved alone (and the oracle's, for two of them), byte for byte.
+jobs proved alone (and the oracle's, for two of them), byte for byte.  A
+request that arrives while another batch is on the device is admitted at
+once into a batch of its own, and the two batches' device intervals (CUDA
+events on their streams) overlap.
 """
 import time
 
@@ -49,8 +52,8 @@ def _wait_all(server, tickets, timeout_s=120.0):
     done = {}
     t0 = time.time()
     while len(done) < len(tickets):
-        for tk, st, batch, lat in B.vl_server_poll(server):
-            done[tk] = (st, batch, lat)
+        for tk, st, batch, lat, dev in B.vl_server_poll(server):
+            done[tk] = (st, batch, lat, dev)
         assert time.time() - t0 < timeout_s, "server did not finish"
         time.sleep(0.002)
     return done
@@ -85,8 +88,8 @@ def test_requests_in_the_mix_equal_alone():
         B.vl_server_destroy(server)
     batches = set()
     for tk, out, ref in zip(tickets, outs, alone):
-        st, batch, lat = done[tk]
-        assert st == 0 and lat > 0
+        st, batch, lat, dev = done[tk]
+        assert st == 0 and lat > 0 and dev[1] > dev[0]
         batches.add(batch)
         assert [B.proof_bytes(p) for p in out] == ref
     assert len(batches) >= 2  # the arena forced more than one batch
@@ -122,3 +125,47 @@ def test_request_larger_than_the_arena_is_refused():
         assert B.proof_bytes(out2[0]) == B.proof_bytes(ref)
     finally:
         B.vl_server_destroy(server)
+
+
+def test_request_arriving_while_a_batch_runs_overlaps_it():
+    """Continuous batching: request B arrives only after request A's batch
+    is on the device; B is admitted into a batch of its own on another
+    stream at once (not after A), the two batches' device intervals overlap,
+    and B's proofs equal B's proofs alone (and the oracle's)."""
+    projs = W.make_step("7b", layers=range(16))  # A: 512 products, about 2 ms on the device
+    dev = {}
+    for t in projs:
+        for key in ("X", "W", "A", "B", "dY", "H", "dH"):
+            dev[id(t[key])] = torch.from_numpy(t[key]).cuda()
+    a_jobs = [B.job(dev[id(j["P"])], dev[id(j["Q"])], j["tp"], j["tq"], j["seed"])
+              for t in projs for j in W.projection_products(t)]
+    b_src, b_jobs, keep = _request(64, 256, 256, 16, 40, "v", True)
+    nb = B.vl_workspace_bytes(b_jobs)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    b_alone = [B.proof_bytes(p) for p in B.vl_prove_batch(b_jobs, ws.data_ptr(), nb)]
+    need = B.vl_workspace_bytes(a_jobs) + nb + (64 << 20)
+    arena = torch.empty(need, dtype=torch.uint8, device="cuda")
+    server = B.vl_server_create(arena.data_ptr(), need, max_inflight=2, max_batch_requests=4)
+    try:
+        out_a = (B.vl_proof * len(a_jobs))()
+        ta = B.vl_server_submit(server, a_jobs, out_a)
+        t0 = time.time()
+        while B.vl_server_stats_get(server)["launched"] < 1:  # A's batch is on the device
+            assert time.time() - t0 < 60
+            time.sleep(0.0002)
+        out_b = (B.vl_proof * len(b_jobs))()
+        tb = B.vl_server_submit(server, b_jobs, out_b)
+        done = _wait_all(server, [ta, tb])
+    finally:
+        B.vl_server_destroy(server)
+    (sa, ba, _, da), (sb, bb, _, db) = done[ta], done[tb]
+    assert sa == 0 and sb == 0 and ba != bb
+    assert db[0] < da[1], f"B's batch started at {db[0]:.3f} ms, after A's ended at {da[1]:.3f} ms"
+    assert da[0] < db[1]
+    assert [B.proof_bytes(p) for p in out_b] == b_alone
+    for j, pf in list(zip(b_src, out_b))[:2]:
+        assert B.proof_bytes(pf) == oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes()
+    # A, spot-checked against the oracle
+    j0 = [j for t in projs[:1] for j in W.projection_products(t)]
+    for j, pf in list(zip(j0, out_a))[:2]:
+        assert B.proof_bytes(pf) == oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes()
