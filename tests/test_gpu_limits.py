@@ -144,12 +144,11 @@ def _lookup_properties(S, t0, log2_n, seed, pf):
     T.absorb_fr(b"f", [a_r, s_r, b_r, m_r])
     assert T.state == bytes(pf.state)
     # the four values against the vectors recomputed from S and T
-    s = S.reshape(-1).astype(np.int64)
-    assert n == D  # no padding at this size
+    s = np.concatenate([S.reshape(-1).astype(np.int64), np.full(D - n, t0, dtype=np.int64)])  # padded with t0
     Binv = np.array([fr_inv((beta + t0 + j) % R_MOD) for j in range(N)], dtype=object)
     A = Binv[s - t0]
     assert a_r == oracle.mle_eval_bind(A, rs), "a_r"
-    assert s_r == oracle.mle_eval_bind((s % R_MOD).tolist(), rs), "s_r"
+    assert s_r == oracle.mle_eval_bind(s.astype(object) % R_MOD, rs), "s_r"
     assert b_r == oracle.mle_eval_bind(Binv, r_low), "b_r"
     m = np.bincount(s - t0, minlength=N)
     assert m_r == oracle.mle_eval_bind(m.tolist(), r_low), "m_r"

@@ -4,7 +4,7 @@ CUDA-graph replay exactly as bench.py runs them.
 * The batched 7B-shaped LoRA step (32 layers x {q,k,v,o}, hidden 4096, seq
   512, ranks {8,16,64}; 1024 proofs): EVERY proof is recomputed by the oracle
   (one projection per worker process, spread over the host's cores) and
-  compared byte for byte.
+  compared byte for byte, for the default rounds and the batched rounds.
 * The 13B-shaped step (40 layers x {q,k,v,o}, hidden 5120 padded to 8192,
   seq 2048, rank 16; 1280 proofs): every proof is replayed (below), and the
   eight proofs of 16 projections spread over the layers are compared byte for
@@ -99,12 +99,16 @@ def test_7b_step_every_proof_equals_the_oracle():
         jobs, proofs = _prove_step(projs)
         for j, pf in zip(jobs, proofs):
             _replay(j, pf)
+        batched = B.vl_batch_opts()
+        batched.rounds_variant = 8  # one launch per round over all proofs
+        _, proofs8 = _prove_step(projs, batched)
     except BaseException:
         pool.terminate()
         raise
     ref = oracle_pool.finish(pool, pending)
     assert len(ref) == len(jobs) == 1024
     _compare(jobs, proofs, ref)
+    _compare(jobs, proofs8, ref)
 
 
 def test_13b_step_batched_graph():
