@@ -44,7 +44,8 @@ SM_MAX_MHZ = 2070.0
 # per clock, a wide (64-bit result) one taking two of them.
 MADWIDE_PER_SM_CLK = 32
 STEP_KIND = {"7b-step": "7b", "7b-proj": "7b-proj", "13b-step": "13b", "serve": "7b-proj", "7b-update": "7b",
-             "7b-step-paper-route": "7b", "7b-lookups": "7b", "7b-step-batched": "7b", "7b-step-all": "7b"}
+             "7b-step-paper-route": "7b", "7b-lookups": "7b", "7b-step-batched": "7b", "7b-step-all": "7b",
+             "7b-step-chain": "7b"}
 WORKLOADS = {
     "7b-step": "batched 7B-shaped LoRA step: 32 layers x {q,k,v,o}, hidden 4096, seq 512, ranks {8,16,64}",
     "7b-proj": "one 7B-shaped LoRA projection, n=1024, d=k=4096, r=16, eight products",
@@ -62,6 +63,10 @@ WORKLOADS = {
                    "stream",
     "7b-update": "parameter updates of the 7B-shaped LoRA step (Eq. eq:grad_update_ab): 32 layers x {q,k,v,o} x "
                  "{A' = A - G_A (4096 x r), B' = B - G_B (r x 4096)}, ranks {8,16,64}, linear zkMat, one batched call",
+    "7b-step-chain": "the 7B-shaped LoRA step as 128 chained projection proofs (Sec. IV sequential composition): per "
+                     "projection ten matmul sumchecks under one transcript, the claims on H and dH reduced through "
+                     "the rescale relations to X.A and dY.B^T (proved at two points each) instead of being opened; "
+                     "32 layers x {q,k,v,o}, hidden 4096, seq 512, ranks {8,16,64}",
     "serve": "serving stream: Poisson arrivals (20 jobs/s) of single-layer jobs (one projection's 8 products), "
              "hidden {4096, 5120}, seq {256, 512, 1024, 2048}, rank {8, 16, 64}, 120 GB admission budget",
 }
@@ -84,8 +89,8 @@ def parse():
                     help="phase launches: 0 tensor-core fold where TMA can address the operand, 1 CUDA cores only")
     ap.add_argument("--groups", type=int, default=0,
                     help="phase launches: proof groups pipelined over three streams (0: library default)")
-    ap.add_argument("--rounds-variant", type=int, default=0, choices=[0, 2, 3, 4, 7],
-                    help="rounds kernel register budget (CTAs per SM); 0 = library default")
+    ap.add_argument("--rounds-variant", type=int, default=0, choices=[0, 2, 3, 4, 7, 8],
+                    help="rounds kernel register budget (CTAs per SM), or 8: batched rounds; 0 = library default")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (it also stays off when launch or tile options are given)")
     ap.add_argument("--serve-jobs", type=int, default=200, help="serve workload: requests in the timed stream")
@@ -154,6 +159,13 @@ def _oracle_projection_task(task):
     with the oracle; returns (seconds proving, MACs, proofs)."""
     kind, seed, spec = task
     t = W.lora_projection(seed, *spec)
+    if kind == "7b-step-chain":
+        import oracle
+        t = W.chain_tensors(t)
+        jobs = chain_products(t, seed)
+        t0 = time.perf_counter()
+        oracle.prove_chain(t, seed=W.proof_seed(seed, t["layer"], t["proj"], "chain"))
+        return time.perf_counter() - t0, sum(W.macs(j) for j in jobs), len(jobs)
     jobs = products(kind, t, seed)
     t0 = time.perf_counter()
     _oracle_prove(kind, seed, jobs)
@@ -387,7 +399,7 @@ def serve_main(args, rank, world, local):
     warm_outs = [submit(pool[sh][0], 7 + i) for i, sh in enumerate(shapes)]  # outputs live until done
     warm = [tk for tk, _ in warm_outs]
     while len(done) < len(warm):
-        for tk, st, b, lat in B.vl_server_poll(server):
+        for tk, st, b, lat, _ in B.vl_server_poll(server):
             done[tk] = (st, b, lat)
         time.sleep(0.001)
     torch.cuda.synchronize()
@@ -402,14 +414,14 @@ def serve_main(args, rank, world, local):
             now = time.perf_counter() - t0
             if now >= ta:
                 break
-            for tk, st, b, lat in B.vl_server_poll(server):
+            for tk, st, b, lat, _ in B.vl_server_poll(server):
                 done[tk] = (st, b, lat, time.perf_counter() - t0)
             time.sleep(min(0.0005, ta - now))
         tk, out = submit(pool[sh][0], 1000003 * (i + 1))
         sub[tk] = (time.perf_counter() - t0, sh)
         outs.append(out)
     while len(done) < len(sub):
-        for tk, st, b, lat in B.vl_server_poll(server):
+        for tk, st, b, lat, _ in B.vl_server_poll(server):
             done[tk] = (st, b, lat, time.perf_counter() - t0)
         time.sleep(0.0005)
     clk = clocks.stop()
@@ -846,6 +858,73 @@ def batched_main(args, rank, world, local, cpu=None):
         plans[k].destroy()
 
 
+def chain_products(t, seed):
+    """The ten products of one projection's chained proof, as oracle jobs
+    (the member operands; the chain draws their points itself)."""
+    X, W_, A, B_, dY, H, dH = (t[x] for x in ("X", "W", "A", "B", "dY", "H", "dH"))
+    spec = [(X, W_, 0, 0), (H, B_, 0, 0), (dY, W_, 0, 1), (dH, A, 0, 1), (X, dH, 1, 0), (H, dY, 1, 0),
+            (X, A, 0, 0), (X, A, 0, 0), (dY, B_, 0, 1), (dY, B_, 0, 1)]
+    return [{"P": P, "Q": Q, "tp": tp, "tq": tq} for P, Q, tp, tq in spec]
+
+
+def chain_main(args, rank, world, local, cpu=None):
+    """The 7B step as one batch of chained projection proofs (a vl_chain_plan,
+    rerun every step; each run ends with the proofs copied to the host)."""
+    import torch
+    from paper_2508_21393_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.lib()
+    seed = rank_seed(rank)
+    projs = [W.chain_tensors(t) for t in W.make_step("7b", seed, layers=range(args.layers) if args.layers else None)]
+    macs_step = sum(W.macs(j) for t in projs for j in chain_products(t, seed))
+    entries = sum(W.fold_entries(j) for t in projs for j in chain_products(t, seed))
+    dev = [{k: torch.from_numpy(np.ascontiguousarray(t[k])).cuda() for k in B.CHAIN_MATS} for t in projs]
+    jobs = [B.chain_job(d, seed=W.proof_seed(seed, t["layer"], t["proj"], "chain")) for d, t in zip(dev, projs)]
+    plan = B.ChainPlan(jobs)
+    nws = plan.workspace_bytes()
+    ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        out = plan.run(ws.data_ptr(), nws, stream)
+    assert all(p.status == 0 for p in out)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    time.sleep(0.6)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.run(ws.data_ptr(), nws, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = job_value(macs_step, world, ms_max / 1e3)
+    plan.destroy()
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int16 operands, Fr (255-bit) arithmetic", "data": "synthetic",
+        "config": {"workload": WORKLOADS["7b-step-chain"] + (f", first {args.layers} layers" if args.layers else ""),
+                   "chains_per_step": len(jobs), "sumchecks_per_step": 10 * len(jobs), "macs_per_step": macs_step,
+                   "fold_entries_per_step": entries, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single GPU",
+                   "timed": "vl_chain_plan_run per step, including its synchronising copy of the proofs to the host"},
+        "roofline": None, "cpu_baseline": cpu, "e2e": None, "clocks": clk,
+        "gpu_launches": None,
+    }))
+
+
 def all_main(args, rank, world, local):
     """Matmul proofs, parameter-update proofs and remainder lookups of one 7B
     step, each as its plan on its own stream; ms_per_step is the fork-join
@@ -954,6 +1033,12 @@ def main():
         return serve_main(args, rank, world, local)
     if args.workload == "7b-step-all":
         return all_main(args, rank, world, local)
+    if args.workload == "7b-step-chain":
+        cpu = None
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            cpu = oracle_cores_baseline(args.workload, W.GLOBAL_SEED)
+            cpu["sample"] += "; chained proofs"
+        return chain_main(args, rank, world, local, cpu)
     if args.workload == "7b-step-batched":
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1124,40 +1209,80 @@ def main():
     # End to end through the C ABI: pinned host operands in, host proofs out.
     e2e = None
     if not args.no_e2e:
-        host = {}
-        for t in projs:
-            for key in ("X", "W", "A", "B", "dY", "H", "dH", "dWr"):
-                if key not in t:
-                    continue
-                h = torch.empty(t[key].shape, dtype=torch.int16, pin_memory=True)
-                h.copy_(torch.from_numpy(t[key]))
-                host[id(t[key])] = h
+        # The step in chunks of whole projections (4 layers each), one plan
+        # per chunk, on two streams: a chunk's host operands are copied in
+        # while the previous chunk is proved.  Each chunk's operands sit in
+        # one pinned host buffer (256-byte aligned, back to back), which the
+        # library stages with one copy.  Proofs go to device memory and come
+        # back in one copy at the end of the step.
+        pper = min(16, len(projs))
+        host, arenas = {}, []
+        for c0 in range(0, len(projs), pper):
+            mats = [t[key] for t in projs[c0:c0 + pper]
+                    for key in ("X", "W", "A", "B", "dY", "H", "dH", "dWr") if key in t]
+            offs, tot = [], 0
+            for a in mats:
+                offs.append(tot)
+                tot += (a.nbytes + 255) // 256 * 256
+            arena = torch.empty(tot, dtype=torch.uint8, pin_memory=True)
+            arenas.append(arena)
+            for a, o in zip(mats, offs):
+                h = arena[o:o + a.nbytes].view(torch.int16).view(a.shape)
+                h.copy_(torch.from_numpy(a))
+                host[id(a)] = h
         hjobs = [B.job(host[id(j["P"])], host[id(j["Q"])], j["tp"], j["tq"], j["seed"]) for j in jobs]
         hopts = B.vl_batch_opts.from_buffer_copy(opts)  # the same (tuned) options
         hopts.timing_runs = 1
-        hplan = B.vl_plan_create(hjobs, hopts)
-        hn = B.vl_plan_workspace_bytes(hplan)
+        per = len(jobs) // len(projs) * pper
+        chunks = [hjobs[i:i + per] for i in range(0, len(hjobs), per)]
+        hplans = [B.vl_plan_create(c, hopts) for c in chunks]
+        hsizes = [B.vl_plan_workspace_bytes(p) for p in hplans]
         del ws
-        hws = torch.empty(hn, dtype=torch.uint8, device="cuda")
-        hout = (B.vl_proof * len(hjobs))()
+        hwss = [torch.empty(n, dtype=torch.uint8, device="cuda") for n in hsizes]
+        psz = ctypes.sizeof(B.vl_proof)
+        dproofs = torch.empty(len(hjobs) * psz, dtype=torch.uint8, device="cuda")
+        hproofs = torch.empty(len(hjobs) * psz, dtype=torch.uint8, pin_memory=True)
+        pipes = [torch.cuda.Stream(), torch.cuda.Stream()]
+        fork, joins = torch.cuda.Event(), [torch.cuda.Event(), torch.cuda.Event()]
+
+        def e2e_step():
+            fork.record(stream)
+            off = 0
+            for i, (hp, c) in enumerate(zip(hplans, chunks)):
+                s2 = pipes[i % 2]
+                s2.wait_event(fork)
+                B.vl_plan_run(hp, hwss[i].data_ptr(), hsizes[i], dproofs.data_ptr() + off, B.VL_DEVICE, s2)
+                off += len(c) * psz
+            for ev, s2 in zip(joins, pipes):
+                ev.record(s2)
+                stream.wait_event(ev)
+            hproofs.copy_(dproofs, non_blocking=True)
+            stream.synchronize()
+
         for _ in range(2):
-            B.vl_plan_run(hplan, hws.data_ptr(), hn, hout, B.VL_HOST, stream)
+            e2e_step()
+        st_h = np.frombuffer(hproofs.numpy().tobytes(), dtype=np.int32).reshape(len(hjobs), -1)[:, 6]
+        assert (st_h == 0).all(), "a proof reported a non-OK status (end to end)"
         ksteps = max(1, min(args.steps, 5))
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(ksteps):
-            B.vl_plan_run(hplan, hws.data_ptr(), hn, hout, B.VL_HOST, stream)
+            e2e_step()
         e2e_s = (time.perf_counter() - t0) / ksteps
         e2e_max = max_over_ranks(e2e_s, world, "cuda")
         h2d = int(sum(h.numel() * 2 for h in host.values()))
         rate = pinned_h2d_gbs(stream)
         e2e = {"value": job_value(macs_step, world, e2e_max), "unit": UNIT,
                "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": int(ctypes.sizeof(B.vl_proof) * len(hjobs)),
+               "d2h_bytes_per_step": int(psz * len(hjobs)),
                "ms_per_step": 1e3 * e2e_max, "steps": ksteps,
-               "pinned_h2d_gbs": rate, "copy_bound_ms": 1e3 * h2d / (rate * 1e9)}
-        B.vl_plan_destroy(hplan)
+               "pinned_h2d_gbs": rate, "copy_bound_ms": 1e3 * h2d / (rate * 1e9),
+               "pipeline": f"{len(chunks)} plans of {pper} projections on 2 streams (copy of chunk i+1 overlaps the "
+                           f"proving of chunk i; each chunk's operands in one pinned buffer, staged by one copy), "
+                           f"one proof copy-out per step"}
+        for hp in hplans:
+            B.vl_plan_destroy(hp)
 
     launches = args.steps * B.vl_plan_launches(plan)
     B.vl_plan_destroy(plan)

@@ -485,8 +485,10 @@ int32_t vl_verify_matmul_batched(const vl_job* jobs, const vl_mat* C, int32_t nj
 /* Autotuner (the paper has no counterpart): picks the launch and tile
  * options for `jobs` by timing candidate plans on the caller's workspace and
  * stream — coordinate descent from `base` (NULL: defaults) over the fold
- * engine, tc_seg, rounds_variant, the launch mode and, where CUDA-core fold
- * tiles run, colsum_rows / rowdot_cols; each candidate is run once untimed
+ * engine, tc_seg, rounds_variant (including the batched rounds, 8),
+ * rounds_threads and, where CUDA-core fold tiles run, colsum_rows /
+ * rowdot_cols (the persistent launch is not a candidate: its CUDA-core fold
+ * is slower than phase launches); each candidate is run once untimed
  * and `runs` times timed (0: 3), its time the median.  Candidates needing more
  * workspace than workspace_bytes (which must also hold njobs proofs at its
  * end) are skipped.  The result is cached per shape signature (dimensions,

@@ -133,7 +133,12 @@ extern "C" int32_t vl_autotune(const vl_job* jobs, int32_t njobs, const vl_batch
       {&vl_batch_opts::tc_seg, {0, 8192, 4096, 2048}},
       {&vl_batch_opts::rounds_variant, {7, 4, 3, 2, 8}},
       {&vl_batch_opts::rounds_threads, {0, 192, 256}},
-      {&vl_batch_opts::persistent, {2, 1}},
+      // The persistent single launch (persistent = 1) is not a candidate: it
+      // runs the CUDA-core fold (its fold tiles are pulled from a work queue
+      // by CTAs that also run prologues and rounds, which the tensor-core
+      // fold's one-CTA-per-SM pipeline with all of TMEM cannot share), and
+      // is about 3x slower than phase launches on the LoRA steps.  Callers
+      // can still ask for it.
       {&vl_batch_opts::colsum_rows, {0, 128, 512}},
       {&vl_batch_opts::rowdot_cols, {0, 512, 2048}},
   };

@@ -37,6 +37,12 @@ struct RoundItem {
 static constexpr int RB_PAIRS = 256;    // pairs per item
 static constexpr int RB_THREADS = 128;  // threads of a pass CTA
 static constexpr int RB_WARPS = 4;      // proofs per transcript CTA (one warp each)
+static constexpr int RB_TAIL_LOG = 9;   // rounds with at most 2^9 pairs run in the per-proof tail
+// Rounds of a proof with d1 variables that run batched: those with more than
+// 2^RB_TAIL_LOG pairs (round t has 2^(d1 - t) pairs).
+__host__ __device__ __forceinline__ int batched_rounds(int d1) {
+  return d1 - RB_TAIL_LOG - 1 > 0 ? d1 - RB_TAIL_LOG - 1 : 0;
+}
 
 // Per-proof read-only descriptor (device copy of the plan).
 struct DevProof {
@@ -335,16 +341,18 @@ cudaError_t step_grid(int smem_bytes, int* grid);
 cudaError_t launch_step(const StepItem* items, int nitems, const FoldTask* tasks, const FoldTile* tiles,
                         const DevProof* proofs, int nproofs, vl_proof* out, int* ctl, int grid, int smem_bytes,
                         unsigned long long wait_ns, int never_ready, cudaStream_t st);
-// Batched rounds: round t (1-based) of every proof with d1 >= t.  Pass:
-// fold with r_(t-1) (t > 1; for t = 1 the fold's output is reduced) and
-// evaluate the round over `nitems` items, one canonical partial triple per
-// item; transcript: one warp per proof of [0, nproofs) sums its items'
+// Batched rounds: round t (1-based, t <= batched_rounds(d1)) of every such
+// proof.  Pass: fold with r_(t-1) (for t = 1 the fold's output is reduced)
+// and evaluate the round over `nitems` items, one canonical partial triple
+// per item; transcript: one warp per proof of [0, nproofs) sums its items'
 // partials (items ibase[p] .. ibase[p + 1]), writes and absorbs the round
-// message, squeezes r_t, and after its last round writes the proof.
+// message and squeezes r_t.  Tail: one CTA per proof runs its remaining
+// rounds and writes the proof.
 cudaError_t launch_rounds_pass(const DevProof* proofs, const RoundItem* items, int nitems, Fr* partials, int t,
                                cudaStream_t st);
 cudaError_t launch_rounds_hash(const DevProof* proofs, int nproofs, const int* ibase, const Fr* partials,
                                vl_proof* out, int t, cudaStream_t st);
+cudaError_t launch_rounds_tail(const DevProof* proofs, int nproofs, vl_proof* out, cudaStream_t st);
 cudaError_t launch_rounds(const DevProof* proofs, int nproofs, vl_proof* out, int variant, int threads,
                           cudaStream_t st);
 cudaError_t launch_encode(const int16_t* src, int64_t rows, int64_t cols, int64_t ld, Fr* dst,

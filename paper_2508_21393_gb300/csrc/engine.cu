@@ -77,6 +77,14 @@ struct Staged {
   size_t bytes;
 };
 
+// One host-to-device copy of staged operands: host matrices whose ranges
+// lie close together keep their relative layout in the workspace and move
+// as one range.
+struct StageRun {
+  const void* host;
+  size_t off, bytes;
+};
+
 }  // namespace
 
 struct vl_plan {
@@ -125,6 +133,7 @@ struct vl_plan {
   };
   std::vector<PerProof> pp;
   std::map<const void*, Staged> staging;  // host operand -> device copy
+  std::vector<StageRun> stage_runs;       // the copies that fill the staging
   // bound state
   void* bound_ws = nullptr;
   vl_proof* bound_out = nullptr;
@@ -435,26 +444,26 @@ int build_plan(vl_plan* p) {
     p->pp[i].fac = off;
     off = align_up(off + sizeof(Fr) * 4 * EQ_FAC);
   }
-  // batched rounds: items of RB_PAIRS pairs per proof and round
+  // batched rounds: items of RB_PAIRS pairs per proof and batched round
+  // (proofs with batched rounds are a prefix: k-descending)
   {
-    const int maxd1 = np ? p->proofs[0].d1 : 0;
+    const int maxb = np ? batched_rounds(p->proofs[0].d1) : 0;
     p->ritems.clear();
     p->ibase.clear();
-    p->r_item0.assign(maxd1 + 2, 0);
-    p->r_nitem.assign(maxd1 + 2, 0);
-    p->r_ib0.assign(maxd1 + 2, 0);
-    p->r_np.assign(maxd1 + 2, 0);
+    p->r_item0.assign(maxb + 2, 0);
+    p->r_nitem.assign(maxb + 2, 0);
+    p->r_ib0.assign(maxb + 2, 0);
+    p->r_np.assign(maxb + 2, 0);
     size_t max_items = 1;
-    for (int t = 1; t <= std::max(maxd1, 1); t++) {
+    for (int t = 1; t <= maxb; t++) {
       p->r_item0[t] = (int)p->ritems.size();
       p->r_ib0[t] = (int)p->ibase.size();
       int npt = 0;
       for (int i = 0; i < np; i++) {
         const DevProof& P = p->proofs[i];
-        if (t > 1 && P.d1 < t) break;  // k-descending: the rest have fewer rounds
+        if (batched_rounds(P.d1) < t) break;
         npt = i + 1;
         p->ibase.push_back((int)p->ritems.size() - p->r_item0[t]);
-        if (P.d1 < t) continue;
         const int pairs = 1 << (P.d1 - t);
         for (int j0 = 0; j0 < pairs; j0 += RB_PAIRS)
           p->ritems.push_back(RoundItem{i, j0, std::min(pairs, j0 + RB_PAIRS), 0});
@@ -471,7 +480,13 @@ int build_plan(vl_plan* p) {
     p->off_partials = off;
     off = align_up(off + 3 * sizeof(Fr) * max_items);
   }
-  // staging for host operands (one device copy per distinct host pointer)
+  // staging for host operands: one device copy of each distinct host
+  // matrix.  Matrices whose host ranges follow each other closely (gap of at
+  // most 4 KB, both 16-byte aligned) are staged with the same relative layout
+  // and copied as one range: a step's many small operands then cost a few
+  // large copies instead of one copy each.
+  p->staging.clear();
+  p->stage_runs.clear();
   for (const vl_job& j : p->jobs) {
     for (const vl_mat* M : {&j.P, &j.Q}) {
       if (M->space != VL_HOST) continue;
@@ -481,8 +496,33 @@ int build_plan(vl_plan* p) {
         if (it->second.bytes < bytes) return VL_EINVAL;  // same pointer, different extent
         continue;
       }
-      p->staging[M->data] = Staged{off, bytes};
-      off = align_up(off + bytes);
+      p->staging[M->data] = Staged{0, bytes};
+    }
+  }
+  {
+    const uint8_t* run_host = nullptr;
+    size_t run_off = 0, run_len = 0;
+    for (auto& kv : p->staging) {  // ascending host addresses
+      const uint8_t* h = static_cast<const uint8_t*>(kv.first);
+      const bool aligned = reinterpret_cast<uintptr_t>(h) % 16 == 0;
+      const bool join = run_host && aligned && reinterpret_cast<uintptr_t>(run_host) % 16 == 0 &&
+                        h >= run_host + run_len && (size_t)(h - (run_host + run_len)) <= 4096;
+      if (!join) {
+        if (run_host) {
+          p->stage_runs.push_back(StageRun{run_host, run_off, run_len});
+          off = align_up(run_off + run_len);
+        }
+        run_host = h;
+        run_off = off;
+        run_len = 0;
+      }
+      const size_t rel = (size_t)(h - run_host);
+      kv.second.off = run_off + rel;
+      run_len = std::max(run_len, rel + kv.second.bytes);
+    }
+    if (run_host) {
+      p->stage_runs.push_back(StageRun{run_host, run_off, run_len});
+      off = align_up(run_off + run_len);
     }
   }
   p->total = off;
@@ -726,21 +766,19 @@ cudaError_t enqueue_rounds(vl_plan* p, uint8_t* ws, const DevProof* dp, vl_proof
   const RoundItem* items = reinterpret_cast<const RoundItem*>(ws + p->off_ritems);
   const int* ibase = reinterpret_cast<const int*>(ws + p->off_ibase);
   Fr* partials = reinterpret_cast<Fr*>(ws + p->off_partials);
-  const int maxd1 = np ? p->proofs[0].d1 : 0;
   cudaError_t e = cudaSuccess;
-  for (int t = 1; t <= std::max(maxd1, 1) && e == cudaSuccess; t++) {
-    e = launch_rounds_pass(dp, items + p->r_item0[t], p->r_nitem[t], partials, t, st);
-    if (e == cudaSuccess)
-      e = launch_rounds_hash(dp, t == 1 ? np : p->r_np[t], ibase + p->r_ib0[t], partials, dout, t, st);
+  for (size_t t = 1; t + 1 < p->r_nitem.size() && e == cudaSuccess; t++) {
+    e = launch_rounds_pass(dp, items + p->r_item0[t], p->r_nitem[t], partials, (int)t, st);
+    if (e == cudaSuccess) e = launch_rounds_hash(dp, p->r_np[t], ibase + p->r_ib0[t], partials, dout, (int)t, st);
   }
+  if (e == cudaSuccess) e = launch_rounds_tail(dp, np, dout, st);
   return e;
 }
 
 int rounds_launches(const vl_plan* p) {
   if (p->opts.rounds_variant != 8) return 1;
-  int n = 0;
-  for (size_t t = 1; t < p->r_nitem.size(); t++)
-    n += (p->r_nitem[t] > 0 ? 1 : 0) + ((t == 1 || p->r_np[t] > 0) ? 1 : 0);
+  int n = 1;  // the tail
+  for (size_t t = 1; t + 1 < p->r_nitem.size(); t++) n += (p->r_nitem[t] > 0 ? 1 : 0) + (p->r_np[t] > 0 ? 1 : 0);
   return n;
 }
 
@@ -855,8 +893,8 @@ void drop_graph(vl_plan* p) {
 }
 
 int stage_host_operands(vl_plan* p, uint8_t* ws, cudaStream_t st) {
-  for (auto& kv : p->staging) {
-    cudaError_t e = cudaMemcpyAsync(ws + kv.second.off, kv.first, kv.second.bytes, cudaMemcpyHostToDevice, st);
+  for (const StageRun& r : p->stage_runs) {
+    cudaError_t e = cudaMemcpyAsync(ws + r.off, r.host, r.bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_status(e, "stage host operand");
   }
   return VL_OK;

@@ -48,20 +48,37 @@ cudaError_t launch_rounds(const DevProof* proofs, int nproofs, vl_proof* out, in
 
 // ----------------------------------------------------------- batched rounds --
 //
-// The same claim and rounds as rounds_block, organised by round instead of by
-// proof: a round's vector work (fold with the previous challenge, evaluation
-// of g(0), g(1), g(2)) for all proofs is one launch of many CTAs, each on a
-// range of one proof's pairs, and the round's transcript step is one launch
-// with one warp per proof.  A proof's chain of hashes is then never slowed by
-// another proof's vector work sharing its SM, and the vector work of the
-// first rounds spreads over the whole GPU.
+// The same claim and rounds as rounds_block, with the heavy first rounds
+// organised by round instead of by proof: while a proof's round has more
+// than RB_TAIL pairs, the round's vector work (fold with the previous
+// challenge, evaluation of g(0), g(1), g(2)) for all such proofs is one launch
+// of many CTAs, each on a range of one proof's pairs, and the round's
+// transcript step is one launch with one warp per proof.  The first rounds'
+// vector work (three quarters of a proof's) then spreads over the whole GPU
+// instead of one CTA per proof; the rounds after that, short vector passes
+// between serial hashes, run as before, one CTA per proof (rounds_block from
+// the proof's first unbatched round), in one launch.
 
 namespace vl {
 namespace {
 
-__global__ void __launch_bounds__(RB_THREADS) rounds_pass_kernel(const DevProof* __restrict__ proofs,
-                                                                 const RoundItem* __restrict__ items,
-                                                                 Fr* __restrict__ partials, int t) {
+// accum_g and fold1 with the Montgomery product inlined: the three products
+// of a pair are independent, and inlined the compiler interleaves them.
+__device__ __forceinline__ void accum_g_inl(Fr (&g)[3], const Fr& a0, const Fr& a1, const Fr& b0, const Fr& b1) {
+  const Fr p0 = mont_mul(a0, b0), p1 = mont_mul(a1, b1);
+  const Fr p2 = mont_mul(fr_sub(fr_dbl(a1), a0), fr_sub(fr_dbl(b1), b0));
+  g[0] = fr_add(g[0], p0);
+  g[1] = fr_add(g[1], p1);
+  g[2] = fr_add(g[2], p2);
+}
+
+__device__ __forceinline__ Fr fold1_inl(const Fr& x0, const Fr& x1, const Fr& r) {
+  return fr_add(x0, mont_mul(r, fr_sub(x1, x0)));
+}
+
+__global__ void __launch_bounds__(RB_THREADS, 4) rounds_pass_kernel(const DevProof* __restrict__ proofs,
+                                                                    const RoundItem* __restrict__ items,
+                                                                    Fr* __restrict__ partials, int t) {
   __shared__ Fr gsh[4];
   __shared__ unsigned long long red[3 * 8 * (RB_THREADS / 32)];
   const RoundItem it = items[blockIdx.x];
@@ -72,20 +89,24 @@ __global__ void __launch_bounds__(RB_THREADS) rounds_pass_kernel(const DevProof*
   Fr g[3] = {fr_zero(), fr_zero(), fr_zero()};
   if (t == 1) {
     // f from the fold (reduced, or column sums to reduce here), round 1 on
-    // pairs (j, j + K/2); j + K/2 may be padding
+    // pairs (j, j + K/2); j + K/2 may be padding (written as zeros)
     const int h = K >> 1;
+    const bool da = P.fdirA, db = P.fdirB;
     const Fr corrA = P.scr->corrA, corrB = P.scr->corrB;
     for (int j = it.j0 + tid; j < it.j1; j += RB_THREADS) {
-      const Fr a0 = P.fdirA ? fA[j] : load_acc_fr(P.accA, j, corrA);
-      const Fr b0 = P.fdirB ? fB[j] : load_acc_fr(P.accB, j, corrB);
+      const Fr a0 = da ? fA[j] : load_acc_fr(P.accA, j, corrA);
+      const Fr b0 = db ? fB[j] : load_acc_fr(P.accB, j, corrB);
+      const bool real = j + h < P.k;
       Fr a1 = fr_zero(), b1 = fr_zero();
-      if (j + h < P.k) {
-        a1 = P.fdirA ? fA[j + h] : load_acc_fr(P.accA, j + h, corrA);
-        b1 = P.fdirB ? fB[j + h] : load_acc_fr(P.accB, j + h, corrB);
+      if (real) {
+        a1 = da ? fA[j + h] : load_acc_fr(P.accA, j + h, corrA);
+        b1 = db ? fB[j + h] : load_acc_fr(P.accB, j + h, corrB);
       }
-      fA[j] = a0; fA[j + h] = a1;
-      fB[j] = b0; fB[j + h] = b1;
-      accum_g(g, a0, a1, b0, b1);
+      if (!da) fA[j] = a0;
+      if (!da || !real) fA[j + h] = a1;
+      if (!db) fB[j] = b0;
+      if (!db || !real) fB[j + h] = b1;
+      accum_g_inl(g, a0, a1, b0, b1);
     }
   } else {
     // fold with r_(t-1) (vectors of 2h entries) and evaluate round t on the
@@ -93,11 +114,11 @@ __global__ void __launch_bounds__(RB_THREADS) rounds_pass_kernel(const DevProof*
     const Fr r = P.scr->r;
     const int h = K >> (t - 1), hh = h >> 1;
     for (int j = it.j0 + tid; j < it.j1; j += RB_THREADS) {
-      const Fr a0 = fold1(fA[j], fA[j + h], r), a1 = fold1(fA[j + hh], fA[j + hh + h], r);
-      const Fr b0 = fold1(fB[j], fB[j + h], r), b1 = fold1(fB[j + hh], fB[j + hh + h], r);
+      const Fr a0 = fold1_inl(fA[j], fA[j + h], r), a1 = fold1_inl(fA[j + hh], fA[j + hh + h], r);
+      const Fr b0 = fold1_inl(fB[j], fB[j + h], r), b1 = fold1_inl(fB[j + hh], fB[j + hh + h], r);
       fA[j] = a0; fA[j + hh] = a1;
       fB[j] = b0; fB[j + hh] = b1;
-      accum_g(g, a0, a1, b0, b1);
+      accum_g_inl(g, a0, a1, b0, b1);
     }
   }
   block_sum_canonical<3>(g, gsh, red);
@@ -108,6 +129,8 @@ __device__ __forceinline__ void state_to_bytes(const uint32_t* S, uint8_t* out, 
   out[lane] = (uint8_t)(S[lane >> 2] >> (24 - 8 * (lane & 3)));
 }
 
+// Transcript step of round t for proofs [0, np) (each has more rounds after
+// t: the last rounds are the tail's).
 __global__ void __launch_bounds__(32 * RB_WARPS) rounds_hash_kernel(const DevProof* __restrict__ proofs, int np,
                                                                     const int* __restrict__ ibase,
                                                                     const Fr* __restrict__ partials,
@@ -133,31 +156,6 @@ __global__ void __launch_bounds__(32 * RB_WARPS) rounds_hash_kernel(const DevPro
     }
     for (int i = P.d1 * 3 + lane; i < VL_MAX_ROUNDS * 3; i += 32) store_fr(&pf->g[i / 3][i % 3], fr_zero());
   }
-  __syncwarp();
-  if (P.d1 == 0) {  // k = 1: no rounds, c = a_r . b_r (first launch only)
-    if (t != 1) return;
-    if (lane == 0) {
-      const Fr a = P.fdirA ? P.fA[0] : load_acc_fr(P.accA, 0, P.scr->corrA);
-      const Fr b = P.fdirB ? P.fB[0] : load_acc_fr(P.accB, 0, P.scr->corrB);
-      const Fr fin[2] = {from_mont_ni(a), from_mont_ni(b)};
-      const Fr c[1] = {from_mont_ni(mont_mul_ni(a, b))};
-      store_fr(&pf->c, c[0]);
-      store_fr(&pf->a_r, fin[0]);
-      store_fr(&pf->b_r, fin[1]);
-      uint32_t st[8];
-#pragma unroll
-      for (int i = 0; i < 8; i++) st[i] = S[i];
-      dev_absorb_fr<1>(st, LBL_C, c);
-      dev_absorb_fr<2>(st, LBL_F, fin);
-#pragma unroll
-      for (int i = 0; i < 8; i++) S[i] = st[i];
-      pf->status = P.scr->status;
-    }
-    __syncwarp();
-    state_to_bytes(S, pf->state, lane);
-    return;
-  }
-  if (P.d1 < t) return;
   if (lane == 0) {
     Fr g[3] = {fr_zero(), fr_zero(), fr_zero()};
     for (int i = ibase[p]; i < ibase[p + 1]; i++)
@@ -171,23 +169,17 @@ __global__ void __launch_bounds__(32 * RB_WARPS) rounds_hash_kernel(const DevPro
   if (lane == 0) {
     P.scr->r = r;
     if (P.rch) P.rch[t - 1] = r;  // chained proofs continue from this point
-    if (t == P.d1) {
-      // last round: a_r, b_r by the last fold; absorb them, write the proof
-      const Fr fin[2] = {from_mont_ni(fold1(P.fA[0], P.fA[1], r)), from_mont_ni(fold1(P.fB[0], P.fB[1], r))};
-      store_fr(&pf->a_r, fin[0]);
-      store_fr(&pf->b_r, fin[1]);
-      uint32_t st[8];
-#pragma unroll
-      for (int q = 0; q < 8; q++) st[q] = S[q];
-      dev_absorb_fr<2>(st, LBL_F, fin);
-#pragma unroll
-      for (int q = 0; q < 8; q++) S[q] = st[q];
-      pf->status = P.scr->status;
-    }
   }
   __syncwarp();
-  if (t == P.d1) state_to_bytes(S, pf->state, lane);
-  else state_to_bytes(S, P.scr->state, lane);
+  state_to_bytes(S, P.scr->state, lane);
+}
+
+// The rounds after the batched ones, one CTA per proof.
+__global__ void __launch_bounds__(128, 4) rounds_tail_kernel(const DevProof* __restrict__ proofs,
+                                                             vl_proof* __restrict__ out) {
+  extern __shared__ __align__(128) uint8_t rnd_smem[];
+  const DevProof& P = proofs[blockIdx.x];
+  rounds_block(P, out + P.job, rnd_smem, 1 + batched_rounds(P.d1));
 }
 
 }  // namespace
@@ -204,6 +196,12 @@ cudaError_t launch_rounds_hash(const DevProof* proofs, int nproofs, const int* i
   if (nproofs <= 0) return cudaSuccess;
   rounds_hash_kernel<<<(nproofs + RB_WARPS - 1) / RB_WARPS, 32 * RB_WARPS, 0, st>>>(proofs, nproofs, ibase,
                                                                                     partials, out, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rounds_tail(const DevProof* proofs, int nproofs, vl_proof* out, cudaStream_t st) {
+  if (nproofs <= 0) return cudaSuccess;
+  rounds_tail_kernel<<<nproofs, 128, RND_SMEM, st>>>(proofs, out);
   return cudaGetLastError();
 }
 

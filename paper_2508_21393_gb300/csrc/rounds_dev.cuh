@@ -99,8 +99,12 @@ __device__ __forceinline__ Fr round_transcript(uint32_t* S, const Fr* gsh, bool 
 }
 
 // Claim, rounds and proof of one proof by the whole block (any multiple of
-// 32 threads up to 256).
-static __device__ void rounds_block(const DevProof& P, vl_proof* pf, uint8_t* smem) {
+// 32 threads up to 256), from round t0 on.  t0 = 1: everything.  t0 > 1: the
+// earlier rounds ran batched over many proofs (kernels_rounds.cu): their
+// messages are in the proof already, the transcript state and r_(t0-1) are
+// in the scratch, and the vectors hold the round-(t0-1) values, 2^(d1-t0+2)
+// entries each.
+static __device__ void rounds_block(const DevProof& P, vl_proof* pf, uint8_t* smem, int t0 = 1) {
   uint32_t* S = reinterpret_cast<uint32_t*>(smem);
   Fr* gsh = reinterpret_cast<Fr*>(smem + 32);
   Fr& r_sh = gsh[3];
@@ -110,12 +114,14 @@ static __device__ void rounds_block(const DevProof& P, vl_proof* pf, uint8_t* sm
     const uint8_t* b = P.scr->state + 4 * tid;
     S[tid] = ((uint32_t)b[0] << 24) | ((uint32_t)b[1] << 16) | ((uint32_t)b[2] << 8) | (uint32_t)b[3];
   }
-  if (tid == 0) {
-    pf->m = P.m; pf->k = P.k; pf->n = P.n;
-    pf->d0 = P.d0; pf->d1 = P.d1; pf->d2 = P.d2;
-    pf->reserved = 0;
+  if (t0 == 1) {
+    if (tid == 0) {
+      pf->m = P.m; pf->k = P.k; pf->n = P.n;
+      pf->d0 = P.d0; pf->d1 = P.d1; pf->d2 = P.d2;
+      pf->reserved = 0;
+    }
+    for (int i = P.d1 * 3 + tid; i < VL_MAX_ROUNDS * 3; i += nthr) store_fr(&pf->g[i / 3][i % 3], fr_zero());
   }
-  for (int i = P.d1 * 3 + tid; i < VL_MAX_ROUNDS * 3; i += nthr) store_fr(&pf->g[i / 3][i % 3], fr_zero());
   const int d1 = P.d1, K = 1 << d1;
   const Fr corrA = P.scr->corrA, corrB = P.scr->corrB;
   Fr* fA = P.fA;
@@ -149,9 +155,20 @@ static __device__ void rounds_block(const DevProof& P, vl_proof* pf, uint8_t* sm
     return;
   }
 
-  // Pass 0: f from the accumulators, and round 1 (pairs j, j + K/2).
   Fr g[3] = {fr_zero(), fr_zero(), fr_zero()};
-  {
+  if (t0 > 1) {
+    // fold the round-(t0-1) vectors with r_(t0-1) and evaluate round t0
+    const Fr r = P.scr->r;
+    const int h = K >> (t0 - 1), hh = h >> 1;
+    for (int j = tid; j < hh; j += nthr) {
+      const Fr a0 = fold1(fA[j], fA[j + h], r), a1 = fold1(fA[j + hh], fA[j + hh + h], r);
+      const Fr b0 = fold1(fB[j], fB[j + h], r), b1 = fold1(fB[j + hh], fB[j + hh + h], r);
+      fA[j] = a0; fA[j + hh] = a1;
+      fB[j] = b0; fB[j + hh] = b1;
+      accum_g(g, a0, a1, b0, b1);
+    }
+  } else {
+    // Pass 0: f from the accumulators, and round 1 (pairs j, j + K/2).
     const int h = K >> 1;
     for (int j = tid; j < h; j += nthr) {
       // K/2 < k <= K, so j < k always; j + h may be padding.
@@ -170,7 +187,7 @@ static __device__ void rounds_block(const DevProof& P, vl_proof* pf, uint8_t* sm
   }
   block_sum_canonical<3>(g, gsh, red);
 
-  for (int i = 0; i < d1; i++) {
+  for (int i = t0 - 1; i < d1; i++) {
     if (warp == 0) {
       const Fr r = round_transcript(S, gsh, i == 0, pf, i);
       if ((tid & 31) == 0) {

@@ -433,3 +433,43 @@ def test_paper_backward_route_products():
         assert B.proof_bytes(pf) == ref, j["name"]
         C = W.claimed_product(j)
         assert B.vl_verify_matmul(B.mat(j["P"], j["tp"]), B.mat(j["Q"], j["tq"]), B.mat(C), B.fs_init(j["seed"]), pf)
+
+
+def test_host_operands_packed_in_one_buffer_are_staged_together():
+    """Host operands laid out back to back in one pinned buffer are staged
+    with one copy per run of neighbouring matrices; a matrix at a 2-byte
+    offset (not 16-byte aligned) starts a run of its own.  The proofs equal
+    those of the same jobs with device operands, through a plan run twice."""
+    jobs = _lora_jobs(n=48, d=96, k=80, r=8, layer=9, proj="k")
+    mats, seen = [], set()
+    for j in jobs:
+        for key in ("P", "Q"):
+            if id(j[key]) not in seen:
+                seen.add(id(j[key]))
+                mats.append(j[key])
+    offs, tot = [], 0
+    for i, a in enumerate(mats):
+        offs.append(tot + (2 if i == 3 else 0))  # one matrix off the 16-byte grid
+        tot = offs[-1] + (a.nbytes + 255) // 256 * 256
+    arena = torch.empty(tot + 256, dtype=torch.uint8, pin_memory=True)
+    host = {}
+    for a, o in zip(mats, offs):
+        h = arena[o:o + a.nbytes].view(torch.int16).view(a.shape)
+        h.copy_(torch.from_numpy(np.ascontiguousarray(a)))
+        host[id(a)] = h
+    hj = [B.job(host[id(j["P"])], host[id(j["Q"])], j["tp"], j["tq"], j["seed"]) for j in jobs]
+    dj, keep = _dev_jobs(jobs)
+    nd = B.vl_workspace_bytes(dj)
+    want = [B.proof_bytes(p) for p in B.vl_prove_batch(dj, _ws(nd).data_ptr(), nd)]
+    plan = B.vl_plan_create(hj)
+    try:
+        nb = B.vl_plan_workspace_bytes(plan)
+        ws = _ws(nb)
+        for _ in range(2):
+            out = (B.vl_proof * len(hj))()
+            B.vl_plan_run(plan, ws.data_ptr(), nb, out, B.VL_HOST)
+            assert [B.proof_bytes(p) for p in out] == want
+    finally:
+        B.vl_plan_destroy(plan)
+    ref = oracle.prove_matmul(jobs[0]["P"], jobs[0]["Q"], jobs[0]["tp"], jobs[0]["tq"], seed=jobs[0]["seed"])
+    assert want[0] == ref.to_bytes()
