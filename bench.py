@@ -228,6 +228,40 @@ def oracle_cores_baseline(kind, seed):
                       f"(the slowest worker's proving time)"}
 
 
+# Rounds of one matmul proof with d1 variables: round 1 evaluates g(0), g(1),
+# g(2) on 2^(d1-1) pairs (three field products each); every later round t
+# folds four values and evaluates three products on 2^(d1-t) pairs; the last
+# fold is two products.
+def rounds_products(d1):
+    if d1 == 0:
+        return 1
+    return 3 * (1 << (d1 - 1)) + 7 * ((1 << (d1 - 1)) - 1) + 2
+
+
+# One round's transcript step on the GPU (absorb g(0) || g(2): two SHA-256
+# compressions; squeeze r: one more; the 512-bit reduction): a serial chain
+# of 12.3 K cycles for one warp alone (clock64 over 200 dependent steps on the
+# box, at 2.07 GHz 5.9 us).  The derived field-product peak: 152 SMs x 32
+# IMAD.WIDE per clock x 2.07 GHz / 128 IMAD.WIDE per Montgomery product.
+ROUND_HASH_CYCLES = 12300
+PRODUCTS_PEAK = SMS * MADWIDE_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 128
+
+
+def rounds_bound(jobs, rounds_ms):
+    """Bounds of the claims-and-rounds phase: the field products of every
+    proof's rounds against the derived product peak (throughput), and the
+    longest proof's serial chain of transcript steps (latency)."""
+    d1s = [(W.op_shape(j)[1] - 1).bit_length() for j in jobs]
+    prods = sum(rounds_products(d) for d in d1s)
+    thr_us = prods / PRODUCTS_PEAK * 1e6
+    lat_us = max(d1s) * ROUND_HASH_CYCLES / (SM_MAX_MHZ * 1e6) * 1e6
+    bound_us = max(thr_us, lat_us)
+    return {"field_products": prods, "throughput_bound_us": thr_us, "latency_bound_us": lat_us,
+            "bound_us": bound_us, "measured_us": 1e3 * rounds_ms, "frac": bound_us / (1e3 * rounds_ms),
+            "note": "products at the derived ALU peak (152 SMs x 32 IMAD.WIDE/clk x 2070 MHz / 128 per product); "
+                    "latency = max d1 x 12.3 K-cycle transcript step (measured single-warp chain)"}
+
+
 def pinned_h2d_gbs(stream, nbytes=1 << 30, reps=3):
     """Plain host-to-device copy rate of this machine: one cudaMemcpyAsync of a
     pinned 1 GiB buffer, best of `reps`, timed with CUDA events."""
@@ -1179,7 +1213,10 @@ def main():
                 "frac": hbm_gbs / hbm_peak, "traffic": traffic,
                 "peak_note": f"{hbm_note} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": 2 * entries,
+                "unique_input_bytes": in_bytes,
+                "frac_of_unique_bytes": in_bytes / (fold_ms / 1e3) / 1e9 / hbm_peak,
                 "tensor_tflops_fp16": tflops}
+    rounds_roof = rounds_bound(jobs, rnd_ms)
 
     # Unbatched per-matmul path: each product proved by its own plan (graph),
     # one after another on the same stream.
@@ -1301,7 +1338,7 @@ def main():
                    "launch_mode": "one persistent launch" if persistent else "phase launches (CUDA graph)",
                    "fold_engine": "CUDA cores" if cuda_core else "tensor cores",
                    "autotuned": tuned,
-                   "phase_ms": phase_ms},
+                   "phase_ms": phase_ms, "rounds_bound": rounds_roof},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
