@@ -91,6 +91,8 @@ def parse():
                     help="phase launches: proof groups pipelined over three streams (0: library default)")
     ap.add_argument("--rounds-variant", type=int, default=0, choices=[0, 2, 3, 4, 7, 8],
                     help="rounds kernel register budget (CTAs per SM), or 8: batched rounds; 0 = library default")
+    ap.add_argument("--fold-dual", action="store_true",
+                    help="fold a matrix used as row dots and as column sums in one pass (dual tiles)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (it also stays off when launch or tile options are given)")
     ap.add_argument("--serve-jobs", type=int, default=200, help="serve workload: requests in the timed stream")
@@ -1128,7 +1130,8 @@ def main():
     opts.persistent = 1 if args.persistent else 2
     opts.fold_engine = args.fold_engine
     opts.groups = args.groups
-    forced = args.persistent or args.fold_engine or args.rounds_variant or args.groups
+    opts.fold_dual = 1 if args.fold_dual else 0
+    forced = args.persistent or args.fold_engine or args.rounds_variant or args.groups or args.fold_dual
     tuned = None
     if not args.no_autotune and not forced:
         # Launch and tile options by timing candidates on this workload (not timed).
@@ -1173,6 +1176,8 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
+    status = np.frombuffer(out.cpu().numpy().tobytes(), dtype=np.int32).reshape(len(djobs), -1)[:, 6]
+    assert (status == 0).all(), "a proof of the timed steps reported a non-OK status"
     ms = e0.elapsed_time(e1) / args.steps
     phases = B.vl_plan_phase_ms(plan, args.steps, reset=1)
     ms_max = max_over_ranks(ms, world, "cuda")
@@ -1202,13 +1207,14 @@ def main():
     else:
         # Tensor-core fold: streams every operand entry once from HBM.
         kernel, phase_ms = "fold_tc_kernel", {"clear+prologue": pro_ms, "fold": fold_ms, "rounds": rnd_ms}
-        # 64 fp16 MACs per entry (two bytes x 32 weight bytes) plus the init
-        # MMA of each 64-entry stage (2048 MACs per 128 x 64 entries)
-        tflops = 2 * (64 + 0.25) * entries / (fold_ms / 1e3) / 1e12
+        # 64 fp16 MACs per entry (two bytes x 32 weight bytes) plus the two
+        # constant MMAs of each 128-entry stage (2 x 128 x 32 x 16 MACs per
+        # 128 x 128 entries: 8 per entry)
+        tflops = 2 * (64 + 8) * entries / (fold_ms / 1e3) / 1e12
         # DRAM traffic per launch: ncu capture of the same kernel on the first
-        # two layers (profiles/fold_tc_kernel_7b_2layers.md), 440.6 MB for 746 MB
+        # two layers (profiles/fold_tc_kernel_7b_2layers.md), 444.4 MB for 750 MB
         # algorithmic, scaled by entries (the tile mix repeats per projection).
-        traffic = 0.5906 * 2 * entries if args.workload == "7b-step" else None
+        traffic = 0.5926 * 2 * entries if args.workload == "7b-step" else None
         roof = {"bound": "hbm", "kernel": kernel, "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": hbm_gbs / hbm_peak, "traffic": traffic,
                 "peak_note": f"{hbm_note} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",

@@ -163,6 +163,13 @@ typedef struct vl_batch_opts {
                             whose prologue never signals ready, so that its
                             fold tiles exhaust their bounded wait and report
                             VL_ETIMEOUT (persistent mode); 0: off            */
+  int32_t fold_dual;     /* tensor-core fold, one proof group: a matrix that
+                            one job folds as row dots and another as column
+                            sums (the frozen W of X.W and dY.W^T), with rows
+                            and columns multiples of 128, is streamed once for
+                            both (one conversion, two MMA sets): 1: on, 0: off
+                            (default: on the LoRA steps it is slower than two
+                            passes, the second one hitting L2)               */
 } vl_batch_opts;
 
 typedef struct vl_plan vl_plan; /* opaque batched-step plan */
@@ -485,7 +492,8 @@ int32_t vl_verify_matmul_batched(const vl_job* jobs, const vl_mat* C, int32_t nj
 /* Autotuner (the paper has no counterpart): picks the launch and tile
  * options for `jobs` by timing candidate plans on the caller's workspace and
  * stream — coordinate descent from `base` (NULL: defaults) over the fold
- * engine, tc_seg, rounds_variant (including the batched rounds, 8),
+ * engine, the dual tiles (fold_dual), tc_seg, rounds_variant (including the
+ * batched rounds, 8),
  * rounds_threads and, where CUDA-core fold tiles run, colsum_rows /
  * rowdot_cols (the persistent launch is not a candidate: its CUDA-core fold
  * is slower than phase launches); each candidate is run once untimed

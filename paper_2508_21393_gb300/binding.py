@@ -142,7 +142,7 @@ class vl_batch_opts(ctypes.Structure):
                 ("use_graph", ctypes.c_int32),
                 ("timing_runs", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
                 ("rounds_variant", ctypes.c_int32), ("rounds_threads", ctypes.c_int32), ("tc_seg", ctypes.c_int32),
-                ("test_never_ready", ctypes.c_int32)]
+                ("test_never_ready", ctypes.c_int32), ("fold_dual", ctypes.c_int32)]
 
 
 class VLError(RuntimeError):

@@ -148,24 +148,46 @@ struct TcTile {
   int32_t pad;
 };
 static_assert(sizeof(TcTile) == 72, "tile descriptor");
+
+// Dual tensor-core fold tile: one 128-row strip of a stored int16 matrix W
+// (rows and columns multiples of 128) that one proof folds as row dots (its
+// lines are W's rows) and another as column sums (lines are W's columns),
+// streamed once in stages of 128 columns [k0, k0 + nk).  The row dots of the
+// strip's rows run across the tile (written reduced to fR when the tile
+// covers every column, else added to accR); each stage's column sums cover
+// only the strip's rows and are added to accC.
+struct DualTile {
+  const void* tmap;          // TMA map of W with row-dot boxes (64 columns x 128 rows, 128B swizzle)
+  const uint32_t* w8R;       // fp16 weight bytes of the row-dot side (over W's columns)
+  const uint32_t* w8C;       // fp16 weight bytes of the column-sum side (over W's rows)
+  unsigned long long* accR;  // row-dot accumulators of the strip's first row, or
+  Fr* fR;                    //   its f entries (whole-reduction tiles)
+  const Fr* corrR;           //   minus this offset correction (Montgomery)
+  unsigned long long* accC;  // column-sum accumulators of W's column 0 (8 per column)
+  int32_t w0;                // first row of the strip
+  int32_t k0, nk;            // columns [k0, k0 + nk), nk a multiple of 128
+  int32_t proofR, proofC;    // for status reports
+  int32_t taskR, taskC;      // host bookkeeping
+  int32_t pad[3];
+};
+static_assert(sizeof(DualTile) == 96, "dual tile descriptor");
 static constexpr int TC_M = 128;        // lines per tile (MMA M)
 static constexpr int TC_KS = 128;       // reduction entries per pipeline stage
-static constexpr int TC_KP = 64;        // entries per exact fp32 accumulation period (two per stage)
+static constexpr int TC_KP = 64;        // entries per weight-table chunk and per row-dot TMA box (two per stage)
 static constexpr int TC_SEG = 16384;    // reduction entries per tile (default; a multiple of TC_KS, at most 32768)
 static constexpr int TC_CONV_WARPS = 8;   // int16 -> fp16 byte operands
 static constexpr int TC_DRAIN_WARPS = 8;  // TMEM -> digit sums (two groups of four lane quarters)
+static constexpr int TC_ISSUERS = 4;      // MMA issuing threads (one per warp): two (lo, hi) pairs
 // warp 0 producer, warp 1 first MMA issuer (TMEM owner), then converters,
-// drainers, and the other three MMA issuers last
-static constexpr int TC_THREADS = 32 * (5 + TC_CONV_WARPS + TC_DRAIN_WARPS);
-// Ring depths (overridable at build time for tuning sweeps).
+// drainers, and the other MMA issuers last
+static constexpr int TC_THREADS = 32 * (1 + TC_ISSUERS + TC_CONV_WARPS + TC_DRAIN_WARPS);
+// Ring depths.
 #ifndef TC_NR
 #define TC_NR 4  // operand (TMA) stages, 32 KB of shared memory each
 #endif
-#ifndef TC_NW
-#define TC_NW 4  // weight stages, 8 KB each
-#endif
-static constexpr int TC_NC = 2;   // converted-operand stages (TMEM, 128 columns each)
-static constexpr int TC_NA = 2;   // accumulator buffers (TMEM, 128 columns each: two periods)
+static constexpr int TC_NW = 4;   // weight stages, 8 KB each
+static constexpr int TC_NC = 2;   // converted-operand stages (TMEM, 128 columns each: lo 64, hi 64)
+static constexpr int TC_NA = 4;   // accumulator buffers (TMEM, 64 columns each: lo 32, hi 32)
 static constexpr int TC_HR = 32;  // stage-header ring (> TC_NR + TC_NC + TC_NA)
 static_assert(TC_HR > TC_NR + TC_NC + TC_NA, "header ring");
 static constexpr int TC_SMEM = 1024 + TC_NR * 32768 + TC_NW * 8192 + 5120 + 4096 + 3072;
@@ -227,6 +249,10 @@ cudaError_t launch_fold(const FoldTask* tasks, const FoldTile* tiles, int ntiles
 cudaError_t fold_tc_prepare();
 cudaError_t launch_fold_tc(const TcTile* tiles, int ntiles, const DevProof* proofs, unsigned long long wait_ns,
                            cudaStream_t st);
+// Dual tiles (kernels_fold_tc.cu): CTA b takes tiles b, b + grid, ...
+cudaError_t fold_dual_prepare();
+cudaError_t launch_fold_dual(const DualTile* tiles, int ntiles, const DevProof* proofs, unsigned long long wait_ns,
+                             cudaStream_t st);
 // Linear zkMat (kernels_linear.cu): the statement and the device buffers of
 // one proof, in the workspace.  The tensor-core fold reduces every matrix
 // over one logical dimension (rows when red_rows, else columns) with that

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -85,6 +86,46 @@ struct StageRun {
   size_t off, bytes;
 };
 
+// Where a host operand lives: pinned memory (an allocation of the CUDA
+// driver, with its range when the driver reports it) or other (pageable)
+// memory.  A copy from pinned memory must stay inside one allocation; a copy
+// from pageable memory may only read mapped bytes.
+struct HostRange {
+  bool pinned = false, known = false;
+  uintptr_t base = 0;
+  size_t size = 0;
+};
+
+HostRange host_range(const void* ptr) {
+  using Fn = CUresult (*)(void*, CUpointer_attribute, CUdeviceptr);
+  static const Fn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      return reinterpret_cast<Fn>(f);
+    return static_cast<Fn>(nullptr);
+  }();
+  HostRange r;
+  const CUdeviceptr p = reinterpret_cast<CUdeviceptr>(ptr);
+  unsigned int type = 0;
+  if (!fn) {
+    r.pinned = true;  // cannot tell: treat as pinned of unknown extent (never joined)
+    return r;
+  }
+  if (fn(&type, CU_POINTER_ATTRIBUTE_MEMORY_TYPE, p) != CUDA_SUCCESS) return r;  // not the driver's: pageable
+  r.pinned = true;
+  CUdeviceptr base = 0;
+  size_t size = 0;
+  if (fn(&base, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, p) == CUDA_SUCCESS &&
+      fn(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, p) == CUDA_SUCCESS) {
+    r.known = true;
+    r.base = (uintptr_t)base;
+    r.size = size;
+  }
+  return r;
+}
+
 }  // namespace
 
 struct vl_plan {
@@ -94,6 +135,8 @@ struct vl_plan {
   std::vector<FoldTask> tasks;
   std::vector<FoldTile> tiles;
   std::vector<TcTile> tc_tiles;  // tensor-core fold (phase launches)
+  std::vector<DualTile> dual_tiles;  // tensor-core fold of matrices folded both ways
+  size_t off_dual_tiles = 0;
   std::vector<EqItem> eq_items;  // eq-table chunks, proof by proof
   std::vector<StepItem> items;  // persistent step: queue order
   // Phase launches: proofs in groups (k descending); the graph folds group g
@@ -316,6 +359,64 @@ void build_items(vl_plan* p) {
   }
 }
 
+// Pair each tensor-core row-dot task with a tensor-core column-sum task on
+// the same stored matrix (rows and columns multiples of 128) into dual tiles
+// that stream the matrix once for both; the column-sum side then
+// accumulates (each strip adds its rows' partial sums).  One proof group
+// and phase launches only.
+void build_dual(vl_plan* p) {
+  p->dual_tiles.clear();
+  if (p->opts.fold_dual != 1 || persistent(p) || p->opts.groups > 1) return;
+  const int nt = (int)p->tasks.size();
+  std::vector<int> partner(nt, -1);
+  auto mat_of = [&](int t) -> const vl_mat& {
+    const FoldTask& T = p->tasks[t];
+    const vl_job& j = p->jobs[p->proofs[T.proof].job];
+    return T.side ? j.Q : j.P;
+  };
+  for (int r = 0; r < nt; r++) {
+    const FoldTask& R = p->tasks[r];
+    if (R.bulk != 2 || R.mode != MODE_ROWDOT || R.rows % TC_M || R.cols % TC_KS) continue;
+    const vl_mat& MR = mat_of(r);
+    for (int c = 0; c < nt; c++) {
+      const FoldTask& C = p->tasks[c];
+      if (partner[c] >= 0 || C.bulk != 2 || C.mode != MODE_COLSUM) continue;
+      const vl_mat& MC = mat_of(c);
+      if (MC.data != MR.data || MC.ld != MR.ld || MC.rows != MR.rows || MC.cols != MR.cols || MC.space != MR.space)
+        continue;
+      partner[c] = r;
+      partner[r] = c;
+      break;
+    }
+  }
+  const int seg = p->opts.tc_seg > 0 ? p->opts.tc_seg : TC_SEG;
+  std::vector<TcTile> keep;
+  keep.reserve(p->tc_tiles.size());
+  for (const TcTile& tt : p->tc_tiles)
+    if (partner[tt.task] < 0) keep.push_back(tt);
+  if (keep.size() == p->tc_tiles.size()) return;
+  p->tc_tiles.swap(keep);
+  for (int r = 0; r < nt; r++) {
+    if (partner[r] < 0 || p->tasks[r].mode != MODE_ROWDOT) continue;
+    const int c = partner[r];
+    const FoldTask& R = p->tasks[r];
+    const FoldTask& C = p->tasks[c];
+    (C.side ? p->proofs[C.proof].fdirB : p->proofs[C.proof].fdirA) = 0;  // strips add partial column sums
+    for (int w0 = 0; w0 < R.rows; w0 += TC_M)
+      for (int k0 = 0; k0 < R.cols; k0 += seg) {
+        DualTile d{};
+        d.w0 = w0;
+        d.k0 = k0;
+        d.nk = std::min(seg, R.cols - k0);
+        d.proofR = R.proof;
+        d.proofC = C.proof;
+        d.taskR = r;
+        d.taskC = c;
+        p->dual_tiles.push_back(d);
+      }
+  }
+}
+
 int build_plan(vl_plan* p) {
   const int np = (int)p->jobs.size();
   // u32 digit sums hold at most 512 stages of 64 entries
@@ -368,6 +469,7 @@ int build_plan(vl_plan* p) {
     // f_B: op(Q) over its n columns.  Stored k x n -> row dots; stored n x k -> column sums.
     add_fold_task(p, j.Q, j.Q.trans ? MODE_COLSUM : MODE_ROWDOT, i, 1);
   }
+  build_dual(p);
   // eq-table chunks (tensor-core tables run to a multiple of 128 entries)
   p->eq_items.clear();
   for (int i = 0; i < np; i++) {
@@ -388,6 +490,8 @@ int build_plan(vl_plan* p) {
   off = align_up(off + sizeof(TcTile) * p->tc_tiles.size());
   p->off_eq_items = off;
   off = align_up(off + sizeof(EqItem) * p->eq_items.size());
+  p->off_dual_tiles = off;
+  off = align_up(off + sizeof(DualTile) * p->dual_tiles.size());
   p->off_tmaps = off;
   off = align_up(off + sizeof(CUtensorMap) * p->tasks.size());
   p->off_etmaps = off;
@@ -481,8 +585,9 @@ int build_plan(vl_plan* p) {
     off = align_up(off + 3 * sizeof(Fr) * max_items);
   }
   // staging for host operands: one device copy of each distinct host
-  // matrix.  Matrices whose host ranges follow each other closely (gap of at
-  // most 4 KB, both 16-byte aligned) are staged with the same relative layout
+  // matrix.  Matrices whose host ranges follow each other (both 16-byte
+  // aligned; in one pinned allocation with a gap of at most 4 KB, or both in
+  // pageable memory and touching) are staged with the same relative layout
   // and copied as one range: a step's many small operands then cost a few
   // large copies instead of one copy each.
   p->staging.clear();
@@ -502,17 +607,26 @@ int build_plan(vl_plan* p) {
   {
     const uint8_t* run_host = nullptr;
     size_t run_off = 0, run_len = 0;
+    HostRange run_range;
     for (auto& kv : p->staging) {  // ascending host addresses
       const uint8_t* h = static_cast<const uint8_t*>(kv.first);
+      const HostRange hr = host_range(h);
       const bool aligned = reinterpret_cast<uintptr_t>(h) % 16 == 0;
-      const bool join = run_host && aligned && reinterpret_cast<uintptr_t>(run_host) % 16 == 0 &&
-                        h >= run_host + run_len && (size_t)(h - (run_host + run_len)) <= 4096;
+      const size_t gap = run_host && h >= run_host + run_len ? (size_t)(h - (run_host + run_len)) : SIZE_MAX;
+      bool fits = false;
+      if (run_host && (run_range.pinned || hr.pinned))
+        fits = run_range.known && hr.known && run_range.base == hr.base && gap <= 4096 &&
+               reinterpret_cast<uintptr_t>(h) + kv.second.bytes <= hr.base + hr.size;
+      else if (run_host)
+        fits = gap == 0;
+      const bool join = fits && aligned && reinterpret_cast<uintptr_t>(run_host) % 16 == 0;
       if (!join) {
         if (run_host) {
           p->stage_runs.push_back(StageRun{run_host, run_off, run_len});
           off = align_up(run_off + run_len);
         }
         run_host = h;
+        run_range = hr;
         run_off = off;
         run_len = 0;
       }
@@ -679,8 +793,25 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
     tt.f = direct ? (t.side ? P.fB : P.fA) + tt.w0 : nullptr;
     tt.corr = direct ? (t.side ? &P.scr->corrB : &P.scr->corrA) : nullptr;
   }
+  for (DualTile& d : p->dual_tiles) {
+    const FoldTask& R = p->tasks[d.taskR];
+    const FoldTask& C = p->tasks[d.taskC];
+    const DevProof& PR = p->proofs[R.proof];
+    const DevProof& PC = p->proofs[C.proof];
+    d.tmap = R.tmap;
+    d.w8R = R.side ? PR.w8B : PR.w8A;
+    d.w8C = C.side ? PC.w8B : PC.w8A;
+    const bool direct = R.side ? PR.fdirB : PR.fdirA;
+    d.accR = direct ? nullptr : (R.side ? PR.accB : PR.accA) + (size_t)d.w0 * 8;
+    d.fR = direct ? (R.side ? PR.fB : PR.fA) + d.w0 : nullptr;
+    d.corrR = direct ? (R.side ? &PR.scr->corrB : &PR.scr->corrA) : nullptr;
+    d.accC = C.side ? PC.accB : PC.accA;
+  }
   cudaError_t e = cudaMemcpyAsync(ws + p->off_proofs, p->proofs.data(), sizeof(DevProof) * np,
                                   cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !p->dual_tiles.empty())
+    e = cudaMemcpyAsync(ws + p->off_dual_tiles, p->dual_tiles.data(), sizeof(DualTile) * p->dual_tiles.size(),
+                        cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !p->tasks.empty())
     e = cudaMemcpyAsync(ws + p->off_tasks, p->tasks.data(), sizeof(FoldTask) * p->tasks.size(),
                         cudaMemcpyHostToDevice, st);
@@ -712,6 +843,7 @@ int bind_workspace(vl_plan* p, uint8_t* ws, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess && p->fold_smem > 0) e = fold_set_smem(p->fold_smem);
   if (e == cudaSuccess && !p->tc_tiles.empty()) e = fold_tc_prepare();
+  if (e == cudaSuccess && !p->dual_tiles.empty()) e = fold_dual_prepare();
   if (e == cudaSuccess && persistent(p)) e = step_set_smem(p->step_smem);
   if (e == cudaSuccess && persistent(p) && !p->step_grid) e = step_grid(p->step_smem, &p->step_grid);
   return cuda_status(e, "bind_workspace");
@@ -821,6 +953,9 @@ cudaError_t enqueue_pass(vl_plan* p, uint8_t* ws, vl_proof* dout, cudaStream_t s
     if (e == cudaSuccess) e = cudaMemsetAsync(ws + p->off_ctl, 0, p->off_acc + p->acc_bytes - p->off_ctl, st);
     if (e == cudaSuccess) e = launch_prologue(dp, 0, np, de, (int)p->eq_items.size(), st);
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[1], st, flags);
+    if (e == cudaSuccess)
+      e = launch_fold_dual(reinterpret_cast<const DualTile*>(ws + p->off_dual_tiles), (int)p->dual_tiles.size(), dp,
+                           wait_ns(p), st);
     if (e == cudaSuccess) e = launch_fold_tc(dc, (int)p->tc_tiles.size(), dp, wait_ns(p), st);
     if (e == cudaSuccess) e = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, wait_ns(p), st);
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2], st, flags);
@@ -1044,7 +1179,7 @@ int32_t vl_plan_launches(const vl_plan* plan) {
   int32_t n = 0;
   for (const vl_plan::Group& G : plan->groups)  // prologue (transcripts, eq chunks), folds, rounds
     n += 1 + (G.e1 > G.e0 ? 1 : 0) + (G.c1 > G.c0 ? 1 : 0) + (G.t1 > G.t0 ? 1 : 0) +
-         (plan->groups.size() == 1 ? rounds_launches(plan) : 1);
+         (plan->groups.size() == 1 ? rounds_launches(plan) + (plan->dual_tiles.empty() ? 0 : 1) : 1);
   return n;
 }
 
@@ -1413,6 +1548,9 @@ extern "C" int32_t vl_claims_plan_run(vl_claims_plan* C, void* workspace, size_t
   ce = cudaMemcpyAsync(dS, &C->S, sizeof(BtState), cudaMemcpyHostToDevice, st);  // status, pointers (the plan keeps the source)
   if (ce == cudaSuccess) ce = cudaMemsetAsync(ws + p->off_ctl, 0, p->off_acc + p->acc_bytes - p->off_ctl, st);
   if (ce == cudaSuccess) ce = launch_prologue(dp, 0, np, de, (int)p->eq_items.size(), st);
+  if (ce == cudaSuccess)
+    ce = launch_fold_dual(reinterpret_cast<const DualTile*>(ws + p->off_dual_tiles), (int)p->dual_tiles.size(), dp,
+                          wait_ns(p), st);
   if (ce == cudaSuccess) ce = launch_fold_tc(dc, (int)p->tc_tiles.size(), dp, wait_ns(p), st);
   if (ce == cudaSuccess) ce = launch_fold(dt, dl, (int)p->tiles.size(), dp, p->fold_smem, wait_ns(p), st);
   if (ce == cudaSuccess) ce = launch_batch_claims(dp, np, dS, st);

@@ -473,3 +473,83 @@ def test_host_operands_packed_in_one_buffer_are_staged_together():
         B.vl_plan_destroy(plan)
     ref = oracle.prove_matmul(jobs[0]["P"], jobs[0]["Q"], jobs[0]["tp"], jobs[0]["tq"], seed=jobs[0]["seed"])
     assert want[0] == ref.to_bytes()
+
+
+@pytest.mark.parametrize("d,k,n,fill", [(256, 384, 64, "random"), (128, 128, 8, "random"), (512, 1024, 96, "random"),
+                                        (256, 256, 40, "max"), (384, 128, 16, "min")])
+def test_dual_fold_of_a_matrix_folded_both_ways(d, k, n, fill):
+    """A stored matrix W that one product folds as row dots (X.W) and another
+    as column sums (dY.W^T), rows and columns multiples of 128: the dual
+    tensor-core tiles stream it once for both.  Proofs equal the oracle's,
+    and the same plan without dual tiles, byte for byte; the dual launch is
+    counted."""
+    rng = np.random.default_rng(d * 7 + k + n)
+    if fill == "random":
+        Wm = _rand(rng, (d, k))
+    else:
+        Wm = np.full((d, k), 32767 if fill == "max" else -32768, np.int16)
+    X, dY = _rand(rng, (n, d)), _rand(rng, (n, k))
+    jobs = [{"P": X, "Q": Wm, "tp": 0, "tq": 0, "seed": 71}, {"P": dY, "Q": Wm, "tp": 0, "tq": 1, "seed": 72},
+            {"P": X, "Q": X, "tp": 1, "tq": 0, "seed": 73}]  # X^T.X: two row dots of X, no pair
+    refs = [oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes() for j in jobs]
+    dj, keep = _dev_jobs(jobs)
+    launches = {}
+    for fd in (1, 0):
+        opts = B.vl_batch_opts()
+        opts.fold_dual = fd
+        plan = B.vl_plan_create(dj, opts)
+        try:
+            launches[fd] = B.vl_plan_launches(plan)
+            nb = B.vl_plan_workspace_bytes(plan)
+            ws = _ws(nb)
+            for _ in range(2):
+                out = (B.vl_proof * len(dj))()
+                B.vl_plan_run(plan, ws.data_ptr(), nb, out, B.VL_HOST)
+                assert [B.proof_bytes(p) for p in out] == refs, f"fold_dual {fd}"
+        finally:
+            B.vl_plan_destroy(plan)
+    assert launches[1] == launches[0] + 1  # the dual kernel
+
+
+def test_host_operands_separated_by_an_unmapped_page():
+    """Two pageable host operands one unmapped page apart (the end of one
+    mapping and the start of another): each is staged with its own copy,
+    never with one copy over the gap, and the proof equals the oracle's."""
+    import mmap
+    libc = ctypes.CDLL(None, use_errno=True)
+    libc.mmap.restype = ctypes.c_void_p
+    libc.mmap.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_long]
+    libc.munmap.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+    pg = mmap.PAGESIZE
+    m, k, n = 64, 128, 64
+    pbytes, qbytes = m * k * 2, k * n * 2
+    pp, qp = -(-pbytes // pg), -(-qbytes // pg)  # pages of each operand
+    total = (pp + 1 + qp) * pg
+    base = libc.mmap(None, total, mmap.PROT_READ | mmap.PROT_WRITE, mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS, -1, 0)
+    assert base not in (None, ctypes.c_void_p(-1).value)
+    try:
+        assert libc.munmap(base + pp * pg, pg) == 0  # the hole
+        p_addr = base + pp * pg - pbytes              # P ends where the hole begins
+        q_addr = base + (pp + 1) * pg                 # Q starts where it ends
+        P = np.ctypeslib.as_array((ctypes.c_int16 * (m * k)).from_address(p_addr)).reshape(m, k)
+        Q = np.ctypeslib.as_array((ctypes.c_int16 * (k * n)).from_address(q_addr)).reshape(k, n)
+        rng = np.random.default_rng(91)
+        P[:] = _rand(rng, (m, k))
+        Q[:] = _rand(rng, (k, n))
+        ref = oracle.prove_matmul(P.copy(), Q.copy(), 0, 0, seed=92).to_bytes()
+        hj = [B.job(P, Q, 0, 0, 92)]
+        plan = B.vl_plan_create(hj)
+        try:
+            nb = B.vl_plan_workspace_bytes(plan)
+            ws = _ws(nb)
+            for _ in range(2):
+                out = (B.vl_proof * 1)()
+                B.vl_plan_run(plan, ws.data_ptr(), nb, out, B.VL_HOST)
+                torch.cuda.synchronize()
+                assert B.proof_bytes(out[0]) == ref
+        finally:
+            B.vl_plan_destroy(plan)
+        del P, Q, hj
+    finally:
+        libc.munmap(base, pp * pg)
+        libc.munmap(base + (pp + 1) * pg, qp * pg)
