@@ -114,7 +114,26 @@ __device__ static void squeeze_dev(const uint32_t* Sw, uint32_t label, int count
     }
   }
   __syncthreads();
-  if (tid < count) x[tid] = to_mont_ni(reduce_512_ni(digest_le(dig[2 * tid]), digest_le(dig[2 * tid + 1])));
+  // challenge i = (lo + hi . 2^256) mod r in Montgomery form (lo = digest 2i,
+  // hi = digest 2i + 1) = lo . R + hi . R^2: REDC(lo . R^2) and REDC(hi . R^3)
+  // by two threads at once, then one addition
+  Fr part;
+  if (tid < 2 * count) part = mont_mul_ni(digest_le(dig[tid]), (tid & 1) ? fr_r3() : fr_r2());
+  __syncthreads();
+  if (tid < 2 * count) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) dig[tid][i] = part.v[i];
+  }
+  __syncthreads();
+  if (tid < count) {
+    Fr lo, hi;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      lo.v[i] = dig[2 * tid][i];
+      hi.v[i] = dig[2 * tid + 1][i];
+    }
+    x[tid] = fr_add(lo, hi);
+  }
   __syncthreads();
 }
 

@@ -84,16 +84,22 @@ __device__ __forceinline__ Fr round_transcript(uint32_t* S, const Fr* gsh, bool 
     d[i] = 0;
   }
   if (lane < 3) dev_squeeze_block(st, LBL_R, lane < 2 ? 0u : 1u, lane, d);
-  uint32_t d1[8];
-#pragma unroll
-  for (int i = 0; i < 8; i++) d1[i] = __shfl_sync(0xffffffffu, d[i], 1);
   __syncwarp();
   if (lane == 2) {
 #pragma unroll
     for (int i = 0; i < 8; i++) S[i] = d[i];
   }
+  // r = (lo + hi . 2^256) mod r, in Montgomery form (lo: lane 0's digest,
+  // hi: lane 1's) = lo . R + hi . R^2 mod r: lane 0 forms REDC(lo . R^2) and
+  // lane 1 REDC(hi . R^3) at once, one product on the serial chain instead of
+  // the reduction's and the conversion's two
+  Fr half = fr_zero();
+  if (lane < 2) half = mont_mul_ni(digest_le(d), lane == 0 ? fr_r2() : fr_r3());
+  Fr other;
+#pragma unroll
+  for (int i = 0; i < 8; i++) other.v[i] = __shfl_sync(0xffffffffu, half.v[i], 1);
   Fr r = fr_zero();
-  if (lane == 0) r = to_mont_ni(reduce_512_ni(digest_le(d), digest_le(d1)));
+  if (lane == 0) r = fr_add(half, other);
   __syncwarp();
   return r;
 }
