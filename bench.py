@@ -581,14 +581,22 @@ def update_main(args, rank, world, local, cpu):
         pass
     hbm_peak, hbm_note = (peaks["hbm_gbs"], "measured") if "hbm_gbs" in peaks else (6800.0, "fallback")
     hbm_gbs = 2 * entries / (fold_ms / 1e3) / 1e9
-    # DRAM bytes of one fold launch over the whole update workload, from an ncu
-    # capture of this kernel on it (profiles/fold_tc_kernel_7b_update.md:
-    # 172.4 MB read + 52.1 MB written)
-    traffic = 224.5e6 if not args.layers else None
-    roof = {"bound": "hbm", "kernel": "fold_tc_kernel", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
-            "frac": hbm_gbs / hbm_peak, "traffic": traffic,
-            "peak_note": f"{hbm_note} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-            "algorithmic_bytes_per_launch": 2 * entries}
+    # The LoRA factors reduce over the rank (at most 64 entries): the fold runs
+    # on CUDA cores (lin_short_kernel), one thread per line: eight 32 x 32 ->
+    # 64-bit multiply-adds per entry and one REDC (64 more) per line.  Bound:
+    # those multiply-adds at the derived ALU peak; the 2 B per entry of HBM
+    # traffic would take a fifth of that time.
+    lines = sum(len(st["mats"]) * max(st["mats"][0].shape) for st in stmts)
+    madw = 8 * entries + 64 * lines
+    alu_peak = SMS * MADWIDE_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    roof = {"bound": "alu", "kernel": "lin_short_kernel", "achieved": madw / (fold_ms / 1e3) / 1e12,
+            "peak": alu_peak / 1e12, "unit": "T mad.wide/s", "frac": madw / (fold_ms / 1e3) / alu_peak,
+            "traffic": None,
+            "peak_note": f"derived: {SMS} SMs x {MADWIDE_PER_SM_CLK} IMAD.WIDE/clk x {SM_MAX_MHZ} MHz",
+            "algorithmic_madwide_per_launch": madw,
+            "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
+                    "algorithmic_bytes_per_launch": 2 * entries,
+                    "peak_note": f"{hbm_note} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}}
     # End to end: pinned host operands in (staged by the library), host proofs out.
     host = [[torch.from_numpy(m).pin_memory() for m in st["mats"]] for st in stmts]
     hjobs = [B.lin_job([B.mat(t) for t in h], list(st["coeffs"]), st["seed"]) for h, st in zip(host, stmts)]

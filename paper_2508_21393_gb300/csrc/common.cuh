@@ -274,7 +274,21 @@ struct LinDev {
   unsigned long long* acc;         // several segments: nmats x lines x 8 column sums
   Fr* part;                        // nmats x nblk inner sums (Montgomery)
   ProofScratch* scr;               // status (the fold's DevProof points here)
+  Fr* e2;                          // short reductions: the reduced side's eq table, double-Montgomery
 };
+// Linear zkMat, short reductions (at most LIN_SHORT_MAX entries): the fold on
+// CUDA cores, one thread per line (a tensor-core stage would be mostly
+// padding).  One item per block of LIN_SHORT_LINES lines of one matrix.
+static constexpr int LIN_SHORT_MAX = 128;
+static constexpr int LIN_SHORT_LINES = 256;
+struct LinShort {
+  const int16_t* base;  // stored matrix (device)
+  int64_t ld;           // elements between stored rows
+  int32_t proof, q;     // proof, matrix of the proof
+  int32_t w0, nw;       // lines [w0, w0 + nw): stored rows (ROWDOT) or columns (COLSUM)
+  int32_t mode, red;    // MODE_ROWDOT / MODE_COLSUM, reduced entries per line
+};
+static_assert(sizeof(LinShort) == 40, "short item");
 // Lookup argument (kernels_lookup.cu): one LkDev per proof, in the workspace.
 static constexpr int LK_MAX_L = VL_LOOKUP_MAX_LOG_D;
 struct LkDev {
@@ -359,6 +373,8 @@ void ws_claim(const void* owner, const void* ws);
 void ws_release(const void* owner);
 // Batches: one LinDev per proof; chunks of the reduced side's eq table as
 // EqItem {proof, side (unused), i0, i1}.
+// Short-reduction folds (kernels_linear.cu): f_q of every item's lines.
+cudaError_t launch_linear_short(const LinDev* Ls, const LinShort* items, int nitems, cudaStream_t st);
 cudaError_t launch_linear_start(LinDev* Ls, int nproofs, const EqItem* items, int nitems, cudaStream_t st);
 cudaError_t launch_linear_finish(LinDev* Ls, int nproofs, int max_nblk, int max_nmats, vl_lin_proof* out,
                                  cudaStream_t st);

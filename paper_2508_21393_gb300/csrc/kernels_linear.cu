@@ -8,7 +8,9 @@
 //           offset correction (closed form, in a warp of its own); then, in
 //           chunks, the reduced side's eq table as the tensor-core fold's
 //           fp16 byte table;
-//   (the tensor-core fold writes f_q = the reduced vector of every matrix)
+//   (the tensor-core fold writes f_q = the reduced vector of every matrix;
+//   reductions of at most LIN_SHORT_MAX entries fold on CUDA cores instead,
+//   one thread per line, from the table's limbs)
 //   finish: the lines side's eq table is never formed: with
 //           E[w] = hi[w >> s] . lo[w mod 2^s],
 //             e_q = sum_j hi[j] . (sum_l f_q[j 2^s + l] . lo[l]),
@@ -90,7 +92,93 @@ __global__ void __launch_bounds__(LIN_THREADS) lin_eq_kernel(const LinDev* Ls, c
   for (int i = it.i0 + threadIdx.x; i < it.i1; i += blockDim.x) {
     const Fr e = i < size ? mont_mul_ni(hi[i >> s], lo[i & mask]) : fr_zero();  // eq . R^2
     store_w8(L->w8, i, e);
+    if (L->e2 && i < size) L->e2[i] = e;  // short reductions fold on CUDA cores with the limbs
   }
+}
+
+// Short reductions (red <= LIN_SHORT_MAX): thread w of the block folds line
+// w0 + w of one matrix.  With p = x + 2^15 in [0, 2^16) and e = E R^2,
+// sum_j e_j p_j is an exact integer, kept as eight 64-bit column sums of the
+// limb products (each below 2^48, at most 128 of them); one REDC gives
+// (sum_j E_j p_j) R, and subtracting 2^15 (sum_j E_j) R (the offset
+// correction) leaves f_q[line] = sum_j E_j x_j in Montgomery form: the value
+// the tensor-core fold writes for the same line.
+__global__ void __launch_bounds__(LIN_SHORT_LINES) lin_short_kernel(const LinDev* Ls, const LinShort* items) {
+  __shared__ __align__(16) Fr e2s[LIN_SHORT_MAX];
+  const LinShort it = items[blockIdx.x];
+  const LinDev* L = Ls + it.proof;
+  for (int j = threadIdx.x; j < it.red; j += blockDim.x) e2s[j] = L->e2[j];
+  __syncthreads();
+  const int w = threadIdx.x;
+  if (w >= it.nw) return;
+  const int64_t line = it.w0 + w;
+  unsigned long long acc[8];
+#pragma unroll
+  for (int l = 0; l < 8; l++) acc[l] = 0;
+  // acc[l] += e_j[l] . p_j as one 32 x 32 -> 64-bit multiply-add per limb
+  // (the weights as two 16-byte shared-memory loads)
+  auto add = [&](int j, int16_t x) {
+    const uint32_t p = (uint32_t)((int32_t)x + 32768);
+    const uint4 e0 = reinterpret_cast<const uint4*>(&e2s[j])[0];
+    const uint4 e1 = reinterpret_cast<const uint4*>(&e2s[j])[1];
+    const uint32_t ev[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+#pragma unroll
+    for (int l = 0; l < 8; l++) asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[l]) : "r"(ev[l]), "r"(p));
+  };
+  // Loads are issued in groups before their entries are used, so that each
+  // thread has several in flight.
+  if (it.mode == MODE_ROWDOT) {
+    const int16_t* row = it.base + line * it.ld;
+    int j = 0;
+    if ((reinterpret_cast<uintptr_t>(row) & 15) == 0) {  // eight entries per 16-byte load
+      for (; j + 32 <= it.red; j += 32) {
+        uint4 v[4];
+#pragma unroll
+        for (int b = 0; b < 4; b++) v[b] = __ldg(reinterpret_cast<const uint4*>(row + j) + b);
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+          const uint32_t wv[4] = {v[b].x, v[b].y, v[b].z, v[b].w};
+#pragma unroll
+          for (int i = 0; i < 4; i++) {
+            add(j + 8 * b + 2 * i, (int16_t)(wv[i] & 0xffffu));
+            add(j + 8 * b + 2 * i + 1, (int16_t)(wv[i] >> 16));
+          }
+        }
+      }
+      for (; j + 8 <= it.red; j += 8) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(row + j));
+        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          add(j + 2 * i, (int16_t)(wv[i] & 0xffffu));
+          add(j + 2 * i + 1, (int16_t)(wv[i] >> 16));
+        }
+      }
+    }
+    for (; j + 8 <= it.red; j += 8) {
+      int16_t x[8];
+#pragma unroll
+      for (int i = 0; i < 8; i++) x[i] = __ldg(row + j + i);
+#pragma unroll
+      for (int i = 0; i < 8; i++) add(j + i, x[i]);
+    }
+    for (; j < it.red; j++) add(j, __ldg(row + j));
+  } else {
+    const int16_t* col = it.base + line;  // a warp reads consecutive columns of each row
+    int j = 0;
+    for (; j + 8 <= it.red; j += 8) {
+      int16_t x[8];
+#pragma unroll
+      for (int i = 0; i < 8; i++) x[i] = __ldg(col + (int64_t)(j + i) * it.ld);
+#pragma unroll
+      for (int i = 0; i < 8; i++) add(j + i, x[i]);
+    }
+    for (; j < it.red; j++) add(j, __ldg(col + (int64_t)j * it.ld));
+  }
+  U64x8 a;
+#pragma unroll
+  for (int l = 0; l < 8; l++) a.v[l] = acc[l];
+  L->f[(size_t)it.q * L->lines + line] = fr_sub(redc_columns_ni(a), L->corr);
 }
 
 // Warp w of block (b, q, proof) sums inner block j = 8 b + w of matrix q:
@@ -166,6 +254,11 @@ __global__ void __launch_bounds__(LIN_THREADS) lin_finish_kernel(const LinDev* L
 cudaError_t launch_linear_start(LinDev* Ls, int nproofs, const EqItem* items, int nitems, cudaStream_t st) {
   lin_start_kernel<<<nproofs, LIN_THREADS, 0, st>>>(Ls);
   if (nitems > 0) lin_eq_kernel<<<nitems, LIN_THREADS, 0, st>>>(Ls, items);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_linear_short(const LinDev* Ls, const LinShort* items, int nitems, cudaStream_t st) {
+  if (nitems > 0) lin_short_kernel<<<nitems, LIN_SHORT_LINES, 0, st>>>(Ls, items);
   return cudaGetLastError();
 }
 

@@ -9,7 +9,8 @@
 // tensor-core fold of every matrix over its shorter logical dimension, the
 // partial dot products against the other dimension's eq table, and the
 // finish kernel (per proof: evaluations, absorb, proof); then one copy of the
-// proofs to the host.
+// proofs to the host.  Reductions of at most LIN_SHORT_MAX entries (the LoRA
+// factors' rank dimension) fold on CUDA cores instead of the tensor cores.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -49,20 +50,22 @@ constexpr int LIN_MAX_JOBS = 65535;
 struct LinShape {
   int rows = 0, cols = 0, d0 = 0, d1 = 0, q = 0;
   bool red_rows = true;
-  int red = 0, lines = 0, seg = 0, nsplit = 0, nblk = 0, ntiles = 0;
+  bool shortf = false;  // reduction of at most LIN_SHORT_MAX entries: CUDA-core fold
+  int red = 0, lines = 0, seg = 0, nsplit = 0, nblk = 0, ntiles = 0, nshort = 0;
 };
 
 // Workspace offsets of one proof's buffers.
 struct LinBufs {
-  size_t fac = 0, w8 = 0, f = 0, part = 0;
+  size_t fac = 0, w8 = 0, f = 0, part = 0, e2 = 0;
 };
 
 struct LinLayout {
-  int np = 0, nmats = 0, ntiles = 0, max_nblk = 1, max_q = 1;
+  int np = 0, nmats = 0, ntiles = 0, nshort = 0, max_nblk = 1, max_q = 1;
   std::vector<LinShape> shape;
   std::vector<LinBufs> buf;
   std::vector<EqItem> items;
-  size_t off_L = 0, off_scr = 0, off_dp = 0, off_tiles = 0, off_maps = 0, off_items = 0, off_out = 0, total = 0;
+  size_t off_L = 0, off_scr = 0, off_dp = 0, off_tiles = 0, off_short = 0, off_maps = 0, off_items = 0, off_out = 0,
+         total = 0;
   std::vector<size_t> off_stage;  // per operand (flattened job by job); unused unless staged
   std::vector<int64_t> stage_ld;
   std::vector<char> staged;
@@ -108,6 +111,14 @@ int lin_shape(const vl_lin_job& J, LinShape* S) {
   S->seg = ((S->red + split - 1) / split + TC_KS - 1) / TC_KS * TC_KS;
   S->nsplit = (S->red + S->seg - 1) / S->seg;
   S->ntiles = J.nmats * ntl * S->nsplit;
+  // A short reduction would fill few entries of a tensor-core stage: fold it
+  // on CUDA cores, one thread per line.
+  S->shortf = S->red <= LIN_SHORT_MAX;
+  if (S->shortf) {
+    S->nsplit = 1;
+    S->ntiles = 0;
+    S->nshort = J.nmats * ((S->lines + LIN_SHORT_LINES - 1) / LIN_SHORT_LINES);
+  }
   // inner sums of the lines side: blocks of 2^s lines, s = ceil(d / 2)
   const int dl = S->red_rows ? S->d1 : S->d0, sl = (dl + 1) >> 1;
   S->nblk = (S->lines + (1 << sl) - 1) >> sl;
@@ -125,6 +136,7 @@ int lin_layout(const vl_lin_job* jobs, int32_t njobs, LinLayout* L) {
     const LinShape& S = L->shape[i];
     L->nmats += S.q;
     L->ntiles += S.ntiles;
+    L->nshort += S.nshort;
     L->max_nblk = std::max(L->max_nblk, S.nblk);
     L->max_q = std::max(L->max_q, S.q);
     // chunks of the reduced side's eq table (padded to whole stages)
@@ -141,6 +153,7 @@ int lin_layout(const vl_lin_job* jobs, int32_t njobs, LinLayout* L) {
   L->off_scr = take(sizeof(ProofScratch) * njobs);
   L->off_dp = take(sizeof(DevProof) * njobs);
   L->off_tiles = take(sizeof(TcTile) * (size_t)L->ntiles);
+  L->off_short = take(sizeof(LinShort) * (size_t)L->nshort);
   L->off_maps = take(sizeof(CUtensorMap) * (size_t)L->nmats);
   L->off_items = take(sizeof(EqItem) * L->items.size());
   L->off_out = take(sizeof(vl_lin_proof) * njobs);
@@ -152,6 +165,7 @@ int lin_layout(const vl_lin_job* jobs, int32_t njobs, LinLayout* L) {
     // f (one segment per tile) or the column-sum accumulators (several)
     b.f = take((S.nsplit == 1 ? sizeof(Fr) : 8 * sizeof(unsigned long long)) * (size_t)S.q * S.lines);
     b.part = take(sizeof(Fr) * (size_t)S.q * S.nblk);
+    b.e2 = S.shortf ? take(sizeof(Fr) * (size_t)S.red) : 0;
   }
   L->off_stage.assign(L->nmats, 0);
   L->stage_ld.assign(L->nmats, 0);
@@ -187,6 +201,7 @@ struct vl_lin_plan {
   std::vector<DevProof> dps;
   std::vector<CUtensorMap> maps;
   std::vector<TcTile> tiles;
+  std::vector<LinShort> shorts;
   uint8_t* bound_ws = nullptr;
   int device = -1;
   cudaEvent_t ev[4] = {};
@@ -216,6 +231,7 @@ int lin_bind(vl_lin_plan* P, uint8_t* ws, cudaStream_t st) {
     L.f = S.nsplit == 1 ? reinterpret_cast<Fr*>(ws + b.f) : nullptr;
     L.acc = S.nsplit == 1 ? nullptr : reinterpret_cast<unsigned long long*>(ws + b.f);
     L.part = reinterpret_cast<Fr*>(ws + b.part);
+    L.e2 = S.shortf ? reinterpret_cast<Fr*>(ws + b.e2) : nullptr;
     L.scr = reinterpret_cast<ProofScratch*>(ws + lay.off_scr) + i;
     std::memset(&P->dps[i], 0, sizeof(DevProof));
     P->dps[i].scr = L.scr;  // the fold reports a timeout through this proof's status
@@ -223,6 +239,8 @@ int lin_bind(vl_lin_plan* P, uint8_t* ws, cudaStream_t st) {
   P->maps.assign(lay.nmats, CUtensorMap{});
   P->tiles.clear();
   P->tiles.reserve(lay.ntiles);
+  P->shorts.clear();
+  P->shorts.reserve(lay.nshort);
   int g = 0;
   for (int i = 0; i < np; i++) {
     const LinShape& S = lay.shape[i];
@@ -234,6 +252,21 @@ int lin_bind(vl_lin_plan* P, uint8_t* ws, cudaStream_t st) {
       const int64_t ld = lay.staged[g] ? lay.stage_ld[g] : M.ld;
       // Column sums reduce over stored rows, row dots over stored columns.
       const int32_t mode = (S.red_rows != (M.trans != 0)) ? MODE_COLSUM : MODE_ROWDOT;
+      if (S.shortf) {
+        for (int w0 = 0; w0 < S.lines; w0 += LIN_SHORT_LINES) {
+          LinShort it{};
+          it.base = static_cast<const int16_t*>(base);
+          it.ld = ld;
+          it.proof = i;
+          it.q = q;
+          it.w0 = w0;
+          it.nw = std::min(LIN_SHORT_LINES, S.lines - w0);
+          it.mode = mode;
+          it.red = S.red;
+          P->shorts.push_back(it);
+        }
+        continue;
+      }
       if (!encode_tc_operand(base, M.rows, M.cols, ld, mode, &P->maps[g])) {
         char msg[128];
         snprintf(msg, sizeof(msg), "linear proofs: tensor map of job %d matrix %d could not be encoded", i, q);
@@ -269,6 +302,7 @@ int lin_bind(vl_lin_plan* P, uint8_t* ws, cudaStream_t st) {
   up(lay.off_L, P->Ls.data(), sizeof(LinDev) * np);
   up(lay.off_dp, P->dps.data(), sizeof(DevProof) * np);
   up(lay.off_tiles, P->tiles.data(), sizeof(TcTile) * P->tiles.size());
+  up(lay.off_short, P->shorts.data(), sizeof(LinShort) * P->shorts.size());
   up(lay.off_maps, P->maps.data(), sizeof(CUtensorMap) * P->maps.size());
   up(lay.off_items, lay.items.data(), sizeof(EqItem) * lay.items.size());
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
@@ -375,9 +409,11 @@ extern "C" int32_t vl_lin_plan_run(vl_lin_plan* P, void* workspace, size_t works
     ce = launch_linear_start(dL, lay.np, reinterpret_cast<const EqItem*>(ws + lay.off_items), (int)lay.items.size(),
                              st);
   if (ce == cudaSuccess) ce = cudaEventRecord(ev[1], st);
-  if (ce == cudaSuccess)
+  if (ce == cudaSuccess && lay.ntiles > 0)
     ce = launch_fold_tc(reinterpret_cast<const TcTile*>(ws + lay.off_tiles), lay.ntiles,
                         reinterpret_cast<const DevProof*>(ws + lay.off_dp), FOLD_WAIT_NS, st);
+  if (ce == cudaSuccess)
+    ce = launch_linear_short(dL, reinterpret_cast<const LinShort*>(ws + lay.off_short), lay.nshort, st);
   if (ce == cudaSuccess) ce = cudaEventRecord(ev[2], st);
   if (ce == cudaSuccess) ce = launch_linear_finish(dL, lay.np, lay.max_nblk, lay.max_q, dout, st);
   if (ce == cudaSuccess) ce = cudaEventRecord(ev[3], st);

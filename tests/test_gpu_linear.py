@@ -3,8 +3,9 @@ parameter update of Eq. eq:grad_update_ab): every proof from the CUDA path
 equals the oracle's proof byte for byte, through the C ABI.
 
 Shapes cover both fold orientations (reduction over rows or over columns,
-whichever is shorter), ragged tails of the 128-line tiles and 128-entry
-stages, several reduction segments per line (accumulator path), transposed,
+whichever is shorter), both fold engines (tensor cores; CUDA cores for
+reductions of at most 128 entries), ragged tails of the 128-line tiles and
+128-entry stages, several reduction segments per line (accumulator path), transposed,
 host, unaligned and odd-pitch operands, extreme entries, batches of mixed
 shapes, and the full-size parameter updates of a 7B LoRA step.
 """
@@ -96,6 +97,9 @@ SHAPES = [
     (1500, 1600, 2, [0, 1]),        # two reduction segments per line: accumulator path
     (2100, 2048, 2, [1, 0]),        # accumulator path, reduction over columns
     (200, 40000, 1, [0]),           # 313 line tiles
+    (128, 3000, 3, [0, 1, 0]),      # the longest reduction folded on CUDA cores (rows)
+    (3000, 127, 2, [1, 0]),         # CUDA-core fold over an odd number of columns
+    (600, 72, 2, [0, 1]),           # CUDA-core fold: 16-byte loads of aligned rows, and columns
 ]
 
 
@@ -124,6 +128,17 @@ def test_linear_extreme_entries():
     mats = [np.full((rows, cols), -(1 << 15), np.int16), np.full((rows, cols), (1 << 15) - 1, np.int16),
             np.zeros((rows, cols), np.int16)]
     s = Stmt(mats, [1, 1, 1], seed=3)
+    _, out = gpu_prove([s])
+    assert B.lin_proof_bytes(out[0]) == s.oracle_bytes()
+
+
+@pytest.mark.parametrize("rows,cols", [(100, 700), (700, 128)])
+def test_linear_extreme_entries_short_reduction(rows, cols):
+    """Reductions of at most 128 entries (CUDA-core fold): all-minimum and
+    all-maximum entries, where the limb column sums are largest."""
+    mats = [np.full((rows, cols), -(1 << 15), np.int16), np.full((rows, cols), (1 << 15) - 1, np.int16),
+            np.zeros((rows, cols), np.int16)]
+    s = Stmt(mats, [1, 1, 1], seed=4, trans=[0, 1, 0])
     _, out = gpu_prove([s])
     assert B.lin_proof_bytes(out[0]) == s.oracle_bytes()
 
