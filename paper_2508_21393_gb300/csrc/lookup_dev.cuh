@@ -47,7 +47,8 @@ __device__ __forceinline__ void lk_pair_a(LkDev* L, int t, int k, int h, const F
     // (A S')(X) = (1-X)^2 + X^2 + X(1-X) w with w = a1 s0 + a0 s1:
     // (A S')(0) = 1, (A S')(2) = 5 - 2w, (A S')(3) = 13 - 6w.  Sum f and f w
     // here; lk_mode0_sums forms the three sums.
-    const Fr w = fr_add(mont_mul(a1, s0), mont_mul(a0, s1));
+    // a0 s0 = a1 s1 = 1, so w = (a0 + a1)(s0 + s1) - 2: one product
+    const Fr w = fr_sub(mont_mul(fr_add(a0, a1), fr_add(s0, s1)), fr_dbl(fr_r1()));
     acc[0] = fr_add(acc[0], f);
     acc[1] = fr_add(acc[1], mont_mul(f, w));
   } else {
@@ -107,7 +108,8 @@ __device__ __forceinline__ void lk_pair_b(LkDev* L, int t, int tj, int k, int h,
     b0 = L->WB[k], b1 = L->WB[k + h];
     u0 = L->WT[k], u1 = L->WT[k + h];
     m0 = L->WM[k], m1 = L->WM[k + h];
-    const Fr w = fr_add(mont_mul(b1, u0), mont_mul(b0, u1));
+    // b0 u0 = b1 u1 = 1, so w' = (b0 + b1)(u0 + u1) - 2: one product
+    const Fr w = fr_sub(mont_mul(fr_add(b0, b1), fr_add(u0, u1)), fr_dbl(fr_r1()));
     accb[0] = fr_add(accb[0], f);
     accb[1] = fr_add(accb[1], mont_mul(f, w));
   } else {
