@@ -89,7 +89,7 @@ def parse():
                     help="phase launches: 0 tensor-core fold where TMA can address the operand, 1 CUDA cores only")
     ap.add_argument("--groups", type=int, default=0,
                     help="phase launches: proof groups pipelined over three streams (0: library default)")
-    ap.add_argument("--rounds-variant", type=int, default=0, choices=[0, 2, 3, 4, 7, 8],
+    ap.add_argument("--rounds-variant", type=int, default=0, choices=[0, 2, 3, 4, 5, 6, 7, 8],
                     help="rounds kernel register budget (CTAs per SM), or 8: batched rounds; 0 = library default")
     ap.add_argument("--fold-dual", action="store_true",
                     help="fold a matrix used as row dots and as column sums in one pass (dual tiles)")

@@ -148,8 +148,8 @@ typedef struct vl_batch_opts {
   int32_t wait_limit_us; /* bound on any single device-side wait, in us (0: 2 s);
                             a wait that runs out sets the proof's status to
                             VL_ETIMEOUT and its CTA returns                  */
-  int32_t rounds_variant; /* rounds kernel: CTAs per SM, 7, 4, 3 or 2 (0: 7);
-                            7 and 4 set the register budget, 3 and 2 also
+  int32_t rounds_variant; /* rounds kernel: CTAs per SM, 7, 6, 5, 4, 3 or 2
+                            (0: 7); 7 to 4 set the register budget, 3 and 2 also
                             cap residency (fewer proofs share an SM); 8:
                             batched rounds, one launch per round for the
                             vector work of all proofs and one for their

@@ -132,7 +132,7 @@ extern "C" int32_t vl_autotune(const vl_job* jobs, int32_t njobs, const vl_batch
       {&vl_batch_opts::fold_engine, {0, 1}},
       {&vl_batch_opts::fold_dual, {0, 1}},
       {&vl_batch_opts::tc_seg, {0, 8192, 4096, 2048}},
-      {&vl_batch_opts::rounds_variant, {7, 4, 3, 2, 8}},
+      {&vl_batch_opts::rounds_variant, {7, 6, 5, 4, 3, 2, 8}},
       {&vl_batch_opts::rounds_threads, {0, 192, 256}},
       // The persistent single launch (persistent = 1) is not a candidate: it
       // runs the CUDA-core fold (its fold tiles are pulled from a work queue

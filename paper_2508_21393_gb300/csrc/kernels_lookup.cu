@@ -362,7 +362,10 @@ __device__ void lk_finish(LkDev* L, vl_lookup_proof* out) {
 // One block per proof: its rounds from L->tail on (at most 2^LK_TAIL_LOG
 // pairs each), each a pass over the pairs, a block reduction and the
 // transcript step in this block, then the final evaluations and the proof.
-__global__ void __launch_bounds__(LK_TAIL_THREADS, 4) lk_tail_kernel(LkDev* Ls, vl_lookup_proof* outs) {
+#ifndef LK_TAIL_MINB
+#define LK_TAIL_MINB 4  // resident tail CTAs per SM the register budget allows
+#endif
+__global__ void __launch_bounds__(LK_TAIL_THREADS, LK_TAIL_MINB) lk_tail_kernel(LkDev* Ls, vl_lookup_proof* outs) {
   __shared__ Fr red[6 * (LK_TAIL_THREADS / 32)];
   __shared__ uint32_t Sw[8], Sn[8];
   __shared__ uint32_t dig[3][8];

@@ -13,8 +13,8 @@ __global__ void __launch_bounds__(THREADS, MINB) rounds_kernel(const DevProof* _
   rounds_block(P, out + P.job, rnd_smem);
 }
 
-// variant: CTAs per SM.  7 and 4 set the register allocation (7: one wave of
-// 1064 proofs, tighter registers; 4: more registers per thread).  3 and 2
+// variant: CTAs per SM.  7, 6, 5 and 4 set the register allocation (7: one
+// wave of 1064 proofs, tighter registers; 4: more registers per thread).  3 and 2
 // use the variant-4 code and cap residency by reserving shared memory, for
 // fewer co-resident proofs competing for issue slots.  threads: 128, 192 or
 // 256 per proof (more threads shorten the vector passes of large proofs; the
@@ -38,6 +38,10 @@ cudaError_t launch_rounds(const DevProof* proofs, int nproofs, vl_proof* out, in
     rounds_kernel<4, 128><<<nproofs, 128, smem, st>>>(proofs, out);
   } else if (variant == 4) {
     rounds_kernel<4, 128><<<nproofs, 128, RND_SMEM, st>>>(proofs, out);
+  } else if (variant == 5) {
+    rounds_kernel<5, 128><<<nproofs, 128, RND_SMEM, st>>>(proofs, out);
+  } else if (variant == 6) {
+    rounds_kernel<6, 128><<<nproofs, 128, RND_SMEM, st>>>(proofs, out);
   } else {
     rounds_kernel<7, 128><<<nproofs, 128, RND_SMEM, st>>>(proofs, out);
   }

@@ -284,7 +284,8 @@ def test_launch_modes_and_fold_engines_agree():
     dj, keep = _dev_jobs(jobs)
     refs = [oracle.prove_matmul(j["P"], j["Q"], j["tp"], j["tq"], seed=j["seed"]).to_bytes() for j in jobs]
     for mode, engine, rv, rt in ((1, 0, 0, 0), (2, 0, 0, 0), (2, 1, 0, 0), (0, 0, 0, 0), (2, 0, 4, 192),
-                                 (2, 0, 3, 256), (2, 0, 2, 0), (2, 0, 4, 0), (2, 0, 8, 0), (2, 1, 8, 0)):
+                                 (2, 0, 3, 256), (2, 0, 2, 0), (2, 0, 4, 0), (2, 0, 5, 0), (2, 0, 6, 0),
+                                 (2, 0, 8, 0), (2, 1, 8, 0)):
         opts = B.vl_batch_opts()
         opts.persistent = mode
         opts.fold_engine = engine
