@@ -143,6 +143,17 @@ def test_linear_extreme_entries_short_reduction(rows, cols):
     assert B.lin_proof_bytes(out[0]) == s.oracle_bytes()
 
 
+@pytest.mark.parametrize("rows,cols,trans", [(1 << 16, 128, [0, 1, 0]), (128, 1 << 16, [1, 0, 0])])
+def test_linear_short_reduction_at_max_lines(rows, cols, trans):
+    """The CUDA-core fold at the header's limits: 2^16 lines (VL_MAX_REDUCE)
+    with the longest reduction it takes (128 entries), both orientations."""
+    rng = np.random.default_rng(rows + 3 * cols)
+    mats = [_rand(rng, (rows, cols)) for _ in range(3)]
+    s = Stmt(mats, [5, -2, 9], seed=rows ^ cols, trans=trans)
+    _, out = gpu_prove([s])
+    assert B.lin_proof_bytes(out[0]) == s.oracle_bytes()
+
+
 def test_linear_batch_mixed_shapes_equals_single_proofs():
     rng = np.random.default_rng(12)
     stmts = []
