@@ -208,12 +208,31 @@ static __device__ void rounds_block(const DevProof& P, vl_proof* pf, uint8_t* sm
       // Fold with r_i and evaluate round i + 1 (pairs j, j + h/2) in one pass.
       const int hh = h >> 1;
       Fr gn[3] = {fr_zero(), fr_zero(), fr_zero()};
-      for (int j = tid; j < hh; j += nthr) {
-        const Fr a0 = fold1(fA[j], fA[j + h], r), a1 = fold1(fA[j + hh], fA[j + hh + h], r);
-        const Fr b0 = fold1(fB[j], fB[j + h], r), b1 = fold1(fB[j + hh], fB[j + hh + h], r);
-        fA[j] = a0; fA[j + hh] = a1;
-        fB[j] = b0; fB[j + hh] = b1;
-        accum_g(gn, a0, a1, b0, b1);
+      if (4 * hh <= nthr) {
+        // Few pairs (the last rounds, latency-bound): four lanes of one warp
+        // per pair, one fold each, then three of them one term each (two
+        // products on the chain instead of seven).
+        const int j = tid >> 2, q = tid & 3;
+        if (j < hh) {
+          Fr* f = q < 2 ? fA : fB;
+          const int at = j + (q & 1) * hh;
+          f[at] = fold1(f[at], f[at + h], r);
+        }
+        __syncwarp();
+        if (j < hh && q < 3) {
+          const Fr a0 = fA[j], a1 = fA[j + hh], b0 = fB[j], b1 = fB[j + hh];
+          if (q == 0) gn[0] = mont_mul_ni(a0, b0);
+          else if (q == 1) gn[1] = mont_mul_ni(a1, b1);
+          else gn[2] = mont_mul_ni(fr_sub(fr_dbl(a1), a0), fr_sub(fr_dbl(b1), b0));
+        }
+      } else {
+        for (int j = tid; j < hh; j += nthr) {
+          const Fr a0 = fold1(fA[j], fA[j + h], r), a1 = fold1(fA[j + hh], fA[j + hh + h], r);
+          const Fr b0 = fold1(fB[j], fB[j + h], r), b1 = fold1(fB[j + hh], fB[j + hh + h], r);
+          fA[j] = a0; fA[j + hh] = a1;
+          fB[j] = b0; fB[j + hh] = b1;
+          accum_g(gn, a0, a1, b0, b1);
+        }
       }
       block_sum_canonical<3>(gn, gsh, red);
     } else if (tid == 0) {
