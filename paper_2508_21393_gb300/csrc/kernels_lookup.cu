@@ -27,6 +27,9 @@
 // partial sums of g(0), g(2), g(3)) and a transcript step per proof; finish.
 // A never exists as a vector: its entries are gathered from B by value
 // (A_k = B_{S_k - t0}), and S' from T'.
+#ifndef LK_TAIL_MUL_INLINE
+#define LK_MUL mont_mul_ni  // the tail and setup kernels: one out-of-line product (instruction cache)
+#endif
 #include "lookup_dev.cuh"
 
 namespace vl {
@@ -196,69 +199,112 @@ __global__ void __launch_bounds__(LK_THREADS) lk_table_kernel(LkDev* Ls, const L
   }
 }
 
-// g(r) for the cubic through (0, g0) .. (3, g3) (Lagrange), Montgomery.
-__device__ Fr lk_cubic(const Fr (&g)[4], const Fr& r, const Fr& inv2, const Fr& inv6) {
-  const Fr one = fr_r1(), two = fr_add(one, one), three = fr_add(two, one);
-  const Fr r1 = fr_sub(r, one), r2 = fr_sub(r, two), r3 = fr_sub(r, three);
-  const Fr p12 = mont_mul_ni(r1, r2), p23 = mont_mul_ni(r2, r3), p01 = mont_mul_ni(r, r1);
-  const Fr l0 = fr_neg(mont_mul_ni(mont_mul_ni(p12, r3), inv6));
-  const Fr l1 = mont_mul_ni(mont_mul_ni(r, p23), inv2);
-  const Fr l2 = fr_neg(mont_mul_ni(mont_mul_ni(p01, r3), inv2));
-  const Fr l3 = mont_mul_ni(mont_mul_ni(p01, r2), inv6);
-  Fr s = mont_mul_ni(g[0], l0);
-  s = fr_add(s, mont_mul_ni(g[1], l1));
-  s = fr_add(s, mont_mul_ni(g[2], l2));
-  return fr_add(s, mont_mul_ni(g[3], l3));
-}
-
-// The round polynomial of round t from the summed partials (thread 0):
-// g(X) = alpha c_t eqf(u_t, X) T_X + A_X + table side, g(1) = claim - g(0);
-// the values go into the proof and are absorbed ('g': g0, g2, g3) into Sw.
+// The round polynomial of round t from the summed partials, by warp 0 (the
+// sums valid in all its lanes): g(X) = alpha c_t eqf(u_t, X) T_X + A_X +
+// table side for X = 0, 2, 3 by lanes 0..2 at once (the scalars they share
+// formed in each), g(1) = claim - g(0); lanes 0..3 convert the four values
+// for the proof; lane 0 absorbs ('g': g0, g2, g3) into Sw.  gsh[0..3]: the
+// values (Montgomery), for lk_step_r.
 __device__ void lk_step_g(LkDev* L, int t, const Fr (&acc)[6], const Fr (&accb)[6], bool jr, vl_lookup_proof* out,
-                          Fr (&g)[4], uint32_t (&Sw)[8]) {
-  const Fr alpha = L->alpha, a2 = mont_mul_ni(alpha, alpha);
+                          Fr* gsh, uint32_t* Sw) {
+  const int lane = threadIdx.x & 31, q = lane < 3 ? lane : 0;
   // eqf(u_t, X) for X = 0, 2, 3: eqf(u, X) = (1 - u) + X (2u - 1)
   const Fr ut = L->u[t - 1], one = fr_r1();
   const Fr e0 = fr_sub(one, ut), d = fr_sub(fr_add(ut, ut), one);
-  const Fr e2 = fr_add(e0, fr_add(d, d)), e3 = fr_add(e2, d);
-  Fr tab[3];
-  if (jr) {  // (N/D) (alpha^2 c'_t eqf(u_t, X) U_X - V_X)
-    const Fr ac2 = mont_mul_ni(a2, L->ctj);
-    const Fr ex[3] = {e0, e2, e3};
-    for (int i = 0; i < 3; i++)
-      tab[i] = mont_mul_ni(L->c_nd, fr_sub(mont_mul_ni(mont_mul_ni(ac2, ex[i]), accb[i]), accb[3 + i]));
-  } else {
-    L->half_t = mont_mul_ni(L->half_t, L->inv2);
-    const Fr c = mont_mul_ni(L->half_t, L->Cb);
-    tab[0] = tab[1] = tab[2] = c;
+  const Fr eq = q == 0 ? e0 : (q == 1 ? fr_add(e0, fr_add(d, d)) : fr_add(fr_add(e0, fr_add(d, d)), d));
+  const Fr half_t = L->half_t;
+  Fr gq = fr_zero(), ht = fr_zero();
+  if (lane < 3) {
+    const Fr alpha = L->alpha;
+    Fr tab;
+    if (jr) {  // (N/D) (alpha^2 c'_t eqf(u_t, X) U_X - V_X)
+      const Fr ac2 = mont_mul_ni(mont_mul_ni(alpha, alpha), L->ctj);
+      tab = mont_mul_ni(L->c_nd, fr_sub(mont_mul_ni(mont_mul_ni(ac2, eq), accb[q]), accb[3 + q]));
+    } else {
+      ht = mont_mul_ni(half_t, L->inv2);
+      tab = mont_mul_ni(ht, L->Cb);
+    }
+    const Fr ac = mont_mul_ni(alpha, L->ct);
+    gq = fr_add(fr_add(mont_mul_ni(mont_mul_ni(ac, eq), acc[q]), acc[3 + q]), tab);
   }
-  const Fr ac = mont_mul_ni(alpha, L->ct);
-  g[0] = fr_add(fr_add(mont_mul_ni(mont_mul_ni(ac, e0), acc[0]), acc[3]), tab[0]);
-  g[2] = fr_add(fr_add(mont_mul_ni(mont_mul_ni(ac, e2), acc[1]), acc[4]), tab[1]);
-  g[3] = fr_add(fr_add(mont_mul_ni(mont_mul_ni(ac, e3), acc[2]), acc[5]), tab[2]);
-  g[1] = fr_sub(L->claim, g[0]);
+  __syncwarp();
+  if (!jr && lane == 0) L->half_t = ht;
+  Fr G[4];
+#pragma unroll
+  for (int l = 0; l < 8; l++) {
+    G[0].v[l] = __shfl_sync(0xffffffffu, gq.v[l], 0);
+    G[2].v[l] = __shfl_sync(0xffffffffu, gq.v[l], 1);
+    G[3].v[l] = __shfl_sync(0xffffffffu, gq.v[l], 2);
+  }
+  G[1] = fr_sub(L->claim, G[0]);
+  const Fr mine = lane == 0 ? G[0] : (lane == 1 ? G[1] : (lane == 2 ? G[2] : G[3]));
+  Fr c = fr_zero();
+  if (lane < 4) {
+    c = from_mont_ni(mine);
+    for (int l = 0; l < 8; l++) out->g[t - 1][lane].limb[l] = c.v[l];
+    gsh[lane] = mine;
+  }
   Fr gc[3];
-  for (int i = 0; i < 4; i++) {
-    const Fr c = from_mont_ni(g[i]);
-    for (int l = 0; l < 8; l++) out->g[t - 1][i].limb[l] = c.v[l];
-    if (i != 1) gc[i == 0 ? 0 : i - 1] = c;
+#pragma unroll
+  for (int l = 0; l < 8; l++) {
+    gc[0].v[l] = __shfl_sync(0xffffffffu, c.v[l], 0);
+    gc[1].v[l] = __shfl_sync(0xffffffffu, c.v[l], 2);
+    gc[2].v[l] = __shfl_sync(0xffffffffu, c.v[l], 3);
   }
-  uint32_t S[8];
-  for (int i = 0; i < 8; i++) S[i] = L->St[i];
-  dev_absorb_fr<3>(S, LBL_G, gc);
-  for (int i = 0; i < 8; i++) Sw[i] = S[i];
+  if (lane == 0) {
+    uint32_t S[8];
+    for (int i = 0; i < 8; i++) S[i] = L->St[i];
+    dev_absorb_fr<3>(S, LBL_G, gc);
+    for (int i = 0; i < 8; i++) Sw[i] = S[i];
+  }
+  __syncwarp();
 }
 
-// After the squeeze of r_t (thread 0): store r_t and the state, fold c_t,
-// the new claim g(r_t).
-__device__ void lk_step_r(LkDev* L, int t, const Fr& r, const uint32_t (&Sn)[8], const Fr (&g)[4]) {
-  L->r[t - 1] = r;
-  for (int i = 0; i < 8; i++) L->St[i] = Sn[i];
+// After the squeeze of r_t, by warp 0: store r_t and the state, fold c_t
+// (and c'_t for a table variable) by eqf(u_t, r_t), and the new claim
+// g(r_t) = sum_i g(i) L_i(r_t) over the nodes 0..3, lane i forming L_i and
+// its term (the same products as a serial evaluation, in another order).
+__device__ void lk_step_r(LkDev* L, int t, const Fr& r, const uint32_t* Sn, const Fr* gsh) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    L->r[t - 1] = r;
+    for (int i = 0; i < 8; i++) L->St[i] = Sn[i];
+  }
   const Fr ut = L->u[t - 1], one = fr_r1();
-  const Fr ef = fr_add(mont_mul_ni(ut, r), mont_mul_ni(fr_sub(one, ut), fr_sub(one, r)));
-  L->ct = mont_mul_ni(L->ct, ef);
-  if (t > L->L - L->log2_n) L->ctj = mont_mul_ni(L->ctj, ef);  // a table variable
-  L->claim = lk_cubic(g, r, L->inv2, L->inv6);
+  // eqf(u_t, r) = u r + (1 - u)(1 - r): the two products on lanes 0, 1
+  Fr part = fr_zero();
+  if (lane < 2) part = lane == 0 ? mont_mul_ni(ut, r) : mont_mul_ni(fr_sub(one, ut), fr_sub(one, r));
+  Fr ef;
+#pragma unroll
+  for (int l = 0; l < 8; l++) ef.v[l] = __shfl_sync(0xffffffffu, part.v[l], 1);
+  ef = fr_add(part, ef);  // valid in lane 0
+#pragma unroll
+  for (int l = 0; l < 8; l++) ef.v[l] = __shfl_sync(0xffffffffu, ef.v[l], 0);
+  const bool tabvar = t > L->L - L->log2_n;
+  if (lane == 0) L->ct = mont_mul_ni(L->ct, ef);
+  if (lane == 1 && tabvar) L->ctj = mont_mul_ni(L->ctj, ef);
+  // Lagrange weights over the nodes 0..3 at r:
+  //   L0 = -(r-1)(r-2)(r-3)/6, L1 = r(r-2)(r-3)/2, L2 = -r(r-1)(r-3)/2, L3 = r(r-1)(r-2)/6
+  const Fr two = fr_add(one, one), three = fr_add(two, one);
+  const Fr r1 = fr_sub(r, one), r2 = fr_sub(r, two), r3 = fr_sub(r, three);
+  Fr term = fr_zero();
+  if (lane < 4) {
+    const Fr x = lane == 0 ? r1 : r, y = lane == 1 ? r2 : (lane == 0 ? r2 : r1);
+    const Fr z = lane == 3 ? r2 : r3;
+    const Fr inv = (lane == 0 || lane == 3) ? L->inv6 : L->inv2;
+    Fr li = mont_mul_ni(mont_mul_ni(mont_mul_ni(x, y), z), inv);
+    if (lane == 0 || lane == 2) li = fr_neg(li);
+    term = mont_mul_ni(gsh[lane], li);
+  }
+  Fr t1, t2, t3;
+#pragma unroll
+  for (int l = 0; l < 8; l++) {
+    t1.v[l] = __shfl_sync(0xffffffffu, term.v[l], 1);
+    t2.v[l] = __shfl_sync(0xffffffffu, term.v[l], 2);
+    t3.v[l] = __shfl_sync(0xffffffffu, term.v[l], 3);
+  }
+  if (lane == 0) L->claim = fr_add(fr_add(fr_add(term, t1), t2), t3);
+  __syncwarp();
 }
 
 // The table side's cube sum Cb = alpha^2 X1 - X2 from the table kernel's
@@ -296,21 +342,10 @@ __global__ void __launch_bounds__(LK_ROUND_THREADS) lk_round_kernel(LkDev* Ls, i
   }
   block_sum_fr<6>(acc, red);
   if (jr) block_sum_fr<6>(accb, red);
-  if (tid == 0) {
-    Fr g[4];
-    uint32_t S[8];
-    lk_step_g(L, t, acc, accb, jr, outs + blockIdx.x, g, S);
-    for (int i = 0; i < 4; i++) gsh[i] = g[i];
-    for (int i = 0; i < 8; i++) Sw[i] = S[i];
-  }
+  if (tid < 32) lk_step_g(L, t, acc, accb, jr, outs + blockIdx.x, gsh, Sw);
   __syncthreads();
   squeeze_dev(Sw, LBL_R, 1, rch, Sn, dig);
-  if (tid == 0) {
-    const Fr g[4] = {gsh[0], gsh[1], gsh[2], gsh[3]};
-    uint32_t S[8];
-    for (int i = 0; i < 8; i++) S[i] = Sn[i];
-    lk_step_r(L, t, rch[0], S, g);
-  }
+  if (tid < 32) lk_step_r(L, t, rch[0], Sn, gsh);
 }
 
 // The final evaluations (the last pair folded with r_L), absorb 'f', the
@@ -394,21 +429,10 @@ __global__ void __launch_bounds__(LK_TAIL_THREADS, LK_TAIL_MINB) lk_tail_kernel(
     if (jr && tj == 1) lk_mode0_sums(accb);
     block_sum_fr<6>(acc, red);
     if (jr) block_sum_fr<6>(accb, red);
-    if (tid == 0) {
-      Fr g[4];
-      uint32_t S[8];
-      lk_step_g(L, t, acc, accb, jr, out, g, S);
-      for (int i = 0; i < 4; i++) gsh[i] = g[i];
-      for (int i = 0; i < 8; i++) Sw[i] = S[i];
-    }
+    if (tid < 32) lk_step_g(L, t, acc, accb, jr, out, gsh, Sw);
     __syncthreads();
     squeeze_dev(Sw, LBL_R, 1, rch, Sn, dig);
-    if (tid == 0) {
-      const Fr g[4] = {gsh[0], gsh[1], gsh[2], gsh[3]};
-      uint32_t S[8];
-      for (int i = 0; i < 8; i++) S[i] = Sn[i];
-      lk_step_r(L, t, rch[0], S, g);
-    }
+    if (tid < 32) lk_step_r(L, t, rch[0], Sn, gsh);
     __syncthreads();  // r_t and the folded vectors are visible to the next round
   }
   lk_finish(L, out);
