@@ -27,9 +27,6 @@
 // partial sums of g(0), g(2), g(3)) and a transcript step per proof; finish.
 // A never exists as a vector: its entries are gathered from B by value
 // (A_k = B_{S_k - t0}), and S' from T'.
-#ifndef LK_TAIL_MUL_INLINE
-#define LK_MUL mont_mul_ni  // the tail and setup kernels: one out-of-line product (instruction cache)
-#endif
 #include "lookup_dev.cuh"
 
 namespace vl {
@@ -419,7 +416,7 @@ __global__ void __launch_bounds__(LK_TAIL_THREADS, LK_TAIL_MINB) lk_tail_kernel(
     for (int i = 0; i < 6; i++) acc[i] = accb[i] = fr_zero();
     for (int k = tid; k < h; k += blockDim.x) {
       Fr f = q.f_tab[k & q.f_mask];
-      if (q.high) f = mont_mul(f, q.hi_tab[k >> L->sE]);
+      if (q.high) f = mont_mul_ni(f, q.hi_tab[k >> L->sE]);
       if (t == 1) lk_pair_a<0>(L, t, k, h, f, acc);
       else if (t == 2) lk_pair_a<1>(L, t, k, h, f, acc);
       else lk_pair_a<2>(L, t, k, h, f, acc);

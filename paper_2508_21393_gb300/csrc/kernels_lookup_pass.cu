@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(LK_THREADS, LK_PASS_MINB) lk_pass_kernel(LkDev
 #pragma unroll 1
   for (int k = kw + (threadIdx.x & 31); k < min(it.k1, kw + 32 * LK_PPT); k += 32) {
     Fr f = q.f_tab[k & q.f_mask];
-    if (q.high && !lane_factor) f = mont_mul(f, q.hi_tab[k >> L->sE]);
+    if (q.high && !lane_factor) f = mont_mul_ni(f, q.hi_tab[k >> L->sE]);
     lk_pair_a<MODE>(L, t, k, h, f, acc);
     if constexpr (JR) lk_pair_b(L, t, tj, k, h, f, accb);
   }

@@ -66,18 +66,19 @@ cudaError_t launch_rounds(const DevProof* proofs, int nproofs, vl_proof* out, in
 namespace vl {
 namespace {
 
-// accum_g and fold1 with the Montgomery product inlined: the three products
-// of a pair are independent, and inlined the compiler interleaves them.
+// accum_g and fold1 of the batched passes (the one out-of-line copy of the
+// Montgomery product: an inlined copy per call made the kernel larger than
+// the instruction cache).
 __device__ __forceinline__ void accum_g_inl(Fr (&g)[3], const Fr& a0, const Fr& a1, const Fr& b0, const Fr& b1) {
-  const Fr p0 = mont_mul(a0, b0), p1 = mont_mul(a1, b1);
-  const Fr p2 = mont_mul(fr_sub(fr_dbl(a1), a0), fr_sub(fr_dbl(b1), b0));
+  const Fr p0 = mont_mul_ni(a0, b0), p1 = mont_mul_ni(a1, b1);
+  const Fr p2 = mont_mul_ni(fr_sub(fr_dbl(a1), a0), fr_sub(fr_dbl(b1), b0));
   g[0] = fr_add(g[0], p0);
   g[1] = fr_add(g[1], p1);
   g[2] = fr_add(g[2], p2);
 }
 
 __device__ __forceinline__ Fr fold1_inl(const Fr& x0, const Fr& x1, const Fr& r) {
-  return fr_add(x0, mont_mul(r, fr_sub(x1, x0)));
+  return fr_add(x0, mont_mul_ni(r, fr_sub(x1, x0)));
 }
 
 __global__ void __launch_bounds__(RB_THREADS, 4) rounds_pass_kernel(const DevProof* __restrict__ proofs,
