@@ -74,6 +74,26 @@ __global__ void __launch_bounds__(LK_THREADS) lk_start_kernel(LkDev* Ls) {
   }
 }
 
+// eq table over nv <= 8 variables x[0..nv) (MSB first) into tab[0..2^nv),
+// block-wide: doubling, each level appending the next variable as the new
+// lowest bit (one product per new entry).
+__device__ void lk_eq_small(Fr* tab, const Fr* x, int nv) {
+  if (threadIdx.x == 0) tab[0] = fr_r1();
+  __syncthreads();
+  for (int l = 0; l < nv; l++) {
+    const int j = threadIdx.x;
+    Fr a = fr_zero();
+    if (j < (1 << l)) a = tab[j];
+    __syncthreads();
+    if (j < (1 << l)) {
+      const Fr xl = x[l];
+      tab[2 * j] = mont_mul_ni(a, fr_sub(fr_r1(), xl));
+      tab[2 * j + 1] = mont_mul_ni(a, xl);
+    }
+    __syncthreads();
+  }
+}
+
 // Suffix eq tables: item.slot 0 = loP (levels m = 0..sE: eq over the last
 // m variables of u), 1 = hiP (levels m = 0..L-sE-1: eq over the last m of
 // the first L - sE variables), 2 = eq(u_low, .) into WE (the last log2 N).
@@ -82,17 +102,23 @@ __global__ void __launch_bounds__(LK_THREADS) lk_start_kernel(LkDev* Ls) {
 __global__ void __launch_bounds__(LK_THREADS) lk_factor_kernel(LkDev* Ls, const LkItem* items) {
   const LkItem it = items[blockIdx.x];
   LkDev* L = Ls + it.proof;
-  Fr* out = it.slot == 0 ? L->loP : it.slot == 1 ? L->hiP : L->WE;
+  if (it.slot == 2) {
+    // eq(u_low, i) over the last n = log2 N variables, MSB first, as
+    // hi[i >> s] . lo[i mod 2^s]: lo over the last s = min(n, 8) variables,
+    // hi over the n - s before them (both at most 256 entries, built in
+    // shared memory), then one product per entry instead of n.
+    __shared__ Fr lo[256], hi[256];
+    const int nb = L->log2_n, sl = nb < 8 ? nb : 8;
+    lk_eq_small(lo, L->u + (L->L - sl), sl);
+    lk_eq_small(hi, L->u + (L->L - nb), nb - sl);
+    for (int e = it.k0 + threadIdx.x; e < it.k1; e += blockDim.x)
+      L->WE[e] = mont_mul_ni(hi[e >> sl], lo[e & ((1 << sl) - 1)]);
+    return;
+  }
+  Fr* out = it.slot == 0 ? L->loP : L->hiP;
   const int top = it.slot == 1 ? L->L - L->sE : L->L;  // the suffixes end at variable top - 1 (0-based)
   for (int e = it.k0 + threadIdx.x; e < it.k1; e += blockDim.x) {
-    int m, i;
-    if (it.slot == 2) {
-      m = L->log2_n;
-      i = e;
-    } else {
-      m = 31 - __clz(e + 1);
-      i = e + 1 - (1 << m);
-    }
+    const int m = 31 - __clz(e + 1), i = e + 1 - (1 << m);
     Fr acc = fr_r1();
     for (int t = 0; t < m; t++) {
       const Fr& x = L->u[top - m + t];
